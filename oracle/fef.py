@@ -1,0 +1,288 @@
+"""CPU oracle: the fragment-effective-field (FEF) mean field, plain NumPy in FP64.
+
+TEST INFRASTRUCTURE ONLY: only the tests, the smoke check and the CPU-baseline leg of the
+benchmark may import this module.  It shares no code with the CUDA library.
+
+Follows the paper's Theory section, "Fragment Mean Field":
+
+* product ansatz with the antisymmetriser dropped (Eq. prodspace): each fragment x has its own
+  determinant in its own monomer-centred AO basis, and there is no inter-fragment exchange;
+* the polarisation-screened fragment Fock matrix F~ = h(1) + (2J - K) + omega_x; in AO form with
+  D = 2 C_occ C_occ^T this is F^x = h^x + G[D^x] + omega_x with G[D] = J[D] - K[D]/2;
+* omega_x = h~ + 2 v (Eq. wc): h~ is the attraction of x's electrons to the nuclei of every other
+  fragment (equation after Eq. wc) and 2 v^{mu j}_{nu j} with v from Eq. dp2e equals the Coulomb
+  matrix J[D^y] of each other fragment's density, J[D^y]_{mu nu} = sum_{lambda sigma in y}
+  (mu nu|lambda sigma) D^y_{lambda sigma};
+* the field is "fully relaxed to infinite order": every fragment's RHF is solved in the field of
+  the others and the field is rebuilt until all fragments are self-consistent;
+* energies from the reference expectation values <H_x> and <H_xy> of the Hamiltonian partition
+  (Eqs. NHx, NHxy, clusterH), with pairs counted once.
+
+Readings of points the paper leaves open (units bohr/hartree, h(1) with own nuclei only, the
+cutoff dropping J and V of a fragment together, Schwarz screening at shell level, unordered pair
+sums, canonical orthogonalisation, nested macro/micro iteration) are the ones listed in the design
+notes of this repository.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+from synth.systems import ANGSTROM_PER_BOHR, frag_n_occ
+from . import integrals as I
+
+
+def canonical_orthogonaliser(S: np.ndarray, s_min: float = 1e-7) -> np.ndarray:
+    """X = U s^{-1/2} over eigenvalues s >= s_min of S, so that X^T S X = 1."""
+    s, U = np.linalg.eigh(S)
+    keep = s >= s_min
+    return U[:, keep] / np.sqrt(s[keep])
+
+
+def density_from_orbitals(C_occ: np.ndarray) -> np.ndarray:
+    return 2.0 * C_occ @ C_occ.T
+
+
+def orthonormal_density(G: np.ndarray, S: np.ndarray) -> np.ndarray:
+    """D = 2 C C^T with C = G (G^T S G)^{-1/2}, i.e. occupied orbitals orthonormal in the S metric."""
+    M = G.T @ S @ G
+    w, V = np.linalg.eigh(M)
+    C = G @ (V / np.sqrt(w)) @ V.T
+    return density_from_orbitals(C)
+
+
+def coulomb(eri: np.ndarray, D: np.ndarray) -> np.ndarray:
+    """J[D]_{mu nu} = sum_{lambda sigma} (mu nu|lambda sigma) D_{lambda sigma}."""
+    n1 = eri.shape[0]
+    return (eri.reshape(n1 * n1, -1) @ D.ravel()).reshape(n1, n1)
+
+
+def exchange(eri: np.ndarray, D: np.ndarray) -> np.ndarray:
+    """K[D]_{mu nu} = sum_{lambda sigma} (mu lambda|nu sigma) D_{lambda sigma}."""
+    return np.einsum("mlns,ls->mn", eri, D, optimize=True)
+
+
+def nuclear_repulsion(Z1, R1, Z2=None, R2=None) -> float:
+    """sum over distinct nucleus pairs Z_A Z_B / R_AB (within one set, or between two sets)."""
+    if Z2 is None:
+        e = 0.0
+        for a in range(len(Z1)):
+            for b in range(a):
+                e += Z1[a] * Z1[b] / np.linalg.norm(R1[a] - R1[b])
+        return e
+    e = 0.0
+    for a in range(len(Z1)):
+        for b in range(len(Z2)):
+            e += Z1[a] * Z2[b] / np.linalg.norm(R1[a] - R2[b])
+    return e
+
+
+class Fragments:
+    """All integrals of a fragmented system the FEF mean field needs, held in memory.
+
+    cutoff_A: fragment pairs whose minimum inter-fragment atom-atom distance is not below the
+    cutoff are dropped (both J and V).  None keeps all pairs.
+    schwarz: shell quartets with Q_ab Q_cd < schwarz are dropped (0 keeps all).
+    """
+
+    def __init__(self, system, cutoff_A: float | None = None, schwarz: float = 0.0, inter: bool = True):
+        self.system = system
+        self.nf = system.n_frag
+        self.schwarz_tau = schwarz
+        self.shells = [I.fragment_shells(system, x) for x in range(self.nf)]
+        self.n_ao = [s.n_ao for s in self.shells]
+        self.n_occ = [frag_n_occ(system, x) for x in range(self.nf)]
+        self.atoms = [system.frag_atoms(x) for x in range(self.nf)]
+        self.Zn = [system.Z[a].astype(np.float64) for a in self.atoms]
+        self.Rn = [system.xyz[a] / ANGSTROM_PER_BOHR for a in self.atoms]
+        self.S = [s.overlap() for s in self.shells]
+        self.T = [s.kinetic() for s in self.shells]
+        self.Vown = [self.shells[x].nuclear(self.Rn[x], self.Zn[x]) for x in range(self.nf)]
+        self.h = [self.T[x] + self.Vown[x] for x in range(self.nf)]
+        self.X = [canonical_orthogonaliser(S) for S in self.S]
+        self.Q = [s.schwarz() for s in self.shells]
+        self.E_nn_intra = [nuclear_repulsion(self.Zn[x], self.Rn[x]) for x in range(self.nf)]
+        self.eri_intra = [I.eri_block(s, s, Q, Q, schwarz) if schwarz > 0 else I.eri_block(s, s)
+                          for s, Q in zip(self.shells, self.Q)]
+        self.pairs = self.neighbour_pairs(cutoff_A)
+        self.nbr = [[] for _ in range(self.nf)]
+        for x, y in self.pairs:
+            self.nbr[x].append(y)
+            self.nbr[y].append(x)
+        # V^y on x for every neighbour y (directed), and the inter-fragment ERI block per pair
+        self.V = {}
+        self.eri = {}
+        self.E_nn = {}
+        if inter:
+            for x, y in self.pairs:
+                self.V[(x, y)] = self.shells[x].nuclear(self.Rn[y], self.Zn[y])
+                self.V[(y, x)] = self.shells[y].nuclear(self.Rn[x], self.Zn[x])
+                self.E_nn[(x, y)] = nuclear_repulsion(self.Zn[x], self.Rn[x], self.Zn[y], self.Rn[y])
+                if schwarz > 0:
+                    self.eri[(x, y)] = I.eri_block(self.shells[x], self.shells[y], self.Q[x], self.Q[y], schwarz)
+                else:
+                    self.eri[(x, y)] = I.eri_block(self.shells[x], self.shells[y])
+
+    def neighbour_pairs(self, cutoff_A):
+        pairs = []
+        xyz = self.system.xyz
+        for x in range(self.nf):
+            for y in range(x + 1, self.nf):
+                if cutoff_A is None:
+                    pairs.append((x, y))
+                    continue
+                d = np.linalg.norm(xyz[self.atoms[x]][:, None, :] - xyz[self.atoms[y]][None, :, :], axis=-1)
+                if d.min() < cutoff_A:
+                    pairs.append((x, y))
+        return pairs
+
+    def shell_quartets(self) -> int:
+        """Inter-fragment shell quartets (a<=b in x, c<=d in y, x<y) surviving screening."""
+        tau = self.schwarz_tau
+        return sum(I.count_quartets(self.shells[x], self.shells[y], self.Q[x], self.Q[y], tau)
+                   for x, y in self.pairs)
+
+    # ------------------------------------------------------------------------------------ Fock
+
+    def G(self, x: int, D: np.ndarray) -> np.ndarray:
+        """(2J - K) in AO form: G[D] = J[D] - K[D]/2 over the fragment's own AOs."""
+        e = self.eri_intra[x]
+        return coulomb(e, D) - 0.5 * exchange(e, D)
+
+    def omega(self, Ds) -> list:
+        """omega_x = sum_{y in N(x)} (V^y + J[D^y]) for every fragment x."""
+        om = [np.zeros((n, n)) for n in self.n_ao]
+        for x, y in self.pairs:
+            e = self.eri[(x, y)]
+            nx, ny = self.n_ao[x], self.n_ao[y]
+            M = e.reshape(nx * nx, ny * ny)
+            om[x] += self.V[(x, y)] + (M @ Ds[y].ravel()).reshape(nx, nx)
+            om[y] += self.V[(y, x)] + (M.T @ Ds[x].ravel()).reshape(ny, ny)
+        return om
+
+    def fock(self, Ds) -> list:
+        """F^x = h^x + G[D^x] + omega_x for every fragment."""
+        om = self.omega(Ds)
+        return [self.h[x] + self.G(x, Ds[x]) + om[x] for x in range(self.nf)]
+
+    # ------------------------------------------------------------------------------------ RHF
+
+    def rhf(self, x: int, omega: np.ndarray, D0=None, max_iter: int = 200, diis_size: int = 8,
+            e_tol: float = 1e-11, comm_tol: float = 1e-9):
+        """Fragment RHF in a frozen field omega: F = h + omega + G[D], F C = S C eps.
+
+        Canonical orthogonalisation, aufbau occupation of the lowest n_occ orbitals, DIIS (Pulay)
+        on the commutator e = F D S - S D F.  Start: D0, else the core guess (F = h + omega).
+        Returns (D, F, E_scf, iterations, converged).
+        """
+        S, X, h = self.S[x], self.X[x], self.h[x]
+        nocc = self.n_occ[x]
+        hw = h + omega
+
+        def diag(F):
+            eps, Cp = np.linalg.eigh(X.T @ F @ X)
+            C = X @ Cp
+            return density_from_orbitals(C[:, :nocc])
+
+        D = diag(hw) if D0 is None else D0
+        Fs, es = [], []
+        E_old = None
+        for it in range(1, max_iter + 1):
+            F = hw + self.G(x, D)
+            E = 0.5 * np.sum(D * (hw + F)) + self.E_nn_intra[x]
+            err = F @ D @ S - S @ D @ F
+            derr = np.abs(err).max()
+            if E_old is not None and abs(E - E_old) < e_tol and derr < comm_tol:
+                return D, F, E, it, True
+            E_old = E
+            Fs.append(F)
+            es.append(X.T @ err @ X)
+            if len(Fs) > diis_size:
+                Fs.pop(0)
+                es.pop(0)
+            Fx = F
+            m = len(Fs)
+            if m >= 2:
+                B = -np.ones((m + 1, m + 1))
+                B[m, m] = 0.0
+                for i in range(m):
+                    for j in range(m):
+                        B[i, j] = np.sum(es[i] * es[j])
+                rhs = np.zeros(m + 1)
+                rhs[m] = -1.0
+                try:
+                    c = np.linalg.solve(B, rhs)[:m]
+                    Fx = sum(ci * Fi for ci, Fi in zip(c, Fs))
+                except np.linalg.LinAlgError:
+                    Fx = F
+            D = diag(Fx)
+        return D, F, E, max_iter, False
+
+    # ------------------------------------------------------------------------------------ energies
+
+    def energies(self, Ds) -> dict:
+        """Reference energies of the Hartree product.
+
+        E_x^int = tr[D^x (2 h^x + G[D^x])]/2 + sum_{A<B in x} Z_A Z_B / R_AB
+        E_xy    = tr[D^x V^y] + tr[D^y V^x] + tr[D^x J[D^y]] + sum_{A in x, B in y} Z_A Z_B / R_AB
+        E_tot   = sum_x E_x^int + sum_{pairs x<y} E_xy
+        E_x     = E_x^int + (1/2) sum_{y in N(x)} E_xy      (so that sum_x E_x = E_tot)
+        E_x^scf = E_x^int + tr[D^x omega_x]
+        """
+        nf = self.nf
+        E_int = np.array([0.5 * np.sum(Ds[x] * (2 * self.h[x] + self.G(x, Ds[x]))) + self.E_nn_intra[x]
+                          for x in range(nf)])
+        E_pair = {}
+        for x, y in self.pairs:
+            nx, ny = self.n_ao[x], self.n_ao[y]
+            Jxy = coulomb(self.eri[(x, y)], Ds[y])
+            E_pair[(x, y)] = (np.sum(Ds[x] * self.V[(x, y)]) + np.sum(Ds[y] * self.V[(y, x)]) +
+                              np.sum(Ds[x] * Jxy) + self.E_nn[(x, y)])
+        E_x = E_int.copy()
+        for (x, y), e in E_pair.items():
+            E_x[x] += 0.5 * e
+            E_x[y] += 0.5 * e
+        om = self.omega(Ds)
+        E_scf = np.array([E_int[x] + np.sum(Ds[x] * om[x]) for x in range(nf)])
+        E_tot = float(E_int.sum() + sum(E_pair.values()))
+        return dict(E_int=E_int, E_pair=E_pair, E_x=E_x, E_tot=E_tot, E_scf=E_scf)
+
+    # ------------------------------------------------------------------------------------ FEF loop
+
+    def isolated(self, **kw):
+        """Isolated-fragment RHF densities (omega = 0): the superposition start."""
+        out = []
+        for x in range(self.nf):
+            D, F, E, it, ok = self.rhf(x, np.zeros_like(self.h[x]), **kw)
+            if not ok:
+                raise RuntimeError(f"isolated RHF of fragment {x} did not converge")
+            out.append(D)
+        return out
+
+    def solve(self, D0=None, e_tol: float = 1e-8, max_macro: int = 100, **rhf_kw):
+        """FEF self-consistency.
+
+        D^(0): superposition of isolated-fragment RHF densities (or D0).  Macro-iteration k builds
+        omega^(k) from D^(k-1) of all fragments, then solves every fragment's RHF in its frozen
+        omega^(k) to get D^(k).  Stops when |dE_tot| < e_tol and max_x |dE_x| < e_tol.
+        Returns dict(D, F, energies, n_macro, converged, history).
+        """
+        Ds = self.isolated(**rhf_kw) if D0 is None else [d.copy() for d in D0]
+        En = self.energies(Ds)
+        history = [En["E_tot"]]
+        for k in range(1, max_macro + 1):
+            om = self.omega(Ds)
+            new = []
+            for x in range(self.nf):
+                D, F, E, it, ok = self.rhf(x, om[x], D0=Ds[x], **rhf_kw)
+                if not ok:
+                    raise RuntimeError(f"fragment {x} RHF in the field did not converge at macro {k}")
+                new.append(D)
+            Ds = new
+            En_new = self.energies(Ds)
+            history.append(En_new["E_tot"])
+            dE = abs(En_new["E_tot"] - En["E_tot"])
+            dEx = np.abs(En_new["E_x"] - En["E_x"]).max()
+            En = En_new
+            if dE < e_tol and dEx < e_tol:
+                return dict(D=Ds, F=self.fock(Ds), energies=En, n_macro=k, converged=True, history=history)
+        return dict(D=Ds, F=self.fock(Ds), energies=En, n_macro=max_macro, converged=False, history=history)

@@ -1,0 +1,413 @@
+"""Pins of the CPU oracle against things other than itself (CPU only).
+
+Each test names what fixes the expected value: a closed form, an identity of the mathematics,
+brute-force quadrature written independently in ``tests/quadrature.py``, a library routine, or an
+invariant of the method (Theory, "Fragment Mean Field").  The paper prints no numbers, so there is
+no printed-value pin.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import integrals as I
+from oracle.fef import Fragments, orthonormal_density, canonical_orthogonaliser
+from synth import systems as S
+from tests import quadrature as Q
+
+BOHR = S.ANGSTROM_PER_BOHR
+
+
+# ----------------------------------------------------------------------------------------- Boys
+
+def test_boys_at_zero():
+    """F_m(0) = 1/(2m+1)."""
+    F = I.boys(16, 0.0)
+    assert np.allclose(F, 1.0 / (2 * np.arange(17) + 1), rtol=0, atol=1e-16)
+
+
+@pytest.mark.parametrize("T", [1e-3, 0.3, 1.0, 4.7, 12.0, 29.99, 30.0, 30.01, 45.0, 120.0])
+def test_boys_f0_erf(T):
+    """F_0(T) = (1/2) sqrt(pi/T) erf(sqrt(T))."""
+    F = I.boys(0, T)
+    assert abs(F[0] - 0.5 * math.sqrt(math.pi / T) * math.erf(math.sqrt(T))) < 1e-15
+
+
+@pytest.mark.parametrize("T", [0.0, 0.5, 2.0, 7.3, 18.0, 29.9, 30.0, 33.0, 60.0])
+def test_boys_recursion_identity(T):
+    """F_m(T) = (2T F_{m+1}(T) + exp(-T)) / (2m+1) for m < 8."""
+    F = I.boys(8, T)
+    for m in range(8):
+        assert abs(F[m] - (2 * T * F[m + 1] + math.exp(-T)) / (2 * m + 1)) < 1e-15
+
+
+def test_boys_mpmath_quadrature():
+    """F_m(T) = int_0^1 t^(2m) exp(-T t^2) dt by 30-digit mpmath quadrature, m <= 8, T in [0, 60],
+    including both sides of the series / asymptotic switch at T = 30: |error| <= 1e-14."""
+    mp = pytest.importorskip("mpmath")
+    mp.mp.dps = 30
+    worst = 0.0
+    for T in [0.0, 0.01, 0.5, 1.0, 2.5, 5.0, 9.9, 15.0, 22.2, 29.5, 29.999, 30.0, 30.5, 37.0, 45.0, 60.0]:
+        F = I.boys(8, T)
+        for m in range(9):
+            ref = mp.quad(lambda t: t ** (2 * m) * mp.exp(-T * t * t), [0, 0.5, 1])
+            worst = max(worst, abs(F[m] - float(ref)))
+    assert worst <= 1e-14, worst
+
+
+# ----------------------------------------------------------------------------------------- closed forms
+
+def _s_prim(center, a):
+    return I.ShellSet(np.array([center]), [0], [np.array([a])], [np.array([1.0])])
+
+
+def test_closed_form_ss_one_electron():
+    """Szabo-Ostlund closed forms for normalised s primitives:
+    S = (4ab/p^2)^{3/4} e^{-mu R^2}; T = mu (3 - 2 mu R^2) S; V = -Z (2 pi/p) N_a N_b e^{-mu R^2} F_0(p R_PC^2)."""
+    A, B, C = np.array([0.1, -0.3, 0.7]), np.array([1.2, 0.4, -0.5]), np.array([-0.8, 0.9, 1.6])
+    a, b, Z = 1.7, 0.35, 3.0
+    ss = I.ShellSet(np.array([A, B]), [0, 0], [np.array([a]), np.array([b])], [np.array([1.0]), np.array([1.0])])
+    p, mu = a + b, a * b / (a + b)
+    R2 = np.sum((A - B) ** 2)
+    Na, Nb = (2 * a / math.pi) ** 0.75, (2 * b / math.pi) ** 0.75
+    Sab = Na * Nb * (math.pi / p) ** 1.5 * math.exp(-mu * R2)
+    Tab = mu * (3 - 2 * mu * R2) * Sab
+    P = (a * A + b * B) / p
+    T = p * np.sum((P - C) ** 2)
+    F0 = 0.5 * math.sqrt(math.pi / T) * math.erf(math.sqrt(T))
+    Vab = -Z * 2 * math.pi / p * Na * Nb * math.exp(-mu * R2) * F0
+    Sm, Tm, Vm = ss.overlap(), ss.kinetic(), ss.nuclear(C[None], [Z])
+    assert abs(Sm[0, 1] - Sab) < 1e-15 and abs(Sm[0, 0] - 1) < 1e-15
+    assert abs(Tm[0, 1] - Tab) < 1e-14
+    assert abs(Vm[0, 1] - Vab) < 1e-14
+
+
+def test_closed_form_ss_eri():
+    """(ss|ss) = N_a N_b N_c N_d 2 pi^{5/2} / (p q sqrt(p+q)) e^{-mu_ab R_AB^2} e^{-mu_cd R_CD^2} F_0(rho R_PQ^2)."""
+    A, B = np.array([0.0, 0.2, -0.4]), np.array([0.9, -0.6, 0.3])
+    C, D = np.array([2.1, 1.0, 0.5]), np.array([1.5, 2.2, -0.8])
+    a, b, c, d = 2.3, 0.41, 0.9, 5.5
+    s1 = I.ShellSet(np.array([A, B]), [0, 0], [np.array([a]), np.array([b])], [np.array([1.0])] * 2)
+    s2 = I.ShellSet(np.array([C, D]), [0, 0], [np.array([c]), np.array([d])], [np.array([1.0])] * 2)
+    e = I.eri_block(s1, s2)
+    p, q = a + b, c + d
+    P, Qc = (a * A + b * B) / p, (c * C + d * D) / q
+    rho = p * q / (p + q)
+    T = rho * np.sum((P - Qc) ** 2)
+    N = np.prod([(2 * x / math.pi) ** 0.75 for x in (a, b, c, d)])
+    ref = N * 2 * math.pi ** 2.5 / (p * q * math.sqrt(p + q)) * math.exp(-a * b / p * np.sum((A - B) ** 2)) \
+        * math.exp(-c * d / q * np.sum((C - D) ** 2)) * 0.5 * math.sqrt(math.pi / T) * math.erf(math.sqrt(T))
+    assert abs(e[0, 1, 0, 1] - ref) < 1e-15
+
+
+# ----------------------------------------------------------------------------------------- quadrature
+
+TINY = [
+    (np.array([0.0, 0.0, 0.0]), 1, [1.3, 0.4], [0.7, 0.5]),
+    (np.array([0.3, -0.9, 1.1]), 2, [0.9], [1.0]),
+    (np.array([-1.0, 0.5, 0.2]), 0, [2.0, 0.3], [0.4, 0.8]),
+]
+
+
+def _oracle_set(shells):
+    return I.ShellSet(np.array([s[0] for s in shells]), [s[1] for s in shells],
+                      [np.array(s[2]) for s in shells], [np.array(s[3]) for s in shells])
+
+
+def test_quadrature_overlap_kinetic():
+    """S and T (p, d, s shells, contracted) against Gauss-Hermite quadrature; T in gradient form."""
+    o, q = _oracle_set(TINY), Q.QShells(TINY)
+    assert np.abs(o.overlap() - Q.overlap(q)).max() < 1e-13
+    assert np.abs(o.kinetic() - Q.kinetic(q)).max() < 1e-12
+
+
+def test_quadrature_nuclear():
+    """V against quadrature of the Gaussian transform of 1/r, two point charges."""
+    o, q = _oracle_set(TINY), Q.QShells(TINY)
+    C = np.array([[0.4, 0.4, -0.7], [-1.5, 1.0, 0.9]])
+    Z = [8.0, 1.0]
+    assert np.abs(o.nuclear(C, Z) - Q.nuclear(q, C, Z)).max() < 1e-11
+
+
+def test_quadrature_eri_sp_d():
+    """(mu nu|lambda sigma) with p/s bra shells and d/s ket shells against quadrature of the
+    Gaussian transform of 1/r12 (2D Gauss-Hermite per Cartesian direction)."""
+    bra = [TINY[0], TINY[2]]
+    ket = [TINY[1], (np.array([0.8, 0.1, -0.6]), 0, [0.6], [1.0])]
+    ob, ok = _oracle_set(bra), _oracle_set(ket)
+    qb, qk = Q.QShells(bra), Q.QShells(ket)
+    e_or = I.eri_block(ob, ok)
+    e_q = Q.eri(qb, qk)
+    assert np.abs(e_or - e_q).max() < 1e-11
+
+
+def test_quadrature_eri_dd():
+    """A (dd|dd)-containing block, one primitive, against quadrature."""
+    sh = [(np.array([0.0, 0.0, 0.0]), 2, [0.7], [1.0]), (np.array([0.5, -0.4, 0.9]), 2, [1.1], [1.0])]
+    o, q = _oracle_set(sh[:1]), Q.QShells(sh[:1])
+    o2, q2 = _oracle_set(sh[1:]), Q.QShells(sh[1:])
+    assert np.abs(I.eri_block(o, o2) - Q.eri(q, q2)).max() < 1e-11
+
+
+# ----------------------------------------------------------------------------------------- invariants
+
+@pytest.fixture(scope="module")
+def dimer():
+    return S.water_dimer(0)
+
+
+@pytest.fixture(scope="module")
+def dimer_frags(dimer):
+    return Fragments(dimer)
+
+
+def test_eri_eightfold_symmetry(dimer_frags):
+    e = dimer_frags.eri_intra[0]
+    for perm in [(1, 0, 2, 3), (0, 1, 3, 2), (2, 3, 0, 1), (3, 2, 1, 0)]:
+        assert np.abs(e - e.transpose(perm)).max() < 1e-13
+    x = dimer_frags.eri[(0, 1)]
+    y = I.eri_block(dimer_frags.shells[1], dimer_frags.shells[0])
+    assert np.abs(x - y.transpose(2, 3, 0, 1)).max() < 1e-13
+
+
+def test_schwarz_and_psd(dimer_frags):
+    """The pair-ERI matrix M_(mu nu),(lambda sigma) is positive semidefinite and obeys Schwarz."""
+    e = dimer_frags.eri_intra[0]
+    n = e.shape[0]
+    M = e.reshape(n * n, n * n)
+    w = np.linalg.eigvalsh(M)
+    assert w.min() > -1e-12 * w.max()
+    d = np.sqrt(np.abs(np.diag(M)))
+    assert np.all(np.abs(M) <= np.outer(d, d) * (1 + 1e-12) + 1e-15)
+
+
+def test_unit_self_overlap(dimer_frags):
+    for Sm in dimer_frags.S:
+        assert np.abs(np.diag(Sm) - 1).max() < 1e-14
+
+
+def test_translation_invariance(dimer):
+    sh0 = I.fragment_shells(dimer, 0)
+    shifted = S.System(**{**dimer.__dict__, "xyz": dimer.xyz + np.array([3.3, -1.2, 7.0])})
+    sh1 = I.fragment_shells(shifted, 0)
+    assert np.abs(sh0.kinetic() - sh1.kinetic()).max() < 1e-12
+    C0 = dimer.xyz[3:] / BOHR
+    assert np.abs(sh0.nuclear(C0, [8, 1, 1]) - sh1.nuclear(C0 + np.array([3.3, -1.2, 7.0]) / BOHR, [8, 1, 1])).max() < 1e-12
+    assert np.abs(I.eri_block(sh0, sh0) - I.eri_block(sh1, sh1)).max() < 1e-12
+
+
+def _rot_block(system, x, R):
+    """AO transformation for s and p shells under a rotation R (p components as a vector)."""
+    blocks = []
+    for a in system.frag_atoms(x):
+        bs = system.basis_sets[system.basis_of_atom[a]]
+        for l in bs.l:
+            blocks.append(np.eye(1) if l == 0 else R)
+    n = sum(b.shape[0] for b in blocks)
+    B = np.zeros((n, n))
+    i = 0
+    for b in blocks:
+        B[i:i + b.shape[0], i:i + b.shape[0]] = b
+        i += b.shape[0]
+    return B
+
+
+def test_rotation_covariance_sp(dimer):
+    """Rotating the molecule by R: s blocks invariant, p blocks transform as vectors, S' = B S B^T."""
+    R = S.random_rotation(np.random.default_rng(5))
+    rot = S.System(**{**dimer.__dict__, "xyz": dimer.xyz @ R.T})
+    s0, s1 = I.fragment_shells(dimer, 0), I.fragment_shells(rot, 0)
+    B = _rot_block(dimer, 0, R)
+    for f in ("overlap", "kinetic"):
+        assert np.abs(B @ getattr(s0, f)() @ B.T - getattr(s1, f)()).max() < 1e-12
+    e0, e1 = I.eri_block(s0, s0), I.eri_block(s1, s1)
+    e0r = np.einsum("ai,bj,ck,dl,ijkl->abcd", B, B, B, B, e0, optimize=True)
+    assert np.abs(e0r - e1).max() < 1e-12
+
+
+def _ch_fragment(seed=3):
+    """A two-atom fragment: C with 3s2p1d, H with 2s (one cation to keep the electron count even)."""
+    rng = np.random.default_rng(seed)
+    bs = [S.random_basis_set(rng, S.SHELLS_HEAVY_SPD), S.random_basis_set(rng, S.SHELLS_H)]
+    return S.System(Z=np.array([6, 1], np.int32), xyz=np.array([[0.0, 0.0, 0.0], [0.7, 0.5, 0.6]]),
+                    frag_of_atom=np.array([0, 0], np.int32), charge=np.array([1], np.int32),
+                    basis_of_atom=np.array([0, 1], np.int32), basis_sets=bs)
+
+
+def test_rotation_invariants_with_d():
+    """With d shells (Cartesian d blocks do not transform orthogonally): the generalised eigenvalues
+    of (T, S) and (h, S), of the pair-ERI matrix in the S (x) S metric, and the isolated RHF energy
+    are invariant under a rigid rotation."""
+    import scipy.linalg
+    sysd = _ch_fragment()
+    R = S.random_rotation(np.random.default_rng(11))
+    rot = S.System(**{**sysd.__dict__, "xyz": sysd.xyz @ R.T})
+    f0, f1 = Fragments(sysd), Fragments(rot)
+    for mat in ("T", "h"):
+        a = scipy.linalg.eigh(getattr(f0, mat)[0], f0.S[0], eigvals_only=True)
+        b = scipy.linalg.eigh(getattr(f1, mat)[0], f1.S[0], eigvals_only=True)
+        assert np.abs(a - b).max() < 1e-11 * np.abs(a).max()
+    n = f0.n_ao[0]
+    w = []
+    for f in (f0, f1):
+        SS = np.kron(f.S[0], f.S[0])
+        w.append(scipy.linalg.eigh(f.eri_intra[0].reshape(n * n, n * n), SS + 1e-300, eigvals_only=True,
+                                   subset_by_index=[n * n - 40, n * n - 1]))
+    assert np.abs(w[0] - w[1]).max() < 1e-9 * np.abs(w[0]).max()
+    e0 = f0.rhf(0, np.zeros((n, n)))[2]
+    e1 = f1.rhf(0, np.zeros((n, n)))[2]
+    assert abs(e0 - e1) < 1e-9
+
+
+# ----------------------------------------------------------------------------------------- multipole limits
+
+def test_ss_far_limit():
+    """Two same-centre s-shell pairs far apart: (ab|cd) R -> S_ab S_cd (charge-charge limit)."""
+    sa = I.ShellSet(np.zeros((2, 3)), [0, 0], [np.array([1.1, 0.3]), np.array([0.5, 2.0])],
+                    [np.array([0.6, 0.8]), np.array([0.9, 0.4])])
+    for R in (40.0, 90.0):
+        sb = I.ShellSet(np.array([[0, 0, R], [0, 0, R]]), [0, 0], [np.array([0.7, 0.2]), np.array([3.0, 0.8])],
+                        [np.array([0.5, 0.5]), np.array([0.3, 0.9])])
+        e = I.eri_block(sa, sb)
+        Sa, Sb = sa.overlap(), sb.overlap()
+        assert abs(e[0, 1, 0, 1] * R - Sa[0, 1] * Sb[0, 1]) < 1e-13
+
+
+def test_water_pair_dipole_limit(dimer):
+    """E_xy of two neutral fragments with frozen isolated densities, translated apart along n:
+    E_xy -> dipole-dipole (mu_x.mu_y - 3 (mu_x.n)(mu_y.n)) / R^3, with the residual falling as R^-4.
+    Dipoles come from quadrature dipole integrals (tests/quadrature.py), not from the oracle."""
+    base = Fragments(dimer, inter=False)
+    D = base.isolated()
+    n = np.array([0.3, -0.5, 0.8])
+    n /= np.linalg.norm(n)
+    mus = []
+    for x in range(2):
+        atoms = dimer.frag_atoms(x)
+        cen = (dimer.Z[atoms][:, None] * dimer.xyz[atoms]).sum(0) / dimer.Z[atoms].sum() / BOHR
+        shells = []
+        for a in atoms:
+            bs = dimer.basis_sets[dimer.basis_of_atom[a]]
+            for l, e, c in zip(bs.l, bs.exps, bs.coefs):
+                shells.append((dimer.xyz[a] / BOHR, l, e, c))
+        M = Q.dipole(Q.QShells(shells), origin=cen)
+        nuc = (dimer.Z[atoms][:, None] * (dimer.xyz[atoms] / BOHR - cen)).sum(0)
+        mus.append(nuc - np.einsum("kij,ij->k", M, D[x]))
+    scaled = []
+    for R in (60.0, 120.0, 240.0):
+        moved = dimer.xyz.copy()
+        c0 = (dimer.Z[:3, None] * dimer.xyz[:3]).sum(0) / 10
+        c1 = (dimer.Z[3:, None] * dimer.xyz[3:]).sum(0) / 10
+        moved[3:] += (c0 - c1) + n * R * BOHR
+        fr = Fragments(S.System(**{**dimer.__dict__, "xyz": moved}))
+        Exy = fr.energies(D)["E_pair"][(0, 1)]
+        Edd = (mus[0] @ mus[1] - 3 * (mus[0] @ n) * (mus[1] @ n)) / R ** 3
+        assert abs(Exy - Edd) < 0.25 * abs(Edd)
+        scaled.append((Exy - Edd) * R ** 4)
+    # the residual is the dipole-quadrupole term: (E_xy - E_dd) R^4 is constant up to O(1/R)
+    assert abs(scaled[1] / scaled[0] - 1) < 0.01 and abs(scaled[2] / scaled[1] - 1) < 0.005
+
+
+# ----------------------------------------------------------------------------------------- SCF / FEF
+
+def test_config0_density_is_valid(dimer_frags):
+    """D = 2 C C^T with C = G (G^T S G)^{-1/2}: tr(DS) = N_e and D S D = 2 D."""
+    for x in range(2):
+        G = S.random_orbital_coefficients(100 + x, dimer_frags.n_ao[x], 5)
+        D = orthonormal_density(G, dimer_frags.S[x])
+        assert abs(np.trace(D @ dimer_frags.S[x]) - 10) < 1e-12
+        assert np.abs(D @ dimer_frags.S[x] @ D - 2 * D).max() < 1e-12
+
+
+def test_isolated_rhf_invariants(dimer_frags):
+    """Isolated-fragment RHF: tr(DS) = N_e, DSD = 2D, FDS - SDF = 0, and the orbital energies
+    from the oracle's orthogonalised problem equal scipy's generalised symmetric eigensolver."""
+    import scipy.linalg
+    D = dimer_frags.isolated()
+    for x in range(2):
+        Sx = dimer_frags.S[x]
+        F = dimer_frags.h[x] + dimer_frags.G(x, D[x])
+        assert abs(np.trace(D[x] @ Sx) - 10) < 1e-10
+        assert np.abs(D[x] @ Sx @ D[x] - 2 * D[x]).max() < 1e-10
+        assert np.abs(F @ D[x] @ Sx - Sx @ D[x] @ F).max() < 1e-8
+        X = dimer_frags.X[x]
+        if X.shape[1] == Sx.shape[0]:
+            e1 = np.linalg.eigvalsh(X.T @ F @ X)
+            e2 = scipy.linalg.eigh(F, Sx, eigvals_only=True)
+            assert np.abs(e1 - e2).max() < 1e-9
+
+
+def test_canonical_orthogonaliser_drops_dependence():
+    """X^T S X = 1, and an exactly duplicated function is dropped."""
+    rng = np.random.default_rng(0)
+    A = rng.standard_normal((6, 6))
+    Sm = A @ A.T + 6 * np.eye(6)
+    Sd = np.block([[Sm, Sm[:, :1]], [Sm[:1, :], Sm[:1, :1]]])
+    X = canonical_orthogonaliser(Sd)
+    assert X.shape == (7, 6)
+    assert np.abs(X.T @ Sd @ X - np.eye(6)).max() < 1e-12
+
+
+@pytest.fixture(scope="module")
+def dimer_solution(dimer_frags):
+    return dimer_frags.solve(e_tol=1e-11)
+
+
+def test_fef_fixed_point_commutators(dimer_frags, dimer_solution):
+    """At the FEF fixed point every fragment's full F^x = h + G + omega commutes with D^x in the S metric."""
+    D = dimer_solution["D"]
+    F = dimer_frags.fock(D)
+    for x in range(2):
+        Sx = dimer_frags.S[x]
+        assert np.abs(F[x] @ D[x] @ Sx - Sx @ D[x] @ F[x]).max() < 1e-7
+
+
+def test_energy_partition_sums(dimer_frags, dimer_solution):
+    En = dimer_solution["energies"]
+    assert abs(En["E_x"].sum() - En["E_tot"]) < 1e-10
+
+
+def test_pair_coulomb_symmetry(dimer_frags, dimer_solution):
+    """tr(D^x J[D^y]) = tr(D^y J[D^x]), built from the ERI blocks computed in each order."""
+    from oracle.fef import coulomb
+    D = dimer_solution["D"]
+    e01 = dimer_frags.eri[(0, 1)]
+    e10 = I.eri_block(dimer_frags.shells[1], dimer_frags.shells[0])
+    assert abs(np.sum(D[0] * coulomb(e01, D[1])) - np.sum(D[1] * coulomb(e10, D[0]))) < 1e-11
+
+
+def test_total_energy_stationary(dimer_frags, dimer_solution):
+    """E_tot is stationary at the fixed point (F^x = dE_tot/dD^x): an occupied-virtual rotation by
+    kappa changes E_tot by O(kappa^2)."""
+    D = dimer_solution["D"]
+    F = dimer_frags.fock(D)
+    E0 = dimer_frags.energies(D)["E_tot"]
+    x = 0
+    X = dimer_frags.X[x]
+    eps, Cp = np.linalg.eigh(X.T @ F[x] @ X)
+    C = X @ Cp
+    nocc = 5
+
+    def rotated(k):
+        Cn = C.copy()
+        i, a = nocc - 1, nocc + 1
+        Cn[:, i] = math.cos(k) * C[:, i] + math.sin(k) * C[:, a]
+        Dn = [d.copy() for d in D]
+        Dn[x] = 2 * Cn[:, :nocc] @ Cn[:, :nocc].T
+        return dimer_frags.energies(Dn)["E_tot"] - E0
+
+    d1, d2 = rotated(1e-3), rotated(2e-3)
+    assert abs(d1) < 1e-4
+    assert 3.6 < d2 / d1 < 4.4
+
+
+def test_single_fragment_is_plain_rhf():
+    """One fragment (or a cutoff that keeps no pair): FEF reduces to the fragment's own RHF."""
+    sysm = S.water_dimer(1, r_oo=3.0)
+    fr = Fragments(sysm, cutoff_A=0.1)
+    assert fr.pairs == []
+    res = fr.solve(e_tol=1e-10)
+    iso = fr.isolated()
+    for x in range(2):
+        assert np.abs(res["D"][x] - iso[x]).max() < 1e-8
+    assert res["n_macro"] == 1
