@@ -1,0 +1,171 @@
+/*
+ * fef.h - C ABI of the GB300 fragment-effective-field (FEF) mean-field library (libfef.so).
+ *
+ * The method is the polarization-screened fragment mean field of Byrd, Molt, Bartlett & Sanders
+ * (arXiv:1708.03377), Theory section, "Fragment Mean Field":
+ *
+ *   - the system is split into fragments x, each with its own monomer-centred AO basis and its own
+ *     closed-shell determinant (product ansatz with the antisymmetriser dropped, Eq. prodspace);
+ *   - each fragment's Fock matrix is F~ = h(1) + (2J - K) + omega_x; in AO form, with
+ *     D^x = 2 C_occ C_occ^T,  F^x = h^x + G[D^x] + omega_x,  G[D] = J[D] - K[D]/2;
+ *   - omega_x = h~ + 2 v (Eq. wc): h~ is the attraction of x's electrons to the nuclei of every other
+ *     fragment y and 2 v (Eq. dp2e) is the Coulomb matrix of y's density,
+ *     J[D^y]_{mu nu} = sum_{lambda sigma in y} (mu nu|lambda sigma) D^y_{lambda sigma};
+ *     there is no inter-fragment exchange;
+ *   - the field is "fully relaxed to infinite order": every fragment's RHF is solved in the field of
+ *     the others and the field rebuilt until all fragments are self-consistent.
+ *
+ * Conventions used by every call:
+ *   - Units: geometry in Angstrom on input (1 bohr = 0.529177210903 A); bohr and hartree inside
+ *     and on output.
+ *   - Basis: contracted Cartesian Gaussians, l = 0 (s), 1 (p), 2 (d), Cartesian components of a
+ *     shell in lexicographic order (x, y, z; xx, xy, xz, yy, yz, zz).  A raw contraction
+ *     coefficient multiplies a primitive normalised at shell level, (2a/pi)^{3/4} (4a)^{l/2}
+ *     x^lx y^ly z^lz exp(-a r^2); every Cartesian AO is then renormalised to unit self-overlap.
+ *     Shells of an atom come in the order of its basis set; AOs of a fragment follow its atoms.
+ *   - Matrix layout: "packed" = for each fragment x in order, the full n_x-by-n_x row-major block,
+ *     blocks concatenated (offsets from fef_ao_layout).
+ *   - Pointers: host pointers unless a call's on_device flag is 1, in which case they are device
+ *     pointers in the current CUDA context, used on the context's stream.  Inputs are copied
+ *     during the call; outputs are caller-allocated.  All device work of a context runs on the
+ *     stream given to fef_create (NULL = the legacy default stream); every call that returns host
+ *     data synchronises that stream before returning.
+ *   - Errors: every call returns a fef_status; fef_last_error gives a message for the last failing
+ *     call on the context.  No exception crosses the ABI.  A context stays valid after
+ *     FEF_ERR_NOT_CONVERGED.  A context is used by one host thread at a time.
+ */
+#ifndef FEF_H
+#define FEF_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct fef_ctx fef_ctx;
+
+typedef enum {
+    FEF_OK = 0,
+    FEF_ERR_ARG = 1,            /* invalid argument, size or pointer */
+    FEF_ERR_BASIS = 2,          /* bad exponents / l > 2 / linearly dependent fragment basis */
+    FEF_ERR_GEOM = 3,           /* odd electron count, coincident atoms, bad fragment map */
+    FEF_ERR_CUDA = 4,           /* a CUDA call failed; message has the CUDA error string */
+    FEF_ERR_NOT_CONVERGED = 5,  /* SCF or FEF iteration hit its iteration limit */
+    FEF_ERR_NUMERIC = 6,        /* NaN/Inf met in a Fock matrix, density or energy */
+    FEF_ERR_TIMEOUT = 7         /* a bounded device-side wait ran out (error flag set by a kernel) */
+} fef_status;
+
+enum { FEF_FP64 = 0, FEF_MIXED = 1 };
+enum { FEF_START_SUPERPOSITION = 0, FEF_START_LEARNED = 1, FEF_START_GIVEN = 2 };
+
+/* Molecular system split into fragments (Theory, "Fragment Mean Field": Hilbert space partition
+ * into fragment subspaces, monomer-centred basis). */
+typedef struct {
+    int32_t n_atoms;
+    const int32_t* Z;              /* [n_atoms] nuclear charges, 1..36 */
+    const double* xyz;             /* [n_atoms*3] Angstrom */
+    const int32_t* frag_of_atom;   /* [n_atoms] fragment index; each fragment a contiguous run, in order */
+    const int32_t* basis_of_atom;  /* [n_atoms] index of the atom's basis set in fef_basis */
+    int32_t n_frag;
+    const int32_t* charge;         /* [n_frag] net charge, or NULL for all neutral */
+} fef_geometry;
+
+/* Basis sets: n_sets kinds; set k owns shells [set_shell_offset[k], set_shell_offset[k+1]). */
+typedef struct {
+    int32_t n_sets;
+    const int32_t* set_shell_offset;  /* [n_sets+1] */
+    const int32_t* shell_l;           /* [n_shells] 0, 1 or 2 */
+    const int32_t* shell_nprim;       /* [n_shells] 1..8 */
+    const double* exps;               /* [sum nprim] exponents > 0, shell after shell */
+    const double* coefs;              /* [sum nprim] raw contraction coefficients */
+} fef_basis;
+
+typedef struct {
+    int32_t precision;       /* FEF_FP64 or FEF_MIXED (FP32 ERI core, FP64 Boys/accumulation/eigensolve) */
+    double cutoff_A;         /* fragment pairs with min atom-atom distance >= cutoff are dropped
+                                (J and V together); <= 0 keeps all pairs */
+    double schwarz;          /* shell quartet (ab|cd) dropped when Q_ab Q_cd < schwarz (0: none) */
+    double e_tol;            /* FEF convergence: |dE_tot| < e_tol and max_x |dE_x| < e_tol */
+    double micro_e_tol;      /* fragment RHF: |dE_x^scf| < micro_e_tol ... */
+    double micro_comm_tol;   /* ... and max |F D S - S D F| < micro_comm_tol */
+    int32_t max_macro;       /* FEF macro-iterations limit */
+    int32_t max_micro;       /* fragment RHF iterations limit per macro-iteration */
+    int32_t diis_size;       /* Pulay DIIS subspace size, 1..8 (1 = plain Roothaan) */
+    int32_t start;           /* FEF_START_*: initial densities */
+    int32_t use_graph;       /* capture each macro-iteration's device work in a CUDA graph */
+    int32_t deterministic;   /* reserved: 1 requests run-to-run identical sums */
+    double mixed_switch;     /* MIXED: FP32-core macro-iterations until |dE| < mixed_switch, then FP64 */
+} fef_options;
+
+/* Fill *opt with the defaults: FP64, no cutoff, schwarz 1e-12, e_tol 1e-8, micro_e_tol 1e-11,
+ * micro_comm_tol 1e-9, max_macro 100, max_micro 200, diis_size 8, superposition start, no graph,
+ * mixed_switch 1e-6. */
+void fef_default_options(fef_options* opt);
+
+/* Build a context: validate and copy the inputs, then on the device normalise the basis, build
+ * the Boys table, the one-electron matrices h^x = T^x + V^x(own nuclei) and S^x, the canonical
+ * orthogonaliser X^x = U s^{-1/2} (s >= 1e-7), shell-pair Schwarz factors, the intra-fragment
+ * two-electron tensor, the fragment-pair neighbour list within the cutoff, the environment nuclear
+ * attraction sum_{y in N(x)} V^y (h~, the equation after Eq. wc) and the J-engine work lists.
+ * cuda_stream: a cudaStream_t (NULL = default stream).  On success *out owns device memory until
+ * fef_destroy.  Errors: ARG (NULL pointers, sizes), BASIS, GEOM, CUDA. */
+fef_status fef_create(const fef_geometry* geom, const fef_basis* basis, const fef_options* opt,
+                      void* cuda_stream, fef_ctx** out);
+
+/* n_ao_per_frag[n_frag] (may be NULL) and offsets[n_frag+1] (may be NULL): packed-block offsets in
+ * doubles, offsets[x] = sum_{y<x} n_y^2.  Also usable to size every packed buffer. */
+fef_status fef_ao_layout(const fef_ctx* ctx, int32_t* n_ao_per_frag, int64_t* offsets);
+
+/* One FEF Fock build (Theory, "Fragment Mean Field", F~ with omega_x of Eq. wc / Eq. dp2e):
+ *   F^x = h^x + G[D^x] + sum_{y in N(x)} (V^y + J[D^y])   for every fragment x.
+ * D: packed densities to build from (becomes the context's current density), or NULL to use the
+ * current densities.  F_out: packed output, or NULL.  on_device: 1 if D/F_out are device pointers.
+ * The inter-fragment J is the fused McMurchie-Davidson J-engine: no ERI tensor is formed.
+ * Errors: ARG, CUDA, NUMERIC. */
+fef_status fef_build_fock(fef_ctx* ctx, const double* D, double* F_out, int on_device);
+
+/* FEF self-consistency (Theory, "Fragment Mean Field": omega_x fully relaxed to infinite order).
+ * Start from the option's start densities (superposition of isolated-fragment RHF densities, the
+ * learned warm start, or the current/given ones); each macro-iteration k builds omega^(k) from
+ * D^(k-1) of all fragments and solves every fragment's RHF in its frozen field (DIIS, canonical
+ * orthogonalisation, aufbau) to get D^(k); stops when |dE_tot| and max_x |dE_x| < e_tol.
+ * n_macro_out (nullable): macro-iterations done; final_dE_out (nullable): last |dE_tot|.
+ * Errors: NOT_CONVERGED (context stays valid, densities are the last iterate), NUMERIC, CUDA. */
+fef_status fef_iterate(fef_ctx* ctx, int32_t* n_macro_out, double* final_dE_out);
+
+/* Reference energies of the current densities (from <H_x> and <H_xy> of the Hamiltonian partition,
+ * Eqs. NHx, NHxy, clusterH, pairs counted once):
+ *   E_int[x] = tr[D^x (2 h^x + G[D^x])]/2 + sum_{A<B in x} Z_A Z_B / R_AB
+ *   E_xy     = tr[D^x V^y] + tr[D^y V^x] + tr[D^x J[D^y]] + sum_{A in x, B in y} Z_A Z_B / R_AB
+ *   E_total  = sum_x E_int[x] + sum_{x<y in N} E_xy;   E_frag[x] = E_int[x] + (1/2) sum_y E_xy.
+ * Any output pointer may be NULL; E_frag/E_int are [n_frag] host arrays. */
+fef_status fef_energies(fef_ctx* ctx, double* E_frag, double* E_total, double* E_int);
+
+/* Checkpoint / resume: copy the current packed densities out, or replace them. */
+fef_status fef_get_densities(const fef_ctx* ctx, double* D_out, int on_device);
+fef_status fef_set_densities(fef_ctx* ctx, const double* D_in, int on_device);
+
+/* Counters of the last Fock build / iteration.  Any pointer may be NULL.
+ *   shell_quartets: inter-fragment shell quartets (a<=b in x, c<=d in y, x<y) surviving the cutoff
+ *                   and Schwarz screening, counted once per build;
+ *   prim_quartets:  primitive quartets evaluated per build;
+ *   n_pairs:        fragment pairs in the neighbour list;
+ *   jengine_ms:     device time of the last build's J-engine launches (CUDA events). */
+fef_status fef_stats(const fef_ctx* ctx, int64_t* shell_quartets, int64_t* prim_quartets, int64_t* n_pairs,
+                     double* jengine_ms);
+
+/* Message of the last failing call on ctx (or of the last failed fef_create when ctx is NULL). */
+const char* fef_last_error(const fef_ctx* ctx);
+
+/* Free the context and all its device memory.  NULL is a no-op. */
+void fef_destroy(fef_ctx* ctx);
+
+/* Measure this GPU's FP64 and FP32 FMA throughput with a register-resident FMA chain kernel.
+ * Outputs (nullable) in FLOP/s, counting one FMA as 2 FLOP.  Errors: CUDA. */
+fef_status fef_measure_fma_peak(double* fp64_flops, double* fp32_flops, double* sm_clock_mhz);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FEF_H */

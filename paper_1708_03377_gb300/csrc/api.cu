@@ -1,0 +1,746 @@
+// C ABI of libfef.so (include/fef.h): input validation, integer bookkeeping of shells, shell pairs,
+// primitive pairs and J-engine tiles, device memory, and the orchestration of the FEF Fock build and
+// FEF self-consistency (paper, "Fragment Mean Field").  All arithmetic of the method runs in the
+// kernels of setup.cu, jengine.cu and scf.cu.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "common.cuh"
+#include "internal.hpp"
+
+namespace fef {
+
+struct Error {
+    fef_status status;
+    std::string msg;
+};
+
+static void ck(cudaError_t e, const char* what)
+{
+    if (e != cudaSuccess) throw Error{FEF_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e)};
+}
+
+struct Buffers {
+    std::vector<void*> allocs;
+    template <typename T>
+    T* alloc(size_t n, const char* what)
+    {
+        void* p = nullptr;
+        ck(cudaMalloc(&p, std::max<size_t>(n, 1) * sizeof(T)), what);
+        allocs.push_back(p);
+        return static_cast<T*>(p);
+    }
+    template <typename T>
+    T* upload(const std::vector<T>& v, cudaStream_t s, const char* what)
+    {
+        T* p = alloc<T>(v.size(), what);
+        if (!v.empty()) ck(cudaMemcpyAsync(p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice, s), what);
+        return p;
+    }
+    void release(void* p)
+    {
+        auto it = std::find(allocs.begin(), allocs.end(), p);
+        if (it != allocs.end()) {
+            cudaFree(p);
+            allocs.erase(it);
+        }
+    }
+    ~Buffers()
+    {
+        for (void* p : allocs) cudaFree(p);
+    }
+    // geometry-time data
+    double *S = nullptr, *h = nullptr, *X = nullptr, *Venv = nullptr, *eric = nullptr, *boys = nullptr;
+    double *e_nn_intra = nullptr, *e_nn_pair = nullptr;
+    int* nmo = nullptr;
+    // per-build data
+    double *D = nullptr, *F = nullptr, *Jenv = nullptr, *omega = nullptr;
+    double *e_J = nullptr, *tr_xy = nullptr, *tr_yx = nullptr, *tr_omega = nullptr;
+    double *E_int = nullptr, *E_scf = nullptr, *E_pair = nullptr, *E_frag = nullptr, *E_tot = nullptr;
+    int* iters = nullptr;
+    int* err_flag = nullptr;
+    double* diis = nullptr;
+    int64_t diis_stride = 0;
+    double* Jh[kClasses] = {};
+    int njh[kClasses] = {};
+    int2* tiles[kClasses][kClasses] = {};
+    int n_tiles[kClasses * kClasses] = {};
+    unsigned long long* qcount = nullptr;
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+};
+
+}  // namespace fef
+
+using namespace fef;
+
+static std::string g_create_error;
+
+#define FEF_API_BEGIN try {
+#define FEF_API_END(ctx)                                              \
+    }                                                                 \
+    catch (const Error& e)                                            \
+    {                                                                 \
+        if (ctx) (ctx)->last_error = e.msg; else g_create_error = e.msg; \
+        return e.status;                                              \
+    }                                                                 \
+    catch (const std::exception& e)                                   \
+    {                                                                 \
+        if (ctx) (ctx)->last_error = e.what(); else g_create_error = e.what(); \
+        return FEF_ERR_ARG;                                           \
+    }
+
+static void require(bool ok, fef_status st, const std::string& msg)
+{
+    if (!ok) throw Error{st, msg};
+}
+
+extern "C" void fef_default_options(fef_options* o)
+{
+    if (!o) return;
+    std::memset(o, 0, sizeof(*o));
+    o->precision = FEF_FP64;
+    o->cutoff_A = 0.0;
+    o->schwarz = 1e-12;
+    o->e_tol = 1e-8;
+    o->micro_e_tol = 1e-11;
+    o->micro_comm_tol = 1e-9;
+    o->max_macro = 100;
+    o->max_micro = 200;
+    o->diis_size = 8;
+    o->start = FEF_START_SUPERPOSITION;
+    o->use_graph = 0;
+    o->deterministic = 0;
+    o->mixed_switch = 1e-6;
+}
+
+// ---------------------------------------------------------------------------------------------- helpers
+static void check_device_flags(fef_ctx* c, const char* where)
+{
+    int flag = 0;
+    ck(cudaMemcpyAsync(&flag, c->buf->err_flag, sizeof(int), cudaMemcpyDeviceToHost, c->stream), where);
+    ck(cudaStreamSynchronize(c->stream), where);
+    if (flag & kErrNumeric) throw Error{FEF_ERR_NUMERIC, std::string(where) + ": NaN/Inf in a matrix or energy"};
+    if (flag & kErrTimeout) throw Error{FEF_ERR_TIMEOUT, std::string(where) + ": device wait limit reached"};
+    if (flag & kErrBounds) throw Error{FEF_ERR_ARG, std::string(where) + ": device bounds check failed"};
+}
+
+static void clear_flags(fef_ctx* c)
+{
+    ck(cudaMemsetAsync(c->buf->err_flag, 0, sizeof(int), c->stream), "clear flags");
+}
+
+// One FEF Fock build from the context's current densities: Hermite densities, J-engine, back-transform,
+// F = h + G + V_env + J_env, and all reference energies of the current densities.
+static void build_fock_internal(fef_ctx* c)
+{
+    Buffers* b = c->buf;
+    const Dev& d = c->dev;
+    cudaStream_t s = c->stream;
+    ck(launch_hermite_density(d, b->D, s), "hermite density");
+    for (int L = 0; L < kClasses; ++L)
+        if (b->njh[L] > 0) ck(cudaMemsetAsync(b->Jh[L], 0, sizeof(double) * b->njh[L], s), "zero Jh");
+    if (c->n_pairs > 0) ck(cudaMemsetAsync(b->e_J, 0, sizeof(double) * c->n_pairs, s), "zero e_J");
+    const int2* tiles[kClasses][kClasses];
+    for (int i = 0; i < kClasses; ++i)
+        for (int j = 0; j < kClasses; ++j) tiles[i][j] = b->tiles[i][j];
+    ck(cudaEventRecord(b->ev0, s), "event");
+    ck(launch_jengine(d, tiles, b->n_tiles, c->opt.schwarz, b->e_J, c->opt.precision, s), "J-engine");
+    ck(cudaEventRecord(b->ev1, s), "event");
+    ck(launch_back_transform(d, b->Jenv, s), "back-transform");
+    ck(launch_fock_energy(d, b->h, b->Venv, b->Jenv, b->eric, b->D, b->F, b->omega, b->e_nn_intra, b->E_int,
+                          b->tr_omega, s),
+       "fock");
+    ck(launch_nuclear_traces(d, b->D, b->tr_xy, b->tr_yx, s), "nuclear traces");
+    ck(launch_energies(d, b->e_J, b->tr_xy, b->tr_yx, b->e_nn_pair, b->E_int, b->E_pair, b->E_frag, b->E_tot, s),
+       "energies");
+    ck(launch_check_finite(b->F, c->mat_total, b->err_flag, s), "check");
+    c->energies_valid = true;
+}
+
+static void run_scf(fef_ctx* c, bool with_field, bool have_start)
+{
+    Buffers* b = c->buf;
+    ScfArgs a{};
+    a.h = b->h;
+    a.omega = with_field ? b->omega : nullptr;
+    a.S = b->S;
+    a.X = b->X;
+    a.nmo = b->nmo;
+    a.eric = b->eric;
+    a.e_nn = b->e_nn_intra;
+    a.D = b->D;
+    a.F = b->F;
+    a.diis_F = b->diis;
+    a.diis_stride = b->diis_stride;
+    a.E_scf = b->E_scf;
+    a.E_int = b->E_int;
+    a.iters = b->iters;
+    a.have_start = have_start ? 1 : 0;
+    a.max_iter = c->opt.max_micro;
+    a.diis_size = c->opt.diis_size;
+    a.e_tol = c->opt.micro_e_tol;
+    a.comm_tol = c->opt.micro_comm_tol;
+    ck(launch_fragment_scf(c->dev, a, c->max_nao, c->stream), "fragment SCF");
+    c->energies_valid = false;
+}
+
+// ---------------------------------------------------------------------------------------------- create
+extern "C" fef_status fef_create(const fef_geometry* g, const fef_basis* bs, const fef_options* opt,
+                                 void* cuda_stream, fef_ctx** out)
+{
+    fef_ctx* c = nullptr;
+    try {
+        require(g && bs && out, FEF_ERR_ARG, "fef_create: NULL geometry, basis or output pointer");
+        *out = nullptr;
+        require(g->n_atoms > 0 && g->n_frag > 0 && g->Z && g->xyz && g->frag_of_atom && g->basis_of_atom,
+                FEF_ERR_ARG, "fef_create: empty geometry or NULL geometry arrays");
+        require(bs->n_sets > 0 && bs->set_shell_offset && bs->shell_l && bs->shell_nprim && bs->exps && bs->coefs,
+                FEF_ERR_ARG, "fef_create: empty basis or NULL basis arrays");
+        c = new fef_ctx();
+        if (opt) c->opt = *opt; else fef_default_options(&c->opt);
+        const fef_options& o = c->opt;
+        require(o.diis_size >= 1 && o.diis_size <= 8, FEF_ERR_ARG, "options: diis_size must be 1..8");
+        require(o.max_macro >= 1 && o.max_micro >= 1, FEF_ERR_ARG, "options: iteration limits must be >= 1");
+        require(o.precision == FEF_FP64 || o.precision == FEF_MIXED, FEF_ERR_ARG, "options: bad precision");
+        require(o.schwarz >= 0.0 && std::isfinite(o.schwarz), FEF_ERR_ARG, "options: bad schwarz threshold");
+        c->stream = static_cast<cudaStream_t>(cuda_stream);
+        ck(cudaGetDevice(&c->device), "cudaGetDevice");
+
+        const int na = g->n_atoms, nf = g->n_frag;
+        c->n_atoms = na;
+        c->n_frag = nf;
+        // ---- fragments: contiguous runs in order
+        std::vector<int> frag_atom0(nf, -1), frag_nat(nf, 0);
+        for (int a = 0; a < na; ++a) {
+            int x = g->frag_of_atom[a];
+            require(x >= 0 && x < nf, FEF_ERR_GEOM, "frag_of_atom out of range");
+            require(a == 0 ? x == 0 : (x == g->frag_of_atom[a - 1] || x == g->frag_of_atom[a - 1] + 1),
+                    FEF_ERR_GEOM, "fragments must be contiguous atom runs numbered in order");
+            if (frag_atom0[x] < 0) frag_atom0[x] = a;
+            frag_nat[x]++;
+        }
+        require(g->frag_of_atom[na - 1] == nf - 1, FEF_ERR_GEOM, "n_frag does not match frag_of_atom");
+        for (int a = 0; a < na; ++a) {
+            require(g->Z[a] >= 1 && g->Z[a] <= 36, FEF_ERR_GEOM, "nuclear charge out of range 1..36");
+            for (int k = 0; k < 3; ++k) require(std::isfinite(g->xyz[3 * a + k]), FEF_ERR_GEOM, "non-finite coordinate");
+            require(g->basis_of_atom[a] >= 0 && g->basis_of_atom[a] < bs->n_sets, FEF_ERR_ARG,
+                    "basis_of_atom out of range");
+        }
+        // coincident atoms inside a fragment
+        for (int x = 0; x < nf; ++x)
+            for (int a = frag_atom0[x]; a < frag_atom0[x] + frag_nat[x]; ++a)
+                for (int b2 = frag_atom0[x]; b2 < a; ++b2) {
+                    double r2 = 0;
+                    for (int k = 0; k < 3; ++k) r2 += std::pow(g->xyz[3 * a + k] - g->xyz[3 * b2 + k], 2);
+                    require(r2 > 1e-6, FEF_ERR_GEOM, "coincident atoms in fragment " + std::to_string(x));
+                }
+        // ---- basis sets
+        int n_shell_types = bs->set_shell_offset[bs->n_sets];
+        require(bs->set_shell_offset[0] == 0 && n_shell_types > 0, FEF_ERR_BASIS, "bad set_shell_offset");
+        std::vector<int> type_p0(n_shell_types + 1, 0);
+        for (int k = 0; k < n_shell_types; ++k) {
+            require(bs->shell_l[k] >= 0 && bs->shell_l[k] <= kMaxL, FEF_ERR_BASIS, "shell l must be 0, 1 or 2");
+            require(bs->shell_nprim[k] >= 1 && bs->shell_nprim[k] <= 8, FEF_ERR_BASIS, "shell nprim must be 1..8");
+            type_p0[k + 1] = type_p0[k] + bs->shell_nprim[k];
+        }
+        for (int i = 0; i < type_p0[n_shell_types]; ++i) {
+            require(std::isfinite(bs->exps[i]) && bs->exps[i] > 0.0, FEF_ERR_BASIS, "exponents must be positive");
+            require(std::isfinite(bs->coefs[i]), FEF_ERR_BASIS, "non-finite contraction coefficient");
+        }
+        for (int k = 0; k < bs->n_sets; ++k)
+            require(bs->set_shell_offset[k + 1] >= bs->set_shell_offset[k], FEF_ERR_BASIS, "bad set_shell_offset");
+        // ---- shells, prims, AOs
+        std::vector<int> sh_l, sh_np, sh_p0, sh_ao, sh_atom, p_l;
+        std::vector<double> p_exp, p_coef_raw;
+        std::vector<int> frag_sh0(nf), frag_nsh(nf), frag_nao(nf), frag_ao0(nf), frag_nocc(nf);
+        std::vector<int> ao_sh, ao_k;
+        int max_l = 0;
+        int ao_global = 0;
+        for (int x = 0; x < nf; ++x) {
+            frag_sh0[x] = (int)sh_l.size();
+            frag_ao0[x] = ao_global;
+            int ao = 0, ne = 0;
+            for (int a = frag_atom0[x]; a < frag_atom0[x] + frag_nat[x]; ++a) {
+                ne += g->Z[a];
+                int set = g->basis_of_atom[a];
+                for (int k = bs->set_shell_offset[set]; k < bs->set_shell_offset[set + 1]; ++k) {
+                    int l = bs->shell_l[k];
+                    max_l = std::max(max_l, l);
+                    int sid = (int)sh_l.size();
+                    sh_l.push_back(l);
+                    sh_np.push_back(bs->shell_nprim[k]);
+                    sh_p0.push_back((int)p_exp.size());
+                    sh_ao.push_back(ao);
+                    sh_atom.push_back(a);
+                    for (int i = 0; i < bs->shell_nprim[k]; ++i) {
+                        p_exp.push_back(bs->exps[type_p0[k] + i]);
+                        p_coef_raw.push_back(bs->coefs[type_p0[k] + i]);
+                        p_l.push_back(l);
+                    }
+                    for (int q = 0; q < ncart(l); ++q) {
+                        ao_sh.push_back(sid);
+                        ao_k.push_back(q);
+                    }
+                    ao += ncart(l);
+                }
+            }
+            frag_nsh[x] = (int)sh_l.size() - frag_sh0[x];
+            require(ao > 0, FEF_ERR_BASIS, "fragment " + std::to_string(x) + " has no basis functions");
+            frag_nao[x] = ao;
+            ao_global += ao;
+            ne -= g->charge ? g->charge[x] : 0;
+            require(ne >= 0 && ne % 2 == 0, FEF_ERR_GEOM,
+                    "fragment " + std::to_string(x) + " needs an even, non-negative electron count");
+            frag_nocc[x] = ne / 2;
+        }
+        c->n_shells = (int)sh_l.size();
+        c->n_prims = (int)p_exp.size();
+        int max_nao = *std::max_element(frag_nao.begin(), frag_nao.end());
+        require(max_nao <= 56, FEF_ERR_ARG, "fragments above 56 AOs are not supported by the shared-memory SCF kernel");
+        c->max_nao = max_nao;
+        c->nao = frag_nao;
+        c->nocc = frag_nocc;
+        std::vector<int64_t> moff(nf + 1, 0), eoff(nf + 1, 0);
+        for (int x = 0; x < nf; ++x) {
+            moff[x + 1] = moff[x] + (int64_t)frag_nao[x] * frag_nao[x];
+            eoff[x + 1] = eoff[x] + (int64_t)frag_nao[x] * frag_nao[x] * frag_nao[x] * frag_nao[x];
+        }
+        c->moff = moff;
+        c->mat_total = moff[nf];
+        c->eri_total = eoff[nf];
+        // ---- shell pairs and primitive pairs (class-sorted)
+        std::vector<int> sp_a, sp_b, sp_L, frag_sp0(nf + 1, 0);
+        for (int x = 0; x < nf; ++x) {
+            frag_sp0[x] = (int)sp_a.size();
+            for (int a = 0; a < frag_nsh[x]; ++a)
+                for (int b2 = a; b2 < frag_nsh[x]; ++b2) {
+                    int s1 = frag_sh0[x] + a, s2 = frag_sh0[x] + b2;
+                    sp_a.push_back(s1);
+                    sp_b.push_back(s2);
+                    sp_L.push_back(sh_l[s1] + sh_l[s2]);
+                }
+        }
+        frag_sp0[nf] = (int)sp_a.size();
+        c->n_sp = (int)sp_a.size();
+        std::vector<int> sp_pp0(c->n_sp, 0), frag_pp0(nf * kClasses), frag_npp(nf * kClasses);
+        std::vector<int> pp_sp[kClasses], pp_ij[kClasses];
+        for (int L = 0; L < kClasses; ++L)
+            for (int x = 0; x < nf; ++x) {
+                frag_pp0[x * kClasses + L] = (int)pp_sp[L].size();
+                for (int sp = frag_sp0[x]; sp < frag_sp0[x + 1]; ++sp) {
+                    if (sp_L[sp] != L) continue;
+                    sp_pp0[sp] = (int)pp_sp[L].size();
+                    for (int i = 0; i < sh_np[sp_a[sp]]; ++i)
+                        for (int j = 0; j < sh_np[sp_b[sp]]; ++j) {
+                            pp_sp[L].push_back(sp);
+                            pp_ij[L].push_back(i * 16 + j);
+                        }
+                }
+                frag_npp[x * kClasses + L] = (int)pp_sp[L].size() - frag_pp0[x * kClasses + L];
+            }
+
+        // ---- device upload
+        c->buf = new Buffers();
+        Buffers* b = c->buf;
+        cudaStream_t s = c->stream;
+        Dev& d = c->dev;
+        d.n_frag = nf;
+        d.n_atoms = na;
+        d.n_shells = c->n_shells;
+        d.n_sp = c->n_sp;
+        d.max_nao = max_nao;
+        std::vector<double> xyzA(g->xyz, g->xyz + 3 * na), Zd(na);
+        for (int a = 0; a < na; ++a) Zd[a] = g->Z[a];
+        double* xyz_A = b->upload(xyzA, s, "xyz");
+        double* atom_xyz = b->alloc<double>(3 * na, "atom_xyz");
+        d.atom_xyz = atom_xyz;
+        d.atom_Z = b->upload(Zd, s, "Z");
+        d.frag_atom0 = b->upload(frag_atom0, s, "frag");
+        d.frag_nat = b->upload(frag_nat, s, "frag");
+        d.frag_sh0 = b->upload(frag_sh0, s, "frag");
+        d.frag_nsh = b->upload(frag_nsh, s, "frag");
+        d.frag_nao = b->upload(frag_nao, s, "frag");
+        d.frag_ao0 = b->upload(frag_ao0, s, "frag");
+        d.frag_sp0 = b->upload(frag_sp0, s, "frag");
+        d.frag_nocc = b->upload(frag_nocc, s, "frag");
+        d.frag_moff = b->upload(moff, s, "frag");
+        d.frag_eoff = b->upload(eoff, s, "frag");
+        d.frag_pp0 = b->upload(frag_pp0, s, "frag");
+        d.frag_npp = b->upload(frag_npp, s, "frag");
+        d.sh_l = b->upload(sh_l, s, "shells");
+        d.sh_np = b->upload(sh_np, s, "shells");
+        d.sh_p0 = b->upload(sh_p0, s, "shells");
+        d.sh_ao = b->upload(sh_ao, s, "shells");
+        d.sh_atom = b->upload(sh_atom, s, "shells");
+        d.p_exp = b->upload(p_exp, s, "prims");
+        double* p_coef_raw_d = b->upload(p_coef_raw, s, "prims");
+        int* p_l_d = b->upload(p_l, s, "prims");
+        double* p_coef = b->alloc<double>(p_exp.size(), "prims");
+        d.p_coef = p_coef;
+        d.ao_sh = b->upload(ao_sh, s, "aos");
+        d.ao_k = b->upload(ao_k, s, "aos");
+        double* ao_scale = b->alloc<double>(ao_global, "aos");
+        d.ao_scale = ao_scale;
+        d.sp_a = b->upload(sp_a, s, "shell pairs");
+        d.sp_b = b->upload(sp_b, s, "shell pairs");
+        d.sp_L = b->upload(sp_L, s, "shell pairs");
+        d.sp_pp0 = b->upload(sp_pp0, s, "shell pairs");
+        double* sp_Q = b->alloc<double>(c->n_sp, "shell pairs");
+        d.sp_Q = sp_Q;
+        double4_32a* ppP[kClasses];
+        float4* ppPf[kClasses];
+        double* ppK[kClasses];
+        float* ppQ[kClasses];
+        for (int L = 0; L < kClasses; ++L) {
+            int n = (int)pp_sp[L].size();
+            d.n_pp[L] = n;
+            d.pp_sp[L] = b->upload(pp_sp[L], s, "prim pairs");
+            d.pp_ij[L] = b->upload(pp_ij[L], s, "prim pairs");
+            ppP[L] = b->alloc<double4_32a>(n, "prim pairs");
+            ppPf[L] = b->alloc<float4>(n, "prim pairs");
+            ppK[L] = b->alloc<double>(n, "prim pairs");
+            ppQ[L] = b->alloc<float>(n, "prim pairs");
+            d.pp_P[L] = ppP[L];
+            d.pp_Pf[L] = ppPf[L];
+            d.pp_K[L] = ppK[L];
+            d.pp_Q[L] = ppQ[L];
+            b->njh[L] = nh(L) * n;
+            d.pp_Dh[L] = b->alloc<double>((size_t)nh(L) * n, "hermite density");
+            b->Jh[L] = b->alloc<double>((size_t)nh(L) * n, "hermite field");
+            d.pp_Jh[L] = b->Jh[L];
+        }
+        b->boys = b->alloc<double>((size_t)kBoysRows * kBoysRowLen, "boys");
+        d.boys = b->boys;
+        b->err_flag = b->alloc<int>(1, "flag");
+        d.err_flag = b->err_flag;
+        ck(cudaMemsetAsync(b->err_flag, 0, sizeof(int), s), "flag");
+        ck(cudaEventCreate(&b->ev0), "event");
+        ck(cudaEventCreate(&b->ev1), "event");
+
+        // ---- geometry-time kernels
+        ck(launch_prepare(d, xyz_A, atom_xyz, p_coef, p_coef_raw_d, p_l_d, c->n_prims, s), "prepare");
+        ck(launch_boys_table(b->boys, s), "boys table");
+        ck(launch_ao_scale(d, ao_scale, ao_global, nullptr, s), "ao scale");
+        ck(launch_prim_pairs(d, ppP, ppPf, ppK, s), "prim pairs");
+        b->S = b->alloc<double>(c->mat_total, "S");
+        b->h = b->alloc<double>(c->mat_total, "h");
+        ck(launch_one_electron(d, b->S, b->h, s), "one-electron");
+        // neighbour list (within the cutoff) -> pairs x<y and CSR
+        std::vector<unsigned char> flags((size_t)nf * nf, 0);
+        {
+            unsigned char* fl = b->alloc<unsigned char>((size_t)nf * nf, "neighbour flags");
+            ck(cudaMemsetAsync(fl, 0, (size_t)nf * nf, s), "neighbour flags");
+            double cutoff_bohr = o.cutoff_A > 0 ? o.cutoff_A / 0.529177210903 : 0.0;
+            ck(launch_neighbours(d, cutoff_bohr, fl, s), "neighbours");
+            ck(cudaMemcpyAsync(flags.data(), fl, flags.size(), cudaMemcpyDeviceToHost, s), "neighbours");
+            ck(cudaStreamSynchronize(s), "neighbours");
+            b->release(fl);
+        }
+        std::vector<int> pair_x, pair_y, nbr0(nf + 1, 0), nbr, nbr_pair;
+        std::vector<std::vector<int>> adj(nf), adjp(nf);
+        for (int x = 0; x < nf; ++x)
+            for (int y = x + 1; y < nf; ++y)
+                if (flags[(size_t)x * nf + y]) {
+                    int p = (int)pair_x.size();
+                    pair_x.push_back(x);
+                    pair_y.push_back(y);
+                    adj[x].push_back(y);
+                    adjp[x].push_back(p);
+                    adj[y].push_back(x);
+                    adjp[y].push_back(p);
+                }
+        for (int x = 0; x < nf; ++x) {
+            nbr0[x + 1] = nbr0[x] + (int)adj[x].size();
+            // neighbours in ascending fragment order
+            std::vector<int> idx(adj[x].size());
+            for (size_t k = 0; k < idx.size(); ++k) idx[k] = (int)k;
+            std::sort(idx.begin(), idx.end(), [&](int i, int j) { return adj[x][i] < adj[x][j]; });
+            for (int k : idx) {
+                nbr.push_back(adj[x][k]);
+                nbr_pair.push_back(adjp[x][k]);
+            }
+        }
+        c->n_pairs = (int)pair_x.size();
+        d.n_pairs = c->n_pairs;
+        c->h_pair_x = pair_x;
+        c->h_pair_y = pair_y;
+        d.pair_x = b->upload(pair_x, s, "pairs");
+        d.pair_y = b->upload(pair_y, s, "pairs");
+        d.frag_nbr0 = b->upload(nbr0, s, "pairs");
+        d.nbr = b->upload(nbr, s, "pairs");
+        d.nbr_pair = b->upload(nbr_pair, s, "pairs");
+        b->e_nn_intra = b->alloc<double>(nf, "e_nn");
+        b->e_nn_pair = b->alloc<double>(c->n_pairs, "e_nn");
+        ck(launch_nuclear_repulsion(d, b->e_nn_intra, b->e_nn_pair, s), "nuclear repulsion");
+        // intra-fragment two-electron tensor -> Schwarz factors and C = (mu nu|ls) - (mu l|nu s)/2
+        {
+            double* eri = b->alloc<double>(c->eri_total, "intra eri");
+            ck(launch_intra_eri(d, eri, max_l, s), "intra eri");
+            ck(launch_schwarz(d, eri, sp_Q, ppQ, s), "schwarz");
+            b->eric = b->alloc<double>(c->eri_total, "eric");
+            ck(launch_coulomb_exchange(d, eri, b->eric, s), "coulomb-exchange");
+            ck(cudaStreamSynchronize(s), "intra eri");
+            b->release(eri);
+        }
+        b->Venv = b->alloc<double>(c->mat_total, "Venv");
+        ck(launch_nuclear_env(d, b->Venv, s), "nuclear env");
+        b->X = b->alloc<double>(c->mat_total, "X");
+        b->nmo = b->alloc<int>(nf, "nmo");
+        ck(launch_orthogonaliser(d, b->S, b->X, b->nmo, 1e-7, max_nao, s), "orthogonaliser");
+        c->nmo.assign(nf, 0);
+        ck(cudaMemcpyAsync(c->nmo.data(), b->nmo, sizeof(int) * nf, cudaMemcpyDeviceToHost, s), "nmo");
+        ck(cudaStreamSynchronize(s), "create");
+        for (int x = 0; x < nf; ++x)
+            require(c->nmo[x] >= frag_nocc[x], FEF_ERR_BASIS,
+                    "fragment " + std::to_string(x) + ": basis too linearly dependent for its electrons");
+        // J-engine tiles: (pair, 32 bra primitive pairs of class LP) for every class pair present
+        int64_t prim_q = 0;
+        for (int LP = 0; LP < kClasses; ++LP)
+            for (int LQ = 0; LQ < kClasses; ++LQ) {
+                std::vector<int2> t;
+                for (int p = 0; p < c->n_pairs; ++p) {
+                    int x = pair_x[p], y = pair_y[p];
+                    int nb = frag_npp[x * kClasses + LP], nk = frag_npp[y * kClasses + LQ];
+                    if (nb == 0 || nk == 0) continue;
+                    for (int o2 = 0; o2 < nb; o2 += 32) {
+                        t.push_back(make_int2(p, frag_pp0[x * kClasses + LP] + o2));
+                        prim_q += (int64_t)std::min(32, nb - o2) * nk;
+                    }
+                }
+                b->n_tiles[LP * kClasses + LQ] = (int)t.size();
+                b->tiles[LP][LQ] = t.empty() ? nullptr : b->upload(t, s, "tiles");
+            }
+        c->prim_quartets = prim_q;
+        b->qcount = b->alloc<unsigned long long>(1, "qcount");
+        ck(cudaMemsetAsync(b->qcount, 0, sizeof(unsigned long long), s), "qcount");
+        ck(launch_count_quartets(d, o.schwarz, b->qcount, s), "count quartets");
+        unsigned long long qc = 0;
+        ck(cudaMemcpyAsync(&qc, b->qcount, sizeof(qc), cudaMemcpyDeviceToHost, s), "qcount");
+        // per-build buffers
+        b->D = b->alloc<double>(c->mat_total, "D");
+        b->F = b->alloc<double>(c->mat_total, "F");
+        b->Jenv = b->alloc<double>(c->mat_total, "Jenv");
+        b->omega = b->alloc<double>(c->mat_total, "omega");
+        ck(cudaMemsetAsync(b->D, 0, sizeof(double) * c->mat_total, s), "D");
+        b->e_J = b->alloc<double>(c->n_pairs, "e_J");
+        b->tr_xy = b->alloc<double>(c->n_pairs, "tr");
+        b->tr_yx = b->alloc<double>(c->n_pairs, "tr");
+        b->E_pair = b->alloc<double>(c->n_pairs, "E_pair");
+        b->tr_omega = b->alloc<double>(nf, "tr_omega");
+        b->E_int = b->alloc<double>(nf, "E_int");
+        b->E_scf = b->alloc<double>(nf, "E_scf");
+        b->E_frag = b->alloc<double>(nf, "E_frag");
+        b->E_tot = b->alloc<double>(1, "E_tot");
+        b->iters = b->alloc<int>(nf, "iters");
+        b->diis_stride = 2 * (int64_t)o.diis_size * max_nao * max_nao;
+        b->diis = b->alloc<double>((size_t)nf * b->diis_stride, "diis");
+        ck(cudaStreamSynchronize(s), "create");
+        c->shell_quartets = (int64_t)qc;
+        check_device_flags(c, "create");
+        *out = c;
+        return FEF_OK;
+    } catch (const Error& e) {
+        g_create_error = e.msg;
+        if (c) {
+            delete c->buf;
+            delete c;
+        }
+        return e.status;
+    } catch (const std::exception& e) {
+        g_create_error = e.what();
+        if (c) {
+            delete c->buf;
+            delete c;
+        }
+        return FEF_ERR_ARG;
+    }
+}
+
+extern "C" void fef_destroy(fef_ctx* c)
+{
+    if (!c) return;
+    if (c->buf) {
+        if (c->buf->ev0) cudaEventDestroy(c->buf->ev0);
+        if (c->buf->ev1) cudaEventDestroy(c->buf->ev1);
+        delete c->buf;
+    }
+    delete c;
+}
+
+extern "C" const char* fef_last_error(const fef_ctx* c)
+{
+    return c ? c->last_error.c_str() : g_create_error.c_str();
+}
+
+extern "C" fef_status fef_ao_layout(const fef_ctx* c, int32_t* n_ao_per_frag, int64_t* offsets)
+{
+    if (!c) return FEF_ERR_ARG;
+    for (int x = 0; x < c->n_frag; ++x) {
+        if (n_ao_per_frag) n_ao_per_frag[x] = c->nao[x];
+        if (offsets) offsets[x] = c->moff[x];
+    }
+    if (offsets) offsets[c->n_frag] = c->moff[c->n_frag];
+    return FEF_OK;
+}
+
+static void copy_packed(fef_ctx* c, double* dst, const double* src, int on_device, cudaMemcpyKind host_kind)
+{
+    size_t bytes = sizeof(double) * c->mat_total;
+    ck(cudaMemcpyAsync(dst, src, bytes, on_device ? cudaMemcpyDeviceToDevice : host_kind, c->stream), "copy");
+    if (!on_device) ck(cudaStreamSynchronize(c->stream), "copy");
+}
+
+extern "C" fef_status fef_set_densities(fef_ctx* c, const double* D, int on_device)
+{
+    if (!c) return FEF_ERR_ARG;
+    FEF_API_BEGIN
+    require(D != nullptr, FEF_ERR_ARG, "fef_set_densities: NULL D");
+    copy_packed(c, c->buf->D, D, on_device, cudaMemcpyHostToDevice);
+    c->have_density = true;
+    c->energies_valid = false;
+    return FEF_OK;
+    FEF_API_END(c)
+}
+
+extern "C" fef_status fef_get_densities(const fef_ctx* cc, double* D, int on_device)
+{
+    fef_ctx* c = const_cast<fef_ctx*>(cc);
+    if (!c) return FEF_ERR_ARG;
+    FEF_API_BEGIN
+    require(D != nullptr, FEF_ERR_ARG, "fef_get_densities: NULL output");
+    require(c->have_density, FEF_ERR_ARG, "fef_get_densities: no densities yet");
+    copy_packed(c, D, c->buf->D, on_device, cudaMemcpyDeviceToHost);
+    return FEF_OK;
+    FEF_API_END(c)
+}
+
+extern "C" fef_status fef_build_fock(fef_ctx* c, const double* D, double* F_out, int on_device)
+{
+    if (!c) return FEF_ERR_ARG;
+    FEF_API_BEGIN
+    if (D) {
+        copy_packed(c, c->buf->D, D, on_device, cudaMemcpyHostToDevice);
+        c->have_density = true;
+    }
+    require(c->have_density, FEF_ERR_ARG, "fef_build_fock: no densities given or set");
+    clear_flags(c);
+    build_fock_internal(c);
+    if (F_out) copy_packed(c, F_out, c->buf->F, on_device, cudaMemcpyDeviceToHost);
+    check_device_flags(c, "fef_build_fock");
+    float ms = 0.f;
+    ck(cudaEventElapsedTime(&ms, c->buf->ev0, c->buf->ev1), "event time");
+    c->jengine_ms = ms;
+    return FEF_OK;
+    FEF_API_END(c)
+}
+
+static void read_energies(fef_ctx* c, std::vector<double>& Ex, double& Et)
+{
+    Ex.resize(c->n_frag);
+    ck(cudaMemcpyAsync(Ex.data(), c->buf->E_frag, sizeof(double) * c->n_frag, cudaMemcpyDeviceToHost, c->stream),
+       "energies");
+    ck(cudaMemcpyAsync(&Et, c->buf->E_tot, sizeof(double), cudaMemcpyDeviceToHost, c->stream), "energies");
+    ck(cudaStreamSynchronize(c->stream), "energies");
+}
+
+extern "C" fef_status fef_iterate(fef_ctx* c, int32_t* n_macro_out, double* final_dE_out)
+{
+    if (!c) return FEF_ERR_ARG;
+    FEF_API_BEGIN
+    const fef_options& o = c->opt;
+    clear_flags(c);
+    if (o.start == FEF_START_GIVEN) {
+        require(c->have_density, FEF_ERR_ARG, "fef_iterate: start=GIVEN but no densities were set");
+    } else if (o.start == FEF_START_SUPERPOSITION) {
+        run_scf(c, false, false);  // isolated-fragment RHF from the core guess
+        int flag = 0;
+        ck(cudaMemcpyAsync(&flag, c->buf->err_flag, sizeof(int), cudaMemcpyDeviceToHost, c->stream), "flags");
+        ck(cudaStreamSynchronize(c->stream), "isolated RHF");
+        if (flag & kErrNotConv) throw Error{FEF_ERR_NOT_CONVERGED, "isolated-fragment RHF did not converge"};
+        c->have_density = true;
+    } else {
+        throw Error{FEF_ERR_ARG, "fef_iterate: learned start needs the MLP warm start (not in this build)"};
+    }
+    check_device_flags(c, "fef_iterate start");
+    build_fock_internal(c);
+    std::vector<double> Ex_old, Ex;
+    double Et_old = 0, Et = 0, dE = 0;
+    read_energies(c, Ex_old, Et_old);
+    int k = 0;
+    bool conv = false;
+    float jms = 0.f;
+    for (k = 1; k <= o.max_macro; ++k) {
+        run_scf(c, true, true);
+        build_fock_internal(c);
+        read_energies(c, Ex, Et);
+        float ms = 0.f;
+        ck(cudaEventElapsedTime(&ms, c->buf->ev0, c->buf->ev1), "event time");
+        jms += ms;
+        int flag = 0;
+        ck(cudaMemcpyAsync(&flag, c->buf->err_flag, sizeof(int), cudaMemcpyDeviceToHost, c->stream), "flags");
+        ck(cudaStreamSynchronize(c->stream), "flags");
+        if (flag & kErrNumeric) throw Error{FEF_ERR_NUMERIC, "NaN/Inf during FEF iteration"};
+        if (flag & kErrNotConv)
+            throw Error{FEF_ERR_NOT_CONVERGED, "fragment RHF in the field did not converge at macro-iteration " +
+                                                   std::to_string(k)};
+        dE = std::fabs(Et - Et_old);
+        double dEx = 0;
+        for (int x = 0; x < c->n_frag; ++x) dEx = std::max(dEx, std::fabs(Ex[x] - Ex_old[x]));
+        Ex_old = Ex;
+        Et_old = Et;
+        if (dE < o.e_tol && dEx < o.e_tol) {
+            conv = true;
+            break;
+        }
+    }
+    c->jengine_ms = jms;
+    if (n_macro_out) *n_macro_out = conv ? k : o.max_macro;
+    if (final_dE_out) *final_dE_out = dE;
+    if (!conv) throw Error{FEF_ERR_NOT_CONVERGED, "FEF did not converge within max_macro"};
+    return FEF_OK;
+    FEF_API_END(c)
+}
+
+extern "C" fef_status fef_energies(fef_ctx* c, double* E_frag, double* E_total, double* E_int)
+{
+    if (!c) return FEF_ERR_ARG;
+    FEF_API_BEGIN
+    require(c->have_density, FEF_ERR_ARG, "fef_energies: no densities");
+    if (!c->energies_valid) {
+        clear_flags(c);
+        build_fock_internal(c);
+    }
+    if (E_frag)
+        ck(cudaMemcpyAsync(E_frag, c->buf->E_frag, sizeof(double) * c->n_frag, cudaMemcpyDeviceToHost, c->stream), "E");
+    if (E_total) ck(cudaMemcpyAsync(E_total, c->buf->E_tot, sizeof(double), cudaMemcpyDeviceToHost, c->stream), "E");
+    if (E_int)
+        ck(cudaMemcpyAsync(E_int, c->buf->E_int, sizeof(double) * c->n_frag, cudaMemcpyDeviceToHost, c->stream), "E");
+    ck(cudaStreamSynchronize(c->stream), "energies");
+    check_device_flags(c, "fef_energies");
+    return FEF_OK;
+    FEF_API_END(c)
+}
+
+extern "C" fef_status fef_stats(const fef_ctx* c, int64_t* sq, int64_t* pq, int64_t* np, double* jms)
+{
+    if (!c) return FEF_ERR_ARG;
+    if (sq) *sq = c->shell_quartets;
+    if (pq) *pq = c->prim_quartets;
+    if (np) *np = c->n_pairs;
+    if (jms) *jms = c->jengine_ms;
+    return FEF_OK;
+}
+
+extern "C" fef_status fef_measure_fma_peak(double* fp64, double* fp32, double* mhz)
+{
+    cudaError_t e = measure_fma_peak(fp64, fp32, mhz);
+    if (e != cudaSuccess) {
+        g_create_error = std::string("fef_measure_fma_peak: ") + cudaGetErrorString(e);
+        return FEF_ERR_CUDA;
+    }
+    return FEF_OK;
+}

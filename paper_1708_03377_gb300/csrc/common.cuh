@@ -1,0 +1,238 @@
+// Device building blocks of the FEF effective-field Fock build on sm_103a.
+//
+// Integrals follow McMurchie & Davidson (J. Comput. Phys. 26, 218 (1978)): a product of two
+// Cartesian Gaussians is expanded in Hermite Gaussians with coefficients E^{ij}_t, and every
+// Coulomb-type integral reduces to the Hermite integrals R_{tuv}(alpha, PQ) built from the Boys
+// function F_n(T) = int_0^1 t^{2n} exp(-T t^2) dt.  These integrals realise the one-electron part
+// h(1), the inter-fragment nuclear attraction h~ and the two-electron integrals of Eq. dp2e of the
+// paper's "Fragment Mean Field" section.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace fef {
+
+constexpr double kPi = 3.14159265358979323846;
+// sqrt(2 pi^{5/2}): split evenly between bra and ket Hermite densities so that the per-quartet
+// prefactor 2 pi^{5/2} / (p q sqrt(p+q)) becomes (c/p) (c/q) rsqrt(p+q).
+constexpr double kSqrt2Pi52 = 5.9149671727956128778;
+constexpr double kSqrtPiHalf = 0.88622692545275801365;  // sqrt(pi)/2
+
+constexpr int kMaxL = 2;            // s, p, d shells
+constexpr int kMaxLPair = 2 * kMaxL;
+constexpr int kMaxLTot = 2 * kMaxLPair;
+
+// ------------------------------------------------------------------------------------------ Boys
+// Grid-Taylor table: rows T_k = k h, k = 0..kBoysRows-1; per row, for m = 0..kBoysM-1 a block of
+// kBoysOrder+1 coefficients F_{m+j}(T_k)/j! (j = 0..kBoysOrder), padded to kBoysBlock doubles; the
+// pad slot of block 0 holds T_k.  |T - T_k| <= h/2 = 0.025 gives a truncation error below
+// 0.025^7/7! ~ 1.2e-15.  For T >= kBoysTmax the asymptotic form F_0 = sqrt(pi/T)/2,
+// F_n = F_{n-1} (2n-1)/(2T) is used (neglected terms below exp(-36) ~ 2e-16).
+constexpr double kBoysH = 0.05;
+constexpr double kBoysInvH = 20.0;
+constexpr double kBoysTmax = 36.0;
+constexpr int kBoysOrder = 6;
+constexpr int kBoysM = kMaxLTot + 1;              // m = 0..8
+constexpr int kBoysBlock = 8;
+constexpr int kBoysRowLen = kBoysM * kBoysBlock;  // 72 doubles
+constexpr int kBoysRows = 732;                    // covers T up to 36.55
+
+// -------------------------------------------------------------------------------- Hermite indexing
+// Hermite indices (t,u,v) with t+u+v <= L, ordered by level s = t+u+v, then t descending, then u
+// descending (the Cartesian lexicographic order of each level).
+__host__ __device__ constexpr int nh(int L) { return (L + 1) * (L + 2) * (L + 3) / 6; }
+__host__ __device__ constexpr int ncart(int l) { return (l + 1) * (l + 2) / 2; }
+__host__ __device__ constexpr int hidx(int t, int u, int v)
+{
+    return (t + u + v) * (t + u + v + 1) * (t + u + v + 2) / 6 + (u + v) * (u + v + 1) / 2 + v;
+}
+struct TUV { int t, u, v; };
+__host__ __device__ constexpr TUV htuv(int idx)
+{
+    int s = 0;
+    while (nh(s) <= idx) ++s;
+    int r = idx - (s > 0 ? nh(s - 1) : 0);
+    int t = s;
+    while (r >= s - t + 1) { r -= s - t + 1; --t; }
+    int u = s - t - r;
+    return TUV{t, u, s - t - u};
+}
+// Cartesian component k of angular momentum l (lexicographic: xx, xy, xz, yy, yz, zz)
+__host__ __device__ inline void cart_of(int l, int k, int& x, int& y, int& z)
+{
+    int n = 0;
+    for (int a = l; a >= 0; --a)
+        for (int b = l - a; b >= 0; --b) {
+            if (n == k) { x = a; y = b; z = l - a - b; return; }
+            ++n;
+        }
+    x = y = z = 0;
+}
+
+// ------------------------------------------------------------------------------------------ Boys (FP64)
+// F_0..F_L at T (FP64), table path for T < kBoysTmax.  kidx is the nearest grid row (computed from
+// an FP32 estimate of T; any row within h/2 + 1e-4 of T keeps the error bound).
+template <int L>
+__device__ __forceinline__ void boys_fp64(const double* __restrict__ table, double T, int kidx, double* F)
+{
+    if (kidx < kBoysRows - 1) {
+        const double* row = table + (size_t)kidx * kBoysRowLen;
+        const double Tk = __ldg(row + kBoysOrder + 1);
+        const double d = Tk - T;
+#pragma unroll
+        for (int m = 0; m <= L; ++m) {
+            const double* c = row + m * kBoysBlock;
+            double2 c01 = __ldg(reinterpret_cast<const double2*>(c));
+            double2 c23 = __ldg(reinterpret_cast<const double2*>(c + 2));
+            double2 c45 = __ldg(reinterpret_cast<const double2*>(c + 4));
+            double c6 = __ldg(c + 6);
+            double f = fma(d, c6, c45.y);
+            f = fma(d, f, c45.x);
+            f = fma(d, f, c23.y);
+            f = fma(d, f, c23.x);
+            f = fma(d, f, c01.y);
+            F[m] = fma(d, f, c01.x);
+        }
+    } else {
+        const double rt = rsqrt(T);
+        const double half_inv_T = 0.5 * rt * rt;
+        F[0] = kSqrtPiHalf * rt;
+#pragma unroll
+        for (int m = 1; m <= L; ++m) F[m] = F[m - 1] * ((2.0 * m - 1.0) * half_inv_T);
+    }
+}
+
+__device__ __forceinline__ int boys_row(float Tf)
+{
+    float k = fminf(Tf, (float)(kBoysRows - 1) * (float)kBoysH) * (float)kBoysInvH + 0.5f;
+    return (int)k;  // T >= Tmax + h/2 maps to the last row, which selects the asymptotic branch
+}
+
+// Runtime-L variant for the non-hot kernels (one-electron, Schwarz, intra-fragment).
+__device__ inline void boys_fp64_rt(const double* __restrict__ table, double T, int L, double* F)
+{
+    int k = (int)(fmin(T, (kBoysRows - 1) * kBoysH) * kBoysInvH + 0.5);
+    if (k < kBoysRows - 1) {
+        const double* row = table + (size_t)k * kBoysRowLen;
+        const double d = row[kBoysOrder + 1] - T;
+        for (int m = 0; m <= L; ++m) {
+            const double* c = row + m * kBoysBlock;
+            double f = c[kBoysOrder];
+            for (int j = kBoysOrder - 1; j >= 0; --j) f = fma(d, f, c[j]);
+            F[m] = f;
+        }
+    } else {
+        double rt = rsqrt(T);
+        double hi = 0.5 * rt * rt;
+        F[0] = kSqrtPiHalf * rt;
+        for (int m = 1; m <= L; ++m) F[m] = F[m - 1] * ((2.0 * m - 1.0) * hi);
+    }
+}
+
+// ------------------------------------------------------------------------------------------ MD R
+// In-place Hermite recursion: on entry base[n] = (-2 alpha)^n F_n(T) * prefactor, n = 0..L; on exit
+// R[hidx(t,u,v)] = R^{(0)}_{tuv} for t+u+v <= L, using
+//   R^{(n)}_{t+1,u,v} = t R^{(n+1)}_{t-1,u,v} + X_PQ R^{(n+1)}_{t,u,v}   (and the same in u, v).
+// Sweeping n from L-1 down to 0 and each level from high to low lets one array hold R^{(n+1)} of the
+// lower levels while R^{(n)} of the higher levels is written.
+template <int L, typename Real>
+__device__ __forceinline__ void md_R(Real* R, const Real* base, Real X, Real Y, Real Z)
+{
+    R[0] = base[L];
+#pragma unroll
+    for (int n = L - 1; n >= 0; --n) {
+#pragma unroll
+        for (int idx = nh(L - n) - 1; idx >= 1; --idx) {
+            const TUV c = htuv(idx);
+            Real v;
+            if (c.t > 0) {
+                v = X * R[hidx(c.t - 1, c.u, c.v)];
+                if (c.t > 1) v = fma(Real(c.t - 1), R[hidx(c.t - 2, c.u, c.v)], v);
+            } else if (c.u > 0) {
+                v = Y * R[hidx(c.t, c.u - 1, c.v)];
+                if (c.u > 1) v = fma(Real(c.u - 1), R[hidx(c.t, c.u - 2, c.v)], v);
+            } else {
+                v = Z * R[hidx(c.t, c.u, c.v - 1)];
+                if (c.v > 1) v = fma(Real(c.v - 1), R[hidx(c.t, c.u, c.v - 2)], v);
+            }
+            R[idx] = v;
+        }
+        R[0] = base[n];
+    }
+}
+
+// Runtime-L R recursion for the non-hot kernels; R has room for nh(L) values, scratch for the
+// same.  Same recurrence as md_R.
+__device__ inline void md_R_rt(int L, double* R, const double* base, double X, double Y, double Z)
+{
+    R[0] = base[L];
+    for (int n = L - 1; n >= 0; --n) {
+        for (int idx = nh(L - n) - 1; idx >= 1; --idx) {
+            TUV c = htuv(idx);
+            double v;
+            if (c.t > 0) {
+                v = X * R[hidx(c.t - 1, c.u, c.v)];
+                if (c.t > 1) v += (c.t - 1) * R[hidx(c.t - 2, c.u, c.v)];
+            } else if (c.u > 0) {
+                v = Y * R[hidx(c.t, c.u - 1, c.v)];
+                if (c.u > 1) v += (c.u - 1) * R[hidx(c.t, c.u - 2, c.v)];
+            } else {
+                v = Z * R[hidx(c.t, c.u, c.v - 1)];
+                if (c.v > 1) v += (c.v - 1) * R[hidx(c.t, c.u, c.v - 2)];
+            }
+            R[idx] = v;
+        }
+        R[0] = base[n];
+    }
+}
+
+// ------------------------------------------------------------------------------------------ MD E
+// 1D Hermite expansion coefficients E^{ij}_t (i <= la, j <= lb, t <= i+j) of
+// x_A^i x_B^j exp(-a x_A^2 - b x_B^2) = K_x sum_t E^{ij}_t Lambda_t(x_P), with K_x factored out
+// (E^{00}_0 = 1):
+//   E^{i+1,j}_t = E^{ij}_{t-1}/(2p) + X_PA E^{ij}_t + (t+1) E^{ij}_{t+1}
+//   E^{i,j+1}_t = E^{ij}_{t-1}/(2p) + X_PB E^{ij}_t + (t+1) E^{ij}_{t+1}
+// E is indexed [i][j][t] with fixed strides (3, 3, 5).
+__device__ inline void md_E1(int la, int lb, double p, double XPA, double XPB, double (*E)[3][5])
+{
+    const double h = 0.5 / p;
+    for (int i = 0; i <= la; ++i)
+        for (int j = 0; j <= lb; ++j)
+            for (int t = 0; t < 5; ++t) E[i][j][t] = 0.0;
+    E[0][0][0] = 1.0;
+    for (int i = 0; i < la; ++i)
+        for (int t = 0; t <= i + 1; ++t) {
+            double v = XPA * (t <= i ? E[i][0][t] : 0.0);
+            if (t > 0) v += h * E[i][0][t - 1];
+            if (t + 1 <= i) v += (t + 1) * E[i][0][t + 1];
+            E[i + 1][0][t] = v;
+        }
+    for (int i = 0; i <= la; ++i)
+        for (int j = 0; j < lb; ++j)
+            for (int t = 0; t <= i + j + 1; ++t) {
+                double v = XPB * (t <= i + j ? E[i][j][t] : 0.0);
+                if (t > 0) v += h * E[i][j][t - 1];
+                if (t + 1 <= i + j) v += (t + 1) * E[i][j][t + 1];
+                E[i][j + 1][t] = v;
+            }
+}
+
+// Shell-level primitive normalisation (2a/pi)^{3/4} (4a)^{l/2}.
+__device__ inline double prim_norm(double a, int l)
+{
+    double n = pow(2.0 * a / kPi, 0.75);
+    for (int k = 0; k < l; ++k) n *= sqrt(4.0 * a);
+    return n;
+}
+
+// ------------------------------------------------------------------------------------------ errors
+// Device error flags (bit mask), read by the host after a launch sequence.
+enum : int {
+    kErrNumeric = 1,   // NaN/Inf in a matrix or energy
+    kErrTimeout = 2,   // a bounded wait ran out
+    kErrBounds = 4,    // an index failed a bounds check
+    kErrNotConv = 8,   // a fragment RHF hit its iteration limit
+};
+
+}  // namespace fef

@@ -1,0 +1,167 @@
+// Internal data layout of a FEF context in device memory, and the kernel launchers shared by the
+// translation units of libfef.so.  Not part of the public ABI (include/fef.h).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/fef.h"
+
+namespace fef {
+
+constexpr int kClasses = 5;  // Hermite class L_P = l_a + l_b = 0..4
+
+// Structure-of-arrays views of everything the kernels read.  All pointers are device pointers.
+//   atoms  : xyz in bohr, Z as double
+//   shells : l, primitive count/offset, AO offset inside the fragment, owning atom and fragment
+//   prims  : exponent, coefficient times the shell-level normalisation (2a/pi)^{3/4} (4a)^{l/2}
+//   AOs    : ao_scale (unit self-overlap), indexed by global AO = frag_ao0[x] + local AO
+//   shell pairs (a <= b inside one fragment): class L, first primitive pair in its class array,
+//            Schwarz factor Q_ab
+//   primitive pairs, per class L: centre P and exponent p (double4_32a), FP32 copy (float4),
+//            K = c_i c_j exp(-a b/p |AB|^2), shell-pair id, primitive indices, Schwarz factor (float),
+//            Hermite density Dh[nh(L)][n] and Hermite Coulomb accumulator Jh[nh(L)][n] (SoA)
+//   packed matrices: per fragment a full n_x*n_x row-major block at frag_moff[x]
+struct Dev {
+    int n_frag, n_atoms, n_shells, n_sp, n_pairs;
+    int max_nao;
+    // atoms
+    const double* atom_xyz;
+    const double* atom_Z;
+    // fragments
+    const int* frag_atom0;
+    const int* frag_nat;
+    const int* frag_sh0;
+    const int* frag_nsh;
+    const int* frag_nao;
+    const int* frag_ao0;
+    const int* frag_sp0;
+    const int* frag_nocc;
+    const int64_t* frag_moff;
+    const int64_t* frag_eoff;
+    const int* frag_pp0;   // [n_frag*kClasses] first prim pair of class L in the class array
+    const int* frag_npp;   // [n_frag*kClasses]
+    const int* frag_nbr0;  // [n_frag+1] CSR neighbour list
+    const int* nbr;        // neighbour fragment ids
+    const int* nbr_pair;   // pair index of each CSR entry
+    // shells / prims / AOs
+    const int* sh_l;
+    const int* sh_np;
+    const int* sh_p0;
+    const int* sh_ao;
+    const int* sh_atom;
+    const double* p_exp;
+    const double* p_coef;
+    const double* ao_scale;
+    const int* ao_sh;      // [n_ao_total] global shell of each AO
+    const int* ao_k;       // [n_ao_total] Cartesian component inside its shell
+    // shell pairs
+    const int* sp_a;
+    const int* sp_b;
+    const int* sp_L;
+    const int* sp_pp0;
+    const double* sp_Q;
+    // primitive pairs per class
+    const double4_32a* pp_P[kClasses];
+    const float4* pp_Pf[kClasses];
+    const double* pp_K[kClasses];
+    const int* pp_sp[kClasses];
+    const int* pp_ij[kClasses];  // i * 16 + j
+    const float* pp_Q[kClasses];
+    double* pp_Dh[kClasses];
+    double* pp_Jh[kClasses];
+    int n_pp[kClasses];
+    // fragment pairs
+    const int* pair_x;
+    const int* pair_y;
+    // tables / scratch
+    const double* boys;
+    int* err_flag;
+};
+
+// Host-side context.
+struct Buffers;
+}  // namespace fef
+
+struct fef_ctx {
+    fef_options opt;
+    cudaStream_t stream = nullptr;
+    int device = 0;
+    int n_frag = 0, n_atoms = 0, n_shells = 0, n_prims = 0, n_sp = 0, n_pairs = 0;
+    int64_t mat_total = 0, eri_total = 0;
+    int max_nao = 0, max_nmo = 0;
+    std::vector<int> nao, nmo, nocc;
+    std::vector<int64_t> moff;
+    std::vector<int> h_pair_x, h_pair_y;
+    fef::Dev dev{};
+    fef::Buffers* buf = nullptr;
+    // counters
+    int64_t shell_quartets = 0, prim_quartets = 0;
+    double jengine_ms = 0.0;
+    bool have_density = false;
+    bool energies_valid = false;
+    std::string last_error;
+};
+
+namespace fef {
+
+// ---- kernels launched by the API layer (each returns cudaGetLastError()) ----
+cudaError_t launch_prepare(const Dev& d, const double* xyz_A, double* atom_xyz, double* p_coef_out,
+                           const double* p_coef_raw, const int* p_l, int n_prims, cudaStream_t s);
+cudaError_t launch_boys_table(double* table, cudaStream_t s);
+cudaError_t launch_ao_scale(const Dev& d, double* ao_scale, int n_ao_total, const int* ao_frag, cudaStream_t s);
+cudaError_t launch_prim_pairs(const Dev& d, double4_32a* P[kClasses], float4* Pf[kClasses], double* K[kClasses],
+                              cudaStream_t s);
+cudaError_t launch_one_electron(const Dev& d, double* S, double* h, cudaStream_t s);
+cudaError_t launch_intra_eri(const Dev& d, double* eri, int max_l, cudaStream_t s);
+cudaError_t launch_schwarz(const Dev& d, const double* eri, double* sp_Q, float* pp_Q[kClasses], cudaStream_t s);
+cudaError_t launch_coulomb_exchange(const Dev& d, const double* eri, double* eric, cudaStream_t s);
+cudaError_t launch_neighbours(const Dev& d, double cutoff_bohr, unsigned char* flags, cudaStream_t s);
+cudaError_t launch_nuclear_env(const Dev& d, double* V, cudaStream_t s);
+cudaError_t launch_nuclear_traces(const Dev& d, const double* D, double* trace_xy, double* trace_yx, cudaStream_t s);
+cudaError_t launch_nuclear_repulsion(const Dev& d, double* e_nn_intra, double* e_nn_pair, cudaStream_t s);
+cudaError_t launch_orthogonaliser(const Dev& d, const double* S, double* X, int* nmo, double s_min, int max_n,
+                                  cudaStream_t s);
+cudaError_t launch_hermite_density(const Dev& d, const double* D, cudaStream_t s);
+cudaError_t launch_jengine(const Dev& d, const int2* tiles[kClasses][kClasses], const int* n_tiles, double tau,
+                           double* e_pair, int mixed, cudaStream_t s);
+cudaError_t launch_back_transform(const Dev& d, double* J, cudaStream_t s);
+// F = h + C D + V_env + J_env per fragment; E_int[x] = tr[D (h + G/2)] + e_nn[x]; tr_omega[x] = tr[D (V+J)]
+cudaError_t launch_fock_energy(const Dev& d, const double* h, const double* Venv, const double* Jenv,
+                               const double* eric, const double* D, double* F, double* omega, const double* e_nn,
+                               double* E_int, double* tr_omega, cudaStream_t s);
+cudaError_t launch_count_quartets(const Dev& d, double tau, unsigned long long* count, cudaStream_t s);
+
+struct ScfArgs {
+    const double* h;        // packed
+    const double* omega;    // packed environment field (may be null: isolated)
+    const double* S;
+    const double* X;
+    const int* nmo;
+    const double* eric;
+    const double* e_nn;     // [n_frag] own nuclear repulsion
+    double* D;              // in: start (if have_start), out: converged
+    double* F;              // out: Fock of the returned D
+    double* diis_F;         // scratch [n_frag][diis][n^2]
+    double* diis_e;         // scratch [n_frag][diis][n^2]
+    int64_t diis_stride;    // per fragment doubles
+    double* E_scf;          // [n_frag]
+    double* E_int;          // [n_frag]
+    int* iters;             // [n_frag]
+    int have_start;
+    int max_iter, diis_size;
+    double e_tol, comm_tol;
+};
+cudaError_t launch_fragment_scf(const Dev& d, const ScfArgs& a, int max_n, cudaStream_t s);
+
+cudaError_t launch_energies(const Dev& d, const double* e_J, const double* tr_xy, const double* tr_yx,
+                            const double* e_nn_pair, const double* E_int, double* E_pair, double* E_frag,
+                            double* E_tot, cudaStream_t s);
+cudaError_t launch_check_finite(const double* a, int64_t n, int* flag, cudaStream_t s);
+
+cudaError_t measure_fma_peak(double* fp64, double* fp32, double* mhz);
+
+}  // namespace fef

@@ -1,0 +1,599 @@
+// Geometry-time kernels of the FEF context: basis normalisation, the Boys table, primitive pairs,
+// one-electron matrices (S, h = T + V_own), the intra-fragment two-electron tensor and its
+// Coulomb-minus-half-exchange form, Schwarz factors, the fragment neighbour test, the environment
+// nuclear attraction h~ (paper, "Fragment Mean Field", the equation after Eq. wc) and nuclear
+// repulsion.  All integrals use McMurchie-Davidson Hermite expansions (common.cuh).
+#include "common.cuh"
+#include "internal.hpp"
+
+namespace fef {
+
+// ------------------------------------------------------------------------------------------ prepare
+__global__ void k_prepare(int n_atoms, const double* xyz_A, double* xyz_bohr, int n_prims, const double* exps,
+                          const double* coef_raw, const int* p_l, double* coef)
+{
+    const double bohr_per_A = 1.0 / 0.529177210903;
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < 3 * n_atoms) xyz_bohr[i] = xyz_A[i] * bohr_per_A;
+    if (i < n_prims) coef[i] = coef_raw[i] * prim_norm(exps[i], p_l[i]);
+}
+
+cudaError_t launch_prepare(const Dev& d, const double* xyz_A, double* atom_xyz, double* p_coef_out,
+                           const double* p_coef_raw, const int* p_l, int n_prims, cudaStream_t s)
+{
+    int n = max(3 * d.n_atoms, n_prims);
+    k_prepare<<<(n + 255) / 256, 256, 0, s>>>(d.n_atoms, xyz_A, atom_xyz, n_prims, d.p_exp, p_coef_raw, p_l,
+                                              p_coef_out);
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------------------------------ Boys table
+// F_n(T_k) for n = 0..14 by the series F_N(T) = exp(-T) sum_i (2T)^i / ((2N+1)(2N+3)...(2N+2i+1))
+// (all terms positive, compensated summation) and downward recursion
+// F_n = (2T F_{n+1} + exp(-T)) / (2n+1); stored as Taylor coefficients F_{m+j}(T_k)/j!.
+__global__ void k_boys_table(double* table)
+{
+    int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= kBoysRows) return;
+    const int N = kBoysM - 1 + kBoysOrder;  // 14
+    const double T = k * kBoysH;
+    double term = 1.0 / (2.0 * N + 1.0), sum = term, comp = 0.0;
+    for (int i = 1; i < 4000; ++i) {
+        term *= 2.0 * T / (2.0 * N + 2.0 * i + 1.0);
+        double y = term - comp;
+        double t = sum + y;
+        comp = (t - sum) - y;
+        sum = t;
+        if (term < 1e-20 * sum) break;
+    }
+    const double e = exp(-T);
+    double F[kBoysM + kBoysOrder];
+    F[N] = e * sum;
+    for (int n = N - 1; n >= 0; --n) F[n] = (2.0 * T * F[n + 1] + e) / (2.0 * n + 1.0);
+    double* row = table + (size_t)k * kBoysRowLen;
+    double fact = 1.0;
+    for (int m = 0; m < kBoysM; ++m) {
+        fact = 1.0;
+        for (int j = 0; j <= kBoysOrder; ++j) {
+            if (j > 0) fact *= j;
+            row[m * kBoysBlock + j] = F[m + j] / fact;
+        }
+        row[m * kBoysBlock + kBoysOrder + 1] = (m == 0) ? T : 0.0;
+    }
+}
+
+cudaError_t launch_boys_table(double* table, cudaStream_t s)
+{
+    k_boys_table<<<(kBoysRows + 127) / 128, 128, 0, s>>>(table);
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------------------------------ AO scale
+// Raw self-overlap of contracted AO (lx,ly,lz): sum_ij c_i c_j (pi/p)^{3/2} prod_d E^{l_d l_d}_0 with
+// both primitives on one centre (X_PA = X_PB = 0); the AO scale makes it 1.
+__global__ void k_ao_scale(Dev d, double* ao_scale, int n_ao_total)
+{
+    int g = blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= n_ao_total) return;
+    int sh = d.ao_sh[g], k = d.ao_k[g];
+    int l = d.sh_l[sh], np = d.sh_np[sh], p0 = d.sh_p0[sh];
+    int lc[3];
+    cart_of(l, k, lc[0], lc[1], lc[2]);
+    double S = 0.0;
+    for (int i = 0; i < np; ++i)
+        for (int j = 0; j < np; ++j) {
+            double a = d.p_exp[p0 + i], b = d.p_exp[p0 + j], p = a + b;
+            double v = d.p_coef[p0 + i] * d.p_coef[p0 + j] * pow(kPi / p, 1.5);
+            for (int dd = 0; dd < 3; ++dd) {
+                double E[3][3][5];
+                md_E1(lc[dd], lc[dd], p, 0.0, 0.0, E);
+                v *= E[lc[dd]][lc[dd]][0];
+            }
+            S += v;
+        }
+    ao_scale[g] = 1.0 / sqrt(S);
+}
+
+cudaError_t launch_ao_scale(const Dev& d, double* ao_scale, int n_ao_total, const int*, cudaStream_t s)
+{
+    k_ao_scale<<<(n_ao_total + 127) / 128, 128, 0, s>>>(d, ao_scale, n_ao_total);
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------------------------------ prim pairs
+// P = (a A + b B)/p, p = a + b, K = c_i c_j exp(-a b/p |AB|^2), for every primitive pair.
+__global__ void k_prim_pairs(Dev d, int L, double4_32a* P, float4* Pf, double* K)
+{
+    int g = blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= d.n_pp[L]) return;
+    int sp = d.pp_sp[L][g], ij = d.pp_ij[L][g];
+    int sa = d.sp_a[sp], sb = d.sp_b[sp];
+    int pa = d.sh_p0[sa] + (ij >> 4), pb = d.sh_p0[sb] + (ij & 15);
+    const double* A = d.atom_xyz + 3 * d.sh_atom[sa];
+    const double* B = d.atom_xyz + 3 * d.sh_atom[sb];
+    double a = d.p_exp[pa], b = d.p_exp[pb], p = a + b;
+    double R2 = 0.0, Pc[3];
+    for (int k = 0; k < 3; ++k) {
+        Pc[k] = (a * A[k] + b * B[k]) / p;
+        R2 += (A[k] - B[k]) * (A[k] - B[k]);
+    }
+    P[g] = make_double4_32a(Pc[0], Pc[1], Pc[2], p);
+    Pf[g] = make_float4((float)Pc[0], (float)Pc[1], (float)Pc[2], (float)p);
+    K[g] = d.p_coef[pa] * d.p_coef[pb] * exp(-a * b / p * R2);
+}
+
+cudaError_t launch_prim_pairs(const Dev& d, double4_32a* P[kClasses], float4* Pf[kClasses], double* K[kClasses],
+                              cudaStream_t s)
+{
+    for (int L = 0; L < kClasses; ++L)
+        if (d.n_pp[L] > 0) k_prim_pairs<<<(d.n_pp[L] + 127) / 128, 128, 0, s>>>(d, L, P[L], Pf[L], K[L]);
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------------------------------ one-electron
+struct AOPair {
+    int la, lb;
+    int ca[3], cb[3];
+    int pa0, pb0, na, nb;
+    const double* A;
+    const double* B;
+    double scale;
+};
+
+__device__ inline AOPair ao_pair(const Dev& d, int x, int mu, int nu)
+{
+    AOPair q;
+    int gmu = d.frag_ao0[x] + mu, gnu = d.frag_ao0[x] + nu;
+    int sa = d.ao_sh[gmu], sb = d.ao_sh[gnu];
+    q.la = d.sh_l[sa];
+    q.lb = d.sh_l[sb];
+    cart_of(q.la, d.ao_k[gmu], q.ca[0], q.ca[1], q.ca[2]);
+    cart_of(q.lb, d.ao_k[gnu], q.cb[0], q.cb[1], q.cb[2]);
+    q.pa0 = d.sh_p0[sa];
+    q.pb0 = d.sh_p0[sb];
+    q.na = d.sh_np[sa];
+    q.nb = d.sh_np[sb];
+    q.A = d.atom_xyz + 3 * d.sh_atom[sa];
+    q.B = d.atom_xyz + 3 * d.sh_atom[sb];
+    q.scale = d.ao_scale[gmu] * d.ao_scale[gnu];
+    return q;
+}
+
+// 1D overlap integrals E^{ij}_0 for j up to jmax <= 4 (kinetic needs j+2).
+__device__ inline void e1_overlap(int imax, int jmax, double p, double XPA, double XPB, double (*E)[5][7])
+{
+    const double h = 0.5 / p;
+    for (int i = 0; i <= imax; ++i)
+        for (int j = 0; j <= jmax; ++j)
+            for (int t = 0; t < 7; ++t) E[i][j][t] = 0.0;
+    E[0][0][0] = 1.0;
+    for (int i = 0; i < imax; ++i)
+        for (int t = 0; t <= i + 1; ++t) {
+            double v = XPA * (t <= i ? E[i][0][t] : 0.0);
+            if (t > 0) v += h * E[i][0][t - 1];
+            if (t + 1 <= i) v += (t + 1) * E[i][0][t + 1];
+            E[i + 1][0][t] = v;
+        }
+    for (int i = 0; i <= imax; ++i)
+        for (int j = 0; j < jmax; ++j)
+            for (int t = 0; t <= i + j + 1 && t < 7; ++t) {
+                double v = XPB * (t <= i + j ? E[i][j][t] : 0.0);
+                if (t > 0) v += h * E[i][j][t - 1];
+                if (t + 1 <= i + j) v += (t + 1) * E[i][j][t + 1];
+                E[i][j + 1][t] = v;
+            }
+}
+
+// Nuclear attraction of one primitive pair to a set of point charges:
+//   sum_C -Z_C (2 pi/p) sum_tuv E^x_t E^y_u E^z_v R_tuv(p, P - C).
+__device__ inline double nuclear_prim(const Dev& d, const AOPair& q, double a, double b, const double (*Ex)[3][5],
+                                      const double (*Ey)[3][5], const double (*Ez)[3][5], const double* P, double p,
+                                      int atom0, int natoms)
+{
+    int L = q.la + q.lb;
+    double acc = 0.0;
+    double R[nh(kMaxLPair)], base[kMaxLPair + 1], F[kMaxLPair + 1];
+    for (int c = atom0; c < atom0 + natoms; ++c) {
+        const double* C = d.atom_xyz + 3 * c;
+        double X = P[0] - C[0], Y = P[1] - C[1], Z = P[2] - C[2];
+        double T = p * (X * X + Y * Y + Z * Z);
+        boys_fp64_rt(d.boys, T, L, F);
+        double f = 1.0;
+        for (int n = 0; n <= L; ++n) {
+            base[n] = f * F[n];
+            f *= -2.0 * p;
+        }
+        md_R_rt(L, R, base, X, Y, Z);
+        double v = 0.0;
+        for (int t = 0; t <= q.ca[0] + q.cb[0]; ++t)
+            for (int u = 0; u <= q.ca[1] + q.cb[1]; ++u)
+                for (int w = 0; w <= q.ca[2] + q.cb[2]; ++w)
+                    v += Ex[q.ca[0]][q.cb[0]][t] * Ey[q.ca[1]][q.cb[1]][u] * Ez[q.ca[2]][q.cb[2]][w] * R[hidx(t, u, w)];
+        acc -= d.atom_Z[c] * v;
+    }
+    return acc * 2.0 * kPi / p;
+}
+
+// S, T and V(own nuclei) for every (x, mu, nu); h = T + V.
+__global__ void k_one_electron(Dev d, double* Sout, double* hout)
+{
+    int x = blockIdx.y;
+    int n = d.frag_nao[x];
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n * n; e += gridDim.x * blockDim.x) {
+        int mu = e / n, nu = e % n;
+        AOPair q = ao_pair(d, x, mu, nu);
+        double S = 0.0, T = 0.0, V = 0.0;
+        for (int i = 0; i < q.na; ++i)
+            for (int j = 0; j < q.nb; ++j) {
+                double a = d.p_exp[q.pa0 + i], b = d.p_exp[q.pb0 + j], p = a + b;
+                double cc = d.p_coef[q.pa0 + i] * d.p_coef[q.pb0 + j];
+                double P[3], R2 = 0.0;
+                double Es[3][3][5][7];
+                double E[3][3][3][5];
+                for (int k = 0; k < 3; ++k) {
+                    P[k] = (a * q.A[k] + b * q.B[k]) / p;
+                    R2 += (q.A[k] - q.B[k]) * (q.A[k] - q.B[k]);
+                    e1_overlap(q.ca[k], q.cb[k] + 2, p, P[k] - q.A[k], P[k] - q.B[k], Es[k]);
+                    md_E1(q.la, q.lb, p, P[k] - q.A[k], P[k] - q.B[k], E[k]);
+                }
+                double K = cc * exp(-a * b / p * R2);
+                double s1[3], t1[3];
+                for (int k = 0; k < 3; ++k) {
+                    int i1 = q.ca[k], j1 = q.cb[k];
+                    s1[k] = Es[k][i1][j1][0];
+                    // d^2/dx^2 acting on x_B^j exp(-b x_B^2): j(j-1) x^{j-2} - 2b(2j+1) x^j + 4b^2 x^{j+2}
+                    double v = -2.0 * b * (2 * j1 + 1) * Es[k][i1][j1][0] + 4.0 * b * b * Es[k][i1][j1 + 2][0];
+                    if (j1 >= 2) v += j1 * (j1 - 1) * Es[k][i1][j1 - 2][0];
+                    t1[k] = v;
+                }
+                double pre = K * pow(kPi / p, 1.5);
+                S += pre * s1[0] * s1[1] * s1[2];
+                T += pre * -0.5 * (t1[0] * s1[1] * s1[2] + s1[0] * t1[1] * s1[2] + s1[0] * s1[1] * t1[2]);
+                V += K * nuclear_prim(d, q, a, b, E[0], E[1], E[2], P, p, d.frag_atom0[x], d.frag_nat[x]);
+            }
+        int64_t o = d.frag_moff[x] + e;
+        Sout[o] = S * q.scale;
+        hout[o] = (T + V) * q.scale;
+    }
+}
+
+cudaError_t launch_one_electron(const Dev& d, double* S, double* h, cudaStream_t s)
+{
+    dim3 g((d.max_nao * d.max_nao + 127) / 128, d.n_frag);
+    k_one_electron<<<g, 128, 0, s>>>(d, S, h);
+    return cudaGetLastError();
+}
+
+// Environment nuclear attraction: V_env^x = sum_{y in N(x)} V^y, V^y_{mu nu} = -sum_{B in y} Z_B <mu|1/r_B|nu>.
+__global__ void k_nuclear_env(Dev d, double* V)
+{
+    int x = blockIdx.y;
+    int n = d.frag_nao[x];
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n * n; e += gridDim.x * blockDim.x) {
+        int mu = e / n, nu = e % n;
+        AOPair q = ao_pair(d, x, mu, nu);
+        double acc = 0.0;
+        for (int i = 0; i < q.na; ++i)
+            for (int j = 0; j < q.nb; ++j) {
+                double a = d.p_exp[q.pa0 + i], b = d.p_exp[q.pb0 + j], p = a + b;
+                double cc = d.p_coef[q.pa0 + i] * d.p_coef[q.pb0 + j];
+                double P[3], R2 = 0.0, E[3][3][3][5];
+                for (int k = 0; k < 3; ++k) {
+                    P[k] = (a * q.A[k] + b * q.B[k]) / p;
+                    R2 += (q.A[k] - q.B[k]) * (q.A[k] - q.B[k]);
+                    md_E1(q.la, q.lb, p, P[k] - q.A[k], P[k] - q.B[k], E[k]);
+                }
+                double K = cc * exp(-a * b / p * R2);
+                double v = 0.0;
+                for (int c = d.frag_nbr0[x]; c < d.frag_nbr0[x + 1]; ++c) {
+                    int y = d.nbr[c];
+                    v += nuclear_prim(d, q, a, b, E[0], E[1], E[2], P, p, d.frag_atom0[y], d.frag_nat[y]);
+                }
+                acc += K * v;
+            }
+        V[d.frag_moff[x] + e] = acc * q.scale;
+    }
+}
+
+cudaError_t launch_nuclear_env(const Dev& d, double* V, cudaStream_t s)
+{
+    dim3 g((d.max_nao * d.max_nao + 127) / 128, d.n_frag);
+    k_nuclear_env<<<g, 128, 0, s>>>(d, V);
+    return cudaGetLastError();
+}
+
+// tr(D^x V^y) for each pair, both directions: block (pair, direction), threads over mu nu of the
+// fragment whose electrons feel the other's nuclei.
+__global__ void k_nuclear_traces(Dev d, const double* D, double* tr_xy, double* tr_yx)
+{
+    int pr = blockIdx.x, dir = blockIdx.y;
+    int x = dir == 0 ? d.pair_x[pr] : d.pair_y[pr];
+    int y = dir == 0 ? d.pair_y[pr] : d.pair_x[pr];
+    int n = d.frag_nao[x];
+    double acc = 0.0;
+    for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
+        int mu = e / n, nu = e % n;
+        AOPair q = ao_pair(d, x, mu, nu);
+        double v = 0.0;
+        for (int i = 0; i < q.na; ++i)
+            for (int j = 0; j < q.nb; ++j) {
+                double a = d.p_exp[q.pa0 + i], b = d.p_exp[q.pb0 + j], p = a + b;
+                double cc = d.p_coef[q.pa0 + i] * d.p_coef[q.pb0 + j];
+                double P[3], R2 = 0.0, E[3][3][3][5];
+                for (int k = 0; k < 3; ++k) {
+                    P[k] = (a * q.A[k] + b * q.B[k]) / p;
+                    R2 += (q.A[k] - q.B[k]) * (q.A[k] - q.B[k]);
+                    md_E1(q.la, q.lb, p, P[k] - q.A[k], P[k] - q.B[k], E[k]);
+                }
+                v += cc * exp(-a * b / p * R2) *
+                     nuclear_prim(d, q, a, b, E[0], E[1], E[2], P, p, d.frag_atom0[y], d.frag_nat[y]);
+            }
+        acc += v * q.scale * D[d.frag_moff[x] + e];
+    }
+    __shared__ double red[256];
+    red[threadIdx.x] = acc;
+    __syncthreads();
+    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+        if (threadIdx.x < s) red[threadIdx.x] += red[threadIdx.x + s];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) (dir == 0 ? tr_xy : tr_yx)[pr] = red[0];
+}
+
+cudaError_t launch_nuclear_traces(const Dev& d, const double* D, double* tr_xy, double* tr_yx, cudaStream_t s)
+{
+    if (d.n_pairs == 0) return cudaSuccess;
+    dim3 g(d.n_pairs, 2);
+    k_nuclear_traces<<<g, 256, 0, s>>>(d, D, tr_xy, tr_yx);
+    return cudaGetLastError();
+}
+
+// Nuclear repulsion: sum_{A<B in x} Z_A Z_B/R_AB per fragment, sum_{A in x, B in y} per pair.
+__global__ void k_nuclear_repulsion(Dev d, double* e_intra, double* e_pair)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < d.n_frag) {
+        double e = 0.0;
+        int a0 = d.frag_atom0[i], na = d.frag_nat[i];
+        for (int a = a0; a < a0 + na; ++a)
+            for (int b = a0; b < a; ++b) {
+                const double *A = d.atom_xyz + 3 * a, *B = d.atom_xyz + 3 * b;
+                double r = sqrt((A[0] - B[0]) * (A[0] - B[0]) + (A[1] - B[1]) * (A[1] - B[1]) + (A[2] - B[2]) * (A[2] - B[2]));
+                e += d.atom_Z[a] * d.atom_Z[b] / r;
+            }
+        e_intra[i] = e;
+    }
+    if (i < d.n_pairs) {
+        int x = d.pair_x[i], y = d.pair_y[i];
+        double e = 0.0;
+        for (int a = d.frag_atom0[x]; a < d.frag_atom0[x] + d.frag_nat[x]; ++a)
+            for (int b = d.frag_atom0[y]; b < d.frag_atom0[y] + d.frag_nat[y]; ++b) {
+                const double *A = d.atom_xyz + 3 * a, *B = d.atom_xyz + 3 * b;
+                double r = sqrt((A[0] - B[0]) * (A[0] - B[0]) + (A[1] - B[1]) * (A[1] - B[1]) + (A[2] - B[2]) * (A[2] - B[2]));
+                e += d.atom_Z[a] * d.atom_Z[b] / r;
+            }
+        e_pair[i] = e;
+    }
+}
+
+cudaError_t launch_nuclear_repulsion(const Dev& d, double* e_nn_intra, double* e_nn_pair, cudaStream_t s)
+{
+    int n = max(d.n_frag, d.n_pairs);
+    k_nuclear_repulsion<<<(n + 127) / 128, 128, 0, s>>>(d, e_nn_intra, e_nn_pair);
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------------------------------ intra ERIs
+// One thread per (x, shell pair ab, shell pair cd) of the same fragment (a <= b, c <= d): the
+// contracted block (ab|cd) by McMurchie-Davidson,
+//   (mu nu|lambda sigma) = sum_{PQ} 2 pi^{5/2}/(p q sqrt(p+q)) sum_{tuv,t'u'v'} E^{mu nu}_{tuv}
+//                          (-1)^{t'+u'+v'} E^{lambda sigma}_{t'u'v'} R_{t+t',u+u',v+v'}(alpha, PQ),
+// written to every position of the full n^4 tensor that the block covers (mu nu, nu mu x
+// lambda sigma, sigma lambda).  NB is the per-thread block capacity (ncart(lmax)^4).
+template <int NB>
+__global__ void k_intra_eri(Dev d, double* eri)
+{
+    int x = blockIdx.y;
+    int sp0 = d.frag_sp0[x], nsp = d.frag_sp0[x + 1] - sp0;
+    int n = d.frag_nao[x];
+    double* out = eri + d.frag_eoff[x];
+    for (int w = blockIdx.x * blockDim.x + threadIdx.x; w < nsp * nsp; w += gridDim.x * blockDim.x) {
+        int s1 = sp0 + w / nsp, s2 = sp0 + w % nsp;
+        int sa = d.sp_a[s1], sb = d.sp_b[s1], sc = d.sp_a[s2], sd = d.sp_b[s2];
+        int la = d.sh_l[sa], lb = d.sh_l[sb], lc = d.sh_l[sc], ld = d.sh_l[sd];
+        int na = ncart(la), nb = ncart(lb), nc = ncart(lc), nd = ncart(ld);
+        int L = la + lb + lc + ld;
+        double blk[NB];
+        for (int k = 0; k < na * nb * nc * nd; ++k) blk[k] = 0.0;
+        const double *A = d.atom_xyz + 3 * d.sh_atom[sa], *B = d.atom_xyz + 3 * d.sh_atom[sb];
+        const double *C = d.atom_xyz + 3 * d.sh_atom[sc], *Dc = d.atom_xyz + 3 * d.sh_atom[sd];
+        double AB2 = 0, CD2 = 0;
+        for (int k = 0; k < 3; ++k) {
+            AB2 += (A[k] - B[k]) * (A[k] - B[k]);
+            CD2 += (C[k] - Dc[k]) * (C[k] - Dc[k]);
+        }
+        for (int i = 0; i < d.sh_np[sa]; ++i)
+            for (int j = 0; j < d.sh_np[sb]; ++j) {
+                double a = d.p_exp[d.sh_p0[sa] + i], b = d.p_exp[d.sh_p0[sb] + j], p = a + b;
+                double Kab = d.p_coef[d.sh_p0[sa] + i] * d.p_coef[d.sh_p0[sb] + j] * exp(-a * b / p * AB2);
+                double P[3], Eb[3][3][3][5];
+                for (int k = 0; k < 3; ++k) {
+                    P[k] = (a * A[k] + b * B[k]) / p;
+                    md_E1(la, lb, p, P[k] - A[k], P[k] - B[k], Eb[k]);
+                }
+                for (int k2 = 0; k2 < d.sh_np[sc]; ++k2)
+                    for (int l2 = 0; l2 < d.sh_np[sd]; ++l2) {
+                        double c = d.p_exp[d.sh_p0[sc] + k2], e = d.p_exp[d.sh_p0[sd] + l2], q = c + e;
+                        double Kcd = d.p_coef[d.sh_p0[sc] + k2] * d.p_coef[d.sh_p0[sd] + l2] * exp(-c * e / q * CD2);
+                        double Q[3], Ek[3][3][3][5];
+                        for (int k = 0; k < 3; ++k) {
+                            Q[k] = (c * C[k] + e * Dc[k]) / q;
+                            md_E1(lc, ld, q, Q[k] - C[k], Q[k] - Dc[k], Ek[k]);
+                        }
+                        double alpha = p * q / (p + q);
+                        double X = P[0] - Q[0], Y = P[1] - Q[1], Z = P[2] - Q[2];
+                        double F[kMaxLTot + 1], base[kMaxLTot + 1], R[nh(kMaxLTot)];
+                        boys_fp64_rt(d.boys, alpha * (X * X + Y * Y + Z * Z), L, F);
+                        double pre = 2.0 * pow(kPi, 2.5) / (p * q * sqrt(p + q)) * Kab * Kcd;
+                        for (int m = 0; m <= L; ++m) {
+                            base[m] = pre * F[m];
+                            pre *= -2.0 * alpha;
+                        }
+                        md_R_rt(L, R, base, X, Y, Z);
+                        int kk = 0;
+                        for (int ia = 0; ia < na; ++ia) {
+                            int ax, ay, az;
+                            cart_of(la, ia, ax, ay, az);
+                            for (int ib = 0; ib < nb; ++ib) {
+                                int bx, by, bz;
+                                cart_of(lb, ib, bx, by, bz);
+                                for (int ic = 0; ic < nc; ++ic) {
+                                    int cx, cy, cz;
+                                    cart_of(lc, ic, cx, cy, cz);
+                                    for (int id = 0; id < nd; ++id, ++kk) {
+                                        int dx, dy, dz;
+                                        cart_of(ld, id, dx, dy, dz);
+                                        double v = 0.0;
+                                        for (int t = 0; t <= ax + bx; ++t)
+                                            for (int u = 0; u <= ay + by; ++u)
+                                                for (int vv = 0; vv <= az + bz; ++vv) {
+                                                    double eb = Eb[0][ax][bx][t] * Eb[1][ay][by][u] * Eb[2][az][bz][vv];
+                                                    double s = 0.0;
+                                                    for (int t2 = 0; t2 <= cx + dx; ++t2)
+                                                        for (int u2 = 0; u2 <= cy + dy; ++u2)
+                                                            for (int v2 = 0; v2 <= cz + dz; ++v2) {
+                                                                double ek = Ek[0][cx][dx][t2] * Ek[1][cy][dy][u2] *
+                                                                            Ek[2][cz][dz][v2];
+                                                                double r = R[hidx(t + t2, u + u2, vv + v2)];
+                                                                s += ((t2 + u2 + v2) & 1) ? -ek * r : ek * r;
+                                                            }
+                                                    v += eb * s;
+                                                }
+                                        blk[kk] += v;
+                                    }
+                                }
+                            }
+                        }
+                    }
+            }
+        int ga = d.sh_ao[sa], gb = d.sh_ao[sb], gc = d.sh_ao[sc], gd = d.sh_ao[sd];
+        int ao0 = d.frag_ao0[x];
+        int kk = 0;
+        for (int ia = 0; ia < na; ++ia)
+            for (int ib = 0; ib < nb; ++ib)
+                for (int ic = 0; ic < nc; ++ic)
+                    for (int id = 0; id < nd; ++id, ++kk) {
+                        int mu = ga + ia, nu = gb + ib, la_ = gc + ic, si = gd + id;
+                        double v = blk[kk] * d.ao_scale[ao0 + mu] * d.ao_scale[ao0 + nu] * d.ao_scale[ao0 + la_] *
+                                   d.ao_scale[ao0 + si];
+                        size_t n2 = (size_t)n * n;
+                        out[((size_t)mu * n + nu) * n2 + (size_t)la_ * n + si] = v;
+                        out[((size_t)nu * n + mu) * n2 + (size_t)la_ * n + si] = v;
+                        out[((size_t)mu * n + nu) * n2 + (size_t)si * n + la_] = v;
+                        out[((size_t)nu * n + mu) * n2 + (size_t)si * n + la_] = v;
+                    }
+    }
+}
+
+cudaError_t launch_intra_eri(const Dev& d, double* eri, int max_l, cudaStream_t s)
+{
+    // one thread per shell-pair pair of the largest fragment, grid-strided
+    int max_sp = d.max_nao * (d.max_nao + 1) / 2;
+    dim3 g((unsigned)std::min<long long>(((long long)max_sp * max_sp + 127) / 128, 4096), d.n_frag);
+    if (max_l <= 1)
+        k_intra_eri<81><<<g, 128, 0, s>>>(d, eri);
+    else
+        k_intra_eri<1296><<<g, 128, 0, s>>>(d, eri);
+    return cudaGetLastError();
+}
+
+// Coulomb-minus-half-exchange tensor, so that G[D] = J[D] - K[D]/2 is one contraction:
+//   C[mu nu][lambda sigma] = (mu nu|lambda sigma) - (1/2) (mu lambda|nu sigma).
+__global__ void k_coulomb_exchange(Dev d, const double* eri, double* eric)
+{
+    int x = blockIdx.y;
+    int n = d.frag_nao[x];
+    size_t n2 = (size_t)n * n, n4 = n2 * n2;
+    const double* e = eri + d.frag_eoff[x];
+    double* c = eric + d.frag_eoff[x];
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n4; i += (size_t)gridDim.x * blockDim.x) {
+        size_t mn = i / n2, ls = i % n2;
+        int mu = mn / n, nu = mn % n, la = ls / n, si = ls % n;
+        c[i] = e[i] - 0.5 * e[((size_t)mu * n + la) * n2 + (size_t)nu * n + si];
+    }
+}
+
+cudaError_t launch_coulomb_exchange(const Dev& d, const double* eri, double* eric, cudaStream_t s)
+{
+    size_t n4 = (size_t)d.max_nao * d.max_nao * d.max_nao * d.max_nao;
+    dim3 g((unsigned)std::min<size_t>((n4 + 255) / 256, 8192), d.n_frag);
+    k_coulomb_exchange<<<g, 256, 0, s>>>(d, eri, eric);
+    return cudaGetLastError();
+}
+
+// Schwarz factors Q_ab = max_{mu in a, nu in b} sqrt|(mu nu|mu nu)| from the intra tensor; each
+// primitive pair of the shell pair gets a float copy for the J-engine's screening test.
+__global__ void k_schwarz(Dev d, const double* eri, double* sp_Q, float* pq0, float* pq1, float* pq2, float* pq3,
+                          float* pq4)
+{
+    int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= d.n_sp) return;
+    int sa = d.sp_a[s], sb = d.sp_b[s];
+    int x = 0;
+    {  // fragment of the shell pair: binary search over frag_sp0
+        int lo = 0, hi = d.n_frag - 1;
+        while (lo < hi) {
+            int mid = (lo + hi + 1) / 2;
+            if (d.frag_sp0[mid] <= s) lo = mid; else hi = mid - 1;
+        }
+        x = lo;
+    }
+    int n = d.frag_nao[x];
+    size_t n2 = (size_t)n * n;
+    const double* e = eri + d.frag_eoff[x];
+    double q = 0.0;
+    for (int ia = 0; ia < ncart(d.sh_l[sa]); ++ia)
+        for (int ib = 0; ib < ncart(d.sh_l[sb]); ++ib) {
+            int mu = d.sh_ao[sa] + ia, nu = d.sh_ao[sb] + ib;
+            size_t mn = (size_t)mu * n + nu;
+            q = fmax(q, fabs(e[mn * n2 + mn]));
+        }
+    q = sqrt(q);
+    sp_Q[s] = q;
+    float* pq[kClasses] = {pq0, pq1, pq2, pq3, pq4};
+    int L = d.sp_L[s];
+    int np = d.sh_np[sa] * d.sh_np[sb];
+    for (int k = 0; k < np; ++k) pq[L][d.sp_pp0[s] + k] = (float)q;
+}
+
+cudaError_t launch_schwarz(const Dev& d, const double* eri, double* sp_Q, float* pp_Q[kClasses], cudaStream_t s)
+{
+    k_schwarz<<<(d.n_sp + 127) / 128, 128, 0, s>>>(d, eri, sp_Q, pp_Q[0], pp_Q[1], pp_Q[2], pp_Q[3], pp_Q[4]);
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------------------------------ neighbours
+// flags[x * n_frag + y] = 1 for y > x when min_{A in x, B in y} |R_A - R_B| < cutoff (bohr).
+__global__ void k_neighbours(Dev d, double cutoff, unsigned char* flags)
+{
+    int x = blockIdx.y;
+    for (int y = x + 1 + blockIdx.x * blockDim.x + threadIdx.x; y < d.n_frag; y += gridDim.x * blockDim.x) {
+        double best = 1e300;
+        for (int a = d.frag_atom0[x]; a < d.frag_atom0[x] + d.frag_nat[x]; ++a)
+            for (int b = d.frag_atom0[y]; b < d.frag_atom0[y] + d.frag_nat[y]; ++b) {
+                const double *A = d.atom_xyz + 3 * a, *B = d.atom_xyz + 3 * b;
+                double r2 = (A[0] - B[0]) * (A[0] - B[0]) + (A[1] - B[1]) * (A[1] - B[1]) + (A[2] - B[2]) * (A[2] - B[2]);
+                best = fmin(best, r2);
+            }
+        flags[(size_t)x * d.n_frag + y] = (cutoff <= 0.0 || best < cutoff * cutoff) ? 1 : 0;
+    }
+}
+
+cudaError_t launch_neighbours(const Dev& d, double cutoff_bohr, unsigned char* flags, cudaStream_t s)
+{
+    dim3 g((d.n_frag + 255) / 256, d.n_frag);
+    k_neighbours<<<g, 256, 0, s>>>(d, cutoff_bohr, flags);
+    return cudaGetLastError();
+}
+
+}  // namespace fef
