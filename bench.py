@@ -1,0 +1,347 @@
+#!/usr/bin/env python
+"""Benchmark of the FEF effective-field Fock build and FEF self-consistency on GB300.
+
+Workload: 64 water-like fragments (O 3s2p, H 2s, 3 primitives per shell, seeded random bases) in a
+12.42 A cube at 1 g/cm^3, 8 A fragment-pair cutoff, Schwarz 1e-12, FEF converged to 1e-8 Eh.
+
+One step = one complete pass of the hot path on one synthetic snapshot through the public C ABI:
+fef_create (normalisation, Boys table, one-electron and intra-fragment integrals, neighbour list,
+nuclear field, orthogonalisers, work lists) + fef_iterate (superposition start, macro-iterations of
+Hermite densities, J-engine, Fock assembly, device fragment SCF, energies) + fef_energies.
+
+value  = inter-fragment shell quartets processed (surviving quartets x Fock builds) / device time,
+         CUDA events on the context stream, L2 flushed (256 MiB write) between steps.
+e2e    = the same step plus the device->host read of every converged density, wall clock.
+roofline: the J-engine (9 class-pair kernels of one Fock build) against the FP64 ALU peak.
+--impl reference: the CPU oracle on a bounded sample of the same workload.
+
+Multi-GPU (torchrun): independent replicas, one snapshot per rank (seed = rank), no collective
+on the data path; value sums all ranks' quartets over the slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "FEF shell quartets/s & time to 1e-8 Eh FEF: mixed+learned vs FP64 (1 GB300)"
+UNIT = "shell quartets/s"
+WORKLOAD = "64 water-like fragments, 12.42 A cube (1 g/cm^3), 8 A cutoff, Schwarz 1e-12, FEF to 1e-8 Eh, FP64"
+N_WATER, CUTOFF_A, SCHWARZ, E_TOL = 64, 8.0, 1e-12, 1e-8
+SMS, SM_MAX_MHZ = 152, 2070.0
+# GB300 FP64: 1.25 TFLOP/s nominal = 152 SMs x 2 FP64 FMA/clk x 2 FLOP x 2.07 GHz
+FP64_PEAK = SMS * 2 * 2 * SM_MAX_MHZ * 1e6
+
+
+def log(*a):
+    print(*a, file=sys.stderr, flush=True)
+
+
+# ----------------------------------------------------------------------------------------- flop model
+def nh(L):
+    return (L + 1) * (L + 2) * (L + 3) // 6
+
+
+def flops_per_prim_quartet(LP, LQ):
+    """Algorithmic FP64 work of one primitive quartet of Hermite class (L_P, L_Q) in the fused
+    J-engine: 40 (setup, Boys, prefactor) + 3 per R^{(n)}_{tuv} of the MD recursion + 2 N(L_P) N(L_Q)
+    for the two contractions (field on the bra and on the ket)."""
+    L = LP + LQ
+    return 40 + 3 * sum(nh(k) for k in range(L + 1)) + 2 * nh(LP) * nh(LQ)
+
+
+def algorithmic_flops(class_quartets):
+    cq = np.asarray(class_quartets).reshape(5, 5)
+    return float(sum(cq[a, b] * flops_per_prim_quartet(a, b) for a in range(5) for b in range(5)))
+
+
+# ----------------------------------------------------------------------------------------- clocks
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled every 200 ms while running."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{gpu_index}.csv")
+
+    def __enter__(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.fh, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+            self.fh.close()
+
+    def summary(self):
+        if self.proc is None or not os.path.exists(self.path):
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax = float(parts[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ----------------------------------------------------------------------------------------- helpers
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def profile_traffic():
+    """DRAM bytes per J-engine build from the committed ncu summary, if it was taken on the
+    current J-engine source (matching hash); else None."""
+    path = os.path.join(ROOT, "profiles", "jengine_water64_fp64.txt")
+    src = os.path.join(ROOT, "paper_1708_03377_gb300", "csrc", "jengine.cu")
+    if not os.path.exists(path):
+        return None
+    h = hashlib.sha1(open(src, "rb").read()).hexdigest()[:12]
+    traffic, hh = None, None
+    for line in open(path):
+        if line.startswith("jengine_source_sha1:"):
+            hh = line.split(":", 1)[1].strip()
+        if line.startswith("dram_bytes_per_build:"):
+            traffic = float(line.split(":", 1)[1].strip())
+    return traffic if hh == h else None
+
+
+def cpu_baseline(seconds=12.0):
+    """The CPU oracle on a bounded sample of the workload: Obara-Saika ERI blocks and the J
+    contraction for the first fragment pairs of the neighbour list (shell quartets/s)."""
+    from oracle import integrals as I
+    from synth import systems as S
+    system = S.water_box(N_WATER, seed=0)
+    nf = system.n_frag
+    shells = [I.fragment_shells(system, x) for x in range(nf)]
+    t0 = time.perf_counter()
+    Q = [s.schwarz() for s in shells]
+    pairs = []
+    xyz = system.xyz
+    for x in range(nf):
+        ax = system.frag_atoms(x)
+        for y in range(x + 1, nf):
+            ay = system.frag_atoms(y)
+            if np.linalg.norm(xyz[ax][:, None] - xyz[ay][None], axis=-1).min() < CUTOFF_A:
+                pairs.append((x, y))
+    rng = np.random.default_rng(0)
+    quartets, done = 0, 0
+    for x, y in pairs:
+        e = I.eri_block(shells[x], shells[y], Q[x], Q[y], SCHWARZ)
+        nx, ny = shells[x].n_ao, shells[y].n_ao
+        D = rng.standard_normal((ny, ny))
+        _ = e.reshape(nx * nx, ny * ny) @ (D + D.T).ravel()
+        quartets += I.count_quartets(shells[x], shells[y], Q[x], Q[y], SCHWARZ)
+        done += 1
+        if time.perf_counter() - t0 > seconds:
+            break
+    dt = time.perf_counter() - t0
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    return {"value": quartets / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"Schwarz factors of all 64 fragments + Obara-Saika ERI blocks and J contraction of the "
+                      f"first {done} of {len(pairs)} fragment pairs ({quartets} shell quartets, {dt:.1f} s)"}
+
+
+# ----------------------------------------------------------------------------------------- reference arm
+def run_reference(args, ws, rank):
+    if rank != 0:
+        return 0
+    vals, times = [], []
+    for i in range(args.warmup + args.steps):
+        r = cpu_baseline(seconds=args.ref_seconds)
+        if i >= args.warmup:
+            vals.append(r["value"])
+            times.append(float(r["sample"].split(", ")[-1].split(" s")[0]))
+    v = float(np.mean(vals))
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * float(np.mean(times)), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD + " (bounded sample per step)", "n_frag": N_WATER,
+                       "cutoff_A": CUTOFF_A, "schwarz": SCHWARZ},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": r["cores"], "kind": "oracle", "sample": r["sample"]},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ----------------------------------------------------------------------------------------- our arm
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--ref-seconds", type=float, default=8.0)
+    args = ap.parse_args()
+    ws, rank, local = dist_env()
+    if args.impl == "reference":
+        return run_reference(args, ws, rank)
+
+    import torch
+    import paper_1708_03377_gb300 as fef
+    from synth import systems as S
+
+    torch.cuda.set_device(local)
+    pg = None
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+        pg = dist
+    stream = torch.cuda.Stream()
+    system = S.water_box(N_WATER, seed=rank)
+    opts = fef.fef_default_options(cutoff_A=CUTOFF_A, schwarz=SCHWARZ, e_tol=E_TOL)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    fef.lib()
+    fp64_probe, fp32_probe, _ = fef.fef_measure_fma_peak()
+
+    def one_step(read_back=False):
+        ctx = fef.fef_create_system(system, opts, stream=stream.cuda_stream)
+        t_it0 = torch.cuda.Event(enable_timing=True)
+        t_it1 = torch.cuda.Event(enable_timing=True)
+        t_it0.record(stream)
+        n_macro, dE = fef.fef_iterate(ctx)
+        t_it1.record(stream)
+        E_frag, E_tot, _ = fef.fef_energies(ctx)
+        D = fef.fef_get_densities(ctx) if read_back else None
+        st = fef.fef_stats(ctx)
+        ctx.close()
+        return dict(n_macro=n_macro, E_tot=E_tot, stats=st, ev=(t_it0, t_it1), D=D)
+
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            one_step()
+        torch.cuda.synchronize()
+        if pg:
+            pg.barrier()
+        launches0 = fef.fef_stats()["kernel_launches"]
+        step_ms, iter_ms, quartets, results = [], [], 0, []
+        with ClockSampler(local) as clk:
+            torch.cuda.synchronize()
+            if pg:
+                pg.barrier()
+            wall0 = time.perf_counter()
+            for k in range(args.steps):
+                flush.zero_()
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                r = one_step()
+                e1.record(stream)
+                e1.synchronize()
+                step_ms.append(e0.elapsed_time(e1))
+                iter_ms.append(r["ev"][0].elapsed_time(r["ev"][1]))
+                quartets += r["stats"]["shell_quartets"] * (r["n_macro"] + 1)
+                results.append(r)
+            torch.cuda.synchronize()
+            if pg:
+                pg.barrier()
+            wall = time.perf_counter() - wall0
+        launches = fef.fef_stats()["kernel_launches"] - launches0
+        clocks = clk.summary()
+        # e2e: the same step through the public API plus the density read-back, wall clock
+        e2e_ms = []
+        for k in range(max(2, args.steps // 2)):
+            flush.zero_()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            r = one_step(read_back=True)
+            e2e_ms.append(1e3 * (time.perf_counter() - t0))
+        torch.cuda.synchronize()
+
+    total_ms = float(sum(step_ms))
+    if pg:
+        t = torch.tensor([total_ms, float(quartets), float(launches)], dtype=torch.float64, device="cuda")
+        tmax = t.clone()
+        pg.all_reduce(tmax, op=pg.ReduceOp.MAX)
+        pg.all_reduce(t, op=pg.ReduceOp.SUM)
+        total_ms, quartets, launches = float(tmax[0]), float(t[1]), int(t[2])
+    if rank != 0:
+        if pg:
+            pg.destroy_process_group()
+        return 0
+
+    last = results[-1]
+    st = last["stats"]
+    builds = last["n_macro"] + 1
+    jms_per_build = st["jengine_ms"] / builds
+    flops_build = algorithmic_flops(st["class_quartets"])
+    achieved = flops_build / (jms_per_build * 1e-3)
+    value = quartets / (total_ms * 1e-3)
+    so, sl, sn, ex, co = system.flat_basis()
+    h2d = sum(a.nbytes for a in (system.Z, system.xyz, system.frag_of_atom, system.basis_of_atom, system.charge,
+                                  so, sl, sn, ex, co))
+    d2h = int(r["D"].nbytes) + 8 * (2 * N_WATER + 1)   # densities + E_frag, E_int, E_total
+    e2e_value = st["shell_quartets"] * builds / (float(np.mean(e2e_ms)) * 1e-3)
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "n_frag": N_WATER, "cutoff_A": CUTOFF_A, "schwarz": SCHWARZ,
+                   "e_tol": E_TOL, "precision": "fp64", "start": "superposition", "seed": "rank",
+                   "l2": "flushed between steps (256 MiB write)", "parallelism": f"replicas x{ws}"},
+        "time_to_1e-8_ms": float(np.mean(iter_ms)), "setup_and_energies_ms": total_ms / args.steps - float(np.mean(iter_ms)),
+        "n_macro": last["n_macro"], "fock_builds_per_step": builds,
+        "shell_quartets_per_build": st["shell_quartets"], "prim_quartets_per_build": int(np.sum(st["class_quartets"])),
+        "E_tot": last["E_tot"],
+        "roofline": {"bound": "alu", "achieved": achieved / 1e12, "peak": FP64_PEAK / 1e12, "unit": "TFLOP/s",
+                     "frac": achieved / FP64_PEAK, "traffic": profile_traffic(),
+                     "kernel": "k_jengine<LP,LQ> (9 class-pair launches of one Fock build)",
+                     "jengine_ms_per_build": jms_per_build, "algorithmic_flop_per_build": flops_build,
+                     "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x 2 FLOP x 2070 MHz (1.25 TFLOP/s nominal)",
+                     "fma_probe_fp64_tflops": fp64_probe / 1e12, "fma_probe_fp32_tflops": fp32_probe / 1e12},
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
+                "ms_per_step": float(np.mean(e2e_ms))},
+        "gpu_launches": int(launches),
+        "clocks": clocks,
+        "wall_s": wall,
+    }
+    if ws == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline()
+    print(json.dumps(line), flush=True)
+    if pg:
+        pg.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

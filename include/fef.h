@@ -151,9 +151,14 @@ fef_status fef_set_densities(fef_ctx* ctx, const double* D_in, int on_device);
  *                   and Schwarz screening, counted once per build;
  *   prim_quartets:  primitive quartets evaluated per build;
  *   n_pairs:        fragment pairs in the neighbour list;
- *   jengine_ms:     device time of the last build's J-engine launches (CUDA events). */
+ *   jengine_ms:     device time of the J-engine launches of the last fef_build_fock, or summed over
+ *                   the builds of the last fef_iterate (CUDA events on the context stream);
+ *   kernel_launches: kernels launched by this library (all contexts) since it was loaded;
+ *   class_quartets: [25] primitive quartets of the surviving shell quartets per Hermite class,
+ *                   index L_bra*5 + L_ket with L = l_a + l_b of the shell pair.
+ * ctx may be NULL when only kernel_launches is asked for. */
 fef_status fef_stats(const fef_ctx* ctx, int64_t* shell_quartets, int64_t* prim_quartets, int64_t* n_pairs,
-                     double* jengine_ms);
+                     double* jengine_ms, int64_t* kernel_launches, int64_t* class_quartets);
 
 /* Message of the last failing call on ctx (or of the last failed fef_create when ctx is NULL). */
 const char* fef_last_error(const fef_ctx* ctx);

@@ -85,7 +85,7 @@ def lib():
     L.fef_energies.argtypes = [vp, dp, dp, dp]
     L.fef_get_densities.argtypes = [vp, vp, ctypes.c_int]
     L.fef_set_densities.argtypes = [vp, vp, ctypes.c_int]
-    L.fef_stats.argtypes = [vp, i64p, i64p, i64p, dp]
+    L.fef_stats.argtypes = [vp, i64p, i64p, i64p, dp, i64p, i64p]
     L.fef_last_error.argtypes = [vp]
     L.fef_last_error.restype = ctypes.c_char_p
     L.fef_destroy.argtypes = [vp]
@@ -240,12 +240,15 @@ def fef_set_densities(ctx: Context, D):
     _check(lib().fef_set_densities(ctx.ptr, p, dev), ctx.ptr)
 
 
-def fef_stats(ctx: Context) -> dict:
-    sq, pq, npairs = ctypes.c_int64(0), ctypes.c_int64(0), ctypes.c_int64(0)
+def fef_stats(ctx: Context | None = None) -> dict:
+    sq, pq, npairs, nl = ctypes.c_int64(0), ctypes.c_int64(0), ctypes.c_int64(0), ctypes.c_int64(0)
     ms = ctypes.c_double(0.0)
-    _check(lib().fef_stats(ctx.ptr, ctypes.byref(sq), ctypes.byref(pq), ctypes.byref(npairs), ctypes.byref(ms)),
-           ctx.ptr)
-    return dict(shell_quartets=sq.value, prim_quartets=pq.value, n_pairs=npairs.value, jengine_ms=ms.value)
+    ptr = ctx.ptr if ctx is not None else None
+    cls = np.zeros(25, np.int64)
+    _check(lib().fef_stats(ptr, ctypes.byref(sq), ctypes.byref(pq), ctypes.byref(npairs), ctypes.byref(ms),
+                           ctypes.byref(nl), _ptr(cls, ctypes.c_int64) if ptr else None), ptr)
+    return dict(shell_quartets=sq.value, prim_quartets=pq.value, n_pairs=npairs.value, jengine_ms=ms.value,
+                kernel_launches=nl.value, class_quartets=cls.reshape(5, 5))
 
 
 def fef_destroy(ctx: Context):

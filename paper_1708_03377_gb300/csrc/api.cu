@@ -3,6 +3,7 @@
 // FEF self-consistency (paper, "Fragment Mean Field").  All arithmetic of the method runs in the
 // kernels of setup.cu, jengine.cu and scf.cu.
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -73,6 +74,12 @@ struct Buffers {
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
 };
 
+}  // namespace fef
+
+namespace fef {
+static std::atomic<long long> g_launches{0};
+void note_launches(long long n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+long long launches_so_far() { return g_launches.load(std::memory_order_relaxed); }
 }  // namespace fef
 
 using namespace fef;
@@ -515,11 +522,12 @@ extern "C" fef_status fef_create(const fef_geometry* g, const fef_basis* bs, con
                 b->tiles[LP][LQ] = t.empty() ? nullptr : b->upload(t, s, "tiles");
             }
         c->prim_quartets = prim_q;
-        b->qcount = b->alloc<unsigned long long>(1, "qcount");
-        ck(cudaMemsetAsync(b->qcount, 0, sizeof(unsigned long long), s), "qcount");
+        const int ncount = 1 + kClasses * kClasses;
+        b->qcount = b->alloc<unsigned long long>(ncount, "qcount");
+        ck(cudaMemsetAsync(b->qcount, 0, sizeof(unsigned long long) * ncount, s), "qcount");
         ck(launch_count_quartets(d, o.schwarz, b->qcount, s), "count quartets");
-        unsigned long long qc = 0;
-        ck(cudaMemcpyAsync(&qc, b->qcount, sizeof(qc), cudaMemcpyDeviceToHost, s), "qcount");
+        unsigned long long qc[1 + kClasses * kClasses] = {};
+        ck(cudaMemcpyAsync(qc, b->qcount, sizeof(qc), cudaMemcpyDeviceToHost, s), "qcount");
         // per-build buffers
         b->D = b->alloc<double>(c->mat_total, "D");
         b->F = b->alloc<double>(c->mat_total, "F");
@@ -539,7 +547,8 @@ extern "C" fef_status fef_create(const fef_geometry* g, const fef_basis* bs, con
         b->diis_stride = 2 * (int64_t)o.diis_size * max_nao * max_nao;
         b->diis = b->alloc<double>((size_t)nf * b->diis_stride, "diis");
         ck(cudaStreamSynchronize(s), "create");
-        c->shell_quartets = (int64_t)qc;
+        c->shell_quartets = (int64_t)qc[0];
+        for (int i = 0; i < kClasses * kClasses; ++i) c->class_quartets[i] = (int64_t)qc[1 + i];
         check_device_flags(c, "create");
         *out = c;
         return FEF_OK;
@@ -725,9 +734,13 @@ extern "C" fef_status fef_energies(fef_ctx* c, double* E_frag, double* E_total, 
     FEF_API_END(c)
 }
 
-extern "C" fef_status fef_stats(const fef_ctx* c, int64_t* sq, int64_t* pq, int64_t* np, double* jms)
+extern "C" fef_status fef_stats(const fef_ctx* c, int64_t* sq, int64_t* pq, int64_t* np, double* jms,
+                                int64_t* launches, int64_t* class_quartets)
 {
-    if (!c) return FEF_ERR_ARG;
+    if (launches) *launches = launches_so_far();
+    if (!c) return launches ? FEF_OK : FEF_ERR_ARG;
+    if (class_quartets)
+        for (int i = 0; i < kClasses * kClasses; ++i) class_quartets[i] = c->class_quartets[i];
     if (sq) *sq = c->shell_quartets;
     if (pq) *pq = c->prim_quartets;
     if (np) *np = c->n_pairs;

@@ -100,6 +100,7 @@ struct fef_ctx {
     fef::Buffers* buf = nullptr;
     // counters
     int64_t shell_quartets = 0, prim_quartets = 0;
+    int64_t class_quartets[25] = {};
     double jengine_ms = 0.0;
     bool have_density = false;
     bool energies_valid = false;
@@ -107,6 +108,10 @@ struct fef_ctx {
 };
 
 namespace fef {
+
+// Number of kernels launched by this library since load (incremented at every launch site).
+void note_launches(long long n);
+long long launches_so_far();
 
 // ---- kernels launched by the API layer (each returns cudaGetLastError()) ----
 cudaError_t launch_prepare(const Dev& d, const double* xyz_A, double* atom_xyz, double* p_coef_out,

@@ -72,7 +72,10 @@ __global__ void k_hermite_density(Dev d, int L, const double* __restrict__ D)
 cudaError_t launch_hermite_density(const Dev& d, const double* D, cudaStream_t s)
 {
     for (int L = 0; L < kClasses; ++L)
-        if (d.n_pp[L] > 0) k_hermite_density<<<(d.n_pp[L] + 127) / 128, 128, 0, s>>>(d, L, D);
+        if (d.n_pp[L] > 0) {
+            k_hermite_density<<<(d.n_pp[L] + 127) / 128, 128, 0, s>>>(d, L, D);
+            note_launches(1);
+        }
     return cudaGetLastError();
 }
 
@@ -184,6 +187,7 @@ static void launch_one(const Dev& d, const int2* t, int n, float tau, double* e,
     if (n <= 0) return;
     const int warps_per_block = 4;
     k_jengine<LP, LQ><<<(n + warps_per_block - 1) / warps_per_block, 32 * warps_per_block, 0, s>>>(d, t, n, tau, e);
+    note_launches(1);
 }
 
 cudaError_t launch_jengine(const Dev& d, const int2* tiles[kClasses][kClasses], const int* n_tiles, double tau,
@@ -248,6 +252,7 @@ cudaError_t launch_back_transform(const Dev& d, double* J, cudaStream_t s)
 {
     dim3 g((d.max_nao * d.max_nao + 127) / 128, d.n_frag);
     k_back_transform<<<g, 128, 0, s>>>(d, J);
+    note_launches(1);
     return cudaGetLastError();
 }
 
@@ -303,6 +308,7 @@ cudaError_t launch_fock_energy(const Dev& d, const double* h, const double* Venv
                                double* E_int, double* tr_omega, cudaStream_t s)
 {
     k_fock_assemble<<<d.n_frag, 256, 0, s>>>(d, h, Venv, Jenv, eric, D, F, omega, e_nn, E_int, tr_omega);
+    note_launches(1);
     return cudaGetLastError();
 }
 
@@ -344,9 +350,14 @@ cudaError_t launch_energies(const Dev& d, const double* e_J, const double* tr_xy
                             const double* e_nn_pair, const double* E_int, double* E_pair, double* E_frag,
                             double* E_tot, cudaStream_t s)
 {
-    if (d.n_pairs > 0) k_pair_energy<<<(d.n_pairs + 255) / 256, 256, 0, s>>>(d, e_J, tr_xy, tr_yx, e_nn_pair, E_pair);
+    if (d.n_pairs > 0) {
+        k_pair_energy<<<(d.n_pairs + 255) / 256, 256, 0, s>>>(d, e_J, tr_xy, tr_yx, e_nn_pair, E_pair);
+        note_launches(1);
+    }
     k_frag_energy<<<(d.n_frag + 255) / 256, 256, 0, s>>>(d, E_int, E_pair, E_frag);
+    note_launches(1);
     k_total_energy<<<1, 256, 0, s>>>(d, E_int, E_pair, E_tot);
+    note_launches(1);
     return cudaGetLastError();
 }
 
@@ -365,29 +376,48 @@ cudaError_t launch_check_finite(const double* a, int64_t n, int* flag, cudaStrea
     if (n <= 0) return cudaSuccess;
     int blocks = (int)std::min<int64_t>((n + 255) / 256, 1024);
     k_check_finite<<<blocks, 256, 0, s>>>(a, n, flag);
+    note_launches(1);
     return cudaGetLastError();
 }
 
 }  // namespace fef
 
 namespace fef {
-// Inter-fragment shell quartets (a<=b in x, c<=d in y, x<y) with Q_ab Q_cd >= tau: one block per pair.
+// Inter-fragment shell quartets (a<=b in x, c<=d in y, x<y) with Q_ab Q_cd >= tau, and their
+// primitive quartets per Hermite class (L_ab, L_cd): one block per pair.  count[0] = shell
+// quartets, count[1 + L_ab*kClasses + L_cd] = primitive quartets of that class.
 __global__ void k_count_quartets(Dev d, double tau, unsigned long long* count)
 {
+    __shared__ unsigned long long cls[kClasses * kClasses];
+    for (int i = threadIdx.x; i < kClasses * kClasses; i += blockDim.x) cls[i] = 0;
+    __syncthreads();
     int pr = blockIdx.x;
     int x = d.pair_x[pr], y = d.pair_y[pr];
     int s0 = d.frag_sp0[x], ns = d.frag_sp0[x + 1] - s0;
     int t0 = d.frag_sp0[y], nt = d.frag_sp0[y + 1] - t0;
     unsigned long long c = 0;
-    for (int w = threadIdx.x; w < ns * nt; w += blockDim.x)
-        if (d.sp_Q[s0 + w / nt] * d.sp_Q[t0 + w % nt] >= tau) ++c;
+    for (int w = threadIdx.x; w < ns * nt; w += blockDim.x) {
+        int s1 = s0 + w / nt, s2 = t0 + w % nt;
+        if (d.sp_Q[s1] * d.sp_Q[s2] >= tau) {
+            ++c;
+            unsigned long long np = (unsigned long long)d.sh_np[d.sp_a[s1]] * d.sh_np[d.sp_b[s1]] *
+                                    d.sh_np[d.sp_a[s2]] * d.sh_np[d.sp_b[s2]];
+            atomicAdd(&cls[d.sp_L[s1] * kClasses + d.sp_L[s2]], np);
+        }
+    }
     for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
     if ((threadIdx.x & 31) == 0) atomicAdd(count, c);
+    __syncthreads();
+    for (int i = threadIdx.x; i < kClasses * kClasses; i += blockDim.x)
+        if (cls[i]) atomicAdd(count + 1 + i, cls[i]);
 }
 
 cudaError_t launch_count_quartets(const Dev& d, double tau, unsigned long long* count, cudaStream_t s)
 {
-    if (d.n_pairs > 0) k_count_quartets<<<d.n_pairs, 128, 0, s>>>(d, tau, count);
+    if (d.n_pairs > 0) {
+        k_count_quartets<<<d.n_pairs, 128, 0, s>>>(d, tau, count);
+        note_launches(1);
+    }
     return cudaGetLastError();
 }
 }  // namespace fef

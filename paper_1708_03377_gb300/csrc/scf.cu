@@ -178,6 +178,7 @@ cudaError_t launch_orthogonaliser(const Dev& d, const double* S, double* X, int*
     size_t smem = 2 * (size_t)max_n * max_n * sizeof(double);
     cudaFuncSetAttribute(k_orthogonaliser, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     k_orthogonaliser<<<d.n_frag, 256, smem, s>>>(d, S, X, nmo, s_min);
+    note_launches(1);
     return cudaGetLastError();
 }
 
@@ -376,6 +377,7 @@ cudaError_t launch_fragment_scf(const Dev& d, const ScfArgs& a, int max_n, cudaS
     cudaError_t e = cudaFuncSetAttribute(k_fragment_scf, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     k_fragment_scf<<<d.n_frag, 256, smem, s>>>(d, a);
+    note_launches(1);
     return cudaGetLastError();
 }
 

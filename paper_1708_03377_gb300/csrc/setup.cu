@@ -24,6 +24,7 @@ cudaError_t launch_prepare(const Dev& d, const double* xyz_A, double* atom_xyz, 
     int n = max(3 * d.n_atoms, n_prims);
     k_prepare<<<(n + 255) / 256, 256, 0, s>>>(d.n_atoms, xyz_A, atom_xyz, n_prims, d.p_exp, p_coef_raw, p_l,
                                               p_coef_out);
+    note_launches(1);
     return cudaGetLastError();
 }
 
@@ -65,6 +66,7 @@ __global__ void k_boys_table(double* table)
 cudaError_t launch_boys_table(double* table, cudaStream_t s)
 {
     k_boys_table<<<(kBoysRows + 127) / 128, 128, 0, s>>>(table);
+    note_launches(1);
     return cudaGetLastError();
 }
 
@@ -97,6 +99,7 @@ __global__ void k_ao_scale(Dev d, double* ao_scale, int n_ao_total)
 cudaError_t launch_ao_scale(const Dev& d, double* ao_scale, int n_ao_total, const int*, cudaStream_t s)
 {
     k_ao_scale<<<(n_ao_total + 127) / 128, 128, 0, s>>>(d, ao_scale, n_ao_total);
+    note_launches(1);
     return cudaGetLastError();
 }
 
@@ -126,7 +129,10 @@ cudaError_t launch_prim_pairs(const Dev& d, double4_32a* P[kClasses], float4* Pf
                               cudaStream_t s)
 {
     for (int L = 0; L < kClasses; ++L)
-        if (d.n_pp[L] > 0) k_prim_pairs<<<(d.n_pp[L] + 127) / 128, 128, 0, s>>>(d, L, P[L], Pf[L], K[L]);
+        if (d.n_pp[L] > 0) {
+            k_prim_pairs<<<(d.n_pp[L] + 127) / 128, 128, 0, s>>>(d, L, P[L], Pf[L], K[L]);
+            note_launches(1);
+        }
     return cudaGetLastError();
 }
 
@@ -261,6 +267,7 @@ cudaError_t launch_one_electron(const Dev& d, double* S, double* h, cudaStream_t
 {
     dim3 g((d.max_nao * d.max_nao + 127) / 128, d.n_frag);
     k_one_electron<<<g, 128, 0, s>>>(d, S, h);
+    note_launches(1);
     return cudaGetLastError();
 }
 
@@ -299,6 +306,7 @@ cudaError_t launch_nuclear_env(const Dev& d, double* V, cudaStream_t s)
 {
     dim3 g((d.max_nao * d.max_nao + 127) / 128, d.n_frag);
     k_nuclear_env<<<g, 128, 0, s>>>(d, V);
+    note_launches(1);
     return cudaGetLastError();
 }
 
@@ -345,6 +353,7 @@ cudaError_t launch_nuclear_traces(const Dev& d, const double* D, double* tr_xy, 
     if (d.n_pairs == 0) return cudaSuccess;
     dim3 g(d.n_pairs, 2);
     k_nuclear_traces<<<g, 256, 0, s>>>(d, D, tr_xy, tr_yx);
+    note_launches(1);
     return cudaGetLastError();
 }
 
@@ -380,6 +389,7 @@ cudaError_t launch_nuclear_repulsion(const Dev& d, double* e_nn_intra, double* e
 {
     int n = max(d.n_frag, d.n_pairs);
     k_nuclear_repulsion<<<(n + 127) / 128, 128, 0, s>>>(d, e_nn_intra, e_nn_pair);
+    note_launches(1);
     return cudaGetLastError();
 }
 
@@ -504,6 +514,7 @@ cudaError_t launch_intra_eri(const Dev& d, double* eri, int max_l, cudaStream_t 
         k_intra_eri<81><<<g, 128, 0, s>>>(d, eri);
     else
         k_intra_eri<1296><<<g, 128, 0, s>>>(d, eri);
+    note_launches(1);
     return cudaGetLastError();
 }
 
@@ -528,6 +539,7 @@ cudaError_t launch_coulomb_exchange(const Dev& d, const double* eri, double* eri
     size_t n4 = (size_t)d.max_nao * d.max_nao * d.max_nao * d.max_nao;
     dim3 g((unsigned)std::min<size_t>((n4 + 255) / 256, 8192), d.n_frag);
     k_coulomb_exchange<<<g, 256, 0, s>>>(d, eri, eric);
+    note_launches(1);
     return cudaGetLastError();
 }
 
@@ -569,6 +581,7 @@ __global__ void k_schwarz(Dev d, const double* eri, double* sp_Q, float* pq0, fl
 cudaError_t launch_schwarz(const Dev& d, const double* eri, double* sp_Q, float* pp_Q[kClasses], cudaStream_t s)
 {
     k_schwarz<<<(d.n_sp + 127) / 128, 128, 0, s>>>(d, eri, sp_Q, pp_Q[0], pp_Q[1], pp_Q[2], pp_Q[3], pp_Q[4]);
+    note_launches(1);
     return cudaGetLastError();
 }
 
@@ -593,6 +606,7 @@ cudaError_t launch_neighbours(const Dev& d, double cutoff_bohr, unsigned char* f
 {
     dim3 g((d.n_frag + 255) / 256, d.n_frag);
     k_neighbours<<<g, 256, 0, s>>>(d, cutoff_bohr, flags);
+    note_launches(1);
     return cudaGetLastError();
 }
 
