@@ -170,6 +170,42 @@ void fef_destroy(fef_ctx* ctx);
  * Outputs (nullable) in FLOP/s, counting one FMA as 2 FLOP.  Errors: CUDA. */
 fef_status fef_measure_fma_peak(double* fp64_flops, double* fp32_flops, double* sm_clock_mhz);
 
+/* Batched closed-shell RHF of independent fragments in frozen fields, for callers that cannot
+ * allocate device memory.  The paper has no counterpart: this is a service entry point of this
+ * library.  Some callers own every byte of device memory themselves (a dynamics or embedding
+ * driver with a fixed budget or its own pool), run while a CUDA stream is being captured, or must
+ * not serialise on cudaMalloc/cudaFree inside a time step; this call allocates nothing.
+ *
+ * It runs the same kernels as the fragment RHF of fef_iterate (canonical orthogonaliser
+ * X = U s^{-1/2} dropping s < 1e-7, then the device micro loop: F = h + omega + C D, Pulay DIIS,
+ * cyclic Jacobi, aufbau, D = 2 C_occ C_occ^T until |dE| < micro_e_tol and max|FDS-SDF| <
+ * micro_comm_tol).  Its working memory (orthogonalisers, DIIS history, offsets, status flag) lives
+ * in a fixed 16 MiB device array inside libfef.so, held by every GPU that loads the library until
+ * the process exits.
+ *   n_frag              1..65535 fragments, batched in one launch.
+ *   n_ao, n_occ, e_nn   HOST arrays [n_frag]: AOs (1..56), doubly occupied orbitals, nuclear
+ *                       repulsion of the fragment's own nuclei (hartree).
+ *   S, h, omega         DEVICE packed n_x*n_x blocks (overlap, core Hamiltonian, environment field;
+ *                       omega may be NULL for isolated fragments).
+ *   eri_c               DEVICE, per fragment the full n_x^4 tensor
+ *                       C[mu nu][lambda sigma] = (mu nu|lambda sigma) - (mu lambda|nu sigma)/2,
+ *                       blocks concatenated.
+ *   D_start             DEVICE packed start densities, or NULL for the core guess (F = h + omega).
+ *   D_out, F_out        DEVICE packed outputs: converged densities and their Fock matrices.
+ *   E_scf               DEVICE [n_frag] output: tr[D(h + omega + F)]/2 + e_nn.
+ *   opt                 micro_e_tol, micro_comm_tol, max_micro, diis_size are used (NULL: defaults).
+ *   cuda_stream         stream for all work; the call synchronises it before returning.
+ * Limits: the batch must fit the 16 MiB scratch: per fragment n_x^2 doubles of orthogonaliser and
+ * 2*diis_size*max_n^2 doubles of DIIS history (about 700 13-AO fragments with diis_size 8), else
+ * FEF_ERR_ARG.  Set-up: the first call on each device resolves the scratch address with
+ * cudaGetSymbolAddress; make it before any stream capture.  All calls share the scratch and it keeps
+ * the last call's contents: calls whose device work overlaps race.  Errors (message from
+ * fef_last_error(NULL)): ARG, CUDA, NOT_CONVERGED (outputs hold the last iterate), NUMERIC. */
+fef_status fef_fragment_rhf_noalloc(int32_t n_frag, const int32_t* n_ao, const int32_t* n_occ, const double* e_nn,
+                                    const double* S, const double* h, const double* omega, const double* eri_c,
+                                    const double* D_start, double* D_out, double* F_out, double* E_scf,
+                                    const fef_options* opt, void* cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -26,7 +26,7 @@ STATUS_NAMES = {0: "FEF_OK", 1: "FEF_ERR_ARG", 2: "FEF_ERR_BASIS", 3: "FEF_ERR_G
 
 EXPORTED = ["fef_default_options", "fef_create", "fef_ao_layout", "fef_build_fock", "fef_iterate", "fef_energies",
             "fef_get_densities", "fef_set_densities", "fef_stats", "fef_last_error", "fef_destroy",
-            "fef_measure_fma_peak"]
+            "fef_measure_fma_peak", "fef_fragment_rhf_noalloc"]
 
 
 class FefError(RuntimeError):
@@ -91,6 +91,8 @@ def lib():
     L.fef_destroy.argtypes = [vp]
     L.fef_destroy.restype = None
     L.fef_measure_fma_peak.argtypes = [dp, dp, dp]
+    L.fef_fragment_rhf_noalloc.argtypes = [ctypes.c_int32, ip, ip, dp, vp, vp, vp, vp, vp, vp, vp, vp,
+                                           ctypes.POINTER(fef_options), vp]
     for name in EXPORTED:
         if name not in ("fef_default_options", "fef_last_error", "fef_destroy"):
             getattr(L, name).restype = ctypes.c_int
@@ -260,3 +262,23 @@ def fef_measure_fma_peak():
     a, b, c = ctypes.c_double(0), ctypes.c_double(0), ctypes.c_double(0)
     _check(lib().fef_measure_fma_peak(ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)), None)
     return a.value, b.value, c.value
+
+
+def fef_fragment_rhf_noalloc(n_ao, n_occ, e_nn, S, h, omega, eri_c, D_start, D_out, F_out, E_scf,
+                             options: fef_options | None = None, stream=None):
+    """Batched fragment RHF that allocates no device memory (see include/fef.h).
+
+    n_ao, n_occ, e_nn: host sequences.  S, h, omega (or None), eri_c, D_start (or None), D_out,
+    F_out, E_scf: CUDA torch tensors (float64, packed as documented in fef.h).  For callers that
+    cannot allocate device memory themselves, e.g. inside a stream capture or under a fixed budget.
+    """
+    nao = np.ascontiguousarray(n_ao, np.int32)
+    nocc = np.ascontiguousarray(n_occ, np.int32)
+    enn = np.ascontiguousarray(e_nn, np.float64)
+    dev = lambda t: None if t is None else ctypes.c_void_p(t.data_ptr())
+    opt = options if options is not None else fef_default_options()
+    s = ctypes.c_void_p(stream) if stream else None
+    _check(lib().fef_fragment_rhf_noalloc(int(nao.shape[0]), _ptr(nao, ctypes.c_int32), _ptr(nocc, ctypes.c_int32),
+                                          _ptr(enn, ctypes.c_double), dev(S), dev(h), dev(omega), dev(eri_c),
+                                          dev(D_start), dev(D_out), dev(F_out), dev(E_scf), ctypes.byref(opt), s),
+           None)

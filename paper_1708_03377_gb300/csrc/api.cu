@@ -86,6 +86,10 @@ using namespace fef;
 
 static std::string g_create_error;
 
+namespace fef {
+void set_global_error(const char* msg) { g_create_error = msg; }
+}  // namespace fef
+
 #define FEF_API_BEGIN try {
 #define FEF_API_END(ctx)                                              \
     }                                                                 \
