@@ -160,6 +160,12 @@ fef_status fef_set_densities(fef_ctx* ctx, const double* D_in, int on_device);
 fef_status fef_stats(const fef_ctx* ctx, int64_t* shell_quartets, int64_t* prim_quartets, int64_t* n_pairs,
                      double* jengine_ms, int64_t* kernel_launches, int64_t* class_quartets);
 
+/* Per-macro-iteration log of the last fef_iterate (record 0 = the start densities).  Each record is
+ * 8 doubles: k, E_total, |dE_total|, max_x |dE_x|, max micro-iterations over fragments, summed
+ * micro-iterations, J-engine ms of the Fock build, fragment-SCF ms (CUDA events).  Copies
+ * min(n, max_records) records into records (host, nullable); *n_records (nullable) gets n. */
+fef_status fef_history(const fef_ctx* ctx, int32_t max_records, double* records, int32_t* n_records);
+
 /* Message of the last failing call on ctx (or of the last failed fef_create when ctx is NULL). */
 const char* fef_last_error(const fef_ctx* ctx);
 

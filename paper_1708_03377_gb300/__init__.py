@@ -26,7 +26,7 @@ STATUS_NAMES = {0: "FEF_OK", 1: "FEF_ERR_ARG", 2: "FEF_ERR_BASIS", 3: "FEF_ERR_G
 
 EXPORTED = ["fef_default_options", "fef_create", "fef_ao_layout", "fef_build_fock", "fef_iterate", "fef_energies",
             "fef_get_densities", "fef_set_densities", "fef_stats", "fef_last_error", "fef_destroy",
-            "fef_measure_fma_peak", "fef_fragment_rhf_noalloc"]
+            "fef_measure_fma_peak", "fef_fragment_rhf_noalloc", "fef_history"]
 
 
 class FefError(RuntimeError):
@@ -91,6 +91,7 @@ def lib():
     L.fef_destroy.argtypes = [vp]
     L.fef_destroy.restype = None
     L.fef_measure_fma_peak.argtypes = [dp, dp, dp]
+    L.fef_history.argtypes = [vp, ctypes.c_int32, dp, ip]
     L.fef_fragment_rhf_noalloc.argtypes = [ctypes.c_int32, ip, ip, dp, vp, vp, vp, vp, vp, vp, vp, vp,
                                            ctypes.POINTER(fef_options), vp]
     for name in EXPORTED:
@@ -251,6 +252,16 @@ def fef_stats(ctx: Context | None = None) -> dict:
                            ctypes.byref(nl), _ptr(cls, ctypes.c_int64) if ptr else None), ptr)
     return dict(shell_quartets=sq.value, prim_quartets=pq.value, n_pairs=npairs.value, jengine_ms=ms.value,
                 kernel_launches=nl.value, class_quartets=cls.reshape(5, 5))
+
+
+def fef_history(ctx: Context) -> list:
+    """Per-macro-iteration records of the last fef_iterate as dicts."""
+    n = ctypes.c_int32(0)
+    _check(lib().fef_history(ctx.ptr, 0, None, ctypes.byref(n)), ctx.ptr)
+    buf = np.zeros(max(1, n.value) * 8)
+    _check(lib().fef_history(ctx.ptr, n.value, _ptr(buf, ctypes.c_double), ctypes.byref(n)), ctx.ptr)
+    keys = ("k", "E_tot", "dE_tot", "dE_x_max", "micro_max", "micro_sum", "jengine_ms", "scf_ms")
+    return [dict(zip(keys, buf[8 * i:8 * i + 8].tolist())) for i in range(n.value)]
 
 
 def fef_destroy(ctx: Context):

@@ -71,7 +71,7 @@ struct Buffers {
     int2* tiles[kClasses][kClasses] = {};
     int n_tiles[kClasses * kClasses] = {};
     unsigned long long* qcount = nullptr;
-    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr, ev2 = nullptr, ev3 = nullptr;
 };
 
 }  // namespace fef
@@ -182,6 +182,7 @@ static void run_scf(fef_ctx* c, bool with_field, bool have_start)
     a.X = b->X;
     a.nmo = b->nmo;
     a.eric = b->eric;
+    a.eric_packed = 1;
     a.e_nn = b->e_nn_intra;
     a.D = b->D;
     a.F = b->F;
@@ -195,8 +196,27 @@ static void run_scf(fef_ctx* c, bool with_field, bool have_start)
     a.diis_size = c->opt.diis_size;
     a.e_tol = c->opt.micro_e_tol;
     a.comm_tol = c->opt.micro_comm_tol;
+    ck(cudaEventRecord(b->ev2, c->stream), "event");
     ck(launch_fragment_scf(c->dev, a, c->max_nao, c->stream), "fragment SCF");
+    ck(cudaEventRecord(b->ev3, c->stream), "event");
     c->energies_valid = false;
+}
+
+// micro-iteration counts of the last fragment SCF launch (negative = not converged) and its time
+static void scf_counts(fef_ctx* c, double& max_it, double& sum_it, double& ms)
+{
+    std::vector<int> it(c->n_frag);
+    ck(cudaMemcpyAsync(it.data(), c->buf->iters, sizeof(int) * c->n_frag, cudaMemcpyDeviceToHost, c->stream), "iters");
+    ck(cudaStreamSynchronize(c->stream), "iters");
+    max_it = 0;
+    sum_it = 0;
+    for (int v : it) {
+        max_it = std::max<double>(max_it, std::abs(v));
+        sum_it += std::abs(v);
+    }
+    float f = 0.f;
+    ck(cudaEventElapsedTime(&f, c->buf->ev2, c->buf->ev3), "event time");
+    ms = f;
 }
 
 // ---------------------------------------------------------------------------------------------- create
@@ -315,11 +335,14 @@ extern "C" fef_status fef_create(const fef_geometry* g, const fef_basis* bs, con
         c->max_nao = max_nao;
         c->nao = frag_nao;
         c->nocc = frag_nocc;
-        std::vector<int64_t> moff(nf + 1, 0), eoff(nf + 1, 0);
+        std::vector<int64_t> moff(nf + 1, 0), eoff(nf + 1, 0), coff(nf + 1, 0);
         for (int x = 0; x < nf; ++x) {
-            moff[x + 1] = moff[x] + (int64_t)frag_nao[x] * frag_nao[x];
-            eoff[x + 1] = eoff[x] + (int64_t)frag_nao[x] * frag_nao[x] * frag_nao[x] * frag_nao[x];
+            int64_t n = frag_nao[x], np = n * (n + 1) / 2;
+            moff[x + 1] = moff[x] + n * n;
+            eoff[x + 1] = eoff[x] + n * n * n * n;
+            coff[x + 1] = coff[x] + np * np;
         }
+        c->coff_total = coff[nf];
         c->moff = moff;
         c->mat_total = moff[nf];
         c->eri_total = eoff[nf];
@@ -380,6 +403,7 @@ extern "C" fef_status fef_create(const fef_geometry* g, const fef_basis* bs, con
         d.frag_nocc = b->upload(frag_nocc, s, "frag");
         d.frag_moff = b->upload(moff, s, "frag");
         d.frag_eoff = b->upload(eoff, s, "frag");
+        d.frag_coff = b->upload(coff, s, "frag");
         d.frag_pp0 = b->upload(frag_pp0, s, "frag");
         d.frag_npp = b->upload(frag_npp, s, "frag");
         d.sh_l = b->upload(sh_l, s, "shells");
@@ -431,6 +455,8 @@ extern "C" fef_status fef_create(const fef_geometry* g, const fef_basis* bs, con
         ck(cudaMemsetAsync(b->err_flag, 0, sizeof(int), s), "flag");
         ck(cudaEventCreate(&b->ev0), "event");
         ck(cudaEventCreate(&b->ev1), "event");
+        ck(cudaEventCreate(&b->ev2), "event");
+        ck(cudaEventCreate(&b->ev3), "event");
 
         // ---- geometry-time kernels
         ck(launch_prepare(d, xyz_A, atom_xyz, p_coef, p_coef_raw_d, p_l_d, c->n_prims, s), "prepare");
@@ -492,13 +518,19 @@ extern "C" fef_status fef_create(const fef_geometry* g, const fef_basis* bs, con
             double* eri = b->alloc<double>(c->eri_total, "intra eri");
             ck(launch_intra_eri(d, eri, max_l, s), "intra eri");
             ck(launch_schwarz(d, eri, sp_Q, ppQ, s), "schwarz");
-            b->eric = b->alloc<double>(c->eri_total, "eric");
+            b->eric = b->alloc<double>(c->coff_total, "eric");
             ck(launch_coulomb_exchange(d, eri, b->eric, s), "coulomb-exchange");
             ck(cudaStreamSynchronize(s), "intra eri");
             b->release(eri);
         }
         b->Venv = b->alloc<double>(c->mat_total, "Venv");
-        ck(launch_nuclear_env(d, b->Venv, s), "nuclear env");
+        {
+            double* vh[kClasses];
+            for (int L = 0; L < kClasses; ++L) vh[L] = b->alloc<double>((size_t)nh(L) * d.n_pp[L], "Vh");
+            ck(launch_nuclear_env(d, vh, b->Venv, s), "nuclear env");
+            ck(cudaStreamSynchronize(s), "nuclear env");
+            for (int L = 0; L < kClasses; ++L) b->release(vh[L]);
+        }
         b->X = b->alloc<double>(c->mat_total, "X");
         b->nmo = b->alloc<int>(nf, "nmo");
         ck(launch_orthogonaliser(d, b->S, b->X, b->nmo, 1e-7, max_nao, s), "orthogonaliser");
@@ -579,6 +611,8 @@ extern "C" void fef_destroy(fef_ctx* c)
     if (c->buf) {
         if (c->buf->ev0) cudaEventDestroy(c->buf->ev0);
         if (c->buf->ev1) cudaEventDestroy(c->buf->ev1);
+        if (c->buf->ev2) cudaEventDestroy(c->buf->ev2);
+        if (c->buf->ev3) cudaEventDestroy(c->buf->ev3);
         delete c->buf;
     }
     delete c;
@@ -678,11 +712,20 @@ extern "C" fef_status fef_iterate(fef_ctx* c, int32_t* n_macro_out, double* fina
     } else {
         throw Error{FEF_ERR_ARG, "fef_iterate: learned start needs the MLP warm start (not in this build)"};
     }
+    double it_max = 0, it_sum = 0, scf_ms = 0;
+    if (o.start == FEF_START_SUPERPOSITION) scf_counts(c, it_max, it_sum, scf_ms);
     check_device_flags(c, "fef_iterate start");
     build_fock_internal(c);
     std::vector<double> Ex_old, Ex;
     double Et_old = 0, Et = 0, dE = 0;
     read_energies(c, Ex_old, Et_old);
+    c->history.clear();
+    {
+        float ms0 = 0.f;
+        ck(cudaEventElapsedTime(&ms0, c->buf->ev0, c->buf->ev1), "event time");
+        double rec[8] = {0, Et_old, 0, 0, it_max, it_sum, ms0, scf_ms};
+        c->history.insert(c->history.end(), rec, rec + 8);
+    }
     int k = 0;
     bool conv = false;
     float jms = 0.f;
@@ -690,6 +733,7 @@ extern "C" fef_status fef_iterate(fef_ctx* c, int32_t* n_macro_out, double* fina
         run_scf(c, true, true);
         build_fock_internal(c);
         read_energies(c, Ex, Et);
+        scf_counts(c, it_max, it_sum, scf_ms);
         float ms = 0.f;
         ck(cudaEventElapsedTime(&ms, c->buf->ev0, c->buf->ev1), "event time");
         jms += ms;
@@ -703,6 +747,10 @@ extern "C" fef_status fef_iterate(fef_ctx* c, int32_t* n_macro_out, double* fina
         dE = std::fabs(Et - Et_old);
         double dEx = 0;
         for (int x = 0; x < c->n_frag; ++x) dEx = std::max(dEx, std::fabs(Ex[x] - Ex_old[x]));
+        {
+            double rec[8] = {(double)k, Et, dE, dEx, it_max, it_sum, (double)ms, scf_ms};
+            c->history.insert(c->history.end(), rec, rec + 8);
+        }
         Ex_old = Ex;
         Et_old = Et;
         if (dE < o.e_tol && dEx < o.e_tol) {
@@ -758,6 +806,18 @@ extern "C" fef_status fef_measure_fma_peak(double* fp64, double* fp32, double* m
     if (e != cudaSuccess) {
         g_create_error = std::string("fef_measure_fma_peak: ") + cudaGetErrorString(e);
         return FEF_ERR_CUDA;
+    }
+    return FEF_OK;
+}
+
+extern "C" fef_status fef_history(const fef_ctx* c, int32_t max_records, double* records, int32_t* n_records)
+{
+    if (!c) return FEF_ERR_ARG;
+    int n = (int)(c->history.size() / 8);
+    if (n_records) *n_records = n;
+    if (records && max_records > 0) {
+        int m = std::min(n, (int)max_records);
+        std::memcpy(records, c->history.data(), sizeof(double) * 8 * m);
     }
     return FEF_OK;
 }

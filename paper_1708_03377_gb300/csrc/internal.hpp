@@ -42,6 +42,7 @@ struct Dev {
     const int* frag_nocc;
     const int64_t* frag_moff;
     const int64_t* frag_eoff;
+    const int64_t* frag_coff;  // packed Coulomb-minus-half-exchange tensor, (n(n+1)/2)^2 per fragment
     const int* frag_pp0;   // [n_frag*kClasses] first prim pair of class L in the class array
     const int* frag_npp;   // [n_frag*kClasses]
     const int* frag_nbr0;  // [n_frag+1] CSR neighbour list
@@ -91,7 +92,7 @@ struct fef_ctx {
     cudaStream_t stream = nullptr;
     int device = 0;
     int n_frag = 0, n_atoms = 0, n_shells = 0, n_prims = 0, n_sp = 0, n_pairs = 0;
-    int64_t mat_total = 0, eri_total = 0;
+    int64_t mat_total = 0, eri_total = 0, coff_total = 0;
     int max_nao = 0, max_nmo = 0;
     std::vector<int> nao, nmo, nocc;
     std::vector<int64_t> moff;
@@ -102,6 +103,9 @@ struct fef_ctx {
     int64_t shell_quartets = 0, prim_quartets = 0;
     int64_t class_quartets[25] = {};
     double jengine_ms = 0.0;
+    // one record per macro-iteration of the last fef_iterate (index 0: the start densities):
+    // k, E_tot, |dE_tot|, max|dE_x|, max micro-iterations, summed micro-iterations, J-engine ms, SCF ms
+    std::vector<double> history;
     bool have_density = false;
     bool energies_valid = false;
     std::string last_error;
@@ -125,7 +129,7 @@ cudaError_t launch_intra_eri(const Dev& d, double* eri, int max_l, cudaStream_t 
 cudaError_t launch_schwarz(const Dev& d, const double* eri, double* sp_Q, float* pp_Q[kClasses], cudaStream_t s);
 cudaError_t launch_coulomb_exchange(const Dev& d, const double* eri, double* eric, cudaStream_t s);
 cudaError_t launch_neighbours(const Dev& d, double cutoff_bohr, unsigned char* flags, cudaStream_t s);
-cudaError_t launch_nuclear_env(const Dev& d, double* V, cudaStream_t s);
+cudaError_t launch_nuclear_env(const Dev& d, double* vh[kClasses], double* V, cudaStream_t s);
 cudaError_t launch_nuclear_traces(const Dev& d, const double* D, double* trace_xy, double* trace_yx, cudaStream_t s);
 cudaError_t launch_nuclear_repulsion(const Dev& d, double* e_nn_intra, double* e_nn_pair, cudaStream_t s);
 cudaError_t launch_orthogonaliser(const Dev& d, const double* S, double* X, int* nmo, double s_min, int max_n,
@@ -146,7 +150,9 @@ struct ScfArgs {
     const double* S;
     const double* X;
     const int* nmo;
-    const double* eric;
+    const double* eric;     // eric_packed = 0: full C[mu nu][lambda sigma], n^4 at frag_eoff;
+                            // eric_packed = 1: packed transposed CT[rs][pq] at frag_coff (see setup.cu)
+    int eric_packed;
     const double* e_nn;     // [n_frag] own nuclear repulsion
     double* D;              // in: start (if have_start), out: converged
     double* F;              // out: Fock of the returned D

@@ -257,36 +257,51 @@ cudaError_t launch_back_transform(const Dev& d, double* J, cudaStream_t s)
 }
 
 // ------------------------------------------------------------------------------------------ Fock
-// F^x = h^x + G[D^x] + V_env^x + J_env^x with G = C D (C: Coulomb-minus-half-exchange tensor), plus
-// E_int[x] = tr[D (h + G/2)] + E_nn(x) and tr[D omega] (omega = V_env + J_env).  One block per
-// fragment; one warp per row of C (coalesced), warp-reduced.
+// F^x = h^x + G[D^x] + V_env^x + J_env^x with G = C D (C: packed transposed Coulomb-minus-half-
+// exchange tensor, see setup.cu), plus E_int[x] = tr[D (h + G/2)] + E_nn(x) and tr[D omega]
+// (omega = V_env + J_env).  One block per fragment; thread per packed row pq = (mu <= nu).
 __global__ void k_fock_assemble(Dev d, const double* h, const double* Venv, const double* Jenv, const double* eric,
                                 const double* D, double* F, double* omega, const double* e_nn, double* E_int,
                                 double* tr_omega)
 {
     int x = blockIdx.x;
     int n = d.frag_nao[x];
-    int n2 = n * n;
-    const double* C = eric + d.frag_eoff[x];
+    int np = n * (n + 1) / 2;
+    const double* C = eric + d.frag_coff[x];
     const double* Dx = D + d.frag_moff[x];
-    int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    extern __shared__ double dpk[];  // packed D_rs
+    for (int rs = threadIdx.x; rs < np; rs += blockDim.x) {
+        int la = 0, r = rs;
+        while (r >= n - la) { r -= n - la; ++la; }
+        dpk[rs] = Dx[la * n + la + r];
+    }
+    __syncthreads();
     double eint = 0.0, eom = 0.0;
-    for (int row = warp; row < n2; row += nw) {
+    for (int pq = threadIdx.x; pq < np; pq += blockDim.x) {
+        int mu = 0, r = pq;
+        while (r >= n - mu) { r -= n - mu; ++mu; }
+        int nu = mu + r;
         double g = 0.0;
-        for (int c = lane; c < n2; c += 32) g = fma(C[(size_t)row * n2 + c], Dx[c], g);
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) g += __shfl_xor_sync(0xffffffffu, g, o);
-        if (lane == 0) {
-            int64_t o = d.frag_moff[x] + row;
+        for (int rs = 0; rs < np; ++rs) g = fma(C[(size_t)rs * np + pq], dpk[rs], g);
+        const double w = (mu == nu) ? 1.0 : 2.0;
+        for (int k = 0; k < (mu == nu ? 1 : 2); ++k) {
+            int64_t o = d.frag_moff[x] + (k == 0 ? mu * n + nu : nu * n + mu);
             double om = (Venv ? Venv[o] : 0.0) + (Jenv ? Jenv[o] : 0.0);
-            double f = h[o] + g + om;
-            if (F) F[o] = f;
+            if (F) F[o] = h[o] + g + om;
             if (omega) omega[o] = om;
-            eint += Dx[row] * (h[o] + 0.5 * g);
-            eom += Dx[row] * om;
         }
+        int64_t o = d.frag_moff[x] + mu * n + nu;
+        double om = (Venv ? Venv[o] : 0.0) + (Jenv ? Jenv[o] : 0.0);
+        eint += w * Dx[mu * n + nu] * (h[o] + 0.5 * g);
+        eom += w * Dx[mu * n + nu] * om;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        eint += __shfl_xor_sync(0xffffffffu, eint, o);
+        eom += __shfl_xor_sync(0xffffffffu, eom, o);
     }
     __shared__ double r1[32], r2[32];
+    int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
     if (lane == 0) {
         r1[warp] = eint;
         r2[warp] = eom;
@@ -307,7 +322,8 @@ cudaError_t launch_fock_energy(const Dev& d, const double* h, const double* Venv
                                const double* eric, const double* D, double* F, double* omega, const double* e_nn,
                                double* E_int, double* tr_omega, cudaStream_t s)
 {
-    k_fock_assemble<<<d.n_frag, 256, 0, s>>>(d, h, Venv, Jenv, eric, D, F, omega, e_nn, E_int, tr_omega);
+    size_t smem = sizeof(double) * (size_t)d.max_nao * (d.max_nao + 1) / 2;
+    k_fock_assemble<<<d.n_frag, 256, smem, s>>>(d, h, Venv, Jenv, eric, D, F, omega, e_nn, E_int, tr_omega);
     note_launches(1);
     return cudaGetLastError();
 }

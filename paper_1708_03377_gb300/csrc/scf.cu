@@ -65,12 +65,23 @@ struct JacobiScratch {
 
 // Cyclic Jacobi on the symmetric m x m matrix A (shared, leading dimension ld), m <= 128.
 // Parallel ordering: round-robin pairing (circle method), m/2 disjoint rotations per round, each
-// zeroing A_pq with t = sgn(theta)/(|theta| + sqrt(theta^2 + 1)), theta = (A_qq - A_pp)/(2 A_pq).
+// zeroing A_pq with t = sgn(theta)/(|theta| + sqrt(theta^2 + 1)), theta = (A_qq - A_pp)/(2 A_pq)
+// (Golub & Van Loan, symmetric Schur decomposition).
 // On exit diag(A) holds the eigenvalues and the columns of V the eigenvectors.  Stops when the
 // off-diagonal Frobenius norm is below 1e-14 times the largest diagonal magnitude.
 __device__ void jacobi_eigh(double* A, double* V, int m, int ld, JacobiScratch* js, double* red)
 {
-    for (int e = threadIdx.x; e < m * m; e += blockDim.x) V[(e / m) * ld + e % m] = (e / m == e % m) ? 1.0 : 0.0;
+    // A built from matrix products is symmetric only to rounding; an orthogonal similarity keeps
+    // the antisymmetric part, so symmetrise first and measure convergence on the upper triangle.
+    for (int e = threadIdx.x; e < m * m; e += blockDim.x) {
+        int r = e / m, c = e % m;
+        V[r * ld + c] = (r == c) ? 1.0 : 0.0;
+        if (r < c) {
+            double v = 0.5 * (A[r * ld + c] + A[c * ld + r]);
+            A[r * ld + c] = v;
+            A[c * ld + r] = v;
+        }
+    }
     __syncthreads();
     const int M = m + (m & 1);
     const int half = M / 2;
@@ -79,7 +90,7 @@ __device__ void jacobi_eigh(double* A, double* V, int m, int ld, JacobiScratch* 
         for (int e = threadIdx.x; e < m * m; e += blockDim.x) {
             int r = e / m, c = e % m;
             double v = A[r * ld + c];
-            if (r != c) off += v * v; else dg = fmax(dg, fabs(v));
+            if (r < c) off += 2.0 * v * v; else if (r == c) dg = fmax(dg, fabs(v));
         }
         off = block_sum(off, red);
         dg = block_max(dg, red);
@@ -92,13 +103,16 @@ __device__ void jacobi_eigh(double* A, double* V, int m, int ld, JacobiScratch* 
                 int p = min(i1, i2), q = max(i1, i2);
                 double c = 1.0, s = 0.0;
                 if (q < m) {
-                    double apq = A[p * ld + q];
-                    if (apq != 0.0) {
-                        double theta = (A[q * ld + q] - A[p * ld + p]) / (2.0 * apq);
-                        double t = 1.0 / (fabs(theta) + sqrt(fma(theta, theta, 1.0)));
-                        if (theta < 0.0) t = -t;
-                        c = rsqrt(fma(t, t, 1.0));
-                        s = t * c;
+                    // rotation angle in FP32 (any exact rotation reduces A_pq; FP32 t leaves a 1e-7
+                    // residual that the next sweep removes); c and s in FP64 so c^2 + s^2 = 1
+                    const float apq = (float)A[p * ld + q];
+                    if (apq != 0.0f) {
+                        const float theta = (float)(A[q * ld + q] - A[p * ld + p]) / (2.0f * apq);
+                        float t = 1.0f / (fabsf(theta) + sqrtf(fmaf(theta, theta, 1.0f)));
+                        if (theta < 0.0f) t = -t;
+                        const double td = (double)t;
+                        c = rsqrt(fma(td, td, 1.0));
+                        s = td * c;
                     }
                 }
                 js->p[k] = p;
@@ -183,6 +197,12 @@ cudaError_t launch_orthogonaliser(const Dev& d, const double* S, double* X, int*
 }
 
 // ------------------------------------------------------------------------------------------ fragment SCF
+// PACKED: G from the packed transposed tensor CT[rs][pq] (setup.cu), thread per pq = (mu <= nu);
+// otherwise from the full C[mu nu][lambda sigma], one warp per row.
+// Shared memory: Hw Ss Xs Ds Fs W A V Vp, nine n x n doubles (W doubles as the packed density).
+// The Jacobi of each micro-iteration starts from the previous eigenvectors Vp: A <- Vp^T A Vp,
+// so only the small change of F' between iterations has to be rotated away.
+template <bool PACKED>
 __global__ void __launch_bounds__(256) k_fragment_scf(Dev d, ScfArgs a)
 {
     const int x = blockIdx.x;
@@ -190,6 +210,7 @@ __global__ void __launch_bounds__(256) k_fragment_scf(Dev d, ScfArgs a)
     const int m = a.nmo[x];
     const int nocc = d.frag_nocc[x];
     const int n2 = n * n;
+    const int np = n * (n + 1) / 2;
     const int64_t mo = d.frag_moff[x];
     extern __shared__ double sm[];
     double* Hw = sm;
@@ -200,6 +221,7 @@ __global__ void __launch_bounds__(256) k_fragment_scf(Dev d, ScfArgs a)
     double* W = Fs + n2;
     double* A = W + n2;
     double* V = A + n2;
+    double* Vp = V + n2;
     __shared__ JacobiScratch js;
     __shared__ double red[32];
     __shared__ double B[8][8];
@@ -207,7 +229,7 @@ __global__ void __launch_bounds__(256) k_fragment_scf(Dev d, ScfArgs a)
     __shared__ int order[128];
     const int tid = threadIdx.x, nt = blockDim.x;
     const int lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
-    const double* C = a.eric + d.frag_eoff[x];
+    const double* C = PACKED ? a.eric + d.frag_coff[x] : a.eric + d.frag_eoff[x];
     double* hF = a.diis_F + (int64_t)x * a.diis_stride;
     double* he = hF + (int64_t)a.diis_size * n2;
 
@@ -218,12 +240,32 @@ __global__ void __launch_bounds__(256) k_fragment_scf(Dev d, ScfArgs a)
         if (a.have_start) Ds[e] = a.D[mo + e];
     }
     __syncthreads();
+    bool have_vp = false;
 
     // Roothaan step: W holds the (extrapolated) Fock matrix on entry; Ds gets the aufbau density.
     auto roothaan = [&]() {
         mm(V, W, Xs, n, n, m, n, false);      // V = F X        (n x m)
         mm(A, Xs, V, m, n, m, n, true);       // A = X^T F X    (m x m)
+        if (have_vp) {
+            mm(V, A, Vp, m, m, m, n, false);  // A <- Vp^T A Vp
+            mm(A, Vp, V, m, m, m, n, true);
+        }
         jacobi_eigh(A, V, m, n, &js, red);    // A -> eigenvalues, V -> eigenvectors (m x m)
+        if (have_vp) {
+            mm(W, Vp, V, m, m, m, n, false);  // full eigenvectors Vp V
+            for (int e = tid; e < m * m; e += nt) {
+                int i = e / m, j = e % m;
+                V[i * n + j] = W[i * n + j];
+                Vp[i * n + j] = W[i * n + j];
+            }
+        } else {
+            for (int e = tid; e < m * m; e += nt) {
+                int i = e / m, j = e % m;
+                Vp[i * n + j] = V[i * n + j];
+            }
+        }
+        have_vp = true;
+        __syncthreads();
         if (tid == 0) {
             for (int k = 0; k < m; ++k) order[k] = k;
             for (int k = 0; k < nocc; ++k) {  // selection of the nocc lowest, ties by index
@@ -263,13 +305,32 @@ __global__ void __launch_bounds__(256) k_fragment_scf(Dev d, ScfArgs a)
     bool conv = false;
     int it = 0;
     for (it = 1; it <= a.max_iter; ++it) {
-        // F = h + omega + C D  (one warp per row of C, coalesced)
-        for (int row = warp; row < n2; row += nw) {
-            double g = 0.0;
-            for (int c = lane; c < n2; c += 32) g = fma(C[(size_t)row * n2 + c], Ds[c], g);
+        // F = h + omega + G[D]
+        if (PACKED) {
+            double* dpk = W;
+            for (int rs = tid; rs < np; rs += nt) {
+                int la = 0, r = rs;
+                while (r >= n - la) { r -= n - la; ++la; }
+                dpk[rs] = Ds[la * n + la + r];
+            }
+            __syncthreads();
+            for (int pq = tid; pq < np; pq += nt) {
+                int mu = 0, r = pq;
+                while (r >= n - mu) { r -= n - mu; ++mu; }
+                int nu = mu + r;
+                double g = 0.0;
+                for (int rs = 0; rs < np; ++rs) g = fma(C[(size_t)rs * np + pq], dpk[rs], g);
+                Fs[mu * n + nu] = Hw[mu * n + nu] + g;
+                Fs[nu * n + mu] = Hw[nu * n + mu] + g;
+            }
+        } else {
+            for (int row = warp; row < n2; row += nw) {
+                double g = 0.0;
+                for (int c = lane; c < n2; c += 32) g = fma(C[(size_t)row * n2 + c], Ds[c], g);
 #pragma unroll
-            for (int o = 16; o > 0; o >>= 1) g += __shfl_xor_sync(0xffffffffu, g, o);
-            if (lane == 0) Fs[row] = Hw[row] + g;
+                for (int o = 16; o > 0; o >>= 1) g += __shfl_xor_sync(0xffffffffu, g, o);
+                if (lane == 0) Fs[row] = Hw[row] + g;
+            }
         }
         __syncthreads();
         double part = 0.0;
@@ -317,7 +378,7 @@ __global__ void __launch_bounds__(256) k_fragment_scf(Dev d, ScfArgs a)
         }
         __syncthreads();
         if (hist >= 2) {
-            if (tid == 0) {  // solve [B -1; -1 0] [c; l] = [0; -1] by Gaussian elimination, partial pivoting
+            if (tid == 0) {  // solve [B -1; -1 0] [c; l] = [0; -1] by Gauss-Jordan, partial pivoting
                 double M[9][10];
                 const int s = hist + 1;
                 for (int i = 0; i < s; ++i)
@@ -373,10 +434,11 @@ __global__ void __launch_bounds__(256) k_fragment_scf(Dev d, ScfArgs a)
 
 cudaError_t launch_fragment_scf(const Dev& d, const ScfArgs& a, int max_n, cudaStream_t s)
 {
-    size_t smem = 8 * (size_t)max_n * max_n * sizeof(double);
-    cudaError_t e = cudaFuncSetAttribute(k_fragment_scf, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    size_t smem = 9 * (size_t)max_n * max_n * sizeof(double);
+    auto kern = a.eric_packed ? k_fragment_scf<true> : k_fragment_scf<false>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    k_fragment_scf<<<d.n_frag, 256, smem, s>>>(d, a);
+    kern<<<d.n_frag, 256, smem, s>>>(d, a);
     note_launches(1);
     return cudaGetLastError();
 }

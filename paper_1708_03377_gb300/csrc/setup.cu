@@ -271,88 +271,126 @@ cudaError_t launch_one_electron(const Dev& d, double* S, double* h, cudaStream_t
     return cudaGetLastError();
 }
 
-// Environment nuclear attraction: V_env^x = sum_{y in N(x)} V^y, V^y_{mu nu} = -sum_{B in y} Z_B <mu|1/r_B|nu>.
-__global__ void k_nuclear_env(Dev d, double* V)
+// ------------------------------------------------------------------------------------------ nuclear (Hermite)
+// Field of the nuclei of fragment y on primitive pair P in Hermite form (McMurchie-Davidson):
+//   V~_P[tuv] = sum_{C in y} -Z_C (2 pi/p) R_tuv(p, P - C),
+// so that V^y_{mu nu} = sum_{P in (mu,nu)} K_P sum_tuv E^{mu nu}_tuv V~_P[tuv] and
+// tr(D^x V^y) = sum_P sum_tuv Dtrue_P[tuv] V~_P[tuv] with Dtrue_P = Dh_P p/c (c = sqrt(2 pi^{5/2})).
+template <int L>
+__device__ inline void nuclear_field(const Dev& d, const double4_32a P, int atom0, int nat, double* acc)
 {
-    int x = blockIdx.y;
-    int n = d.frag_nao[x];
-    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n * n; e += gridDim.x * blockDim.x) {
-        int mu = e / n, nu = e % n;
-        AOPair q = ao_pair(d, x, mu, nu);
-        double acc = 0.0;
-        for (int i = 0; i < q.na; ++i)
-            for (int j = 0; j < q.nb; ++j) {
-                double a = d.p_exp[q.pa0 + i], b = d.p_exp[q.pb0 + j], p = a + b;
-                double cc = d.p_coef[q.pa0 + i] * d.p_coef[q.pb0 + j];
-                double P[3], R2 = 0.0, E[3][3][3][5];
-                for (int k = 0; k < 3; ++k) {
-                    P[k] = (a * q.A[k] + b * q.B[k]) / p;
-                    R2 += (q.A[k] - q.B[k]) * (q.A[k] - q.B[k]);
-                    md_E1(q.la, q.lb, p, P[k] - q.A[k], P[k] - q.B[k], E[k]);
-                }
-                double K = cc * exp(-a * b / p * R2);
-                double v = 0.0;
-                for (int c = d.frag_nbr0[x]; c < d.frag_nbr0[x + 1]; ++c) {
-                    int y = d.nbr[c];
-                    v += nuclear_prim(d, q, a, b, E[0], E[1], E[2], P, p, d.frag_atom0[y], d.frag_nat[y]);
-                }
-                acc += K * v;
-            }
-        V[d.frag_moff[x] + e] = acc * q.scale;
+    double F[L + 1], base[L + 1], R[nh(L)];
+    for (int c = atom0; c < atom0 + nat; ++c) {
+        const double* C = d.atom_xyz + 3 * c;
+        double X = P.x - C[0], Y = P.y - C[1], Z = P.z - C[2];
+        double T = P.w * (X * X + Y * Y + Z * Z);
+        boys_fp64_rt(d.boys, T, L, F);
+        double f = -d.atom_Z[c] * 2.0 * kPi / P.w;
+#pragma unroll
+        for (int n = 0; n <= L; ++n) {
+            base[n] = f * F[n];
+            f *= -2.0 * P.w;
+        }
+        md_R<L, double>(R, base, X, Y, Z);
+#pragma unroll
+        for (int k = 0; k < nh(L); ++k) acc[k] += R[k];
     }
 }
 
-cudaError_t launch_nuclear_env(const Dev& d, double* V, cudaStream_t s)
+__device__ inline void nuclear_field_rt(const Dev& d, int L, const double4_32a P, int atom0, int nat, double* acc)
 {
-    dim3 g((d.max_nao * d.max_nao + 127) / 128, d.n_frag);
-    k_nuclear_env<<<g, 128, 0, s>>>(d, V);
-    note_launches(1);
-    return cudaGetLastError();
+    switch (L) {
+        case 0: nuclear_field<0>(d, P, atom0, nat, acc); break;
+        case 1: nuclear_field<1>(d, P, atom0, nat, acc); break;
+        case 2: nuclear_field<2>(d, P, atom0, nat, acc); break;
+        case 3: nuclear_field<3>(d, P, atom0, nat, acc); break;
+        default: nuclear_field<4>(d, P, atom0, nat, acc); break;
+    }
 }
 
-// tr(D^x V^y) for each pair, both directions: block (pair, direction), threads over mu nu of the
-// fragment whose electrons feel the other's nuclei.
-__global__ void k_nuclear_traces(Dev d, const double* D, double* tr_xy, double* tr_yx)
+// primitive pair number t of fragment x (classes in order) -> (class, global index in the class)
+__device__ inline bool frag_prim_pair(const Dev& d, int x, int t, int& L, int& g)
+{
+    for (L = 0; L < kClasses; ++L) {
+        int n = d.frag_npp[x * kClasses + L];
+        if (t < n) {
+            g = d.frag_pp0[x * kClasses + L] + t;
+            return true;
+        }
+        t -= n;
+    }
+    return false;
+}
+
+// Environment field of all neighbours' nuclei on every primitive pair of x, in Hermite form,
+// stored pre-scaled by p/c so that the J back-transform turns it into V_env.
+__global__ void k_nuclear_env_h(Dev d, double* vh0, double* vh1, double* vh2, double* vh3, double* vh4)
+{
+    double* vh[kClasses] = {vh0, vh1, vh2, vh3, vh4};
+    int x = blockIdx.y;
+    int npp = 0;
+    for (int L = 0; L < kClasses; ++L) npp += d.frag_npp[x * kClasses + L];
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < npp; t += gridDim.x * blockDim.x) {
+        int L, g;
+        if (!frag_prim_pair(d, x, t, L, g)) continue;
+        double4_32a P = d.pp_P[L][g];
+        double acc[nh(kMaxLPair)];
+        for (int k = 0; k < nh(L); ++k) acc[k] = 0.0;
+        for (int c = d.frag_nbr0[x]; c < d.frag_nbr0[x + 1]; ++c) {
+            int y = d.nbr[c];
+            nuclear_field_rt(d, L, P, d.frag_atom0[y], d.frag_nat[y], acc);
+        }
+        double sc = P.w / kSqrt2Pi52;
+        for (int k = 0; k < nh(L); ++k) vh[L][(size_t)k * d.n_pp[L] + g] = acc[k] * sc;
+    }
+}
+
+cudaError_t launch_nuclear_env(const Dev& d, double* vh[kClasses], double* V, cudaStream_t s)
+{
+    dim3 g(8, d.n_frag);
+    k_nuclear_env_h<<<g, 128, 0, s>>>(d, vh[0], vh[1], vh[2], vh[3], vh[4]);
+    note_launches(1);
+    Dev dv = d;
+    for (int L = 0; L < kClasses; ++L) dv.pp_Jh[L] = vh[L];
+    return launch_back_transform(dv, V, s);
+}
+
+// tr(D^x V^y) for each pair, both directions: block (pair, direction), threads over the primitive
+// pairs of the fragment whose electrons feel the other fragment's nuclei.
+__global__ void k_nuclear_traces_h(Dev d, double* tr_xy, double* tr_yx)
 {
     int pr = blockIdx.x, dir = blockIdx.y;
     int x = dir == 0 ? d.pair_x[pr] : d.pair_y[pr];
     int y = dir == 0 ? d.pair_y[pr] : d.pair_x[pr];
-    int n = d.frag_nao[x];
+    int npp = 0;
+    for (int L = 0; L < kClasses; ++L) npp += d.frag_npp[x * kClasses + L];
     double acc = 0.0;
-    for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
-        int mu = e / n, nu = e % n;
-        AOPair q = ao_pair(d, x, mu, nu);
-        double v = 0.0;
-        for (int i = 0; i < q.na; ++i)
-            for (int j = 0; j < q.nb; ++j) {
-                double a = d.p_exp[q.pa0 + i], b = d.p_exp[q.pb0 + j], p = a + b;
-                double cc = d.p_coef[q.pa0 + i] * d.p_coef[q.pb0 + j];
-                double P[3], R2 = 0.0, E[3][3][3][5];
-                for (int k = 0; k < 3; ++k) {
-                    P[k] = (a * q.A[k] + b * q.B[k]) / p;
-                    R2 += (q.A[k] - q.B[k]) * (q.A[k] - q.B[k]);
-                    md_E1(q.la, q.lb, p, P[k] - q.A[k], P[k] - q.B[k], E[k]);
-                }
-                v += cc * exp(-a * b / p * R2) *
-                     nuclear_prim(d, q, a, b, E[0], E[1], E[2], P, p, d.frag_atom0[y], d.frag_nat[y]);
-            }
-        acc += v * q.scale * D[d.frag_moff[x] + e];
+    for (int t = threadIdx.x; t < npp; t += blockDim.x) {
+        int L, g;
+        if (!frag_prim_pair(d, x, t, L, g)) continue;
+        double4_32a P = d.pp_P[L][g];
+        double v[nh(kMaxLPair)];
+        for (int k = 0; k < nh(L); ++k) v[k] = 0.0;
+        nuclear_field_rt(d, L, P, d.frag_atom0[y], d.frag_nat[y], v);
+        double s = 0.0;
+        for (int k = 0; k < nh(L); ++k) s += d.pp_Dh[L][(size_t)k * d.n_pp[L] + g] * v[k];
+        acc += s * P.w / kSqrt2Pi52;
     }
     __shared__ double red[256];
     red[threadIdx.x] = acc;
     __syncthreads();
-    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
-        if (threadIdx.x < s) red[threadIdx.x] += red[threadIdx.x + s];
+    for (int st = blockDim.x / 2; st > 0; st >>= 1) {
+        if (threadIdx.x < st) red[threadIdx.x] += red[threadIdx.x + st];
         __syncthreads();
     }
     if (threadIdx.x == 0) (dir == 0 ? tr_xy : tr_yx)[pr] = red[0];
 }
 
-cudaError_t launch_nuclear_traces(const Dev& d, const double* D, double* tr_xy, double* tr_yx, cudaStream_t s)
+cudaError_t launch_nuclear_traces(const Dev& d, const double* /*D*/, double* tr_xy, double* tr_yx, cudaStream_t s)
 {
     if (d.n_pairs == 0) return cudaSuccess;
     dim3 g(d.n_pairs, 2);
-    k_nuclear_traces<<<g, 256, 0, s>>>(d, D, tr_xy, tr_yx);
+    k_nuclear_traces_h<<<g, 256, 0, s>>>(d, tr_xy, tr_yx);
     note_launches(1);
     return cudaGetLastError();
 }
@@ -520,17 +558,34 @@ cudaError_t launch_intra_eri(const Dev& d, double* eri, int max_l, cudaStream_t 
 
 // Coulomb-minus-half-exchange tensor, so that G[D] = J[D] - K[D]/2 is one contraction:
 //   C[mu nu][lambda sigma] = (mu nu|lambda sigma) - (1/2) (mu lambda|nu sigma).
+// Stored packed over mu <= nu and lambda <= sigma (D and G are symmetric) and transposed:
+//   CT[rs][pq] = C[mu nu][lambda sigma] + [lambda != sigma] C[mu nu][sigma lambda],
+// with pq = pair(mu, nu), rs = pair(lambda, sigma), pair(i, j) = i n - i (i - 1)/2 + (j - i), i <= j,
+// so that G_pq = sum_rs CT[rs][pq] D_rs and a warp of consecutive pq reads consecutive doubles.
+__device__ inline int tri_i(int p, int n)
+{
+    int i = 0;
+    while (p >= n - i) { p -= n - i; ++i; }
+    return i;
+}
+
 __global__ void k_coulomb_exchange(Dev d, const double* eri, double* eric)
 {
     int x = blockIdx.y;
     int n = d.frag_nao[x];
-    size_t n2 = (size_t)n * n, n4 = n2 * n2;
+    int np = n * (n + 1) / 2;
+    size_t n2 = (size_t)n * n;
     const double* e = eri + d.frag_eoff[x];
-    double* c = eric + d.frag_eoff[x];
-    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n4; i += (size_t)gridDim.x * blockDim.x) {
-        size_t mn = i / n2, ls = i % n2;
-        int mu = mn / n, nu = mn % n, la = ls / n, si = ls % n;
-        c[i] = e[i] - 0.5 * e[((size_t)mu * n + la) * n2 + (size_t)nu * n + si];
+    double* c = eric + d.frag_coff[x];
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < (size_t)np * np;
+         i += (size_t)gridDim.x * blockDim.x) {
+        int rs = (int)(i / np), pq = (int)(i % np);
+        int mu = tri_i(pq, n), nu = mu + pq - (mu * n - mu * (mu - 1) / 2);
+        int la = tri_i(rs, n), si = la + rs - (la * n - la * (la - 1) / 2);
+        size_t mn = (size_t)mu * n + nu;
+        double v = e[mn * n2 + (size_t)la * n + si] - 0.5 * e[((size_t)mu * n + la) * n2 + (size_t)nu * n + si];
+        if (la != si) v += e[mn * n2 + (size_t)si * n + la] - 0.5 * e[((size_t)mu * n + si) * n2 + (size_t)nu * n + la];
+        c[i] = v;
     }
 }
 
