@@ -82,7 +82,10 @@ typedef struct {
 } fef_basis;
 
 typedef struct {
-    int32_t precision;       /* FEF_FP64 or FEF_MIXED (FP32 ERI core, FP64 Boys/accumulation/eigensolve) */
+    int32_t precision;       /* FEF_FP64, or FEF_MIXED: Fock builds after the first FP64 one add the FP32-core
+                                J-engine of D - D_ref to the FP64 field of D_ref (FP64 accumulation,
+                                FP64 intra-fragment G, eigensolve and energies) until |dE| <
+                                mixed_switch, then FP64 builds until convergence */
     double cutoff_A;         /* fragment pairs with min atom-atom distance >= cutoff are dropped
                                 (J and V together); <= 0 keeps all pairs */
     double schwarz;          /* shell quartet (ab|cd) dropped when Q_ab Q_cd < schwarz (0: none) */
@@ -122,6 +125,8 @@ fef_status fef_ao_layout(const fef_ctx* ctx, int32_t* n_ao_per_frag, int64_t* of
  * D: packed densities to build from (becomes the context's current density), or NULL to use the
  * current densities.  F_out: packed output, or NULL.  on_device: 1 if D/F_out are device pointers.
  * The inter-fragment J is the fused McMurchie-Davidson J-engine: no ERI tensor is formed.
+ * FP64 mode: the full FP64 J-engine.  MIXED: J[D^y] = J[D_ref] + J_fp32[D^y - D_ref] relative to the
+ * last FP64 build of this context (the first build is FP64 and becomes the reference).
  * Errors: ARG, CUDA, NUMERIC. */
 fef_status fef_build_fock(fef_ctx* ctx, const double* D, double* F_out, int on_device);
 
@@ -161,9 +166,10 @@ fef_status fef_stats(const fef_ctx* ctx, int64_t* shell_quartets, int64_t* prim_
                      double* jengine_ms, int64_t* kernel_launches, int64_t* class_quartets);
 
 /* Per-macro-iteration log of the last fef_iterate (record 0 = the start densities).  Each record is
- * 8 doubles: k, E_total, |dE_total|, max_x |dE_x|, max micro-iterations over fragments, summed
- * micro-iterations, J-engine ms of the Fock build, fragment-SCF ms (CUDA events).  Copies
- * min(n, max_records) records into records (host, nullable); *n_records (nullable) gets n. */
+ * 9 doubles: k, E_total, |dE_total|, max_x |dE_x|, max micro-iterations over fragments, summed
+ * micro-iterations, J-engine ms of the Fock build, fragment-SCF ms (CUDA events), and 1.0 if the
+ * build used the FP32 core (MIXED) else 0.0.  Copies min(n, max_records) records into records
+ * (host, nullable); *n_records (nullable) gets n. */
 fef_status fef_history(const fef_ctx* ctx, int32_t max_records, double* records, int32_t* n_records);
 
 /* Message of the last failing call on ctx (or of the last failed fef_create when ctx is NULL). */

@@ -258,10 +258,11 @@ def fef_history(ctx: Context) -> list:
     """Per-macro-iteration records of the last fef_iterate as dicts."""
     n = ctypes.c_int32(0)
     _check(lib().fef_history(ctx.ptr, 0, None, ctypes.byref(n)), ctx.ptr)
-    buf = np.zeros(max(1, n.value) * 8)
+    nf = 9
+    buf = np.zeros(max(1, n.value) * nf)
     _check(lib().fef_history(ctx.ptr, n.value, _ptr(buf, ctypes.c_double), ctypes.byref(n)), ctx.ptr)
-    keys = ("k", "E_tot", "dE_tot", "dE_x_max", "micro_max", "micro_sum", "jengine_ms", "scf_ms")
-    return [dict(zip(keys, buf[8 * i:8 * i + 8].tolist())) for i in range(n.value)]
+    keys = ("k", "E_tot", "dE_tot", "dE_x_max", "micro_max", "micro_sum", "jengine_ms", "scf_ms", "fp32")
+    return [dict(zip(keys, buf[nf * i:nf * i + nf].tolist())) for i in range(n.value)]
 
 
 def fef_destroy(ctx: Context):

@@ -60,8 +60,13 @@ struct Buffers {
     int* nmo = nullptr;
     // per-build data
     double *D = nullptr, *F = nullptr, *Jenv = nullptr, *omega = nullptr;
-    double *e_J = nullptr, *tr_xy = nullptr, *tr_yx = nullptr, *tr_omega = nullptr;
-    double *E_int = nullptr, *E_scf = nullptr, *E_pair = nullptr, *E_frag = nullptr, *E_tot = nullptr;
+    double *tr_xy = nullptr, *tr_yx = nullptr, *trV = nullptr, *trJ = nullptr;
+    double *E_int = nullptr, *E_scf = nullptr, *E_frag = nullptr, *E_tot = nullptr;
+    // mixed precision: FP64 reference Hermite density and field of the last FP64 build
+    double* Dh_ref[kClasses] = {};
+    double* Jh_ref[kClasses] = {};
+    bool have_ref = false;
+    float* boys32 = nullptr;
     int* iters = nullptr;
     int* err_flag = nullptr;
     double* diis = nullptr;
@@ -146,27 +151,46 @@ static void clear_flags(fef_ctx* c)
 
 // One FEF Fock build from the context's current densities: Hermite densities, J-engine, back-transform,
 // F = h + G + V_env + J_env, and all reference energies of the current densities.
-static void build_fock_internal(fef_ctx* c)
+//   fp32 = false: full FP64 J-engine; the Hermite density and field become the mixed-precision
+//                 reference (D_ref, J[D_ref]).
+//   fp32 = true : incremental J[D] = J[D_ref] + J_fp32[D - D_ref] (needs a reference).
+static void build_fock_internal(fef_ctx* c, bool fp32 = false)
 {
     Buffers* b = c->buf;
     const Dev& d = c->dev;
     cudaStream_t s = c->stream;
+    if (fp32 && !b->have_ref) fp32 = false;
     ck(launch_hermite_density(d, b->D, s), "hermite density");
-    for (int L = 0; L < kClasses; ++L)
-        if (b->njh[L] > 0) ck(cudaMemsetAsync(b->Jh[L], 0, sizeof(double) * b->njh[L], s), "zero Jh");
-    if (c->n_pairs > 0) ck(cudaMemsetAsync(b->e_J, 0, sizeof(double) * c->n_pairs, s), "zero e_J");
+    for (int L = 0; L < kClasses; ++L) {
+        if (b->njh[L] == 0) continue;
+        if (fp32)
+            ck(cudaMemcpyAsync(b->Jh[L], b->Jh_ref[L], sizeof(double) * b->njh[L], cudaMemcpyDeviceToDevice, s), "Jh");
+        else
+            ck(cudaMemsetAsync(b->Jh[L], 0, sizeof(double) * b->njh[L], s), "zero Jh");
+    }
+    if (fp32) ck(launch_delta_density(d, b->Dh_ref, s), "delta density");
     const int2* tiles[kClasses][kClasses];
     for (int i = 0; i < kClasses; ++i)
         for (int j = 0; j < kClasses; ++j) tiles[i][j] = b->tiles[i][j];
     ck(cudaEventRecord(b->ev0, s), "event");
-    ck(launch_jengine(d, tiles, b->n_tiles, c->opt.schwarz, b->e_J, c->opt.precision, s), "J-engine");
+    ck(launch_jengine(d, tiles, b->n_tiles, c->opt.schwarz, fp32 ? 1 : 0, s), "J-engine");
     ck(cudaEventRecord(b->ev1, s), "event");
+    if (!fp32) {
+        for (int L = 0; L < kClasses; ++L) {
+            if (b->njh[L] == 0) continue;
+            ck(cudaMemcpyAsync(b->Jh_ref[L], b->Jh[L], sizeof(double) * b->njh[L], cudaMemcpyDeviceToDevice, s), "ref");
+            ck(cudaMemcpyAsync(b->Dh_ref[L], d.pp_Dh[L], sizeof(double) * b->njh[L], cudaMemcpyDeviceToDevice, s),
+               "ref");
+        }
+        b->have_ref = true;
+    }
+    c->last_build_fp32 = fp32;
     ck(launch_back_transform(d, b->Jenv, s), "back-transform");
     ck(launch_fock_energy(d, b->h, b->Venv, b->Jenv, b->eric, b->D, b->F, b->omega, b->e_nn_intra, b->E_int,
-                          b->tr_omega, s),
+                          b->trV, b->trJ, s),
        "fock");
     ck(launch_nuclear_traces(d, b->D, b->tr_xy, b->tr_yx, s), "nuclear traces");
-    ck(launch_energies(d, b->e_J, b->tr_xy, b->tr_yx, b->e_nn_pair, b->E_int, b->E_pair, b->E_frag, b->E_tot, s),
+    ck(launch_energies(d, b->E_int, b->trV, b->trJ, b->tr_xy, b->tr_yx, b->e_nn_pair, b->E_frag, b->E_tot, s),
        "energies");
     ck(launch_check_finite(b->F, c->mat_total, b->err_flag, s), "check");
     c->energies_valid = true;
@@ -428,6 +452,7 @@ extern "C" fef_status fef_create(const fef_geometry* g, const fef_basis* bs, con
         d.sp_Q = sp_Q;
         double4_32a* ppP[kClasses];
         float4* ppPf[kClasses];
+        float4* ppPr[kClasses];
         double* ppK[kClasses];
         float* ppQ[kClasses];
         for (int L = 0; L < kClasses; ++L) {
@@ -437,6 +462,11 @@ extern "C" fef_status fef_create(const fef_geometry* g, const fef_basis* bs, con
             d.pp_ij[L] = b->upload(pp_ij[L], s, "prim pairs");
             ppP[L] = b->alloc<double4_32a>(n, "prim pairs");
             ppPf[L] = b->alloc<float4>(n, "prim pairs");
+            ppPr[L] = b->alloc<float4>(n, "prim pairs");
+            d.pp_Pr[L] = ppPr[L];
+            d.pp_Dh32[L] = b->alloc<float>((size_t)nh(L) * n, "hermite density fp32");
+            b->Dh_ref[L] = b->alloc<double>((size_t)nh(L) * n, "hermite density ref");
+            b->Jh_ref[L] = b->alloc<double>((size_t)nh(L) * n, "hermite field ref");
             ppK[L] = b->alloc<double>(n, "prim pairs");
             ppQ[L] = b->alloc<float>(n, "prim pairs");
             d.pp_P[L] = ppP[L];
@@ -450,6 +480,8 @@ extern "C" fef_status fef_create(const fef_geometry* g, const fef_basis* bs, con
         }
         b->boys = b->alloc<double>((size_t)kBoysRows * kBoysRowLen, "boys");
         d.boys = b->boys;
+        b->boys32 = b->alloc<float>((size_t)kBoys32Rows * kBoysRowLen, "boys32");
+        d.boys32 = b->boys32;
         b->err_flag = b->alloc<int>(1, "flag");
         d.err_flag = b->err_flag;
         ck(cudaMemsetAsync(b->err_flag, 0, sizeof(int), s), "flag");
@@ -461,8 +493,9 @@ extern "C" fef_status fef_create(const fef_geometry* g, const fef_basis* bs, con
         // ---- geometry-time kernels
         ck(launch_prepare(d, xyz_A, atom_xyz, p_coef, p_coef_raw_d, p_l_d, c->n_prims, s), "prepare");
         ck(launch_boys_table(b->boys, s), "boys table");
+        ck(launch_boys_table32(b->boys, b->boys32, s), "boys table fp32");
         ck(launch_ao_scale(d, ao_scale, ao_global, nullptr, s), "ao scale");
-        ck(launch_prim_pairs(d, ppP, ppPf, ppK, s), "prim pairs");
+        ck(launch_prim_pairs(d, ppP, ppPf, ppK, ppPr, s), "prim pairs");
         b->S = b->alloc<double>(c->mat_total, "S");
         b->h = b->alloc<double>(c->mat_total, "h");
         ck(launch_one_electron(d, b->S, b->h, s), "one-electron");
@@ -516,12 +549,28 @@ extern "C" fef_status fef_create(const fef_geometry* g, const fef_basis* bs, con
         // intra-fragment two-electron tensor -> Schwarz factors and C = (mu nu|ls) - (mu l|nu s)/2
         {
             double* eri = b->alloc<double>(c->eri_total, "intra eri");
-            ck(launch_intra_eri(d, eri, max_l, s), "intra eri");
+            // tasks: (fragment, shell pair s1 <= s2, bra component), sorted by class
+            std::vector<std::pair<int, int4>> tk;
+            for (int x = 0; x < nf; ++x)
+                for (int s1 = frag_sp0[x]; s1 < frag_sp0[x + 1]; ++s1)
+                    for (int s2 = s1; s2 < frag_sp0[x + 1]; ++s2) {
+                        int la = sh_l[sp_a[s1]], lb = sh_l[sp_b[s1]], lc = sh_l[sp_a[s2]], ld = sh_l[sp_b[s2]];
+                        int cls = ((la * 3 + lb) * 3 + lc) * 3 + ld;
+                        for (int k = 0; k < ncart(la) * ncart(lb); ++k) tk.push_back({cls, make_int4(x, s1, s2, k)});
+                    }
+            std::stable_sort(tk.begin(), tk.end(), [](const std::pair<int, int4>& u, const std::pair<int, int4>& v) {
+                return u.first < v.first;
+            });
+            std::vector<int4> tasks(tk.size());
+            for (size_t i = 0; i < tk.size(); ++i) tasks[i] = tk[i].second;
+            int4* tasks_d = b->upload(tasks, s, "intra tasks");
+            ck(launch_intra_eri(d, tasks_d, (int)tasks.size(), eri, s), "intra eri");
             ck(launch_schwarz(d, eri, sp_Q, ppQ, s), "schwarz");
             b->eric = b->alloc<double>(c->coff_total, "eric");
             ck(launch_coulomb_exchange(d, eri, b->eric, s), "coulomb-exchange");
             ck(cudaStreamSynchronize(s), "intra eri");
             b->release(eri);
+            b->release(tasks_d);
         }
         b->Venv = b->alloc<double>(c->mat_total, "Venv");
         {
@@ -570,11 +619,10 @@ extern "C" fef_status fef_create(const fef_geometry* g, const fef_basis* bs, con
         b->Jenv = b->alloc<double>(c->mat_total, "Jenv");
         b->omega = b->alloc<double>(c->mat_total, "omega");
         ck(cudaMemsetAsync(b->D, 0, sizeof(double) * c->mat_total, s), "D");
-        b->e_J = b->alloc<double>(c->n_pairs, "e_J");
         b->tr_xy = b->alloc<double>(c->n_pairs, "tr");
         b->tr_yx = b->alloc<double>(c->n_pairs, "tr");
-        b->E_pair = b->alloc<double>(c->n_pairs, "E_pair");
-        b->tr_omega = b->alloc<double>(nf, "tr_omega");
+        b->trV = b->alloc<double>(nf, "trV");
+        b->trJ = b->alloc<double>(nf, "trJ");
         b->E_int = b->alloc<double>(nf, "E_int");
         b->E_scf = b->alloc<double>(nf, "E_scf");
         b->E_frag = b->alloc<double>(nf, "E_frag");
@@ -675,7 +723,7 @@ extern "C" fef_status fef_build_fock(fef_ctx* c, const double* D, double* F_out,
     }
     require(c->have_density, FEF_ERR_ARG, "fef_build_fock: no densities given or set");
     clear_flags(c);
-    build_fock_internal(c);
+    build_fock_internal(c, c->opt.precision == FEF_MIXED);
     if (F_out) copy_packed(c, F_out, c->buf->F, on_device, cudaMemcpyDeviceToHost);
     check_device_flags(c, "fef_build_fock");
     float ms = 0.f;
@@ -723,15 +771,20 @@ extern "C" fef_status fef_iterate(fef_ctx* c, int32_t* n_macro_out, double* fina
     {
         float ms0 = 0.f;
         ck(cudaEventElapsedTime(&ms0, c->buf->ev0, c->buf->ev1), "event time");
-        double rec[8] = {0, Et_old, 0, 0, it_max, it_sum, ms0, scf_ms};
-        c->history.insert(c->history.end(), rec, rec + 8);
+        double rec[kHistoryFields] = {0, Et_old, 0, 0, it_max, it_sum, ms0, scf_ms, 0};
+        c->history.insert(c->history.end(), rec, rec + kHistoryFields);
     }
     int k = 0;
     bool conv = false;
     float jms = 0.f;
+    // MIXED: FP32-core incremental builds while |dE| >= mixed_switch, then FP64 builds; convergence is
+    // only declared between two consecutive FP64 energies.
+    bool fp32_phase = (o.precision == FEF_MIXED);
+    bool prev_fp64 = true;
     for (k = 1; k <= o.max_macro; ++k) {
         run_scf(c, true, true);
-        build_fock_internal(c);
+        build_fock_internal(c, fp32_phase);
+        const bool this_fp64 = !c->last_build_fp32;
         read_energies(c, Ex, Et);
         scf_counts(c, it_max, it_sum, scf_ms);
         float ms = 0.f;
@@ -748,15 +801,18 @@ extern "C" fef_status fef_iterate(fef_ctx* c, int32_t* n_macro_out, double* fina
         double dEx = 0;
         for (int x = 0; x < c->n_frag; ++x) dEx = std::max(dEx, std::fabs(Ex[x] - Ex_old[x]));
         {
-            double rec[8] = {(double)k, Et, dE, dEx, it_max, it_sum, (double)ms, scf_ms};
-            c->history.insert(c->history.end(), rec, rec + 8);
+            double rec[kHistoryFields] = {(double)k, Et, dE, dEx, it_max, it_sum, (double)ms, scf_ms,
+                                          this_fp64 ? 0.0 : 1.0};
+            c->history.insert(c->history.end(), rec, rec + kHistoryFields);
         }
         Ex_old = Ex;
         Et_old = Et;
-        if (dE < o.e_tol && dEx < o.e_tol) {
+        if (fp32_phase && dE < o.mixed_switch && dEx < o.mixed_switch) fp32_phase = false;
+        if (this_fp64 && prev_fp64 && dE < o.e_tol && dEx < o.e_tol) {
             conv = true;
             break;
         }
+        prev_fp64 = this_fp64;
     }
     c->jengine_ms = jms;
     if (n_macro_out) *n_macro_out = conv ? k : o.max_macro;
@@ -813,11 +869,11 @@ extern "C" fef_status fef_measure_fma_peak(double* fp64, double* fp32, double* m
 extern "C" fef_status fef_history(const fef_ctx* c, int32_t max_records, double* records, int32_t* n_records)
 {
     if (!c) return FEF_ERR_ARG;
-    int n = (int)(c->history.size() / 8);
+    int n = (int)(c->history.size() / kHistoryFields);
     if (n_records) *n_records = n;
     if (records && max_records > 0) {
         int m = std::min(n, (int)max_records);
-        std::memcpy(records, c->history.data(), sizeof(double) * 8 * m);
+        std::memcpy(records, c->history.data(), sizeof(double) * kHistoryFields * m);
     }
     return FEF_OK;
 }

@@ -11,7 +11,22 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <utility>
+
 namespace fef {
+
+// Compile-time loop: f(std::integral_constant<int, i>) for i = 0..N-1, so that array indices
+// derived from i are constants and the arrays stay in registers.
+template <typename F, int... I>
+__device__ __forceinline__ void static_for_impl(F&& f, std::integer_sequence<int, I...>)
+{
+    (f(std::integral_constant<int, I>{}), ...);
+}
+template <int N, typename F>
+__device__ __forceinline__ void static_for(F&& f)
+{
+    static_for_impl(f, std::make_integer_sequence<int, N>{});
+}
 
 constexpr double kPi = 3.14159265358979323846;
 // sqrt(2 pi^{5/2}): split evenly between bra and ket Hermite densities so that the per-quartet
@@ -24,6 +39,13 @@ constexpr int kMaxLPair = 2 * kMaxL;
 constexpr int kMaxLTot = 2 * kMaxLPair;
 
 // ------------------------------------------------------------------------------------------ Boys
+// FP32 grid-Taylor table for the mixed-precision J-engine: same grid, F_{m+j}(T_k)/j! for
+// j = 0..4 (truncation below 0.025^5/5! ~ 8e-11, far under FP32 resolution), switch to the
+// asymptotic form at T = 25 where the neglected exp(-T) terms are below 1e-10 of F_m.
+constexpr int kBoys32Order = 4;
+constexpr int kBoys32Rows = 502;                  // T up to 25.05
+constexpr float kBoys32Tmax = 25.0f;
+
 // Grid-Taylor table: rows T_k = k h, k = 0..kBoysRows-1; per row, for m = 0..kBoysM-1 a block of
 // kBoysOrder+1 coefficients F_{m+j}(T_k)/j! (j = 0..kBoysOrder), padded to kBoysBlock doubles; the
 // pad slot of block 0 holds T_k.  |T - T_k| <= h/2 = 0.025 gives a truncation error below
@@ -103,6 +125,29 @@ __device__ __forceinline__ void boys_fp64(const double* __restrict__ table, doub
     }
 }
 
+// F_0..F_L at T in FP32 (mixed-precision core).
+template <int L>
+__device__ __forceinline__ void boys_fp32(const float* __restrict__ table, float T, float* F)
+{
+    const int k = (int)(fminf(T, (float)(kBoys32Rows - 1) * (float)kBoysH) * (float)kBoysInvH + 0.5f);
+    if (k < kBoys32Rows - 1) {
+        const float* row = table + (size_t)k * kBoysRowLen;
+        const float d = __ldg(row + kBoys32Order + 3) - T;
+#pragma unroll
+        for (int m = 0; m <= L; ++m) {
+            const float4 c = __ldg(reinterpret_cast<const float4*>(row + m * kBoysBlock));
+            const float c4 = __ldg(row + m * kBoysBlock + 4);
+            F[m] = fmaf(d, fmaf(d, fmaf(d, fmaf(d, c4, c.w), c.z), c.y), c.x);
+        }
+    } else {
+        const float rt = rsqrtf(T);
+        const float half_inv_T = 0.5f * rt * rt;
+        F[0] = (float)kSqrtPiHalf * rt;
+#pragma unroll
+        for (int m = 1; m <= L; ++m) F[m] = F[m - 1] * ((2.0f * m - 1.0f) * half_inv_T);
+    }
+}
+
 __device__ __forceinline__ int boys_row(float Tf)
 {
     float k = fminf(Tf, (float)(kBoysRows - 1) * (float)kBoysH) * (float)kBoysInvH + 0.5f;
@@ -136,30 +181,53 @@ __device__ inline void boys_fp64_rt(const double* __restrict__ table, double T, 
 //   R^{(n)}_{t+1,u,v} = t R^{(n+1)}_{t-1,u,v} + X_PQ R^{(n+1)}_{t,u,v}   (and the same in u, v).
 // Sweeping n from L-1 down to 0 and each level from high to low lets one array hold R^{(n+1)} of the
 // lower levels while R^{(n)} of the higher levels is written.
+namespace detail {
+// One level sweep of md_R at order N, for Hermite index IDX down to 1 (compile-time recursion so that
+// every R index is a constant and R stays in registers).
+template <int IDX, typename Real>
+struct MdRStep {
+    static __device__ __forceinline__ void run(Real* R, Real X, Real Y, Real Z)
+    {
+        constexpr TUV c = htuv(IDX);
+        Real v;
+        if constexpr (c.t > 0) {
+            v = X * R[hidx(c.t - 1, c.u, c.v)];
+            if constexpr (c.t > 1) v = fma(Real(c.t - 1), R[hidx(c.t - 2, c.u, c.v)], v);
+        } else if constexpr (c.u > 0) {
+            v = Y * R[hidx(c.t, c.u - 1, c.v)];
+            if constexpr (c.u > 1) v = fma(Real(c.u - 1), R[hidx(c.t, c.u - 2, c.v)], v);
+        } else {
+            v = Z * R[hidx(c.t, c.u, c.v - 1)];
+            if constexpr (c.v > 1) v = fma(Real(c.v - 1), R[hidx(c.t, c.u, c.v - 2)], v);
+        }
+        R[IDX] = v;
+        MdRStep<IDX - 1, Real>::run(R, X, Y, Z);
+    }
+};
+template <typename Real>
+struct MdRStep<0, Real> {
+    static __device__ __forceinline__ void run(Real*, Real, Real, Real) {}
+};
+template <int L, int N, typename Real>
+struct MdRLevel {
+    static __device__ __forceinline__ void run(Real* R, const Real* base, Real X, Real Y, Real Z)
+    {
+        MdRStep<nh(L - N) - 1, Real>::run(R, X, Y, Z);
+        R[0] = base[N];
+        MdRLevel<L, N - 1, Real>::run(R, base, X, Y, Z);
+    }
+};
+template <int L, typename Real>
+struct MdRLevel<L, -1, Real> {
+    static __device__ __forceinline__ void run(Real*, const Real*, Real, Real, Real) {}
+};
+}  // namespace detail
+
 template <int L, typename Real>
 __device__ __forceinline__ void md_R(Real* R, const Real* base, Real X, Real Y, Real Z)
 {
     R[0] = base[L];
-#pragma unroll
-    for (int n = L - 1; n >= 0; --n) {
-#pragma unroll
-        for (int idx = nh(L - n) - 1; idx >= 1; --idx) {
-            const TUV c = htuv(idx);
-            Real v;
-            if (c.t > 0) {
-                v = X * R[hidx(c.t - 1, c.u, c.v)];
-                if (c.t > 1) v = fma(Real(c.t - 1), R[hidx(c.t - 2, c.u, c.v)], v);
-            } else if (c.u > 0) {
-                v = Y * R[hidx(c.t, c.u - 1, c.v)];
-                if (c.u > 1) v = fma(Real(c.u - 1), R[hidx(c.t, c.u - 2, c.v)], v);
-            } else {
-                v = Z * R[hidx(c.t, c.u, c.v - 1)];
-                if (c.v > 1) v = fma(Real(c.v - 1), R[hidx(c.t, c.u, c.v - 2)], v);
-            }
-            R[idx] = v;
-        }
-        R[0] = base[n];
-    }
+    detail::MdRLevel<L, L - 1, Real>::run(R, base, X, Y, Z);
 }
 
 // Runtime-L R recursion for the non-hot kernels; R has room for nh(L) values, scratch for the

@@ -74,17 +74,32 @@ struct Dev {
     const float* pp_Q[kClasses];
     double* pp_Dh[kClasses];
     double* pp_Jh[kClasses];
+    const float4* pp_Pr[kClasses];   // FP32 (P - anchor of the fragment, p) for the mixed J-engine
+    float* pp_Dh32[kClasses];        // FP32 Hermite density difference D_P - D_P^ref (mixed builds)
     int n_pp[kClasses];
     // fragment pairs
     const int* pair_x;
     const int* pair_y;
     // tables / scratch
     const double* boys;
+    const float* boys32;
     int* err_flag;
 };
 
+// fragment owning shell pair s (frag_sp0 is ascending)
+__device__ inline int frag_of_shellpair(const Dev& d, int s)
+{
+    int lo = 0, hi = d.n_frag - 1;
+    while (lo < hi) {
+        int mid = (lo + hi + 1) / 2;
+        if (d.frag_sp0[mid] <= s) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
 // Host-side context.
 struct Buffers;
+constexpr int kHistoryFields = 9;
 }  // namespace fef
 
 struct fef_ctx {
@@ -104,9 +119,11 @@ struct fef_ctx {
     int64_t class_quartets[25] = {};
     double jengine_ms = 0.0;
     // one record per macro-iteration of the last fef_iterate (index 0: the start densities):
-    // k, E_tot, |dE_tot|, max|dE_x|, max micro-iterations, summed micro-iterations, J-engine ms, SCF ms
+    // k, E_tot, |dE_tot|, max|dE_x|, max micro-iterations, summed micro-iterations, J-engine ms, SCF ms,
+    // 1 if the build used the FP32 core
     std::vector<double> history;
     bool have_density = false;
+    bool last_build_fp32 = false;
     bool energies_valid = false;
     std::string last_error;
 };
@@ -123,9 +140,12 @@ cudaError_t launch_prepare(const Dev& d, const double* xyz_A, double* atom_xyz, 
 cudaError_t launch_boys_table(double* table, cudaStream_t s);
 cudaError_t launch_ao_scale(const Dev& d, double* ao_scale, int n_ao_total, const int* ao_frag, cudaStream_t s);
 cudaError_t launch_prim_pairs(const Dev& d, double4_32a* P[kClasses], float4* Pf[kClasses], double* K[kClasses],
-                              cudaStream_t s);
+                              float4* Pr[kClasses], cudaStream_t s);
+cudaError_t launch_boys_table32(const double* table64, float* table32, cudaStream_t s);
+// Dh32 = float(Dh - Dh_ref) for every class
+cudaError_t launch_delta_density(const Dev& d, double* const Dh_ref[kClasses], cudaStream_t s);
 cudaError_t launch_one_electron(const Dev& d, double* S, double* h, cudaStream_t s);
-cudaError_t launch_intra_eri(const Dev& d, double* eri, int max_l, cudaStream_t s);
+cudaError_t launch_intra_eri(const Dev& d, const int4* tasks, int n_tasks, double* eri, cudaStream_t s);
 cudaError_t launch_schwarz(const Dev& d, const double* eri, double* sp_Q, float* pp_Q[kClasses], cudaStream_t s);
 cudaError_t launch_coulomb_exchange(const Dev& d, const double* eri, double* eric, cudaStream_t s);
 cudaError_t launch_neighbours(const Dev& d, double cutoff_bohr, unsigned char* flags, cudaStream_t s);
@@ -135,13 +155,16 @@ cudaError_t launch_nuclear_repulsion(const Dev& d, double* e_nn_intra, double* e
 cudaError_t launch_orthogonaliser(const Dev& d, const double* S, double* X, int* nmo, double s_min, int max_n,
                                   cudaStream_t s);
 cudaError_t launch_hermite_density(const Dev& d, const double* D, cudaStream_t s);
+// FP64 J-engine (fp32 = 0) on pp_Dh, or the FP32-core J-engine (fp32 = 1) on pp_Dh32; both add
+// into the FP64 accumulators pp_Jh.
 cudaError_t launch_jengine(const Dev& d, const int2* tiles[kClasses][kClasses], const int* n_tiles, double tau,
-                           double* e_pair, int mixed, cudaStream_t s);
+                           int fp32, cudaStream_t s);
 cudaError_t launch_back_transform(const Dev& d, double* J, cudaStream_t s);
 // F = h + C D + V_env + J_env per fragment; E_int[x] = tr[D (h + G/2)] + e_nn[x]; tr_omega[x] = tr[D (V+J)]
+// also trV[x] = tr(D^x V_env^x), trJ[x] = tr(D^x J_env^x)
 cudaError_t launch_fock_energy(const Dev& d, const double* h, const double* Venv, const double* Jenv,
                                const double* eric, const double* D, double* F, double* omega, const double* e_nn,
-                               double* E_int, double* tr_omega, cudaStream_t s);
+                               double* E_int, double* trV, double* trJ, cudaStream_t s);
 cudaError_t launch_count_quartets(const Dev& d, double tau, unsigned long long* count, cudaStream_t s);
 
 struct ScfArgs {
@@ -168,8 +191,9 @@ struct ScfArgs {
 };
 cudaError_t launch_fragment_scf(const Dev& d, const ScfArgs& a, int max_n, cudaStream_t s);
 
-cudaError_t launch_energies(const Dev& d, const double* e_J, const double* tr_xy, const double* tr_yx,
-                            const double* e_nn_pair, const double* E_int, double* E_pair, double* E_frag,
+// E_frag[x] = E_int[x] + (trV[x] + sum_y tr(D^y V^x) + trJ[x] + sum_y E_nn(x,y)) / 2, E_tot = sum E_frag
+cudaError_t launch_energies(const Dev& d, const double* E_int, const double* trV, const double* trJ,
+                            const double* tr_xy, const double* tr_yx, const double* e_nn_pair, double* E_frag,
                             double* E_tot, cudaStream_t s);
 cudaError_t launch_check_finite(const double* a, int64_t n, int* flag, cudaStream_t s);
 

@@ -17,16 +17,6 @@
 namespace fef {
 
 // ------------------------------------------------------------------------------------------ densities
-__device__ inline int frag_of_shellpair(const Dev& d, int s)
-{
-    int lo = 0, hi = d.n_frag - 1;
-    while (lo < hi) {
-        int mid = (lo + hi + 1) / 2;
-        if (d.frag_sp0[mid] <= s) lo = mid; else hi = mid - 1;
-    }
-    return lo;
-}
-
 __global__ void k_hermite_density(Dev d, int L, const double* __restrict__ D)
 {
     int g = blockIdx.x * blockDim.x + threadIdx.x;
@@ -80,14 +70,50 @@ cudaError_t launch_hermite_density(const Dev& d, const double* D, cudaStream_t s
 }
 
 // ------------------------------------------------------------------------------------------ J-engine
+// Both contractions of one primitive quartet with compile-time Hermite indices:
+//   JP[i] += sum_j (-1)^{|j|} R[i + j] DQ[j]                      (field on the bra pair, registers)
+//   QJ[j][k] += (-1)^{|j|} sum_lanes sum_i R[i + j] DP[i]          (field on the ket pair, warp sum)
+template <int NP, int NQ, typename Real>
+__device__ __forceinline__ void hermite_contract(const Real* R, const Real* DP, const Real* DQ, Real* JP,
+                                                 double* __restrict__ QJ, size_t nQ, int k, int lane)
+{
+    static_for<NP>([&](auto I) {
+        constexpr TUV a = htuv(decltype(I)::value);
+        Real acc = JP[decltype(I)::value];
+        static_for<NQ>([&](auto Jc) {
+            constexpr TUV b = htuv(decltype(Jc)::value);
+            constexpr int r = hidx(a.t + b.t, a.u + b.u, a.v + b.v);
+            if constexpr (((b.t + b.u + b.v) & 1) != 0)
+                acc = fma(-R[r], DQ[decltype(Jc)::value], acc);
+            else
+                acc = fma(R[r], DQ[decltype(Jc)::value], acc);
+        });
+        JP[decltype(I)::value] = acc;
+    });
+    Real sq[NQ];
+    static_for<NQ>([&](auto Jc) {
+        constexpr TUV b = htuv(decltype(Jc)::value);
+        Real s = Real(0);
+        static_for<NP>([&](auto I) {
+            constexpr TUV a = htuv(decltype(I)::value);
+            s = fma(R[hidx(a.t + b.t, a.u + b.u, a.v + b.v)], DP[decltype(I)::value], s);
+        });
+        sq[decltype(Jc)::value] = ((b.t + b.u + b.v) & 1) ? -s : s;
+    });
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+        static_for<NQ>([&](auto Jc) { sq[decltype(Jc)::value] += __shfl_xor_sync(0xffffffffu, sq[decltype(Jc)::value], o); });
+    if (lane == 0)
+        static_for<NQ>([&](auto Jc) { atomicAdd(QJ + (size_t)decltype(Jc)::value * nQ + k, (double)sq[decltype(Jc)::value]); });
+}
+
 // One warp per tile = (fragment pair x<y, up to 32 bra primitive pairs of class LP in x) against all
 // ket primitive pairs of class LQ in y.  Lane i owns bra pair P_i: its centre, Hermite density and
 // Hermite field accumulator stay in registers.  Ket data are warp-uniform loads.  The field on the
 // ket pair is reduced across the warp with shuffles and added to global memory by lane 0.
 // Shell quartets with Q_ab Q_cd < tau contribute nothing (Schwarz screening at shell level).
 template <int LP, int LQ>
-__global__ void __launch_bounds__(128) k_jengine(Dev d, const int2* __restrict__ tiles, int n_tiles, float tau,
-                                                  double* __restrict__ e_pair)
+__global__ void __launch_bounds__(128) k_jengine(Dev d, const int2* __restrict__ tiles, int n_tiles, float tau)
 {
     constexpr int NP = nh(LP), NQ = nh(LQ), L = LP + LQ, NR = nh(LP + LQ);
     const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -144,60 +170,132 @@ __global__ void __launch_bounds__(128) k_jengine(Dev d, const int2* __restrict__
         }
         double R[NR];
         md_R<L, double>(R, base, X, Y, Z);
-#pragma unroll
-        for (int i = 0; i < NP; ++i) {
-            const TUV a = htuv(i);
-            double acc = JP[i];
-#pragma unroll
-            for (int j = 0; j < NQ; ++j) {
-                const TUV b = htuv(j);
-                const double rr = R[hidx(a.t + b.t, a.u + b.u, a.v + b.v)];
-                acc = ((b.t + b.u + b.v) & 1) ? fma(-rr, DQ[j], acc) : fma(rr, DQ[j], acc);
-            }
-            JP[i] = acc;
-        }
-#pragma unroll
-        for (int j = 0; j < NQ; ++j) {
-            const TUV b = htuv(j);
-            double s = 0.0;
-#pragma unroll
-            for (int i = 0; i < NP; ++i) {
-                const TUV a = htuv(i);
-                s = fma(R[hidx(a.t + b.t, a.u + b.u, a.v + b.v)], DP[i], s);
-            }
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-            if (lane == 0) atomicAdd(QJ + (size_t)j * nQ + k, ((b.t + b.u + b.v) & 1) ? -s : s);
-        }
+        hermite_contract<NP, NQ, double>(R, DP, DQ, JP, QJ, (size_t)nQ, k, lane);
     }
-    double e = 0.0;
+    if (valid) {
+#pragma unroll
+        for (int i = 0; i < NP; ++i) atomicAdd(d.pp_Jh[LP] + (size_t)i * nP + Pg, JP[i]);
+    }
+}
+
+// Mixed-precision core: the same contraction on the FP32 Hermite density difference
+// Dh32 = D_P - D_P^ref, with FP32 geometry (centres relative to each fragment's first atom plus the
+// FP64-computed anchor offset), FP32 Boys, R recursion and contractions.  The bra field is flushed to
+// FP64 registers every 16 ket pairs and all global accumulation is FP64 (atomics on pp_Jh).
+template <int LP, int LQ>
+__global__ void __launch_bounds__(128) k_jengine32(Dev d, const int2* __restrict__ tiles, int n_tiles, float tau)
+{
+    constexpr int NP = nh(LP), NQ = nh(LQ), L = LP + LQ, NR = nh(LP + LQ);
+    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (warp >= n_tiles) return;
+    const int2 tl = tiles[warp];
+    const int x = d.pair_x[tl.x], y = d.pair_y[tl.x];
+    const double* ax = d.atom_xyz + 3 * d.frag_atom0[x];
+    const double* ay = d.atom_xyz + 3 * d.frag_atom0[y];
+    const float ox = (float)(ax[0] - ay[0]), oy = (float)(ax[1] - ay[1]), oz = (float)(ax[2] - ay[2]);
+    const int bra_end = d.frag_pp0[x * kClasses + LP] + d.frag_npp[x * kClasses + LP];
+    const int Pg = tl.y + lane;
+    const bool valid = Pg < bra_end;
+    const int Pl = valid ? Pg : tl.y;
+    const int nP = d.n_pp[LP], nQ = d.n_pp[LQ];
+    const float4 Pr = d.pp_Pr[LP][Pl];
+    const float qP = valid ? d.pp_Q[LP][Pl] : 0.0f;
+    float DP[NP], JP[NP];
+    double JP64[NP];
 #pragma unroll
     for (int i = 0; i < NP; ++i) {
-        if (valid) atomicAdd(d.pp_Jh[LP] + (size_t)i * nP + Pg, JP[i]);
-        e = fma(DP[i], JP[i], e);
+        DP[i] = valid ? d.pp_Dh32[LP][(size_t)i * nP + Pl] : 0.0f;
+        JP[i] = 0.0f;
+        JP64[i] = 0.0;
     }
+    const int k0 = d.frag_pp0[y * kClasses + LQ];
+    const int k1 = k0 + d.frag_npp[y * kClasses + LQ];
+    const float4* __restrict__ QPr = d.pp_Pr[LQ];
+    const float* __restrict__ QQ = d.pp_Q[LQ];
+    const float* __restrict__ QD = d.pp_Dh32[LQ];
+    double* __restrict__ QJ = d.pp_Jh[LQ];
+    int since_flush = 0;
+    for (int k = k0; k < k1; ++k) {
+        const float qQ = __ldg(QQ + k);
+        const bool keep = qP * qQ >= tau;
+        if (!__any_sync(0xffffffffu, keep)) continue;
+        const float4 Qr = __ldg(QPr + k);
+        float DQ[NQ];
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) e += __shfl_xor_sync(0xffffffffu, e, o);
-    if (lane == 0) atomicAdd(e_pair + tl.x, e);
+        for (int j = 0; j < NQ; ++j) DQ[j] = __ldg(QD + (size_t)j * nQ + k);
+        const float X = (Pr.x - Qr.x) + ox, Y = (Pr.y - Qr.y) + oy, Z = (Pr.z - Qr.z) + oz;
+        const float R2 = fmaf(X, X, fmaf(Y, Y, Z * Z));
+        const float r = rsqrtf(Pr.w + Qr.w);
+        const float alpha = Pr.w * Qr.w * (r * r);
+        float F[L + 1];
+        boys_fp32<L>(d.boys32, alpha * R2, F);
+        float base[L + 1];
+        float pre = keep ? r : 0.0f;
+        const float m2a = -2.0f * alpha;
+#pragma unroll
+        for (int n = 0; n <= L; ++n) {
+            base[n] = pre * F[n];
+            pre *= m2a;
+        }
+        float R[NR];
+        md_R<L, float>(R, base, X, Y, Z);
+        hermite_contract<NP, NQ, float>(R, DP, DQ, JP, QJ, (size_t)nQ, k, lane);
+        if (++since_flush == 16) {
+            since_flush = 0;
+#pragma unroll
+            for (int i = 0; i < NP; ++i) {
+                JP64[i] += (double)JP[i];
+                JP[i] = 0.0f;
+            }
+        }
+    }
+    if (valid) {
+#pragma unroll
+        for (int i = 0; i < NP; ++i) atomicAdd(d.pp_Jh[LP] + (size_t)i * nP + Pg, JP64[i] + (double)JP[i]);
+    }
 }
 
 template <int LP, int LQ>
-static void launch_one(const Dev& d, const int2* t, int n, float tau, double* e, cudaStream_t s)
+static void launch_one(const Dev& d, const int2* t, int n, float tau, int fp32, cudaStream_t s)
 {
     if (n <= 0) return;
     const int warps_per_block = 4;
-    k_jengine<LP, LQ><<<(n + warps_per_block - 1) / warps_per_block, 32 * warps_per_block, 0, s>>>(d, t, n, tau, e);
+    const int blocks = (n + warps_per_block - 1) / warps_per_block;
+    if (fp32)
+        k_jengine32<LP, LQ><<<blocks, 32 * warps_per_block, 0, s>>>(d, t, n, tau);
+    else
+        k_jengine<LP, LQ><<<blocks, 32 * warps_per_block, 0, s>>>(d, t, n, tau);
     note_launches(1);
 }
 
 cudaError_t launch_jengine(const Dev& d, const int2* tiles[kClasses][kClasses], const int* n_tiles, double tau,
-                           double* e_pair, int /*mixed*/, cudaStream_t s)
+                           int fp32, cudaStream_t s)
 {
     const float ft = (float)tau;
-#define FEF_J(LP, LQ) launch_one<LP, LQ>(d, tiles[LP][LQ], n_tiles[LP * kClasses + LQ], ft, e_pair, s)
+#define FEF_J(LP, LQ) launch_one<LP, LQ>(d, tiles[LP][LQ], n_tiles[LP * kClasses + LQ], ft, fp32, s)
     FEF_J(0, 0); FEF_J(0, 1); FEF_J(0, 2); FEF_J(1, 0); FEF_J(1, 1); FEF_J(1, 2); FEF_J(2, 0); FEF_J(2, 1);
     FEF_J(2, 2);
 #undef FEF_J
+    return cudaGetLastError();
+}
+
+// Dh32 = float(Dh - Dh_ref): the Hermite density of D - D_ref (linear in D).
+__global__ void k_delta_density(const double* __restrict__ Dh, const double* __restrict__ ref, float* out, size_t n)
+{
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+        out[i] = (float)(Dh[i] - ref[i]);
+}
+
+cudaError_t launch_delta_density(const Dev& d, double* const Dh_ref[kClasses], cudaStream_t s)
+{
+    for (int L = 0; L < kClasses; ++L) {
+        size_t n = (size_t)nh(L) * d.n_pp[L];
+        if (n == 0) continue;
+        k_delta_density<<<(unsigned)std::min<size_t>((n + 255) / 256, 2048), 256, 0, s>>>(d.pp_Dh[L], Dh_ref[L],
+                                                                                       d.pp_Dh32[L], n);
+        note_launches(1);
+    }
     return cudaGetLastError();
 }
 
@@ -262,7 +360,7 @@ cudaError_t launch_back_transform(const Dev& d, double* J, cudaStream_t s)
 // (omega = V_env + J_env).  One block per fragment; thread per packed row pq = (mu <= nu).
 __global__ void k_fock_assemble(Dev d, const double* h, const double* Venv, const double* Jenv, const double* eric,
                                 const double* D, double* F, double* omega, const double* e_nn, double* E_int,
-                                double* tr_omega)
+                                double* trV, double* trJ)
 {
     int x = blockIdx.x;
     int n = d.frag_nao[x];
@@ -276,7 +374,7 @@ __global__ void k_fock_assemble(Dev d, const double* h, const double* Venv, cons
         dpk[rs] = Dx[la * n + la + r];
     }
     __syncthreads();
-    double eint = 0.0, eom = 0.0;
+    double eint = 0.0, ev = 0.0, ej = 0.0;
     for (int pq = threadIdx.x; pq < np; pq += blockDim.x) {
         int mu = 0, r = pq;
         while (r >= n - mu) { r -= n - mu; ++mu; }
@@ -291,68 +389,73 @@ __global__ void k_fock_assemble(Dev d, const double* h, const double* Venv, cons
             if (omega) omega[o] = om;
         }
         int64_t o = d.frag_moff[x] + mu * n + nu;
-        double om = (Venv ? Venv[o] : 0.0) + (Jenv ? Jenv[o] : 0.0);
-        eint += w * Dx[mu * n + nu] * (h[o] + 0.5 * g);
-        eom += w * Dx[mu * n + nu] * om;
+        const double dw = w * Dx[mu * n + nu];
+        eint += dw * (h[o] + 0.5 * g);
+        ev += dw * (Venv ? Venv[o] : 0.0);
+        ej += dw * (Jenv ? Jenv[o] : 0.0);
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
         eint += __shfl_xor_sync(0xffffffffu, eint, o);
-        eom += __shfl_xor_sync(0xffffffffu, eom, o);
+        ev += __shfl_xor_sync(0xffffffffu, ev, o);
+        ej += __shfl_xor_sync(0xffffffffu, ej, o);
     }
-    __shared__ double r1[32], r2[32];
+    __shared__ double r1[32], r2[32], r3[32];
     int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
     if (lane == 0) {
         r1[warp] = eint;
-        r2[warp] = eom;
+        r2[warp] = ev;
+        r3[warp] = ej;
     }
     __syncthreads();
     if (threadIdx.x == 0) {
-        double a = 0.0, b = 0.0;
+        double a = 0.0, b = 0.0, c = 0.0;
         for (int w = 0; w < nw; ++w) {
             a += r1[w];
             b += r2[w];
+            c += r3[w];
         }
         if (E_int) E_int[x] = a + e_nn[x];
-        if (tr_omega) tr_omega[x] = b;
+        if (trV) trV[x] = b;
+        if (trJ) trJ[x] = c;
     }
 }
 
 cudaError_t launch_fock_energy(const Dev& d, const double* h, const double* Venv, const double* Jenv,
                                const double* eric, const double* D, double* F, double* omega, const double* e_nn,
-                               double* E_int, double* tr_omega, cudaStream_t s)
+                               double* E_int, double* trV, double* trJ, cudaStream_t s)
 {
     size_t smem = sizeof(double) * (size_t)d.max_nao * (d.max_nao + 1) / 2;
-    k_fock_assemble<<<d.n_frag, 256, smem, s>>>(d, h, Venv, Jenv, eric, D, F, omega, e_nn, E_int, tr_omega);
+    k_fock_assemble<<<d.n_frag, 256, smem, s>>>(d, h, Venv, Jenv, eric, D, F, omega, e_nn, E_int, trV, trJ);
     note_launches(1);
     return cudaGetLastError();
 }
 
 // ------------------------------------------------------------------------------------------ energies
-// E_xy = tr[D^x V^y] + tr[D^y V^x] + tr[D^x J[D^y]] + E_nn(x,y) per pair; E_frag[x] = E_int[x] +
-// (1/2) sum_{y in N(x)} E_xy; E_total = sum_x E_int + sum_pairs E_xy (one block, fixed order).
-__global__ void k_pair_energy(Dev d, const double* e_J, const double* tr_xy, const double* tr_yx, const double* e_nn,
-                              double* E_pair)
-{
-    int p = blockIdx.x * blockDim.x + threadIdx.x;
-    if (p < d.n_pairs) E_pair[p] = tr_xy[p] + tr_yx[p] + e_J[p] + e_nn[p];
-}
-
-__global__ void k_frag_energy(Dev d, const double* E_int, const double* E_pair, double* E_frag)
+// Pair energy E_xy = tr[D^x V^y] + tr[D^y V^x] + tr[D^x J[D^y]] + E_nn(x,y).  Summed over the
+// neighbours y of x, sum_y tr[D^x V^y] = tr[D^x V_env^x] and sum_y tr[D^x J[D^y]] = tr[D^x J_env^x]
+// (the accumulated fields), so only the attraction of x's nuclei on each neighbour's electrons is
+// needed per pair:
+//   E_frag[x] = E_int[x] + (1/2) (tr[D^x V_env] + sum_y tr[D^y V^x] + tr[D^x J_env] + sum_y E_nn(x,y)),
+//   E_total = sum_x E_frag[x] = sum_x E_int[x] + sum_{pairs} E_xy.
+__global__ void k_frag_energy(Dev d, const double* E_int, const double* trV, const double* trJ, const double* tr_xy,
+                              const double* tr_yx, const double* e_nn, double* E_frag)
 {
     int x = blockIdx.x * blockDim.x + threadIdx.x;
     if (x >= d.n_frag) return;
-    double e = 0.0;
-    for (int c = d.frag_nbr0[x]; c < d.frag_nbr0[x + 1]; ++c) e += E_pair[d.nbr_pair[c]];
+    double e = trV[x] + trJ[x];
+    for (int c = d.frag_nbr0[x]; c < d.frag_nbr0[x + 1]; ++c) {
+        int p = d.nbr_pair[c];
+        e += (d.pair_x[p] == x ? tr_yx[p] : tr_xy[p]) + e_nn[p];
+    }
     E_frag[x] = E_int[x] + 0.5 * e;
 }
 
-__global__ void k_total_energy(Dev d, const double* E_int, const double* E_pair, double* E_tot)
+__global__ void k_total_energy(Dev d, const double* E_frag, double* E_tot)
 {
     __shared__ double red[256];
     double a = 0.0;
-    for (int i = threadIdx.x; i < d.n_frag; i += blockDim.x) a += E_int[i];
-    for (int i = threadIdx.x; i < d.n_pairs; i += blockDim.x) a += E_pair[i];
+    for (int i = threadIdx.x; i < d.n_frag; i += blockDim.x) a += E_frag[i];
     red[threadIdx.x] = a;
     __syncthreads();
     for (int s = blockDim.x / 2; s > 0; s >>= 1) {
@@ -362,17 +465,13 @@ __global__ void k_total_energy(Dev d, const double* E_int, const double* E_pair,
     if (threadIdx.x == 0) *E_tot = red[0];
 }
 
-cudaError_t launch_energies(const Dev& d, const double* e_J, const double* tr_xy, const double* tr_yx,
-                            const double* e_nn_pair, const double* E_int, double* E_pair, double* E_frag,
+cudaError_t launch_energies(const Dev& d, const double* E_int, const double* trV, const double* trJ,
+                            const double* tr_xy, const double* tr_yx, const double* e_nn_pair, double* E_frag,
                             double* E_tot, cudaStream_t s)
 {
-    if (d.n_pairs > 0) {
-        k_pair_energy<<<(d.n_pairs + 255) / 256, 256, 0, s>>>(d, e_J, tr_xy, tr_yx, e_nn_pair, E_pair);
-        note_launches(1);
-    }
-    k_frag_energy<<<(d.n_frag + 255) / 256, 256, 0, s>>>(d, E_int, E_pair, E_frag);
+    k_frag_energy<<<(d.n_frag + 255) / 256, 256, 0, s>>>(d, E_int, trV, trJ, tr_xy, tr_yx, e_nn_pair, E_frag);
     note_launches(1);
-    k_total_energy<<<1, 256, 0, s>>>(d, E_int, E_pair, E_tot);
+    k_total_energy<<<1, 256, 0, s>>>(d, E_frag, E_tot);
     note_launches(1);
     return cudaGetLastError();
 }

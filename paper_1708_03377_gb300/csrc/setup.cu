@@ -70,6 +70,39 @@ cudaError_t launch_boys_table(double* table, cudaStream_t s)
     return cudaGetLastError();
 }
 
+// FP32 table for the mixed-precision core, from the FP64 table: row k, block m holds F_{m+j}(T_k)/j!
+// (j = 0..4); F_n for n <= 8 is block n coefficient 0, for n > 8 block 8 coefficient n-8 times (n-8)!.
+__global__ void k_boys_table32(const double* t64, float* t32)
+{
+    int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= kBoys32Rows) return;
+    const double* row = t64 + (size_t)k * kBoysRowLen;
+    double F[kBoysM + kBoys32Order];
+    for (int n = 0; n < kBoysM; ++n) F[n] = row[n * kBoysBlock];
+    double fact = 1.0;
+    for (int j = 1; j <= kBoys32Order; ++j) {
+        fact *= j;
+        F[kBoysM - 1 + j] = row[(kBoysM - 1) * kBoysBlock + j] * fact;
+    }
+    float* out = t32 + (size_t)k * kBoysRowLen;
+    for (int m = 0; m < kBoysM; ++m) {
+        double f = 1.0;
+        for (int j = 0; j <= kBoys32Order; ++j) {
+            if (j > 0) f *= j;
+            out[m * kBoysBlock + j] = (float)(F[m + j] / f);
+        }
+        for (int j = kBoys32Order + 1; j < kBoysBlock; ++j) out[m * kBoysBlock + j] = 0.0f;
+    }
+    out[kBoys32Order + 3] = (float)row[kBoysOrder + 1];  // T_k
+}
+
+cudaError_t launch_boys_table32(const double* table64, float* table32, cudaStream_t s)
+{
+    k_boys_table32<<<(kBoys32Rows + 127) / 128, 128, 0, s>>>(table64, table32);
+    note_launches(1);
+    return cudaGetLastError();
+}
+
 // ------------------------------------------------------------------------------------------ AO scale
 // Raw self-overlap of contracted AO (lx,ly,lz): sum_ij c_i c_j (pi/p)^{3/2} prod_d E^{l_d l_d}_0 with
 // both primitives on one centre (X_PA = X_PB = 0); the AO scale makes it 1.
@@ -105,7 +138,7 @@ cudaError_t launch_ao_scale(const Dev& d, double* ao_scale, int n_ao_total, cons
 
 // ------------------------------------------------------------------------------------------ prim pairs
 // P = (a A + b B)/p, p = a + b, K = c_i c_j exp(-a b/p |AB|^2), for every primitive pair.
-__global__ void k_prim_pairs(Dev d, int L, double4_32a* P, float4* Pf, double* K)
+__global__ void k_prim_pairs(Dev d, int L, double4_32a* P, float4* Pf, double* K, float4* Pr)
 {
     int g = blockIdx.x * blockDim.x + threadIdx.x;
     if (g >= d.n_pp[L]) return;
@@ -122,15 +155,17 @@ __global__ void k_prim_pairs(Dev d, int L, double4_32a* P, float4* Pf, double* K
     }
     P[g] = make_double4_32a(Pc[0], Pc[1], Pc[2], p);
     Pf[g] = make_float4((float)Pc[0], (float)Pc[1], (float)Pc[2], (float)p);
+    const double* anc = d.atom_xyz + 3 * d.frag_atom0[frag_of_shellpair(d, sp)];
+    Pr[g] = make_float4((float)(Pc[0] - anc[0]), (float)(Pc[1] - anc[1]), (float)(Pc[2] - anc[2]), (float)p);
     K[g] = d.p_coef[pa] * d.p_coef[pb] * exp(-a * b / p * R2);
 }
 
 cudaError_t launch_prim_pairs(const Dev& d, double4_32a* P[kClasses], float4* Pf[kClasses], double* K[kClasses],
-                              cudaStream_t s)
+                              float4* Pr[kClasses], cudaStream_t s)
 {
     for (int L = 0; L < kClasses; ++L)
         if (d.n_pp[L] > 0) {
-            k_prim_pairs<<<(d.n_pp[L] + 127) / 128, 128, 0, s>>>(d, L, P[L], Pf[L], K[L]);
+            k_prim_pairs<<<(d.n_pp[L] + 127) / 128, 128, 0, s>>>(d, L, P[L], Pf[L], K[L], Pr[L]);
             note_launches(1);
         }
     return cudaGetLastError();
@@ -432,127 +467,124 @@ cudaError_t launch_nuclear_repulsion(const Dev& d, double* e_nn_intra, double* e
 }
 
 // ------------------------------------------------------------------------------------------ intra ERIs
-// One thread per (x, shell pair ab, shell pair cd) of the same fragment (a <= b, c <= d): the
-// contracted block (ab|cd) by McMurchie-Davidson,
+// One thread per task = (fragment x, shell pairs s1 <= s2 of x, one bra component mu nu of s1):
+// the row (mu nu|lambda sigma) for all lambda sigma of s2 by McMurchie-Davidson,
 //   (mu nu|lambda sigma) = sum_{PQ} 2 pi^{5/2}/(p q sqrt(p+q)) sum_{tuv,t'u'v'} E^{mu nu}_{tuv}
 //                          (-1)^{t'+u'+v'} E^{lambda sigma}_{t'u'v'} R_{t+t',u+u',v+v'}(alpha, PQ),
-// written to every position of the full n^4 tensor that the block covers (mu nu, nu mu x
-// lambda sigma, sigma lambda).  NB is the per-thread block capacity (ncart(lmax)^4).
-template <int NB>
-__global__ void k_intra_eri(Dev d, double* eri)
+// written to the 8 positions of the full n^4 tensor it covers (bra-ket and index symmetry).  Tasks
+// are sorted by angular-momentum class so that the threads of a warp follow the same path.
+__global__ void k_intra_eri(Dev d, const int4* __restrict__ tasks, int n_tasks, double* eri)
 {
-    int x = blockIdx.y;
-    int sp0 = d.frag_sp0[x], nsp = d.frag_sp0[x + 1] - sp0;
-    int n = d.frag_nao[x];
-    double* out = eri + d.frag_eoff[x];
-    for (int w = blockIdx.x * blockDim.x + threadIdx.x; w < nsp * nsp; w += gridDim.x * blockDim.x) {
-        int s1 = sp0 + w / nsp, s2 = sp0 + w % nsp;
-        int sa = d.sp_a[s1], sb = d.sp_b[s1], sc = d.sp_a[s2], sd = d.sp_b[s2];
-        int la = d.sh_l[sa], lb = d.sh_l[sb], lc = d.sh_l[sc], ld = d.sh_l[sd];
-        int na = ncart(la), nb = ncart(lb), nc = ncart(lc), nd = ncart(ld);
-        int L = la + lb + lc + ld;
-        double blk[NB];
-        for (int k = 0; k < na * nb * nc * nd; ++k) blk[k] = 0.0;
-        const double *A = d.atom_xyz + 3 * d.sh_atom[sa], *B = d.atom_xyz + 3 * d.sh_atom[sb];
-        const double *C = d.atom_xyz + 3 * d.sh_atom[sc], *Dc = d.atom_xyz + 3 * d.sh_atom[sd];
-        double AB2 = 0, CD2 = 0;
-        for (int k = 0; k < 3; ++k) {
-            AB2 += (A[k] - B[k]) * (A[k] - B[k]);
-            CD2 += (C[k] - Dc[k]) * (C[k] - Dc[k]);
+    int w = blockIdx.x * blockDim.x + threadIdx.x;
+    if (w >= n_tasks) return;
+    const int4 tk = tasks[w];
+    const int x = tk.x, s1 = tk.y, s2 = tk.z, kb = tk.w;
+    const int sa = d.sp_a[s1], sb = d.sp_b[s1], sc = d.sp_a[s2], sd = d.sp_b[s2];
+    const int la = d.sh_l[sa], lb = d.sh_l[sb], lc = d.sh_l[sc], ld = d.sh_l[sd];
+    const int nc = ncart(lc), nd = ncart(ld);
+    const int L = la + lb + lc + ld;
+    int ax, ay, az, bx, by, bz;
+    cart_of(la, kb / ncart(lb), ax, ay, az);
+    cart_of(lb, kb % ncart(lb), bx, by, bz);
+    double out[36];
+    for (int k = 0; k < nc * nd; ++k) out[k] = 0.0;
+    const double *A = d.atom_xyz + 3 * d.sh_atom[sa], *B = d.atom_xyz + 3 * d.sh_atom[sb];
+    const double *C = d.atom_xyz + 3 * d.sh_atom[sc], *Dc = d.atom_xyz + 3 * d.sh_atom[sd];
+    double AB2 = 0, CD2 = 0;
+    for (int k = 0; k < 3; ++k) {
+        AB2 += (A[k] - B[k]) * (A[k] - B[k]);
+        CD2 += (C[k] - Dc[k]) * (C[k] - Dc[k]);
+    }
+    int kc[36][3];
+    for (int ic = 0; ic < nc; ++ic)
+        for (int id = 0; id < nd; ++id) {
+            int cx, cy, cz, dx, dy, dz;
+            cart_of(lc, ic, cx, cy, cz);
+            cart_of(ld, id, dx, dy, dz);
+            kc[ic * nd + id][0] = cx * 8 + dx;  // packed (c, d) exponent pairs per direction
+            kc[ic * nd + id][1] = cy * 8 + dy;
+            kc[ic * nd + id][2] = cz * 8 + dz;
         }
-        for (int i = 0; i < d.sh_np[sa]; ++i)
-            for (int j = 0; j < d.sh_np[sb]; ++j) {
-                double a = d.p_exp[d.sh_p0[sa] + i], b = d.p_exp[d.sh_p0[sb] + j], p = a + b;
-                double Kab = d.p_coef[d.sh_p0[sa] + i] * d.p_coef[d.sh_p0[sb] + j] * exp(-a * b / p * AB2);
-                double P[3], Eb[3][3][3][5];
-                for (int k = 0; k < 3; ++k) {
-                    P[k] = (a * A[k] + b * B[k]) / p;
-                    md_E1(la, lb, p, P[k] - A[k], P[k] - B[k], Eb[k]);
-                }
-                for (int k2 = 0; k2 < d.sh_np[sc]; ++k2)
-                    for (int l2 = 0; l2 < d.sh_np[sd]; ++l2) {
-                        double c = d.p_exp[d.sh_p0[sc] + k2], e = d.p_exp[d.sh_p0[sd] + l2], q = c + e;
-                        double Kcd = d.p_coef[d.sh_p0[sc] + k2] * d.p_coef[d.sh_p0[sd] + l2] * exp(-c * e / q * CD2);
-                        double Q[3], Ek[3][3][3][5];
-                        for (int k = 0; k < 3; ++k) {
-                            Q[k] = (c * C[k] + e * Dc[k]) / q;
-                            md_E1(lc, ld, q, Q[k] - C[k], Q[k] - Dc[k], Ek[k]);
-                        }
-                        double alpha = p * q / (p + q);
-                        double X = P[0] - Q[0], Y = P[1] - Q[1], Z = P[2] - Q[2];
-                        double F[kMaxLTot + 1], base[kMaxLTot + 1], R[nh(kMaxLTot)];
-                        boys_fp64_rt(d.boys, alpha * (X * X + Y * Y + Z * Z), L, F);
-                        double pre = 2.0 * pow(kPi, 2.5) / (p * q * sqrt(p + q)) * Kab * Kcd;
-                        for (int m = 0; m <= L; ++m) {
-                            base[m] = pre * F[m];
-                            pre *= -2.0 * alpha;
-                        }
-                        md_R_rt(L, R, base, X, Y, Z);
-                        int kk = 0;
-                        for (int ia = 0; ia < na; ++ia) {
-                            int ax, ay, az;
-                            cart_of(la, ia, ax, ay, az);
-                            for (int ib = 0; ib < nb; ++ib) {
-                                int bx, by, bz;
-                                cart_of(lb, ib, bx, by, bz);
-                                for (int ic = 0; ic < nc; ++ic) {
-                                    int cx, cy, cz;
-                                    cart_of(lc, ic, cx, cy, cz);
-                                    for (int id = 0; id < nd; ++id, ++kk) {
-                                        int dx, dy, dz;
-                                        cart_of(ld, id, dx, dy, dz);
-                                        double v = 0.0;
-                                        for (int t = 0; t <= ax + bx; ++t)
-                                            for (int u = 0; u <= ay + by; ++u)
-                                                for (int vv = 0; vv <= az + bz; ++vv) {
-                                                    double eb = Eb[0][ax][bx][t] * Eb[1][ay][by][u] * Eb[2][az][bz][vv];
-                                                    double s = 0.0;
-                                                    for (int t2 = 0; t2 <= cx + dx; ++t2)
-                                                        for (int u2 = 0; u2 <= cy + dy; ++u2)
-                                                            for (int v2 = 0; v2 <= cz + dz; ++v2) {
-                                                                double ek = Ek[0][cx][dx][t2] * Ek[1][cy][dy][u2] *
-                                                                            Ek[2][cz][dz][v2];
-                                                                double r = R[hidx(t + t2, u + u2, vv + v2)];
-                                                                s += ((t2 + u2 + v2) & 1) ? -ek * r : ek * r;
-                                                            }
-                                                    v += eb * s;
-                                                }
-                                        blk[kk] += v;
-                                    }
-                                }
-                            }
-                        }
-                    }
+    for (int i = 0; i < d.sh_np[sa]; ++i)
+        for (int j = 0; j < d.sh_np[sb]; ++j) {
+            double a = d.p_exp[d.sh_p0[sa] + i], b = d.p_exp[d.sh_p0[sb] + j], p = a + b;
+            double Kab = d.p_coef[d.sh_p0[sa] + i] * d.p_coef[d.sh_p0[sb] + j] * exp(-a * b / p * AB2);
+            double P[3], Eb[3][5];
+            for (int k = 0; k < 3; ++k) P[k] = (a * A[k] + b * B[k]) / p;
+            {
+                double E[3][3][5];
+                md_E1(ax, bx, p, P[0] - A[0], P[0] - B[0], E);
+                for (int t = 0; t < 5; ++t) Eb[0][t] = t <= ax + bx ? E[ax][bx][t] : 0.0;
+                md_E1(ay, by, p, P[1] - A[1], P[1] - B[1], E);
+                for (int t = 0; t < 5; ++t) Eb[1][t] = t <= ay + by ? E[ay][by][t] : 0.0;
+                md_E1(az, bz, p, P[2] - A[2], P[2] - B[2], E);
+                for (int t = 0; t < 5; ++t) Eb[2][t] = t <= az + bz ? E[az][bz][t] : 0.0;
             }
-        int ga = d.sh_ao[sa], gb = d.sh_ao[sb], gc = d.sh_ao[sc], gd = d.sh_ao[sd];
-        int ao0 = d.frag_ao0[x];
-        int kk = 0;
-        for (int ia = 0; ia < na; ++ia)
-            for (int ib = 0; ib < nb; ++ib)
-                for (int ic = 0; ic < nc; ++ic)
-                    for (int id = 0; id < nd; ++id, ++kk) {
-                        int mu = ga + ia, nu = gb + ib, la_ = gc + ic, si = gd + id;
-                        double v = blk[kk] * d.ao_scale[ao0 + mu] * d.ao_scale[ao0 + nu] * d.ao_scale[ao0 + la_] *
-                                   d.ao_scale[ao0 + si];
-                        size_t n2 = (size_t)n * n;
-                        out[((size_t)mu * n + nu) * n2 + (size_t)la_ * n + si] = v;
-                        out[((size_t)nu * n + mu) * n2 + (size_t)la_ * n + si] = v;
-                        out[((size_t)mu * n + nu) * n2 + (size_t)si * n + la_] = v;
-                        out[((size_t)nu * n + mu) * n2 + (size_t)si * n + la_] = v;
+            for (int k2 = 0; k2 < d.sh_np[sc]; ++k2)
+                for (int l2 = 0; l2 < d.sh_np[sd]; ++l2) {
+                    double c = d.p_exp[d.sh_p0[sc] + k2], e = d.p_exp[d.sh_p0[sd] + l2], q = c + e;
+                    double Kcd = d.p_coef[d.sh_p0[sc] + k2] * d.p_coef[d.sh_p0[sd] + l2] * exp(-c * e / q * CD2);
+                    double Q[3], Ek[3][3][3][5];
+                    for (int k = 0; k < 3; ++k) {
+                        Q[k] = (c * C[k] + e * Dc[k]) / q;
+                        md_E1(lc, ld, q, Q[k] - C[k], Q[k] - Dc[k], Ek[k]);
                     }
+                    double alpha = p * q / (p + q);
+                    double X = P[0] - Q[0], Y = P[1] - Q[1], Z = P[2] - Q[2];
+                    double F[kMaxLTot + 1], base[kMaxLTot + 1], R[nh(kMaxLTot)];
+                    boys_fp64_rt(d.boys, alpha * (X * X + Y * Y + Z * Z), L, F);
+                    double pre = 2.0 * pow(kPi, 2.5) / (p * q * sqrt(p + q)) * Kab * Kcd;
+                    for (int m = 0; m <= L; ++m) {
+                        base[m] = pre * F[m];
+                        pre *= -2.0 * alpha;
+                    }
+                    md_R_rt(L, R, base, X, Y, Z);
+                    // Ybra[t'u'v'] = sum_tuv Eb R[t+t', ...]
+                    double Yb[nh(2 * kMaxL)];
+                    const int LCD = lc + ld;
+                    for (int h = 0; h < nh(LCD); ++h) {
+                        TUV c2 = htuv(h);
+                        double y = 0.0;
+                        for (int t = 0; t <= ax + bx; ++t)
+                            for (int u = 0; u <= ay + by; ++u)
+                                for (int v = 0; v <= az + bz; ++v)
+                                    y += Eb[0][t] * Eb[1][u] * Eb[2][v] * R[hidx(t + c2.t, u + c2.u, v + c2.v)];
+                        Yb[h] = ((c2.t + c2.u + c2.v) & 1) ? -y : y;
+                    }
+                    for (int k = 0; k < nc * nd; ++k) {
+                        int cx = kc[k][0] >> 3, dx = kc[k][0] & 7, cy = kc[k][1] >> 3, dy = kc[k][1] & 7;
+                        int cz = kc[k][2] >> 3, dz = kc[k][2] & 7;
+                        double v = 0.0;
+                        for (int t = 0; t <= cx + dx; ++t)
+                            for (int u = 0; u <= cy + dy; ++u)
+                                for (int vv = 0; vv <= cz + dz; ++vv)
+                                    v += Ek[0][cx][dx][t] * Ek[1][cy][dy][u] * Ek[2][cz][dz][vv] * Yb[hidx(t, u, vv)];
+                        out[k] += v;
+                    }
+                }
+        }
+    const int n = d.frag_nao[x];
+    const int ao0 = d.frag_ao0[x];
+    double* T = eri + d.frag_eoff[x];
+    const size_t n2 = (size_t)n * n;
+    const int mu = d.sh_ao[sa] + kb / ncart(lb), nu = d.sh_ao[sb] + kb % ncart(lb);
+    const double smn = d.ao_scale[ao0 + mu] * d.ao_scale[ao0 + nu];
+    for (int k = 0; k < nc * nd; ++k) {
+        int la_ = d.sh_ao[sc] + k / nd, si = d.sh_ao[sd] + k % nd;
+        double v = out[k] * smn * d.ao_scale[ao0 + la_] * d.ao_scale[ao0 + si];
+        size_t m1 = (size_t)mu * n + nu, m2 = (size_t)nu * n + mu;
+        size_t k1 = (size_t)la_ * n + si, k2 = (size_t)si * n + la_;
+        T[m1 * n2 + k1] = v; T[m2 * n2 + k1] = v; T[m1 * n2 + k2] = v; T[m2 * n2 + k2] = v;
+        T[k1 * n2 + m1] = v; T[k1 * n2 + m2] = v; T[k2 * n2 + m1] = v; T[k2 * n2 + m2] = v;
     }
 }
 
-cudaError_t launch_intra_eri(const Dev& d, double* eri, int max_l, cudaStream_t s)
+cudaError_t launch_intra_eri(const Dev& d, const int4* tasks, int n_tasks, double* eri, cudaStream_t s)
 {
-    // one thread per shell-pair pair of the largest fragment, grid-strided
-    int max_sp = d.max_nao * (d.max_nao + 1) / 2;
-    dim3 g((unsigned)std::min<long long>(((long long)max_sp * max_sp + 127) / 128, 4096), d.n_frag);
-    if (max_l <= 1)
-        k_intra_eri<81><<<g, 128, 0, s>>>(d, eri);
-    else
-        k_intra_eri<1296><<<g, 128, 0, s>>>(d, eri);
-    note_launches(1);
+    if (n_tasks > 0) {
+        k_intra_eri<<<(n_tasks + 127) / 128, 128, 0, s>>>(d, tasks, n_tasks, eri);
+        note_launches(1);
+    }
     return cudaGetLastError();
 }
 
