@@ -234,8 +234,8 @@ def main():
     fef.lib()
     fp64_probe, fp32_probe, _ = fef.fef_measure_fma_peak()
 
-    def one_step(read_back=False):
-        ctx = fef.fef_create_system(system, opts, stream=stream.cuda_stream)
+    def one_step(read_back=False, options=None):
+        ctx = fef.fef_create_system(system, options or opts, stream=stream.cuda_stream)
         t_it0 = torch.cuda.Event(enable_timing=True)
         t_it1 = torch.cuda.Event(enable_timing=True)
         t_it0.record(stream)
@@ -244,8 +244,9 @@ def main():
         E_frag, E_tot, _ = fef.fef_energies(ctx)
         D = fef.fef_get_densities(ctx) if read_back else None
         st = fef.fef_stats(ctx)
+        hist = fef.fef_history(ctx)
         ctx.close()
-        return dict(n_macro=n_macro, E_tot=E_tot, stats=st, ev=(t_it0, t_it1), D=D)
+        return dict(n_macro=n_macro, E_tot=E_tot, stats=st, ev=(t_it0, t_it1), D=D, hist=hist)
 
     with torch.cuda.stream(stream):
         for _ in range(args.warmup):
@@ -278,6 +279,20 @@ def main():
             wall = time.perf_counter() - wall0
         launches = fef.fef_stats()["kernel_launches"] - launches0
         clocks = clk.summary()
+        # MIXED: FP32-core incremental builds, then FP64 polish (same workload, time to 1e-8 Eh)
+        mopts = fef.fef_default_options(cutoff_A=CUTOFF_A, schwarz=SCHWARZ, e_tol=E_TOL, precision=fef.FEF_MIXED)
+        mixed_ms, mixed_step_ms, mres = [], [], None
+        for k in range(args.warmup + max(2, args.steps // 2)):
+            flush.zero_()
+            m0 = torch.cuda.Event(enable_timing=True)
+            m1 = torch.cuda.Event(enable_timing=True)
+            m0.record(stream)
+            mres = one_step(options=mopts)
+            m1.record(stream)
+            m1.synchronize()
+            if k >= args.warmup:
+                mixed_ms.append(mres["ev"][0].elapsed_time(mres["ev"][1]))
+                mixed_step_ms.append(m0.elapsed_time(m1))
         # e2e: the same step through the public API plus the density read-back, wall clock
         e2e_ms = []
         for k in range(max(2, args.steps // 2)):
@@ -323,6 +338,15 @@ def main():
         "n_macro": last["n_macro"], "fock_builds_per_step": builds,
         "shell_quartets_per_build": st["shell_quartets"], "prim_quartets_per_build": int(np.sum(st["class_quartets"])),
         "E_tot": last["E_tot"],
+        "mixed": {"time_to_1e-8_ms": float(np.mean(mixed_ms)), "ms_per_step": float(np.mean(mixed_step_ms)),
+                  "n_macro": mres["n_macro"],
+                  "fp32_builds": int(sum(h["fp32"] for h in mres["hist"])),
+                  "fp64_builds": int(sum(1 - h["fp32"] for h in mres["hist"])),
+                  "jengine_fp32_ms_per_build": float(np.mean([h["jengine_ms"] for h in mres["hist"] if h["fp32"]]
+                                                             or [0.0])),
+                  "E_tot_minus_fp64": mres["E_tot"] - last["E_tot"],
+                  "value": st["shell_quartets"] * (mres["n_macro"] + 1) / (float(np.mean(mixed_step_ms)) * 1e-3),
+                  "speedup_time_to_1e-8_vs_fp64": float(np.mean(iter_ms)) / float(np.mean(mixed_ms))},
         "roofline": {"bound": "alu", "achieved": achieved / 1e12, "peak": FP64_PEAK / 1e12, "unit": "TFLOP/s",
                      "frac": achieved / FP64_PEAK, "traffic": profile_traffic(),
                      "kernel": "k_jengine<LP,LQ> (9 class-pair launches of one Fock build)",

@@ -589,22 +589,28 @@ extern "C" fef_status fef_create(const fef_geometry* g, const fef_basis* bs, con
         for (int x = 0; x < nf; ++x)
             require(c->nmo[x] >= frag_nocc[x], FEF_ERR_BASIS,
                     "fragment " + std::to_string(x) + ": basis too linearly dependent for its electrons");
-        // J-engine tiles: (pair, 32 bra primitive pairs of class LP) for every class pair present
+        // J-engine tiles: (2*pair + swap, first of 32 bra primitive pairs).  For a pair (x, y) and
+        // classes (Lx, Ly) the member with the larger class is the bra (lane-owned, no reduction);
+        // swap = 1 when that is y.  Kernels with L_bra < L_ket are never needed.
         int64_t prim_q = 0;
-        for (int LP = 0; LP < kClasses; ++LP)
-            for (int LQ = 0; LQ < kClasses; ++LQ) {
-                std::vector<int2> t;
-                for (int p = 0; p < c->n_pairs; ++p) {
-                    int x = pair_x[p], y = pair_y[p];
-                    int nb = frag_npp[x * kClasses + LP], nk = frag_npp[y * kClasses + LQ];
+        std::vector<int2> tl[kClasses][kClasses];
+        for (int p = 0; p < c->n_pairs; ++p)
+            for (int Lx = 0; Lx < kClasses; ++Lx)
+                for (int Ly = 0; Ly < kClasses; ++Ly) {
+                    const bool swap = Lx < Ly;
+                    const int bx = swap ? pair_y[p] : pair_x[p], ky = swap ? pair_x[p] : pair_y[p];
+                    const int LP = swap ? Ly : Lx, LQ = swap ? Lx : Ly;
+                    int nb = frag_npp[bx * kClasses + LP], nk = frag_npp[ky * kClasses + LQ];
                     if (nb == 0 || nk == 0) continue;
                     for (int o2 = 0; o2 < nb; o2 += 32) {
-                        t.push_back(make_int2(p, frag_pp0[x * kClasses + LP] + o2));
+                        tl[LP][LQ].push_back(make_int2(2 * p + (swap ? 1 : 0), frag_pp0[bx * kClasses + LP] + o2));
                         prim_q += (int64_t)std::min(32, nb - o2) * nk;
                     }
                 }
-                b->n_tiles[LP * kClasses + LQ] = (int)t.size();
-                b->tiles[LP][LQ] = t.empty() ? nullptr : b->upload(t, s, "tiles");
+        for (int LP = 0; LP < kClasses; ++LP)
+            for (int LQ = 0; LQ < kClasses; ++LQ) {
+                b->n_tiles[LP * kClasses + LQ] = (int)tl[LP][LQ].size();
+                b->tiles[LP][LQ] = tl[LP][LQ].empty() ? nullptr : b->upload(tl[LP][LQ], s, "tiles");
             }
         c->prim_quartets = prim_q;
         const int ncount = 1 + kClasses * kClasses;

@@ -107,8 +107,9 @@ __device__ __forceinline__ void hermite_contract(const Real* R, const Real* DP, 
         static_for<NQ>([&](auto Jc) { atomicAdd(QJ + (size_t)decltype(Jc)::value * nQ + k, (double)sq[decltype(Jc)::value]); });
 }
 
-// One warp per tile = (fragment pair x<y, up to 32 bra primitive pairs of class LP in x) against all
-// ket primitive pairs of class LQ in y.  Lane i owns bra pair P_i: its centre, Hermite density and
+// One warp per tile = (fragment pair, up to 32 bra primitive pairs of class LP in one member x)
+// against all ket primitive pairs of class LQ <= LP in the other member y (the pair's two J
+// directions are both produced, so the member with the larger class is put on the bra side).  Lane i owns bra pair P_i: its centre, Hermite density and
 // Hermite field accumulator stay in registers.  Ket data are warp-uniform loads.  The field on the
 // ket pair is reduced across the warp with shuffles and added to global memory by lane 0.
 // Shell quartets with Q_ab Q_cd < tau contribute nothing (Schwarz screening at shell level).
@@ -120,7 +121,10 @@ __global__ void __launch_bounds__(128) k_jengine(Dev d, const int2* __restrict__
     const int lane = threadIdx.x & 31;
     if (warp >= n_tiles) return;
     const int2 tl = tiles[warp];
-    const int x = d.pair_x[tl.x], y = d.pair_y[tl.x];
+    // tile.x = 2 * pair + swap: the bra fragment is the pair member holding the larger class
+    const int pr = tl.x >> 1;
+    const int x = (tl.x & 1) ? d.pair_y[pr] : d.pair_x[pr];
+    const int y = (tl.x & 1) ? d.pair_x[pr] : d.pair_y[pr];
     const int bra_end = d.frag_pp0[x * kClasses + LP] + d.frag_npp[x * kClasses + LP];
     const int Pg = tl.y + lane;
     const bool valid = Pg < bra_end;
@@ -190,7 +194,10 @@ __global__ void __launch_bounds__(128) k_jengine32(Dev d, const int2* __restrict
     const int lane = threadIdx.x & 31;
     if (warp >= n_tiles) return;
     const int2 tl = tiles[warp];
-    const int x = d.pair_x[tl.x], y = d.pair_y[tl.x];
+    // tile.x = 2 * pair + swap: the bra fragment is the pair member holding the larger class
+    const int pr = tl.x >> 1;
+    const int x = (tl.x & 1) ? d.pair_y[pr] : d.pair_x[pr];
+    const int y = (tl.x & 1) ? d.pair_x[pr] : d.pair_y[pr];
     const double* ax = d.atom_xyz + 3 * d.frag_atom0[x];
     const double* ay = d.atom_xyz + 3 * d.frag_atom0[y];
     const float ox = (float)(ax[0] - ay[0]), oy = (float)(ax[1] - ay[1]), oz = (float)(ax[2] - ay[2]);
@@ -274,8 +281,7 @@ cudaError_t launch_jengine(const Dev& d, const int2* tiles[kClasses][kClasses], 
 {
     const float ft = (float)tau;
 #define FEF_J(LP, LQ) launch_one<LP, LQ>(d, tiles[LP][LQ], n_tiles[LP * kClasses + LQ], ft, fp32, s)
-    FEF_J(0, 0); FEF_J(0, 1); FEF_J(0, 2); FEF_J(1, 0); FEF_J(1, 1); FEF_J(1, 2); FEF_J(2, 0); FEF_J(2, 1);
-    FEF_J(2, 2);
+    FEF_J(0, 0); FEF_J(1, 0); FEF_J(1, 1); FEF_J(2, 0); FEF_J(2, 1); FEF_J(2, 2);
 #undef FEF_J
     return cudaGetLastError();
 }
