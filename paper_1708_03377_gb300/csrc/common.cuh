@@ -183,10 +183,10 @@ __device__ inline void boys_fp64_rt(const double* __restrict__ table, double T, 
 // lower levels while R^{(n)} of the higher levels is written.
 namespace detail {
 // One level sweep of md_R at order N, for Hermite index IDX down to 1 (compile-time recursion so that
-// every R index is a constant and R stays in registers).
-template <int IDX, typename Real>
+// every R index is a constant and R stays in registers, or at constant offsets of a shared slice).
+template <int IDX, typename Real, typename Arr>
 struct MdRStep {
-    static __device__ __forceinline__ void run(Real* R, Real X, Real Y, Real Z)
+    static __device__ __forceinline__ void run(Arr R, Real X, Real Y, Real Z)
     {
         constexpr TUV c = htuv(IDX);
         Real v;
@@ -201,34 +201,41 @@ struct MdRStep {
             if constexpr (c.v > 1) v = fma(Real(c.v - 1), R[hidx(c.t, c.u, c.v - 2)], v);
         }
         R[IDX] = v;
-        MdRStep<IDX - 1, Real>::run(R, X, Y, Z);
+        MdRStep<IDX - 1, Real, Arr>::run(R, X, Y, Z);
     }
 };
-template <typename Real>
-struct MdRStep<0, Real> {
-    static __device__ __forceinline__ void run(Real*, Real, Real, Real) {}
+template <typename Real, typename Arr>
+struct MdRStep<0, Real, Arr> {
+    static __device__ __forceinline__ void run(Arr, Real, Real, Real) {}
 };
-template <int L, int N, typename Real>
+template <int L, int N, typename Real, typename Arr>
 struct MdRLevel {
-    static __device__ __forceinline__ void run(Real* R, const Real* base, Real X, Real Y, Real Z)
+    static __device__ __forceinline__ void run(Arr R, const Real* base, Real X, Real Y, Real Z)
     {
-        MdRStep<nh(L - N) - 1, Real>::run(R, X, Y, Z);
+        MdRStep<nh(L - N) - 1, Real, Arr>::run(R, X, Y, Z);
         R[0] = base[N];
-        MdRLevel<L, N - 1, Real>::run(R, base, X, Y, Z);
+        MdRLevel<L, N - 1, Real, Arr>::run(R, base, X, Y, Z);
     }
 };
-template <int L, typename Real>
-struct MdRLevel<L, -1, Real> {
-    static __device__ __forceinline__ void run(Real*, const Real*, Real, Real, Real) {}
+template <int L, typename Real, typename Arr>
+struct MdRLevel<L, -1, Real, Arr> {
+    static __device__ __forceinline__ void run(Arr, const Real*, Real, Real, Real) {}
 };
 }  // namespace detail
 
-template <int L, typename Real>
-__device__ __forceinline__ void md_R(Real* R, const Real* base, Real X, Real Y, Real Z)
+template <int L, typename Real, typename Arr>
+__device__ __forceinline__ void md_R(Arr R, const Real* base, Real X, Real Y, Real Z)
 {
     R[0] = base[L];
-    detail::MdRLevel<L, L - 1, Real>::run(R, base, X, Y, Z);
+    detail::MdRLevel<L, L - 1, Real, Arr>::run(R, base, X, Y, Z);
 }
+
+// Per-lane slice of a warp's shared buffer, element i of lane l at p[i * 32 + l] (conflict-free).
+template <typename Real>
+struct LaneSlice {
+    Real* p;
+    __device__ __forceinline__ Real& operator[](int i) const { return p[i * 32]; }
+};
 
 // Runtime-L R recursion for the non-hot kernels; R has room for nh(L) values, scratch for the
 // same.  Same recurrence as md_R.

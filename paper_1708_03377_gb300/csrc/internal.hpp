@@ -159,6 +159,8 @@ cudaError_t launch_hermite_density(const Dev& d, const double* D, cudaStream_t s
 // into the FP64 accumulators pp_Jh.
 cudaError_t launch_jengine(const Dev& d, const int2* tiles[kClasses][kClasses], const int* n_tiles, double tau,
                            int fp32, cudaStream_t s);
+cudaError_t launch_jengine_big(const Dev& d, const int2* tiles[kClasses][kClasses], const int* n_tiles, float tau,
+                               int fp32, cudaStream_t s);
 cudaError_t launch_back_transform(const Dev& d, double* J, cudaStream_t s);
 // F = h + C D + V_env + J_env per fragment; E_int[x] = tr[D (h + G/2)] + e_nn[x]; tr_omega[x] = tr[D (V+J)]
 // also trV[x] = tr(D^x V_env^x), trJ[x] = tr(D^x J_env^x)

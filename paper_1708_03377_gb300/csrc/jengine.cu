@@ -282,8 +282,9 @@ cudaError_t launch_jengine(const Dev& d, const int2* tiles[kClasses][kClasses], 
     const float ft = (float)tau;
 #define FEF_J(LP, LQ) launch_one<LP, LQ>(d, tiles[LP][LQ], n_tiles[LP * kClasses + LQ], ft, fp32, s)
     FEF_J(0, 0); FEF_J(1, 0); FEF_J(1, 1); FEF_J(2, 0); FEF_J(2, 1); FEF_J(2, 2);
+    FEF_J(3, 0); FEF_J(3, 1); FEF_J(4, 0);
 #undef FEF_J
-    return cudaGetLastError();
+    return launch_jengine_big(d, tiles, n_tiles, ft, fp32, s);  // classes with L_P + L_Q >= 5
 }
 
 // Dh32 = float(Dh - Dh_ref): the Hermite density of D - D_ref (linear in D).

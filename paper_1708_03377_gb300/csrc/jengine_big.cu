@@ -1,0 +1,223 @@
+// J-engine classes with L = L_P + L_Q >= 5 (shell pairs with d functions; up to (dd|dd), L = 8).
+// Same contraction as the register kernels of jengine.cu (McMurchie-Davidson Hermite field of the
+// partner fragment's density, paper Eq. dp2e / Eq. wc), but each lane keeps its nh(L) Hermite
+// integrals R_{tuv} in a lane-strided slice of shared memory (too many for registers at L >= 5), the
+// warp-uniform ket Hermite density is staged in shared memory, and the field on the ket pair is
+// reduced across the warp in chunks of 5 components.  Two warps per block.
+#include <type_traits>
+
+#include "common.cuh"
+#include "internal.hpp"
+
+namespace fef {
+
+namespace {
+
+constexpr int kBigWarps = 2;
+
+template <int LP, int LQ>
+__host__ __device__ constexpr int big_slice()  // Reals per warp: R slices of 32 lanes + ket density (+ pad to 2)
+{
+    return 32 * nh(LP + LQ) + ((nh(LQ) + 1) & ~1);
+}
+
+template <int NP, int NQ, typename Real, typename RArr>
+__device__ __forceinline__ void contract_big(RArr R, const Real* DP, const Real* DQ, Real* JP,
+                                             double* __restrict__ QJ, size_t nQ, int k, int lane)
+{
+    static_for<NP>([&](auto I) {
+        constexpr TUV a = htuv(decltype(I)::value);
+        Real acc = JP[decltype(I)::value];
+        static_for<NQ>([&](auto Jc) {
+            constexpr TUV b = htuv(decltype(Jc)::value);
+            constexpr int r = hidx(a.t + b.t, a.u + b.u, a.v + b.v);
+            if constexpr (((b.t + b.u + b.v) & 1) != 0)
+                acc = fma(-R[r], DQ[decltype(Jc)::value], acc);
+            else
+                acc = fma(R[r], DQ[decltype(Jc)::value], acc);
+        });
+        JP[decltype(I)::value] = acc;
+    });
+    constexpr int CH = 5;
+    static_for<(NQ + CH - 1) / CH>([&](auto C) {
+        constexpr int j0 = decltype(C)::value * CH;
+        Real sq[CH];
+        static_for<CH>([&](auto Jj) {
+            constexpr int j = j0 + decltype(Jj)::value;
+            if constexpr (j < NQ) {
+                constexpr TUV b = htuv(j);
+                Real s = Real(0);
+                static_for<NP>([&](auto I) {
+                    constexpr TUV a = htuv(decltype(I)::value);
+                    s = fma(R[hidx(a.t + b.t, a.u + b.u, a.v + b.v)], DP[decltype(I)::value], s);
+                });
+                sq[decltype(Jj)::value] = ((b.t + b.u + b.v) & 1) ? -s : s;
+            } else {
+                sq[decltype(Jj)::value] = Real(0);
+            }
+        });
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1)
+            static_for<CH>([&](auto Jj) {
+                sq[decltype(Jj)::value] += __shfl_xor_sync(0xffffffffu, sq[decltype(Jj)::value], o);
+            });
+        if (lane == 0)
+            static_for<CH>([&](auto Jj) {
+                constexpr int j = j0 + decltype(Jj)::value;
+                if constexpr (j < NQ) atomicAdd(QJ + (size_t)j * nQ + k, (double)sq[decltype(Jj)::value]);
+            });
+    });
+}
+
+// Real = double: full FP64 build on pp_Dh.  Real = float: the mixed-precision core on pp_Dh32 with
+// FP32 geometry relative to each fragment's first atom, flushed to FP64 every 16 ket pairs.
+template <int LP, int LQ, typename Real>
+__global__ void __launch_bounds__(32 * kBigWarps) k_jengine_big(Dev d, const int2* __restrict__ tiles, int n_tiles,
+                                                                 float tau)
+{
+    constexpr bool F32 = std::is_same<Real, float>::value;
+    constexpr int NP = nh(LP), NQ = nh(LQ), L = LP + LQ;
+    extern __shared__ __align__(16) unsigned char smraw[];
+    const int wib = threadIdx.x >> 5;
+    const int lane = threadIdx.x & 31;
+    Real* sm = reinterpret_cast<Real*>(smraw) + wib * big_slice<LP, LQ>();
+    LaneSlice<Real> R{sm + lane};
+    Real* DQ = sm + 32 * nh(L);
+    const int warp = blockIdx.x * kBigWarps + wib;
+    if (warp >= n_tiles) return;
+    const int2 tl = tiles[warp];
+    const int pr = tl.x >> 1;
+    const int x = (tl.x & 1) ? d.pair_y[pr] : d.pair_x[pr];
+    const int y = (tl.x & 1) ? d.pair_x[pr] : d.pair_y[pr];
+    const int bra_end = d.frag_pp0[x * kClasses + LP] + d.frag_npp[x * kClasses + LP];
+    const int Pg = tl.y + lane;
+    const bool valid = Pg < bra_end;
+    const int Pl = valid ? Pg : tl.y;
+    const int nP = d.n_pp[LP], nQ = d.n_pp[LQ];
+    const float qP = valid ? d.pp_Q[LP][Pl] : 0.0f;
+    Real DP[NP], JP[NP];
+    double JP64[NP];
+#pragma unroll
+    for (int i = 0; i < NP; ++i) {
+        if constexpr (F32)
+            DP[i] = valid ? d.pp_Dh32[LP][(size_t)i * nP + Pl] : 0.0f;
+        else
+            DP[i] = valid ? d.pp_Dh[LP][(size_t)i * nP + Pl] : 0.0;
+        JP[i] = Real(0);
+        JP64[i] = 0.0;
+    }
+    // geometry of the bra pair
+    double4_32a Pd{};
+    float4 Pf{}, Pr{};
+    float ox = 0.f, oy = 0.f, oz = 0.f;
+    if constexpr (F32) {
+        const double* ax = d.atom_xyz + 3 * d.frag_atom0[x];
+        const double* ay = d.atom_xyz + 3 * d.frag_atom0[y];
+        ox = (float)(ax[0] - ay[0]);
+        oy = (float)(ax[1] - ay[1]);
+        oz = (float)(ax[2] - ay[2]);
+        Pr = d.pp_Pr[LP][Pl];
+    } else {
+        Pd = d.pp_P[LP][Pl];
+        Pf = d.pp_Pf[LP][Pl];
+    }
+    const int k0 = d.frag_pp0[y * kClasses + LQ];
+    const int k1 = k0 + d.frag_npp[y * kClasses + LQ];
+    double* __restrict__ QJ = d.pp_Jh[LQ];
+    int since_flush = 0;
+    for (int k = k0; k < k1; ++k) {
+        const float qQ = __ldg(d.pp_Q[LQ] + k);
+        const bool keep = qP * qQ >= tau;
+        if (!__any_sync(0xffffffffu, keep)) continue;
+        __syncwarp();
+        for (int j = lane; j < NQ; j += 32) {
+            if constexpr (F32)
+                DQ[j] = __ldg(d.pp_Dh32[LQ] + (size_t)j * nQ + k);
+            else
+                DQ[j] = __ldg(d.pp_Dh[LQ] + (size_t)j * nQ + k);
+        }
+        __syncwarp();
+        Real base[L + 1];
+        Real X, Y, Z;
+        if constexpr (F32) {
+            const float4 Qr = __ldg(d.pp_Pr[LQ] + k);
+            X = (Pr.x - Qr.x) + ox;
+            Y = (Pr.y - Qr.y) + oy;
+            Z = (Pr.z - Qr.z) + oz;
+            const float r = rsqrtf(Pr.w + Qr.w);
+            const float alpha = Pr.w * Qr.w * (r * r);
+            float F[L + 1];
+            boys_fp32<L>(d.boys32, alpha * fmaf(X, X, fmaf(Y, Y, Z * Z)), F);
+            float pre = keep ? r : 0.0f;
+#pragma unroll
+            for (int n = 0; n <= L; ++n) {
+                base[n] = pre * F[n];
+                pre *= -2.0f * alpha;
+            }
+        } else {
+            const double4_32a Qd = d.pp_P[LQ][k];
+            const float4 Qf = __ldg(d.pp_Pf[LQ] + k);
+            X = Pd.x - Qd.x;
+            Y = Pd.y - Qd.y;
+            Z = Pd.z - Qd.z;
+            const double r = rsqrt(Pd.w + Qd.w);
+            const double alpha = Pd.w * Qd.w * (r * r);
+            const float Xf = Pf.x - Qf.x, Yf = Pf.y - Qf.y, Zf = Pf.z - Qf.z;
+            const float Tf = __fdividef(Pf.w * Qf.w, Pf.w + Qf.w) * fmaf(Xf, Xf, fmaf(Yf, Yf, Zf * Zf));
+            double F[L + 1];
+            boys_fp64<L>(d.boys, alpha * fma(X, X, fma(Y, Y, Z * Z)), boys_row(Tf), F);
+            double pre = keep ? r : 0.0;
+#pragma unroll
+            for (int n = 0; n <= L; ++n) {
+                base[n] = pre * F[n];
+                pre *= -2.0 * alpha;
+            }
+        }
+        md_R<L, Real>(R, base, X, Y, Z);
+        contract_big<NP, NQ, Real>(R, DP, DQ, JP, QJ, (size_t)nQ, k, lane);
+        if constexpr (F32) {
+            if (++since_flush == 16) {
+                since_flush = 0;
+#pragma unroll
+                for (int i = 0; i < NP; ++i) {
+                    JP64[i] += (double)JP[i];
+                    JP[i] = 0.0f;
+                }
+            }
+        }
+    }
+    if (valid) {
+#pragma unroll
+        for (int i = 0; i < NP; ++i) atomicAdd(d.pp_Jh[LP] + (size_t)i * nP + Pg, JP64[i] + (double)JP[i]);
+    }
+}
+
+template <int LP, int LQ>
+void launch_big(const Dev& d, const int2* t, int n, float tau, int fp32, cudaStream_t s)
+{
+    if (n <= 0) return;
+    const int blocks = (n + kBigWarps - 1) / kBigWarps;
+    if (fp32) {
+        const size_t smem = (size_t)kBigWarps * big_slice<LP, LQ>() * sizeof(float);
+        cudaFuncSetAttribute(k_jengine_big<LP, LQ, float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        k_jengine_big<LP, LQ, float><<<blocks, 32 * kBigWarps, smem, s>>>(d, t, n, tau);
+    } else {
+        const size_t smem = (size_t)kBigWarps * big_slice<LP, LQ>() * sizeof(double);
+        cudaFuncSetAttribute(k_jengine_big<LP, LQ, double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        k_jengine_big<LP, LQ, double><<<blocks, 32 * kBigWarps, smem, s>>>(d, t, n, tau);
+    }
+    note_launches(1);
+}
+
+}  // namespace
+
+cudaError_t launch_jengine_big(const Dev& d, const int2* tiles[kClasses][kClasses], const int* n_tiles, float tau,
+                               int fp32, cudaStream_t s)
+{
+#define FEF_JB(LP, LQ) launch_big<LP, LQ>(d, tiles[LP][LQ], n_tiles[LP * kClasses + LQ], tau, fp32, s)
+    FEF_JB(3, 2); FEF_JB(3, 3); FEF_JB(4, 1); FEF_JB(4, 2); FEF_JB(4, 3); FEF_JB(4, 4);
+#undef FEF_JB
+    return cudaGetLastError();
+}
+
+}  // namespace fef
