@@ -234,8 +234,10 @@ def main():
     fef.lib()
     fp64_probe, fp32_probe, _ = fef.fef_measure_fma_peak()
 
-    def one_step(read_back=False, options=None):
+    def one_step(read_back=False, options=None, warm=None):
         ctx = fef.fef_create_system(system, options or opts, stream=stream.cuda_stream)
+        if warm is not None:
+            fef.fef_set_warm_start(ctx, warm)
         t_it0 = torch.cuda.Event(enable_timing=True)
         t_it1 = torch.cuda.Event(enable_timing=True)
         t_it0.record(stream)
@@ -279,20 +281,48 @@ def main():
             wall = time.perf_counter() - wall0
         launches = fef.fef_stats()["kernel_launches"] - launches0
         clocks = clk.summary()
-        # MIXED: FP32-core incremental builds, then FP64 polish (same workload, time to 1e-8 Eh)
+        # MIXED: FP32-core incremental builds + FP64 reference refresh (same workload, to 1e-8 Eh)
+        def variant(options, warm=None):
+            it_ms, step_ms, res = [], [], None
+            for k in range(args.warmup + max(2, args.steps // 2)):
+                flush.zero_()
+                m0 = torch.cuda.Event(enable_timing=True)
+                m1 = torch.cuda.Event(enable_timing=True)
+                m0.record(stream)
+                res = one_step(options=options, warm=warm)
+                m1.record(stream)
+                m1.synchronize()
+                if k >= args.warmup:
+                    it_ms.append(res["ev"][0].elapsed_time(res["ev"][1]))
+                    step_ms.append(m0.elapsed_time(m1))
+            return it_ms, step_ms, res
+
+        def summary(it_ms, step_ms, res):
+            return {"time_to_1e-8_ms": float(np.mean(it_ms)), "ms_per_step": float(np.mean(step_ms)),
+                    "n_macro": res["n_macro"],
+                    "fp32_builds": int(sum(h["fp32"] for h in res["hist"])),
+                    "fp64_builds": int(sum(1 - h["fp32"] for h in res["hist"])),
+                    "E_tot_minus_fp64": res["E_tot"] - results[-1]["E_tot"],
+                    "value": res["stats"]["shell_quartets"] * (res["n_macro"] + 1) / (float(np.mean(step_ms)) * 1e-3),
+                    "speedup_time_to_1e-8_vs_fp64": float(np.mean(iter_ms)) / float(np.mean(it_ms))}
+
         mopts = fef.fef_default_options(cutoff_A=CUTOFF_A, schwarz=SCHWARZ, e_tol=E_TOL, precision=fef.FEF_MIXED)
-        mixed_ms, mixed_step_ms, mres = [], [], None
-        for k in range(args.warmup + max(2, args.steps // 2)):
-            flush.zero_()
-            m0 = torch.cuda.Event(enable_timing=True)
-            m1 = torch.cuda.Event(enable_timing=True)
-            m0.record(stream)
-            mres = one_step(options=mopts)
-            m1.record(stream)
-            m1.synchronize()
-            if k >= args.warmup:
-                mixed_ms.append(mres["ev"][0].elapsed_time(mres["ev"][1]))
-                mixed_step_ms.append(m0.elapsed_time(m1))
+        mixed_ms, mixed_step_ms, mres = variant(mopts)
+        # MIXED + learned warm start: the network is trained beforehand (not timed) on converged densities
+        # of 40 seeded 32-water snapshots with the workload's basis
+        from paper_1708_03377_gb300 import learned as lrn
+        Xs, Ts = [], []
+        for sd in range(1000, 1040):
+            try:
+                Xq, Tq = lrn.snapshot_samples(S.water_box(32, seed=sd, basis_sets=system.basis_sets), cutoff_A=CUTOFF_A)
+                Xs.append(Xq)
+                Ts.append(Tq)
+            except fef.FefError:
+                pass
+        net, net_loss = lrn.train_warm_start(np.concatenate(Xs), np.concatenate(Ts), hidden=256, epochs=300, batch=128)
+        lopts = fef.fef_default_options(cutoff_A=CUTOFF_A, schwarz=SCHWARZ, e_tol=E_TOL, precision=fef.FEF_MIXED,
+                                        start=fef.FEF_START_LEARNED)
+        ml_ms, ml_step_ms, mlres = variant(lopts, warm=net)
         # e2e: the same step through the public API plus the density read-back, wall clock
         e2e_ms = []
         for k in range(max(2, args.steps // 2)):
@@ -338,15 +368,11 @@ def main():
         "n_macro": last["n_macro"], "fock_builds_per_step": builds,
         "shell_quartets_per_build": st["shell_quartets"], "prim_quartets_per_build": int(np.sum(st["class_quartets"])),
         "E_tot": last["E_tot"],
-        "mixed": {"time_to_1e-8_ms": float(np.mean(mixed_ms)), "ms_per_step": float(np.mean(mixed_step_ms)),
-                  "n_macro": mres["n_macro"],
-                  "fp32_builds": int(sum(h["fp32"] for h in mres["hist"])),
-                  "fp64_builds": int(sum(1 - h["fp32"] for h in mres["hist"])),
+        "mixed": {**summary(mixed_ms, mixed_step_ms, mres),
                   "jengine_fp32_ms_per_build": float(np.mean([h["jengine_ms"] for h in mres["hist"] if h["fp32"]]
-                                                             or [0.0])),
-                  "E_tot_minus_fp64": mres["E_tot"] - last["E_tot"],
-                  "value": st["shell_quartets"] * (mres["n_macro"] + 1) / (float(np.mean(mixed_step_ms)) * 1e-3),
-                  "speedup_time_to_1e-8_vs_fp64": float(np.mean(iter_ms)) / float(np.mean(mixed_ms))},
+                                                             or [0.0]))},
+        "mixed_learned": {**summary(ml_ms, ml_step_ms, mlres), "train_samples": int(sum(len(x) for x in Xs)),
+                          "train_loss": net_loss},
         "roofline": {"bound": "alu", "achieved": achieved / 1e12, "peak": FP64_PEAK / 1e12, "unit": "TFLOP/s",
                      "frac": achieved / FP64_PEAK, "traffic": profile_traffic(),
                      "kernel": "k_jengine<LP,LQ> (9 class-pair launches of one Fock build)",

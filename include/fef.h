@@ -82,10 +82,13 @@ typedef struct {
 } fef_basis;
 
 typedef struct {
-    int32_t precision;       /* FEF_FP64, or FEF_MIXED: Fock builds after the first FP64 one add the FP32-core
-                                J-engine of D - D_ref to the FP64 field of D_ref (FP64 accumulation,
+    int32_t precision;       /* FEF_FP64, or FEF_MIXED: fef_iterate's first field comes from the FP32-core
+                                J-engine and becomes the reference D_ref; later builds add the FP32-core
+                                J-engine of D - D_ref to the stored field of D_ref (FP64 accumulation,
                                 FP64 intra-fragment G, eigensolve and energies) until |dE| <
-                                mixed_switch, then FP64 builds until convergence */
+                                mixed_switch (or stops decreasing); then one FP64 build becomes the
+                                exact reference and FP32 increments relative to it continue to
+                                convergence.  After a learned start the first field is the FP64 one. */
     double cutoff_A;         /* fragment pairs with min atom-atom distance >= cutoff are dropped
                                 (J and V together); <= 0 keeps all pairs */
     double schwarz;          /* shell quartet (ab|cd) dropped when Q_ab Q_cd < schwarz (0: none) */
@@ -98,7 +101,7 @@ typedef struct {
     int32_t start;           /* FEF_START_*: initial densities */
     int32_t use_graph;       /* capture each macro-iteration's device work in a CUDA graph */
     int32_t deterministic;   /* reserved: 1 requests run-to-run identical sums */
-    double mixed_switch;     /* MIXED: FP32-core macro-iterations until |dE| < mixed_switch, then FP64 */
+    double mixed_switch;     /* MIXED: coarse FP32-core macro-iterations until |dE| < mixed_switch */
 } fef_options;
 
 /* Fill *opt with the defaults: FP64, no cutoff, schwarz 1e-12, e_tol 1e-8, micro_e_tol 1e-11,
@@ -126,13 +129,13 @@ fef_status fef_ao_layout(const fef_ctx* ctx, int32_t* n_ao_per_frag, int64_t* of
  * current densities.  F_out: packed output, or NULL.  on_device: 1 if D/F_out are device pointers.
  * The inter-fragment J is the fused McMurchie-Davidson J-engine: no ERI tensor is formed.
  * FP64 mode: the full FP64 J-engine.  MIXED: J[D^y] = J[D_ref] + J_fp32[D^y - D_ref] relative to the
- * last FP64 build of this context (the first build is FP64 and becomes the reference).
+ * last FP64 build of this context; without one the build is FP64 and becomes the reference.
  * Errors: ARG, CUDA, NUMERIC. */
 fef_status fef_build_fock(fef_ctx* ctx, const double* D, double* F_out, int on_device);
 
 /* FEF self-consistency (Theory, "Fragment Mean Field": omega_x fully relaxed to infinite order).
  * Start from the option's start densities (superposition of isolated-fragment RHF densities, the
- * learned warm start, or the current/given ones); each macro-iteration k builds omega^(k) from
+ * learned warm start (fef_set_warm_start), or the current/given ones); each macro-iteration k builds omega^(k) from
  * D^(k-1) of all fragments and solves every fragment's RHF in its frozen field (DIIS, canonical
  * orthogonalisation, aufbau) to get D^(k); stops when |dE_tot| and max_x |dE_x| < e_tol.
  * n_macro_out (nullable): macro-iterations done; final_dE_out (nullable): last |dE_tot|.
@@ -181,6 +184,55 @@ void fef_destroy(fef_ctx* ctx);
 /* Measure this GPU's FP64 and FP32 FMA throughput with a register-resident FMA chain kernel.
  * Outputs (nullable) in FLOP/s, counting one FMA as 2 FLOP.  Errors: CUDA. */
 fef_status fef_measure_fma_peak(double* fp64_flops, double* fp32_flops, double* sm_clock_mhz);
+
+/* ---------------------------------------------------------------------------------------------
+ * Learned warm start.  The paper has no learned component: this is an accelerator of the FEF
+ * iterations that leaves the fixed point unchanged (the plain FEF loop still converges the result
+ * and judges the energy).  A small perceptron maps the environment of each fragment to the change
+ * of its density from the isolated-fragment RHF density, in the fragment's molecule-fixed frame
+ * (axes from atoms 0, 1, 2 in input order).  It needs fragments of one kind (same atoms, s/p basis).
+ * ------------------------------------------------------------------------------------------- */
+typedef struct fef_mlp fef_mlp;
+
+/* Network Y = W3 tanh(W2 tanh(W1 X + b1) + b2) + b3 with n_in inputs, two hidden layers of n_hidden,
+ * n_out outputs; FP32 weights, Glorot-uniform initialisation from seed (splitmix64).  All work on
+ * cuda_stream.  Errors: ARG, CUDA. */
+fef_status fef_mlp_create(int32_t n_in, int32_t n_hidden, int32_t n_out, uint64_t seed, void* cuda_stream,
+                          fef_mlp** out);
+void fef_mlp_destroy(fef_mlp* m);
+/* Get (set = 0) or set (set = 1) the flat parameters W1 (n_in x n_hidden, row-major), b1, W2, b2, W3, b3
+ * through the HOST array params (nullable); *n_params (nullable) gets their number.  Setting resets Adam. */
+fef_status fef_mlp_params(fef_mlp* m, float* params, int64_t* n_params, int32_t set);
+/* Affine scaling used by fef_mlp_predict and by the warm start: the network sees (X - in_shift)/in_scale
+ * and its output y becomes out_shift + out_scale * y.  Host arrays of n_in / n_out floats. */
+fef_status fef_mlp_set_scaling(fef_mlp* m, const float* in_shift, const float* in_scale, const float* out_shift,
+                               const float* out_scale);
+/* Mean squared error L = sum (Y - T)^2 / (n n_out) of the raw network (no scaling) on DEVICE arrays
+ * X [n x n_in], T [n x n_out], and its gradient into the DEVICE array grad [n_params] (nullable). */
+fef_status fef_mlp_loss_grad(fef_mlp* m, const float* X, const float* T, int32_t n, float* loss, float* grad);
+/* Adam (beta 0.9/0.999, eps 1e-8) on mini-batches of the raw network, shuffled every epoch; DEVICE
+ * X, T as above; *final_loss (nullable) = mean squared error over the last epoch. */
+fef_status fef_mlp_train(fef_mlp* m, const float* X, const float* T, int32_t n, int32_t epochs, int32_t batch,
+                         float lr, float* final_loss);
+/* Y [n x n_out] = scaled network(X [n x n_in]); DEVICE arrays. */
+fef_status fef_mlp_predict(fef_mlp* m, const float* X, float* Y, int32_t n);
+const char* fef_mlp_last_error(const fef_mlp* m);
+
+/* Features of the learned warm start for the densities D (packed, becomes the current density; NULL =
+ * current): X [n_frag x n_feat] = per atom the potential and field (frame components) of all neighbour
+ * fragments' nuclei and electrons (4 n_atoms values), then the environment operator omega_x of a
+ * Fock build of D in the Loewdin basis (S^{-1/2} omega S^{-1/2}) and the molecule-fixed frame, upper
+ * triangle (n_pack values): n_feat = 4 n_atoms + n_pack.  Y_local [n_frag x n_pack] = the
+ * density in the Loewdin basis (S^{1/2} D S^{1/2}, S^{1/2} symmetric) expressed in the molecule-fixed
+ * frame, upper triangle row-major (n_pack = n(n+1)/2).  X, Y_local are
+ * host arrays, or device arrays when on_device = 1; either may be NULL.  *n_feat, *n_pack (nullable)
+ * are 0 when the fragments are not of one kind.  Errors: ARG, CUDA. */
+fef_status fef_learned_features(fef_ctx* ctx, const double* D, float* X, float* Y_local, int on_device,
+                                int32_t* n_feat, int32_t* n_pack);
+/* Attach the network used by fef_iterate when opt.start = FEF_START_LEARNED (NULL detaches; the
+ * caller keeps ownership).  Its outputs are the change of the local-frame Loewdin-basis density from
+ * the isolated-fragment one; the start is D_isolated + S^{-1/2} (that change, rotated back) S^{-1/2}. */
+fef_status fef_set_warm_start(fef_ctx* ctx, fef_mlp* m);
 
 /* Batched closed-shell RHF of independent fragments in frozen fields, for callers that cannot
  * allocate device memory.  The paper has no counterpart: this is a service entry point of this

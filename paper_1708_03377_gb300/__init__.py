@@ -26,7 +26,9 @@ STATUS_NAMES = {0: "FEF_OK", 1: "FEF_ERR_ARG", 2: "FEF_ERR_BASIS", 3: "FEF_ERR_G
 
 EXPORTED = ["fef_default_options", "fef_create", "fef_ao_layout", "fef_build_fock", "fef_iterate", "fef_energies",
             "fef_get_densities", "fef_set_densities", "fef_stats", "fef_last_error", "fef_destroy",
-            "fef_measure_fma_peak", "fef_fragment_rhf_noalloc", "fef_history"]
+            "fef_measure_fma_peak", "fef_fragment_rhf_noalloc", "fef_history", "fef_mlp_create", "fef_mlp_destroy",
+            "fef_mlp_params", "fef_mlp_set_scaling", "fef_mlp_loss_grad", "fef_mlp_train", "fef_mlp_predict",
+            "fef_mlp_last_error", "fef_learned_features", "fef_set_warm_start"]
 
 
 class FefError(RuntimeError):
@@ -92,10 +94,23 @@ def lib():
     L.fef_destroy.restype = None
     L.fef_measure_fma_peak.argtypes = [dp, dp, dp]
     L.fef_history.argtypes = [vp, ctypes.c_int32, dp, ip]
+    fp = ctypes.POINTER(ctypes.c_float)
+    L.fef_mlp_create.argtypes = [ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_uint64, vp, ctypes.POINTER(vp)]
+    L.fef_mlp_destroy.argtypes = [vp]
+    L.fef_mlp_destroy.restype = None
+    L.fef_mlp_params.argtypes = [vp, fp, i64p, ctypes.c_int32]
+    L.fef_mlp_set_scaling.argtypes = [vp, fp, fp, fp, fp]
+    L.fef_mlp_loss_grad.argtypes = [vp, vp, vp, ctypes.c_int32, fp, vp]
+    L.fef_mlp_train.argtypes = [vp, vp, vp, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_float, fp]
+    L.fef_mlp_predict.argtypes = [vp, vp, vp, ctypes.c_int32]
+    L.fef_mlp_last_error.argtypes = [vp]
+    L.fef_mlp_last_error.restype = ctypes.c_char_p
+    L.fef_learned_features.argtypes = [vp, vp, vp, vp, ctypes.c_int, ip, ip]
+    L.fef_set_warm_start.argtypes = [vp, vp]
     L.fef_fragment_rhf_noalloc.argtypes = [ctypes.c_int32, ip, ip, dp, vp, vp, vp, vp, vp, vp, vp, vp,
                                            ctypes.POINTER(fef_options), vp]
     for name in EXPORTED:
-        if name not in ("fef_default_options", "fef_last_error", "fef_destroy"):
+        if name not in ("fef_default_options", "fef_last_error", "fef_destroy", "fef_mlp_destroy", "fef_mlp_last_error"):
             getattr(L, name).restype = ctypes.c_int
     _lib = L
     return L
@@ -294,3 +309,99 @@ def fef_fragment_rhf_noalloc(n_ao, n_occ, e_nn, S, h, omega, eri_c, D_start, D_o
                                           _ptr(enn, ctypes.c_double), dev(S), dev(h), dev(omega), dev(eri_c),
                                           dev(D_start), dev(D_out), dev(F_out), dev(E_scf), ctypes.byref(opt), s),
            None)
+
+
+# ------------------------------------------------------------------------------------------ learned warm start
+
+def _mlp_check(status, m):
+    if status != FEF_OK:
+        msg = lib().fef_mlp_last_error(m.ptr if m is not None else None)
+        raise FefError(status, msg.decode() if msg else "")
+
+
+class Mlp:
+    """Owns a fef_mlp (the warm-start network)."""
+
+    def __init__(self, ptr, n_in, n_hidden, n_out):
+        self.ptr = ctypes.c_void_p(ptr)
+        self.n_in, self.n_hidden, self.n_out = n_in, n_hidden, n_out
+
+    def close(self):
+        if self.ptr:
+            lib().fef_mlp_destroy(self.ptr)
+            self.ptr = ctypes.c_void_p(None)
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def fef_mlp_create(n_in, n_hidden, n_out, seed=0, stream=None) -> Mlp:
+    out = ctypes.c_void_p()
+    _check(lib().fef_mlp_create(n_in, n_hidden, n_out, seed, ctypes.c_void_p(stream) if stream else None,
+                                ctypes.byref(out)), None)
+    return Mlp(out.value, n_in, n_hidden, n_out)
+
+
+def fef_mlp_params(m: Mlp, params=None):
+    """Returns the flat parameters (float32 numpy); sets them first when params is given."""
+    n = ctypes.c_int64(0)
+    _mlp_check(lib().fef_mlp_params(m.ptr, None, ctypes.byref(n), 0), m)
+    if params is not None:
+        p = np.ascontiguousarray(params, np.float32)
+        assert p.shape[0] == n.value
+        _mlp_check(lib().fef_mlp_params(m.ptr, _ptr(p, ctypes.c_float), None, 1), m)
+    out = np.zeros(n.value, np.float32)
+    _mlp_check(lib().fef_mlp_params(m.ptr, _ptr(out, ctypes.c_float), None, 0), m)
+    return out
+
+
+def fef_mlp_set_scaling(m: Mlp, in_shift, in_scale, out_shift, out_scale):
+    arrs = [np.ascontiguousarray(a, np.float32) for a in (in_shift, in_scale, out_shift, out_scale)]
+    _mlp_check(lib().fef_mlp_set_scaling(m.ptr, *[_ptr(a, ctypes.c_float) for a in arrs]), m)
+
+
+def fef_mlp_loss_grad(m: Mlp, X, T, grad=None):
+    """X, T, grad: CUDA float32 tensors.  Returns the loss."""
+    loss = ctypes.c_float(0)
+    g = ctypes.c_void_p(grad.data_ptr()) if grad is not None else None
+    _mlp_check(lib().fef_mlp_loss_grad(m.ptr, ctypes.c_void_p(X.data_ptr()), ctypes.c_void_p(T.data_ptr()),
+                                       int(X.shape[0]), ctypes.byref(loss), g), m)
+    return loss.value
+
+
+def fef_mlp_train(m: Mlp, X, T, epochs, batch=256, lr=1e-3):
+    loss = ctypes.c_float(0)
+    _mlp_check(lib().fef_mlp_train(m.ptr, ctypes.c_void_p(X.data_ptr()), ctypes.c_void_p(T.data_ptr()),
+                                   int(X.shape[0]), int(epochs), int(batch), float(lr), ctypes.byref(loss)), m)
+    return loss.value
+
+
+def fef_mlp_predict(m: Mlp, X, Y):
+    _mlp_check(lib().fef_mlp_predict(m.ptr, ctypes.c_void_p(X.data_ptr()), ctypes.c_void_p(Y.data_ptr()),
+                                     int(X.shape[0])), m)
+    return Y
+
+
+def fef_learned_features(ctx: Context, D=None, want_X=True, want_Y=True):
+    """(X [n_frag x n_feat], Y_local [n_frag x n_pack]) as host float32 arrays for densities D
+    (packed host array, or None for the current densities)."""
+    nf, npk = ctypes.c_int32(0), ctypes.c_int32(0)
+    _check(lib().fef_learned_features(ctx.ptr, None, None, None, 0, ctypes.byref(nf), ctypes.byref(npk)), ctx.ptr)
+    if nf.value == 0:
+        raise FefError(FEF_ERR_ARG, "fragments are not of one kind: no learned features")
+    X = np.zeros((ctx.n_frag, nf.value), np.float32) if want_X else None
+    Y = np.zeros((ctx.n_frag, npk.value), np.float32) if want_Y else None
+    Dp = None if D is None else ctypes.c_void_p(np.ascontiguousarray(D, np.float64).ctypes.data)
+    Dkeep = None if D is None else np.ascontiguousarray(D, np.float64)
+    if Dkeep is not None:
+        Dp = ctypes.c_void_p(Dkeep.ctypes.data)
+    _check(lib().fef_learned_features(ctx.ptr, Dp, _ptr(X, ctypes.c_float) if X is not None else None,
+                                      _ptr(Y, ctypes.c_float) if Y is not None else None, 0, None, None), ctx.ptr)
+    return X, Y
+
+
+def fef_set_warm_start(ctx: Context, m: Mlp | None):
+    _check(lib().fef_set_warm_start(ctx.ptr, m.ptr if m is not None else None), ctx.ptr)

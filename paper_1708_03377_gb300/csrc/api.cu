@@ -66,6 +66,7 @@ struct Buffers {
     double* Dh_ref[kClasses] = {};
     double* Jh_ref[kClasses] = {};
     bool have_ref = false;
+    bool ref_exact = false;  // the reference field came from an FP64 build
     float* boys32 = nullptr;
     int* iters = nullptr;
     int* err_flag = nullptr;
@@ -76,6 +77,13 @@ struct Buffers {
     int2* tiles[kClasses][kClasses] = {};
     int n_tiles[kClasses * kClasses] = {};
     unsigned long long* qcount = nullptr;
+    // learned warm start
+    double* rot = nullptr;
+    double* Sh = nullptr;   // S^{1/2} per fragment (packed)
+    double* Sih = nullptr;  // S^{-1/2} per fragment (packed)
+    double* D_iso = nullptr;
+    float* Xd = nullptr;
+    float* Yd = nullptr;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr, ev2 = nullptr, ev3 = nullptr;
 };
 
@@ -154,19 +162,28 @@ static void clear_flags(fef_ctx* c)
 //   fp32 = false: full FP64 J-engine; the Hermite density and field become the mixed-precision
 //                 reference (D_ref, J[D_ref]).
 //   fp32 = true : incremental J[D] = J[D_ref] + J_fp32[D - D_ref] (needs a reference).
-static void build_fock_internal(fef_ctx* c, bool fp32 = false)
+// Kinds of Fock build.  FP64: the J-engine in FP64; its field becomes the exact reference.
+// FP32_INC: J[D] = J[D_ref] + J_fp32[D - D_ref] with the stored reference (falls back to FP64 when
+// there is none).  FP32_REF: the whole field from the FP32 core (D_ref = 0); it becomes an inexact
+// reference, whose error is then the same for every later increment relative to it.
+enum BuildKind { kBuildFP64 = 0, kBuildFP32Inc = 1, kBuildFP32Ref = 2 };
+
+static void build_fock_internal(fef_ctx* c, int kind = kBuildFP64)
 {
     Buffers* b = c->buf;
     const Dev& d = c->dev;
     cudaStream_t s = c->stream;
-    if (fp32 && !b->have_ref) fp32 = false;
+    if (kind == kBuildFP32Inc && !b->have_ref) kind = kBuildFP64;
+    const bool fp32 = kind != kBuildFP64;
     ck(launch_hermite_density(d, b->D, s), "hermite density");
     for (int L = 0; L < kClasses; ++L) {
         if (b->njh[L] == 0) continue;
-        if (fp32)
+        if (kind == kBuildFP32Inc)
             ck(cudaMemcpyAsync(b->Jh[L], b->Jh_ref[L], sizeof(double) * b->njh[L], cudaMemcpyDeviceToDevice, s), "Jh");
         else
             ck(cudaMemsetAsync(b->Jh[L], 0, sizeof(double) * b->njh[L], s), "zero Jh");
+        if (kind == kBuildFP32Ref)
+            ck(cudaMemsetAsync(b->Dh_ref[L], 0, sizeof(double) * b->njh[L], s), "zero reference");
     }
     if (fp32) ck(launch_delta_density(d, b->Dh_ref, s), "delta density");
     const int2* tiles[kClasses][kClasses];
@@ -175,7 +192,7 @@ static void build_fock_internal(fef_ctx* c, bool fp32 = false)
     ck(cudaEventRecord(b->ev0, s), "event");
     ck(launch_jengine(d, tiles, b->n_tiles, c->opt.schwarz, fp32 ? 1 : 0, s), "J-engine");
     ck(cudaEventRecord(b->ev1, s), "event");
-    if (!fp32) {
+    if (kind != kBuildFP32Inc) {
         for (int L = 0; L < kClasses; ++L) {
             if (b->njh[L] == 0) continue;
             ck(cudaMemcpyAsync(b->Jh_ref[L], b->Jh[L], sizeof(double) * b->njh[L], cudaMemcpyDeviceToDevice, s), "ref");
@@ -183,6 +200,7 @@ static void build_fock_internal(fef_ctx* c, bool fp32 = false)
                "ref");
         }
         b->have_ref = true;
+        b->ref_exact = kind == kBuildFP64;
     }
     c->last_build_fp32 = fp32;
     ck(launch_back_transform(d, b->Jenv, s), "back-transform");
@@ -499,6 +517,17 @@ extern "C" fef_status fef_create(const fef_geometry* g, const fef_basis* bs, con
         b->S = b->alloc<double>(c->mat_total, "S");
         b->h = b->alloc<double>(c->mat_total, "h");
         ck(launch_one_electron(d, b->S, b->h, s), "one-electron");
+        b->rot = b->alloc<double>((size_t)9 * nf, "frames");
+        ck(launch_frames(d, b->rot, s), "frames");
+        {  // the learned warm start needs fragments of one kind (same atoms and s/p basis)
+            bool uniform = true;
+            for (int x = 1; x < nf && uniform; ++x) uniform = frag_nat[x] == frag_nat[0] && frag_nao[x] == frag_nao[0];
+            if (uniform && max_l <= 1) {
+                c->learn_desc = 4 * frag_nat[0];
+                c->learn_pack = frag_nao[0] * (frag_nao[0] + 1) / 2;
+                c->learn_feat = c->learn_desc + c->learn_pack;  // + the environment operator omega
+            }
+        }
         // neighbour list (within the cutoff) -> pairs x<y and CSR
         std::vector<unsigned char> flags((size_t)nf * nf, 0);
         {
@@ -582,7 +611,9 @@ extern "C" fef_status fef_create(const fef_geometry* g, const fef_basis* bs, con
         }
         b->X = b->alloc<double>(c->mat_total, "X");
         b->nmo = b->alloc<int>(nf, "nmo");
-        ck(launch_orthogonaliser(d, b->S, b->X, b->nmo, 1e-7, max_nao, s), "orthogonaliser");
+        b->Sh = b->alloc<double>(c->mat_total, "S^1/2");
+        b->Sih = b->alloc<double>(c->mat_total, "S^-1/2");
+        ck(launch_orthogonaliser(d, b->S, b->X, b->nmo, 1e-7, max_nao, s, b->Sh, b->Sih), "orthogonaliser");
         c->nmo.assign(nf, 0);
         ck(cudaMemcpyAsync(c->nmo.data(), b->nmo, sizeof(int) * nf, cudaMemcpyDeviceToHost, s), "nmo");
         ck(cudaStreamSynchronize(s), "create");
@@ -729,7 +760,7 @@ extern "C" fef_status fef_build_fock(fef_ctx* c, const double* D, double* F_out,
     }
     require(c->have_density, FEF_ERR_ARG, "fef_build_fock: no densities given or set");
     clear_flags(c);
-    build_fock_internal(c, c->opt.precision == FEF_MIXED);
+    build_fock_internal(c, c->opt.precision == FEF_MIXED && c->buf->ref_exact ? kBuildFP32Inc : kBuildFP64);
     if (F_out) copy_packed(c, F_out, c->buf->F, on_device, cudaMemcpyDeviceToHost);
     check_device_flags(c, "fef_build_fock");
     float ms = 0.f;
@@ -748,6 +779,94 @@ static void read_energies(fef_ctx* c, std::vector<double>& Ex, double& Et)
     ck(cudaStreamSynchronize(c->stream), "energies");
 }
 
+static void ensure_learn_buffers(fef_ctx* c)
+{
+    require(c->learn_feat > 0, FEF_ERR_ARG,
+            "learned warm start: fragments must all be of one kind (same atoms, s/p basis)");
+    Buffers* b = c->buf;
+    if (!b->Xd) {
+        b->Xd = b->alloc<float>((size_t)c->n_frag * c->learn_feat, "learned X");
+        b->Yd = b->alloc<float>((size_t)c->n_frag * c->learn_pack, "learned Y");
+        b->D_iso = b->alloc<double>(c->mat_total, "D_iso");
+    }
+}
+
+// Features of the current densities into b->Xd: potential and field at the atoms (columns
+// [0, learn_desc)) and the environment operator omega of a Fock build of the current densities in
+// the Loewdin basis and molecule-fixed frame (columns [learn_desc, learn_feat)).  The features are
+// FP32 network inputs, so omega comes from an FP32-core build.
+static void compute_features(fef_ctx* c)
+{
+    Buffers* b = c->buf;
+    build_fock_internal(c, kBuildFP32Ref);  // omega of the current densities (and their Hermite densities)
+    ck(launch_descriptors(c->dev, b->rot, c->learn_feat, b->Xd, c->stream), "descriptors");
+    ck(launch_local_density(c->dev, b->rot, b->Sih, b->omega, c->learn_feat, c->learn_desc, b->Xd, c->stream),
+       "environment operator");
+}
+
+// D <- D_iso + S^{-1/2} B f(features(D_iso)) B^T S^{-1/2}: the current densities are the isolated ones.
+static void learned_start(fef_ctx* c)
+{
+    ensure_learn_buffers(c);
+    Buffers* b = c->buf;
+    require(mlp_n_in(c->warm_start) == c->learn_feat && mlp_n_out(c->warm_start) == c->learn_pack, FEF_ERR_ARG,
+            "warm-start network dimensions do not match the fragments");
+    ck(cudaMemcpyAsync(b->D_iso, b->D, sizeof(double) * c->mat_total, cudaMemcpyDeviceToDevice, c->stream), "D_iso");
+    compute_features(c);
+    ck(cudaStreamSynchronize(c->stream), "descriptors");
+    ck(mlp_predict_device(c->warm_start, b->Xd, b->Yd, c->n_frag), "warm-start network");
+    ck(cudaDeviceSynchronize(), "warm-start network");
+    ck(launch_apply_learned(c->dev, b->rot, b->Sih, b->D_iso, b->Yd, c->learn_pack, b->D, c->stream), "apply learned");
+    c->energies_valid = false;
+}
+
+extern "C" fef_status fef_set_warm_start(fef_ctx* c, fef_mlp* m)
+{
+    if (!c) return FEF_ERR_ARG;
+    FEF_API_BEGIN
+    if (m) {
+        require(c->learn_feat > 0, FEF_ERR_ARG,
+                "learned warm start: fragments must all be of one kind (same atoms, s/p basis)");
+        require(mlp_n_in(m) == c->learn_feat && mlp_n_out(m) == c->learn_pack, FEF_ERR_ARG,
+                "warm-start network dimensions do not match the fragments");
+    }
+    c->warm_start = m;
+    return FEF_OK;
+    FEF_API_END(c)
+}
+
+extern "C" fef_status fef_learned_features(fef_ctx* c, const double* D, float* X, float* Y_local, int on_device,
+                                           int32_t* n_feat, int32_t* n_pack)
+{
+    if (!c) return FEF_ERR_ARG;
+    FEF_API_BEGIN
+    if (n_feat) *n_feat = c->learn_feat;
+    if (n_pack) *n_pack = c->learn_pack;
+    if (!X && !Y_local) return FEF_OK;
+    ensure_learn_buffers(c);
+    Buffers* b = c->buf;
+    if (D) {
+        copy_packed(c, b->D, D, on_device, cudaMemcpyHostToDevice);
+        c->have_density = true;
+        c->energies_valid = false;
+    }
+    require(c->have_density, FEF_ERR_ARG, "fef_learned_features: no densities given or set");
+    const size_t nx = (size_t)c->n_frag * c->learn_feat, ny = (size_t)c->n_frag * c->learn_pack;
+    if (X) {
+        compute_features(c);
+        ck(cudaMemcpyAsync(X, b->Xd, sizeof(float) * nx, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                           c->stream), "X");
+    }
+    if (Y_local) {
+        ck(launch_local_density(c->dev, b->rot, b->Sh, b->D, c->learn_pack, 0, b->Yd, c->stream), "local density");
+        ck(cudaMemcpyAsync(Y_local, b->Yd, sizeof(float) * ny,
+                           on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, c->stream), "Y");
+    }
+    ck(cudaStreamSynchronize(c->stream), "learned features");
+    return FEF_OK;
+    FEF_API_END(c)
+}
+
 extern "C" fef_status fef_iterate(fef_ctx* c, int32_t* n_macro_out, double* final_dE_out)
 {
     if (!c) return FEF_ERR_ARG;
@@ -764,12 +883,26 @@ extern "C" fef_status fef_iterate(fef_ctx* c, int32_t* n_macro_out, double* fina
         if (flag & kErrNotConv) throw Error{FEF_ERR_NOT_CONVERGED, "isolated-fragment RHF did not converge"};
         c->have_density = true;
     } else {
-        throw Error{FEF_ERR_ARG, "fef_iterate: learned start needs the MLP warm start (not in this build)"};
+        // learned: isolated-fragment RHF, then D = D_iso + the network's predicted change from the
+        // environment potential and field at each atom (molecule-fixed frames)
+        require(c->warm_start != nullptr, FEF_ERR_ARG, "fef_iterate: start=LEARNED needs fef_set_warm_start");
+        run_scf(c, false, false);
+        int flag = 0;
+        ck(cudaMemcpyAsync(&flag, c->buf->err_flag, sizeof(int), cudaMemcpyDeviceToHost, c->stream), "flags");
+        ck(cudaStreamSynchronize(c->stream), "isolated RHF");
+        if (flag & kErrNotConv) throw Error{FEF_ERR_NOT_CONVERGED, "isolated-fragment RHF did not converge"};
+        learned_start(c);
+        c->have_density = true;
     }
     double it_max = 0, it_sum = 0, scf_ms = 0;
-    if (o.start == FEF_START_SUPERPOSITION) scf_counts(c, it_max, it_sum, scf_ms);
+    if (o.start != FEF_START_GIVEN) scf_counts(c, it_max, it_sum, scf_ms);
     check_device_flags(c, "fef_iterate start");
-    build_fock_internal(c);
+    // MIXED: from a superposition (or given) start the first field is an FP32-core reference and
+    // the coarse phase follows; a learned start is already close to self-consistency, so its first
+    // field is the FP64 reference and the fine phase starts at once.
+    const bool mixed = (o.precision == FEF_MIXED);
+    const bool learned = (o.start == FEF_START_LEARNED);
+    build_fock_internal(c, mixed && !learned ? kBuildFP32Ref : kBuildFP64);
     std::vector<double> Ex_old, Ex;
     double Et_old = 0, Et = 0, dE = 0;
     read_energies(c, Ex_old, Et_old);
@@ -777,20 +910,27 @@ extern "C" fef_status fef_iterate(fef_ctx* c, int32_t* n_macro_out, double* fina
     {
         float ms0 = 0.f;
         ck(cudaEventElapsedTime(&ms0, c->buf->ev0, c->buf->ev1), "event time");
-        double rec[kHistoryFields] = {0, Et_old, 0, 0, it_max, it_sum, ms0, scf_ms, 0};
+        double rec[kHistoryFields] = {0, Et_old, 0, 0, it_max, it_sum, ms0, scf_ms, c->last_build_fp32 ? 1.0 : 0.0};
         c->history.insert(c->history.end(), rec, rec + kHistoryFields);
     }
     int k = 0;
     bool conv = false;
     float jms = 0.f;
-    // MIXED: FP32-core incremental builds while |dE| >= mixed_switch, then FP64 builds; convergence is
-    // only declared between two consecutive FP64 energies.
-    bool fp32_phase = (o.precision == FEF_MIXED);
-    bool prev_fp64 = true;
+    // MIXED: a coarse phase of FP32-core increments relative to the FP32 reference field, until
+    // |dE| < mixed_switch or the energy change stops decreasing; then one FP64 build becomes the
+    // exact reference and the fine phase continues with FP32 increments relative to it, whose error
+    // (it grows with |D - D_ref|) is now far below e_tol.  Convergence is declared only between two
+    // consecutive accurate energies (FP64, or FP32 increments on an exact reference); a stalled fine
+    // phase refreshes the reference again.
+    bool fine = !mixed || learned;
+    bool next_fp32 = mixed;
+    bool prev_acc = !c->last_build_fp32;
+    double dE_prev = 1e300;
     for (k = 1; k <= o.max_macro; ++k) {
         run_scf(c, true, true);
-        build_fock_internal(c, fp32_phase);
+        build_fock_internal(c, next_fp32 ? kBuildFP32Inc : kBuildFP64);
         const bool this_fp64 = !c->last_build_fp32;
+        const bool this_acc = this_fp64 || (fine && c->buf->ref_exact);
         read_energies(c, Ex, Et);
         scf_counts(c, it_max, it_sum, scf_ms);
         float ms = 0.f;
@@ -813,12 +953,24 @@ extern "C" fef_status fef_iterate(fef_ctx* c, int32_t* n_macro_out, double* fina
         }
         Ex_old = Ex;
         Et_old = Et;
-        if (fp32_phase && dE < o.mixed_switch && dEx < o.mixed_switch) fp32_phase = false;
-        if (this_fp64 && prev_fp64 && dE < o.e_tol && dEx < o.e_tol) {
+        if (this_acc && prev_acc && dE < o.e_tol && dEx < o.e_tol) {
             conv = true;
             break;
         }
-        prev_fp64 = this_fp64;
+        if (mixed) {
+            if (!fine) {
+                if ((dE < o.mixed_switch && dEx < o.mixed_switch) || dE > dE_prev) {
+                    fine = true;        // refresh the FP64 reference next
+                    next_fp32 = false;
+                }
+            } else if (this_fp64) {
+                next_fp32 = true;       // fine increments relative to the fresh reference
+            } else if (dE > dE_prev) {
+                next_fp32 = false;      // stalled: refresh again
+            }
+        }
+        prev_acc = this_acc;
+        dE_prev = dE;
     }
     c->jengine_ms = jms;
     if (n_macro_out) *n_macro_out = conv ? k : o.max_macro;

@@ -124,6 +124,9 @@ struct fef_ctx {
     std::vector<double> history;
     bool have_density = false;
     bool last_build_fp32 = false;
+    fef_mlp* warm_start = nullptr;  // network used when start = FEF_START_LEARNED (not owned)
+    int learn_feat = 0, learn_pack = 0;  // 0: fragments not uniform or have d shells
+    int learn_desc = 0;                  // potential/field part of the features (4 per atom)
     bool energies_valid = false;
     std::string last_error;
 };
@@ -152,8 +155,9 @@ cudaError_t launch_neighbours(const Dev& d, double cutoff_bohr, unsigned char* f
 cudaError_t launch_nuclear_env(const Dev& d, double* vh[kClasses], double* V, cudaStream_t s);
 cudaError_t launch_nuclear_traces(const Dev& d, const double* D, double* trace_xy, double* trace_yx, cudaStream_t s);
 cudaError_t launch_nuclear_repulsion(const Dev& d, double* e_nn_intra, double* e_nn_pair, cudaStream_t s);
+// X = U s^{-1/2} (canonical); optionally S^{1/2} and S^{-1/2} (symmetric) into Sh, Sih
 cudaError_t launch_orthogonaliser(const Dev& d, const double* S, double* X, int* nmo, double s_min, int max_n,
-                                  cudaStream_t s);
+                                  cudaStream_t s, double* Sh = nullptr, double* Sih = nullptr);
 cudaError_t launch_hermite_density(const Dev& d, const double* D, cudaStream_t s);
 // FP64 J-engine (fp32 = 0) on pp_Dh, or the FP32-core J-engine (fp32 = 1) on pp_Dh32; both add
 // into the FP64 accumulators pp_Jh.
@@ -200,5 +204,16 @@ cudaError_t launch_energies(const Dev& d, const double* E_int, const double* trV
 cudaError_t launch_check_finite(const double* a, int64_t n, int* flag, cudaStream_t s);
 
 cudaError_t measure_fma_peak(double* fp64, double* fp32, double* mhz);
+
+// learned warm start (learned.cu, mlp.cu)
+cudaError_t launch_frames(const Dev& d, double* rot, cudaStream_t s);
+cudaError_t launch_descriptors(const Dev& d, const double* rot, int n_feat, float* X, cudaStream_t s);
+cudaError_t launch_local_density(const Dev& d, const double* rot, const double* Sh, const double* D, int stride,
+                                 int col0, float* out, cudaStream_t s);
+cudaError_t launch_apply_learned(const Dev& d, const double* rot, const double* Sih, const double* D_iso,
+                                 const float* dloc, int n_pack, double* D, cudaStream_t s);
+cudaError_t mlp_predict_device(fef_mlp* m, const float* X, float* Y, int n);
+int mlp_n_in(const fef_mlp* m);
+int mlp_n_out(const fef_mlp* m);
 
 }  // namespace fef

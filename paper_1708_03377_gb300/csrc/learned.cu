@@ -1,0 +1,295 @@
+// Inputs and outputs of the learned warm start, in each fragment's molecule-fixed frame.
+//
+// Frame of fragment x: e1 along R_1 - R_0, e2 the part of R_2 - R_0 orthogonal to e1, e3 = e1 x e2
+// (atoms in input order); the rotation Rot has these axes as columns, r_global = Rot r_local.
+// Descriptors: at every atom A of x, the electrostatic potential and field of all neighbour
+// fragments y in N(x) (their nuclei and their electron densities D^y), the field rotated into the
+// frame:   phi(A) = sum_{B in y} Z_B/|A-B| - sum_Q sum_tuv Dt_Q[tuv] (2 pi/q) R_tuv(q, Q - A),
+//          E(A)   = sum_{B in y} Z_B (A-B)/|A-B|^3 - sum_Q sum_tuv Dt_Q[tuv] (2 pi/q) R_{t+e}(q, Q - A),
+// with Dt_Q the Hermite density of primitive pair Q (McMurchie-Davidson, as in the J-engine).
+// Densities in the frame and in the Loewdin basis: with B the AO transformation of the frame (1 for
+// s, Rot for p; orthogonal), D_local = B^T S^{1/2} D S^{1/2} B and back D = S^{-1/2} B D_local B^T
+// S^{-1/2}.  The Loewdin basis keeps the learned quantity well conditioned: in the AO basis a
+// density change is dominated by near-linearly-dependent directions of S.
+#include "common.cuh"
+#include "internal.hpp"
+
+namespace fef {
+
+__global__ void k_frames(Dev d, double* rot)
+{
+    int x = blockIdx.x * blockDim.x + threadIdx.x;
+    if (x >= d.n_frag) return;
+    const int a0 = d.frag_atom0[x], nat = d.frag_nat[x];
+    double e1[3] = {1, 0, 0}, e2[3] = {0, 1, 0}, e3[3] = {0, 0, 1};
+    if (nat >= 2) {
+        const double* A = d.atom_xyz + 3 * a0;
+        const double* B = d.atom_xyz + 3 * (a0 + 1);
+        double n = 0;
+        for (int k = 0; k < 3; ++k) { e1[k] = B[k] - A[k]; n += e1[k] * e1[k]; }
+        n = sqrt(n);
+        for (int k = 0; k < 3; ++k) e1[k] /= n;
+        double v[3];
+        if (nat >= 3) {
+            const double* C = d.atom_xyz + 3 * (a0 + 2);
+            for (int k = 0; k < 3; ++k) v[k] = C[k] - A[k];
+        } else {
+            v[0] = fabs(e1[0]) < 0.9 ? 1.0 : 0.0;
+            v[1] = fabs(e1[0]) < 0.9 ? 0.0 : 1.0;
+            v[2] = 0.0;
+        }
+        double dot = v[0] * e1[0] + v[1] * e1[1] + v[2] * e1[2];
+        n = 0;
+        for (int k = 0; k < 3; ++k) { e2[k] = v[k] - dot * e1[k]; n += e2[k] * e2[k]; }
+        n = sqrt(n);
+        for (int k = 0; k < 3; ++k) e2[k] /= n;
+        e3[0] = e1[1] * e2[2] - e1[2] * e2[1];
+        e3[1] = e1[2] * e2[0] - e1[0] * e2[2];
+        e3[2] = e1[0] * e2[1] - e1[1] * e2[0];
+    }
+    double* R = rot + 9 * x;  // row-major, columns = local axes
+    for (int k = 0; k < 3; ++k) {
+        R[3 * k + 0] = e1[k];
+        R[3 * k + 1] = e2[k];
+        R[3 * k + 2] = e3[k];
+    }
+}
+
+// potential and field at point A from the Hermite density of one primitive pair (class L <= 4)
+__device__ inline void pair_potential(const Dev& d, int L, int g, const double* A, double& phi, double* E)
+{
+    const double4_32a Q = d.pp_P[L][g];
+    const double q = Q.w;
+    const double X = Q.x - A[0], Y = Q.y - A[1], Z = Q.z - A[2];
+    const int L1 = L + 1;
+    double F[kMaxLPair + 2], base[kMaxLPair + 2], R[nh(kMaxLPair + 1)];
+    boys_fp64_rt(d.boys, q * (X * X + Y * Y + Z * Z), L1, F);
+    double f = 2.0 * kPi / q;
+    for (int n = 0; n <= L1; ++n) {
+        base[n] = f * F[n];
+        f *= -2.0 * q;
+    }
+    md_R_rt(L1, R, base, X, Y, Z);
+    const int npp = d.n_pp[L];
+    const double sc = q / kSqrt2Pi52;  // Dh holds D K c/q
+    for (int k = 0; k < nh(L); ++k) {
+        const TUV c = htuv(k);
+        const double Dt = d.pp_Dh[L][(size_t)k * npp + g] * sc;
+        phi -= Dt * R[k];
+        E[0] -= Dt * R[hidx(c.t + 1, c.u, c.v)];
+        E[1] -= Dt * R[hidx(c.t, c.u + 1, c.v)];
+        E[2] -= Dt * R[hidx(c.t, c.u, c.v + 1)];
+    }
+}
+
+// X[x][4a + (0..3)] = (phi, E_local) at atom a of fragment x.  One block per fragment; for each atom
+// the block's threads split every neighbour's nuclei and primitive pairs, then a block reduction.
+__global__ void __launch_bounds__(256) k_descriptors(Dev d, const double* rot, int n_feat, float* X)
+{
+    __shared__ double red[8][4];
+    const int x = blockIdx.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int nat = d.frag_nat[x];
+    const int c0 = d.frag_nbr0[x], c1 = d.frag_nbr0[x + 1];
+    for (int a = 0; a < nat; ++a) {
+        const double* A = d.atom_xyz + 3 * (d.frag_atom0[x] + a);
+        double v[4] = {0.0, 0.0, 0.0, 0.0};
+        for (int c = c0; c < c1; ++c) {
+            const int y = d.nbr[c];
+            const int naty = d.frag_nat[y];
+            int n_items = naty;
+            for (int L = 0; L < kClasses; ++L) n_items += d.frag_npp[y * kClasses + L];
+            for (int t = tid; t < n_items; t += blockDim.x) {
+                if (t < naty) {
+                    const double* B = d.atom_xyz + 3 * (d.frag_atom0[y] + t);
+                    const double Zb = d.atom_Z[d.frag_atom0[y] + t];
+                    const double dx = A[0] - B[0], dy = A[1] - B[1], dz = A[2] - B[2];
+                    const double r2 = dx * dx + dy * dy + dz * dz, r = sqrt(r2);
+                    const double f = Zb / (r2 * r);
+                    v[0] += Zb / r;
+                    v[1] += f * dx;
+                    v[2] += f * dy;
+                    v[3] += f * dz;
+                } else {
+                    int u = t - naty, L = 0;
+                    while (u >= d.frag_npp[y * kClasses + L]) u -= d.frag_npp[y * kClasses + L++];
+                    double phi = 0.0, E[3] = {0.0, 0.0, 0.0};
+                    pair_potential(d, L, d.frag_pp0[y * kClasses + L] + u, A, phi, E);
+                    v[0] += phi;
+                    v[1] += E[0];
+                    v[2] += E[1];
+                    v[3] += E[2];
+                }
+            }
+        }
+        for (int k = 0; k < 4; ++k) {
+            double w = v[k];
+            for (int o = 16; o > 0; o >>= 1) w += __shfl_xor_sync(0xffffffffu, w, o);
+            if (lane == 0) red[warp][k] = w;
+        }
+        __syncthreads();
+        if (tid == 0) {
+            double s4[4] = {0.0, 0.0, 0.0, 0.0};
+            for (int w = 0; w < (int)(blockDim.x >> 5); ++w)
+                for (int k = 0; k < 4; ++k) s4[k] += red[w][k];
+            const double* R = rot + 9 * x;
+            float* out = X + (size_t)x * n_feat + 4 * a;
+            out[0] = (float)s4[0];
+            for (int k = 0; k < 3; ++k)
+                out[1 + k] = (float)(R[0 * 3 + k] * s4[1] + R[1 * 3 + k] * s4[2] + R[2 * 3 + k] * s4[3]);
+        }
+        __syncthreads();
+    }
+}
+
+// B (n x n) of fragment x into shared memory: 1 on s functions, Rot on each p shell.
+__device__ inline void frame_ao_matrix(const Dev& d, int x, const double* Rt, double* B, int n)
+{
+    for (int e = threadIdx.x; e < n * n; e += blockDim.x) B[e] = 0.0;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int s = d.frag_sh0[x]; s < d.frag_sh0[x] + d.frag_nsh[x]; ++s) {
+            const int o = d.sh_ao[s];
+            if (d.sh_l[s] == 0) {
+                B[o * n + o] = 1.0;
+            } else {  // p (d shells are rejected by the caller)
+                for (int k = 0; k < 3; ++k)
+                    for (int m = 0; m < 3; ++m) B[(o + k) * n + o + m] = Rt[3 * k + m];
+            }
+        }
+    }
+    __syncthreads();
+}
+
+// out[x][packed i<=j] = (B^T S^{1/2} D S^{1/2} B)_ij, one block per fragment.  Passing S^{-1/2} as Sh
+// gives the Loewdin-basis form of an operator instead (S^{-1/2} F S^{-1/2}), so that tr(D F) is kept.
+// out row stride is `stride` floats, written from column `col0`.
+__global__ void k_local_density(Dev d, const double* rot, const double* Sh, const double* D, int stride, int col0,
+                                float* out)
+{
+    const int x = blockIdx.x;
+    const int n = d.frag_nao[x];
+    extern __shared__ double sm[];
+    double* B = sm;
+    double* T = B + n * n;
+    double* U = T + n * n;
+    frame_ao_matrix(d, x, rot + 9 * x, B, n);
+    const double* Dx = D + d.frag_moff[x];
+    const double* Hx = Sh + d.frag_moff[x];
+    for (int e = threadIdx.x; e < n * n; e += blockDim.x) {  // T = D S^{1/2}
+        int i = e / n, j = e % n;
+        double s = 0.0;
+        for (int k = 0; k < n; ++k) s += Dx[i * n + k] * Hx[k * n + j];
+        T[e] = s;
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < n * n; e += blockDim.x) {  // U = S^{1/2} T
+        int i = e / n, j = e % n;
+        double s = 0.0;
+        for (int k = 0; k < n; ++k) s += Hx[i * n + k] * T[k * n + j];
+        U[e] = s;
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < n * n; e += blockDim.x) {  // T = U B
+        int i = e / n, j = e % n;
+        double s = 0.0;
+        for (int k = 0; k < n; ++k) s += U[i * n + k] * B[k * n + j];
+        T[e] = s;
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < n * (n + 1) / 2; e += blockDim.x) {  // (B^T T)_ij, i <= j
+        int i = 0, r = e;
+        while (r >= n - i) { r -= n - i; ++i; }
+        int j = i + r;
+        double s = 0.0;
+        for (int k = 0; k < n; ++k) s += B[k * n + i] * T[k * n + j];
+        out[(size_t)x * stride + col0 + e] = (float)s;
+    }
+}
+
+// D = D_iso + S^{-1/2} B dL B^T S^{-1/2} with dL the packed local-frame Loewdin-basis density
+// change; one block per fragment.
+__global__ void k_apply_learned(Dev d, const double* rot, const double* Sih, const double* D_iso, const float* dloc,
+                                int n_pack, double* D)
+{
+    const int x = blockIdx.x;
+    const int n = d.frag_nao[x];
+    extern __shared__ double sm[];
+    double* B = sm;
+    double* M = B + n * n;
+    double* T = M + n * n;
+    frame_ao_matrix(d, x, rot + 9 * x, B, n);
+    const double* Gx = Sih + d.frag_moff[x];
+    for (int e = threadIdx.x; e < n * (n + 1) / 2; e += blockDim.x) {
+        int i = 0, r = e;
+        while (r >= n - i) { r -= n - i; ++i; }
+        int j = i + r;
+        double v = (double)dloc[(size_t)x * n_pack + e];
+        M[i * n + j] = v;
+        M[j * n + i] = v;
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < n * n; e += blockDim.x) {  // T = M B^T
+        int i = e / n, j = e % n;
+        double s = 0.0;
+        for (int k = 0; k < n; ++k) s += M[i * n + k] * B[j * n + k];
+        T[e] = s;
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < n * n; e += blockDim.x) {  // M = B T  (global-frame Loewdin change)
+        int i = e / n, j = e % n;
+        double s = 0.0;
+        for (int k = 0; k < n; ++k) s += B[i * n + k] * T[k * n + j];
+        M[e] = s;
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < n * n; e += blockDim.x) {  // T = M S^{-1/2}
+        int i = e / n, j = e % n;
+        double s = 0.0;
+        for (int k = 0; k < n; ++k) s += M[i * n + k] * Gx[k * n + j];
+        T[e] = s;
+    }
+    __syncthreads();
+    const int64_t mo = d.frag_moff[x];
+    for (int e = threadIdx.x; e < n * n; e += blockDim.x) {  // D = D_iso + S^{-1/2} T
+        int i = e / n, j = e % n;
+        double s = 0.0;
+        for (int k = 0; k < n; ++k) s += Gx[i * n + k] * T[k * n + j];
+        D[mo + e] = D_iso[mo + e] + s;
+    }
+}
+
+cudaError_t launch_frames(const Dev& d, double* rot, cudaStream_t s)
+{
+    k_frames<<<(d.n_frag + 127) / 128, 128, 0, s>>>(d, rot);
+    note_launches(1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_descriptors(const Dev& d, const double* rot, int n_feat, float* X, cudaStream_t s)
+{
+    k_descriptors<<<d.n_frag, 256, 0, s>>>(d, rot, n_feat, X);
+    note_launches(1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_local_density(const Dev& d, const double* rot, const double* Sh, const double* D, int stride,
+                                 int col0, float* out, cudaStream_t s)
+{
+    size_t smem = 3 * sizeof(double) * (size_t)d.max_nao * d.max_nao;
+    cudaFuncSetAttribute(k_local_density, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    k_local_density<<<d.n_frag, 128, smem, s>>>(d, rot, Sh, D, stride, col0, out);
+    note_launches(1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_apply_learned(const Dev& d, const double* rot, const double* Sih, const double* D_iso,
+                                 const float* dloc, int n_pack, double* D, cudaStream_t s)
+{
+    size_t smem = 3 * sizeof(double) * (size_t)d.max_nao * d.max_nao;
+    cudaFuncSetAttribute(k_apply_learned, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    k_apply_learned<<<d.n_frag, 128, smem, s>>>(d, rot, Sih, D_iso, dloc, n_pack, D);
+    note_launches(1);
+    return cudaGetLastError();
+}
+
+}  // namespace fef

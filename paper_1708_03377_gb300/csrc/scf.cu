@@ -151,7 +151,10 @@ __device__ void jacobi_eigh(double* A, double* V, int m, int ld, JacobiScratch* 
 }  // namespace
 
 // ------------------------------------------------------------------------------------------ X = U s^{-1/2}
-__global__ void k_orthogonaliser(Dev d, const double* S, double* X, int* nmo_out, double s_min)
+// Also, when Sh / Sih are given: the symmetric square roots S^{1/2} = U s^{1/2} U^T and
+// S^{-1/2} = U s^{-1/2} U^T (over s >= s_min), used to express densities in the Loewdin basis.
+__global__ void k_orthogonaliser(Dev d, const double* S, double* X, int* nmo_out, double s_min, double* Sh,
+                                 double* Sih)
 {
     const int x = blockIdx.x;
     const int n = d.frag_nao[x];
@@ -184,14 +187,29 @@ __global__ void k_orthogonaliser(Dev d, const double* S, double* X, int* nmo_out
         }
         Xx[e] = v;
     }
+    if (Sh || Sih) {
+        for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
+            int i = e / n, j = e % n;
+            double a = 0.0, b = 0.0;
+            for (int k = 0; k < n; ++k) {
+                double s = A[k * n + k];
+                if (s < s_min) continue;
+                double vv = V[i * n + k] * V[j * n + k];
+                a += vv * sqrt(s);
+                b += vv * rsqrt(s);
+            }
+            if (Sh) Sh[d.frag_moff[x] + e] = a;
+            if (Sih) Sih[d.frag_moff[x] + e] = b;
+        }
+    }
 }
 
 cudaError_t launch_orthogonaliser(const Dev& d, const double* S, double* X, int* nmo, double s_min, int max_n,
-                                  cudaStream_t s)
+                                  cudaStream_t s, double* Sh, double* Sih)
 {
     size_t smem = 2 * (size_t)max_n * max_n * sizeof(double);
     cudaFuncSetAttribute(k_orthogonaliser, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    k_orthogonaliser<<<d.n_frag, 256, smem, s>>>(d, S, X, nmo, s_min);
+    k_orthogonaliser<<<d.n_frag, 256, smem, s>>>(d, S, X, nmo, s_min, Sh, Sih);
     note_launches(1);
     return cudaGetLastError();
 }

@@ -411,3 +411,25 @@ def test_single_fragment_is_plain_rhf():
     for x in range(2):
         assert np.abs(res["D"][x] - iso[x]).max() < 1e-8
     assert res["n_macro"] == 1
+
+
+# ----------------------------------------------------------------------------------------- warm-start network
+
+def test_mlp_oracle_gradient_finite_differences():
+    """The oracle MLP's analytic gradient against central finite differences of its loss."""
+    from oracle import mlp
+    rng = np.random.default_rng(3)
+    n_in, n_h, n_out = 5, 7, 4
+    n_par = sum(int(np.prod(s)) for s in mlp.shapes(n_in, n_h, n_out))
+    theta = rng.standard_normal(n_par) * 0.4
+    X = rng.standard_normal((9, n_in))
+    T = rng.standard_normal((9, n_out))
+    L, g = mlp.loss_and_grad(theta, X, T, n_in, n_h, n_out)
+    h = 1e-6
+    for i in rng.choice(n_par, 25, replace=False):
+        tp, tm = theta.copy(), theta.copy()
+        tp[i] += h
+        tm[i] -= h
+        fd = (mlp.loss_and_grad(tp, X, T, n_in, n_h, n_out)[0] - mlp.loss_and_grad(tm, X, T, n_in, n_h, n_out)[0]) / (2 * h)
+        assert abs(fd - g[i]) < 1e-8 * max(1.0, abs(fd))
+    assert abs(L - np.mean((mlp.forward(theta, X, n_in, n_h, n_out)[0] - T) ** 2)) < 1e-14
