@@ -799,7 +799,7 @@ static void compute_features(fef_ctx* c)
 {
     Buffers* b = c->buf;
     build_fock_internal(c, kBuildFP32Ref);  // omega of the current densities (and their Hermite densities)
-    ck(launch_descriptors(c->dev, b->rot, c->learn_feat, b->Xd, c->stream), "descriptors");
+    ck(launch_descriptors(c->dev, b->rot, c->learn_feat, c->learn_desc / 4, b->Xd, c->stream), "descriptors");
     ck(launch_local_density(c->dev, b->rot, b->Sih, b->omega, c->learn_feat, c->learn_desc, b->Xd, c->stream),
        "environment operator");
 }
@@ -813,9 +813,7 @@ static void learned_start(fef_ctx* c)
             "warm-start network dimensions do not match the fragments");
     ck(cudaMemcpyAsync(b->D_iso, b->D, sizeof(double) * c->mat_total, cudaMemcpyDeviceToDevice, c->stream), "D_iso");
     compute_features(c);
-    ck(cudaStreamSynchronize(c->stream), "descriptors");
-    ck(mlp_predict_device(c->warm_start, b->Xd, b->Yd, c->n_frag), "warm-start network");
-    ck(cudaDeviceSynchronize(), "warm-start network");
+    ck(mlp_predict_device(c->warm_start, b->Xd, b->Yd, c->n_frag, c->stream), "warm-start network");
     ck(launch_apply_learned(c->dev, b->rot, b->Sih, b->D_iso, b->Yd, c->learn_pack, b->D, c->stream), "apply learned");
     c->energies_valid = false;
 }
@@ -907,17 +905,18 @@ extern "C" fef_status fef_iterate(fef_ctx* c, int32_t* n_macro_out, double* fina
     double Et_old = 0, Et = 0, dE = 0;
     read_energies(c, Ex_old, Et_old);
     c->history.clear();
+    float jms = 0.f;
     {
         float ms0 = 0.f;
         ck(cudaEventElapsedTime(&ms0, c->buf->ev0, c->buf->ev1), "event time");
         double rec[kHistoryFields] = {0, Et_old, 0, 0, it_max, it_sum, ms0, scf_ms, c->last_build_fp32 ? 1.0 : 0.0};
         c->history.insert(c->history.end(), rec, rec + kHistoryFields);
+        jms = ms0;
     }
     int k = 0;
     bool conv = false;
-    float jms = 0.f;
     // MIXED: a coarse phase of FP32-core increments relative to the FP32 reference field, until
-    // |dE| < mixed_switch or the energy change stops decreasing; then one FP64 build becomes the
+    // the energy changes fall below mixed_switch or stop decreasing; then one FP64 build becomes the
     // exact reference and the fine phase continues with FP32 increments relative to it, whose error
     // (it grows with |D - D_ref|) is now far below e_tol.  Convergence is declared only between two
     // consecutive accurate energies (FP64, or FP32 increments on an exact reference); a stalled fine
@@ -957,20 +956,23 @@ extern "C" fef_status fef_iterate(fef_ctx* c, int32_t* n_macro_out, double* fina
             conv = true;
             break;
         }
+        // progress measure: the larger of |dE_tot| and max_x |dE_x| (|dE_tot| alone can drop by
+        // cancellation between fragments and then rise again without any stall)
+        const double prog = std::max(dE, dEx);
         if (mixed) {
             if (!fine) {
-                if ((dE < o.mixed_switch && dEx < o.mixed_switch) || dE > dE_prev) {
+                if (prog < o.mixed_switch || prog > dE_prev) {
                     fine = true;        // refresh the FP64 reference next
                     next_fp32 = false;
                 }
             } else if (this_fp64) {
                 next_fp32 = true;       // fine increments relative to the fresh reference
-            } else if (dE > dE_prev) {
+            } else if (prog > dE_prev) {
                 next_fp32 = false;      // stalled: refresh again
             }
         }
         prev_acc = this_acc;
-        dE_prev = dE;
+        dE_prev = prog;
     }
     c->jengine_ms = jms;
     if (n_macro_out) *n_macro_out = conv ? k : o.max_macro;

@@ -207,12 +207,12 @@ cudaError_t measure_fma_peak(double* fp64, double* fp32, double* mhz);
 
 // learned warm start (learned.cu, mlp.cu)
 cudaError_t launch_frames(const Dev& d, double* rot, cudaStream_t s);
-cudaError_t launch_descriptors(const Dev& d, const double* rot, int n_feat, float* X, cudaStream_t s);
+cudaError_t launch_descriptors(const Dev& d, const double* rot, int n_feat, int max_nat, float* X, cudaStream_t s);
 cudaError_t launch_local_density(const Dev& d, const double* rot, const double* Sh, const double* D, int stride,
                                  int col0, float* out, cudaStream_t s);
 cudaError_t launch_apply_learned(const Dev& d, const double* rot, const double* Sih, const double* D_iso,
                                  const float* dloc, int n_pack, double* D, cudaStream_t s);
-cudaError_t mlp_predict_device(fef_mlp* m, const float* X, float* Y, int n);
+cudaError_t mlp_predict_device(fef_mlp* m, const float* X, float* Y, int n, cudaStream_t st);
 int mlp_n_in(const fef_mlp* m);
 int mlp_n_out(const fef_mlp* m);
 

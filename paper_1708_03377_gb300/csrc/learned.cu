@@ -55,89 +55,99 @@ __global__ void k_frames(Dev d, double* rot)
     }
 }
 
-// potential and field at point A from the Hermite density of one primitive pair (class L <= 4)
-__device__ inline void pair_potential(const Dev& d, int L, int g, const double* A, double& phi, double* E)
+// Potential and field at A from the Hermite density of one primitive pair of class L, in FP32
+// (the descriptors are FP32 network inputs): Boys, R recursion and contraction in FP32 on the
+// FP64-formed difference Q - A.
+template <int L>
+__device__ __forceinline__ void pair_potential32(const Dev& d, int g, const double* A, float* out)
 {
     const double4_32a Q = d.pp_P[L][g];
-    const double q = Q.w;
-    const double X = Q.x - A[0], Y = Q.y - A[1], Z = Q.z - A[2];
-    const int L1 = L + 1;
-    double F[kMaxLPair + 2], base[kMaxLPair + 2], R[nh(kMaxLPair + 1)];
-    boys_fp64_rt(d.boys, q * (X * X + Y * Y + Z * Z), L1, F);
-    double f = 2.0 * kPi / q;
-    for (int n = 0; n <= L1; ++n) {
+    const float q = (float)Q.w;
+    const float X = (float)(Q.x - A[0]), Y = (float)(Q.y - A[1]), Z = (float)(Q.z - A[2]);
+    float F[L + 2], base[L + 2], R[nh(L + 1)];
+    boys_fp32<L + 1>(d.boys32, q * (X * X + Y * Y + Z * Z), F);
+    float f = 2.0f * (float)kPi / q;
+#pragma unroll
+    for (int n = 0; n <= L + 1; ++n) {
         base[n] = f * F[n];
-        f *= -2.0 * q;
+        f *= -2.0f * q;
     }
-    md_R_rt(L1, R, base, X, Y, Z);
+    md_R<L + 1, float>(R, base, X, Y, Z);
     const int npp = d.n_pp[L];
-    const double sc = q / kSqrt2Pi52;  // Dh holds D K c/q
-    for (int k = 0; k < nh(L); ++k) {
-        const TUV c = htuv(k);
-        const double Dt = d.pp_Dh[L][(size_t)k * npp + g] * sc;
-        phi -= Dt * R[k];
-        E[0] -= Dt * R[hidx(c.t + 1, c.u, c.v)];
-        E[1] -= Dt * R[hidx(c.t, c.u + 1, c.v)];
-        E[2] -= Dt * R[hidx(c.t, c.u, c.v + 1)];
-    }
+    const double sc = Q.w / kSqrt2Pi52;  // Dh holds D K c/q
+    static_for<nh(L)>([&](auto kk) {
+        constexpr int k = decltype(kk)::value;
+        constexpr TUV c = htuv(k);
+        const float Dt = (float)(d.pp_Dh[L][(size_t)k * npp + g] * sc);
+        out[0] = fmaf(-Dt, R[k], out[0]);
+        out[1] = fmaf(-Dt, R[hidx(c.t + 1, c.u, c.v)], out[1]);
+        out[2] = fmaf(-Dt, R[hidx(c.t, c.u + 1, c.v)], out[2]);
+        out[3] = fmaf(-Dt, R[hidx(c.t, c.u, c.v + 1)], out[3]);
+    });
 }
 
-// X[x][4a + (0..3)] = (phi, E_local) at atom a of fragment x.  One block per fragment; for each atom
-// the block's threads split every neighbour's nuclei and primitive pairs, then a block reduction.
-__global__ void __launch_bounds__(256) k_descriptors(Dev d, const double* rot, int n_feat, float* X)
+// X[x][4a + (0..3)] = (phi, E_local) at atom a of fragment x.  One block per (fragment, atom); its
+// threads split every neighbour's nuclei and primitive pairs (terms in FP32, sums in FP64), then a
+// block reduction.
+constexpr int kDescThreads = 128;
+
+__global__ void __launch_bounds__(kDescThreads) k_descriptors(Dev d, const double* rot, int n_feat, int max_nat,
+                                                              float* X)
 {
-    __shared__ double red[8][4];
-    const int x = blockIdx.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int nat = d.frag_nat[x];
+    __shared__ double red[kDescThreads / 32][4];
+    const int x = blockIdx.x / max_nat, a = blockIdx.x % max_nat;
+    if (a >= d.frag_nat[x]) return;  // whole block leaves together
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int c0 = d.frag_nbr0[x], c1 = d.frag_nbr0[x + 1];
-    for (int a = 0; a < nat; ++a) {
-        const double* A = d.atom_xyz + 3 * (d.frag_atom0[x] + a);
-        double v[4] = {0.0, 0.0, 0.0, 0.0};
-        for (int c = c0; c < c1; ++c) {
-            const int y = d.nbr[c];
-            const int naty = d.frag_nat[y];
-            int n_items = naty;
-            for (int L = 0; L < kClasses; ++L) n_items += d.frag_npp[y * kClasses + L];
-            for (int t = tid; t < n_items; t += blockDim.x) {
-                if (t < naty) {
-                    const double* B = d.atom_xyz + 3 * (d.frag_atom0[y] + t);
-                    const double Zb = d.atom_Z[d.frag_atom0[y] + t];
-                    const double dx = A[0] - B[0], dy = A[1] - B[1], dz = A[2] - B[2];
-                    const double r2 = dx * dx + dy * dy + dz * dz, r = sqrt(r2);
-                    const double f = Zb / (r2 * r);
-                    v[0] += Zb / r;
-                    v[1] += f * dx;
-                    v[2] += f * dy;
-                    v[3] += f * dz;
-                } else {
-                    int u = t - naty, L = 0;
-                    while (u >= d.frag_npp[y * kClasses + L]) u -= d.frag_npp[y * kClasses + L++];
-                    double phi = 0.0, E[3] = {0.0, 0.0, 0.0};
-                    pair_potential(d, L, d.frag_pp0[y * kClasses + L] + u, A, phi, E);
-                    v[0] += phi;
-                    v[1] += E[0];
-                    v[2] += E[1];
-                    v[3] += E[2];
+    const double* A = d.atom_xyz + 3 * (d.frag_atom0[x] + a);
+    double v[4] = {0.0, 0.0, 0.0, 0.0};
+    for (int c = c0; c < c1; ++c) {
+        const int y = d.nbr[c];
+        const int naty = d.frag_nat[y];
+        int n_items = naty;
+        for (int L = 0; L < kClasses; ++L) n_items += d.frag_npp[y * kClasses + L];
+        for (int t = tid; t < n_items; t += kDescThreads) {
+            if (t < naty) {
+                const double* B = d.atom_xyz + 3 * (d.frag_atom0[y] + t);
+                const double Zb = d.atom_Z[d.frag_atom0[y] + t];
+                const double dx = A[0] - B[0], dy = A[1] - B[1], dz = A[2] - B[2];
+                const double r2 = dx * dx + dy * dy + dz * dz, r = sqrt(r2);
+                const double f = Zb / (r2 * r);
+                v[0] += Zb / r;
+                v[1] += f * dx;
+                v[2] += f * dy;
+                v[3] += f * dz;
+            } else {
+                int u = t - naty, L = 0;
+                while (u >= d.frag_npp[y * kClasses + L]) u -= d.frag_npp[y * kClasses + L++];
+                const int g = d.frag_pp0[y * kClasses + L] + u;
+                float o[4] = {0.f, 0.f, 0.f, 0.f};
+                switch (L) {
+                    case 0: pair_potential32<0>(d, g, A, o); break;
+                    case 1: pair_potential32<1>(d, g, A, o); break;
+                    case 2: pair_potential32<2>(d, g, A, o); break;
+                    case 3: pair_potential32<3>(d, g, A, o); break;
+                    default: pair_potential32<4>(d, g, A, o); break;
                 }
+                for (int k = 0; k < 4; ++k) v[k] += (double)o[k];
             }
         }
-        for (int k = 0; k < 4; ++k) {
-            double w = v[k];
-            for (int o = 16; o > 0; o >>= 1) w += __shfl_xor_sync(0xffffffffu, w, o);
-            if (lane == 0) red[warp][k] = w;
-        }
-        __syncthreads();
-        if (tid == 0) {
-            double s4[4] = {0.0, 0.0, 0.0, 0.0};
-            for (int w = 0; w < (int)(blockDim.x >> 5); ++w)
-                for (int k = 0; k < 4; ++k) s4[k] += red[w][k];
-            const double* R = rot + 9 * x;
-            float* out = X + (size_t)x * n_feat + 4 * a;
-            out[0] = (float)s4[0];
-            for (int k = 0; k < 3; ++k)
-                out[1 + k] = (float)(R[0 * 3 + k] * s4[1] + R[1 * 3 + k] * s4[2] + R[2 * 3 + k] * s4[3]);
-        }
-        __syncthreads();
+    }
+    for (int k = 0; k < 4; ++k) {
+        double w = v[k];
+        for (int off = 16; off > 0; off >>= 1) w += __shfl_xor_sync(0xffffffffu, w, off);
+        if (lane == 0) red[warp][k] = w;
+    }
+    __syncthreads();
+    if (tid == 0) {
+        double s4[4] = {0.0, 0.0, 0.0, 0.0};
+        for (int w = 0; w < kDescThreads / 32; ++w)
+            for (int k = 0; k < 4; ++k) s4[k] += red[w][k];
+        const double* R = rot + 9 * x;
+        float* out = X + (size_t)x * n_feat + 4 * a;
+        out[0] = (float)s4[0];
+        for (int k = 0; k < 3; ++k)
+            out[1 + k] = (float)(R[0 * 3 + k] * s4[1] + R[1 * 3 + k] * s4[2] + R[2 * 3 + k] * s4[3]);
     }
 }
 
@@ -265,9 +275,9 @@ cudaError_t launch_frames(const Dev& d, double* rot, cudaStream_t s)
     return cudaGetLastError();
 }
 
-cudaError_t launch_descriptors(const Dev& d, const double* rot, int n_feat, float* X, cudaStream_t s)
+cudaError_t launch_descriptors(const Dev& d, const double* rot, int n_feat, int max_nat, float* X, cudaStream_t s)
 {
-    k_descriptors<<<d.n_frag, 256, 0, s>>>(d, rot, n_feat, X);
+    k_descriptors<<<d.n_frag * max_nat, kDescThreads, 0, s>>>(d, rot, n_feat, max_nat, X);
     note_launches(1);
     return cudaGetLastError();
 }

@@ -183,7 +183,7 @@ cudaError_t ensure_cap(fef_mlp* m, int rows)
 }
 
 // forward of rows x n_in (already standardised) into m->H1, m->H2, m->Y
-void forward(fef_mlp* m, int rows, const float* X)
+void forward(fef_mlp* m, int rows, const float* X, cudaStream_t st)
 {
     const float* W1 = m->theta;
     const float* b1 = W1 + (size_t)m->n_in * m->n_h;
@@ -191,9 +191,9 @@ void forward(fef_mlp* m, int rows, const float* X)
     const float* b2 = W2 + (size_t)m->n_h * m->n_h;
     const float* W3 = b2 + m->n_h;
     const float* b3 = W3 + (size_t)m->n_h * m->n_out;
-    gemm<0, 0, 1>(m->stream, rows, m->n_h, m->n_in, X, W1, b1, nullptr, m->H1);
-    gemm<0, 0, 1>(m->stream, rows, m->n_h, m->n_h, m->H1, W2, b2, nullptr, m->H2);
-    gemm<0, 0, 0>(m->stream, rows, m->n_out, m->n_h, m->H2, W3, b3, nullptr, m->Y);
+    gemm<0, 0, 1>(st, rows, m->n_h, m->n_in, X, W1, b1, nullptr, m->H1);
+    gemm<0, 0, 1>(st, rows, m->n_h, m->n_h, m->H1, W2, b2, nullptr, m->H2);
+    gemm<0, 0, 0>(st, rows, m->n_out, m->n_h, m->H2, W3, b3, nullptr, m->Y);
 }
 
 // loss and gradient of rows x (X, T) into m->grad; adds sum of squares to *m->loss_acc
@@ -319,7 +319,7 @@ extern "C" fef_status fef_mlp_loss_grad(fef_mlp* m, const float* X, const float*
     cudaError_t e = ensure_cap(m, n);
     if (e != cudaSuccess) { set_err(m, cudaGetErrorString(e)); return FEF_ERR_CUDA; }
     cudaMemsetAsync(m->loss_acc, 0, sizeof(double), m->stream);
-    forward(m, n, X);
+    forward(m, n, X, m->stream);
     backward(m, n, X, T, 1.0f / ((float)n * m->n_out));
     double acc = 0.0;
     e = cudaMemcpyAsync(&acc, m->loss_acc, sizeof(double), cudaMemcpyDeviceToHost, m->stream);
@@ -357,7 +357,7 @@ extern "C" fef_status fef_mlp_train(fef_mlp* m, const float* X, const float* T, 
             k_gather<<<128, 256, 0, m->stream>>>(rows, m->n_in, m->perm, off, X, m->Xb);
             k_gather<<<128, 256, 0, m->stream>>>(rows, m->n_out, m->perm, off, T, m->Tb);
             note_launches(2);
-            forward(m, rows, m->Xb);
+            forward(m, rows, m->Xb, m->stream);
             backward(m, rows, m->Xb, m->Tb, 1.0f / ((float)rows * m->n_out));
             ++m->step;
             const float b1 = 0.9f, b2 = 0.999f;
@@ -378,25 +378,26 @@ extern "C" fef_status fef_mlp_train(fef_mlp* m, const float* X, const float* T, 
 }
 
 namespace fef {
-// Y[n x n_out] = network(X[n x n_in]) on stream s, applying the input/output scaling when set.
-cudaError_t mlp_predict_device(fef_mlp* m, const float* X, float* Y, int n)
+// Y[n x n_out] = network(X[n x n_in]) on stream st, applying the input/output scaling when set.
+// The network's scratch rows are shared: one prediction or training call at a time per network.
+cudaError_t mlp_predict_device(fef_mlp* m, const float* X, float* Y, int n, cudaStream_t st)
 {
     cudaError_t e = ensure_cap(m, n);
     if (e != cudaSuccess) return e;
     const float* Xin = X;
     if (m->scaled) {
-        e = cudaMemcpyAsync(m->Xb, X, sizeof(float) * (size_t)n * m->n_in, cudaMemcpyDeviceToDevice, m->stream);
+        e = cudaMemcpyAsync(m->Xb, X, sizeof(float) * (size_t)n * m->n_in, cudaMemcpyDeviceToDevice, st);
         if (e != cudaSuccess) return e;
-        k_affine<<<128, 256, 0, m->stream>>>((int64_t)n * m->n_in, m->n_in, m->Xb, m->in_shift, m->in_scale, 0);
+        k_affine<<<128, 256, 0, st>>>((int64_t)n * m->n_in, m->n_in, m->Xb, m->in_shift, m->in_scale, 0);
         note_launches(1);
         Xin = m->Xb;
     }
-    forward(m, n, Xin);
+    forward(m, n, Xin, st);
     if (m->scaled) {
-        k_affine<<<128, 256, 0, m->stream>>>((int64_t)n * m->n_out, m->n_out, m->Y, m->out_shift, m->out_scale, 1);
+        k_affine<<<128, 256, 0, st>>>((int64_t)n * m->n_out, m->n_out, m->Y, m->out_shift, m->out_scale, 1);
         note_launches(1);
     }
-    e = cudaMemcpyAsync(Y, m->Y, sizeof(float) * (size_t)n * m->n_out, cudaMemcpyDeviceToDevice, m->stream);
+    e = cudaMemcpyAsync(Y, m->Y, sizeof(float) * (size_t)n * m->n_out, cudaMemcpyDeviceToDevice, st);
     if (e == cudaSuccess) e = cudaGetLastError();
     return e;
 }
@@ -407,7 +408,7 @@ int mlp_n_out(const fef_mlp* m) { return m->n_out; }
 extern "C" fef_status fef_mlp_predict(fef_mlp* m, const float* X, float* Y, int32_t n)
 {
     if (!m || !X || !Y || n < 1) return FEF_ERR_ARG;
-    cudaError_t e = mlp_predict_device(m, X, Y, n);
+    cudaError_t e = mlp_predict_device(m, X, Y, n, m->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(m->stream);
     if (e != cudaSuccess) { set_err(m, cudaGetErrorString(e)); return FEF_ERR_CUDA; }
     return FEF_OK;
