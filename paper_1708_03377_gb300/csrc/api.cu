@@ -56,6 +56,7 @@ struct Buffers {
     }
     // geometry-time data
     double *S = nullptr, *h = nullptr, *X = nullptr, *Venv = nullptr, *eric = nullptr, *boys = nullptr;
+    double* scf_ws = nullptr;  // fragment-SCF workspace for fragments above kScfSmemMaxN AOs
     double *e_nn_intra = nullptr, *e_nn_pair = nullptr;
     int* nmo = nullptr;
     // per-build data
@@ -238,6 +239,8 @@ static void run_scf(fef_ctx* c, bool with_field, bool have_start)
     a.diis_size = c->opt.diis_size;
     a.e_tol = c->opt.micro_e_tol;
     a.comm_tol = c->opt.micro_comm_tol;
+    a.ws = b->scf_ws;
+    a.diis_by_moff = 1;
     ck(cudaEventRecord(b->ev2, c->stream), "event");
     ck(launch_fragment_scf(c->dev, a, c->max_nao, c->stream), "fragment SCF");
     ck(cudaEventRecord(b->ev3, c->stream), "event");
@@ -373,7 +376,8 @@ extern "C" fef_status fef_create(const fef_geometry* g, const fef_basis* bs, con
         c->n_shells = (int)sh_l.size();
         c->n_prims = (int)p_exp.size();
         int max_nao = *std::max_element(frag_nao.begin(), frag_nao.end());
-        require(max_nao <= 56, FEF_ERR_ARG, "fragments above 56 AOs are not supported by the shared-memory SCF kernel");
+        require(max_nao <= kMaxFragAO, FEF_ERR_ARG,
+                "fragments above " + std::to_string(kMaxFragAO) + " AOs are not supported");
         c->max_nao = max_nao;
         c->nao = frag_nao;
         c->nocc = frag_nocc;
@@ -577,7 +581,7 @@ extern "C" fef_status fef_create(const fef_geometry* g, const fef_basis* bs, con
         ck(launch_nuclear_repulsion(d, b->e_nn_intra, b->e_nn_pair, s), "nuclear repulsion");
         // intra-fragment two-electron tensor -> Schwarz factors and C = (mu nu|ls) - (mu l|nu s)/2
         {
-            double* eri = b->alloc<double>(c->eri_total, "intra eri");
+            double* eri = b->alloc<double>(c->coff_total, "intra eri");  // pair-packed U[pq][rs]
             // tasks: (fragment, shell pair s1 <= s2, bra component), sorted by class
             std::vector<std::pair<int, int4>> tk;
             for (int x = 0; x < nf; ++x)
@@ -613,10 +617,13 @@ extern "C" fef_status fef_create(const fef_geometry* g, const fef_basis* bs, con
         b->nmo = b->alloc<int>(nf, "nmo");
         b->Sh = b->alloc<double>(c->mat_total, "S^1/2");
         b->Sih = b->alloc<double>(c->mat_total, "S^-1/2");
-        ck(launch_orthogonaliser(d, b->S, b->X, b->nmo, 1e-7, max_nao, s, b->Sh, b->Sih), "orthogonaliser");
+        double* orth_ws = max_nao > kOrthSmemMaxN ? b->alloc<double>(2 * c->mat_total, "orthogonaliser workspace")
+                                                  : nullptr;
+        ck(launch_orthogonaliser(d, b->S, b->X, b->nmo, 1e-7, max_nao, s, b->Sh, b->Sih, orth_ws), "orthogonaliser");
         c->nmo.assign(nf, 0);
         ck(cudaMemcpyAsync(c->nmo.data(), b->nmo, sizeof(int) * nf, cudaMemcpyDeviceToHost, s), "nmo");
         ck(cudaStreamSynchronize(s), "create");
+        if (orth_ws) b->release(orth_ws);
         for (int x = 0; x < nf; ++x)
             require(c->nmo[x] >= frag_nocc[x], FEF_ERR_BASIS,
                     "fragment " + std::to_string(x) + ": basis too linearly dependent for its electrons");
@@ -665,8 +672,11 @@ extern "C" fef_status fef_create(const fef_geometry* g, const fef_basis* bs, con
         b->E_frag = b->alloc<double>(nf, "E_frag");
         b->E_tot = b->alloc<double>(1, "E_tot");
         b->iters = b->alloc<int>(nf, "iters");
-        b->diis_stride = 2 * (int64_t)o.diis_size * max_nao * max_nao;
-        b->diis = b->alloc<double>((size_t)nf * b->diis_stride, "diis");
+        // DIIS history at 2 diis_size frag_moff[x] (sized per fragment); SCF workspace in global
+        // memory only for fragments too large for shared memory
+        b->diis_stride = 0;
+        b->diis = b->alloc<double>(2 * (size_t)o.diis_size * c->mat_total, "diis");
+        b->scf_ws = max_nao > kScfSmemMaxN ? b->alloc<double>(9 * c->mat_total, "SCF workspace") : nullptr;
         ck(cudaStreamSynchronize(s), "create");
         c->shell_quartets = (int64_t)qc[0];
         for (int i = 0; i < kClasses * kClasses; ++i) c->class_quartets[i] = (int64_t)qc[1 + i];

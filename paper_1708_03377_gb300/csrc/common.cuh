@@ -35,6 +35,9 @@ constexpr double kSqrt2Pi52 = 5.9149671727956128778;
 constexpr double kSqrtPiHalf = 0.88622692545275801365;  // sqrt(pi)/2
 
 constexpr int kMaxL = 2;            // s, p, d shells
+constexpr int kMaxFragAO = 232;     // AOs per fragment (packed n(n+1)/2 doubles fit in 227 KB of shared memory)
+constexpr int kScfSmemMaxN = 56;    // fragment SCF: 9 n^2 doubles in shared memory up to this n
+constexpr int kOrthSmemMaxN = 112;  // orthogonaliser: 2 n^2 doubles in shared memory up to this n
 constexpr int kMaxLPair = 2 * kMaxL;
 constexpr int kMaxLTot = 2 * kMaxLPair;
 
@@ -81,6 +84,14 @@ __host__ __device__ constexpr TUV htuv(int idx)
     return TUV{t, u, s - t - u};
 }
 // Cartesian component k of angular momentum l (lexicographic: xx, xy, xz, yy, yz, zz)
+// Row-major upper-triangle index of the AO pair (i, j), either order: i' = min, j' = max,
+// i' n - i'(i'-1)/2 + (j' - i').
+__host__ __device__ inline int64_t pair_pack(int i, int j, int n)
+{
+    const int a = i < j ? i : j, b = i < j ? j : i;
+    return (int64_t)a * n - (int64_t)a * (a - 1) / 2 + (b - a);
+}
+
 __host__ __device__ inline void cart_of(int l, int k, int& x, int& y, int& z)
 {
     int n = 0;

@@ -157,7 +157,8 @@ cudaError_t launch_nuclear_traces(const Dev& d, const double* D, double* trace_x
 cudaError_t launch_nuclear_repulsion(const Dev& d, double* e_nn_intra, double* e_nn_pair, cudaStream_t s);
 // X = U s^{-1/2} (canonical); optionally S^{1/2} and S^{-1/2} (symmetric) into Sh, Sih
 cudaError_t launch_orthogonaliser(const Dev& d, const double* S, double* X, int* nmo, double s_min, int max_n,
-                                  cudaStream_t s, double* Sh = nullptr, double* Sih = nullptr);
+                                  cudaStream_t s, double* Sh = nullptr, double* Sih = nullptr,
+                                  double* ws = nullptr);
 cudaError_t launch_hermite_density(const Dev& d, const double* D, cudaStream_t s);
 // FP64 J-engine (fp32 = 0) on pp_Dh, or the FP32-core J-engine (fp32 = 1) on pp_Dh32; both add
 // into the FP64 accumulators pp_Jh.
@@ -194,6 +195,10 @@ struct ScfArgs {
     int have_start;
     int max_iter, diis_size;
     double e_tol, comm_tol;
+    double* ws;             // global workspace, 9 n^2 doubles per fragment at 9 frag_moff[x]: used by
+                            // fragments above kScfSmemMaxN AOs (null when there are none)
+    int diis_by_moff;       // 1: DIIS history at 2 diis_size frag_moff[x] (sized per fragment),
+                            // 0: at x * diis_stride
 };
 cudaError_t launch_fragment_scf(const Dev& d, const ScfArgs& a, int max_n, cudaStream_t s);
 

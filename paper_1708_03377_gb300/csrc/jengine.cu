@@ -432,7 +432,9 @@ cudaError_t launch_fock_energy(const Dev& d, const double* h, const double* Venv
                                const double* eric, const double* D, double* F, double* omega, const double* e_nn,
                                double* E_int, double* trV, double* trJ, cudaStream_t s)
 {
-    size_t smem = sizeof(double) * (size_t)d.max_nao * (d.max_nao + 1) / 2;
+    size_t smem = sizeof(double) * (size_t)d.max_nao * (d.max_nao + 1) / 2;  // packed density, <= 227 KB
+    cudaError_t e = cudaFuncSetAttribute(k_fock_assemble, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
     k_fock_assemble<<<d.n_frag, 256, smem, s>>>(d, h, Venv, Jenv, eric, D, F, omega, e_nn, E_int, trV, trJ);
     note_launches(1);
     return cudaGetLastError();

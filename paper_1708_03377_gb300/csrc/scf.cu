@@ -59,11 +59,12 @@ __device__ inline void mm(double* C, const double* A, const double* B, int m, in
 }
 
 struct JacobiScratch {
-    double c[64], s[64];
-    int p[64], q[64];
+    double c[kMaxFragAO / 2], s[kMaxFragAO / 2];
+    int p[kMaxFragAO / 2], q[kMaxFragAO / 2];
 };
 
-// Cyclic Jacobi on the symmetric m x m matrix A (shared, leading dimension ld), m <= 128.
+// Cyclic Jacobi on the symmetric m x m matrix A (shared or global, leading dimension ld),
+// m <= kMaxFragAO.
 // Parallel ordering: round-robin pairing (circle method), m/2 disjoint rotations per round, each
 // zeroing A_pq with t = sgn(theta)/(|theta| + sqrt(theta^2 + 1)), theta = (A_qq - A_pp)/(2 A_pq)
 // (Golub & Van Loan, symmetric Schur decomposition).
@@ -153,17 +154,22 @@ __device__ void jacobi_eigh(double* A, double* V, int m, int ld, JacobiScratch* 
 // ------------------------------------------------------------------------------------------ X = U s^{-1/2}
 // Also, when Sh / Sih are given: the symmetric square roots S^{1/2} = U s^{1/2} U^T and
 // S^{-1/2} = U s^{-1/2} U^T (over s >= s_min), used to express densities in the Loewdin basis.
+// Fragments above kOrthSmemMaxN AOs work in the global workspace ws (2 n^2 doubles at 2 frag_moff[x]).
 __global__ void k_orthogonaliser(Dev d, const double* S, double* X, int* nmo_out, double s_min, double* Sh,
-                                 double* Sih)
+                                 double* Sih, double* ws)
 {
     const int x = blockIdx.x;
     const int n = d.frag_nao[x];
     extern __shared__ double sm[];
-    double* A = sm;
+    if (n > kOrthSmemMaxN && !ws) {
+        if (threadIdx.x == 0) atomicOr(d.err_flag, kErrBounds);
+        return;
+    }
+    double* A = n <= kOrthSmemMaxN ? sm : ws + 2 * d.frag_moff[x];
     double* V = A + n * n;
     __shared__ JacobiScratch js;
     __shared__ double red[32];
-    __shared__ int keep_idx[128];
+    __shared__ int keep_idx[kMaxFragAO];
     __shared__ int nkeep;
     const double* Sx = S + d.frag_moff[x];
     for (int e = threadIdx.x; e < n * n; e += blockDim.x) A[e] = Sx[e];
@@ -205,11 +211,12 @@ __global__ void k_orthogonaliser(Dev d, const double* S, double* X, int* nmo_out
 }
 
 cudaError_t launch_orthogonaliser(const Dev& d, const double* S, double* X, int* nmo, double s_min, int max_n,
-                                  cudaStream_t s, double* Sh, double* Sih)
+                                  cudaStream_t s, double* Sh, double* Sih, double* ws)
 {
-    size_t smem = 2 * (size_t)max_n * max_n * sizeof(double);
+    const size_t ns = (size_t)std::min(max_n, kOrthSmemMaxN);
+    size_t smem = 2 * ns * ns * sizeof(double);
     cudaFuncSetAttribute(k_orthogonaliser, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    k_orthogonaliser<<<d.n_frag, 256, smem, s>>>(d, S, X, nmo, s_min, Sh, Sih);
+    k_orthogonaliser<<<d.n_frag, 256, smem, s>>>(d, S, X, nmo, s_min, Sh, Sih, ws);
     note_launches(1);
     return cudaGetLastError();
 }
@@ -217,7 +224,8 @@ cudaError_t launch_orthogonaliser(const Dev& d, const double* S, double* X, int*
 // ------------------------------------------------------------------------------------------ fragment SCF
 // PACKED: G from the packed transposed tensor CT[rs][pq] (setup.cu), thread per pq = (mu <= nu);
 // otherwise from the full C[mu nu][lambda sigma], one warp per row.
-// Shared memory: Hw Ss Xs Ds Fs W A V Vp, nine n x n doubles (W doubles as the packed density).
+// Working matrices Hw Ss Xs Ds Fs W A V Vp, nine n x n doubles (W doubles as the packed density):
+// in shared memory up to kScfSmemMaxN AOs, else in the global workspace a.ws at 9 frag_moff[x].
 // The Jacobi of each micro-iteration starts from the previous eigenvectors Vp: A <- Vp^T A Vp,
 // so only the small change of F' between iterations has to be rotated away.
 template <bool PACKED>
@@ -231,7 +239,11 @@ __global__ void __launch_bounds__(256) k_fragment_scf(Dev d, ScfArgs a)
     const int np = n * (n + 1) / 2;
     const int64_t mo = d.frag_moff[x];
     extern __shared__ double sm[];
-    double* Hw = sm;
+    if (n > kScfSmemMaxN && !a.ws) {
+        if (threadIdx.x == 0) atomicOr(d.err_flag, kErrBounds);
+        return;
+    }
+    double* Hw = n <= kScfSmemMaxN ? sm : a.ws + 9 * mo;
     double* Ss = Hw + n2;
     double* Xs = Ss + n2;
     double* Ds = Xs + n2;
@@ -244,11 +256,11 @@ __global__ void __launch_bounds__(256) k_fragment_scf(Dev d, ScfArgs a)
     __shared__ double red[32];
     __shared__ double B[8][8];
     __shared__ double coef[9];
-    __shared__ int order[128];
+    __shared__ int order[kMaxFragAO];
     const int tid = threadIdx.x, nt = blockDim.x;
     const int lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
     const double* C = PACKED ? a.eric + d.frag_coff[x] : a.eric + d.frag_eoff[x];
-    double* hF = a.diis_F + (int64_t)x * a.diis_stride;
+    double* hF = a.diis_by_moff ? a.diis_F + 2 * (int64_t)a.diis_size * mo : a.diis_F + (int64_t)x * a.diis_stride;
     double* he = hF + (int64_t)a.diis_size * n2;
 
     for (int e = tid; e < n2; e += nt) {
@@ -452,7 +464,8 @@ __global__ void __launch_bounds__(256) k_fragment_scf(Dev d, ScfArgs a)
 
 cudaError_t launch_fragment_scf(const Dev& d, const ScfArgs& a, int max_n, cudaStream_t s)
 {
-    size_t smem = 9 * (size_t)max_n * max_n * sizeof(double);
+    const size_t ns = (size_t)std::min(max_n, kScfSmemMaxN);
+    size_t smem = 9 * ns * ns * sizeof(double);
     auto kern = a.eric_packed ? k_fragment_scf<true> : k_fragment_scf<false>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;

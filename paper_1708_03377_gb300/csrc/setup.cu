@@ -471,7 +471,8 @@ cudaError_t launch_nuclear_repulsion(const Dev& d, double* e_nn_intra, double* e
 // the row (mu nu|lambda sigma) for all lambda sigma of s2 by McMurchie-Davidson,
 //   (mu nu|lambda sigma) = sum_{PQ} 2 pi^{5/2}/(p q sqrt(p+q)) sum_{tuv,t'u'v'} E^{mu nu}_{tuv}
 //                          (-1)^{t'+u'+v'} E^{lambda sigma}_{t'u'v'} R_{t+t',u+u',v+v'}(alpha, PQ),
-// written to the 8 positions of the full n^4 tensor it covers (bra-ket and index symmetry).  Tasks
+// written to the pair-packed tensor U[pq][rs] = (mu nu|lambda sigma), pq = pack(min(mu,nu),
+// max(mu,nu)), np = n(n+1)/2 rows per fragment at frag_coff (both U[pq][rs] and U[rs][pq]).  Tasks
 // are sorted by angular-momentum class so that the threads of a warp follow the same path.
 __global__ void k_intra_eri(Dev d, const int4* __restrict__ tasks, int n_tasks, double* eri)
 {
@@ -565,17 +566,17 @@ __global__ void k_intra_eri(Dev d, const int4* __restrict__ tasks, int n_tasks, 
         }
     const int n = d.frag_nao[x];
     const int ao0 = d.frag_ao0[x];
-    double* T = eri + d.frag_eoff[x];
-    const size_t n2 = (size_t)n * n;
+    const int64_t np = (int64_t)n * (n + 1) / 2;
+    double* U = eri + d.frag_coff[x];
     const int mu = d.sh_ao[sa] + kb / ncart(lb), nu = d.sh_ao[sb] + kb % ncart(lb);
     const double smn = d.ao_scale[ao0 + mu] * d.ao_scale[ao0 + nu];
+    const int64_t pq = pair_pack(mu, nu, n);
     for (int k = 0; k < nc * nd; ++k) {
         int la_ = d.sh_ao[sc] + k / nd, si = d.sh_ao[sd] + k % nd;
         double v = out[k] * smn * d.ao_scale[ao0 + la_] * d.ao_scale[ao0 + si];
-        size_t m1 = (size_t)mu * n + nu, m2 = (size_t)nu * n + mu;
-        size_t k1 = (size_t)la_ * n + si, k2 = (size_t)si * n + la_;
-        T[m1 * n2 + k1] = v; T[m2 * n2 + k1] = v; T[m1 * n2 + k2] = v; T[m2 * n2 + k2] = v;
-        T[k1 * n2 + m1] = v; T[k1 * n2 + m2] = v; T[k2 * n2 + m1] = v; T[k2 * n2 + m2] = v;
+        const int64_t rs = pair_pack(la_, si, n);
+        U[pq * np + rs] = v;
+        U[rs * np + pq] = v;
     }
 }
 
@@ -601,29 +602,29 @@ __device__ inline int tri_i(int p, int n)
     return i;
 }
 
+// CT[rs][pq] = (mu nu|la si) - (mu la|nu si)/2 + [la != si] ((mu nu|si la) - (mu si|nu la)/2) from the
+// pair-packed U, so that G[D]_{mu nu} = sum_{rs} CT[rs][pq] D_{la si} over la <= si.
 __global__ void k_coulomb_exchange(Dev d, const double* eri, double* eric)
 {
     int x = blockIdx.y;
     int n = d.frag_nao[x];
-    int np = n * (n + 1) / 2;
-    size_t n2 = (size_t)n * n;
-    const double* e = eri + d.frag_eoff[x];
+    int64_t np = (int64_t)n * (n + 1) / 2;
+    const double* U = eri + d.frag_coff[x];
     double* c = eric + d.frag_coff[x];
-    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < (size_t)np * np;
-         i += (size_t)gridDim.x * blockDim.x) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < np * np; i += (int64_t)gridDim.x * blockDim.x) {
         int rs = (int)(i / np), pq = (int)(i % np);
         int mu = tri_i(pq, n), nu = mu + pq - (mu * n - mu * (mu - 1) / 2);
         int la = tri_i(rs, n), si = la + rs - (la * n - la * (la - 1) / 2);
-        size_t mn = (size_t)mu * n + nu;
-        double v = e[mn * n2 + (size_t)la * n + si] - 0.5 * e[((size_t)mu * n + la) * n2 + (size_t)nu * n + si];
-        if (la != si) v += e[mn * n2 + (size_t)si * n + la] - 0.5 * e[((size_t)mu * n + si) * n2 + (size_t)nu * n + la];
+        double v = U[(int64_t)pq * np + rs] - 0.5 * U[pair_pack(mu, la, n) * np + pair_pack(nu, si, n)];
+        if (la != si) v += U[(int64_t)pq * np + rs] - 0.5 * U[pair_pack(mu, si, n) * np + pair_pack(nu, la, n)];
         c[i] = v;
     }
 }
 
 cudaError_t launch_coulomb_exchange(const Dev& d, const double* eri, double* eric, cudaStream_t s)
 {
-    size_t n4 = (size_t)d.max_nao * d.max_nao * d.max_nao * d.max_nao;
+    size_t npm = (size_t)d.max_nao * (d.max_nao + 1) / 2;
+    size_t n4 = npm * npm;
     dim3 g((unsigned)std::min<size_t>((n4 + 255) / 256, 8192), d.n_frag);
     k_coulomb_exchange<<<g, 256, 0, s>>>(d, eri, eric);
     note_launches(1);
@@ -648,21 +649,21 @@ __global__ void k_schwarz(Dev d, const double* eri, double* sp_Q, float* pq0, fl
         x = lo;
     }
     int n = d.frag_nao[x];
-    size_t n2 = (size_t)n * n;
-    const double* e = eri + d.frag_eoff[x];
+    const int64_t np = (int64_t)n * (n + 1) / 2;
+    const double* U = eri + d.frag_coff[x];
     double q = 0.0;
     for (int ia = 0; ia < ncart(d.sh_l[sa]); ++ia)
         for (int ib = 0; ib < ncart(d.sh_l[sb]); ++ib) {
             int mu = d.sh_ao[sa] + ia, nu = d.sh_ao[sb] + ib;
-            size_t mn = (size_t)mu * n + nu;
-            q = fmax(q, fabs(e[mn * n2 + mn]));
+            const int64_t mn = pair_pack(mu, nu, n);
+            q = fmax(q, fabs(U[mn * np + mn]));
         }
     q = sqrt(q);
     sp_Q[s] = q;
     float* pq[kClasses] = {pq0, pq1, pq2, pq3, pq4};
     int L = d.sp_L[s];
-    int np = d.sh_np[sa] * d.sh_np[sb];
-    for (int k = 0; k < np; ++k) pq[L][d.sp_pp0[s] + k] = (float)q;
+    const int npp = d.sh_np[sa] * d.sh_np[sb];
+    for (int k = 0; k < npp; ++k) pq[L][d.sp_pp0[s] + k] = (float)q;
 }
 
 cudaError_t launch_schwarz(const Dev& d, const double* eri, double* sp_Q, float* pp_Q[kClasses], cudaStream_t s)

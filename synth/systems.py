@@ -340,12 +340,13 @@ def _place(rg, shapes, side, max_tries, fixed=None):
     return frags
 
 
-def solvated_heterocycle(n_water: int = 1000, side: float = 31.0, seed: int = 0) -> System:
-    """A cytosine-like C4N3OH5 fragment (heavy atoms 3s2p1d, H 2s) at the cube centre, plus
-    ``n_water`` water-like fragments (O 3s2p, H 2s) placed around it."""
+def solvated_heterocycle(n_water: int = 1000, side: float = 31.0, seed: int = 0, heavy_shells=None) -> System:
+    """A cytosine-like C4N3OH5 fragment (heavy atoms 3s2p1d, 130 AOs; or ``heavy_shells``, e.g.
+    SHELLS_O_SP for an 82-AO s/p solute) at the cube centre, plus ``n_water`` water-like fragments
+    (O 3s2p, H 2s) placed around it."""
     rb, rg = _streams(seed, 2)
     bs = [random_basis_set(rb, SHELLS_O_SP), random_basis_set(rb, SHELLS_H)]
-    heavy = {zz: random_basis_set(rb, SHELLS_HEAVY_SPD) for zz in (6, 7, 8)}
+    heavy = {zz: random_basis_set(rb, SHELLS_HEAVY_SPD if heavy_shells is None else heavy_shells) for zz in (6, 7, 8)}
     kind_of = {}
     for zz in (6, 7, 8):
         kind_of[zz] = len(bs)
