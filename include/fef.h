@@ -57,6 +57,7 @@ typedef enum {
 } fef_status;
 
 enum { FEF_FP64 = 0, FEF_MIXED = 1 };
+enum { FEF_ENGINE_FP64 = 0, FEF_ENGINE_DF64 = 1 };
 enum { FEF_START_SUPERPOSITION = 0, FEF_START_LEARNED = 1, FEF_START_GIVEN = 2 };
 
 /* Molecular system split into fragments (Theory, "Fragment Mean Field": Hilbert space partition
@@ -102,6 +103,11 @@ typedef struct {
     int32_t use_graph;       /* capture each macro-iteration's device work in a CUDA graph */
     int32_t deterministic;   /* reserved: 1 requests run-to-run identical sums */
     double mixed_switch;     /* MIXED: coarse FP32-core macro-iterations until |dE| < mixed_switch */
+    int32_t exact_engine;    /* J-engine of the FP64-accurate builds (every build in FEF_FP64, the
+                                reference builds in FEF_MIXED): FEF_ENGINE_FP64 = native FP64 FMA,
+                                FEF_ENGINE_DF64 = float-float arithmetic on the FP32 pipes (48-bit
+                                significand, ~1e-14 relative; s/p Hermite classes, d-shell classes
+                                stay FP64) */
 } fef_options;
 
 /* Fill *opt with the defaults: FP64, no cutoff, schwarz 1e-12, e_tol 1e-8, micro_e_tol 1e-11,

@@ -20,6 +20,7 @@ LIB_PATH = os.path.join(_HERE, "libfef.so")
 FEF_OK, FEF_ERR_ARG, FEF_ERR_BASIS, FEF_ERR_GEOM, FEF_ERR_CUDA, FEF_ERR_NOT_CONVERGED, FEF_ERR_NUMERIC, \
     FEF_ERR_TIMEOUT = range(8)
 FEF_FP64, FEF_MIXED = 0, 1
+FEF_ENGINE_FP64, FEF_ENGINE_DF64 = 0, 1
 FEF_START_SUPERPOSITION, FEF_START_LEARNED, FEF_START_GIVEN = 0, 1, 2
 STATUS_NAMES = {0: "FEF_OK", 1: "FEF_ERR_ARG", 2: "FEF_ERR_BASIS", 3: "FEF_ERR_GEOM", 4: "FEF_ERR_CUDA",
                 5: "FEF_ERR_NOT_CONVERGED", 6: "FEF_ERR_NUMERIC", 7: "FEF_ERR_TIMEOUT"}
@@ -55,7 +56,7 @@ class fef_options(ctypes.Structure):
                 ("e_tol", ctypes.c_double), ("micro_e_tol", ctypes.c_double), ("micro_comm_tol", ctypes.c_double),
                 ("max_macro", ctypes.c_int32), ("max_micro", ctypes.c_int32), ("diis_size", ctypes.c_int32),
                 ("start", ctypes.c_int32), ("use_graph", ctypes.c_int32), ("deterministic", ctypes.c_int32),
-                ("mixed_switch", ctypes.c_double)]
+                ("mixed_switch", ctypes.c_double), ("exact_engine", ctypes.c_int32)]
 
 
 _lib = None

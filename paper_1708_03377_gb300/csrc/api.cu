@@ -140,6 +140,7 @@ extern "C" void fef_default_options(fef_options* o)
     o->use_graph = 0;
     o->deterministic = 0;
     o->mixed_switch = 1e-6;
+    o->exact_engine = FEF_ENGINE_FP64;
 }
 
 // ---------------------------------------------------------------------------------------------- helpers
@@ -187,11 +188,13 @@ static void build_fock_internal(fef_ctx* c, int kind = kBuildFP64)
             ck(cudaMemsetAsync(b->Dh_ref[L], 0, sizeof(double) * b->njh[L], s), "zero reference");
     }
     if (fp32) ck(launch_delta_density(d, b->Dh_ref, s), "delta density");
+    const bool df = !fp32 && c->opt.exact_engine == FEF_ENGINE_DF64;
+    if (df) ck(launch_df_density(d, s), "df64 density");
     const int2* tiles[kClasses][kClasses];
     for (int i = 0; i < kClasses; ++i)
         for (int j = 0; j < kClasses; ++j) tiles[i][j] = b->tiles[i][j];
     ck(cudaEventRecord(b->ev0, s), "event");
-    ck(launch_jengine(d, tiles, b->n_tiles, c->opt.schwarz, fp32 ? 1 : 0, s), "J-engine");
+    ck(launch_jengine(d, tiles, b->n_tiles, c->opt.schwarz, fp32 ? 1 : (df ? 2 : 0), s), "J-engine");
     ck(cudaEventRecord(b->ev1, s), "event");
     if (kind != kBuildFP32Inc) {
         for (int L = 0; L < kClasses; ++L) {
@@ -282,6 +285,8 @@ extern "C" fef_status fef_create(const fef_geometry* g, const fef_basis* bs, con
         require(o.diis_size >= 1 && o.diis_size <= 8, FEF_ERR_ARG, "options: diis_size must be 1..8");
         require(o.max_macro >= 1 && o.max_micro >= 1, FEF_ERR_ARG, "options: iteration limits must be >= 1");
         require(o.precision == FEF_FP64 || o.precision == FEF_MIXED, FEF_ERR_ARG, "options: bad precision");
+        require(o.exact_engine == FEF_ENGINE_FP64 || o.exact_engine == FEF_ENGINE_DF64, FEF_ERR_ARG,
+                "options: bad exact_engine");
         require(o.schwarz >= 0.0 && std::isfinite(o.schwarz), FEF_ERR_ARG, "options: bad schwarz threshold");
         c->stream = static_cast<cudaStream_t>(cuda_stream);
         ck(cudaGetDevice(&c->device), "cudaGetDevice");
@@ -475,6 +480,8 @@ extern "C" fef_status fef_create(const fef_geometry* g, const fef_basis* bs, con
         double4_32a* ppP[kClasses];
         float4* ppPf[kClasses];
         float4* ppPr[kClasses];
+        float4* ppPhi[kClasses];
+        float4* ppPlo[kClasses];
         double* ppK[kClasses];
         float* ppQ[kClasses];
         for (int L = 0; L < kClasses; ++L) {
@@ -487,6 +494,11 @@ extern "C" fef_status fef_create(const fef_geometry* g, const fef_basis* bs, con
             ppPr[L] = b->alloc<float4>(n, "prim pairs");
             d.pp_Pr[L] = ppPr[L];
             d.pp_Dh32[L] = b->alloc<float>((size_t)nh(L) * n, "hermite density fp32");
+            ppPhi[L] = b->alloc<float4>(n, "prim pairs df64");
+            ppPlo[L] = b->alloc<float4>(n, "prim pairs df64");
+            d.pp_Phi[L] = ppPhi[L];
+            d.pp_Plo[L] = ppPlo[L];
+            d.pp_Dhdf[L] = b->alloc<float2>((size_t)nh(L) * n, "hermite density df64");
             b->Dh_ref[L] = b->alloc<double>((size_t)nh(L) * n, "hermite density ref");
             b->Jh_ref[L] = b->alloc<double>((size_t)nh(L) * n, "hermite field ref");
             ppK[L] = b->alloc<double>(n, "prim pairs");
@@ -504,6 +516,8 @@ extern "C" fef_status fef_create(const fef_geometry* g, const fef_basis* bs, con
         d.boys = b->boys;
         b->boys32 = b->alloc<float>((size_t)kBoys32Rows * kBoysRowLen, "boys32");
         d.boys32 = b->boys32;
+        float2* boysdf = b->alloc<float2>((size_t)kBoysRows * kBoysRowLen, "boys df64");
+        d.boysdf = boysdf;
         b->err_flag = b->alloc<int>(1, "flag");
         d.err_flag = b->err_flag;
         ck(cudaMemsetAsync(b->err_flag, 0, sizeof(int), s), "flag");
@@ -518,6 +532,7 @@ extern "C" fef_status fef_create(const fef_geometry* g, const fef_basis* bs, con
         ck(launch_boys_table32(b->boys, b->boys32, s), "boys table fp32");
         ck(launch_ao_scale(d, ao_scale, ao_global, nullptr, s), "ao scale");
         ck(launch_prim_pairs(d, ppP, ppPf, ppK, ppPr, s), "prim pairs");
+        ck(launch_df_setup(d, ppPhi, ppPlo, boysdf, s), "df64 pair data");
         b->S = b->alloc<double>(c->mat_total, "S");
         b->h = b->alloc<double>(c->mat_total, "h");
         ck(launch_one_electron(d, b->S, b->h, s), "one-electron");

@@ -76,6 +76,9 @@ struct Dev {
     double* pp_Jh[kClasses];
     const float4* pp_Pr[kClasses];   // FP32 (P - anchor of the fragment, p) for the mixed J-engine
     float* pp_Dh32[kClasses];        // FP32 Hermite density difference D_P - D_P^ref (mixed builds)
+    const float4* pp_Phi[kClasses];  // df64 (P, p): high floats ...
+    const float4* pp_Plo[kClasses];  // ... and low floats (float-float J-engine)
+    float2* pp_Dhdf[kClasses];       // df64 Hermite density (hi, lo)
     int n_pp[kClasses];
     // fragment pairs
     const int* pair_x;
@@ -83,6 +86,7 @@ struct Dev {
     // tables / scratch
     const double* boys;
     const float* boys32;
+    const float2* boysdf;            // df64 copy of the FP64 Boys table
     int* err_flag;
 };
 
@@ -160,10 +164,16 @@ cudaError_t launch_orthogonaliser(const Dev& d, const double* S, double* X, int*
                                   cudaStream_t s, double* Sh = nullptr, double* Sih = nullptr,
                                   double* ws = nullptr);
 cudaError_t launch_hermite_density(const Dev& d, const double* D, cudaStream_t s);
-// FP64 J-engine (fp32 = 0) on pp_Dh, or the FP32-core J-engine (fp32 = 1) on pp_Dh32; both add
-// into the FP64 accumulators pp_Jh.
+// mode 0: FP64 J-engine on pp_Dh; mode 1: FP32-core J-engine on pp_Dh32; mode 2: float-float
+// J-engine on pp_Dhdf for the s/p classes, FP64 for the rest.  All add into the FP64 accumulators
+// pp_Jh.
 cudaError_t launch_jengine(const Dev& d, const int2* tiles[kClasses][kClasses], const int* n_tiles, double tau,
-                           int fp32, cudaStream_t s);
+                           int mode, cudaStream_t s);
+cudaError_t launch_jengine_df(const Dev& d, const int2* tiles[kClasses][kClasses], const int* n_tiles, float tau,
+                              cudaStream_t s);
+cudaError_t launch_df_setup(const Dev& d, float4* const Phi[kClasses], float4* const Plo[kClasses], float2* boysdf,
+                            cudaStream_t s);
+cudaError_t launch_df_density(const Dev& d, cudaStream_t s);
 cudaError_t launch_jengine_big(const Dev& d, const int2* tiles[kClasses][kClasses], const int* n_tiles, float tau,
                                int fp32, cudaStream_t s);
 cudaError_t launch_back_transform(const Dev& d, double* J, cudaStream_t s);

@@ -277,11 +277,17 @@ static void launch_one(const Dev& d, const int2* t, int n, float tau, int fp32, 
 }
 
 cudaError_t launch_jengine(const Dev& d, const int2* tiles[kClasses][kClasses], const int* n_tiles, double tau,
-                           int fp32, cudaStream_t s)
+                           int mode, cudaStream_t s)
 {
     const float ft = (float)tau;
+    const int fp32 = mode == 1 ? 1 : 0;
 #define FEF_J(LP, LQ) launch_one<LP, LQ>(d, tiles[LP][LQ], n_tiles[LP * kClasses + LQ], ft, fp32, s)
-    FEF_J(0, 0); FEF_J(1, 0); FEF_J(1, 1); FEF_J(2, 0); FEF_J(2, 1); FEF_J(2, 2);
+    if (mode == 2) {
+        cudaError_t e = launch_jengine_df(d, tiles, n_tiles, ft, s);
+        if (e != cudaSuccess) return e;
+    } else {
+        FEF_J(0, 0); FEF_J(1, 0); FEF_J(1, 1); FEF_J(2, 0); FEF_J(2, 1); FEF_J(2, 2);
+    }
     FEF_J(3, 0); FEF_J(3, 1); FEF_J(4, 0);
 #undef FEF_J
     return launch_jengine_big(d, tiles, n_tiles, ft, fp32, s);  // classes with L_P + L_Q >= 5

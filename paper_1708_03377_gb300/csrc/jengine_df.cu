@@ -1,0 +1,330 @@
+// FP64-accurate J-engine on the FP32 pipes: float-float ("df64") arithmetic.
+//
+// A df64 value is an unevaluated sum hi + lo of two floats with |lo| <= ulp(hi)/2 (48-bit
+// significand, FP32 exponent range).  Sums use Knuth's error-free two-sum, products the FMA
+// two-product (Dekker 1971; the double-double scheme of Hida, Li and Bailey, 2001), so every
+// operation is a handful of FP32 instructions: GB300 issues FP32 at ~70x its FP64 rate, which is
+// what makes this faster than native DFMA for the fused McMurchie-Davidson contraction.
+//
+// Same work decomposition as k_jengine (one warp = 32 bra primitive pairs of class L_P against all
+// ket pairs of class L_Q <= L_P of the partner fragment), same screening, same outputs (FP64
+// Hermite fields pp_Jh):
+//   * centres, exponents, Hermite densities and the Boys table are df64 copies of the FP64 data;
+//   * Boys F_m by the same grid-Taylor table (order 6, h = 0.05) evaluated in df64, asymptotic
+//     form above T = 36 with a df64 reciprocal square root (float seed + Newton steps);
+//   * R recursion and both contractions in df64; the bra field is flushed into FP64 registers
+//     every 32 kets, the ket field is summed over the warp in df64 and added to memory as two FP64
+//     atomics (hi and lo), converted from float by exponent re-biasing on the integer pipe.
+// Values below the FP32 normal range (~1e-38) are flushed to zero, far below every tolerance.
+// Classes with L_P >= 3 (d shells) and L_P + L_Q >= 5 use the native FP64 kernels.
+#include "common.cuh"
+#include "internal.hpp"
+
+namespace fef {
+
+namespace {
+
+struct df64 {
+    float hi, lo;
+    df64() = default;
+    __device__ __forceinline__ df64(float h, float l) : hi(h), lo(l) {}
+    __device__ __forceinline__ explicit df64(int i) : hi((float)i), lo(0.0f) {}
+};
+
+__device__ __forceinline__ df64 quick_two_sum(float a, float b)  // |a| >= |b|
+{
+    const float s = __fadd_rn(a, b);
+    return df64(s, __fsub_rn(b, __fsub_rn(s, a)));
+}
+
+__device__ __forceinline__ df64 two_sum(float a, float b)
+{
+    const float s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    return df64(s, __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb)));
+}
+
+__device__ __forceinline__ df64 operator+(df64 a, df64 b)
+{
+    const df64 t = two_sum(a.hi, b.hi);
+    return quick_two_sum(t.hi, __fadd_rn(t.lo, __fadd_rn(a.lo, b.lo)));
+}
+
+__device__ __forceinline__ df64 operator-(df64 a) { return df64(-a.hi, -a.lo); }
+__device__ __forceinline__ df64 operator-(df64 a, df64 b) { return a + (-b); }
+
+__device__ __forceinline__ df64 operator*(df64 a, df64 b)
+{
+    const float p = __fmul_rn(a.hi, b.hi);
+    float e = __fmaf_rn(a.hi, b.hi, -p);
+    e = __fmaf_rn(a.hi, b.lo, e);
+    e = __fmaf_rn(a.lo, b.hi, e);
+    return quick_two_sum(p, e);
+}
+
+// a b + c
+__device__ __forceinline__ df64 fma(df64 a, df64 b, df64 c)
+{
+    const float p = __fmul_rn(a.hi, b.hi);
+    float e = __fmaf_rn(a.hi, b.hi, -p);
+    e = __fmaf_rn(a.hi, b.lo, e);
+    e = __fmaf_rn(a.lo, b.hi, e);
+    const df64 t = two_sum(p, c.hi);
+    return quick_two_sum(t.hi, __fadd_rn(t.lo, __fadd_rn(e, c.lo)));
+}
+
+__device__ __forceinline__ df64 shfl_xor(df64 v, int o)
+{
+    return df64(__shfl_xor_sync(0xffffffffu, v.hi, o), __shfl_xor_sync(0xffffffffu, v.lo, o));
+}
+
+// 1/sqrt(x), x > 0: float seed, one float Newton step, one df64 Newton step (relative error ~1e-14).
+__device__ __forceinline__ df64 rsqrt_df(df64 x)
+{
+    float r = rsqrtf(x.hi);
+    r = r * (1.5f - 0.5f * x.hi * r * r);
+    const df64 y(r, 0.0f);
+    const df64 e = df64(1.0f, 0.0f) - x * (y * y);  // ~1e-7
+    return quick_two_sum(r, 0.5f * r * e.hi);
+}
+
+// float -> double by exponent re-biasing on the integer pipe (no FP64 instruction).  Zero and
+// subnormal floats give 0; Inf and NaN give NaN.
+__device__ __forceinline__ double f2d(float f)
+{
+    const unsigned u = __float_as_uint(f);
+    const unsigned ex = (u >> 23) & 0xffu, man = u & 0x7fffffu, sign = u & 0x80000000u;
+    unsigned hi = sign | ((ex + 896u) << 20) | (man >> 3);
+    unsigned lo = man << 29;
+    if (ex == 0u) { hi = sign; lo = 0u; }
+    if (ex == 255u) { hi = 0x7ff80000u; lo = 0u; }
+    return __hiloint2double((int)hi, (int)lo);
+}
+
+__device__ __forceinline__ df64 ld_df(const float2* p)
+{
+    const float2 v = __ldg(p);
+    return df64(v.x, v.y);
+}
+
+constexpr float kSqrtPiHalfHi = (float)kSqrtPiHalf;
+constexpr float kSqrtPiHalfLo = (float)(kSqrtPiHalf - (double)(float)kSqrtPiHalf);
+
+// F_0..F_L at T in df64 from the df64 copy of the grid-Taylor table (row kidx from an FP32 T).
+template <int L>
+__device__ __forceinline__ void boys_df(const float2* __restrict__ table, df64 T, int kidx, df64* F)
+{
+    if (kidx < kBoysRows - 1) {
+        const float2* row = table + (size_t)kidx * kBoysRowLen;
+        const df64 d = ld_df(row + kBoysOrder + 1) - T;
+#pragma unroll
+        for (int m = 0; m <= L; ++m) {
+            const float2* c = row + m * kBoysBlock;
+            const float4 c01 = __ldg(reinterpret_cast<const float4*>(c));
+            const float4 c23 = __ldg(reinterpret_cast<const float4*>(c + 2));
+            const float4 c45 = __ldg(reinterpret_cast<const float4*>(c + 4));
+            const float2 c6 = __ldg(c + 6);
+            df64 f = fma(d, df64(c6.x, c6.y), df64(c45.z, c45.w));
+            f = fma(d, f, df64(c45.x, c45.y));
+            f = fma(d, f, df64(c23.z, c23.w));
+            f = fma(d, f, df64(c23.x, c23.y));
+            f = fma(d, f, df64(c01.z, c01.w));
+            F[m] = fma(d, f, df64(c01.x, c01.y));
+        }
+    } else {
+        const df64 r = rsqrt_df(T);
+        const df64 half_inv_T = df64(0.5f, 0.0f) * (r * r);
+        F[0] = df64(kSqrtPiHalfHi, kSqrtPiHalfLo) * r;
+#pragma unroll
+        for (int m = 1; m <= L; ++m) F[m] = F[m - 1] * (half_inv_T * df64(2 * m - 1));
+    }
+}
+
+constexpr int kFlushKets = 32;
+
+template <int LP, int LQ>
+__global__ void __launch_bounds__(128) k_jengine_df(Dev d, const int2* __restrict__ tiles, int n_tiles, float tau)
+{
+    constexpr int NP = nh(LP), NQ = nh(LQ), L = LP + LQ, NR = nh(LP + LQ);
+    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (warp >= n_tiles) return;
+    const int2 tl = tiles[warp];
+    const int pr = tl.x >> 1;
+    const int x = (tl.x & 1) ? d.pair_y[pr] : d.pair_x[pr];
+    const int y = (tl.x & 1) ? d.pair_x[pr] : d.pair_y[pr];
+    const int bra_end = d.frag_pp0[x * kClasses + LP] + d.frag_npp[x * kClasses + LP];
+    const int Pg = tl.y + lane;
+    const bool valid = Pg < bra_end;
+    const int Pl = valid ? Pg : tl.y;
+    const int nP = d.n_pp[LP], nQ = d.n_pp[LQ];
+    const float4 Ph = d.pp_Phi[LP][Pl], Plo = d.pp_Plo[LP][Pl];
+    const df64 Px(Ph.x, Plo.x), Py(Ph.y, Plo.y), Pz(Ph.z, Plo.z), p(Ph.w, Plo.w);
+    const float4 Pf = d.pp_Pf[LP][Pl];
+    const float qP = valid ? d.pp_Q[LP][Pl] : 0.0f;
+    df64 DP[NP], JP[NP];
+    double JP64[NP];
+#pragma unroll
+    for (int i = 0; i < NP; ++i) {
+        DP[i] = valid ? ld_df(d.pp_Dhdf[LP] + (size_t)i * nP + Pl) : df64(0.0f, 0.0f);
+        JP[i] = df64(0.0f, 0.0f);
+        JP64[i] = 0.0;
+    }
+    const int k0 = d.frag_pp0[y * kClasses + LQ];
+    const int k1 = k0 + d.frag_npp[y * kClasses + LQ];
+    const float4* __restrict__ QH = d.pp_Phi[LQ];
+    const float4* __restrict__ QL = d.pp_Plo[LQ];
+    const float4* __restrict__ QPf = d.pp_Pf[LQ];
+    const float* __restrict__ QQ = d.pp_Q[LQ];
+    const float2* __restrict__ QD = d.pp_Dhdf[LQ];
+    double* __restrict__ QJ = d.pp_Jh[LQ];
+    int since_flush = 0;
+    for (int k = k0; k < k1; ++k) {
+        const float qQ = __ldg(QQ + k);
+        const bool keep = qP * qQ >= tau;
+        if (!__any_sync(0xffffffffu, keep)) continue;
+        const float4 Qh = __ldg(QH + k), Ql = __ldg(QL + k);
+        const float4 Qf = __ldg(QPf + k);
+        df64 DQ[NQ];
+#pragma unroll
+        for (int j = 0; j < NQ; ++j) DQ[j] = ld_df(QD + (size_t)j * nQ + k);
+        const df64 X = Px - df64(Qh.x, Ql.x), Y = Py - df64(Qh.y, Ql.y), Z = Pz - df64(Qh.z, Ql.z);
+        const df64 q(Qh.w, Ql.w);
+        const df64 R2 = fma(X, X, fma(Y, Y, Z * Z));
+        const df64 r = rsqrt_df(p + q);
+        const df64 alpha = (p * q) * (r * r);
+        const df64 T = alpha * R2;
+        const float Xf = Pf.x - Qf.x, Yf = Pf.y - Qf.y, Zf = Pf.z - Qf.z;
+        const float Tf = __fdividef(Pf.w * Qf.w, Pf.w + Qf.w) * fmaf(Xf, Xf, fmaf(Yf, Yf, Zf * Zf));
+        df64 F[L + 1];
+        boys_df<L>(d.boysdf, T, boys_row(Tf), F);
+        df64 base[L + 1];
+        df64 pre = keep ? r : df64(0.0f, 0.0f);
+        const df64 m2a(-2.0f * alpha.hi, -2.0f * alpha.lo);
+#pragma unroll
+        for (int n = 0; n <= L; ++n) {
+            base[n] = pre * F[n];
+            if (n < L) pre = pre * m2a;
+        }
+        df64 R[NR];
+        md_R<L, df64>(R, base, X, Y, Z);
+        // field on the bra pair (registers)
+        static_for<NP>([&](auto I) {
+            constexpr TUV a = htuv(decltype(I)::value);
+            df64 acc = JP[decltype(I)::value];
+            static_for<NQ>([&](auto Jc) {
+                constexpr TUV b = htuv(decltype(Jc)::value);
+                constexpr int rr = hidx(a.t + b.t, a.u + b.u, a.v + b.v);
+                if constexpr (((b.t + b.u + b.v) & 1) != 0)
+                    acc = fma(-R[rr], DQ[decltype(Jc)::value], acc);
+                else
+                    acc = fma(R[rr], DQ[decltype(Jc)::value], acc);
+            });
+            JP[decltype(I)::value] = acc;
+        });
+        // field on the ket pair: warp sum in df64, then FP64 atomics (hi and lo) by lanes 0..NQ-1
+        df64 sq[NQ];
+        static_for<NQ>([&](auto Jc) {
+            constexpr TUV b = htuv(decltype(Jc)::value);
+            df64 s(0.0f, 0.0f);
+            static_for<NP>([&](auto I) {
+                constexpr TUV a = htuv(decltype(I)::value);
+                s = fma(R[hidx(a.t + b.t, a.u + b.u, a.v + b.v)], DP[decltype(I)::value], s);
+            });
+            sq[decltype(Jc)::value] = ((b.t + b.u + b.v) & 1) ? -s : s;
+        });
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1)
+            static_for<NQ>([&](auto Jc) { sq[decltype(Jc)::value] = sq[decltype(Jc)::value] + shfl_xor(sq[decltype(Jc)::value], o); });
+        df64 mine = sq[0];
+        static_for<NQ>([&](auto Jc) {
+            if (lane == decltype(Jc)::value) mine = sq[decltype(Jc)::value];
+        });
+        if (lane < NQ) {
+            double* dst = QJ + (size_t)lane * nQ + k;
+            atomicAdd(dst, f2d(mine.hi));
+            atomicAdd(dst, f2d(mine.lo));
+        }
+        if (++since_flush == kFlushKets) {
+            since_flush = 0;
+#pragma unroll
+            for (int i = 0; i < NP; ++i) {
+                JP64[i] += f2d(JP[i].hi) + f2d(JP[i].lo);
+                JP[i] = df64(0.0f, 0.0f);
+            }
+        }
+    }
+    if (valid) {
+#pragma unroll
+        for (int i = 0; i < NP; ++i)
+            atomicAdd(d.pp_Jh[LP] + (size_t)i * nP + Pg, JP64[i] + (f2d(JP[i].hi) + f2d(JP[i].lo)));
+    }
+}
+
+template <int LP, int LQ>
+void launch_df_one(const Dev& d, const int2* t, int n, float tau, cudaStream_t s)
+{
+    if (n <= 0) return;
+    const int warps_per_block = 4;
+    k_jengine_df<LP, LQ><<<(n + warps_per_block - 1) / warps_per_block, 32 * warps_per_block, 0, s>>>(d, t, n, tau);
+    note_launches(1);
+}
+
+// df64 copies of the FP64 pair data and Boys table (once per geometry)
+__global__ void k_split_pairs(const double4_32a* __restrict__ P, float4* hi, float4* lo, int n)
+{
+    const int g = blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= n) return;
+    const double4_32a v = P[g];
+    const float hx = (float)v.x, hy = (float)v.y, hz = (float)v.z, hw = (float)v.w;
+    hi[g] = make_float4(hx, hy, hz, hw);
+    lo[g] = make_float4((float)(v.x - hx), (float)(v.y - hy), (float)(v.z - hz), (float)(v.w - hw));
+}
+
+__global__ void k_split_array(const double* __restrict__ a, float2* out, size_t n)
+{
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+        const double v = a[i];
+        const float h = (float)v;
+        out[i] = make_float2(h, (float)(v - h));
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_df_setup(const Dev& d, float4* const Phi[kClasses], float4* const Plo[kClasses], float2* boysdf,
+                            cudaStream_t s)
+{
+    for (int L = 0; L < kClasses; ++L) {
+        if (d.n_pp[L] == 0) continue;
+        k_split_pairs<<<(d.n_pp[L] + 127) / 128, 128, 0, s>>>(d.pp_P[L], Phi[L], Plo[L], d.n_pp[L]);
+        note_launches(1);
+    }
+    const size_t nb = (size_t)kBoysRows * kBoysRowLen;
+    k_split_array<<<(unsigned)((nb + 255) / 256), 256, 0, s>>>(d.boys, boysdf, nb);
+    note_launches(1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_df_density(const Dev& d, cudaStream_t s)
+{
+    for (int L = 0; L < kClasses; ++L) {
+        const size_t n = (size_t)nh(L) * d.n_pp[L];
+        if (n == 0) continue;
+        k_split_array<<<(unsigned)std::min<size_t>((n + 255) / 256, 2048), 256, 0, s>>>(d.pp_Dh[L], d.pp_Dhdf[L], n);
+        note_launches(1);
+    }
+    return cudaGetLastError();
+}
+
+// Class pairs with L_P <= 2 in df64; the others (d shells) in native FP64.
+cudaError_t launch_jengine_df(const Dev& d, const int2* tiles[kClasses][kClasses], const int* n_tiles, float tau,
+                              cudaStream_t s)
+{
+#define FEF_JD(LP, LQ) launch_df_one<LP, LQ>(d, tiles[LP][LQ], n_tiles[LP * kClasses + LQ], tau, s)
+    FEF_JD(0, 0); FEF_JD(1, 0); FEF_JD(1, 1); FEF_JD(2, 0); FEF_JD(2, 1); FEF_JD(2, 2);
+#undef FEF_JD
+    return cudaGetLastError();
+}
+
+}  // namespace fef

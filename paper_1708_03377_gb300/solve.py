@@ -29,6 +29,8 @@ def main(argv=None):
     ap.add_argument("--schwarz", type=float, default=1e-12)
     ap.add_argument("--e-tol", type=float, default=1e-8)
     ap.add_argument("--precision", choices=("fp64", "mixed"), default="fp64")
+    ap.add_argument("--engine", choices=("fp64", "df64"), default="fp64",
+                    help="J-engine of the FP64-accurate builds: native FP64 or float-float")
     ap.add_argument("--repeat", type=int, default=1)
     ap.add_argument("--build-only", action="store_true")
     a = ap.parse_args(argv)
@@ -39,7 +41,9 @@ def main(argv=None):
 
     system = S.water_box(a.waters, seed=a.seed)
     prec = fef.FEF_MIXED if a.precision == "mixed" else fef.FEF_FP64
-    opts = fef.fef_default_options(cutoff_A=a.cutoff, schwarz=a.schwarz, e_tol=a.e_tol, precision=prec)
+    eng = fef.FEF_ENGINE_DF64 if a.engine == "df64" else fef.FEF_ENGINE_FP64
+    opts = fef.fef_default_options(cutoff_A=a.cutoff, schwarz=a.schwarz, e_tol=a.e_tol, precision=prec,
+                                   exact_engine=eng)
     stream = torch.cuda.Stream()
     with torch.cuda.stream(stream):
         for _ in range(a.repeat):
