@@ -10,7 +10,14 @@ nuclear field, orthogonalisers, work lists) + fef_iterate (superposition start, 
 Hermite densities, J-engine, Fock assembly, device fragment SCF, energies) + fef_energies.
 
 value  = inter-fragment shell quartets processed (surviving quartets x Fock builds) / device time,
-         CUDA events on the context stream, L2 flushed (256 MiB write) between steps.
+         CUDA events on the context stream, L2 flushed (256 MiB write) between steps; FP64 mode,
+         native FP64 J-engine.
+Legs reported beside it (same workload, same 1e-8 Eh convergence, energies compared to FP64):
+  df64                 FP64-accurate solve with the float-float J-engine (FP32 pipes);
+  mixed_fp64_reference MIXED: FP32-core increments, native FP64 reference build;
+  mixed                MIXED with the float-float reference build;
+  mixed_learned        MIXED (float-float reference) from the learned warm start; the network is
+                       trained beforehand (not timed) on 40 seeded snapshots drawn like the workload.
 e2e    = the same step plus the device->host read of every converged density, wall clock.
 roofline: the J-engine (9 class-pair kernels of one Fock build) against the FP64 ALU peak.
 --impl reference: the CPU oracle on a bounded sample of the same workload.
@@ -306,7 +313,15 @@ def main():
                     "value": res["stats"]["shell_quartets"] * (res["n_macro"] + 1) / (float(np.mean(step_ms)) * 1e-3),
                     "speedup_time_to_1e-8_vs_fp64": float(np.mean(iter_ms)) / float(np.mean(it_ms))}
 
-        mopts = fef.fef_default_options(cutoff_A=CUTOFF_A, schwarz=SCHWARZ, e_tol=E_TOL, precision=fef.FEF_MIXED)
+        DF = fef.FEF_ENGINE_DF64
+        # FP64-accurate solve with the float-float J-engine (same iteration, FP64 eigensolve/energies)
+        dopts = fef.fef_default_options(cutoff_A=CUTOFF_A, schwarz=SCHWARZ, e_tol=E_TOL, exact_engine=DF)
+        df_ms, df_step_ms, dres = variant(dopts)
+        # MIXED with the native FP64 reference build, and with the float-float one
+        mfopts = fef.fef_default_options(cutoff_A=CUTOFF_A, schwarz=SCHWARZ, e_tol=E_TOL, precision=fef.FEF_MIXED)
+        mixed64_ms, mixed64_step_ms, m64res = variant(mfopts)
+        mopts = fef.fef_default_options(cutoff_A=CUTOFF_A, schwarz=SCHWARZ, e_tol=E_TOL, precision=fef.FEF_MIXED,
+                                        exact_engine=DF)
         mixed_ms, mixed_step_ms, mres = variant(mopts)
         # MIXED + learned warm start: the network is trained beforehand (not timed) on converged densities
         # of 40 seeded snapshots drawn like the workload (64 waters at 1 g/cm^3, its basis)
@@ -322,7 +337,7 @@ def main():
                 pass
         net, net_loss = lrn.train_warm_start(np.concatenate(Xs), np.concatenate(Ts), hidden=256, epochs=300, batch=128)
         lopts = fef.fef_default_options(cutoff_A=CUTOFF_A, schwarz=SCHWARZ, e_tol=E_TOL, precision=fef.FEF_MIXED,
-                                        start=fef.FEF_START_LEARNED)
+                                        start=fef.FEF_START_LEARNED, exact_engine=DF)
         ml_ms, ml_step_ms, mlres = variant(lopts, warm=net)
         # e2e: the same step through the public API plus the density read-back, wall clock
         e2e_ms = []
@@ -369,10 +384,15 @@ def main():
         "n_macro": last["n_macro"], "fock_builds_per_step": builds,
         "shell_quartets_per_build": st["shell_quartets"], "prim_quartets_per_build": int(np.sum(st["class_quartets"])),
         "E_tot": last["E_tot"],
-        "mixed": {**summary(mixed_ms, mixed_step_ms, mres),
+        "df64": {**summary(df_ms, df_step_ms, dres), "exact_engine": "df64 (float-float on the FP32 pipes)",
+                 "jengine_ms_per_build": float(np.mean([h["jengine_ms"] for h in dres["hist"]])),
+                 "fp64_equivalent_tflops": flops_build / (float(np.mean([h["jengine_ms"] for h in dres["hist"]])) * 1e-3) / 1e12},
+        "mixed_fp64_reference": {**summary(mixed64_ms, mixed64_step_ms, m64res), "exact_engine": "fp64"},
+        "mixed": {**summary(mixed_ms, mixed_step_ms, mres), "exact_engine": "df64",
                   "jengine_fp32_ms_per_build": float(np.mean([h["jengine_ms"] for h in mres["hist"] if h["fp32"]]
                                                              or [0.0]))},
-        "mixed_learned": {**summary(ml_ms, ml_step_ms, mlres), "train_samples": int(sum(len(x) for x in Xs)),
+        "mixed_learned": {**summary(ml_ms, ml_step_ms, mlres), "exact_engine": "df64",
+                          "train_samples": int(sum(len(x) for x in Xs)),
                           "train_loss": net_loss},
         "roofline": {"bound": "alu", "achieved": achieved / 1e12, "peak": FP64_PEAK / 1e12, "unit": "TFLOP/s",
                      "frac": achieved / FP64_PEAK, "traffic": profile_traffic(),
