@@ -236,7 +236,9 @@ def main():
         pg = dist
     stream = torch.cuda.Stream()
     system = S.water_box(N_WATER, seed=rank)
-    opts = fef.fef_default_options(cutoff_A=CUTOFF_A, schwarz=SCHWARZ, e_tol=E_TOL)
+    # FP64 leg with eager launches: its J-engine time per build comes from CUDA events on the
+    # context stream (inside a captured graph the library times phases with device timestamps)
+    opts = fef.fef_default_options(cutoff_A=CUTOFF_A, schwarz=SCHWARZ, e_tol=E_TOL, use_graph=0)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
     fef.lib()
     fp64_probe, fp32_probe, _ = fef.fef_measure_fma_peak()

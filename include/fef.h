@@ -100,7 +100,9 @@ typedef struct {
     int32_t max_micro;       /* fragment RHF iterations limit per macro-iteration */
     int32_t diis_size;       /* Pulay DIIS subspace size, 1..8 (1 = plain Roothaan) */
     int32_t start;           /* FEF_START_*: initial densities */
-    int32_t use_graph;       /* capture each macro-iteration's device work in a CUDA graph */
+    int32_t use_graph;       /* 1 (default): each macro-iteration (fragment SCF, Fock build, read-back) is
+                                one CUDA graph launch, captured on first use per kind of build; 0: eager
+                                launches */
     int32_t deterministic;   /* reserved: 1 requests run-to-run identical sums */
     double mixed_switch;     /* MIXED: coarse FP32-core macro-iterations until |dE| < mixed_switch */
     int32_t exact_engine;    /* J-engine of the FP64-accurate builds (every build in FEF_FP64, the
@@ -112,7 +114,7 @@ typedef struct {
 
 /* Fill *opt with the defaults: FP64, no cutoff, schwarz 1e-12, e_tol 1e-8, micro_e_tol 1e-11,
  * micro_comm_tol 1e-9, max_macro 100, max_micro 200, diis_size 8, superposition start, no graph,
- * mixed_switch 1e-6. */
+ * mixed_switch 1e-6, use_graph 1, exact_engine FEF_ENGINE_FP64. */
 void fef_default_options(fef_options* opt);
 
 /* Build a context: validate and copy the inputs, then on the device normalise the basis, build
@@ -147,6 +149,16 @@ fef_status fef_build_fock(fef_ctx* ctx, const double* D, double* F_out, int on_d
  * n_macro_out (nullable): macro-iterations done; final_dE_out (nullable): last |dE_tot|.
  * Errors: NOT_CONVERGED (context stays valid, densities are the last iterate), NUMERIC, CUDA. */
 fef_status fef_iterate(fef_ctx* ctx, int32_t* n_macro_out, double* final_dE_out);
+
+/* The non-interacting mean field (Theory, "Fragment Mean Field", the first of the two mean-field
+ * choices: F = h(1) + (2J - K) per fragment, inter-fragment terms left to perturbation theory).
+ * Solves every fragment's RHF without environment field (core guess, DIIS) and makes these
+ * densities the current ones, so that fef_energies then gives the energies of the unperturbed
+ * product state (E_x^int + half the first-order pair terms) and fef_build_fock(ctx, NULL, ...)
+ * the Fock matrices with omega_x built from the unperturbed densities of the other fragments.
+ * These are also the superposition start of fef_iterate.
+ * Errors: NOT_CONVERGED (a fragment RHF; densities are the last iterate), NUMERIC, CUDA. */
+fef_status fef_noninteracting_scf(fef_ctx* ctx);
 
 /* Reference energies of the current densities (from <H_x> and <H_xy> of the Hamiltonian partition,
  * Eqs. NHx, NHxy, clusterH, pairs counted once):

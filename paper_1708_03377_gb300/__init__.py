@@ -29,7 +29,8 @@ EXPORTED = ["fef_default_options", "fef_create", "fef_ao_layout", "fef_build_foc
             "fef_get_densities", "fef_set_densities", "fef_stats", "fef_last_error", "fef_destroy",
             "fef_measure_fma_peak", "fef_fragment_rhf_noalloc", "fef_history", "fef_mlp_create", "fef_mlp_destroy",
             "fef_mlp_params", "fef_mlp_set_scaling", "fef_mlp_loss_grad", "fef_mlp_train", "fef_mlp_predict",
-            "fef_mlp_last_error", "fef_learned_features", "fef_set_warm_start"]
+            "fef_mlp_last_error", "fef_learned_features", "fef_set_warm_start",
+            "fef_noninteracting_scf"]
 
 
 class FefError(RuntimeError):
@@ -85,6 +86,7 @@ def lib():
     L.fef_ao_layout.argtypes = [vp, ip, i64p]
     L.fef_build_fock.argtypes = [vp, vp, vp, ctypes.c_int]
     L.fef_iterate.argtypes = [vp, ip, dp]
+    L.fef_noninteracting_scf.argtypes = [vp]
     L.fef_energies.argtypes = [vp, dp, dp, dp]
     L.fef_get_densities.argtypes = [vp, vp, ctypes.c_int]
     L.fef_set_densities.argtypes = [vp, vp, ctypes.c_int]
@@ -234,6 +236,11 @@ def fef_iterate(ctx: Context):
     de = ctypes.c_double(0.0)
     _check(lib().fef_iterate(ctx.ptr, ctypes.byref(n), ctypes.byref(de)), ctx.ptr)
     return n.value, de.value
+
+
+def fef_noninteracting_scf(ctx: Context):
+    """Isolated-fragment RHF densities become the current densities (the non-interacting mean field)."""
+    _check(lib().fef_noninteracting_scf(ctx.ptr), ctx.ptr)
 
 
 def fef_energies(ctx: Context):

@@ -52,8 +52,21 @@ struct Buffers {
     }
     ~Buffers()
     {
+        for (auto& g : macro_graph)
+            if (g) cudaGraphExecDestroy(g);
+        if (capture_stream) cudaStreamDestroy(capture_stream);
+        if (stage) cudaFreeHost(stage);
         for (void* p : allocs) cudaFree(p);
     }
+    // one CUDA graph per kind of macro-iteration (fragment SCF + Fock build + read-back), built on
+    // first use; launches of this library inside each graph
+    cudaGraphExec_t macro_graph[3] = {};
+    cudaStream_t capture_stream = nullptr;  // private stream for captures (the context stream may be the legacy one)
+    bool capturing = false;
+    unsigned long long* stamps = nullptr;   // [4] device timestamps of the phase marks in graph mode
+    long long macro_graph_launches[3] = {};
+    // pinned read-back of one macro-iteration: E_tot, error flag, E_frag[n], iters[n]
+    unsigned char* stage = nullptr;
     // geometry-time data
     double *S = nullptr, *h = nullptr, *X = nullptr, *Venv = nullptr, *eric = nullptr, *boys = nullptr;
     double* scf_ws = nullptr;  // fragment-SCF workspace for fragments above kScfSmemMaxN AOs
@@ -137,7 +150,7 @@ extern "C" void fef_default_options(fef_options* o)
     o->max_micro = 200;
     o->diis_size = 8;
     o->start = FEF_START_SUPERPOSITION;
-    o->use_graph = 0;
+    o->use_graph = 1;
     o->deterministic = 0;
     o->mixed_switch = 1e-6;
     o->exact_engine = FEF_ENGINE_FP64;
@@ -170,12 +183,40 @@ static void clear_flags(fef_ctx* c)
 // reference, whose error is then the same for every later increment relative to it.
 enum BuildKind { kBuildFP64 = 0, kBuildFP32Inc = 1, kBuildFP32Ref = 2 };
 
-static void build_fock_internal(fef_ctx* c, int kind = kBuildFP64)
+// Device timestamp (ns, %globaltimer) at this point of the stream: the per-phase timing inside a
+// captured graph, where events cannot be timed.
+__global__ void k_timestamp(unsigned long long* t)
+{
+    unsigned long long v;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(v));
+    *t = v;
+}
+
+// Phase marks: CUDA events when launching eagerly, device timestamps while capturing.
+static void mark(fef_ctx* c, int i)
+{
+    Buffers* b = c->buf;
+    if (b->capturing) {
+        k_timestamp<<<1, 1, 0, c->stream>>>(b->stamps + i);
+        note_launches(1);
+        ck(cudaGetLastError(), "timestamp");
+    } else {
+        cudaEvent_t ev[4] = {b->ev0, b->ev1, b->ev2, b->ev3};
+        ck(cudaEventRecord(ev[i], c->stream), "event");
+    }
+}
+
+static int resolve_kind(const fef_ctx* c, int kind)
+{
+    return (kind == kBuildFP32Inc && !c->buf->have_ref) ? kBuildFP64 : kind;
+}
+
+// Device work of a build of a resolved kind (stream-ordered only, so that it can be captured).
+static void build_fock_device(fef_ctx* c, int kind)
 {
     Buffers* b = c->buf;
     const Dev& d = c->dev;
     cudaStream_t s = c->stream;
-    if (kind == kBuildFP32Inc && !b->have_ref) kind = kBuildFP64;
     const bool fp32 = kind != kBuildFP64;
     ck(launch_hermite_density(d, b->D, s), "hermite density");
     for (int L = 0; L < kClasses; ++L) {
@@ -193,9 +234,9 @@ static void build_fock_internal(fef_ctx* c, int kind = kBuildFP64)
     const int2* tiles[kClasses][kClasses];
     for (int i = 0; i < kClasses; ++i)
         for (int j = 0; j < kClasses; ++j) tiles[i][j] = b->tiles[i][j];
-    ck(cudaEventRecord(b->ev0, s), "event");
+    mark(c, 0);
     ck(launch_jengine(d, tiles, b->n_tiles, c->opt.schwarz, fp32 ? 1 : (df ? 2 : 0), s), "J-engine");
-    ck(cudaEventRecord(b->ev1, s), "event");
+    mark(c, 1);
     if (kind != kBuildFP32Inc) {
         for (int L = 0; L < kClasses; ++L) {
             if (b->njh[L] == 0) continue;
@@ -203,10 +244,7 @@ static void build_fock_internal(fef_ctx* c, int kind = kBuildFP64)
             ck(cudaMemcpyAsync(b->Dh_ref[L], d.pp_Dh[L], sizeof(double) * b->njh[L], cudaMemcpyDeviceToDevice, s),
                "ref");
         }
-        b->have_ref = true;
-        b->ref_exact = kind == kBuildFP64;
     }
-    c->last_build_fp32 = fp32;
     ck(launch_back_transform(d, b->Jenv, s), "back-transform");
     ck(launch_fock_energy(d, b->h, b->Venv, b->Jenv, b->eric, b->D, b->F, b->omega, b->e_nn_intra, b->E_int,
                           b->trV, b->trJ, s),
@@ -215,7 +253,24 @@ static void build_fock_internal(fef_ctx* c, int kind = kBuildFP64)
     ck(launch_energies(d, b->E_int, b->trV, b->trJ, b->tr_xy, b->tr_yx, b->e_nn_pair, b->E_frag, b->E_tot, s),
        "energies");
     ck(launch_check_finite(b->F, c->mat_total, b->err_flag, s), "check");
+}
+
+// Host-side state after a build of a resolved kind.
+static void build_fock_host(fef_ctx* c, int kind)
+{
+    if (kind != kBuildFP32Inc) {
+        c->buf->have_ref = true;
+        c->buf->ref_exact = kind == kBuildFP64;
+    }
+    c->last_build_fp32 = kind != kBuildFP64;
     c->energies_valid = true;
+}
+
+static void build_fock_internal(fef_ctx* c, int kind = kBuildFP64)
+{
+    kind = resolve_kind(c, kind);
+    build_fock_device(c, kind);
+    build_fock_host(c, kind);
 }
 
 static void run_scf(fef_ctx* c, bool with_field, bool have_start)
@@ -244,9 +299,9 @@ static void run_scf(fef_ctx* c, bool with_field, bool have_start)
     a.comm_tol = c->opt.micro_comm_tol;
     a.ws = b->scf_ws;
     a.diis_by_moff = 1;
-    ck(cudaEventRecord(b->ev2, c->stream), "event");
+    mark(c, 2);
     ck(launch_fragment_scf(c->dev, a, c->max_nao, c->stream), "fragment SCF");
-    ck(cudaEventRecord(b->ev3, c->stream), "event");
+    mark(c, 3);
     c->energies_valid = false;
 }
 
@@ -265,6 +320,86 @@ static void scf_counts(fef_ctx* c, double& max_it, double& sum_it, double& ms)
     float f = 0.f;
     ck(cudaEventElapsedTime(&f, c->buf->ev2, c->buf->ev3), "event time");
     ms = f;
+}
+
+// ------------------------------------------------------------------------------ one macro-iteration
+// Pinned read-back layout: E_tot at 0, error flag at 8, E_frag[n] at 16, iters[n] after E_frag.
+static double* stage_Et(fef_ctx* c) { return reinterpret_cast<double*>(c->buf->stage); }
+static int* stage_flag(fef_ctx* c) { return reinterpret_cast<int*>(c->buf->stage + 8); }
+static double* stage_Ex(fef_ctx* c) { return reinterpret_cast<double*>(c->buf->stage + 16); }
+static int* stage_iters(fef_ctx* c) { return reinterpret_cast<int*>(c->buf->stage + 16 + 8 * (size_t)c->n_frag); }
+static unsigned long long* stage_stamps(fef_ctx* c)
+{
+    return reinterpret_cast<unsigned long long*>(c->buf->stage + 16 + 16 * (size_t)c->n_frag);
+}
+
+// Device work of macro-iteration k >= 1: every fragment's RHF in the field omega^(k) (from D^(k-1)),
+// then the Fock build of the kind given from D^(k), then the read-back of the energies, the
+// micro-iteration counts and the error flag into pinned memory.  Stream-ordered only.
+static void macro_step_device(fef_ctx* c, int kind)
+{
+    Buffers* b = c->buf;
+    cudaStream_t s = c->stream;
+    run_scf(c, true, true);
+    build_fock_device(c, kind);
+    ck(cudaMemcpyAsync(stage_Et(c), b->E_tot, sizeof(double), cudaMemcpyDeviceToHost, s), "read-back");
+    ck(cudaMemcpyAsync(stage_flag(c), b->err_flag, sizeof(int), cudaMemcpyDeviceToHost, s), "read-back");
+    ck(cudaMemcpyAsync(stage_Ex(c), b->E_frag, sizeof(double) * c->n_frag, cudaMemcpyDeviceToHost, s), "read-back");
+    ck(cudaMemcpyAsync(stage_iters(c), b->iters, sizeof(int) * c->n_frag, cudaMemcpyDeviceToHost, s), "read-back");
+    if (b->capturing)
+        ck(cudaMemcpyAsync(stage_stamps(c), b->stamps, 4 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s),
+           "read-back");
+}
+
+// One macro-iteration: with opt.use_graph, replay the CUDA graph of this kind (captured on first
+// use: one graph launch instead of ~30 kernel launches and copies); then one synchronisation.
+static void macro_step(fef_ctx* c, int kind)
+{
+    Buffers* b = c->buf;
+    if (c->opt.use_graph) {
+        if (!b->macro_graph[kind]) {
+            // captured on a private non-blocking stream (the legacy default stream cannot be
+            // captured), replayed on the context stream
+            if (!b->capture_stream)
+                ck(cudaStreamCreateWithFlags(&b->capture_stream, cudaStreamNonBlocking), "capture stream");
+            ck(cudaStreamSynchronize(c->stream), "graph capture");
+            const long long l0 = launches_so_far();
+            cudaGraph_t g = nullptr;
+            const cudaStream_t user = c->stream;
+            c->stream = b->capture_stream;
+            b->capturing = true;
+            // relaxed: the launchers set kernel attributes (cudaFuncSetAttribute) while capturing
+            cudaError_t e0 = cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeRelaxed);
+            if (e0 != cudaSuccess) {
+                c->stream = user;
+                b->capturing = false;
+            }
+            ck(e0, "graph capture");
+            try {
+                macro_step_device(c, kind);
+            } catch (...) {
+                cudaStreamEndCapture(c->stream, &g);
+                if (g) cudaGraphDestroy(g);
+                c->stream = user;
+                b->capturing = false;
+                throw;
+            }
+            const cudaError_t e1 = cudaStreamEndCapture(c->stream, &g);
+            c->stream = user;
+            b->capturing = false;
+            ck(e1, "graph capture");
+            const cudaError_t e = cudaGraphInstantiate(&b->macro_graph[kind], g, 0);
+            cudaGraphDestroy(g);
+            ck(e, "graph instantiate");
+            b->macro_graph_launches[kind] = launches_so_far() - l0;
+            note_launches(-b->macro_graph_launches[kind]);  // nothing ran during the capture
+        }
+        ck(cudaGraphLaunch(b->macro_graph[kind], c->stream), "graph launch");
+        note_launches(b->macro_graph_launches[kind]);
+    } else {
+        macro_step_device(c, kind);
+    }
+    ck(cudaStreamSynchronize(c->stream), "macro-iteration");
 }
 
 // ---------------------------------------------------------------------------------------------- create
@@ -686,6 +821,8 @@ extern "C" fef_status fef_create(const fef_geometry* g, const fef_basis* bs, con
         b->E_scf = b->alloc<double>(nf, "E_scf");
         b->E_frag = b->alloc<double>(nf, "E_frag");
         b->E_tot = b->alloc<double>(1, "E_tot");
+        ck(cudaMallocHost(&b->stage, 16 + 16 * (size_t)nf + 32), "pinned read-back");
+        b->stamps = b->alloc<unsigned long long>(4, "timestamps");
         b->iters = b->alloc<int>(nf, "iters");
         // DIIS history at 2 diis_size frag_moff[x] (sized per fragment); SCF workspace in global
         // memory only for fragments too large for shared memory
@@ -890,6 +1027,23 @@ extern "C" fef_status fef_learned_features(fef_ctx* c, const double* D, float* X
     FEF_API_END(c)
 }
 
+extern "C" fef_status fef_noninteracting_scf(fef_ctx* c)
+{
+    if (!c) return FEF_ERR_ARG;
+    FEF_API_BEGIN
+    clear_flags(c);
+    run_scf(c, false, false);
+    int flag = 0;
+    ck(cudaMemcpyAsync(&flag, c->buf->err_flag, sizeof(int), cudaMemcpyDeviceToHost, c->stream), "flags");
+    ck(cudaStreamSynchronize(c->stream), "isolated RHF");
+    c->have_density = true;
+    c->energies_valid = false;
+    if (flag & kErrNumeric) throw Error{FEF_ERR_NUMERIC, "NaN/Inf in an isolated-fragment RHF"};
+    if (flag & kErrNotConv) throw Error{FEF_ERR_NOT_CONVERGED, "isolated-fragment RHF did not converge"};
+    return FEF_OK;
+    FEF_API_END(c)
+}
+
 extern "C" fef_status fef_iterate(fef_ctx* c, int32_t* n_macro_out, double* final_dE_out)
 {
     if (!c) return FEF_ERR_ARG;
@@ -951,18 +1105,31 @@ extern "C" fef_status fef_iterate(fef_ctx* c, int32_t* n_macro_out, double* fina
     bool prev_acc = !c->last_build_fp32;
     double dE_prev = 1e300;
     for (k = 1; k <= o.max_macro; ++k) {
-        run_scf(c, true, true);
-        build_fock_internal(c, next_fp32 ? kBuildFP32Inc : kBuildFP64);
+        const int kind = resolve_kind(c, next_fp32 ? kBuildFP32Inc : kBuildFP64);
+        macro_step(c, kind);
+        build_fock_host(c, kind);
         const bool this_fp64 = !c->last_build_fp32;
         const bool this_acc = this_fp64 || (fine && c->buf->ref_exact);
-        read_energies(c, Ex, Et);
-        scf_counts(c, it_max, it_sum, scf_ms);
-        float ms = 0.f;
-        ck(cudaEventElapsedTime(&ms, c->buf->ev0, c->buf->ev1), "event time");
+        Et = *stage_Et(c);
+        Ex.assign(stage_Ex(c), stage_Ex(c) + c->n_frag);
+        it_max = 0;
+        it_sum = 0;
+        for (int x = 0; x < c->n_frag; ++x) {
+            it_max = std::max<double>(it_max, std::abs(stage_iters(c)[x]));
+            it_sum += std::abs(stage_iters(c)[x]);
+        }
+        float ms = 0.f, sms = 0.f;
+        if (o.use_graph) {  // device timestamps of the graph's phase marks
+            const unsigned long long* t = stage_stamps(c);
+            ms = (float)((t[1] - t[0]) * 1e-6);
+            sms = (float)((t[3] - t[2]) * 1e-6);
+        } else {
+            ck(cudaEventElapsedTime(&ms, c->buf->ev0, c->buf->ev1), "event time");
+            ck(cudaEventElapsedTime(&sms, c->buf->ev2, c->buf->ev3), "event time");
+        }
+        scf_ms = sms;
         jms += ms;
-        int flag = 0;
-        ck(cudaMemcpyAsync(&flag, c->buf->err_flag, sizeof(int), cudaMemcpyDeviceToHost, c->stream), "flags");
-        ck(cudaStreamSynchronize(c->stream), "flags");
+        const int flag = *stage_flag(c);
         if (flag & kErrNumeric) throw Error{FEF_ERR_NUMERIC, "NaN/Inf during FEF iteration"};
         if (flag & kErrNotConv)
             throw Error{FEF_ERR_NOT_CONVERGED, "fragment RHF in the field did not converge at macro-iteration " +

@@ -244,3 +244,47 @@ def test_build_without_density_is_an_error(dimer):
     with pytest.raises(fef.FefError) as e:
         fef.fef_build_fock(ctx)
     assert e.value.status == fef.FEF_ERR_ARG
+
+
+def test_noninteracting_mean_field(box8):
+    """Non-interacting mean field: isolated-fragment RHF densities; energies of the unperturbed
+    product state and the Fock matrices with omega from unperturbed densities, against the oracle;
+    the same state is record 0 of fef_iterate's history."""
+    fef = _fef()
+    ref = _oracle(box8, cutoff_A=4.0, schwarz=1e-12)
+    iso = ref.isolated()
+    En = ref.energies(iso)
+    F_ref = ref.fock(iso)
+    ctx = fef.fef_create_system(box8, fef.fef_default_options(cutoff_A=4.0, schwarz=1e-12))
+    fef.fef_noninteracting_scf(ctx)
+    D = ctx.unpack(fef.fef_get_densities(ctx))
+    for x in range(ref.nf):
+        assert np.abs(D[x] - iso[x]).max() < 1e-6
+    # both sides converge each fragment RHF to |FDS - SDF| < 1e-9, so the densities agree to about
+    # that and the (first-order) interaction energies to ~1e-8
+    E_frag, E_tot, _ = fef.fef_energies(ctx)
+    assert abs(E_tot - En["E_tot"]) < 1e-8
+    assert np.abs(E_frag - En["E_x"]).max() < 1e-8
+    F = ctx.unpack(fef.fef_build_fock(ctx))
+    for x in range(ref.nf):
+        assert np.abs(F[x] - F_ref[x]).max() < 1e-6
+    fef.fef_iterate(ctx)
+    assert abs(fef.fef_history(ctx)[0]["E_tot"] - E_tot) < 1e-10
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_graph_and_eager_macro_iterations_agree(box8, precision):
+    """use_graph = 1 (one CUDA graph launch per macro-iteration) and use_graph = 0 (eager launches)
+    run the same iterations: same macro count, energies equal to rounding."""
+    fef = _fef()
+    prec = fef.FEF_MIXED if precision == "mixed" else fef.FEF_FP64
+    out = []
+    for g in (0, 1, 1):  # graph mode twice: each context captures its own graphs
+        ctx = fef.fef_create_system(box8, fef.fef_default_options(cutoff_A=4.0, schwarz=1e-12, e_tol=1e-10,
+                                                                  precision=prec, use_graph=g))
+        n, _ = fef.fef_iterate(ctx)
+        E_frag, E_tot, _ = fef.fef_energies(ctx)
+        out.append((n, E_tot, E_frag, fef.fef_stats(ctx)["kernel_launches"]))
+    assert out[0][0] == out[1][0] == out[2][0]
+    assert abs(out[0][1] - out[1][1]) < 1e-10 and abs(out[1][1] - out[2][1]) < 1e-10
+    assert np.abs(out[0][2] - out[1][2]).max() < 1e-10
