@@ -63,6 +63,8 @@ struct Buffers {
     cudaGraphExec_t macro_graph[3] = {};
     cudaStream_t capture_stream = nullptr;  // private stream for captures (the context stream may be the legacy one)
     bool capturing = false;
+    int64_t* trf_off = nullptr;             // [2 n_pairs + 1] offsets of the nuclear trace fields
+    double* trf = nullptr;                  // Hermite fields of each pair's nuclei (geometry time)
     unsigned long long* stamps = nullptr;   // [4] device timestamps of the phase marks in graph mode
     long long macro_graph_launches[3] = {};
     // pinned read-back of one macro-iteration: E_tot, error flag, E_frag[n], iters[n]
@@ -249,7 +251,7 @@ static void build_fock_device(fef_ctx* c, int kind)
     ck(launch_fock_energy(d, b->h, b->Venv, b->Jenv, b->eric, b->D, b->F, b->omega, b->e_nn_intra, b->E_int,
                           b->trV, b->trJ, s),
        "fock");
-    ck(launch_nuclear_traces(d, b->D, b->tr_xy, b->tr_yx, s), "nuclear traces");
+    ck(launch_nuclear_traces(d, b->trf_off, b->trf, b->tr_xy, b->tr_yx, s), "nuclear traces");
     ck(launch_energies(d, b->E_int, b->trV, b->trJ, b->tr_xy, b->tr_yx, b->e_nn_pair, b->E_frag, b->E_tot, s),
        "energies");
     ck(launch_check_finite(b->F, c->mat_total, b->err_flag, s), "check");
@@ -813,6 +815,19 @@ extern "C" fef_status fef_create(const fef_geometry* g, const fef_basis* bs, con
         b->Jenv = b->alloc<double>(c->mat_total, "Jenv");
         b->omega = b->alloc<double>(c->mat_total, "omega");
         ck(cudaMemsetAsync(b->D, 0, sizeof(double) * c->mat_total, s), "D");
+        {   // nuclear trace fields: per (pair, direction) sum_L nh(L) npp_x[L] doubles
+            std::vector<int64_t> off(2 * (size_t)c->n_pairs + 1, 0);
+            for (int p = 0; p < c->n_pairs; ++p)
+                for (int dir = 0; dir < 2; ++dir) {
+                    const int x = dir == 0 ? pair_x[p] : pair_y[p];
+                    int64_t w = 0;
+                    for (int L = 0; L < kClasses; ++L) w += (int64_t)nh(L) * frag_npp[x * kClasses + L];
+                    off[2 * p + dir + 1] = off[2 * p + dir] + w;
+                }
+            b->trf_off = b->upload(off, s, "trace fields");
+            b->trf = b->alloc<double>(std::max<int64_t>(off.back(), 1), "trace fields");
+            ck(launch_nuclear_trace_fields(d, b->trf_off, b->trf, s), "trace fields");
+        }
         b->tr_xy = b->alloc<double>(c->n_pairs, "tr");
         b->tr_yx = b->alloc<double>(c->n_pairs, "tr");
         b->trV = b->alloc<double>(nf, "trV");

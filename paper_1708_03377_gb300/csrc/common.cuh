@@ -63,6 +63,21 @@ constexpr int kBoysBlock = 8;
 constexpr int kBoysRowLen = kBoysM * kBoysBlock;  // 72 doubles
 constexpr int kBoysRows = 732;                    // covers T up to 36.55
 
+// float -> double by exponent re-biasing on the integer pipe (no FP64 instruction).  Zero and
+// subnormal floats give 0; Inf and NaN give NaN.
+__device__ __forceinline__ double f2d(float f)
+{
+    const unsigned u = __float_as_uint(f);
+    const unsigned ex = (u >> 23) & 0xffu, man = u & 0x7fffffu, sign = u & 0x80000000u;
+    unsigned hi = sign | ((ex + 896u) << 20) | (man >> 3);
+    unsigned lo = man << 29;
+    if (ex == 0u) { hi = sign; lo = 0u; }
+    if (ex == 255u) { hi = 0x7ff80000u; lo = 0u; }
+    return __hiloint2double((int)hi, (int)lo);
+}
+
+__device__ __forceinline__ double f2d(double v) { return v; }
+
 // -------------------------------------------------------------------------------- Hermite indexing
 // Hermite indices (t,u,v) with t+u+v <= L, ordered by level s = t+u+v, then t descending, then u
 // descending (the Cartesian lexicographic order of each level).

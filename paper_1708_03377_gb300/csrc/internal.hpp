@@ -157,7 +157,11 @@ cudaError_t launch_schwarz(const Dev& d, const double* eri, double* sp_Q, float*
 cudaError_t launch_coulomb_exchange(const Dev& d, const double* eri, double* eric, cudaStream_t s);
 cudaError_t launch_neighbours(const Dev& d, double cutoff_bohr, unsigned char* flags, cudaStream_t s);
 cudaError_t launch_nuclear_env(const Dev& d, double* vh[kClasses], double* V, cudaStream_t s);
-cudaError_t launch_nuclear_traces(const Dev& d, const double* D, double* trace_xy, double* trace_yx, cudaStream_t s);
+// Hermite fields of each pair's nuclei on the other member's primitive pairs (geometry time), and
+// per build tr[D^x V^y] per pair and direction as their dot product with the Hermite densities.
+cudaError_t launch_nuclear_trace_fields(const Dev& d, const int64_t* off, double* fields, cudaStream_t s);
+cudaError_t launch_nuclear_traces(const Dev& d, const int64_t* off, const double* fields, double* trace_xy,
+                                  double* trace_yx, cudaStream_t s);
 cudaError_t launch_nuclear_repulsion(const Dev& d, double* e_nn_intra, double* e_nn_pair, cudaStream_t s);
 // X = U s^{-1/2} (canonical); optionally S^{1/2} and S^{-1/2} (symmetric) into Sh, Sih
 cudaError_t launch_orthogonaliser(const Dev& d, const double* S, double* X, int* nmo, double s_min, int max_n,

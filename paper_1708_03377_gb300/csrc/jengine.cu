@@ -103,8 +103,12 @@ __device__ __forceinline__ void hermite_contract(const Real* R, const Real* DP, 
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1)
         static_for<NQ>([&](auto Jc) { sq[decltype(Jc)::value] += __shfl_xor_sync(0xffffffffu, sq[decltype(Jc)::value], o); });
-    if (lane == 0)
-        static_for<NQ>([&](auto Jc) { atomicAdd(QJ + (size_t)decltype(Jc)::value * nQ + k, (double)sq[decltype(Jc)::value]); });
+    // every lane holds the sums; lane j adds component j (float -> double on the integer pipe)
+    Real mine = sq[0];
+    static_for<NQ>([&](auto Jc) {
+        if (lane == decltype(Jc)::value) mine = sq[decltype(Jc)::value];
+    });
+    if (lane < NQ) atomicAdd(QJ + (size_t)lane * nQ + k, f2d(mine));
 }
 
 // One warp per tile = (fragment pair, up to 32 bra primitive pairs of class LP in one member x)
@@ -252,14 +256,14 @@ __global__ void __launch_bounds__(128) k_jengine32(Dev d, const int2* __restrict
             since_flush = 0;
 #pragma unroll
             for (int i = 0; i < NP; ++i) {
-                JP64[i] += (double)JP[i];
+                JP64[i] += f2d(JP[i]);
                 JP[i] = 0.0f;
             }
         }
     }
     if (valid) {
 #pragma unroll
-        for (int i = 0; i < NP; ++i) atomicAdd(d.pp_Jh[LP] + (size_t)i * nP + Pg, JP64[i] + (double)JP[i]);
+        for (int i = 0; i < NP; ++i) atomicAdd(d.pp_Jh[LP] + (size_t)i * nP + Pg, JP64[i] + f2d(JP[i]));
     }
 }
 

@@ -64,7 +64,7 @@ __device__ __forceinline__ void contract_big(RArr R, const Real* DP, const Real*
         if (lane == 0)
             static_for<CH>([&](auto Jj) {
                 constexpr int j = j0 + decltype(Jj)::value;
-                if constexpr (j < NQ) atomicAdd(QJ + (size_t)j * nQ + k, (double)sq[decltype(Jj)::value]);
+                if constexpr (j < NQ) atomicAdd(QJ + (size_t)j * nQ + k, f2d(sq[decltype(Jj)::value]));
             });
     });
 }
@@ -180,7 +180,7 @@ __global__ void __launch_bounds__(32 * kBigWarps) k_jengine_big(Dev d, const int
                 since_flush = 0;
 #pragma unroll
                 for (int i = 0; i < NP; ++i) {
-                    JP64[i] += (double)JP[i];
+                    JP64[i] += f2d(JP[i]);
                     JP[i] = 0.0f;
                 }
             }
@@ -188,7 +188,7 @@ __global__ void __launch_bounds__(32 * kBigWarps) k_jengine_big(Dev d, const int
     }
     if (valid) {
 #pragma unroll
-        for (int i = 0; i < NP; ++i) atomicAdd(d.pp_Jh[LP] + (size_t)i * nP + Pg, JP64[i] + (double)JP[i]);
+        for (int i = 0; i < NP; ++i) atomicAdd(d.pp_Jh[LP] + (size_t)i * nP + Pg, JP64[i] + f2d(JP[i]));
     }
 }
 

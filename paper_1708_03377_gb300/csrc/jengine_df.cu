@@ -88,19 +88,6 @@ __device__ __forceinline__ df64 rsqrt_df(df64 x)
     return quick_two_sum(r, 0.5f * r * e.hi);
 }
 
-// float -> double by exponent re-biasing on the integer pipe (no FP64 instruction).  Zero and
-// subnormal floats give 0; Inf and NaN give NaN.
-__device__ __forceinline__ double f2d(float f)
-{
-    const unsigned u = __float_as_uint(f);
-    const unsigned ex = (u >> 23) & 0xffu, man = u & 0x7fffffu, sign = u & 0x80000000u;
-    unsigned hi = sign | ((ex + 896u) << 20) | (man >> 3);
-    unsigned lo = man << 29;
-    if (ex == 0u) { hi = sign; lo = 0u; }
-    if (ex == 255u) { hi = 0x7ff80000u; lo = 0u; }
-    return __hiloint2double((int)hi, (int)lo);
-}
-
 __device__ __forceinline__ df64 ld_df(const float2* p)
 {
     const float2 v = __ldg(p);

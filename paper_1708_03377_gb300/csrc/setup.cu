@@ -392,40 +392,72 @@ cudaError_t launch_nuclear_env(const Dev& d, double* vh[kClasses], double* V, cu
 
 // tr(D^x V^y) for each pair, both directions: block (pair, direction), threads over the primitive
 // pairs of the fragment whose electrons feel the other fragment's nuclei.
-__global__ void k_nuclear_traces_h(Dev d, double* tr_xy, double* tr_yx)
+// tr[D^x V^y] for every pair and direction, V^y the attraction of y's nuclei, in two parts:
+// geometry time: the Hermite field of y's nuclei on every primitive pair of x (pre-scaled by p/c
+// so that it contracts directly with the stored Hermite density), stored per (pair, direction) at
+// off[2 pair + dir], class after class, component-major as the Hermite densities;
+// every build: tr = <Dh^x, field>, a dot product that reads the stored fields once.
+__global__ void k_nuclear_trace_fields(Dev d, const int64_t* __restrict__ off, double* fields)
 {
-    int pr = blockIdx.x, dir = blockIdx.y;
-    int x = dir == 0 ? d.pair_x[pr] : d.pair_y[pr];
-    int y = dir == 0 ? d.pair_y[pr] : d.pair_x[pr];
+    const int pr = blockIdx.x, dir = blockIdx.y;
+    const int x = dir == 0 ? d.pair_x[pr] : d.pair_y[pr];
+    const int y = dir == 0 ? d.pair_y[pr] : d.pair_x[pr];
     int npp = 0;
     for (int L = 0; L < kClasses; ++L) npp += d.frag_npp[x * kClasses + L];
-    double acc = 0.0;
     for (int t = threadIdx.x; t < npp; t += blockDim.x) {
         int L, g;
         if (!frag_prim_pair(d, x, t, L, g)) continue;
-        double4_32a P = d.pp_P[L][g];
+        const double4_32a P = d.pp_P[L][g];
         double v[nh(kMaxLPair)];
         for (int k = 0; k < nh(L); ++k) v[k] = 0.0;
         nuclear_field_rt(d, L, P, d.frag_atom0[y], d.frag_nat[y], v);
-        double s = 0.0;
-        for (int k = 0; k < nh(L); ++k) s += d.pp_Dh[L][(size_t)k * d.n_pp[L] + g] * v[k];
-        acc += s * P.w / kSqrt2Pi52;
+        int64_t base = off[2 * pr + dir];
+        for (int L2 = 0; L2 < L; ++L2) base += (int64_t)nh(L2) * d.frag_npp[x * kClasses + L2];
+        const int n = d.frag_npp[x * kClasses + L], i = g - d.frag_pp0[x * kClasses + L];
+        const double sc = P.w / kSqrt2Pi52;
+        for (int k = 0; k < nh(L); ++k) fields[base + (int64_t)k * n + i] = v[k] * sc;
     }
-    __shared__ double red[256];
-    red[threadIdx.x] = acc;
-    __syncthreads();
-    for (int st = blockDim.x / 2; st > 0; st >>= 1) {
-        if (threadIdx.x < st) red[threadIdx.x] += red[threadIdx.x + st];
-        __syncthreads();
-    }
-    if (threadIdx.x == 0) (dir == 0 ? tr_xy : tr_yx)[pr] = red[0];
 }
 
-cudaError_t launch_nuclear_traces(const Dev& d, const double* /*D*/, double* tr_xy, double* tr_yx, cudaStream_t s)
+__global__ void k_nuclear_traces_dot(Dev d, const int64_t* __restrict__ off, const double* __restrict__ fields,
+                                     double* tr_xy, double* tr_yx)
+{
+    const int pr = blockIdx.x, dir = blockIdx.y;
+    const int x = dir == 0 ? d.pair_x[pr] : d.pair_y[pr];
+    double acc = 0.0;
+    int64_t base = off[2 * pr + dir];
+    for (int L = 0; L < kClasses; ++L) {
+        const int n = d.frag_npp[x * kClasses + L], g0 = d.frag_pp0[x * kClasses + L];
+        for (int e = threadIdx.x; e < nh(L) * n; e += blockDim.x) {
+            const int k = e / n, i = e % n;
+            acc = fma(d.pp_Dh[L][(size_t)k * d.n_pp[L] + g0 + i], fields[base + e], acc);
+        }
+        base += (int64_t)nh(L) * n;
+    }
+    __shared__ double red[32];
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
+        (dir == 0 ? tr_xy : tr_yx)[pr] = t;
+    }
+}
+
+cudaError_t launch_nuclear_trace_fields(const Dev& d, const int64_t* off, double* fields, cudaStream_t s)
 {
     if (d.n_pairs == 0) return cudaSuccess;
-    dim3 g(d.n_pairs, 2);
-    k_nuclear_traces_h<<<g, 256, 0, s>>>(d, tr_xy, tr_yx);
+    k_nuclear_trace_fields<<<dim3(d.n_pairs, 2), 128, 0, s>>>(d, off, fields);
+    note_launches(1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_nuclear_traces(const Dev& d, const int64_t* off, const double* fields, double* tr_xy,
+                                  double* tr_yx, cudaStream_t s)
+{
+    if (d.n_pairs == 0) return cudaSuccess;
+    k_nuclear_traces_dot<<<dim3(d.n_pairs, 2), 128, 0, s>>>(d, off, fields, tr_xy, tr_yx);
     note_launches(1);
     return cudaGetLastError();
 }
