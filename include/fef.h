@@ -199,6 +199,41 @@ const char* fef_last_error(const fef_ctx* ctx);
 /* Free the context and all its device memory.  NULL is a no-op. */
 void fef_destroy(fef_ctx* ctx);
 
+/* ---------------------------------------------------------------------------------------------
+ * Tile plans of the inter-fragment J-engine.  The plan decides only how the work of a Fock build is
+ * cut into warp-sized items and scheduled; every plan computes the same J (Eq. dp2e) up to the
+ * order of floating-point additions.  A work item is one warp's tile of 32 bra primitive pairs of
+ * one fragment of a pair against a chunk of the partner's primitive pairs of one Hermite class.
+ * ------------------------------------------------------------------------------------------- */
+enum { FEF_JENGINE_FP64 = 0, FEF_JENGINE_FP32 = 1, FEF_JENGINE_DF64 = 2 };
+
+typedef struct {
+    int32_t persistent;     /* 1: one persistent kernel per register tier (Hermite integrals in registers,
+                               in shared memory, float-float), whose warps take items from a queue sorted
+                               by decreasing cost (all fragment pairs and classes in one launch); the
+                               tiers run concurrently.  0: one launch per class pair over whole ket
+                               ranges (ket_chunk unused). */
+    int32_t ket_chunk[25];  /* ket primitive pairs per item for the class pair L_bra*5 + L_ket
+                               (L = l_a + l_b of the shell pair); 0 = the partner's whole class range */
+    double tuned_ms;        /* J-engine time of one build measured by fef_autotune (0: not tuned) */
+} fef_tile_plan;
+
+/* Read or replace the plan of one engine (FEF_JENGINE_FP64: FP64 builds; FEF_JENGINE_FP32: the FP32-core
+ * builds of FEF_MIXED; FEF_JENGINE_DF64: float-float builds).  Default plans use whole ket ranges,
+ * persistent for FEF_JENGINE_FP64 and one launch per class pair for the other two.  Setting rebuilds
+ * the work queues (synchronous).  Errors: ARG, CUDA. */
+fef_status fef_get_tile_plan(const fef_ctx* ctx, int32_t engine, fef_tile_plan* out);
+fef_status fef_set_tile_plan(fef_ctx* ctx, int32_t engine, const fef_tile_plan* plan);
+
+/* Autotuner: times candidate plans of one engine on this context's own workload with CUDA events and
+ * installs the fastest.  It chooses the ket chunk of each class pair (from whole range, 1024, 256, 64
+ * ket pairs; classes in decreasing order of cost) on every k-th fragment pair, k chosen so that one
+ * timed pass takes about budget_ms/64, then, when a full build fits the budget, persistent queues
+ * against one launch per class pair.  Each candidate is timed reps times (best kept) after a warm-up.
+ * Runs between builds (it overwrites the J-engine accumulators; the next build starts afresh).
+ * out (nullable) receives the chosen plan.  Errors: ARG, CUDA. */
+fef_status fef_autotune(fef_ctx* ctx, int32_t engine, int32_t reps, double budget_ms, fef_tile_plan* out);
+
 /* Measure this GPU's FP64 and FP32 FMA throughput with a register-resident FMA chain kernel.
  * Outputs (nullable) in FLOP/s, counting one FMA as 2 FLOP.  Errors: CUDA. */
 fef_status fef_measure_fma_peak(double* fp64_flops, double* fp32_flops, double* sm_clock_mhz);

@@ -21,6 +21,7 @@ FEF_OK, FEF_ERR_ARG, FEF_ERR_BASIS, FEF_ERR_GEOM, FEF_ERR_CUDA, FEF_ERR_NOT_CONV
     FEF_ERR_TIMEOUT = range(8)
 FEF_FP64, FEF_MIXED = 0, 1
 FEF_ENGINE_FP64, FEF_ENGINE_DF64 = 0, 1
+FEF_JENGINE_FP64, FEF_JENGINE_FP32, FEF_JENGINE_DF64 = 0, 1, 2
 FEF_START_SUPERPOSITION, FEF_START_LEARNED, FEF_START_GIVEN = 0, 1, 2
 STATUS_NAMES = {0: "FEF_OK", 1: "FEF_ERR_ARG", 2: "FEF_ERR_BASIS", 3: "FEF_ERR_GEOM", 4: "FEF_ERR_CUDA",
                 5: "FEF_ERR_NOT_CONVERGED", 6: "FEF_ERR_NUMERIC", 7: "FEF_ERR_TIMEOUT"}
@@ -30,7 +31,7 @@ EXPORTED = ["fef_default_options", "fef_create", "fef_ao_layout", "fef_build_foc
             "fef_measure_fma_peak", "fef_fragment_rhf_noalloc", "fef_history", "fef_mlp_create", "fef_mlp_destroy",
             "fef_mlp_params", "fef_mlp_set_scaling", "fef_mlp_loss_grad", "fef_mlp_train", "fef_mlp_predict",
             "fef_mlp_last_error", "fef_learned_features", "fef_set_warm_start",
-            "fef_noninteracting_scf"]
+            "fef_noninteracting_scf", "fef_get_tile_plan", "fef_set_tile_plan", "fef_autotune"]
 
 
 class FefError(RuntimeError):
@@ -58,6 +59,10 @@ class fef_options(ctypes.Structure):
                 ("max_macro", ctypes.c_int32), ("max_micro", ctypes.c_int32), ("diis_size", ctypes.c_int32),
                 ("start", ctypes.c_int32), ("use_graph", ctypes.c_int32), ("deterministic", ctypes.c_int32),
                 ("mixed_switch", ctypes.c_double), ("exact_engine", ctypes.c_int32)]
+
+
+class fef_tile_plan(ctypes.Structure):
+    _fields_ = [("persistent", ctypes.c_int32), ("ket_chunk", ctypes.c_int32 * 25), ("tuned_ms", ctypes.c_double)]
 
 
 _lib = None
@@ -112,6 +117,9 @@ def lib():
     L.fef_set_warm_start.argtypes = [vp, vp]
     L.fef_fragment_rhf_noalloc.argtypes = [ctypes.c_int32, ip, ip, dp, vp, vp, vp, vp, vp, vp, vp, vp,
                                            ctypes.POINTER(fef_options), vp]
+    L.fef_get_tile_plan.argtypes = [vp, ctypes.c_int32, ctypes.POINTER(fef_tile_plan)]
+    L.fef_set_tile_plan.argtypes = [vp, ctypes.c_int32, ctypes.POINTER(fef_tile_plan)]
+    L.fef_autotune.argtypes = [vp, ctypes.c_int32, ctypes.c_int32, ctypes.c_double, ctypes.POINTER(fef_tile_plan)]
     for name in EXPORTED:
         if name not in ("fef_default_options", "fef_last_error", "fef_destroy", "fef_mlp_destroy", "fef_mlp_last_error"):
             getattr(L, name).restype = ctypes.c_int
@@ -286,6 +294,35 @@ def fef_history(ctx: Context) -> list:
     _check(lib().fef_history(ctx.ptr, n.value, _ptr(buf, ctypes.c_double), ctypes.byref(n)), ctx.ptr)
     keys = ("k", "E_tot", "dE_tot", "dE_x_max", "micro_max", "micro_sum", "jengine_ms", "scf_ms", "fp32")
     return [dict(zip(keys, buf[nf * i:nf * i + nf].tolist())) for i in range(n.value)]
+
+
+def _plan_dict(p: fef_tile_plan) -> dict:
+    return dict(persistent=int(p.persistent), ket_chunk=np.array(list(p.ket_chunk), np.int32).reshape(5, 5),
+                tuned_ms=float(p.tuned_ms))
+
+
+def fef_get_tile_plan(ctx: Context, engine: int = FEF_JENGINE_FP64) -> dict:
+    """The J-engine tile plan of one engine: persistent flag, ket chunk per class pair [5, 5], tuned ms."""
+    p = fef_tile_plan()
+    _check(lib().fef_get_tile_plan(ctx.ptr, engine, ctypes.byref(p)), ctx.ptr)
+    return _plan_dict(p)
+
+
+def fef_set_tile_plan(ctx: Context, engine: int, plan: dict):
+    p = fef_tile_plan()
+    p.persistent = int(plan["persistent"])
+    chunks = np.asarray(plan["ket_chunk"], np.int32).reshape(25)
+    for i in range(25):
+        p.ket_chunk[i] = int(chunks[i])
+    p.tuned_ms = float(plan.get("tuned_ms", 0.0))
+    _check(lib().fef_set_tile_plan(ctx.ptr, engine, ctypes.byref(p)), ctx.ptr)
+
+
+def fef_autotune(ctx: Context, engine: int = FEF_JENGINE_FP64, reps: int = 3, budget_ms: float = 2000.0) -> dict:
+    """Time candidate tile plans of one engine on this context's workload and install the fastest."""
+    p = fef_tile_plan()
+    _check(lib().fef_autotune(ctx.ptr, engine, reps, budget_ms, ctypes.byref(p)), ctx.ptr)
+    return _plan_dict(p)
 
 
 def fef_destroy(ctx: Context):

@@ -55,6 +55,7 @@ struct Buffers {
         for (auto& g : macro_graph)
             if (g) cudaGraphExecDestroy(g);
         if (capture_stream) cudaStreamDestroy(capture_stream);
+        if (jplan) jplan_destroy(jplan);
         if (stage) cudaFreeHost(stage);
         for (void* p : allocs) cudaFree(p);
     }
@@ -72,6 +73,9 @@ struct Buffers {
     // geometry-time data
     double *S = nullptr, *h = nullptr, *X = nullptr, *Venv = nullptr, *eric = nullptr, *boys = nullptr;
     double* scf_ws = nullptr;  // fragment-SCF workspace for fragments above kScfSmemMaxN AOs
+    int* scf_small = nullptr;  // fragments of the one-block-per-fragment SCF launch (when some are large)
+    int* scf_big = nullptr;    // fragments above kScfSmemMaxN AOs: one thread-block cluster each
+    int n_scf_small = 0, n_scf_big = 0;
     double *e_nn_intra = nullptr, *e_nn_pair = nullptr;
     int* nmo = nullptr;
     // per-build data
@@ -93,6 +97,7 @@ struct Buffers {
     int2* tiles[kClasses][kClasses] = {};
     int n_tiles[kClasses * kClasses] = {};
     unsigned long long* qcount = nullptr;
+    JPlanSet* jplan = nullptr;  // J-engine tile plans and work queues per engine
     // learned warm start
     double* rot = nullptr;
     double* Sh = nullptr;   // S^{1/2} per fragment (packed)
@@ -237,7 +242,7 @@ static void build_fock_device(fef_ctx* c, int kind)
     for (int i = 0; i < kClasses; ++i)
         for (int j = 0; j < kClasses; ++j) tiles[i][j] = b->tiles[i][j];
     mark(c, 0);
-    ck(launch_jengine(d, tiles, b->n_tiles, c->opt.schwarz, fp32 ? 1 : (df ? 2 : 0), s), "J-engine");
+    ck(jplan_launch(b->jplan, d, fp32 ? 1 : (df ? 2 : 0), tiles, b->n_tiles, c->opt.schwarz, s), "J-engine");
     mark(c, 1);
     if (kind != kBuildFP32Inc) {
         for (int L = 0; L < kClasses; ++L) {
@@ -300,6 +305,12 @@ static void run_scf(fef_ctx* c, bool with_field, bool have_start)
     a.e_tol = c->opt.micro_e_tol;
     a.comm_tol = c->opt.micro_comm_tol;
     a.ws = b->scf_ws;
+    if (b->n_scf_big > 0) {
+        a.list = b->scf_small;
+        a.n_list = b->n_scf_small;
+        a.big_list = b->scf_big;
+        a.n_big = b->n_scf_big;
+    }
     a.diis_by_moff = 1;
     mark(c, 2);
     ck(launch_fragment_scf(c->dev, a, c->max_nao, c->stream), "fragment SCF");
@@ -802,6 +813,10 @@ extern "C" fef_status fef_create(const fef_geometry* g, const fef_basis* bs, con
                 b->n_tiles[LP * kClasses + LQ] = (int)tl[LP][LQ].size();
                 b->tiles[LP][LQ] = tl[LP][LQ].empty() ? nullptr : b->upload(tl[LP][LQ], s, "tiles");
             }
+        // default tile plans (persistent queues) of the engines this context's builds use
+        b->jplan = jplan_create(tl, frag_npp, pair_x, pair_y, c->device);
+        ck(jplan_prepare(b->jplan, o.exact_engine == FEF_ENGINE_DF64 ? 2 : 0, s), "J-engine plan");
+        if (o.precision == FEF_MIXED) ck(jplan_prepare(b->jplan, 1, s), "J-engine plan");
         c->prim_quartets = prim_q;
         const int ncount = 1 + kClasses * kClasses;
         b->qcount = b->alloc<unsigned long long>(ncount, "qcount");
@@ -844,6 +859,14 @@ extern "C" fef_status fef_create(const fef_geometry* g, const fef_basis* bs, con
         b->diis_stride = 0;
         b->diis = b->alloc<double>(2 * (size_t)o.diis_size * c->mat_total, "diis");
         b->scf_ws = max_nao > kScfSmemMaxN ? b->alloc<double>(9 * c->mat_total, "SCF workspace") : nullptr;
+        if (max_nao > kScfSmemMaxN) {
+            std::vector<int> small, big;
+            for (int x = 0; x < nf; ++x) (c->nao[x] > kScfSmemMaxN ? big : small).push_back(x);
+            b->n_scf_small = (int)small.size();
+            b->n_scf_big = (int)big.size();
+            if (!small.empty()) b->scf_small = b->upload(small, s, "SCF lists");
+            b->scf_big = b->upload(big, s, "SCF lists");
+        }
         ck(cudaStreamSynchronize(s), "create");
         c->shell_quartets = (int64_t)qc[0];
         for (int i = 0; i < kClasses * kClasses; ++i) c->class_quartets[i] = (int64_t)qc[1 + i];
@@ -1243,4 +1266,53 @@ extern "C" fef_status fef_history(const fef_ctx* c, int32_t max_records, double*
         std::memcpy(records, c->history.data(), sizeof(double) * kHistoryFields * m);
     }
     return FEF_OK;
+}
+
+extern "C" fef_status fef_get_tile_plan(const fef_ctx* c, int32_t engine, fef_tile_plan* out)
+{
+    if (!c || !out || engine < 0 || engine > 2) return FEF_ERR_ARG;
+    jplan_get(c->buf->jplan, engine, out);
+    return FEF_OK;
+}
+
+extern "C" fef_status fef_set_tile_plan(fef_ctx* c, int32_t engine, const fef_tile_plan* plan)
+{
+    if (!c) return FEF_ERR_ARG;
+    FEF_API_BEGIN
+    require(plan != nullptr && engine >= 0 && engine <= 2, FEF_ERR_ARG, "fef_set_tile_plan: bad engine or plan");
+    for (int i = 0; i < 25; ++i)
+        require(plan->ket_chunk[i] >= 0 && plan->ket_chunk[i] < (1 << 26), FEF_ERR_ARG,
+                "fef_set_tile_plan: ket_chunk out of range");
+    ck(cudaStreamSynchronize(c->stream), "tile plan");
+    ck(jplan_set(c->buf->jplan, engine, plan, c->stream), "tile plan");
+    for (auto& g : c->buf->macro_graph)  // graphs captured with the old queues are stale
+        if (g) {
+            cudaGraphExecDestroy(g);
+            g = nullptr;
+        }
+    return FEF_OK;
+    FEF_API_END(c)
+}
+
+extern "C" fef_status fef_autotune(fef_ctx* c, int32_t engine, int32_t reps, double budget_ms, fef_tile_plan* out)
+{
+    if (!c) return FEF_ERR_ARG;
+    FEF_API_BEGIN
+    require(engine >= 0 && engine <= 2 && reps >= 1 && reps <= 100 && budget_ms > 0.0, FEF_ERR_ARG,
+            "fef_autotune: bad engine, reps or budget");
+    Buffers* b = c->buf;
+    ck(cudaStreamSynchronize(c->stream), "autotune");
+    const int2* tiles[kClasses][kClasses];
+    for (int i = 0; i < kClasses; ++i)
+        for (int j = 0; j < kClasses; ++j) tiles[i][j] = b->tiles[i][j];
+    ck(jplan_autotune(b->jplan, c->dev, engine, tiles, b->n_tiles, c->opt.schwarz, reps, budget_ms, c->stream, out),
+       "autotune");
+    // the queues changed: graphs captured with the old ones are stale
+    for (auto& g : b->macro_graph)
+        if (g) {
+            cudaGraphExecDestroy(g);
+            g = nullptr;
+        }
+    return FEF_OK;
+    FEF_API_END(c)
 }

@@ -180,6 +180,44 @@ cudaError_t launch_df_setup(const Dev& d, float4* const Phi[kClasses], float4* c
 cudaError_t launch_df_density(const Dev& d, cudaStream_t s);
 cudaError_t launch_jengine_big(const Dev& d, const int2* tiles[kClasses][kClasses], const int* n_tiles, float tau,
                                int fp32, cudaStream_t s);
+// Persistent J-engine (one launch per register tier and Fock build, warps take cost-sorted work
+// items from a queue).  Item (int4): x = 2 pair + swap, y = first bra primitive pair of the 32-pair
+// tile, z = first ket pair and (w >> 5) = end ket pair, both as offsets in the partner fragment's
+// class-LQ range, (w & 31) = LP * kClasses + LQ.
+constexpr int kItemClassBits = 5;
+__host__ __device__ inline int jitem_class(int4 it) { return it.w & ((1 << kItemClassBits) - 1); }
+__host__ __device__ inline int jitem_ket_end(int4 it) { return it.w >> kItemClassBits; }
+struct JQueue {
+    const int4* items = nullptr;  // device, sorted by decreasing estimated cost
+    int n = 0;
+    int* next = nullptr;          // device counter, zeroed by the launcher before every launch
+    int grid = 0;                 // resident blocks of the kernel on this device
+    int smem_slice = 0;           // shared-memory R tier: Reals per warp (largest class of the queue)
+};
+// MODE 0 FP64, 1 FP32 core; spd: the queue holds register classes with L_P >= 3
+cudaError_t jengine_persistent_grid(int mode, bool spd, int* blocks_per_sm);
+cudaError_t launch_jengine_persistent(const Dev& d, int mode, bool spd, const JQueue& q, float tau, cudaStream_t s);
+// float-float core for the s/p classes (L_P <= 2)
+cudaError_t jengine_df_persistent_grid(int* blocks_per_sm);
+cudaError_t launch_jengine_df_persistent(const Dev& d, const JQueue& q, float tau, cudaStream_t s);
+// classes with L_P + L_Q >= 5 (R in shared memory); fp32 selects the FP32 core
+int jengine_big_slice(int LP, int LQ);
+cudaError_t jengine_big_persistent_grid(int fp32, int smem_slice, int* blocks_per_sm);
+cudaError_t launch_jengine_big_persistent(const Dev& d, int fp32, const JQueue& q, float tau, cudaStream_t s);
+// Tile plans of the J-engine (jplan.cu): per engine mode (0 FP64, 1 FP32 core, 2 float-float) the
+// strategy (persistent queues or one launch per class pair) and the ket chunk per class pair.
+struct JPlanSet;
+JPlanSet* jplan_create(const std::vector<int2> (&tiles)[kClasses][kClasses], const std::vector<int>& frag_npp,
+                       const std::vector<int>& pair_x, const std::vector<int>& pair_y, int device);
+void jplan_destroy(JPlanSet* P);
+cudaError_t jplan_prepare(JPlanSet* P, int mode, cudaStream_t s);  // build the queues (not while capturing)
+cudaError_t jplan_launch(JPlanSet* P, const Dev& d, int mode, const int2* tiles[kClasses][kClasses],
+                         const int* n_tiles, double tau, cudaStream_t s);
+void jplan_get(const JPlanSet* P, int mode, fef_tile_plan* out);
+cudaError_t jplan_set(JPlanSet* P, int mode, const fef_tile_plan* in, cudaStream_t s);
+cudaError_t jplan_autotune(JPlanSet* P, const Dev& d, int mode, const int2* tiles[kClasses][kClasses],
+                           const int* n_tiles, double tau, int reps, double budget_ms, cudaStream_t s,
+                           fef_tile_plan* out);
 cudaError_t launch_back_transform(const Dev& d, double* J, cudaStream_t s);
 // F = h + C D + V_env + J_env per fragment; E_int[x] = tr[D (h + G/2)] + e_nn[x]; tr_omega[x] = tr[D (V+J)]
 // also trV[x] = tr(D^x V_env^x), trJ[x] = tr(D^x J_env^x)
@@ -213,6 +251,10 @@ struct ScfArgs {
                             // fragments above kScfSmemMaxN AOs (null when there are none)
     int diis_by_moff;       // 1: DIIS history at 2 diis_size frag_moff[x] (sized per fragment),
                             // 0: at x * diis_stride
+    const int* list;        // fragments of the one-block-per-fragment launch (null: all fragments)
+    int n_list;
+    const int* big_list;    // fragments above kScfSmemMaxN AOs, one thread-block cluster each
+    int n_big;              // (0: none; then list is null or holds every fragment)
 };
 cudaError_t launch_fragment_scf(const Dev& d, const ScfArgs& a, int max_n, cudaStream_t s);
 

@@ -11,6 +11,9 @@
 //   J^x_{mu nu} = sum_{P in (a,b)} sum_tuv E^{mu nu}_{tuv}(P) J_P[tuv].
 // The ERIs (mu nu|lambda sigma) are never formed.  Densities and fields are pre/post-scaled by
 // c/p with c = sqrt(2 pi^{5/2}) so that each primitive quartet only needs rsqrt(p+q).
+#include <algorithm>
+#include <climits>
+
 #include "common.cuh"
 #include "internal.hpp"
 
@@ -112,19 +115,17 @@ __device__ __forceinline__ void hermite_contract(const Real* R, const Real* DP, 
 }
 
 // One warp per tile = (fragment pair, up to 32 bra primitive pairs of class LP in one member x)
-// against all ket primitive pairs of class LQ <= LP in the other member y (the pair's two J
-// directions are both produced, so the member with the larger class is put on the bra side).  Lane i owns bra pair P_i: its centre, Hermite density and
+// against the ket primitive pairs [kb, ke) (offsets in the class-LQ range of the other member y,
+// LQ <= LP; the pair's two J directions are both produced, so the member with the larger class is
+// put on the bra side).  Lane i owns bra pair P_i: its centre, Hermite density and
 // Hermite field accumulator stay in registers.  Ket data are warp-uniform loads.  The field on the
 // ket pair is reduced across the warp with shuffles and added to global memory by lane 0.
 // Shell quartets with Q_ab Q_cd < tau contribute nothing (Schwarz screening at shell level).
 template <int LP, int LQ>
-__global__ void __launch_bounds__(128) k_jengine(Dev d, const int2* __restrict__ tiles, int n_tiles, float tau)
+__device__ __forceinline__ void jtile_fp64(const Dev& d, const int2 tl, const int kb, const int ke, const float tau,
+                                           const int lane)
 {
     constexpr int NP = nh(LP), NQ = nh(LQ), L = LP + LQ, NR = nh(LP + LQ);
-    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int lane = threadIdx.x & 31;
-    if (warp >= n_tiles) return;
-    const int2 tl = tiles[warp];
     // tile.x = 2 * pair + swap: the bra fragment is the pair member holding the larger class
     const int pr = tl.x >> 1;
     const int x = (tl.x & 1) ? d.pair_y[pr] : d.pair_x[pr];
@@ -143,8 +144,9 @@ __global__ void __launch_bounds__(128) k_jengine(Dev d, const int2* __restrict__
         DP[i] = valid ? d.pp_Dh[LP][(size_t)i * nP + Pl] : 0.0;
         JP[i] = 0.0;
     }
-    const int k0 = d.frag_pp0[y * kClasses + LQ];
-    const int k1 = k0 + d.frag_npp[y * kClasses + LQ];
+    const int kc = d.frag_pp0[y * kClasses + LQ];
+    const int k0 = kc + kb;
+    const int k1 = kc + min(ke, d.frag_npp[y * kClasses + LQ]);
     const double4_32a* __restrict__ QP = d.pp_P[LQ];
     const float4* __restrict__ QPf = d.pp_Pf[LQ];
     const float* __restrict__ QQ = d.pp_Q[LQ];
@@ -191,13 +193,10 @@ __global__ void __launch_bounds__(128) k_jengine(Dev d, const int2* __restrict__
 // FP64-computed anchor offset), FP32 Boys, R recursion and contractions.  The bra field is flushed to
 // FP64 registers every 16 ket pairs and all global accumulation is FP64 (atomics on pp_Jh).
 template <int LP, int LQ>
-__global__ void __launch_bounds__(128) k_jengine32(Dev d, const int2* __restrict__ tiles, int n_tiles, float tau)
+__device__ __forceinline__ void jtile_fp32(const Dev& d, const int2 tl, const int kb, const int ke, const float tau,
+                                           const int lane)
 {
     constexpr int NP = nh(LP), NQ = nh(LQ), L = LP + LQ, NR = nh(LP + LQ);
-    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int lane = threadIdx.x & 31;
-    if (warp >= n_tiles) return;
-    const int2 tl = tiles[warp];
     // tile.x = 2 * pair + swap: the bra fragment is the pair member holding the larger class
     const int pr = tl.x >> 1;
     const int x = (tl.x & 1) ? d.pair_y[pr] : d.pair_x[pr];
@@ -220,8 +219,9 @@ __global__ void __launch_bounds__(128) k_jengine32(Dev d, const int2* __restrict
         JP[i] = 0.0f;
         JP64[i] = 0.0;
     }
-    const int k0 = d.frag_pp0[y * kClasses + LQ];
-    const int k1 = k0 + d.frag_npp[y * kClasses + LQ];
+    const int kc = d.frag_pp0[y * kClasses + LQ];
+    const int k0 = kc + kb;
+    const int k1 = kc + min(ke, d.frag_npp[y * kClasses + LQ]);
     const float4* __restrict__ QPr = d.pp_Pr[LQ];
     const float* __restrict__ QQ = d.pp_Q[LQ];
     const float* __restrict__ QD = d.pp_Dh32[LQ];
@@ -265,6 +265,96 @@ __global__ void __launch_bounds__(128) k_jengine32(Dev d, const int2* __restrict
 #pragma unroll
         for (int i = 0; i < NP; ++i) atomicAdd(d.pp_Jh[LP] + (size_t)i * nP + Pg, JP64[i] + f2d(JP[i]));
     }
+}
+
+// One warp per tile over the partner's whole class range (one launch per class pair).
+template <int LP, int LQ>
+__global__ void __launch_bounds__(128) k_jengine(Dev d, const int2* __restrict__ tiles, int n_tiles, float tau)
+{
+    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (warp >= n_tiles) return;
+    jtile_fp64<LP, LQ>(d, tiles[warp], 0, INT_MAX, tau, threadIdx.x & 31);
+}
+
+template <int LP, int LQ>
+__global__ void __launch_bounds__(128) k_jengine32(Dev d, const int2* __restrict__ tiles, int n_tiles, float tau)
+{
+    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (warp >= n_tiles) return;
+    jtile_fp32<LP, LQ>(d, tiles[warp], 0, INT_MAX, tau, threadIdx.x & 31);
+}
+
+// ------------------------------------------------------------------------------------------ persistent
+// Persistent J-engine: the grid is sized to the resident capacity of the GPU and every warp takes
+// work items from a cost-sorted queue (one atomic per item) until it is empty, so quartet classes
+// of all fragment pairs (of uneven size and mixed angular momentum) share one launch and the
+// longest items start first.  An item is one 32-bra-pair tile against a chunk of the partner's
+// ket pairs (JItem encoding in internal.hpp).  MODE 0: FP64 core, 1: FP32 core.  SPD adds the
+// register classes with a d-shell pair (L_P = 3, 4; L_P + L_Q <= 4), whose larger register
+// footprint would otherwise lower the occupancy of the s/p classes.
+template <int MODE, int LP, int LQ>
+__device__ __forceinline__ void jtile(const Dev& d, int2 tl, int kb, int ke, float tau, int lane)
+{
+    if constexpr (MODE == 0)
+        jtile_fp64<LP, LQ>(d, tl, kb, ke, tau, lane);
+    else
+        jtile_fp32<LP, LQ>(d, tl, kb, ke, tau, lane);
+}
+
+template <int MODE, bool SPD>
+__global__ void __launch_bounds__(128) k_jengine_persistent(Dev d, const int4* __restrict__ items, int n_items,
+                                                            int* __restrict__ next, float tau)
+{
+    const int lane = threadIdx.x & 31;
+    for (;;) {
+        int i = 0;
+        if (lane == 0) i = atomicAdd(next, 1);
+        i = __shfl_sync(0xffffffffu, i, 0);
+        if (i >= n_items) return;
+        const int4 it = items[i];
+        const int2 tl = make_int2(it.x, it.y);
+        const int kb = it.z, ke = jitem_ket_end(it);
+        switch (jitem_class(it)) {
+            case 0 * kClasses + 0: jtile<MODE, 0, 0>(d, tl, kb, ke, tau, lane); break;
+            case 1 * kClasses + 0: jtile<MODE, 1, 0>(d, tl, kb, ke, tau, lane); break;
+            case 1 * kClasses + 1: jtile<MODE, 1, 1>(d, tl, kb, ke, tau, lane); break;
+            case 2 * kClasses + 0: jtile<MODE, 2, 0>(d, tl, kb, ke, tau, lane); break;
+            case 2 * kClasses + 1: jtile<MODE, 2, 1>(d, tl, kb, ke, tau, lane); break;
+            case 2 * kClasses + 2: jtile<MODE, 2, 2>(d, tl, kb, ke, tau, lane); break;
+            case 3 * kClasses + 0: if constexpr (SPD) jtile<MODE, 3, 0>(d, tl, kb, ke, tau, lane); break;
+            case 3 * kClasses + 1: if constexpr (SPD) jtile<MODE, 3, 1>(d, tl, kb, ke, tau, lane); break;
+            case 4 * kClasses + 0: if constexpr (SPD) jtile<MODE, 4, 0>(d, tl, kb, ke, tau, lane); break;
+            default: break;
+        }
+    }
+}
+
+static const void* persistent_kernel(int mode, bool spd)
+{
+    if (mode == 0) return spd ? (const void*)k_jengine_persistent<0, true> : (const void*)k_jengine_persistent<0, false>;
+    return spd ? (const void*)k_jengine_persistent<1, true> : (const void*)k_jengine_persistent<1, false>;
+}
+
+cudaError_t jengine_persistent_grid(int mode, bool spd, int* blocks_per_sm)
+{
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, persistent_kernel(mode, spd), 128, 0);
+}
+
+cudaError_t launch_jengine_persistent(const Dev& d, int mode, bool spd, const JQueue& q, float tau, cudaStream_t s)
+{
+    if (q.n <= 0) return cudaSuccess;
+    cudaError_t e = cudaMemsetAsync(q.next, 0, sizeof(int), s);
+    if (e != cudaSuccess) return e;
+    const int blocks = std::max(1, std::min(q.grid, (q.n + 3) / 4));
+    if (mode == 0) {
+        if (spd) k_jengine_persistent<0, true><<<blocks, 128, 0, s>>>(d, q.items, q.n, q.next, tau);
+        else k_jengine_persistent<0, false><<<blocks, 128, 0, s>>>(d, q.items, q.n, q.next, tau);
+    } else {
+        if (spd) k_jengine_persistent<1, true><<<blocks, 128, 0, s>>>(d, q.items, q.n, q.next, tau);
+        else k_jengine_persistent<1, false><<<blocks, 128, 0, s>>>(d, q.items, q.n, q.next, tau);
+    }
+    note_launches(1);
+    return cudaGetLastError();
 }
 
 template <int LP, int LQ>

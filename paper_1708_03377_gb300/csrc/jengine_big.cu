@@ -4,6 +4,8 @@
 // integrals R_{tuv} in a lane-strided slice of shared memory (too many for registers at L >= 5), the
 // warp-uniform ket Hermite density is staged in shared memory, and the field on the ket pair is
 // reduced across the warp in chunks of 5 components.  Two warps per block.
+#include <algorithm>
+#include <climits>
 #include <type_traits>
 
 #include "common.cuh"
@@ -71,21 +73,16 @@ __device__ __forceinline__ void contract_big(RArr R, const Real* DP, const Real*
 
 // Real = double: full FP64 build on pp_Dh.  Real = float: the mixed-precision core on pp_Dh32 with
 // FP32 geometry relative to each fragment's first atom, flushed to FP64 every 16 ket pairs.
+// One warp-tile (32 bra primitive pairs from tl.y) against the ket pairs [kb, ke) (offsets in the
+// partner's class range); sm = this warp's shared-memory slice of big_slice<LP, LQ>() Reals.
 template <int LP, int LQ, typename Real>
-__global__ void __launch_bounds__(32 * kBigWarps) k_jengine_big(Dev d, const int2* __restrict__ tiles, int n_tiles,
-                                                                 float tau)
+__device__ __forceinline__ void jtile_big(const Dev& d, const int2 tl, const int kb, const int ke, const float tau,
+                                          const int lane, Real* sm)
 {
     constexpr bool F32 = std::is_same<Real, float>::value;
     constexpr int NP = nh(LP), NQ = nh(LQ), L = LP + LQ;
-    extern __shared__ __align__(16) unsigned char smraw[];
-    const int wib = threadIdx.x >> 5;
-    const int lane = threadIdx.x & 31;
-    Real* sm = reinterpret_cast<Real*>(smraw) + wib * big_slice<LP, LQ>();
     LaneSlice<Real> R{sm + lane};
     Real* DQ = sm + 32 * nh(L);
-    const int warp = blockIdx.x * kBigWarps + wib;
-    if (warp >= n_tiles) return;
-    const int2 tl = tiles[warp];
     const int pr = tl.x >> 1;
     const int x = (tl.x & 1) ? d.pair_y[pr] : d.pair_x[pr];
     const int y = (tl.x & 1) ? d.pair_x[pr] : d.pair_y[pr];
@@ -121,8 +118,9 @@ __global__ void __launch_bounds__(32 * kBigWarps) k_jengine_big(Dev d, const int
         Pd = d.pp_P[LP][Pl];
         Pf = d.pp_Pf[LP][Pl];
     }
-    const int k0 = d.frag_pp0[y * kClasses + LQ];
-    const int k1 = k0 + d.frag_npp[y * kClasses + LQ];
+    const int kc = d.frag_pp0[y * kClasses + LQ];
+    const int k0 = kc + kb;
+    const int k1 = kc + min(ke, d.frag_npp[y * kClasses + LQ]);
     double* __restrict__ QJ = d.pp_Jh[LQ];
     int since_flush = 0;
     for (int k = k0; k < k1; ++k) {
@@ -192,6 +190,49 @@ __global__ void __launch_bounds__(32 * kBigWarps) k_jengine_big(Dev d, const int
     }
 }
 
+template <int LP, int LQ, typename Real>
+__global__ void __launch_bounds__(32 * kBigWarps) k_jengine_big(Dev d, const int2* __restrict__ tiles, int n_tiles,
+                                                                 float tau)
+{
+    extern __shared__ __align__(16) unsigned char smraw[];
+    const int wib = threadIdx.x >> 5;
+    const int warp = blockIdx.x * kBigWarps + wib;
+    if (warp >= n_tiles) return;
+    Real* sm = reinterpret_cast<Real*>(smraw) + wib * big_slice<LP, LQ>();
+    jtile_big<LP, LQ, Real>(d, tiles[warp], 0, INT_MAX, tau, threadIdx.x & 31, sm);
+}
+
+// Persistent kernel over the classes with L_P + L_Q >= 5: warps take cost-sorted items from a queue
+// (item encoding in internal.hpp); every warp owns a slice of `slice` Reals, the largest class's.
+template <typename Real>
+__global__ void __launch_bounds__(32 * kBigWarps) k_jengine_big_persistent(Dev d, const int4* __restrict__ items,
+                                                                            int n_items, int* __restrict__ next,
+                                                                            float tau, int slice)
+{
+    extern __shared__ __align__(16) unsigned char smraw[];
+    const int lane = threadIdx.x & 31;
+    Real* sm = reinterpret_cast<Real*>(smraw) + (threadIdx.x >> 5) * slice;
+    for (;;) {
+        int i = 0;
+        if (lane == 0) i = atomicAdd(next, 1);
+        i = __shfl_sync(0xffffffffu, i, 0);
+        if (i >= n_items) return;
+        const int4 it = items[i];
+        const int2 tl = make_int2(it.x, it.y);
+        const int kb = it.z, ke = jitem_ket_end(it);
+        switch (jitem_class(it)) {
+            case 3 * kClasses + 2: jtile_big<3, 2, Real>(d, tl, kb, ke, tau, lane, sm); break;
+            case 3 * kClasses + 3: jtile_big<3, 3, Real>(d, tl, kb, ke, tau, lane, sm); break;
+            case 4 * kClasses + 1: jtile_big<4, 1, Real>(d, tl, kb, ke, tau, lane, sm); break;
+            case 4 * kClasses + 2: jtile_big<4, 2, Real>(d, tl, kb, ke, tau, lane, sm); break;
+            case 4 * kClasses + 3: jtile_big<4, 3, Real>(d, tl, kb, ke, tau, lane, sm); break;
+            case 4 * kClasses + 4: jtile_big<4, 4, Real>(d, tl, kb, ke, tau, lane, sm); break;
+            default: break;
+        }
+        __syncwarp();
+    }
+}
+
 template <int LP, int LQ>
 void launch_big(const Dev& d, const int2* t, int n, float tau, int fp32, cudaStream_t s)
 {
@@ -210,6 +251,37 @@ void launch_big(const Dev& d, const int2* t, int n, float tau, int fp32, cudaStr
 }
 
 }  // namespace
+
+int jengine_big_slice(int LP, int LQ) { return 32 * nh(LP + LQ) + ((nh(LQ) + 1) & ~1); }
+
+// The dynamic shared-memory limit of the persistent kernel is raised once to the largest class's
+// need, so that queues of any context (smaller slices) can be launched.
+cudaError_t jengine_big_persistent_grid(int fp32, int smem_slice, int* blocks_per_sm)
+{
+    const size_t real = fp32 ? sizeof(float) : sizeof(double);
+    const size_t smem = (size_t)kBigWarps * smem_slice * real;
+    const size_t smem_max = (size_t)kBigWarps * big_slice<kClasses - 1, kClasses - 1>() * real;
+    if (smem > smem_max) return cudaErrorInvalidValue;
+    const void* k = fp32 ? (const void*)k_jengine_big_persistent<float> : (const void*)k_jengine_big_persistent<double>;
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_max);
+    if (e != cudaSuccess) return e;
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k, 32 * kBigWarps, smem);
+}
+
+cudaError_t launch_jengine_big_persistent(const Dev& d, int fp32, const JQueue& q, float tau, cudaStream_t s)
+{
+    if (q.n <= 0) return cudaSuccess;
+    cudaError_t e = cudaMemsetAsync(q.next, 0, sizeof(int), s);
+    if (e != cudaSuccess) return e;
+    const int blocks = std::max(1, std::min(q.grid, (q.n + kBigWarps - 1) / kBigWarps));
+    const size_t smem = (size_t)kBigWarps * q.smem_slice * (fp32 ? sizeof(float) : sizeof(double));
+    if (fp32)
+        k_jengine_big_persistent<float><<<blocks, 32 * kBigWarps, smem, s>>>(d, q.items, q.n, q.next, tau, q.smem_slice);
+    else
+        k_jengine_big_persistent<double><<<blocks, 32 * kBigWarps, smem, s>>>(d, q.items, q.n, q.next, tau, q.smem_slice);
+    note_launches(1);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_jengine_big(const Dev& d, const int2* tiles[kClasses][kClasses], const int* n_tiles, float tau,
                                int fp32, cudaStream_t s)

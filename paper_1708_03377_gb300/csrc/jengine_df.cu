@@ -17,6 +17,9 @@
 //     atomics (hi and lo), converted from float by exponent re-biasing on the integer pipe.
 // Values below the FP32 normal range (~1e-38) are flushed to zero, far below every tolerance.
 // Classes with L_P >= 3 (d shells) and L_P + L_Q >= 5 use the native FP64 kernels.
+#include <algorithm>
+#include <climits>
+
 #include "common.cuh"
 #include "internal.hpp"
 
@@ -129,14 +132,13 @@ __device__ __forceinline__ void boys_df(const float2* __restrict__ table, df64 T
 
 constexpr int kFlushKets = 32;
 
+// One warp-tile (32 bra primitive pairs from tl.y) against the ket pairs [kb, ke) (offsets in the
+// partner's class range) in float-float arithmetic.
 template <int LP, int LQ>
-__global__ void __launch_bounds__(128) k_jengine_df(Dev d, const int2* __restrict__ tiles, int n_tiles, float tau)
+__device__ __forceinline__ void jtile_df(const Dev& d, const int2 tl, const int kb, const int ke, const float tau,
+                                         const int lane)
 {
     constexpr int NP = nh(LP), NQ = nh(LQ), L = LP + LQ, NR = nh(LP + LQ);
-    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int lane = threadIdx.x & 31;
-    if (warp >= n_tiles) return;
-    const int2 tl = tiles[warp];
     const int pr = tl.x >> 1;
     const int x = (tl.x & 1) ? d.pair_y[pr] : d.pair_x[pr];
     const int y = (tl.x & 1) ? d.pair_x[pr] : d.pair_y[pr];
@@ -157,8 +159,9 @@ __global__ void __launch_bounds__(128) k_jengine_df(Dev d, const int2* __restric
         JP[i] = df64(0.0f, 0.0f);
         JP64[i] = 0.0;
     }
-    const int k0 = d.frag_pp0[y * kClasses + LQ];
-    const int k1 = k0 + d.frag_npp[y * kClasses + LQ];
+    const int kc = d.frag_pp0[y * kClasses + LQ];
+    const int k0 = kc + kb;
+    const int k1 = kc + min(ke, d.frag_npp[y * kClasses + LQ]);
     const float4* __restrict__ QH = d.pp_Phi[LQ];
     const float4* __restrict__ QL = d.pp_Plo[LQ];
     const float4* __restrict__ QPf = d.pp_Pf[LQ];
@@ -249,6 +252,40 @@ __global__ void __launch_bounds__(128) k_jengine_df(Dev d, const int2* __restric
 }
 
 template <int LP, int LQ>
+__global__ void __launch_bounds__(128) k_jengine_df(Dev d, const int2* __restrict__ tiles, int n_tiles, float tau)
+{
+    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (warp >= n_tiles) return;
+    jtile_df<LP, LQ>(d, tiles[warp], 0, INT_MAX, tau, threadIdx.x & 31);
+}
+
+// Persistent float-float J-engine over the s/p classes: warps take cost-sorted items from a queue
+// (item encoding in internal.hpp) until it is empty.
+__global__ void __launch_bounds__(128) k_jengine_df_persistent(Dev d, const int4* __restrict__ items, int n_items,
+                                                               int* __restrict__ next, float tau)
+{
+    const int lane = threadIdx.x & 31;
+    for (;;) {
+        int i = 0;
+        if (lane == 0) i = atomicAdd(next, 1);
+        i = __shfl_sync(0xffffffffu, i, 0);
+        if (i >= n_items) return;
+        const int4 it = items[i];
+        const int2 tl = make_int2(it.x, it.y);
+        const int kb = it.z, ke = jitem_ket_end(it);
+        switch (jitem_class(it)) {
+            case 0 * kClasses + 0: jtile_df<0, 0>(d, tl, kb, ke, tau, lane); break;
+            case 1 * kClasses + 0: jtile_df<1, 0>(d, tl, kb, ke, tau, lane); break;
+            case 1 * kClasses + 1: jtile_df<1, 1>(d, tl, kb, ke, tau, lane); break;
+            case 2 * kClasses + 0: jtile_df<2, 0>(d, tl, kb, ke, tau, lane); break;
+            case 2 * kClasses + 1: jtile_df<2, 1>(d, tl, kb, ke, tau, lane); break;
+            case 2 * kClasses + 2: jtile_df<2, 2>(d, tl, kb, ke, tau, lane); break;
+            default: break;
+        }
+    }
+}
+
+template <int LP, int LQ>
 void launch_df_one(const Dev& d, const int2* t, int n, float tau, cudaStream_t s)
 {
     if (n <= 0) return;
@@ -301,6 +338,22 @@ cudaError_t launch_df_density(const Dev& d, cudaStream_t s)
         k_split_array<<<(unsigned)std::min<size_t>((n + 255) / 256, 2048), 256, 0, s>>>(d.pp_Dh[L], d.pp_Dhdf[L], n);
         note_launches(1);
     }
+    return cudaGetLastError();
+}
+
+cudaError_t jengine_df_persistent_grid(int* blocks_per_sm)
+{
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_jengine_df_persistent, 128, 0);
+}
+
+cudaError_t launch_jengine_df_persistent(const Dev& d, const JQueue& q, float tau, cudaStream_t s)
+{
+    if (q.n <= 0) return cudaSuccess;
+    cudaError_t e = cudaMemsetAsync(q.next, 0, sizeof(int), s);
+    if (e != cudaSuccess) return e;
+    const int blocks = std::max(1, std::min(q.grid, (q.n + 3) / 4));
+    k_jengine_df_persistent<<<blocks, 128, 0, s>>>(d, q.items, q.n, q.next, tau);
+    note_launches(1);
     return cudaGetLastError();
 }
 

@@ -7,6 +7,8 @@
 //   E_scf = tr[D (h + omega + F)]/2 + E_nn, e = F D S - S D F,
 //   Pulay DIIS on X^T e X, F' = X^T F X, cyclic Jacobi eigensolver, aufbau, D = 2 C_occ C_occ^T,
 // until |dE_scf| < e_tol and max|e| < comm_tol.  X = U s^{-1/2} is the canonical orthogonaliser.
+#include <cooperative_groups.h>
+
 #include "common.cuh"
 #include "internal.hpp"
 
@@ -14,39 +16,78 @@ namespace fef {
 
 namespace {
 
-__device__ inline double block_sum(double v, double* red)
+namespace cg = cooperative_groups;
+
+// The threads that share one fragment's micro loop: one thread block (CS = 1), or the CS blocks of a
+// thread-block cluster (fragments above the shared-memory limit, matrices in global memory).  Loops
+// over matrix elements are spread over all CS * blockDim threads; sync() orders the phases (a
+// cluster barrier, release/acquire at cluster scope, for CS > 1).  Every block of a cluster takes
+// the same control-flow decisions: the reductions that feed them are summed in the same order.
+template <int CS>
+struct Team {
+    int rank;
+    __device__ __forceinline__ int g() const { return rank * (int)blockDim.x + (int)threadIdx.x; }
+    __device__ __forceinline__ int gs() const { return CS * (int)blockDim.x; }
+    __device__ __forceinline__ void sync() const
+    {
+        if constexpr (CS == 1)
+            __syncthreads();
+        else
+            cg::this_cluster().sync();
+    }
+};
+
+// Team-wide sum (MAX = false) or maximum; red: 40 doubles of shared memory.
+template <int CS, bool MAX>
+__device__ double team_reduce(const Team<CS>& t, double v, double* red)
 {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    for (int o = 16; o > 0; o >>= 1) {
+        const double u = __shfl_xor_sync(0xffffffffu, v, o);
+        v = MAX ? fmax(v, u) : v + u;
+    }
     __syncthreads();
     if (lane == 0) red[warp] = v;
     __syncthreads();
-    double s = 0.0;
-    for (int w = 0; w < nw; ++w) s += red[w];
-    __syncthreads();
-    return s;
+    if (threadIdx.x == 0) {
+        double s = 0.0;
+        for (int w = 0; w < nw; ++w) s = MAX ? fmax(s, red[w]) : s + red[w];
+        red[32] = s;
+    }
+    if constexpr (CS == 1) {
+        __syncthreads();
+        const double r = red[32];
+        __syncthreads();
+        return r;
+    } else {
+        cg::cluster_group cl = cg::this_cluster();
+        cl.sync();
+        if (threadIdx.x == 0) {
+            double s = 0.0;
+            for (int r = 0; r < CS; ++r) {
+                const double u = *cl.map_shared_rank(red + 32, r);
+                s = MAX ? fmax(s, u) : s + u;
+            }
+            red[33] = s;
+        }
+        cl.sync();
+        return red[33];
+    }
 }
 
-__device__ inline double block_max(double v, double* red)
-{
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
-    __syncthreads();
-    if (lane == 0) red[warp] = v;
-    __syncthreads();
-    double s = 0.0;
-    for (int w = 0; w < nw; ++w) s = fmax(s, red[w]);
-    __syncthreads();
-    return s;
-}
+template <int CS>
+__device__ inline double team_sum(const Team<CS>& t, double v, double* red) { return team_reduce<CS, false>(t, v, red); }
+template <int CS>
+__device__ inline double team_max(const Team<CS>& t, double v, double* red) { return team_reduce<CS, true>(t, v, red); }
 
-// C[m x k] = op(A) B with A, B, C row-major in shared memory, leading dimension ld.
+// C[m x k] = op(A) B with A, B, C row-major, leading dimension ld.
 // transA: C = A^T B with A stored k x m.
-__device__ inline void mm(double* C, const double* A, const double* B, int m, int k, int ncol, int ld, bool transA)
+template <int CS>
+__device__ inline void mm(const Team<CS>& t, double* C, const double* A, const double* B, int m, int k, int ncol,
+                          int ld, bool transA)
 {
-    for (int e = threadIdx.x; e < m * ncol; e += blockDim.x) {
+    for (int e = t.g(); e < m * ncol; e += t.gs()) {
         int i = e / ncol, j = e % ncol;
         double s = 0.0;
         if (transA)
@@ -55,7 +96,7 @@ __device__ inline void mm(double* C, const double* A, const double* B, int m, in
             for (int l = 0; l < k; ++l) s = fma(A[i * ld + l], B[l * ld + j], s);
         C[i * ld + j] = s;
     }
-    __syncthreads();
+    t.sync();
 }
 
 struct JacobiScratch {
@@ -67,14 +108,16 @@ struct JacobiScratch {
 // m <= kMaxFragAO.
 // Parallel ordering: round-robin pairing (circle method), m/2 disjoint rotations per round, each
 // zeroing A_pq with t = sgn(theta)/(|theta| + sqrt(theta^2 + 1)), theta = (A_qq - A_pp)/(2 A_pq)
-// (Golub & Van Loan, symmetric Schur decomposition).
+// (Golub & Van Loan, symmetric Schur decomposition).  Every block of the team computes the rotations
+// of a round itself (into its own scratch); row updates, then column updates, are spread over the team.
 // On exit diag(A) holds the eigenvalues and the columns of V the eigenvectors.  Stops when the
 // off-diagonal Frobenius norm is below 1e-14 times the largest diagonal magnitude.
-__device__ void jacobi_eigh(double* A, double* V, int m, int ld, JacobiScratch* js, double* red)
+template <int CS>
+__device__ void jacobi_eigh(const Team<CS>& t, double* A, double* V, int m, int ld, JacobiScratch* js, double* red)
 {
     // A built from matrix products is symmetric only to rounding; an orthogonal similarity keeps
     // the antisymmetric part, so symmetrise first and measure convergence on the upper triangle.
-    for (int e = threadIdx.x; e < m * m; e += blockDim.x) {
+    for (int e = t.g(); e < m * m; e += t.gs()) {
         int r = e / m, c = e % m;
         V[r * ld + c] = (r == c) ? 1.0 : 0.0;
         if (r < c) {
@@ -83,18 +126,18 @@ __device__ void jacobi_eigh(double* A, double* V, int m, int ld, JacobiScratch* 
             A[c * ld + r] = v;
         }
     }
-    __syncthreads();
+    t.sync();
     const int M = m + (m & 1);
     const int half = M / 2;
     for (int sweep = 0; sweep < 60; ++sweep) {
         double off = 0.0, dg = 0.0;
-        for (int e = threadIdx.x; e < m * m; e += blockDim.x) {
+        for (int e = t.g(); e < m * m; e += t.gs()) {
             int r = e / m, c = e % m;
             double v = A[r * ld + c];
             if (r < c) off += 2.0 * v * v; else if (r == c) dg = fmax(dg, fabs(v));
         }
-        off = block_sum(off, red);
-        dg = block_max(dg, red);
+        off = team_sum(t, off, red);
+        dg = team_max(t, dg, red);
         if (off <= 1e-28 * fmax(dg * dg, 1e-300)) break;
         for (int rnd = 0; rnd < M - 1; ++rnd) {
             for (int k = threadIdx.x; k < half; k += blockDim.x) {
@@ -109,9 +152,9 @@ __device__ void jacobi_eigh(double* A, double* V, int m, int ld, JacobiScratch* 
                     const float apq = (float)A[p * ld + q];
                     if (apq != 0.0f) {
                         const float theta = (float)(A[q * ld + q] - A[p * ld + p]) / (2.0f * apq);
-                        float t = 1.0f / (fabsf(theta) + sqrtf(fmaf(theta, theta, 1.0f)));
-                        if (theta < 0.0f) t = -t;
-                        const double td = (double)t;
+                        float tt = 1.0f / (fabsf(theta) + sqrtf(fmaf(theta, theta, 1.0f)));
+                        if (theta < 0.0f) tt = -tt;
+                        const double td = (double)tt;
                         c = rsqrt(fma(td, td, 1.0));
                         s = td * c;
                     }
@@ -121,8 +164,9 @@ __device__ void jacobi_eigh(double* A, double* V, int m, int ld, JacobiScratch* 
                 js->c[k] = c;
                 js->s[k] = s;
             }
-            __syncthreads();
-            for (int w = threadIdx.x; w < half * m; w += blockDim.x) {
+            // every block has read the A entries of this round before any row is rewritten
+            if constexpr (CS == 1) __syncthreads(); else t.sync();
+            for (int w = t.g(); w < half * m; w += t.gs()) {
                 int k = w / m, j = w % m;
                 int p = js->p[k], q = js->q[k];
                 if (q >= m || js->s[k] == 0.0) continue;
@@ -131,8 +175,8 @@ __device__ void jacobi_eigh(double* A, double* V, int m, int ld, JacobiScratch* 
                 A[p * ld + j] = c * ap - s * aq;
                 A[q * ld + j] = s * ap + c * aq;
             }
-            __syncthreads();
-            for (int w = threadIdx.x; w < half * m; w += blockDim.x) {
+            t.sync();
+            for (int w = t.g(); w < half * m; w += t.gs()) {
                 int k = w / m, i = w % m;
                 int p = js->p[k], q = js->q[k];
                 if (q >= m || js->s[k] == 0.0) continue;
@@ -144,7 +188,7 @@ __device__ void jacobi_eigh(double* A, double* V, int m, int ld, JacobiScratch* 
                 V[i * ld + p] = c * vp - s * vq;
                 V[i * ld + q] = s * vp + c * vq;
             }
-            __syncthreads();
+            t.sync();
         }
     }
 }
@@ -168,13 +212,13 @@ __global__ void k_orthogonaliser(Dev d, const double* S, double* X, int* nmo_out
     double* A = n <= kOrthSmemMaxN ? sm : ws + 2 * d.frag_moff[x];
     double* V = A + n * n;
     __shared__ JacobiScratch js;
-    __shared__ double red[32];
+    __shared__ double red[40];
     __shared__ int keep_idx[kMaxFragAO];
     __shared__ int nkeep;
     const double* Sx = S + d.frag_moff[x];
     for (int e = threadIdx.x; e < n * n; e += blockDim.x) A[e] = Sx[e];
     __syncthreads();
-    jacobi_eigh(A, V, n, n, &js, red);
+    jacobi_eigh(Team<1>{0}, A, V, n, n, &js, red);
     if (threadIdx.x == 0) {
         int c = 0;
         for (int k = 0; k < n; ++k)
@@ -225,25 +269,25 @@ cudaError_t launch_orthogonaliser(const Dev& d, const double* S, double* X, int*
 // PACKED: G from the packed transposed tensor CT[rs][pq] (setup.cu), thread per pq = (mu <= nu);
 // otherwise from the full C[mu nu][lambda sigma], one warp per row.
 // Working matrices Hw Ss Xs Ds Fs W A V Vp, nine n x n doubles (W doubles as the packed density):
-// in shared memory up to kScfSmemMaxN AOs, else in the global workspace a.ws at 9 frag_moff[x].
+// in shared memory up to kScfSmemMaxN AOs (one block per fragment, CS = 1), else in the global
+// workspace a.ws at 9 frag_moff[x] (one thread-block cluster of CS blocks per fragment).
 // The Jacobi of each micro-iteration starts from the previous eigenvectors Vp: A <- Vp^T A Vp,
 // so only the small change of F' between iterations has to be rotated away.
-template <bool PACKED>
-__global__ void __launch_bounds__(256) k_fragment_scf(Dev d, ScfArgs a)
+template <bool PACKED, int CS>
+__device__ __forceinline__ void fragment_scf(const Dev& d, const ScfArgs& a, const int x, const Team<CS> t,
+                                             double* sm)
 {
-    const int x = blockIdx.x;
     const int n = d.frag_nao[x];
     const int m = a.nmo[x];
     const int nocc = d.frag_nocc[x];
     const int n2 = n * n;
     const int np = n * (n + 1) / 2;
     const int64_t mo = d.frag_moff[x];
-    extern __shared__ double sm[];
-    if (n > kScfSmemMaxN && !a.ws) {
+    if ((CS == 1 && n > kScfSmemMaxN && !a.ws) || (CS > 1 && !a.ws)) {
         if (threadIdx.x == 0) atomicOr(d.err_flag, kErrBounds);
         return;
     }
-    double* Hw = n <= kScfSmemMaxN ? sm : a.ws + 9 * mo;
+    double* Hw = (CS == 1 && n <= kScfSmemMaxN) ? sm : a.ws + 9 * mo;
     double* Ss = Hw + n2;
     double* Xs = Ss + n2;
     double* Ds = Xs + n2;
@@ -253,50 +297,52 @@ __global__ void __launch_bounds__(256) k_fragment_scf(Dev d, ScfArgs a)
     double* V = A + n2;
     double* Vp = V + n2;
     __shared__ JacobiScratch js;
-    __shared__ double red[32];
+    __shared__ double red[40];
     __shared__ double B[8][8];
     __shared__ double coef[9];
     __shared__ int order[kMaxFragAO];
-    const int tid = threadIdx.x, nt = blockDim.x;
-    const int lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
+    const int tid = threadIdx.x;
+    const int g0 = t.g(), gs = t.gs();
+    const int lane = tid & 31;
+    const int gw = g0 >> 5, nw = gs >> 5;  // team-wide warp index and count
     const double* C = PACKED ? a.eric + d.frag_coff[x] : a.eric + d.frag_eoff[x];
     double* hF = a.diis_by_moff ? a.diis_F + 2 * (int64_t)a.diis_size * mo : a.diis_F + (int64_t)x * a.diis_stride;
     double* he = hF + (int64_t)a.diis_size * n2;
 
-    for (int e = tid; e < n2; e += nt) {
+    for (int e = g0; e < n2; e += gs) {
         Hw[e] = a.h[mo + e] + (a.omega ? a.omega[mo + e] : 0.0);
         Ss[e] = a.S[mo + e];
         Xs[e] = a.X[mo + e];
         if (a.have_start) Ds[e] = a.D[mo + e];
     }
-    __syncthreads();
+    t.sync();
     bool have_vp = false;
 
     // Roothaan step: W holds the (extrapolated) Fock matrix on entry; Ds gets the aufbau density.
     auto roothaan = [&]() {
-        mm(V, W, Xs, n, n, m, n, false);      // V = F X        (n x m)
-        mm(A, Xs, V, m, n, m, n, true);       // A = X^T F X    (m x m)
+        mm(t, V, W, Xs, n, n, m, n, false);      // V = F X        (n x m)
+        mm(t, A, Xs, V, m, n, m, n, true);       // A = X^T F X    (m x m)
         if (have_vp) {
-            mm(V, A, Vp, m, m, m, n, false);  // A <- Vp^T A Vp
-            mm(A, Vp, V, m, m, m, n, true);
+            mm(t, V, A, Vp, m, m, m, n, false);  // A <- Vp^T A Vp
+            mm(t, A, Vp, V, m, m, m, n, true);
         }
-        jacobi_eigh(A, V, m, n, &js, red);    // A -> eigenvalues, V -> eigenvectors (m x m)
+        jacobi_eigh(t, A, V, m, n, &js, red);    // A -> eigenvalues, V -> eigenvectors (m x m)
         if (have_vp) {
-            mm(W, Vp, V, m, m, m, n, false);  // full eigenvectors Vp V
-            for (int e = tid; e < m * m; e += nt) {
+            mm(t, W, Vp, V, m, m, m, n, false);  // full eigenvectors Vp V
+            for (int e = g0; e < m * m; e += gs) {
                 int i = e / m, j = e % m;
                 V[i * n + j] = W[i * n + j];
                 Vp[i * n + j] = W[i * n + j];
             }
         } else {
-            for (int e = tid; e < m * m; e += nt) {
+            for (int e = g0; e < m * m; e += gs) {
                 int i = e / m, j = e % m;
                 Vp[i * n + j] = V[i * n + j];
             }
         }
         have_vp = true;
-        __syncthreads();
-        if (tid == 0) {
+        t.sync();
+        if (tid == 0) {  // every block of the team orders the same eigenvalues the same way
             for (int k = 0; k < m; ++k) order[k] = k;
             for (int k = 0; k < nocc; ++k) {  // selection of the nocc lowest, ties by index
                 int best = k;
@@ -304,30 +350,30 @@ __global__ void __launch_bounds__(256) k_fragment_scf(Dev d, ScfArgs a)
                     double ej = A[order[j] * n + order[j]], eb = A[order[best] * n + order[best]];
                     if (ej < eb || (ej == eb && order[j] < order[best])) best = j;
                 }
-                int t = order[k]; order[k] = order[best]; order[best] = t;
+                int tmp = order[k]; order[k] = order[best]; order[best] = tmp;
             }
         }
         __syncthreads();
-        for (int e = tid; e < n * nocc; e += nt) {  // W = C_occ = X V_occ  (n x nocc)
+        for (int e = g0; e < n * nocc; e += gs) {  // W = C_occ = X V_occ  (n x nocc)
             int i = e / nocc, k = e % nocc;
             int col = order[k];
             double s = 0.0;
             for (int l = 0; l < m; ++l) s = fma(Xs[i * n + l], V[l * n + col], s);
             W[i * n + k] = s;
         }
-        __syncthreads();
-        for (int e = tid; e < n2; e += nt) {      // D = 2 C_occ C_occ^T
+        t.sync();
+        for (int e = g0; e < n2; e += gs) {      // D = 2 C_occ C_occ^T
             int i = e / n, j = e % n;
             double s = 0.0;
             for (int k = 0; k < nocc; ++k) s = fma(W[i * n + k], W[j * n + k], s);
             Ds[e] = 2.0 * s;
         }
-        __syncthreads();
+        t.sync();
     };
 
     if (!a.have_start) {  // core guess: F = h + omega
-        for (int e = tid; e < n2; e += nt) W[e] = Hw[e];
-        __syncthreads();
+        for (int e = g0; e < n2; e += gs) W[e] = Hw[e];
+        t.sync();
         roothaan();
     }
 
@@ -338,13 +384,13 @@ __global__ void __launch_bounds__(256) k_fragment_scf(Dev d, ScfArgs a)
         // F = h + omega + G[D]
         if (PACKED) {
             double* dpk = W;
-            for (int rs = tid; rs < np; rs += nt) {
+            for (int rs = g0; rs < np; rs += gs) {
                 int la = 0, r = rs;
                 while (r >= n - la) { r -= n - la; ++la; }
                 dpk[rs] = Ds[la * n + la + r];
             }
-            __syncthreads();
-            for (int pq = tid; pq < np; pq += nt) {
+            t.sync();
+            for (int pq = g0; pq < np; pq += gs) {
                 int mu = 0, r = pq;
                 while (r >= n - mu) { r -= n - mu; ++mu; }
                 int nu = mu + r;
@@ -354,7 +400,7 @@ __global__ void __launch_bounds__(256) k_fragment_scf(Dev d, ScfArgs a)
                 Fs[nu * n + mu] = Hw[nu * n + mu] + g;
             }
         } else {
-            for (int row = warp; row < n2; row += nw) {
+            for (int row = gw; row < n2; row += nw) {
                 double g = 0.0;
                 for (int c = lane; c < n2; c += 32) g = fma(C[(size_t)row * n2 + c], Ds[c], g);
 #pragma unroll
@@ -362,99 +408,99 @@ __global__ void __launch_bounds__(256) k_fragment_scf(Dev d, ScfArgs a)
                 if (lane == 0) Fs[row] = Hw[row] + g;
             }
         }
-        __syncthreads();
+        t.sync();
         double part = 0.0;
-        for (int e = tid; e < n2; e += nt) part += Ds[e] * (Hw[e] + Fs[e]);
-        E = 0.5 * block_sum(part, red) + a.e_nn[x];
+        for (int e = g0; e < n2; e += gs) part += Ds[e] * (Hw[e] + Fs[e]);
+        E = 0.5 * team_sum(t, part, red) + a.e_nn[x];
         // e = F D S - S D F = M - M^T with M = F D S
-        mm(W, Fs, Ds, n, n, n, n, false);
-        mm(V, W, Ss, n, n, n, n, false);
+        mm(t, W, Fs, Ds, n, n, n, n, false);
+        mm(t, V, W, Ss, n, n, n, n, false);
         double em = 0.0;
-        for (int e = tid; e < n2; e += nt) {
+        for (int e = g0; e < n2; e += gs) {
             int i = e / n, j = e % n;
             em = fmax(em, fabs(V[i * n + j] - V[j * n + i]));
         }
-        em = block_max(em, red);
+        em = team_max(t, em, red);
         if (it > 1 && fabs(E - E_old) < a.e_tol && em < a.comm_tol) {
             conv = true;
             break;
         }
         if (!isfinite(E)) break;
         E_old = E;
-        for (int e = tid; e < n2; e += nt) {
+        for (int e = g0; e < n2; e += gs) {
             int i = e / n, j = e % n;
             W[e] = V[i * n + j] - V[j * n + i];
         }
-        __syncthreads();
+        t.sync();
         // DIIS history (ring of diis_size): F and X^T e X
         const int slot = (it - 1) % a.diis_size;
         const int hist = min(it, a.diis_size);
-        mm(V, W, Xs, n, n, m, n, false);  // V = e X
-        mm(A, Xs, V, m, n, m, n, true);   // A = X^T e X
-        for (int e = tid; e < n2; e += nt) {
+        mm(t, V, W, Xs, n, n, m, n, false);  // V = e X
+        mm(t, A, Xs, V, m, n, m, n, true);   // A = X^T e X
+        for (int e = g0; e < n2; e += gs) {
             hF[(int64_t)slot * n2 + e] = Fs[e];
             int i = e / n, j = e % n;
             he[(int64_t)slot * n2 + e] = (i < m && j < m) ? A[i * n + j] : 0.0;
         }
-        __syncthreads();
+        t.sync();
         for (int j = 0; j < hist; ++j) {
-            double p = 0.0;
-            for (int e = tid; e < n2; e += nt) p += he[(int64_t)slot * n2 + e] * he[(int64_t)j * n2 + e];
-            p = block_sum(p, red);
+            double pj = 0.0;
+            for (int e = g0; e < n2; e += gs) pj += he[(int64_t)slot * n2 + e] * he[(int64_t)j * n2 + e];
+            pj = team_sum(t, pj, red);
             if (tid == 0) {
-                B[slot][j] = p;
-                B[j][slot] = p;
+                B[slot][j] = pj;
+                B[j][slot] = pj;
             }
         }
         __syncthreads();
         if (hist >= 2) {
             if (tid == 0) {  // solve [B -1; -1 0] [c; l] = [0; -1] by Gauss-Jordan, partial pivoting
                 double M[9][10];
-                const int s = hist + 1;
-                for (int i = 0; i < s; ++i)
-                    for (int j = 0; j <= s; ++j) M[i][j] = 0.0;
+                const int sz = hist + 1;
+                for (int i = 0; i < sz; ++i)
+                    for (int j = 0; j <= sz; ++j) M[i][j] = 0.0;
                 for (int i = 0; i < hist; ++i) {
                     for (int j = 0; j < hist; ++j) M[i][j] = B[i][j];
                     M[i][hist] = -1.0;
                     M[hist][i] = -1.0;
                 }
-                M[hist][s] = -1.0;
+                M[hist][sz] = -1.0;
                 bool ok = true;
-                for (int col = 0; col < s; ++col) {
+                for (int col = 0; col < sz; ++col) {
                     int piv = col;
-                    for (int r = col + 1; r < s; ++r)
+                    for (int r = col + 1; r < sz; ++r)
                         if (fabs(M[r][col]) > fabs(M[piv][col])) piv = r;
                     if (fabs(M[piv][col]) < 1e-300) { ok = false; break; }
-                    for (int j = 0; j <= s; ++j) { double t = M[col][j]; M[col][j] = M[piv][j]; M[piv][j] = t; }
-                    for (int r = 0; r < s; ++r) {
+                    for (int j = 0; j <= sz; ++j) { double tmp = M[col][j]; M[col][j] = M[piv][j]; M[piv][j] = tmp; }
+                    for (int r = 0; r < sz; ++r) {
                         if (r == col) continue;
                         double f = M[r][col] / M[col][col];
-                        for (int j = col; j <= s; ++j) M[r][j] -= f * M[col][j];
+                        for (int j = col; j <= sz; ++j) M[r][j] -= f * M[col][j];
                     }
                 }
-                for (int i = 0; i < hist; ++i) coef[i] = ok ? M[i][s] / M[i][i] : (i == slot ? 1.0 : 0.0);
+                for (int i = 0; i < hist; ++i) coef[i] = ok ? M[i][sz] / M[i][i] : (i == slot ? 1.0 : 0.0);
             }
             __syncthreads();
-            for (int e = tid; e < n2; e += nt) {
+            for (int e = g0; e < n2; e += gs) {
                 double f = 0.0;
                 for (int j = 0; j < hist; ++j) f = fma(coef[j], hF[(int64_t)j * n2 + e], f);
                 W[e] = f;
             }
         } else {
-            for (int e = tid; e < n2; e += nt) W[e] = Fs[e];
+            for (int e = g0; e < n2; e += gs) W[e] = Fs[e];
         }
-        __syncthreads();
+        t.sync();
         roothaan();
     }
     // outputs: D and F of the returned density, energies
     double part = 0.0;
-    for (int e = tid; e < n2; e += nt) {
+    for (int e = g0; e < n2; e += gs) {
         a.D[mo + e] = Ds[e];
         a.F[mo + e] = Fs[e];
         part += Ds[e] * (a.omega ? a.omega[mo + e] : 0.0);
     }
-    double trw = block_sum(part, red);
-    if (tid == 0) {
+    double trw = team_sum(t, part, red);
+    if (tid == 0 && t.rank == 0) {
         a.E_scf[x] = E;
         a.E_int[x] = E - trw;
         a.iters[x] = conv ? it : -a.max_iter;
@@ -462,14 +508,86 @@ __global__ void __launch_bounds__(256) k_fragment_scf(Dev d, ScfArgs a)
     }
 }
 
+// One block per fragment (fragments a.list[0..n_list), or all when a.list is null).
+template <bool PACKED>
+__global__ void __launch_bounds__(256) k_fragment_scf(Dev d, ScfArgs a)
+{
+    extern __shared__ double sm[];
+    const int x = a.list ? a.list[blockIdx.x] : (int)blockIdx.x;
+    fragment_scf<PACKED, 1>(d, a, x, Team<1>{0}, sm);
+}
+
+// One cluster of CS blocks per fragment of a.big_list (matrices in the global workspace).
+template <int CS>
+__global__ void __launch_bounds__(256) k_fragment_scf_cluster(Dev d, ScfArgs a)
+{
+    const int rank = (int)cg::this_cluster().block_rank();
+    const int x = a.big_list[blockIdx.x / CS];
+    fragment_scf<true, CS>(d, a, x, Team<CS>{rank}, nullptr);
+}
+
+template <int CS>
+static cudaError_t launch_cluster_scf(const Dev& d, const ScfArgs& a, cudaStream_t s)
+{
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(a.n_big * CS);
+    cfg.blockDim = dim3(256);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = CS;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, k_fragment_scf_cluster<CS>, d, a);
+}
+
+// Blocks per cluster for the fragments above the shared-memory limit: 16 where the device can
+// co-schedule a 16-block cluster of this kernel, else 8 (portable).
+static int scf_cluster_size()
+{
+    static int cs = 0;
+    if (cs) return cs;
+    cs = 8;
+    if (cudaFuncSetAttribute(k_fragment_scf_cluster<16>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) ==
+        cudaSuccess) {
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3(16);
+        cfg.blockDim = dim3(256);
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeClusterDimension;
+        attr[0].val.clusterDim.x = 16;
+        attr[0].val.clusterDim.y = 1;
+        attr[0].val.clusterDim.z = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        int n = 0;
+        if (cudaOccupancyMaxActiveClusters(&n, k_fragment_scf_cluster<16>, &cfg) == cudaSuccess && n > 0) cs = 16;
+    }
+    cudaGetLastError();
+    return cs;
+}
+
 cudaError_t launch_fragment_scf(const Dev& d, const ScfArgs& a, int max_n, cudaStream_t s)
 {
-    const size_t ns = (size_t)std::min(max_n, kScfSmemMaxN);
+    cudaError_t e = cudaSuccess;
+    if (a.n_big > 0) {  // large fragments first: their clusters run alongside the small-fragment blocks
+        if (!a.eric_packed || !a.ws) return cudaErrorInvalidValue;
+        e = scf_cluster_size() == 16 ? launch_cluster_scf<16>(d, a, s) : launch_cluster_scf<8>(d, a, s);
+        if (e != cudaSuccess) return e;
+        note_launches(1);
+    }
+    const int n_small = a.list ? a.n_list : d.n_frag;
+    if (n_small <= 0) return cudaGetLastError();
+    const int ns_max = a.list ? std::min(max_n, kScfSmemMaxN) : max_n;
+    const size_t ns = (size_t)std::min(ns_max, kScfSmemMaxN);
     size_t smem = 9 * ns * ns * sizeof(double);
     auto kern = a.eric_packed ? k_fragment_scf<true> : k_fragment_scf<false>;
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    kern<<<d.n_frag, 256, smem, s>>>(d, a);
+    kern<<<n_small, 256, smem, s>>>(d, a);
     note_launches(1);
     return cudaGetLastError();
 }
