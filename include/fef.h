@@ -89,7 +89,7 @@ typedef struct {
                                 FP64 intra-fragment G, eigensolve and energies) until |dE| <
                                 mixed_switch (or stops decreasing); then one FP64 build becomes the
                                 exact reference and FP32 increments relative to it continue to
-                                convergence.  After a learned start the first field is the FP64 one. */
+                                convergence (from every start). */
     double cutoff_A;         /* fragment pairs with min atom-atom distance >= cutoff are dropped
                                 (J and V together); <= 0 keeps all pairs */
     double schwarz;          /* shell quartet (ab|cd) dropped when Q_ab Q_cd < schwarz (0: none) */
@@ -192,6 +192,13 @@ fef_status fef_stats(const fef_ctx* ctx, int64_t* shell_quartets, int64_t* prim_
  * build used the FP32 core (MIXED) else 0.0.  Copies min(n, max_records) records into records
  * (host, nullable); *n_records (nullable) gets n. */
 fef_status fef_history(const fef_ctx* ctx, int32_t max_records, double* records, int32_t* n_records);
+
+/* Per-fragment state of the last fragment-RHF launch (the start SCF, or the last macro-iteration's):
+ * micro_iters[n_frag] = micro-iterations to convergence, or -max_micro when the fragment did not
+ * converge; homo_lumo_gap[n_frag] = lowest virtual minus highest occupied orbital energy of the last
+ * Roothaan step (hartree; aufbau is ill-defined when it is near 0); E_scf[n_frag] = tr[D (h + omega +
+ * F)]/2 + own nuclear repulsion.  Host arrays, each nullable.  Errors: ARG, CUDA. */
+fef_status fef_fragment_status(const fef_ctx* ctx, int32_t* micro_iters, double* homo_lumo_gap, double* E_scf);
 
 /* Message of the last failing call on ctx (or of the last failed fef_create when ctx is NULL). */
 const char* fef_last_error(const fef_ctx* ctx);

@@ -167,26 +167,38 @@ class Fragments:
     # ------------------------------------------------------------------------------------ RHF
 
     def rhf(self, x: int, omega: np.ndarray, D0=None, max_iter: int = 200, diis_size: int = 8,
-            e_tol: float = 1e-11, comm_tol: float = 1e-9):
+            e_tol: float = 1e-11, comm_tol: float = 1e-9, shift_after: int = 50, level_shift: float = 0.2):
         """Fragment RHF in a frozen field omega: F = h + omega + G[D], F C = S C eps.
 
         Canonical orthogonalisation, aufbau occupation of the lowest n_occ orbitals, DIIS (Pulay)
         on the commutator e = F D S - S D F.  Start: D0, else the core guess (F = h + omega).
+        A fragment not converged after shift_after iterations restarts from its start density (or
+        the core guess) with a fresh DIIS history and its empty orbitals raised by level_shift
+        (F' + level_shift (1 - P') in the orthonormal basis, P' the occupied projector of the
+        current density): the same self-consistent solutions, a damped path to them.
         Returns (D, F, E_scf, iterations, converged).
         """
         S, X, h = self.S[x], self.X[x], self.h[x]
         nocc = self.n_occ[x]
         hw = h + omega
 
-        def diag(F):
-            eps, Cp = np.linalg.eigh(X.T @ F @ X)
+        def diag(F, D_prev=None, shift=0.0):
+            Fo = X.T @ F @ X
+            if shift and D_prev is not None:
+                Po = X.T @ S @ D_prev @ S @ X / 2.0
+                Fo = Fo + shift * (np.eye(Fo.shape[0]) - Po)
+            eps, Cp = np.linalg.eigh(Fo)
             C = X @ Cp
             return density_from_orbitals(C[:, :nocc])
 
         D = diag(hw) if D0 is None else D0
+        D_start = D
         Fs, es = [], []
         E_old = None
+        shift = 0.0
         for it in range(1, max_iter + 1):
+            if shift_after and it == shift_after + 1:
+                D, Fs, es, shift = D_start, [], [], level_shift
             F = hw + self.G(x, D)
             E = 0.5 * np.sum(D * (hw + F)) + self.E_nn_intra[x]
             err = F @ D @ S - S @ D @ F
@@ -214,7 +226,7 @@ class Fragments:
                     Fx = sum(ci * Fi for ci, Fi in zip(c, Fs))
                 except np.linalg.LinAlgError:
                     Fx = F
-            D = diag(Fx)
+            D = diag(Fx, D, shift)
         return D, F, E, max_iter, False
 
     # ------------------------------------------------------------------------------------ energies

@@ -31,7 +31,8 @@ EXPORTED = ["fef_default_options", "fef_create", "fef_ao_layout", "fef_build_foc
             "fef_measure_fma_peak", "fef_fragment_rhf_noalloc", "fef_history", "fef_mlp_create", "fef_mlp_destroy",
             "fef_mlp_params", "fef_mlp_set_scaling", "fef_mlp_loss_grad", "fef_mlp_train", "fef_mlp_predict",
             "fef_mlp_last_error", "fef_learned_features", "fef_set_warm_start",
-            "fef_noninteracting_scf", "fef_get_tile_plan", "fef_set_tile_plan", "fef_autotune"]
+            "fef_noninteracting_scf", "fef_get_tile_plan", "fef_set_tile_plan", "fef_autotune",
+            "fef_fragment_status"]
 
 
 class FefError(RuntimeError):
@@ -117,6 +118,7 @@ def lib():
     L.fef_set_warm_start.argtypes = [vp, vp]
     L.fef_fragment_rhf_noalloc.argtypes = [ctypes.c_int32, ip, ip, dp, vp, vp, vp, vp, vp, vp, vp, vp,
                                            ctypes.POINTER(fef_options), vp]
+    L.fef_fragment_status.argtypes = [vp, ip, dp, dp]
     L.fef_get_tile_plan.argtypes = [vp, ctypes.c_int32, ctypes.POINTER(fef_tile_plan)]
     L.fef_set_tile_plan.argtypes = [vp, ctypes.c_int32, ctypes.POINTER(fef_tile_plan)]
     L.fef_autotune.argtypes = [vp, ctypes.c_int32, ctypes.c_int32, ctypes.c_double, ctypes.POINTER(fef_tile_plan)]
@@ -294,6 +296,17 @@ def fef_history(ctx: Context) -> list:
     _check(lib().fef_history(ctx.ptr, n.value, _ptr(buf, ctypes.c_double), ctypes.byref(n)), ctx.ptr)
     keys = ("k", "E_tot", "dE_tot", "dE_x_max", "micro_max", "micro_sum", "jengine_ms", "scf_ms", "fp32")
     return [dict(zip(keys, buf[nf * i:nf * i + nf].tolist())) for i in range(n.value)]
+
+
+def fef_fragment_status(ctx: Context) -> dict:
+    """Per-fragment micro-iterations (negative: not converged), HOMO-LUMO gap and E_scf of the last
+    fragment-RHF launch."""
+    it = np.zeros(ctx.n_frag, np.int32)
+    gap = np.zeros(ctx.n_frag)
+    e = np.zeros(ctx.n_frag)
+    _check(lib().fef_fragment_status(ctx.ptr, _ptr(it, ctypes.c_int32), _ptr(gap, ctypes.c_double),
+                                     _ptr(e, ctypes.c_double)), ctx.ptr)
+    return dict(micro_iters=it, homo_lumo_gap=gap, E_scf=e)
 
 
 def _plan_dict(p: fef_tile_plan) -> dict:

@@ -76,6 +76,7 @@ struct Buffers {
     int* scf_small = nullptr;  // fragments of the one-block-per-fragment SCF launch (when some are large)
     int* scf_big = nullptr;    // fragments above kScfSmemMaxN AOs: one thread-block cluster each
     int n_scf_small = 0, n_scf_big = 0;
+    double* gap = nullptr;     // [n_frag] HOMO-LUMO gap of each fragment's last Roothaan step
     double *e_nn_intra = nullptr, *e_nn_pair = nullptr;
     int* nmo = nullptr;
     // per-build data
@@ -305,6 +306,9 @@ static void run_scf(fef_ctx* c, bool with_field, bool have_start)
     a.e_tol = c->opt.micro_e_tol;
     a.comm_tol = c->opt.micro_comm_tol;
     a.ws = b->scf_ws;
+    a.gap = b->gap;
+    a.shift_after = kScfShiftAfter;
+    a.level_shift = kScfLevelShift;
     if (b->n_scf_big > 0) {
         a.list = b->scf_small;
         a.n_list = b->n_scf_small;
@@ -854,6 +858,9 @@ extern "C" fef_status fef_create(const fef_geometry* g, const fef_basis* bs, con
         ck(cudaMallocHost(&b->stage, 16 + 16 * (size_t)nf + 32), "pinned read-back");
         b->stamps = b->alloc<unsigned long long>(4, "timestamps");
         b->iters = b->alloc<int>(nf, "iters");
+        b->gap = b->alloc<double>(nf, "gap");
+        ck(cudaMemsetAsync(b->iters, 0, sizeof(int) * nf, s), "iters");
+        ck(cudaMemsetAsync(b->gap, 0, sizeof(double) * nf, s), "gap");
         // DIIS history at 2 diis_size frag_moff[x] (sized per fragment); SCF workspace in global
         // memory only for fragments too large for shared memory
         b->diis_stride = 0;
@@ -1112,12 +1119,12 @@ extern "C" fef_status fef_iterate(fef_ctx* c, int32_t* n_macro_out, double* fina
     double it_max = 0, it_sum = 0, scf_ms = 0;
     if (o.start != FEF_START_GIVEN) scf_counts(c, it_max, it_sum, scf_ms);
     check_device_flags(c, "fef_iterate start");
-    // MIXED: from a superposition (or given) start the first field is an FP32-core reference and
-    // the coarse phase follows; a learned start is already close to self-consistency, so its first
-    // field is the FP64 reference and the fine phase starts at once.
+    // MIXED: the first field is an FP32-core reference and the coarse phase follows, from any start.
+    // (An exact reference built at a learned start would sit at a density that is not idempotent
+    // and still ~1e-3 from the fixed point; the fine increments relative to it then carry enough
+    // FP32 error to stall near e_tol and force further exact builds.)
     const bool mixed = (o.precision == FEF_MIXED);
-    const bool learned = (o.start == FEF_START_LEARNED);
-    build_fock_internal(c, mixed && !learned ? kBuildFP32Ref : kBuildFP64);
+    build_fock_internal(c, mixed ? kBuildFP32Ref : kBuildFP64);
     std::vector<double> Ex_old, Ex;
     double Et_old = 0, Et = 0, dE = 0;
     read_energies(c, Ex_old, Et_old);
@@ -1138,7 +1145,7 @@ extern "C" fef_status fef_iterate(fef_ctx* c, int32_t* n_macro_out, double* fina
     // (it grows with |D - D_ref|) is now far below e_tol.  Convergence is declared only between two
     // consecutive accurate energies (FP64, or FP32 increments on an exact reference); a stalled fine
     // phase refreshes the reference again.
-    bool fine = !mixed || learned;
+    bool fine = !mixed;
     bool next_fp32 = mixed;
     bool prev_acc = !c->last_build_fp32;
     double dE_prev = 1e300;
@@ -1313,6 +1320,24 @@ extern "C" fef_status fef_autotune(fef_ctx* c, int32_t engine, int32_t reps, dou
             cudaGraphExecDestroy(g);
             g = nullptr;
         }
+    return FEF_OK;
+    FEF_API_END(c)
+}
+
+extern "C" fef_status fef_fragment_status(const fef_ctx* cc, int32_t* micro_iters, double* homo_lumo_gap,
+                                          double* E_scf)
+{
+    if (!cc) return FEF_ERR_ARG;
+    fef_ctx* c = const_cast<fef_ctx*>(cc);
+    FEF_API_BEGIN
+    Buffers* b = c->buf;
+    const int nf = c->n_frag;
+    if (micro_iters)
+        ck(cudaMemcpyAsync(micro_iters, b->iters, sizeof(int) * nf, cudaMemcpyDeviceToHost, c->stream), "status");
+    if (homo_lumo_gap)
+        ck(cudaMemcpyAsync(homo_lumo_gap, b->gap, sizeof(double) * nf, cudaMemcpyDeviceToHost, c->stream), "status");
+    if (E_scf) ck(cudaMemcpyAsync(E_scf, b->E_scf, sizeof(double) * nf, cudaMemcpyDeviceToHost, c->stream), "status");
+    ck(cudaStreamSynchronize(c->stream), "status");
     return FEF_OK;
     FEF_API_END(c)
 }

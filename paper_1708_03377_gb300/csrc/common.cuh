@@ -37,6 +37,10 @@ constexpr double kSqrtPiHalf = 0.88622692545275801365;  // sqrt(pi)/2
 constexpr int kMaxL = 2;            // s, p, d shells
 constexpr int kMaxFragAO = 232;     // AOs per fragment (packed n(n+1)/2 doubles fit in 227 KB of shared memory)
 constexpr int kScfSmemMaxN = 56;    // fragment SCF: 9 n^2 doubles in shared memory up to this n
+// Fragment RHF fallback: a fragment whose DIIS iteration has not converged after kScfShiftAfter
+// micro-iterations continues with the virtual orbitals level-shifted by kScfLevelShift hartree.
+constexpr int kScfShiftAfter = 50;
+constexpr double kScfLevelShift = 0.2;
 constexpr int kOrthSmemMaxN = 112;  // orthogonaliser: 2 n^2 doubles in shared memory up to this n
 constexpr int kMaxLPair = 2 * kMaxL;
 constexpr int kMaxLTot = 2 * kMaxLPair;

@@ -253,6 +253,9 @@ struct ScfArgs {
                             // 0: at x * diis_stride
     const int* list;        // fragments of the one-block-per-fragment launch (null: all fragments)
     int n_list;
+    double* gap;            // [n_frag] HOMO-LUMO gap of the last Roothaan step (nullable)
+    int shift_after;        // > 0: from micro-iteration shift_after + 1 on, level shift the virtual
+    double level_shift;     // orbitals by level_shift (hartree) and restart DIIS (0: never)
     const int* big_list;    // fragments above kScfSmemMaxN AOs, one thread-block cluster each
     int n_big;              // (0: none; then list is null or holds every fragment)
 };

@@ -301,7 +301,9 @@ __device__ __forceinline__ void fragment_scf(const Dev& d, const ScfArgs& a, con
     __shared__ double B[8][8];
     __shared__ double coef[9];
     __shared__ int order[kMaxFragAO];
+    __shared__ double gap;  // HOMO-LUMO gap of the last Roothaan step
     const int tid = threadIdx.x;
+    if (tid == 0) gap = 0.0;
     const int g0 = t.g(), gs = t.gs();
     const int lane = tid & 31;
     const int gw = g0 >> 5, nw = gs >> 5;  // team-wide warp index and count
@@ -317,14 +319,42 @@ __device__ __forceinline__ void fragment_scf(const Dev& d, const ScfArgs& a, con
     }
     t.sync();
     bool have_vp = false;
+    double sigma = 0.0;         // level shift of the virtual orbitals: 0 until the fallback engages
+    bool shift_density = false; // next shift relative to the occupied space of Ds (after a restart)
 
     // Roothaan step: W holds the (extrapolated) Fock matrix on entry; Ds gets the aufbau density.
+    // With a level shift, sigma is added to the orbitals left empty by the previous step (in the
+    // basis of the previous eigenvectors, where the previous occupation is diagonal): the shifted
+    // matrix has the same eigenvectors at self-consistency, so only the path changes.
     auto roothaan = [&]() {
         mm(t, V, W, Xs, n, n, m, n, false);      // V = F X        (n x m)
         mm(t, A, Xs, V, m, n, m, n, true);       // A = X^T F X    (m x m)
+        const double shift = (have_vp || shift_density) ? sigma : 0.0;
+        if (!have_vp && shift != 0.0) {
+            // A += shift (1 - P'), P' = (S X)^T D (S X) / 2 the occupied projector of Ds in the
+            // orthonormal basis (W, V are free once A = X^T F X is formed)
+            mm(t, V, Ss, Xs, n, n, m, n, false);  // V = S X      (n x m)
+            mm(t, W, Ds, V, n, n, m, n, false);   // W = D S X    (n x m)
+            for (int e = g0; e < m * m; e += gs) {
+                const int i = e / m, j = e % m;
+                double pij = 0.0;
+                for (int l = 0; l < n; ++l) pij = fma(V[l * n + i], W[l * n + j], pij);
+                A[i * n + j] += shift * ((i == j ? 1.0 : 0.0) - 0.5 * pij);
+            }
+            t.sync();
+            shift_density = false;
+        }
         if (have_vp) {
             mm(t, V, A, Vp, m, m, m, n, false);  // A <- Vp^T A Vp
             mm(t, A, Vp, V, m, m, m, n, true);
+            if (shift != 0.0) {
+                for (int j = g0; j < m; j += gs) {
+                    bool occ = false;
+                    for (int k = 0; k < nocc; ++k) occ = occ || order[k] == j;
+                    if (!occ) A[j * n + j] += shift;
+                }
+                t.sync();
+            }
         }
         jacobi_eigh(t, A, V, m, n, &js, red);    // A -> eigenvalues, V -> eigenvectors (m x m)
         if (have_vp) {
@@ -352,6 +382,12 @@ __device__ __forceinline__ void fragment_scf(const Dev& d, const ScfArgs& a, con
                 }
                 int tmp = order[k]; order[k] = order[best]; order[best] = tmp;
             }
+            double homo = -1e300, lumo = 1e300;
+            for (int k = 0; k < m; ++k) {
+                const double ek = A[order[k] * n + order[k]];
+                if (k < nocc) homo = fmax(homo, ek); else lumo = fmin(lumo, ek);
+            }
+            gap = (nocc > 0 && nocc < m) ? lumo - homo - shift : 0.0;
         }
         __syncthreads();
         for (int e = g0; e < n * nocc; e += gs) {  // W = C_occ = X V_occ  (n x nocc)
@@ -379,8 +415,25 @@ __device__ __forceinline__ void fragment_scf(const Dev& d, const ScfArgs& a, con
 
     double E_old = 0.0, E = 0.0;
     bool conv = false;
-    int it = 0;
+    int it = 0, it0 = 1;  // it0: first iteration of the current DIIS history
     for (it = 1; it <= a.max_iter; ++it) {
+        // fallback for a fragment that DIIS has not converged in shift_after iterations (DIIS can
+        // wander where no aufbau solution lies): restart from the start density (or core guess)
+        // with the virtual orbitals level-shifted and a fresh DIIS history
+        if (a.shift_after > 0 && it == a.shift_after + 1) {
+            sigma = a.level_shift;
+            it0 = it;
+            have_vp = false;
+            if (a.have_start) {
+                for (int e = g0; e < n2; e += gs) Ds[e] = a.D[mo + e];
+                shift_density = true;
+                t.sync();
+            } else {
+                for (int e = g0; e < n2; e += gs) W[e] = Hw[e];
+                t.sync();
+                roothaan();
+            }
+        }
         // F = h + omega + G[D]
         if (PACKED) {
             double* dpk = W;
@@ -433,8 +486,8 @@ __device__ __forceinline__ void fragment_scf(const Dev& d, const ScfArgs& a, con
         }
         t.sync();
         // DIIS history (ring of diis_size): F and X^T e X
-        const int slot = (it - 1) % a.diis_size;
-        const int hist = min(it, a.diis_size);
+        const int slot = (it - it0) % a.diis_size;
+        const int hist = min(it - it0 + 1, a.diis_size);
         mm(t, V, W, Xs, n, n, m, n, false);  // V = e X
         mm(t, A, Xs, V, m, n, m, n, true);   // A = X^T e X
         for (int e = g0; e < n2; e += gs) {
@@ -501,6 +554,7 @@ __device__ __forceinline__ void fragment_scf(const Dev& d, const ScfArgs& a, con
     }
     double trw = team_sum(t, part, red);
     if (tid == 0 && t.rank == 0) {
+        if (a.gap) a.gap[x] = gap;
         a.E_scf[x] = E;
         a.E_int[x] = E - trw;
         a.iters[x] = conv ? it : -a.max_iter;

@@ -316,27 +316,54 @@ def water_box(n_water: int, seed: int = 0, side: float | None = None,
     return _assemble(frags, basis_sets, kinds, f"water_box(n={n_water}, side={side:.2f}, seed={seed})")
 
 
+class _CellList:
+    """Placed atoms binned in cubic cells of the largest exclusion distance, so that a candidate is
+    tested only against atoms that can lie within that distance (the test's outcome is unchanged)."""
+
+    def __init__(self, cell: float):
+        self.cell = cell
+        self.bins = {}
+        self.xyz = []
+        self.z = []
+
+    def add(self, xyz, z):
+        for r, q in zip(xyz, z):
+            key = tuple(np.floor(r / self.cell).astype(int))
+            self.bins.setdefault(key, []).append(len(self.xyz))
+            self.xyz.append(r)
+            self.z.append(int(q))
+
+    def near(self, xyz):
+        idx = set()
+        for r in xyz:
+            kx, ky, kz = np.floor(r / self.cell).astype(int)
+            for dx in (-1, 0, 1):
+                for dy in (-1, 0, 1):
+                    for dz in (-1, 0, 1):
+                        idx.update(self.bins.get((kx + dx, ky + dy, kz + dz), ()))
+        idx = sorted(idx)
+        return np.array([self.xyz[i] for i in idx]).reshape(-1, 3), np.array([self.z[i] for i in idx], np.int32)
+
+
 def _place(rg, shapes, side, max_tries, fixed=None):
-    placed_xyz = np.zeros((0, 3))
-    placed_z = np.zeros((0,), np.int32)
+    cells = _CellList(2.6)  # the heavy-atom exclusion distance of _min_pair_ok, its largest
     frags = []
     if fixed is not None:
         for z, xyz in fixed:
             frags.append((z, xyz))
-            placed_xyz = np.vstack([placed_xyz, xyz])
-            placed_z = np.concatenate([placed_z, z])
+            cells.add(xyz, z)
     for z, w in shapes:
         for _ in range(max_tries):
             Rm = random_rotation(rg)
             c = rg.uniform(0.0, side, 3)
             xyz = w @ Rm.T + c
-            if _min_pair_ok(xyz, z, placed_xyz, placed_z):
+            near_xyz, near_z = cells.near(xyz)
+            if _min_pair_ok(xyz, z, near_xyz, near_z):
                 break
         else:
             raise RuntimeError("random sequential addition failed; box too dense")
         frags.append((z, xyz))
-        placed_xyz = np.vstack([placed_xyz, xyz])
-        placed_z = np.concatenate([placed_z, z])
+        cells.add(xyz, z)
     return frags
 
 
@@ -362,12 +389,25 @@ def solvated_heterocycle(n_water: int = 1000, side: float = 31.0, seed: int = 0,
 FRAG_TYPES = {3: "water", 6: "formamide", 13: "cytosine", 16: "guanine"}
 
 
-def mixed_snapshot(n_frag: int = 500, seed: int = 0, weights=(0.85, 0.08, 0.05, 0.02)) -> System:
+# Basis-set seed of the mixed (batching) workload: the first of seeds 0-15 whose log-uniform draw
+# gives bound fragments (isolated water-like and formamide-like RHF, which carry all four element
+# bases: highest occupied orbital below -0.2 Eh, gap above 0.3 Eh).  Most draws of 3s2p1d heavy-atom
+# shells leave the highest occupied orbital unbound (up to +1.4 Eh), and such fragments' RHF in a
+# field does not converge.  Fixed once, offline; the generator itself runs no SCF.
+MIXED_BASIS_SEED = 5
+
+
+def mixed_snapshot(n_frag: int = 500, seed: int = 0, weights=(0.85, 0.08, 0.05, 0.02),
+                   basis_seed: int | None = None) -> System:
     """Fragments of uneven size drawn from {3, 6, 13, 16} atoms; all heavy atoms 3s2p1d, H 2s.
 
-    Cube side from the total mass at 1 g/cm^3; larger fragments are placed first.
+    Cube side from the total mass at 1 g/cm^3; larger fragments are placed first.  The basis sets
+    come from the sub-stream of ``basis_seed`` when given (e.g. MIXED_BASIS_SEED, shared by all
+    snapshots of a batch), else from ``seed``.
     """
     rb, rg, rs = _streams(seed, 3)
+    if basis_seed is not None:
+        rb = _streams(basis_seed, 3)[0]
     bs = [random_basis_set(rb, SHELLS_H)]
     kind_of = {1: 0}
     for zz in (6, 7, 8):
@@ -389,7 +429,7 @@ def mixed_snapshot(n_frag: int = 500, seed: int = 0, weights=(0.85, 0.08, 0.05, 
     side = cube_side_for_density(mass)
     frags = _place(rg, shapes, side, 200000)
     kinds = [np.array([kind_of[int(q)] for q in z]) for z, _ in frags]
-    return _assemble(frags, bs, kinds, f"mixed_snapshot(n_frag={n_frag}, seed={seed})")
+    return _assemble(frags, bs, kinds, f"mixed_snapshot(n_frag={n_frag}, seed={seed}, basis_seed={basis_seed})")
 
 
 def random_orbital_coefficients(seed: int, n_ao: int, n_occ: int) -> np.ndarray:
