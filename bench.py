@@ -19,7 +19,7 @@ Legs reported beside it (same workload, same 1e-8 Eh convergence, energies compa
   mixed_learned        MIXED (float-float reference) from the learned warm start; the network is
                        trained beforehand (not timed) on 40 seeded snapshots drawn like the workload.
 e2e    = the same step plus the device->host read of every converged density, wall clock.
-roofline: the J-engine (9 class-pair kernels of one Fock build) against the FP64 ALU peak.
+roofline: the J-engine (one persistent FP64 launch per Fock build) against the FP64 ALU peak.
 --impl reference: the CPU oracle on a bounded sample of the same workload.
 
 Multi-GPU (torchrun): independent replicas, one snapshot per rank (seed = rank), no collective
@@ -398,7 +398,8 @@ def main():
                           "train_loss": net_loss},
         "roofline": {"bound": "alu", "achieved": achieved / 1e12, "peak": FP64_PEAK / 1e12, "unit": "TFLOP/s",
                      "frac": achieved / FP64_PEAK, "traffic": profile_traffic(),
-                     "kernel": "k_jengine<LP,LQ> (9 class-pair launches of one Fock build)",
+                     "kernel": "k_jengine_persistent<0,false> (one persistent launch per Fock build: all "
+                               "fragment pairs and s/p quartet classes, cost-sorted work queue)",
                      "jengine_ms_per_build": jms_per_build, "algorithmic_flop_per_build": flops_build,
                      "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x 2 FLOP x 2070 MHz (1.25 TFLOP/s nominal)",
                      "fma_probe_fp64_tflops": fp64_probe / 1e12, "fma_probe_fp32_tflops": fp32_probe / 1e12},

@@ -2,12 +2,15 @@
 libfef.so).
 
     python -m paper_1708_03377_gb300.solve --waters 64 --cutoff 8 --precision fp64 --repeat 2
+    python -m paper_1708_03377_gb300.solve --workload mixed --fragments 500 --cutoff 10 --precision mixed \
+        --engine df64 --build-only --autotune
 
-Builds the box with synth.systems.water_box(waters, seed) (1 g/cm^3, random orientations, one
-seeded basis), creates a context, iterates the fragment effective field to --e-tol and prints one
-JSON line per repeat: macro-iterations, total energy, device time of fef_iterate, J-engine time and
-the per-macro history.  --build-only does one Fock build of the superposition densities instead of
-the iteration (for profiling a single set of J-engine launches).
+Builds the system (a seeded water box at 1 g/cm^3; the 130-AO solvated heterocycle; or a snapshot of
+fragments of uneven size with s/p/d shells), creates a context, iterates the fragment effective
+field to --e-tol and prints one JSON line per repeat: macro-iterations, total energy, device time of
+fef_iterate, J-engine time and the per-macro history.  --build-only times Fock builds of the
+isolated-fragment densities instead of the iteration; --autotune tunes the J-engine tile plans of
+the engines the options use first.
 """
 from __future__ import annotations
 
@@ -15,6 +18,7 @@ import argparse
 import json
 import os
 import sys
+import time
 
 _ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 if _ROOT not in sys.path:
@@ -23,6 +27,11 @@ if _ROOT not in sys.path:
 
 def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__.splitlines()[0])
+    ap.add_argument("--workload", choices=("water", "heterocycle", "mixed"), default="water",
+                    help="water: seeded water box; heterocycle: 130-AO solute + --waters waters in a 31 A cube; "
+                         "mixed: --fragments fragments of uneven size (3/6/13/16 atoms, s/p/d) per snapshot")
+    ap.add_argument("--fragments", type=int, default=500)
+    ap.add_argument("--autotune", action="store_true", help="autotune the tile plans of the engines used first")
     ap.add_argument("--waters", type=int, default=64)
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--cutoff", type=float, default=8.0)
@@ -39,7 +48,12 @@ def main(argv=None):
     import paper_1708_03377_gb300 as fef
     from synth import systems as S
 
-    system = S.water_box(a.waters, seed=a.seed)
+    if a.workload == "heterocycle":
+        system = S.solvated_heterocycle(n_water=a.waters, seed=a.seed)
+    elif a.workload == "mixed":
+        system = S.mixed_snapshot(a.fragments, seed=a.seed, basis_seed=S.MIXED_BASIS_SEED)
+    else:
+        system = S.water_box(a.waters, seed=a.seed)
     prec = fef.FEF_MIXED if a.precision == "mixed" else fef.FEF_FP64
     eng = fef.FEF_ENGINE_DF64 if a.engine == "df64" else fef.FEF_ENGINE_FP64
     opts = fef.fef_default_options(cutoff_A=a.cutoff, schwarz=a.schwarz, e_tol=a.e_tol, precision=prec,
@@ -47,20 +61,37 @@ def main(argv=None):
     stream = torch.cuda.Stream()
     with torch.cuda.stream(stream):
         for _ in range(a.repeat):
+            t_create = time.time()
             ctx = fef.fef_create_system(system, opts, stream=stream.cuda_stream)
+            stream.synchronize()
+            t_create = time.time() - t_create
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            tuned = {}
+            if a.autotune or a.build_only:
+                fef.fef_noninteracting_scf(ctx)  # densities for the builds (isolated fragments)
+            if a.autotune:
+                engines = [fef.FEF_JENGINE_DF64 if eng == fef.FEF_ENGINE_DF64 else fef.FEF_JENGINE_FP64]
+                if prec == fef.FEF_MIXED:
+                    engines.append(fef.FEF_JENGINE_FP32)
+                for e in engines:
+                    p = fef.fef_autotune(ctx, e, reps=2, budget_ms=4000.0)
+                    tuned[e] = {"persistent": p["persistent"], "tuned_ms": p["tuned_ms"],
+                                "ket_chunk": p["ket_chunk"].tolist()}
             if a.build_only:
-                iso = fef.fef_create_system(system, fef.fef_default_options(cutoff_A=0.1), stream=stream.cuda_stream)
-                fef.fef_iterate(iso)
-                D = fef.fef_get_densities(iso)
-                iso.close()
-                e0.record(stream)
-                fef.fef_build_fock(ctx, D)
-                e1.record(stream)
-                e1.synchronize()
+                D = fef.fef_get_densities(ctx)
+                builds = []
+                for _ in range(3):
+                    e0.record(stream)
+                    fef.fef_build_fock(ctx, D)
+                    e1.record(stream)
+                    e1.synchronize()
+                    builds.append((e0.elapsed_time(e1), fef.fef_stats(ctx)["jengine_ms"]))
                 st = fef.fef_stats(ctx)
-                out = {"build_ms": e0.elapsed_time(e1), "jengine_ms": st["jengine_ms"],
-                       "shell_quartets": st["shell_quartets"]}
+                build_ms, jms = min(builds[1:])
+                out = {"workload": system.name, "create_s": t_create, "build_ms": build_ms, "jengine_ms": jms,
+                       "shell_quartets": st["shell_quartets"], "prim_quartets": st["prim_quartets"],
+                       "n_pairs": st["n_pairs"], "shell_quartets_per_s": st["shell_quartets"] / (jms * 1e-3),
+                       "tuned": tuned}
             else:
                 e0.record(stream)
                 n_macro, dE = fef.fef_iterate(ctx)
@@ -68,7 +99,8 @@ def main(argv=None):
                 e1.synchronize()
                 _, E_tot, _ = fef.fef_energies(ctx)
                 st = fef.fef_stats(ctx)
-                out = {"n_macro": n_macro, "E_tot": E_tot, "iterate_ms": e0.elapsed_time(e1),
+                out = {"workload": system.name, "create_s": t_create, "tuned": tuned,
+                       "n_macro": n_macro, "E_tot": E_tot, "iterate_ms": e0.elapsed_time(e1),
                        "jengine_ms": st["jengine_ms"], "shell_quartets": st["shell_quartets"],
                        "history": fef.fef_history(ctx)}
             ctx.close()
