@@ -31,6 +31,8 @@ def main(argv=None):
                     help="water: seeded water box; heterocycle: 130-AO solute + --waters waters in a 31 A cube; "
                          "mixed: --fragments fragments of uneven size (3/6/13/16 atoms, s/p/d) per snapshot")
     ap.add_argument("--fragments", type=int, default=500)
+    ap.add_argument("--snapshots", type=int, default=1,
+                    help="mixed workload: independent snapshots (seeds seed..seed+n-1) batched into one context")
     ap.add_argument("--autotune", action="store_true", help="autotune the tile plans of the engines used first")
     ap.add_argument("--waters", type=int, default=64)
     ap.add_argument("--seed", type=int, default=0)
@@ -51,7 +53,9 @@ def main(argv=None):
     if a.workload == "heterocycle":
         system = S.solvated_heterocycle(n_water=a.waters, seed=a.seed)
     elif a.workload == "mixed":
-        system = S.mixed_snapshot(a.fragments, seed=a.seed, basis_seed=S.MIXED_BASIS_SEED)
+        snaps = [S.mixed_snapshot(a.fragments, seed=a.seed + k, basis_seed=S.MIXED_BASIS_SEED)
+                 for k in range(a.snapshots)]
+        system = snaps[0] if a.snapshots == 1 else S.batch(snaps, gap=2.0 * a.cutoff)
     else:
         system = S.water_box(a.waters, seed=a.seed)
     prec = fef.FEF_MIXED if a.precision == "mixed" else fef.FEF_FP64

@@ -432,6 +432,26 @@ def mixed_snapshot(n_frag: int = 500, seed: int = 0, weights=(0.85, 0.08, 0.05, 
     return _assemble(frags, bs, kinds, f"mixed_snapshot(n_frag={n_frag}, seed={seed}, basis_seed={basis_seed})")
 
 
+def batch(systems, gap: float = 20.0) -> System:
+    """Independent snapshots in one system: snapshot k is translated along x by k times (the widest
+    snapshot's extent + gap), so that no fragment pair across snapshots falls within a cutoff below
+    gap (A); basis sets are concatenated and re-indexed."""
+    width = max(float(np.ptp(sy.xyz[:, 0])) for sy in systems) + gap
+    Z, xyz, foa, boa, charge, bases = [], [], [], [], [], []
+    f0 = 0
+    for k, sy in enumerate(systems):
+        Z.append(sy.Z)
+        xyz.append(sy.xyz + np.array([k * width, 0.0, 0.0]))
+        foa.append(sy.frag_of_atom + f0)
+        boa.append(sy.basis_of_atom + len(bases))
+        charge.append(sy.charge)
+        bases.extend(sy.basis_sets)
+        f0 += sy.n_frag
+    return System(Z=np.concatenate(Z).astype(np.int32), xyz=np.concatenate(xyz), frag_of_atom=np.concatenate(foa).astype(np.int32),
+                  charge=np.concatenate(charge).astype(np.int32), basis_of_atom=np.concatenate(boa).astype(np.int32),
+                  basis_sets=bases, name=f"batch({len(systems)} x {systems[0].name}, gap={gap})")
+
+
 def random_orbital_coefficients(seed: int, n_ao: int, n_occ: int) -> np.ndarray:
     """G ~ N(0, 1) of shape (n_ao, n_occ): raw occupied-orbital coefficients.
 

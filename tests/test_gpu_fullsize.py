@@ -1,0 +1,87 @@
+"""Full-size parity on sampled outputs: the GPU Fock build of whole workloads (the 64-water box the
+bench times, with its options; a 100-fragment snapshot of uneven s/p/d fragments up to 175 AOs)
+against the CPU oracle evaluated fragment by fragment for a few sampled fragments.  The oracle
+builds F^x = h^x + G[D^x] + sum_{y in N(x)} (V^y + J[D^y]) (Theory, "Fragment Mean Field", Eq. wc
+and Eq. dp2e) from its own Obara-Saika integrals, with the same cutoff and shell-level Schwarz
+screening, from the densities the GPU used.  Bar: 1e-10 Eh per Fock element (FP64 mode)."""
+import numpy as np
+import pytest
+
+from synth import systems as S
+
+pytestmark = pytest.mark.gpu
+
+
+def _fef():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_1708_03377_gb300 as fef
+    return fef
+
+
+def _oracle_fragment_terms(system, x, D_blocks, cutoff_A, tau):
+    """(h^x + G[D^x], omega_x) of fragment x from the oracle, one fragment at a time."""
+    from oracle import integrals as I
+    from oracle.fef import ANGSTROM_PER_BOHR, coulomb, exchange
+    shx = I.fragment_shells(system, x)
+    ax = system.frag_atoms(x)
+    Rb = lambda at: system.xyz[at] / ANGSTROM_PER_BOHR
+    h = shx.kinetic() + shx.nuclear(Rb(ax), system.Z[ax].astype(float))
+    Qx = shx.schwarz()
+    eri = I.eri_block(shx, shx, Qx, Qx, tau)
+    Dx = D_blocks[x]
+    own = h + coulomb(eri, Dx) - 0.5 * exchange(eri, Dx)
+    om = np.zeros_like(h)
+    for y in range(system.n_frag):
+        if y == x:
+            continue
+        ay = system.frag_atoms(y)
+        dmin = np.linalg.norm(system.xyz[ax][:, None] - system.xyz[ay][None], axis=2).min()
+        if dmin >= cutoff_A:
+            continue
+        shy = I.fragment_shells(system, y)
+        om += shx.nuclear(Rb(ay), system.Z[ay].astype(float))
+        e = I.eri_block(shx, shy, Qx, shy.schwarz(), tau)
+        om += np.einsum("ijkl,kl->ij", e, D_blocks[y])
+    return own, om
+
+
+def test_water_box64_sampled_fock():
+    """The bench workload (64 waters, 8 A cutoff, Schwarz 1e-12) in the bench's launch
+    configuration (default persistent FP64 plan): four sampled fragments' full Fock matrices."""
+    fef = _fef()
+    system = S.water_box(64, seed=0)
+    ctx = fef.fef_create_system(system, fef.fef_default_options(cutoff_A=8.0, schwarz=1e-12))
+    fef.fef_noninteracting_scf(ctx)
+    D = fef.fef_get_densities(ctx)
+    F = ctx.unpack(fef.fef_build_fock(ctx, D))
+    Db = ctx.unpack(D)
+    for x in (0, 17, 42, 63):
+        own, om = _oracle_fragment_terms(system, x, Db, 8.0, 1e-12)
+        err = float(np.abs(F[x] - (own + om)).max())
+        assert err <= 1e-10, (x, err)
+    ctx.close()
+
+
+def test_mixed_snapshot_sampled_field():
+    """100 fragments of uneven size (3/6/13/16 atoms; 19, 51, 130 and 175 AOs; classes up to
+    (dd|dd)), 10 A cutoff: the environment field of a water that has 130- and 175-AO neighbours, as
+    F - (h + G[D]) of the GPU build against the oracle's sum over its neighbours."""
+    fef = _fef()
+    system = S.mixed_snapshot(100, seed=0, basis_seed=S.MIXED_BASIS_SEED)
+    x = 73
+    assert S.frag_n_ao(system, x) == 19
+    ctx = fef.fef_create_system(system, fef.fef_default_options(cutoff_A=10.0, schwarz=1e-12))
+    fef.fef_noninteracting_scf(ctx)
+    D = fef.fef_get_densities(ctx)
+    F = ctx.unpack(fef.fef_build_fock(ctx, D))
+    Db = ctx.unpack(D)
+    ctx.close()
+    own, om = _oracle_fragment_terms(system, x, Db, 10.0, 1e-12)
+    big = [y for y in range(system.n_frag) if S.frag_n_ao(system, y) >= 130 and
+           np.linalg.norm(system.xyz[system.frag_atoms(x)][:, None] -
+                          system.xyz[system.frag_atoms(y)][None], axis=2).min() < 10.0]
+    assert big, "the sampled fragment should have large d-shell neighbours"
+    err = float(np.abs(F[x] - (own + om)).max())
+    assert err <= 1e-10, err
