@@ -75,10 +75,26 @@ cudaError_t launch_hermite_density(const Dev& d, const double* D, cudaStream_t s
 // ------------------------------------------------------------------------------------------ J-engine
 // Both contractions of one primitive quartet with compile-time Hermite indices:
 //   JP[i] += sum_j (-1)^{|j|} R[i + j] DQ[j]                      (field on the bra pair, registers)
-//   QJ[j][k] += (-1)^{|j|} sum_lanes sum_i R[i + j] DP[i]          (field on the ket pair, warp sum)
+//   QJ[j][k] += (-1)^{|j|} sum_lanes sum_i R[i + j] DP[i]          (field on the ket pair)
+// The ket-side field is staged per warp instead of butterfly-reduced per ket.  Lane l
+// writes its partial sums of up to 32 ket components (slot = ket of the batch * NQ + component)
+// into row l of a 32 x 33 shared-memory block; once the batch is full, the lane owning a slot sums
+// its column over the 32 rows and adds it to global memory: 31 DADD per 32 components instead of 5
+// shuffle-DADD steps for each.
+constexpr int kKetBufLd = 33;
+constexpr int kKetBufWarp = 32 * kKetBufLd;
+struct KetBuf {
+    double* v;  // [32 lanes][kKetBufLd] partial sums
+    int* k;     // [32] ket pair of each batch position
+};
+struct KetBuf32 {  // the same for the FP32 core
+    float* v;
+    int* k;
+};
+
+// JP[i] += sum_j (-1)^{|j|} R[i + j] DQ[j]  (field on the lane's bra pair)
 template <int NP, int NQ, typename Real>
-__device__ __forceinline__ void hermite_contract(const Real* R, const Real* DP, const Real* DQ, Real* JP,
-                                                 double* __restrict__ QJ, size_t nQ, int k, int lane)
+__device__ __forceinline__ void hermite_bra(const Real* R, const Real* DQ, Real* JP)
 {
     static_for<NP>([&](auto I) {
         constexpr TUV a = htuv(decltype(I)::value);
@@ -93,25 +109,66 @@ __device__ __forceinline__ void hermite_contract(const Real* R, const Real* DP, 
         });
         JP[decltype(I)::value] = acc;
     });
-    Real sq[NQ];
+}
+
+// this lane's partial field on the ket pair, (-1)^{|j|} sum_i R[i + j] DP[i], into batch slot cnt
+template <int NP, int NQ>
+__device__ __forceinline__ void hermite_ket_stage(const double* R, const double* DP, const KetBuf& kb, int cnt,
+                                                  int lane)
+{
+    double* row = kb.v + lane * kKetBufLd + cnt * NQ;
     static_for<NQ>([&](auto Jc) {
         constexpr TUV b = htuv(decltype(Jc)::value);
-        Real s = Real(0);
+        double sum = 0.0;
         static_for<NP>([&](auto I) {
             constexpr TUV a = htuv(decltype(I)::value);
-            s = fma(R[hidx(a.t + b.t, a.u + b.u, a.v + b.v)], DP[decltype(I)::value], s);
+            sum = fma(R[hidx(a.t + b.t, a.u + b.u, a.v + b.v)], DP[decltype(I)::value], sum);
         });
-        sq[decltype(Jc)::value] = ((b.t + b.u + b.v) & 1) ? -s : s;
+        row[decltype(Jc)::value] = ((b.t + b.u + b.v) & 1) ? -sum : sum;
     });
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1)
-        static_for<NQ>([&](auto Jc) { sq[decltype(Jc)::value] += __shfl_xor_sync(0xffffffffu, sq[decltype(Jc)::value], o); });
-    // every lane holds the sums; lane j adds component j (float -> double on the integer pipe)
-    Real mine = sq[0];
+}
+
+template <int NP, int NQ>
+__device__ __forceinline__ void hermite_ket_stage32(const float* R, const float* DP, const KetBuf32& kb, int cnt,
+                                                    int lane)
+{
+    float* row = kb.v + lane * kKetBufLd + cnt * NQ;
     static_for<NQ>([&](auto Jc) {
-        if (lane == decltype(Jc)::value) mine = sq[decltype(Jc)::value];
+        constexpr TUV b = htuv(decltype(Jc)::value);
+        float sum = 0.0f;
+        static_for<NP>([&](auto I) {
+            constexpr TUV a = htuv(decltype(I)::value);
+            sum = fmaf(R[hidx(a.t + b.t, a.u + b.u, a.v + b.v)], DP[decltype(I)::value], sum);
+        });
+        row[decltype(Jc)::value] = ((b.t + b.u + b.v) & 1) ? -sum : sum;
     });
-    if (lane < NQ) atomicAdd(QJ + (size_t)lane * nQ + k, f2d(mine));
+}
+
+template <int NQ>
+__device__ __forceinline__ void ketbuf_flush32(const KetBuf32& kb, int cnt, double* __restrict__ QJ, size_t nQ,
+                                               int lane)
+{
+    __syncwarp();
+    if (lane < cnt * NQ) {
+        float sum = 0.0f;
+#pragma unroll 8
+        for (int r = 0; r < 32; ++r) sum += kb.v[r * kKetBufLd + lane];
+        atomicAdd(QJ + (size_t)(lane % NQ) * nQ + kb.k[lane / NQ], f2d(sum));
+    }
+    __syncwarp();
+}
+
+template <int NQ>
+__device__ __forceinline__ void ketbuf_flush(const KetBuf& kb, int cnt, double* __restrict__ QJ, size_t nQ, int lane)
+{
+    __syncwarp();
+    if (lane < cnt * NQ) {
+        double sum = 0.0;
+#pragma unroll 8
+        for (int r = 0; r < 32; ++r) sum += kb.v[r * kKetBufLd + lane];
+        atomicAdd(QJ + (size_t)(lane % NQ) * nQ + kb.k[lane / NQ], sum);
+    }
+    __syncwarp();
 }
 
 // One warp per tile = (fragment pair, up to 32 bra primitive pairs of class LP in one member x)
@@ -119,12 +176,13 @@ __device__ __forceinline__ void hermite_contract(const Real* R, const Real* DP, 
 // LQ <= LP; the pair's two J directions are both produced, so the member with the larger class is
 // put on the bra side).  Lane i owns bra pair P_i: its centre, Hermite density and
 // Hermite field accumulator stay in registers.  Ket data are warp-uniform loads.  The field on the
-// ket pair is reduced across the warp with shuffles and added to global memory by lane 0.
+// ket pair is staged in the warp's KetBuf and summed over the lanes once per batch of 32 / NQ kets.
 // Shell quartets with Q_ab Q_cd < tau contribute nothing (Schwarz screening at shell level).
 template <int LP, int LQ>
 __device__ __forceinline__ void jtile_fp64(const Dev& d, const int2 tl, const int kb, const int ke, const float tau,
-                                           const int lane)
+                                           const int lane, const KetBuf& kbuf)
 {
+    constexpr int kBatch = 32 / nh(LQ);
     constexpr int NP = nh(LP), NQ = nh(LQ), L = LP + LQ, NR = nh(LP + LQ);
     // tile.x = 2 * pair + swap: the bra fragment is the pair member holding the larger class
     const int pr = tl.x >> 1;
@@ -152,6 +210,7 @@ __device__ __forceinline__ void jtile_fp64(const Dev& d, const int2 tl, const in
     const float* __restrict__ QQ = d.pp_Q[LQ];
     const double* __restrict__ QD = d.pp_Dh[LQ];
     double* __restrict__ QJ = d.pp_Jh[LQ];
+    int cnt = 0;  // kets staged in kbuf
     for (int k = k0; k < k1; ++k) {
         const float qQ = __ldg(QQ + k);
         const bool keep = qP * qQ >= tau;
@@ -180,8 +239,15 @@ __device__ __forceinline__ void jtile_fp64(const Dev& d, const int2 tl, const in
         }
         double R[NR];
         md_R<L, double>(R, base, X, Y, Z);
-        hermite_contract<NP, NQ, double>(R, DP, DQ, JP, QJ, (size_t)nQ, k, lane);
+        hermite_bra<NP, NQ, double>(R, DQ, JP);
+        hermite_ket_stage<NP, NQ>(R, DP, kbuf, cnt, lane);
+        if (lane == 0) kbuf.k[cnt] = k;
+        if (++cnt == kBatch) {
+            ketbuf_flush<NQ>(kbuf, cnt, QJ, (size_t)nQ, lane);
+            cnt = 0;
+        }
     }
+    if (cnt > 0) ketbuf_flush<NQ>(kbuf, cnt, QJ, (size_t)nQ, lane);
     if (valid) {
 #pragma unroll
         for (int i = 0; i < NP; ++i) atomicAdd(d.pp_Jh[LP] + (size_t)i * nP + Pg, JP[i]);
@@ -194,9 +260,10 @@ __device__ __forceinline__ void jtile_fp64(const Dev& d, const int2 tl, const in
 // FP64 registers every 16 ket pairs and all global accumulation is FP64 (atomics on pp_Jh).
 template <int LP, int LQ>
 __device__ __forceinline__ void jtile_fp32(const Dev& d, const int2 tl, const int kb, const int ke, const float tau,
-                                           const int lane)
+                                           const int lane, const KetBuf32& kbuf)
 {
     constexpr int NP = nh(LP), NQ = nh(LQ), L = LP + LQ, NR = nh(LP + LQ);
+    constexpr int kBatch = 32 / NQ;
     // tile.x = 2 * pair + swap: the bra fragment is the pair member holding the larger class
     const int pr = tl.x >> 1;
     const int x = (tl.x & 1) ? d.pair_y[pr] : d.pair_x[pr];
@@ -227,6 +294,7 @@ __device__ __forceinline__ void jtile_fp32(const Dev& d, const int2 tl, const in
     const float* __restrict__ QD = d.pp_Dh32[LQ];
     double* __restrict__ QJ = d.pp_Jh[LQ];
     int since_flush = 0;
+    int cnt = 0;  // kets staged in kbuf
     for (int k = k0; k < k1; ++k) {
         const float qQ = __ldg(QQ + k);
         const bool keep = qP * qQ >= tau;
@@ -251,7 +319,13 @@ __device__ __forceinline__ void jtile_fp32(const Dev& d, const int2 tl, const in
         }
         float R[NR];
         md_R<L, float>(R, base, X, Y, Z);
-        hermite_contract<NP, NQ, float>(R, DP, DQ, JP, QJ, (size_t)nQ, k, lane);
+        hermite_bra<NP, NQ, float>(R, DQ, JP);
+        hermite_ket_stage32<NP, NQ>(R, DP, kbuf, cnt, lane);
+        if (lane == 0) kbuf.k[cnt] = k;
+        if (++cnt == kBatch) {
+            ketbuf_flush32<NQ>(kbuf, cnt, QJ, (size_t)nQ, lane);
+            cnt = 0;
+        }
         if (++since_flush == 16) {
             since_flush = 0;
 #pragma unroll
@@ -261,6 +335,7 @@ __device__ __forceinline__ void jtile_fp32(const Dev& d, const int2 tl, const in
             }
         }
     }
+    if (cnt > 0) ketbuf_flush32<NQ>(kbuf, cnt, QJ, (size_t)nQ, lane);
     if (valid) {
 #pragma unroll
         for (int i = 0; i < NP; ++i) atomicAdd(d.pp_Jh[LP] + (size_t)i * nP + Pg, JP64[i] + f2d(JP[i]));
@@ -271,17 +346,23 @@ __device__ __forceinline__ void jtile_fp32(const Dev& d, const int2 tl, const in
 template <int LP, int LQ>
 __global__ void __launch_bounds__(128) k_jengine(Dev d, const int2* __restrict__ tiles, int n_tiles, float tau)
 {
+    __shared__ double kv[4 * kKetBufWarp];
+    __shared__ int kk[4 * 32];
     const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     if (warp >= n_tiles) return;
-    jtile_fp64<LP, LQ>(d, tiles[warp], 0, INT_MAX, tau, threadIdx.x & 31);
+    const int w = threadIdx.x >> 5;
+    jtile_fp64<LP, LQ>(d, tiles[warp], 0, INT_MAX, tau, threadIdx.x & 31, KetBuf{kv + w * kKetBufWarp, kk + w * 32});
 }
 
 template <int LP, int LQ>
 __global__ void __launch_bounds__(128) k_jengine32(Dev d, const int2* __restrict__ tiles, int n_tiles, float tau)
 {
+    __shared__ float kv[4 * kKetBufWarp];
+    __shared__ int kk[4 * 32];
     const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     if (warp >= n_tiles) return;
-    jtile_fp32<LP, LQ>(d, tiles[warp], 0, INT_MAX, tau, threadIdx.x & 31);
+    const int w = threadIdx.x >> 5;
+    jtile_fp32<LP, LQ>(d, tiles[warp], 0, INT_MAX, tau, threadIdx.x & 31, KetBuf32{kv + w * kKetBufWarp, kk + w * 32});
 }
 
 // ------------------------------------------------------------------------------------------ persistent
@@ -293,19 +374,27 @@ __global__ void __launch_bounds__(128) k_jengine32(Dev d, const int2* __restrict
 // register classes with a d-shell pair (L_P = 3, 4; L_P + L_Q <= 4), whose larger register
 // footprint would otherwise lower the occupancy of the s/p classes.
 template <int MODE, int LP, int LQ>
-__device__ __forceinline__ void jtile(const Dev& d, int2 tl, int kb, int ke, float tau, int lane)
+__device__ __forceinline__ void jtile(const Dev& d, int2 tl, int kb, int ke, float tau, int lane, const KetBuf& kbuf,
+                                      const KetBuf32& kbuf32)
 {
     if constexpr (MODE == 0)
-        jtile_fp64<LP, LQ>(d, tl, kb, ke, tau, lane);
+        jtile_fp64<LP, LQ>(d, tl, kb, ke, tau, lane, kbuf);
     else
-        jtile_fp32<LP, LQ>(d, tl, kb, ke, tau, lane);
+        jtile_fp32<LP, LQ>(d, tl, kb, ke, tau, lane, kbuf32);
 }
 
 template <int MODE, bool SPD>
 __global__ void __launch_bounds__(128) k_jengine_persistent(Dev d, const int4* __restrict__ items, int n_items,
                                                             int* __restrict__ next, float tau)
 {
+    // the ket-side field is staged in shared memory (one buffer per warp, of the core's type)
+    __shared__ double kv[MODE == 0 ? 4 * kKetBufWarp : 1];
+    __shared__ float kv32[MODE == 0 ? 1 : 4 * kKetBufWarp];
+    __shared__ int kk[4 * 32];
     const int lane = threadIdx.x & 31;
+    const int w = threadIdx.x >> 5;
+    const KetBuf kbuf{kv + (MODE == 0 ? w * kKetBufWarp : 0), kk + w * 32};
+    const KetBuf32 kbuf32{kv32 + (MODE == 0 ? 0 : w * kKetBufWarp), kk + w * 32};
     for (;;) {
         int i = 0;
         if (lane == 0) i = atomicAdd(next, 1);
@@ -315,15 +404,15 @@ __global__ void __launch_bounds__(128) k_jengine_persistent(Dev d, const int4* _
         const int2 tl = make_int2(it.x, it.y);
         const int kb = it.z, ke = jitem_ket_end(it);
         switch (jitem_class(it)) {
-            case 0 * kClasses + 0: jtile<MODE, 0, 0>(d, tl, kb, ke, tau, lane); break;
-            case 1 * kClasses + 0: jtile<MODE, 1, 0>(d, tl, kb, ke, tau, lane); break;
-            case 1 * kClasses + 1: jtile<MODE, 1, 1>(d, tl, kb, ke, tau, lane); break;
-            case 2 * kClasses + 0: jtile<MODE, 2, 0>(d, tl, kb, ke, tau, lane); break;
-            case 2 * kClasses + 1: jtile<MODE, 2, 1>(d, tl, kb, ke, tau, lane); break;
-            case 2 * kClasses + 2: jtile<MODE, 2, 2>(d, tl, kb, ke, tau, lane); break;
-            case 3 * kClasses + 0: if constexpr (SPD) jtile<MODE, 3, 0>(d, tl, kb, ke, tau, lane); break;
-            case 3 * kClasses + 1: if constexpr (SPD) jtile<MODE, 3, 1>(d, tl, kb, ke, tau, lane); break;
-            case 4 * kClasses + 0: if constexpr (SPD) jtile<MODE, 4, 0>(d, tl, kb, ke, tau, lane); break;
+            case 0 * kClasses + 0: jtile<MODE, 0, 0>(d, tl, kb, ke, tau, lane, kbuf, kbuf32); break;
+            case 1 * kClasses + 0: jtile<MODE, 1, 0>(d, tl, kb, ke, tau, lane, kbuf, kbuf32); break;
+            case 1 * kClasses + 1: jtile<MODE, 1, 1>(d, tl, kb, ke, tau, lane, kbuf, kbuf32); break;
+            case 2 * kClasses + 0: jtile<MODE, 2, 0>(d, tl, kb, ke, tau, lane, kbuf, kbuf32); break;
+            case 2 * kClasses + 1: jtile<MODE, 2, 1>(d, tl, kb, ke, tau, lane, kbuf, kbuf32); break;
+            case 2 * kClasses + 2: jtile<MODE, 2, 2>(d, tl, kb, ke, tau, lane, kbuf, kbuf32); break;
+            case 3 * kClasses + 0: if constexpr (SPD) jtile<MODE, 3, 0>(d, tl, kb, ke, tau, lane, kbuf, kbuf32); break;
+            case 3 * kClasses + 1: if constexpr (SPD) jtile<MODE, 3, 1>(d, tl, kb, ke, tau, lane, kbuf, kbuf32); break;
+            case 4 * kClasses + 0: if constexpr (SPD) jtile<MODE, 4, 0>(d, tl, kb, ke, tau, lane, kbuf, kbuf32); break;
             default: break;
         }
     }

@@ -132,13 +132,43 @@ __device__ __forceinline__ void boys_df(const float2* __restrict__ table, df64 T
 
 constexpr int kFlushKets = 32;
 
+// The ket-side field is staged per warp (as in the FP64 core): lane l writes its float-float partial
+// sums of up to 32 ket components into row l of a 32 x 33 shared-memory block; once the batch is
+// full, the lane owning a slot sums its column in float-float and adds it to global memory.
+constexpr int kDfBufLd = 33;
+constexpr int kDfBufWarp = 32 * kDfBufLd;
+struct DfKetBuf {
+    float2* v;  // [32 lanes][kDfBufLd] (hi, lo)
+    int* k;     // [32] ket pair of each batch position
+};
+
+template <int NQ>
+__device__ __forceinline__ void df_ketbuf_flush(const DfKetBuf& kb, int cnt, double* __restrict__ QJ, size_t nQ,
+                                                int lane)
+{
+    __syncwarp();
+    if (lane < cnt * NQ) {
+        df64 sum(0.0f, 0.0f);
+#pragma unroll 4
+        for (int r = 0; r < 32; ++r) {
+            const float2 v = kb.v[r * kDfBufLd + lane];
+            sum = sum + df64(v.x, v.y);
+        }
+        double* dst = QJ + (size_t)(lane % NQ) * nQ + kb.k[lane / NQ];
+        atomicAdd(dst, f2d(sum.hi));
+        atomicAdd(dst, f2d(sum.lo));
+    }
+    __syncwarp();
+}
+
 // One warp-tile (32 bra primitive pairs from tl.y) against the ket pairs [kb, ke) (offsets in the
 // partner's class range) in float-float arithmetic.
 template <int LP, int LQ>
 __device__ __forceinline__ void jtile_df(const Dev& d, const int2 tl, const int kb, const int ke, const float tau,
-                                         const int lane)
+                                         const int lane, const DfKetBuf& kbuf)
 {
     constexpr int NP = nh(LP), NQ = nh(LQ), L = LP + LQ, NR = nh(LP + LQ);
+    constexpr int kBatch = 32 / NQ;
     const int pr = tl.x >> 1;
     const int x = (tl.x & 1) ? d.pair_y[pr] : d.pair_x[pr];
     const int y = (tl.x & 1) ? d.pair_x[pr] : d.pair_y[pr];
@@ -169,6 +199,7 @@ __device__ __forceinline__ void jtile_df(const Dev& d, const int2 tl, const int 
     const float2* __restrict__ QD = d.pp_Dhdf[LQ];
     double* __restrict__ QJ = d.pp_Jh[LQ];
     int since_flush = 0;
+    int cnt = 0;  // kets staged in kbuf
     for (int k = k0; k < k1; ++k) {
         const float qQ = __ldg(QQ + k);
         const bool keep = qP * qQ >= tau;
@@ -212,8 +243,8 @@ __device__ __forceinline__ void jtile_df(const Dev& d, const int2 tl, const int 
             });
             JP[decltype(I)::value] = acc;
         });
-        // field on the ket pair: warp sum in df64, then FP64 atomics (hi and lo) by lanes 0..NQ-1
-        df64 sq[NQ];
+        // field on the ket pair: this lane's float-float partial sums, staged for the batch
+        float2* row = kbuf.v + lane * kDfBufLd + cnt * NQ;
         static_for<NQ>([&](auto Jc) {
             constexpr TUV b = htuv(decltype(Jc)::value);
             df64 s(0.0f, 0.0f);
@@ -221,19 +252,13 @@ __device__ __forceinline__ void jtile_df(const Dev& d, const int2 tl, const int 
                 constexpr TUV a = htuv(decltype(I)::value);
                 s = fma(R[hidx(a.t + b.t, a.u + b.u, a.v + b.v)], DP[decltype(I)::value], s);
             });
-            sq[decltype(Jc)::value] = ((b.t + b.u + b.v) & 1) ? -s : s;
+            if ((b.t + b.u + b.v) & 1) s = -s;
+            row[decltype(Jc)::value] = make_float2(s.hi, s.lo);
         });
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1)
-            static_for<NQ>([&](auto Jc) { sq[decltype(Jc)::value] = sq[decltype(Jc)::value] + shfl_xor(sq[decltype(Jc)::value], o); });
-        df64 mine = sq[0];
-        static_for<NQ>([&](auto Jc) {
-            if (lane == decltype(Jc)::value) mine = sq[decltype(Jc)::value];
-        });
-        if (lane < NQ) {
-            double* dst = QJ + (size_t)lane * nQ + k;
-            atomicAdd(dst, f2d(mine.hi));
-            atomicAdd(dst, f2d(mine.lo));
+        if (lane == 0) kbuf.k[cnt] = k;
+        if (++cnt == kBatch) {
+            df_ketbuf_flush<NQ>(kbuf, cnt, QJ, (size_t)nQ, lane);
+            cnt = 0;
         }
         if (++since_flush == kFlushKets) {
             since_flush = 0;
@@ -244,6 +269,7 @@ __device__ __forceinline__ void jtile_df(const Dev& d, const int2 tl, const int 
             }
         }
     }
+    if (cnt > 0) df_ketbuf_flush<NQ>(kbuf, cnt, QJ, (size_t)nQ, lane);
     if (valid) {
 #pragma unroll
         for (int i = 0; i < NP; ++i)
@@ -254,9 +280,12 @@ __device__ __forceinline__ void jtile_df(const Dev& d, const int2 tl, const int 
 template <int LP, int LQ>
 __global__ void __launch_bounds__(128) k_jengine_df(Dev d, const int2* __restrict__ tiles, int n_tiles, float tau)
 {
+    __shared__ float2 kv[4 * kDfBufWarp];
+    __shared__ int kk[4 * 32];
     const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     if (warp >= n_tiles) return;
-    jtile_df<LP, LQ>(d, tiles[warp], 0, INT_MAX, tau, threadIdx.x & 31);
+    const int w = threadIdx.x >> 5;
+    jtile_df<LP, LQ>(d, tiles[warp], 0, INT_MAX, tau, threadIdx.x & 31, DfKetBuf{kv + w * kDfBufWarp, kk + w * 32});
 }
 
 // Persistent float-float J-engine over the s/p classes: warps take cost-sorted items from a queue
@@ -264,7 +293,10 @@ __global__ void __launch_bounds__(128) k_jengine_df(Dev d, const int2* __restric
 __global__ void __launch_bounds__(128) k_jengine_df_persistent(Dev d, const int4* __restrict__ items, int n_items,
                                                                int* __restrict__ next, float tau)
 {
+    __shared__ float2 kv[4 * kDfBufWarp];
+    __shared__ int kk[4 * 32];
     const int lane = threadIdx.x & 31;
+    const DfKetBuf kbuf{kv + (threadIdx.x >> 5) * kDfBufWarp, kk + (threadIdx.x >> 5) * 32};
     for (;;) {
         int i = 0;
         if (lane == 0) i = atomicAdd(next, 1);
@@ -274,12 +306,12 @@ __global__ void __launch_bounds__(128) k_jengine_df_persistent(Dev d, const int4
         const int2 tl = make_int2(it.x, it.y);
         const int kb = it.z, ke = jitem_ket_end(it);
         switch (jitem_class(it)) {
-            case 0 * kClasses + 0: jtile_df<0, 0>(d, tl, kb, ke, tau, lane); break;
-            case 1 * kClasses + 0: jtile_df<1, 0>(d, tl, kb, ke, tau, lane); break;
-            case 1 * kClasses + 1: jtile_df<1, 1>(d, tl, kb, ke, tau, lane); break;
-            case 2 * kClasses + 0: jtile_df<2, 0>(d, tl, kb, ke, tau, lane); break;
-            case 2 * kClasses + 1: jtile_df<2, 1>(d, tl, kb, ke, tau, lane); break;
-            case 2 * kClasses + 2: jtile_df<2, 2>(d, tl, kb, ke, tau, lane); break;
+            case 0 * kClasses + 0: jtile_df<0, 0>(d, tl, kb, ke, tau, lane, kbuf); break;
+            case 1 * kClasses + 0: jtile_df<1, 0>(d, tl, kb, ke, tau, lane, kbuf); break;
+            case 1 * kClasses + 1: jtile_df<1, 1>(d, tl, kb, ke, tau, lane, kbuf); break;
+            case 2 * kClasses + 0: jtile_df<2, 0>(d, tl, kb, ke, tau, lane, kbuf); break;
+            case 2 * kClasses + 1: jtile_df<2, 1>(d, tl, kb, ke, tau, lane, kbuf); break;
+            case 2 * kClasses + 2: jtile_df<2, 2>(d, tl, kb, ke, tau, lane, kbuf); break;
             default: break;
         }
     }
