@@ -211,6 +211,17 @@ def run_reference(args, ws, rank):
 
 
 # ----------------------------------------------------------------------------------------- our arm
+def reduce_over_replicas(dist, total_ms, quartets, launches, device):
+    """Whole-job figures of independent replicas: the slowest rank's time, the summed shell quartets
+    and kernel launches of all ranks (one collective pair, outside the timed region)."""
+    import torch
+    t = torch.tensor([total_ms, float(quartets), float(launches)], dtype=torch.float64, device=device)
+    tmax = t.clone()
+    dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(tmax[0]), float(t[1]), int(t[2])
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -353,11 +364,7 @@ def main():
 
     total_ms = float(sum(step_ms))
     if pg:
-        t = torch.tensor([total_ms, float(quartets), float(launches)], dtype=torch.float64, device="cuda")
-        tmax = t.clone()
-        pg.all_reduce(tmax, op=pg.ReduceOp.MAX)
-        pg.all_reduce(t, op=pg.ReduceOp.SUM)
-        total_ms, quartets, launches = float(tmax[0]), float(t[1]), int(t[2])
+        total_ms, quartets, launches = reduce_over_replicas(pg, total_ms, quartets, launches, "cuda")
     if rank != 0:
         if pg:
             pg.destroy_process_group()

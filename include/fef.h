@@ -95,7 +95,10 @@ typedef struct {
     double schwarz;          /* shell quartet (ab|cd) dropped when Q_ab Q_cd < schwarz (0: none) */
     double e_tol;            /* FEF convergence: |dE_tot| < e_tol and max_x |dE_x| < e_tol */
     double micro_e_tol;      /* fragment RHF: |dE_x^scf| < micro_e_tol ... */
-    double micro_comm_tol;   /* ... and max |F D S - S D F| < micro_comm_tol */
+    double micro_comm_tol;   /* ... and max |F D S - S D F| < micro_comm_tol.  Inside fef_iterate these
+                                are floors: each macro-iteration's fragment RHF stops at
+                                max(floor, min(1e-7, 1e-5 dE)) and max(floor, min(1e-5, 1e-3 dE)),
+                                dE the previous macro-iteration's energy change (1e-3 for the first) */
     int32_t max_macro;       /* FEF macro-iterations limit */
     int32_t max_micro;       /* fragment RHF iterations limit per macro-iteration */
     int32_t diis_size;       /* Pulay DIIS subspace size, 1..8 (1 = plain Roothaan) */

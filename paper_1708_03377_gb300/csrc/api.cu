@@ -57,6 +57,7 @@ struct Buffers {
         if (capture_stream) cudaStreamDestroy(capture_stream);
         if (jplan) jplan_destroy(jplan);
         if (stage) cudaFreeHost(stage);
+        if (scf_tol_host) cudaFreeHost(scf_tol_host);
         for (void* p : allocs) cudaFree(p);
     }
     // one CUDA graph per kind of macro-iteration (fragment SCF + Fock build + read-back), built on
@@ -70,6 +71,8 @@ struct Buffers {
     long long macro_graph_launches[3] = {};
     // pinned read-back of one macro-iteration: E_tot, error flag, E_frag[n], iters[n]
     unsigned char* stage = nullptr;
+    double* scf_tol = nullptr;       // device [2]: micro-iteration thresholds of the next fragment SCF
+    double* scf_tol_host = nullptr;  // pinned staging of scf_tol
     // geometry-time data
     double *S = nullptr, *h = nullptr, *X = nullptr, *Venv = nullptr, *eric = nullptr, *boys = nullptr;
     double* scf_ws = nullptr;  // fragment-SCF workspace for fragments above kScfSmemMaxN AOs
@@ -307,6 +310,7 @@ static void run_scf(fef_ctx* c, bool with_field, bool have_start)
     a.comm_tol = c->opt.micro_comm_tol;
     a.ws = b->scf_ws;
     a.gap = b->gap;
+    a.tol = b->scf_tol;
     a.shift_after = kScfShiftAfter;
     a.level_shift = kScfLevelShift;
     if (b->n_scf_big > 0) {
@@ -337,6 +341,29 @@ static void scf_counts(fef_ctx* c, double& max_it, double& sum_it, double& ms)
     float f = 0.f;
     ck(cudaEventElapsedTime(&f, c->buf->ev2, c->buf->ev3), "event time");
     ms = f;
+}
+
+// Micro-iteration thresholds of the next fragment SCF (stream-ordered copy from pinned memory, made
+// before a graph replay so that captured graphs read them from device memory).  progress: the
+// energy change of the previous macro-iteration (< 0: the options' thresholds).  An SCF in a field
+// that will still move by ~progress need not be converged below ~1e-3 progress (commutator) and
+// ~1e-5 progress (energy); the options' thresholds are the floor, so the last macro-iterations and
+// the fixed point are those of tightly converged fragment SCFs.
+static void set_scf_thresholds(fef_ctx* c, double progress)
+{
+    Buffers* b = c->buf;
+    const fef_options& o = c->opt;
+    double e = o.micro_e_tol, m = o.micro_comm_tol;
+    if (progress >= 0.0) {
+        e = std::max(o.micro_e_tol, std::min(1e-7, 1e-5 * progress));
+        m = std::max(o.micro_comm_tol, std::min(1e-5, 1e-3 * progress));
+    }
+    if (e == b->scf_tol_host[0] && m == b->scf_tol_host[1]) return;
+    ck(cudaStreamSynchronize(c->stream), "thresholds");  // the previous copy has been consumed
+    b->scf_tol_host[0] = e;
+    b->scf_tol_host[1] = m;
+    ck(cudaMemcpyAsync(b->scf_tol, b->scf_tol_host, 2 * sizeof(double), cudaMemcpyHostToDevice, c->stream),
+       "thresholds");
 }
 
 // ------------------------------------------------------------------------------ one macro-iteration
@@ -856,6 +883,11 @@ extern "C" fef_status fef_create(const fef_geometry* g, const fef_basis* bs, con
         b->E_frag = b->alloc<double>(nf, "E_frag");
         b->E_tot = b->alloc<double>(1, "E_tot");
         ck(cudaMallocHost(&b->stage, 16 + 16 * (size_t)nf + 32), "pinned read-back");
+        ck(cudaMallocHost(&b->scf_tol_host, 2 * sizeof(double)), "pinned thresholds");
+        b->scf_tol = b->alloc<double>(2, "SCF thresholds");
+        b->scf_tol_host[0] = o.micro_e_tol;
+        b->scf_tol_host[1] = o.micro_comm_tol;
+        ck(cudaMemcpyAsync(b->scf_tol, b->scf_tol_host, 2 * sizeof(double), cudaMemcpyHostToDevice, s), "thresholds");
         b->stamps = b->alloc<unsigned long long>(4, "timestamps");
         b->iters = b->alloc<int>(nf, "iters");
         b->gap = b->alloc<double>(nf, "gap");
@@ -1077,6 +1109,7 @@ extern "C" fef_status fef_noninteracting_scf(fef_ctx* c)
     if (!c) return FEF_ERR_ARG;
     FEF_API_BEGIN
     clear_flags(c);
+    set_scf_thresholds(c, -1.0);
     run_scf(c, false, false);
     int flag = 0;
     ck(cudaMemcpyAsync(&flag, c->buf->err_flag, sizeof(int), cudaMemcpyDeviceToHost, c->stream), "flags");
@@ -1098,6 +1131,7 @@ extern "C" fef_status fef_iterate(fef_ctx* c, int32_t* n_macro_out, double* fina
     if (o.start == FEF_START_GIVEN) {
         require(c->have_density, FEF_ERR_ARG, "fef_iterate: start=GIVEN but no densities were set");
     } else if (o.start == FEF_START_SUPERPOSITION) {
+        set_scf_thresholds(c, -1.0);
         run_scf(c, false, false);  // isolated-fragment RHF from the core guess
         int flag = 0;
         ck(cudaMemcpyAsync(&flag, c->buf->err_flag, sizeof(int), cudaMemcpyDeviceToHost, c->stream), "flags");
@@ -1108,6 +1142,7 @@ extern "C" fef_status fef_iterate(fef_ctx* c, int32_t* n_macro_out, double* fina
         // learned: isolated-fragment RHF, then D = D_iso + the network's predicted change from the
         // environment potential and field at each atom (molecule-fixed frames)
         require(c->warm_start != nullptr, FEF_ERR_ARG, "fef_iterate: start=LEARNED needs fef_set_warm_start");
+        set_scf_thresholds(c, -1.0);
         run_scf(c, false, false);
         int flag = 0;
         ck(cudaMemcpyAsync(&flag, c->buf->err_flag, sizeof(int), cudaMemcpyDeviceToHost, c->stream), "flags");
@@ -1149,8 +1184,12 @@ extern "C" fef_status fef_iterate(fef_ctx* c, int32_t* n_macro_out, double* fina
     bool next_fp32 = mixed;
     bool prev_acc = !c->last_build_fp32;
     double dE_prev = 1e300;
+    // fragment-SCF thresholds follow the previous macro-iteration's energy change (the first one,
+    // from the isolated or given densities, assumes a 1e-3 Eh polarisation step)
+    double prog_last = 1e-3;
     for (k = 1; k <= o.max_macro; ++k) {
         const int kind = resolve_kind(c, next_fp32 ? kBuildFP32Inc : kBuildFP64);
+        set_scf_thresholds(c, prog_last);
         macro_step(c, kind);
         build_fock_host(c, kind);
         const bool this_fp64 = !c->last_build_fp32;
@@ -1196,6 +1235,7 @@ extern "C" fef_status fef_iterate(fef_ctx* c, int32_t* n_macro_out, double* fina
         // progress measure: the larger of |dE_tot| and max_x |dE_x| (|dE_tot| alone can drop by
         // cancellation between fragments and then rise again without any stall)
         const double prog = std::max(dE, dEx);
+        prog_last = prog;
         if (mixed) {
             if (!fine) {
                 if (prog < o.mixed_switch || prog > dE_prev) {

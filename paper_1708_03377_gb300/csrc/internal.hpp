@@ -254,6 +254,7 @@ struct ScfArgs {
     const int* list;        // fragments of the one-block-per-fragment launch (null: all fragments)
     int n_list;
     double* gap;            // [n_frag] HOMO-LUMO gap of the last Roothaan step (nullable)
+    const double* tol;      // device [2]: e_tol, comm_tol of this launch (null: the fields above)
     int shift_after;        // > 0: from micro-iteration shift_after + 1 on, level shift the virtual
     double level_shift;     // orbitals by level_shift (hartree) and restart DIIS (0: never)
     const int* big_list;    // fragments above kScfSmemMaxN AOs, one thread-block cluster each

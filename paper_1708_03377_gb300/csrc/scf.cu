@@ -416,6 +416,9 @@ __device__ __forceinline__ void fragment_scf(const Dev& d, const ScfArgs& a, con
     double E_old = 0.0, E = 0.0;
     bool conv = false;
     int it = 0, it0 = 1;  // it0: first iteration of the current DIIS history
+    // convergence thresholds: from device memory when given (set between graph replays)
+    const double e_tol = a.tol ? a.tol[0] : a.e_tol;
+    const double comm_tol = a.tol ? a.tol[1] : a.comm_tol;
     for (it = 1; it <= a.max_iter; ++it) {
         // fallback for a fragment that DIIS has not converged in shift_after iterations (DIIS can
         // wander where no aufbau solution lies): restart from the start density (or core guess)
@@ -474,7 +477,7 @@ __device__ __forceinline__ void fragment_scf(const Dev& d, const ScfArgs& a, con
             em = fmax(em, fabs(V[i * n + j] - V[j * n + i]));
         }
         em = team_max(t, em, red);
-        if (it > 1 && fabs(E - E_old) < a.e_tol && em < a.comm_tol) {
+        if (it > 1 && fabs(E - E_old) < e_tol && em < comm_tol) {
             conv = true;
             break;
         }

@@ -288,3 +288,25 @@ def test_graph_and_eager_macro_iterations_agree(box8, precision):
     assert out[0][0] == out[1][0] == out[2][0]
     assert abs(out[0][1] - out[1][1]) < 1e-10 and abs(out[1][1] - out[2][1]) < 1e-10
     assert np.abs(out[0][2] - out[1][2]).max() < 1e-10
+
+
+def test_fragment_status_after_iterate(box8):
+    """fef_fragment_status: every fragment's last RHF converged (positive micro-iteration count), its
+    aufbau is well defined: a positive HOMO-LUMO gap equal to the one of the oracle's Fock matrix of
+    the converged densities (to the last macro-iteration's field change)."""
+    fef = _fef()
+    system = box8
+    ref = _oracle(system, cutoff_A=6.0, schwarz=1e-12)
+    ctx = fef.fef_create_system(system, fef.fef_default_options(cutoff_A=6.0, schwarz=1e-12, e_tol=1e-10))
+    fef.fef_iterate(ctx)
+    st = fef.fef_fragment_status(ctx)
+    assert (st["micro_iters"] > 0).all()
+    D = ctx.unpack(fef.fef_get_densities(ctx))
+    for x in range(ref.nf):
+        om = ref.omega(D)[x]
+        F = ref.h[x] + om + ref.G(x, D[x])
+        eps = np.linalg.eigvalsh(ref.X[x].T @ F @ ref.X[x])
+        gap = eps[ref.n_occ[x]] - eps[ref.n_occ[x] - 1]
+        assert st["homo_lumo_gap"][x] > 0
+        assert abs(st["homo_lumo_gap"][x] - gap) < 1e-5
+    ctx.close()
