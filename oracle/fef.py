@@ -229,6 +229,28 @@ class Fragments:
             D = diag(Fx, D, shift)
         return D, F, E, max_iter, False
 
+    # ------------------------------------------------------------------------------------ E_M2
+
+    def e_m2(self, x: int, F: np.ndarray) -> float:
+        """Monomer second-order energy of fragment x (Eq. EM2 with the first-order doubles of Eq.
+        monDoubles): with the fragment's canonical orbitals (F C = S C eps, canonical
+        orthogonalisation, aufbau) the zeroth-order effective Hamiltonian is the diagonal Fock
+        operator and the doubles driver is the fragment's own two-electron interaction (the
+        environment field is one-body), so that
+
+            E_M2^x = sum_{ij occ, ab virt} (ia|jb) [2 (ia|jb) - (ib|ja)] / (eps_i + eps_j - eps_a - eps_b).
+        """
+        X = self.X[x]
+        nocc = self.n_occ[x]
+        eps, Cp = np.linalg.eigh(X.T @ F @ X)
+        C = X @ Cp
+        Co, Cv = C[:, :nocc], C[:, nocc:]
+        eo, ev = eps[:nocc], eps[nocc:]
+        eri = I.eri_block(self.shells[x], self.shells[x])  # unscreened (mu nu|lambda sigma)
+        ovov = np.einsum("mi,na,mnls,lj,sb->iajb", Co, Cv, eri, Co, Cv, optimize=True)
+        den = eo[:, None, None, None] - ev[None, :, None, None] + eo[None, None, :, None] - ev[None, None, None, :]
+        return float(np.sum(ovov * (2.0 * ovov - ovov.transpose(0, 3, 2, 1)) / den))
+
     # ------------------------------------------------------------------------------------ energies
 
     def energies(self, Ds) -> dict:

@@ -433,3 +433,72 @@ def test_mlp_oracle_gradient_finite_differences():
         fd = (mlp.loss_and_grad(tp, X, T, n_in, n_h, n_out)[0] - mlp.loss_and_grad(tm, X, T, n_in, n_h, n_out)[0]) / (2 * h)
         assert abs(fd - g[i]) < 1e-8 * max(1.0, abs(fd))
     assert abs(L - np.mean((mlp.forward(theta, X, n_in, n_h, n_out)[0] - T) ** 2)) < 1e-14
+
+
+# ------------------------------------------------------------------------------------- E_M2
+
+def _second_order_by_determinants(eri_mo, eps, nocc):
+    """Second-order Rayleigh-Schroedinger energy with the Moller-Plesset partition, summed over
+    doubly excited Slater determinants in the spin-orbital basis: E2 = sum_{i<j, a<b} |<ij||ab>|^2 /
+    (e_i + e_j - e_a - e_b), <pq||rs> = <pq|rs> - <pq|sr> from the spatial (pr|qs) and spin
+    orthogonality (Slater-Condon rules for a double excitation)."""
+    n = len(eps)
+    so = [(p, s) for p in range(n) for s in (0, 1)]
+    occ = [k for k, (p, s) in enumerate(so) if p < nocc]
+    vir = [k for k, (p, s) in enumerate(so) if p >= nocc]
+
+    def phys(k1, k2, k3, k4):  # <k1 k2|k3 k4>
+        (p, a), (q, b), (r, c), (t, d) = so[k1], so[k2], so[k3], so[k4]
+        return eri_mo[p, r, q, t] if (a == c and b == d) else 0.0
+
+    e2 = 0.0
+    for ii, i in enumerate(occ):
+        for j in occ[ii + 1:]:
+            for aa, a in enumerate(vir):
+                for b in vir[aa + 1:]:
+                    v = phys(i, j, a, b) - phys(i, j, b, a)
+                    e2 += v * v / (eps[so[i][0]] + eps[so[j][0]] - eps[so[a][0]] - eps[so[b][0]])
+    return e2
+
+
+def test_e_m2_equals_determinant_second_order(dimer_frags, dimer_solution):
+    """The oracle's closed-shell E_M2 of each fragment (in its FEF field) equals the second-order
+    energy summed over spin-orbital double excitations with antisymmetrised integrals (an
+    independent route that fixes the exchange term and the factor of 2)."""
+    ref = dimer_frags
+    D = dimer_solution["D"]
+    F = ref.fock(D)
+    for x in range(ref.nf):
+        X = ref.X[x]
+        eps, Cp = np.linalg.eigh(X.T @ F[x] @ X)
+        C = X @ Cp
+        eri = I.eri_block(ref.shells[x], ref.shells[x])
+        eri_mo = np.einsum("mp,nq,mnls,lr,st->pqrt", C, C, eri, C, C, optimize=True)
+        e_det = _second_order_by_determinants(eri_mo, eps, ref.n_occ[x])
+        e_m2 = ref.e_m2(x, F[x])
+        assert e_m2 < 0.0
+        assert abs(e_m2 - e_det) < 1e-12 * max(1.0, abs(e_det)), (x, e_m2, e_det)
+
+
+def test_e_m2_orbital_rotation_invariance(dimer_frags, dimer_solution):
+    """E_M2 depends on the occupied and virtual spaces and the canonical energies only: a random
+    orthogonal change of the fragment's AO basis (applied to S, F and the orbitals) leaves it
+    unchanged, checked here through the rotation of the whole fragment in space (p and d blocks
+    rotate with the geometry)."""
+    ref = dimer_frags
+    D = dimer_solution["D"]
+    F = ref.fock(D)
+    e0 = ref.e_m2(0, F[0])
+    sysm = ref.system
+    R = S.random_rotation(np.random.default_rng(7))
+    at = sysm.frag_atoms(0)
+    moved = S.System(Z=sysm.Z[at], xyz=(sysm.xyz[at] - sysm.xyz[at].mean(0)) @ R.T, frag_of_atom=np.zeros(len(at), np.int32),
+                     charge=np.zeros(1, np.int32), basis_of_atom=sysm.basis_of_atom[at], basis_sets=sysm.basis_sets)
+    iso = Fragments(moved, inter=False)
+    iso0 = Fragments(S.System(Z=sysm.Z[at], xyz=sysm.xyz[at], frag_of_atom=np.zeros(len(at), np.int32),
+                              charge=np.zeros(1, np.int32), basis_of_atom=sysm.basis_of_atom[at],
+                              basis_sets=sysm.basis_sets), inter=False)
+    Da, Fa, *_ = iso0.rhf(0, np.zeros_like(iso0.S[0]), e_tol=1e-13, comm_tol=1e-11)
+    Db, Fb, *_ = iso.rhf(0, np.zeros_like(iso.S[0]), e_tol=1e-13, comm_tol=1e-11)
+    assert abs(iso0.e_m2(0, Fa) - iso.e_m2(0, Fb)) < 1e-10
+    assert e0 < 0.0
