@@ -171,6 +171,17 @@ fef_status fef_noninteracting_scf(fef_ctx* ctx);
  * Any output pointer may be NULL; E_frag/E_int are [n_frag] host arrays. */
 fef_status fef_energies(fef_ctx* ctx, double* E_frag, double* E_total, double* E_int);
 
+/* Monomer second-order energy of the FEF cluster perturbation theory (Eq. EM2, with the first-order
+ * monomer doubles of Eq. monDoubles): with each fragment's canonical FEF orbitals (F^x C = S^x C eps
+ * of the current densities' Fock matrices, canonical orthogonalisation, aufbau) the zeroth-order
+ * monomer effective Hamiltonian is the diagonal Fock operator and the doubles are driven by the
+ * fragment's own two-electron interaction (the environment field is one-body), so
+ *   E_M2^x = sum_{ij occ, ab virt} (ia|jb) [2 (ia|jb) - (ib|ja)] / (eps_i + eps_j - eps_a - eps_b).
+ * E_m2[n_frag] (host, nullable) per fragment, *E_m2_total (nullable) their sum.  Fragments up to 64
+ * AOs.  The fragments' integrals are recomputed into temporary device memory for the call.
+ * Errors: ARG (no densities, a fragment above 64 AOs), CUDA. */
+fef_status fef_energy_m2(fef_ctx* ctx, double* E_m2, double* E_m2_total);
+
 /* Checkpoint / resume: copy the current packed densities out, or replace them. */
 fef_status fef_get_densities(const fef_ctx* ctx, double* D_out, int on_device);
 fef_status fef_set_densities(fef_ctx* ctx, const double* D_in, int on_device);

@@ -32,7 +32,7 @@ EXPORTED = ["fef_default_options", "fef_create", "fef_ao_layout", "fef_build_foc
             "fef_mlp_params", "fef_mlp_set_scaling", "fef_mlp_loss_grad", "fef_mlp_train", "fef_mlp_predict",
             "fef_mlp_last_error", "fef_learned_features", "fef_set_warm_start",
             "fef_noninteracting_scf", "fef_get_tile_plan", "fef_set_tile_plan", "fef_autotune",
-            "fef_fragment_status"]
+            "fef_fragment_status", "fef_energy_m2"]
 
 
 class FefError(RuntimeError):
@@ -119,6 +119,7 @@ def lib():
     L.fef_fragment_rhf_noalloc.argtypes = [ctypes.c_int32, ip, ip, dp, vp, vp, vp, vp, vp, vp, vp, vp,
                                            ctypes.POINTER(fef_options), vp]
     L.fef_fragment_status.argtypes = [vp, ip, dp, dp]
+    L.fef_energy_m2.argtypes = [vp, dp, dp]
     L.fef_get_tile_plan.argtypes = [vp, ctypes.c_int32, ctypes.POINTER(fef_tile_plan)]
     L.fef_set_tile_plan.argtypes = [vp, ctypes.c_int32, ctypes.POINTER(fef_tile_plan)]
     L.fef_autotune.argtypes = [vp, ctypes.c_int32, ctypes.c_int32, ctypes.c_double, ctypes.POINTER(fef_tile_plan)]
@@ -307,6 +308,14 @@ def fef_fragment_status(ctx: Context) -> dict:
     _check(lib().fef_fragment_status(ctx.ptr, _ptr(it, ctypes.c_int32), _ptr(gap, ctypes.c_double),
                                      _ptr(e, ctypes.c_double)), ctx.ptr)
     return dict(micro_iters=it, homo_lumo_gap=gap, E_scf=e)
+
+
+def fef_energy_m2(ctx: Context):
+    """(E_M2 per fragment, their sum): monomer second-order energies on the FEF canonical orbitals."""
+    e = np.zeros(ctx.n_frag)
+    tot = ctypes.c_double(0.0)
+    _check(lib().fef_energy_m2(ctx.ptr, _ptr(e, ctypes.c_double), ctypes.byref(tot)), ctx.ptr)
+    return e, tot.value
 
 
 def _plan_dict(p: fef_tile_plan) -> dict:

@@ -765,6 +765,10 @@ extern "C" fef_status fef_create(const fef_geometry* g, const fef_basis* bs, con
         d.n_pairs = c->n_pairs;
         c->h_pair_x = pair_x;
         c->h_pair_y = pair_y;
+        c->h_frag_sp0 = frag_sp0;
+        c->h_sp_a = sp_a;
+        c->h_sp_b = sp_b;
+        c->h_sh_l = sh_l;
         d.pair_x = b->upload(pair_x, s, "pairs");
         d.pair_y = b->upload(pair_y, s, "pairs");
         d.frag_nbr0 = b->upload(nbr0, s, "pairs");
@@ -1378,6 +1382,52 @@ extern "C" fef_status fef_fragment_status(const fef_ctx* cc, int32_t* micro_iter
         ck(cudaMemcpyAsync(homo_lumo_gap, b->gap, sizeof(double) * nf, cudaMemcpyDeviceToHost, c->stream), "status");
     if (E_scf) ck(cudaMemcpyAsync(E_scf, b->E_scf, sizeof(double) * nf, cudaMemcpyDeviceToHost, c->stream), "status");
     ck(cudaStreamSynchronize(c->stream), "status");
+    return FEF_OK;
+    FEF_API_END(c)
+}
+
+extern "C" fef_status fef_energy_m2(fef_ctx* c, double* E_m2, double* E_m2_total)
+{
+    if (!c) return FEF_ERR_ARG;
+    FEF_API_BEGIN
+    require(c->have_density, FEF_ERR_ARG, "fef_energy_m2: no densities");
+    require(c->max_nao <= kM2MaxN, FEF_ERR_ARG,
+            "fef_energy_m2: fragments above " + std::to_string(kM2MaxN) + " AOs are not supported");
+    Buffers* b = c->buf;
+    const Dev& d = c->dev;
+    cudaStream_t s = c->stream;
+    const int nf = c->n_frag;
+    if (!c->energies_valid) build_fock_internal(c, kBuildFP64);  // F of the current densities
+    // intra-fragment (mu nu|lambda sigma), pair-packed, recomputed into a temporary
+    std::vector<int4> tasks;
+    for (int x = 0; x < nf; ++x)
+        for (int s1 = c->h_frag_sp0[x]; s1 < c->h_frag_sp0[x + 1]; ++s1)
+            for (int s2 = s1; s2 < c->h_frag_sp0[x + 1]; ++s2) {
+                const int la = c->h_sh_l[c->h_sp_a[s1]], lb = c->h_sh_l[c->h_sp_b[s1]];
+                for (int k = 0; k < ncart(la) * ncart(lb); ++k) tasks.push_back(make_int4(x, s1, s2, k));
+            }
+    std::vector<int64_t> off(nf + 1, 0);
+    for (int x = 0; x < nf; ++x) off[x + 1] = off[x] + energy_m2_workspace(c->nao[x], c->nocc[x], c->nmo[x]);
+    double* U = b->alloc<double>(std::max<int64_t>(c->coff_total, 1), "E_M2 integrals");
+    int4* tasks_d = b->upload(tasks, s, "E_M2 tasks");
+    int64_t* off_d = b->upload(off, s, "E_M2 offsets");
+    double* ws = b->alloc<double>(std::max<int64_t>(off[nf], 1), "E_M2 workspace");
+    double* E_d = b->alloc<double>(nf, "E_M2");
+    std::vector<double> E(nf, 0.0);
+    cudaError_t e = launch_intra_eri(d, tasks_d, (int)tasks.size(), U, s);
+    if (e == cudaSuccess) e = launch_energy_m2(d, b->F, b->X, b->nmo, U, off_d, ws, E_d, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(E.data(), E_d, sizeof(double) * nf, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    b->release(U);
+    b->release(tasks_d);
+    b->release(off_d);
+    b->release(ws);
+    b->release(E_d);
+    ck(e, "fef_energy_m2");
+    double tot = 0.0;
+    for (double v : E) tot += v;
+    if (E_m2) std::copy(E.begin(), E.end(), E_m2);
+    if (E_m2_total) *E_m2_total = tot;
     return FEF_OK;
     FEF_API_END(c)
 }

@@ -116,6 +116,7 @@ struct fef_ctx {
     std::vector<int> nao, nmo, nocc;
     std::vector<int64_t> moff;
     std::vector<int> h_pair_x, h_pair_y;
+    std::vector<int> h_frag_sp0, h_sp_a, h_sp_b, h_sh_l;  // shell pairs (intra-ERI tasks of E_M2)
     fef::Dev dev{};
     fef::Buffers* buf = nullptr;
     // counters
@@ -261,6 +262,13 @@ struct ScfArgs {
     int n_big;              // (0: none; then list is null or holds every fragment)
 };
 cudaError_t launch_fragment_scf(const Dev& d, const ScfArgs& a, int max_n, cudaStream_t s);
+
+// E_M2 (Eq. EM2) per fragment, one block per fragment with at most kM2MaxN AOs: canonical orbitals of
+// F (packed), (ia|jb) by four quarter-transforms of the pair-packed U, closed-shell second-order sum.
+constexpr int kM2MaxN = 64;
+int64_t energy_m2_workspace(int n, int nocc, int nmo);  // doubles per fragment
+cudaError_t launch_energy_m2(const Dev& d, const double* F, const double* X, const int* nmo, const double* U,
+                             const int64_t* ws_off, double* ws, double* E, cudaStream_t s);
 
 // E_frag[x] = E_int[x] + (trV[x] + sum_y tr(D^y V^x) + trJ[x] + sum_y E_nn(x,y)) / 2, E_tot = sum E_frag
 cudaError_t launch_energies(const Dev& d, const double* E_int, const double* trV, const double* trJ,

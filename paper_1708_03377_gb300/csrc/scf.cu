@@ -193,6 +193,134 @@ __device__ void jacobi_eigh(const Team<CS>& t, double* A, double* V, int m, int 
     }
 }
 
+
+// ------------------------------------------------------------------------------------------ E_M2
+// Monomer second-order energy (Eq. EM2 with the first-order doubles of Eq. monDoubles) of each
+// fragment on its canonical FEF orbitals: F C = S C eps (canonical orthogonaliser X, cyclic Jacobi,
+// ascending order, aufbau), (ia|jb) = sum C_mu i C_nu a C_lambda j C_sigma b (mu nu|lambda sigma) by
+// four quarter-transforms of the pair-packed U (pq = pair(mu <= nu)), then
+//   E_M2^x = sum_{ijab} (ia|jb) [2 (ia|jb) - (ib|ja)] / (eps_i + eps_j - eps_a - eps_b).
+// One block per fragment; workspace per fragment (global): A, V, C (n x n each), T1 [nocc][n][np],
+// T2 [nocc][nvir][np], T3 [nocc][nvir][nocc][n], T4 [nocc][nvir][nocc][nvir].
+__device__ __forceinline__ int m2_pair(int i, int j, int n)  // i <= j
+{
+    return i * n - i * (i - 1) / 2 + (j - i);
+}
+
+__global__ void __launch_bounds__(256) k_energy_m2(Dev d, const double* __restrict__ Fp, const double* __restrict__ Xp,
+                                                   const int* __restrict__ nmo_, const double* __restrict__ Up,
+                                                   const int64_t* __restrict__ ws_off, double* ws_all, double* E_out)
+{
+    const int x = blockIdx.x;
+    const int n = d.frag_nao[x], m = nmo_[x], nocc = d.frag_nocc[x], nv = m - nocc;
+    const int np = n * (n + 1) / 2;
+    const Team<1> t{0};
+    __shared__ JacobiScratch js;
+    __shared__ double red[40];
+    __shared__ int ord[kM2MaxN];
+    __shared__ double eps[kM2MaxN];
+    const int64_t mo = d.frag_moff[x];
+    const double* F = Fp + mo;
+    const double* X = Xp + mo;
+    const double* U = Up + d.frag_coff[x];
+    double* A = ws_all + ws_off[x];
+    double* V = A + n * n;
+    double* C = V + n * n;
+    double* T1 = C + n * n;
+    double* T2 = T1 + (int64_t)nocc * n * np;
+    double* T3 = T2 + (int64_t)nocc * nv * np;
+    double* T4 = T3 + (int64_t)nocc * nv * nocc * n;
+    if (n > kM2MaxN || nocc <= 0 || nv <= 0) {
+        if (threadIdx.x == 0) E_out[x] = 0.0;
+        return;
+    }
+    mm(t, V, F, X, n, n, m, n, false);  // V = F X   (n x m)
+    mm(t, A, X, V, m, n, m, n, true);   // A = X^T F X (m x m)
+    jacobi_eigh(t, A, V, m, n, &js, red);
+    if (threadIdx.x == 0) {  // ascending orbital energies, ties by index
+        for (int k = 0; k < m; ++k) ord[k] = k;
+        for (int k = 0; k < m; ++k) {
+            int best = k;
+            for (int j = k + 1; j < m; ++j) {
+                const double ej = A[ord[j] * n + ord[j]], eb = A[ord[best] * n + ord[best]];
+                if (ej < eb || (ej == eb && ord[j] < ord[best])) best = j;
+            }
+            const int tmp = ord[k]; ord[k] = ord[best]; ord[best] = tmp;
+            eps[k] = A[ord[k] * n + ord[k]];
+        }
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < n * m; e += blockDim.x) {  // C = X V, columns in ascending order
+        const int mu = e / m, k = e % m;
+        double sum = 0.0;
+        for (int l = 0; l < m; ++l) sum = fma(X[mu * n + l], V[l * n + ord[k]], sum);
+        C[mu * n + k] = sum;
+    }
+    __syncthreads();
+    // T1[i][nu][rs] = sum_mu C[mu][i] U[pair(mu,nu)][rs]
+    for (int64_t e = threadIdx.x; e < (int64_t)nocc * n * np; e += blockDim.x) {
+        const int rs = (int)(e % np), nu = (int)((e / np) % n), i = (int)(e / ((int64_t)n * np));
+        double sum = 0.0;
+        for (int mu = 0; mu < n; ++mu)
+            sum = fma(C[mu * n + i], U[(int64_t)(mu <= nu ? m2_pair(mu, nu, n) : m2_pair(nu, mu, n)) * np + rs], sum);
+        T1[e] = sum;
+    }
+    __syncthreads();
+    // T2[i][a][rs] = sum_nu C[nu][nocc + a] T1[i][nu][rs]
+    for (int64_t e = threadIdx.x; e < (int64_t)nocc * nv * np; e += blockDim.x) {
+        const int rs = (int)(e % np), a = (int)((e / np) % nv), i = (int)(e / ((int64_t)nv * np));
+        double sum = 0.0;
+        for (int nu = 0; nu < n; ++nu) sum = fma(C[nu * n + nocc + a], T1[((int64_t)i * n + nu) * np + rs], sum);
+        T2[e] = sum;
+    }
+    __syncthreads();
+    // T3[i][a][j][s] = sum_l C[l][j] T2[i][a][pair(l,s)]
+    for (int64_t e = threadIdx.x; e < (int64_t)nocc * nv * nocc * n; e += blockDim.x) {
+        const int sg = (int)(e % n), j = (int)((e / n) % nocc), ia = (int)(e / ((int64_t)nocc * n));
+        double sum = 0.0;
+        for (int l = 0; l < n; ++l)
+            sum = fma(C[l * n + j], T2[(int64_t)ia * np + (l <= sg ? m2_pair(l, sg, n) : m2_pair(sg, l, n))], sum);
+        T3[e] = sum;
+    }
+    __syncthreads();
+    // T4[i][a][j][b] = sum_s C[s][nocc + b] T3[i][a][j][s]  (= (ia|jb))
+    for (int64_t e = threadIdx.x; e < (int64_t)nocc * nv * nocc * nv; e += blockDim.x) {
+        const int b = (int)(e % nv), iaj = (int)(e / nv);
+        double sum = 0.0;
+        for (int sg = 0; sg < n; ++sg) sum = fma(C[sg * n + nocc + b], T3[(int64_t)iaj * n + sg], sum);
+        T4[e] = sum;
+    }
+    __syncthreads();
+    double part = 0.0;
+    for (int64_t e = threadIdx.x; e < (int64_t)nocc * nv * nocc * nv; e += blockDim.x) {
+        const int b = (int)(e % nv), j = (int)((e / nv) % nocc), a = (int)((e / ((int64_t)nv * nocc)) % nv);
+        const int i = (int)(e / ((int64_t)nv * nocc * nv));
+        const double iajb = T4[e];
+        const double ibja = T4[(((int64_t)i * nv + b) * nocc + j) * nv + a];
+        part += iajb * (2.0 * iajb - ibja) / (eps[i] + eps[j] - eps[nocc + a] - eps[nocc + b]);
+    }
+    const double E = team_sum(t, part, red);
+    if (threadIdx.x == 0) E_out[x] = E;
+}
+
+}  // namespace
+
+int64_t energy_m2_workspace(int n, int nocc, int nmo)
+{
+    const int64_t np = (int64_t)n * (n + 1) / 2, nv = nmo - nocc;
+    return 3 * (int64_t)n * n + (int64_t)nocc * n * np + nocc * nv * np + nocc * nv * nocc * n + nocc * nv * nocc * nv;
+}
+
+cudaError_t launch_energy_m2(const Dev& d, const double* F, const double* X, const int* nmo, const double* U,
+                             const int64_t* ws_off, double* ws, double* E, cudaStream_t s)
+{
+    if (d.n_frag <= 0) return cudaSuccess;
+    k_energy_m2<<<d.n_frag, 256, 0, s>>>(d, F, X, nmo, U, ws_off, ws, E);
+    note_launches(1);
+    return cudaGetLastError();
+}
+
+namespace {
 }  // namespace
 
 // ------------------------------------------------------------------------------------------ X = U s^{-1/2}
