@@ -182,6 +182,16 @@ fef_status fef_energies(fef_ctx* ctx, double* E_frag, double* E_total, double* E
  * Errors: ARG (no densities, a fragment above 64 AOs), CUDA. */
 fef_status fef_energy_m2(fef_ctx* ctx, double* E_m2, double* E_m2_total);
 
+/* Dimer second-order energy of the FEF cluster perturbation theory (Eq. ED2, with the first-order
+ * dimer doubles of Eq. dimDoubles), summed over the fragment pairs within the cutoff (each pair
+ * once): with the canonical FEF orbitals of both fragments the dimer doubles excite one electron on
+ * each fragment and interact directly only (no inter-fragment exchange in the product ansatz):
+ *   E_D2^{xy} = 4 sum_{i,a in x; j,b in y} (ia|jb)^2 / (eps_i + eps_j - eps_a - eps_b).
+ * E_d2_frag[n_frag] (host, nullable) = half of each fragment's pair terms, *E_d2_total (nullable) =
+ * sum over pairs.  Fragments up to 64 AOs; the pair integrals are computed into temporary device
+ * memory, in chunks of pairs.  Errors: ARG (no densities, a fragment above 64 AOs), CUDA. */
+fef_status fef_energy_d2(fef_ctx* ctx, double* E_d2_frag, double* E_d2_total);
+
 /* Checkpoint / resume: copy the current packed densities out, or replace them. */
 fef_status fef_get_densities(const fef_ctx* ctx, double* D_out, int on_device);
 fef_status fef_set_densities(fef_ctx* ctx, const double* D_in, int on_device);

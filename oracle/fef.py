@@ -251,6 +251,29 @@ class Fragments:
         den = eo[:, None, None, None] - ev[None, :, None, None] + eo[None, None, :, None] - ev[None, None, None, :]
         return float(np.sum(ovov * (2.0 * ovov - ovov.transpose(0, 3, 2, 1)) / den))
 
+    def canonical_orbitals(self, x: int, F: np.ndarray):
+        """(C, eps): canonical orbitals of F^x (F C = S C eps via the canonical orthogonaliser)."""
+        X = self.X[x]
+        eps, Cp = np.linalg.eigh(X.T @ F @ X)
+        return X @ Cp, eps
+
+    def e_d2(self, x: int, y: int, Fx: np.ndarray, Fy: np.ndarray) -> float:
+        """Dimer second-order energy of the pair (x, y) (Eq. ED2 with the first-order dimer doubles of
+        Eq. dimDoubles): one excitation on each fragment, direct interaction only (the product
+        ansatz has no inter-fragment exchange), four spin cases:
+
+            E_D2^{xy} = 4 sum_{i,a in x; j,b in y} (ia|jb)^2 / (eps_i + eps_j - eps_a - eps_b).
+        """
+        Cx, ex = self.canonical_orbitals(x, Fx)
+        Cy, ey = self.canonical_orbitals(y, Fy)
+        ox, oy = self.n_occ[x], self.n_occ[y]
+        eri = I.eri_block(self.shells[x], self.shells[y])  # unscreened (mu nu|lambda sigma), mu nu in x
+        ovov = np.einsum("mi,na,mnls,lj,sb->iajb", Cx[:, :ox], Cx[:, ox:], eri, Cy[:, :oy], Cy[:, oy:],
+                         optimize=True)
+        den = (ex[:ox, None, None, None] - ex[None, ox:, None, None] + ey[None, None, :oy, None]
+               - ey[None, None, None, oy:])
+        return float(4.0 * np.sum(ovov * ovov / den))
+
     # ------------------------------------------------------------------------------------ energies
 
     def energies(self, Ds) -> dict:

@@ -32,7 +32,7 @@ EXPORTED = ["fef_default_options", "fef_create", "fef_ao_layout", "fef_build_foc
             "fef_mlp_params", "fef_mlp_set_scaling", "fef_mlp_loss_grad", "fef_mlp_train", "fef_mlp_predict",
             "fef_mlp_last_error", "fef_learned_features", "fef_set_warm_start",
             "fef_noninteracting_scf", "fef_get_tile_plan", "fef_set_tile_plan", "fef_autotune",
-            "fef_fragment_status", "fef_energy_m2"]
+            "fef_fragment_status", "fef_energy_m2", "fef_energy_d2"]
 
 
 class FefError(RuntimeError):
@@ -120,6 +120,7 @@ def lib():
                                            ctypes.POINTER(fef_options), vp]
     L.fef_fragment_status.argtypes = [vp, ip, dp, dp]
     L.fef_energy_m2.argtypes = [vp, dp, dp]
+    L.fef_energy_d2.argtypes = [vp, dp, dp]
     L.fef_get_tile_plan.argtypes = [vp, ctypes.c_int32, ctypes.POINTER(fef_tile_plan)]
     L.fef_set_tile_plan.argtypes = [vp, ctypes.c_int32, ctypes.POINTER(fef_tile_plan)]
     L.fef_autotune.argtypes = [vp, ctypes.c_int32, ctypes.c_int32, ctypes.c_double, ctypes.POINTER(fef_tile_plan)]
@@ -315,6 +316,14 @@ def fef_energy_m2(ctx: Context):
     e = np.zeros(ctx.n_frag)
     tot = ctypes.c_double(0.0)
     _check(lib().fef_energy_m2(ctx.ptr, _ptr(e, ctypes.c_double), ctypes.byref(tot)), ctx.ptr)
+    return e, tot.value
+
+
+def fef_energy_d2(ctx: Context):
+    """(E_D2 half-shares per fragment, total over the pairs within the cutoff)."""
+    e = np.zeros(ctx.n_frag)
+    tot = ctypes.c_double(0.0)
+    _check(lib().fef_energy_d2(ctx.ptr, _ptr(e, ctypes.c_double), ctypes.byref(tot)), ctx.ptr)
     return e, tot.value
 
 

@@ -1431,3 +1431,90 @@ extern "C" fef_status fef_energy_m2(fef_ctx* c, double* E_m2, double* E_m2_total
     return FEF_OK;
     FEF_API_END(c)
 }
+
+extern "C" fef_status fef_energy_d2(fef_ctx* c, double* E_d2_frag, double* E_d2_total)
+{
+    if (!c) return FEF_ERR_ARG;
+    FEF_API_BEGIN
+    require(c->have_density, FEF_ERR_ARG, "fef_energy_d2: no densities");
+    require(c->max_nao <= kM2MaxN, FEF_ERR_ARG,
+            "fef_energy_d2: fragments above " + std::to_string(kM2MaxN) + " AOs are not supported");
+    Buffers* b = c->buf;
+    const Dev& d = c->dev;
+    cudaStream_t s = c->stream;
+    const int nf = c->n_frag;
+    if (!c->energies_valid) build_fock_internal(c, kBuildFP64);  // F of the current densities
+    int nao_total = 0;
+    for (int x = 0; x < nf; ++x) nao_total += c->nao[x];
+    double* C = b->alloc<double>(std::max<int64_t>(c->mat_total, 1), "E_D2 orbitals");
+    double* eps = b->alloc<double>(std::max(nao_total, 1), "E_D2 orbital energies");
+    double* jws = b->alloc<double>(std::max<int64_t>(2 * c->mat_total, 1), "E_D2 Jacobi workspace");
+    std::vector<double> E_pair(c->n_pairs, 0.0);
+    cudaError_t e = launch_canonical_orbitals(d, b->F, b->X, b->nmo, jws, C, eps, s);
+    // pairs in chunks that bound the integral blocks, workspaces and task lists
+    const int64_t kMaxChunkDoubles = 1ll << 27, kMaxChunkTasks = 1ll << 24;
+    std::vector<int> chunk;
+    std::vector<int64_t> woff(1, 0), toff(1, 0);
+    std::vector<int4> tasks;
+    auto flush = [&]() {
+        if (chunk.empty() || e != cudaSuccess) return;
+        const int nq = (int)chunk.size();
+        int* pair_d = b->upload(chunk, s, "E_D2 pairs");
+        int64_t* woff_d = b->upload(woff, s, "E_D2 offsets");
+        int64_t* toff_d = b->upload(toff, s, "E_D2 offsets");
+        int4* tasks_d = b->upload(tasks, s, "E_D2 tasks");
+        double* W = b->alloc<double>(std::max<int64_t>(woff.back(), 1), "E_D2 pair integrals");
+        double* T = b->alloc<double>(std::max<int64_t>(toff.back(), 1), "E_D2 workspace");
+        double* Ed = b->alloc<double>(nq, "E_D2");
+        std::vector<double> Eh(nq);
+        e = launch_pair_eri(d, tasks_d, (int)tasks.size(), pair_d, woff_d, W, s);
+        if (e == cudaSuccess) e = launch_energy_d2(d, nq, pair_d, woff_d, W, C, eps, b->nmo, toff_d, T, Ed, s);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(Eh.data(), Ed, sizeof(double) * nq, cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        for (int q = 0; q < nq; ++q) E_pair[chunk[q]] = Eh[q];
+        for (void* p : {(void*)pair_d, (void*)woff_d, (void*)toff_d, (void*)tasks_d, (void*)W, (void*)T, (void*)Ed})
+            b->release(p);
+        chunk.clear();
+        woff.assign(1, 0);
+        toff.assign(1, 0);
+        tasks.clear();
+    };
+    for (int p = 0; p < c->n_pairs && e == cudaSuccess; ++p) {
+        const int x = c->h_pair_x[p], y = c->h_pair_y[p];
+        const int nx = c->nao[x], ny = c->nao[y];
+        const int64_t wsz = ((int64_t)nx * (nx + 1) / 2) * ((int64_t)ny * (ny + 1) / 2);
+        const int64_t tsz = energy_d2_workspace(nx, c->nocc[x], c->nmo[x], ny, c->nocc[y], c->nmo[y]);
+        int64_t ntask = 0;
+        for (int s1 = c->h_frag_sp0[x]; s1 < c->h_frag_sp0[x + 1]; ++s1)
+            ntask += (int64_t)ncart(c->h_sh_l[c->h_sp_a[s1]]) * ncart(c->h_sh_l[c->h_sp_b[s1]]) *
+                     (c->h_frag_sp0[y + 1] - c->h_frag_sp0[y]);
+        if (!chunk.empty() && (woff.back() + wsz + toff.back() + tsz > kMaxChunkDoubles ||
+                               (int64_t)tasks.size() + ntask > kMaxChunkTasks))
+            flush();
+        const int q = (int)chunk.size();
+        chunk.push_back(p);
+        woff.push_back(woff.back() + wsz);
+        toff.push_back(toff.back() + tsz);
+        for (int s1 = c->h_frag_sp0[x]; s1 < c->h_frag_sp0[x + 1]; ++s1) {
+            const int nk = ncart(c->h_sh_l[c->h_sp_a[s1]]) * ncart(c->h_sh_l[c->h_sp_b[s1]]);
+            for (int s2 = c->h_frag_sp0[y]; s2 < c->h_frag_sp0[y + 1]; ++s2)
+                for (int k = 0; k < nk; ++k) tasks.push_back(make_int4(q, s1, s2, k));
+        }
+    }
+    flush();
+    b->release(C);
+    b->release(eps);
+    b->release(jws);
+    ck(e, "fef_energy_d2");
+    double tot = 0.0;
+    std::vector<double> Ef(nf, 0.0);
+    for (int p = 0; p < c->n_pairs; ++p) {
+        tot += E_pair[p];
+        Ef[c->h_pair_x[p]] += 0.5 * E_pair[p];
+        Ef[c->h_pair_y[p]] += 0.5 * E_pair[p];
+    }
+    if (E_d2_frag) std::copy(Ef.begin(), Ef.end(), E_d2_frag);
+    if (E_d2_total) *E_d2_total = tot;
+    return FEF_OK;
+    FEF_API_END(c)
+}

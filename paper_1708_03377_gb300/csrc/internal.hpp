@@ -267,6 +267,16 @@ cudaError_t launch_fragment_scf(const Dev& d, const ScfArgs& a, int max_n, cudaS
 // F (packed), (ia|jb) by four quarter-transforms of the pair-packed U, closed-shell second-order sum.
 constexpr int kM2MaxN = 64;
 int64_t energy_m2_workspace(int n, int nocc, int nmo);  // doubles per fragment
+// E_D2 (Eq. ED2): canonical orbitals (C packed at frag_moff, eps at frag_ao0; Jacobi workspace
+// 2 frag_moff), inter-fragment pair blocks W (k_pair_eri), per-pair transform and second-order sum
+cudaError_t launch_canonical_orbitals(const Dev& d, const double* F, const double* X, const int* nmo, double* ws,
+                                      double* C, double* eps, cudaStream_t s);
+cudaError_t launch_pair_eri(const Dev& d, const int4* tasks, int n_tasks, const int* pair_of, const int64_t* off,
+                            double* W, cudaStream_t s);
+int64_t energy_d2_workspace(int nx, int ox, int mx, int ny, int oy, int my);  // doubles per pair
+cudaError_t launch_energy_d2(const Dev& d, int n_pairs, const int* pair_of, const int64_t* woff, const double* W,
+                             const double* C, const double* eps, const int* nmo, const int64_t* toff, double* tws,
+                             double* E, cudaStream_t s);
 cudaError_t launch_energy_m2(const Dev& d, const double* F, const double* X, const int* nmo, const double* U,
                              const int64_t* ws_off, double* ws, double* E, cudaStream_t s);
 

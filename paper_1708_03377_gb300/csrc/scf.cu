@@ -321,6 +321,146 @@ cudaError_t launch_energy_m2(const Dev& d, const double* F, const double* X, con
 }
 
 namespace {
+
+// ------------------------------------------------------------------------------------------ E_D2
+// Canonical FEF orbitals of every fragment (n <= kM2MaxN): C (n x m, columns in ascending orbital
+// energy) as the packed n x n block at frag_moff[x], eps[m] at frag_ao0[x]; one block per fragment,
+// Jacobi workspace 2 n^2 at 2 frag_moff[x].
+__global__ void __launch_bounds__(256) k_canonical_orbitals(Dev d, const double* __restrict__ Fp,
+                                                            const double* __restrict__ Xp, const int* __restrict__ nmo_,
+                                                            double* ws, double* Cp, double* eps_out)
+{
+    const int x = blockIdx.x;
+    const int n = d.frag_nao[x], m = nmo_[x];
+    if (n > kM2MaxN) return;
+    const Team<1> t{0};
+    __shared__ JacobiScratch js;
+    __shared__ double red[40];
+    __shared__ int ord[kM2MaxN];
+    const int64_t mo = d.frag_moff[x];
+    const double* F = Fp + mo;
+    const double* X = Xp + mo;
+    double* A = ws + 2 * mo;
+    double* V = A + n * n;
+    double* C = Cp + mo;
+    mm(t, V, F, X, n, n, m, n, false);
+    mm(t, A, X, V, m, n, m, n, true);
+    jacobi_eigh(t, A, V, m, n, &js, red);
+    if (threadIdx.x == 0) {
+        for (int k = 0; k < m; ++k) ord[k] = k;
+        for (int k = 0; k < m; ++k) {
+            int best = k;
+            for (int j = k + 1; j < m; ++j) {
+                const double ej = A[ord[j] * n + ord[j]], eb = A[ord[best] * n + ord[best]];
+                if (ej < eb || (ej == eb && ord[j] < ord[best])) best = j;
+            }
+            const int tmp = ord[k]; ord[k] = ord[best]; ord[best] = tmp;
+            eps_out[d.frag_ao0[x] + k] = A[ord[k] * n + ord[k]];
+        }
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
+        const int mu = e / n, k = e % n;
+        double sum = 0.0;
+        if (k < m)
+            for (int l = 0; l < m; ++l) sum = fma(X[mu * n + l], V[l * n + ord[k]], sum);
+        C[e] = sum;
+    }
+}
+
+// Dimer second-order term of one fragment pair (Eq. ED2 with the first-order dimer doubles of
+// Eq. dimDoubles): one excitation on each fragment, direct interaction only (no inter-fragment
+// exchange in the product ansatz), four spin cases:
+//   E_D2^{xy} = 4 sum_{ia in x, jb in y} (ia|jb)^2 / (eps_i + eps_j - eps_a - eps_b),
+// (ia|jb) by four quarter-transforms of the pair block W[pair(mu,nu) in x][pair(lambda,sigma) in y].
+// One block per pair of the list; workspace per pair: T1 [nocc_x][n_x][np_y], T2 [nocc_x][nv_x][np_y],
+// T3 [ov_x][nocc_y][n_y].
+__global__ void __launch_bounds__(256) k_energy_d2(Dev d, const int* __restrict__ pair_of,
+                                                   const int64_t* __restrict__ woff, const double* __restrict__ W,
+                                                   const double* __restrict__ Cp, const double* __restrict__ eps,
+                                                   const int* __restrict__ nmo_, const int64_t* __restrict__ toff,
+                                                   double* tws, double* E_out)
+{
+    const int q = blockIdx.x;
+    const int pr = pair_of[q];
+    const int x = d.pair_x[pr], y = d.pair_y[pr];
+    const int nx = d.frag_nao[x], ny = d.frag_nao[y];
+    const int ox = d.frag_nocc[x], oy = d.frag_nocc[y];
+    const int vx = nmo_[x] - ox, vy = nmo_[y] - oy;
+    const int npy = ny * (ny + 1) / 2;
+    const Team<1> t{0};
+    __shared__ double red[40];
+    const double* Wq = W + woff[q];
+    const double* Cx = Cp + d.frag_moff[x];
+    const double* Cy = Cp + d.frag_moff[y];
+    const double* ex = eps + d.frag_ao0[x];
+    const double* ey = eps + d.frag_ao0[y];
+    double* T1 = tws + toff[q];
+    double* T2 = T1 + (int64_t)ox * nx * npy;
+    double* T3 = T2 + (int64_t)ox * vx * npy;
+    for (int64_t e = threadIdx.x; e < (int64_t)ox * nx * npy; e += blockDim.x) {
+        const int rs = (int)(e % npy), nu = (int)((e / npy) % nx), i = (int)(e / ((int64_t)nx * npy));
+        double sum = 0.0;
+        for (int mu = 0; mu < nx; ++mu) sum = fma(Cx[mu * nx + i], Wq[pair_pack(mu, nu, nx) * npy + rs], sum);
+        T1[e] = sum;
+    }
+    __syncthreads();
+    for (int64_t e = threadIdx.x; e < (int64_t)ox * vx * npy; e += blockDim.x) {
+        const int rs = (int)(e % npy), a = (int)((e / npy) % vx), i = (int)(e / ((int64_t)vx * npy));
+        double sum = 0.0;
+        for (int nu = 0; nu < nx; ++nu) sum = fma(Cx[nu * nx + ox + a], T1[((int64_t)i * nx + nu) * npy + rs], sum);
+        T2[e] = sum;
+    }
+    __syncthreads();
+    for (int64_t e = threadIdx.x; e < (int64_t)ox * vx * oy * ny; e += blockDim.x) {
+        const int sg = (int)(e % ny), j = (int)((e / ny) % oy), ia = (int)(e / ((int64_t)oy * ny));
+        double sum = 0.0;
+        for (int l = 0; l < ny; ++l) sum = fma(Cy[l * ny + j], T2[(int64_t)ia * npy + pair_pack(l, sg, ny)], sum);
+        T3[e] = sum;
+    }
+    __syncthreads();
+    double part = 0.0;
+    for (int64_t e = threadIdx.x; e < (int64_t)ox * vx * oy * vy; e += blockDim.x) {
+        const int b = (int)(e % vy), j = (int)((e / vy) % oy), a = (int)((e / ((int64_t)vy * oy)) % vx);
+        const int i = (int)(e / ((int64_t)vy * oy * vx));
+        const int64_t iaj = ((int64_t)i * vx + a) * oy + j;
+        double v = 0.0;
+        for (int sg = 0; sg < ny; ++sg) v = fma(Cy[sg * ny + oy + b], T3[iaj * ny + sg], v);
+        part += v * v / (ex[i] + ey[j] - ex[ox + a] - ey[oy + b]);
+    }
+    const double E = team_sum(t, part, red);
+    if (threadIdx.x == 0) E_out[q] = 4.0 * E;
+}
+
+}  // namespace
+
+cudaError_t launch_canonical_orbitals(const Dev& d, const double* F, const double* X, const int* nmo, double* ws,
+                                      double* C, double* eps, cudaStream_t s)
+{
+    if (d.n_frag <= 0) return cudaSuccess;
+    k_canonical_orbitals<<<d.n_frag, 256, 0, s>>>(d, F, X, nmo, ws, C, eps);
+    note_launches(1);
+    return cudaGetLastError();
+}
+
+int64_t energy_d2_workspace(int nx, int ox, int mx, int ny, int oy, int my)
+{
+    const int64_t npy = (int64_t)ny * (ny + 1) / 2, vx = mx - ox, vy = my - oy;
+    (void)vy;
+    return (int64_t)ox * nx * npy + ox * vx * npy + ox * vx * oy * ny;
+}
+
+cudaError_t launch_energy_d2(const Dev& d, int n_pairs, const int* pair_of, const int64_t* woff, const double* W,
+                             const double* C, const double* eps, const int* nmo, const int64_t* toff, double* tws,
+                             double* E, cudaStream_t s)
+{
+    if (n_pairs <= 0) return cudaSuccess;
+    k_energy_d2<<<n_pairs, 256, 0, s>>>(d, pair_of, woff, W, C, eps, nmo, toff, tws, E);
+    note_launches(1);
+    return cudaGetLastError();
+}
+
+namespace {
 }  // namespace
 
 // ------------------------------------------------------------------------------------------ X = U s^{-1/2}

@@ -506,12 +506,11 @@ cudaError_t launch_nuclear_repulsion(const Dev& d, double* e_nn_intra, double* e
 // written to the pair-packed tensor U[pq][rs] = (mu nu|lambda sigma), pq = pack(min(mu,nu),
 // max(mu,nu)), np = n(n+1)/2 rows per fragment at frag_coff (both U[pq][rs] and U[rs][pq]).  Tasks
 // are sorted by angular-momentum class so that the threads of a warp follow the same path.
-__global__ void k_intra_eri(Dev d, const int4* __restrict__ tasks, int n_tasks, double* eri)
+// (mu nu|lambda sigma) for one bra Cartesian component kb of shell pair s1 (shells a <= b) and all
+// components of shell pair s2 (c <= d), unnormalised primitives (ao_scale not applied):
+// out[ic * ncart(ld) + id].  s1 and s2 may belong to different fragments.
+__device__ void eri_bra_row(const Dev& d, const int s1, const int s2, const int kb, double* out)
 {
-    int w = blockIdx.x * blockDim.x + threadIdx.x;
-    if (w >= n_tasks) return;
-    const int4 tk = tasks[w];
-    const int x = tk.x, s1 = tk.y, s2 = tk.z, kb = tk.w;
     const int sa = d.sp_a[s1], sb = d.sp_b[s1], sc = d.sp_a[s2], sd = d.sp_b[s2];
     const int la = d.sh_l[sa], lb = d.sh_l[sb], lc = d.sh_l[sc], ld = d.sh_l[sd];
     const int nc = ncart(lc), nd = ncart(ld);
@@ -519,7 +518,6 @@ __global__ void k_intra_eri(Dev d, const int4* __restrict__ tasks, int n_tasks, 
     int ax, ay, az, bx, by, bz;
     cart_of(la, kb / ncart(lb), ax, ay, az);
     cart_of(lb, kb % ncart(lb), bx, by, bz);
-    double out[36];
     for (int k = 0; k < nc * nd; ++k) out[k] = 0.0;
     const double *A = d.atom_xyz + 3 * d.sh_atom[sa], *B = d.atom_xyz + 3 * d.sh_atom[sb];
     const double *C = d.atom_xyz + 3 * d.sh_atom[sc], *Dc = d.atom_xyz + 3 * d.sh_atom[sd];
@@ -596,6 +594,19 @@ __global__ void k_intra_eri(Dev d, const int4* __restrict__ tasks, int n_tasks, 
                     }
                 }
         }
+}
+
+__global__ void k_intra_eri(Dev d, const int4* __restrict__ tasks, int n_tasks, double* eri)
+{
+    int w = blockIdx.x * blockDim.x + threadIdx.x;
+    if (w >= n_tasks) return;
+    const int4 tk = tasks[w];
+    const int x = tk.x, s1 = tk.y, s2 = tk.z, kb = tk.w;
+    const int sa = d.sp_a[s1], sb = d.sp_b[s1], sc = d.sp_a[s2], sd = d.sp_b[s2];
+    const int lb = d.sh_l[sb];
+    const int nc = ncart(d.sh_l[sc]), nd = ncart(d.sh_l[sd]);
+    double out[36];
+    eri_bra_row(d, s1, s2, kb, out);
     const int n = d.frag_nao[x];
     const int ao0 = d.frag_ao0[x];
     const int64_t np = (int64_t)n * (n + 1) / 2;
@@ -616,6 +627,46 @@ cudaError_t launch_intra_eri(const Dev& d, const int4* tasks, int n_tasks, doubl
 {
     if (n_tasks > 0) {
         k_intra_eri<<<(n_tasks + 127) / 128, 128, 0, s>>>(d, tasks, n_tasks, eri);
+        note_launches(1);
+    }
+    return cudaGetLastError();
+}
+
+// Inter-fragment blocks for a list of fragment pairs: task (list position q, s1 in x, s2 in y, kb),
+// W_q[pq][rs] = (mu nu|lambda sigma), pq = pair(mu <= nu) over x's AOs, rs = pair(lambda <= sigma)
+// over y's AOs, at off[q] (np_x * np_y doubles per pair).
+__global__ void k_pair_eri(Dev d, const int4* __restrict__ tasks, int n_tasks, const int* __restrict__ pair_of,
+                           const int64_t* __restrict__ off, double* W)
+{
+    int w = blockIdx.x * blockDim.x + threadIdx.x;
+    if (w >= n_tasks) return;
+    const int4 tk = tasks[w];
+    const int q = tk.x, s1 = tk.y, s2 = tk.z, kb = tk.w;
+    const int pr = pair_of[q];
+    const int x = d.pair_x[pr], y = d.pair_y[pr];
+    const int sa = d.sp_a[s1], sb = d.sp_b[s1], sc = d.sp_a[s2], sd = d.sp_b[s2];
+    const int lb = d.sh_l[sb];
+    const int nc = ncart(d.sh_l[sc]), nd = ncart(d.sh_l[sd]);
+    double out[36];
+    eri_bra_row(d, s1, s2, kb, out);
+    const int nx = d.frag_nao[x], ny = d.frag_nao[y];
+    const int64_t npy = (int64_t)ny * (ny + 1) / 2;
+    const int mu = d.sh_ao[sa] + kb / ncart(lb), nu = d.sh_ao[sb] + kb % ncart(lb);
+    const double smn = d.ao_scale[d.frag_ao0[x] + mu] * d.ao_scale[d.frag_ao0[x] + nu];
+    const int64_t pq = pair_pack(mu, nu, nx);
+    double* Wq = W + off[q];
+    for (int k = 0; k < nc * nd; ++k) {
+        const int la_ = d.sh_ao[sc] + k / nd, si = d.sh_ao[sd] + k % nd;
+        Wq[pq * npy + pair_pack(la_, si, ny)] =
+            out[k] * smn * d.ao_scale[d.frag_ao0[y] + la_] * d.ao_scale[d.frag_ao0[y] + si];
+    }
+}
+
+cudaError_t launch_pair_eri(const Dev& d, const int4* tasks, int n_tasks, const int* pair_of, const int64_t* off,
+                            double* W, cudaStream_t s)
+{
+    if (n_tasks > 0) {
+        k_pair_eri<<<(n_tasks + 127) / 128, 128, 0, s>>>(d, tasks, n_tasks, pair_of, off, W);
         note_launches(1);
     }
     return cudaGetLastError();

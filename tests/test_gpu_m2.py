@@ -56,3 +56,63 @@ def test_e_m2_rejects_large_fragments():
     with pytest.raises(fef.FefError):
         fef.fef_energy_m2(ctx)
     ctx.close()
+
+
+def _check_d2(fef, system, **opt):
+    from oracle.fef import Fragments
+    ref = Fragments(system, cutoff_A=opt.get("cutoff_A"), schwarz=opt.get("schwarz", 0.0), inter=False)
+    ctx = fef.fef_create_system(system, fef.fef_default_options(e_tol=1e-10, **opt))
+    fef.fef_iterate(ctx)
+    Ef, tot = fef.fef_energy_d2(ctx)
+    D = ctx.unpack(fef.fef_get_densities(ctx))
+    n_pairs = fef.fef_stats(ctx)["n_pairs"]
+    ctx.close()
+    ref_full = Fragments(system, cutoff_A=opt.get("cutoff_A"), schwarz=opt.get("schwarz", 0.0))
+    F = ref_full.fock(D)
+    E_ref, Ef_ref = 0.0, np.zeros(ref.nf)
+    assert len(ref_full.pairs) == n_pairs
+    for x, y in ref_full.pairs:
+        e = ref.e_d2(x, y, F[x], F[y])
+        assert e < 0
+        E_ref += e
+        Ef_ref[x] += 0.5 * e
+        Ef_ref[y] += 0.5 * e
+    assert abs(tot - E_ref) < 1e-10, (tot, E_ref)
+    assert np.abs(Ef - Ef_ref).max() < 1e-10
+
+
+def test_e_d2_water_dimer():
+    _check_d2(_fef(), S.water_dimer(0))
+
+
+def test_e_d2_water_box8():
+    _check_d2(_fef(), S.water_box(8, seed=4, side=7.5), cutoff_A=6.0, schwarz=1e-12)
+
+
+def test_e_d2_d_shell_waters():
+    _check_d2(_fef(), S.mixed_snapshot(n_frag=2, seed=1, weights=(1, 0, 0, 0)), schwarz=1e-12)
+
+
+def test_e_d2_chunks_equal_copies():
+    """Eight copies of the 64-water box, translated apart beyond the cutoff, give eight times the
+    single box's E_D2: the batch's pair integrals and workspaces are processed in two chunks, the
+    single box's in one."""
+    fef = _fef()
+    box = S.water_box(64, seed=0)
+    opts = fef.fef_default_options(cutoff_A=8.0, schwarz=1e-12, precision=fef.FEF_MIXED,
+                                   exact_engine=fef.FEF_ENGINE_DF64)
+    ctx = fef.fef_create_system(box, opts)
+    fef.fef_iterate(ctx)
+    _, e1 = fef.fef_energy_d2(ctx)
+    D1 = fef.fef_get_densities(ctx)
+    ctx.close()
+    batch = S.batch([box] * 8, gap=20.0)
+    ctx = fef.fef_create_system(batch, opts)
+    fef.fef_set_densities(ctx, np.tile(D1, 8))
+    fef.fef_build_fock(ctx)
+    Ef, e8 = fef.fef_energy_d2(ctx)
+    assert fef.fef_stats(ctx)["n_pairs"] == 8 * 1023
+    ctx.close()
+    assert e1 < 0
+    assert abs(e8 - 8 * e1) < 1e-9 * abs(e8), (e8, 8 * e1)
+    assert np.abs(Ef.reshape(8, 64) - Ef[:64]).max() < 1e-11
