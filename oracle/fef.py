@@ -25,6 +25,8 @@ notes of this repository.
 """
 from __future__ import annotations
 
+import math
+
 import numpy as np
 
 from synth.systems import ANGSTROM_PER_BOHR, frag_n_occ
@@ -84,7 +86,8 @@ class Fragments:
     schwarz: shell quartets with Q_ab Q_cd < schwarz are dropped (0 keeps all).
     """
 
-    def __init__(self, system, cutoff_A: float | None = None, schwarz: float = 0.0, inter: bool = True):
+    def __init__(self, system, cutoff_A: float | None = None, schwarz: float = 0.0, inter: bool = True,
+                 far_field: bool = False):
         self.system = system
         self.nf = system.n_frag
         self.schwarz_tau = schwarz
@@ -104,6 +107,22 @@ class Fragments:
         self.eri_intra = [I.eri_block(s, s, Q, Q, schwarz) if schwarz > 0 else I.eri_block(s, s)
                           for s, Q in zip(self.shells, self.Q)]
         self.pairs = self.neighbour_pairs(cutoff_A)
+        # far field: fragment pairs beyond the cutoff interact through the multipoles (charge, dipole,
+        # second moments) of each fragment's nuclei and electrons about its nuclear-charge centroid
+        self.far_field = far_field
+        near = set(self.pairs)
+        self.far_pairs = [(x, y) for x in range(self.nf) for y in range(x + 1, self.nf)
+                          if far_field and (x, y) not in near]
+        self.centre = [(self.Zn[x][:, None] * self.Rn[x]).sum(0) / self.Zn[x].sum() for x in range(self.nf)]
+        if far_field:
+            self.M = [self.shells[x].moments(self.centre[x]) for x in range(self.nf)]
+            self.Mnuc = []
+            for x in range(self.nf):
+                r = self.Rn[x] - self.centre[x]
+                z = self.Zn[x]
+                self.Mnuc.append(np.array([z.sum(), *(z @ r),
+                                           z @ (r[:, 0] * r[:, 0]), z @ (r[:, 0] * r[:, 1]), z @ (r[:, 0] * r[:, 2]),
+                                           z @ (r[:, 1] * r[:, 1]), z @ (r[:, 1] * r[:, 2]), z @ (r[:, 2] * r[:, 2])]))
         self.nbr = [[] for _ in range(self.nf)]
         for x, y in self.pairs:
             self.nbr[x].append(y)
@@ -149,8 +168,12 @@ class Fragments:
         return coulomb(e, D) - 0.5 * exchange(e, D)
 
     def omega(self, Ds) -> list:
-        """omega_x = sum_{y in N(x)} (V^y + J[D^y]) for every fragment x."""
+        """omega_x = sum_{y in N(x)} (V^y + J[D^y]) for every fragment x (plus the far-field
+        multipole terms of the fragments beyond the cutoff when far_field is set)."""
         om = [np.zeros((n, n)) for n in self.n_ao]
+        if self.far_field:
+            om_far, _ = self.far_terms(Ds)
+            om = [o.copy() for o in om_far]
         for x, y in self.pairs:
             e = self.eri[(x, y)]
             nx, ny = self.n_ao[x], self.n_ao[y]
@@ -158,6 +181,65 @@ class Fragments:
             om[x] += self.V[(x, y)] + (M @ Ds[y].ravel()).reshape(nx, nx)
             om[y] += self.V[(y, x)] + (M.T @ Ds[x].ravel()).reshape(ny, ny)
         return om
+
+    # ------------------------------------------------------------------------------------ far field
+
+    def multipoles(self, x: int, D: np.ndarray):
+        """(q, mu[3], M2[3x3]) of fragment x's nuclei and electrons about its centroid."""
+        m = self.Mnuc[x] - np.einsum("kmn,mn->k", self.M[x], D)
+        M2 = np.array([[m[4], m[5], m[6]], [m[5], m[7], m[8]], [m[6], m[8], m[9]]])
+        return m[0], m[1:4], M2
+
+    @staticmethod
+    def interaction_tensors(R):
+        """Cartesian derivatives of 1/|R| up to fourth order: T0, T1[a], T2[a,b], T3[a,b,c], T4[a,b,c,d]."""
+        r2 = float(R @ R)
+        r = math.sqrt(r2)
+        d = np.eye(3)
+        T0 = 1.0 / r
+        T1 = -R / r ** 3
+        T2 = (3.0 * np.einsum("a,b->ab", R, R) - r2 * d) / r ** 5
+        T3 = (-15.0 * np.einsum("a,b,c->abc", R, R, R) / r ** 7
+              + 3.0 * (np.einsum("a,bc->abc", R, d) + np.einsum("b,ac->abc", R, d) + np.einsum("c,ab->abc", R, d))
+              / r ** 5)
+        RR = np.einsum("a,b->ab", R, R)
+        T4 = (105.0 * np.einsum("ab,cd->abcd", RR, RR) / r ** 9
+              - 15.0 * (np.einsum("ab,cd->abcd", RR, d) + np.einsum("ac,bd->abcd", RR, d)
+                        + np.einsum("ad,bc->abcd", RR, d) + np.einsum("bc,ad->abcd", RR, d)
+                        + np.einsum("bd,ac->abcd", RR, d) + np.einsum("cd,ab->abcd", RR, d)) / r ** 7
+              + 3.0 * (np.einsum("ab,cd->abcd", d, d) + np.einsum("ac,bd->abcd", d, d)
+                       + np.einsum("ad,bc->abcd", d, d)) / r ** 5)
+        return T0, T1, T2, T3, T4
+
+    def far_potential(self, x: int, y: int, Dy: np.ndarray):
+        """(phi, grad phi[3], hess phi[3x3]) at x's centroid of y's multipole expansion:
+        phi(r) = q T - mu_a T_a + (1/2) M2_ab T_ab at R = r - c_y (derivatives of 1/|R|)."""
+        q, mu, M2 = self.multipoles(y, Dy)
+        _, T1, T2, T3, T4 = self.interaction_tensors(self.centre[x] - self.centre[y])
+        T0 = 1.0 / np.linalg.norm(self.centre[x] - self.centre[y])
+        phi = q * T0 - mu @ T1 + 0.5 * np.einsum("ab,ab->", M2, T2)
+        g = q * T1 - np.einsum("a,ac->c", mu, T2) + 0.5 * np.einsum("ab,abc->c", M2, T3)
+        H = q * T2 - np.einsum("a,acd->cd", mu, T3) + 0.5 * np.einsum("ab,abcd->cd", M2, T4)
+        return phi, g, H
+
+    def far_terms(self, Ds):
+        """(omega_far per fragment, E_far per far pair): the Taylor expansion of y's potential about
+        x's centroid to second order against x's moments,
+        E_xy = q_x phi + mu_x . grad phi + (1/2) M2_x : hess phi,
+        and its density derivative for x, -(phi S + grad phi . <r> + (1/2) hess phi : <r r>)."""
+        om = [np.zeros((n, n)) for n in self.n_ao]
+        E = {}
+        for x, y in self.far_pairs:
+            for a, b in ((x, y), (y, x)):
+                phi, g, H = self.far_potential(a, b, Ds[b])
+                M = self.M[a]
+                H6 = np.array([H[0, 0], H[0, 1], H[0, 2], H[1, 1], H[1, 2], H[2, 2]])
+                w6 = np.array([1.0, 2.0, 2.0, 1.0, 2.0, 1.0])  # off-diagonal second moments appear twice
+                om[a] -= phi * M[0] + np.einsum("c,cmn->mn", g, M[1:4]) + 0.5 * np.einsum("k,kmn->mn", w6 * H6, M[4:10])
+                if a == x:
+                    q, mu, M2 = self.multipoles(x, Ds[x])
+                    E[(x, y)] = q * phi + mu @ g + 0.5 * np.einsum("cd,cd->", M2, H)
+        return om, E
 
     def fock(self, Ds) -> list:
         """F^x = h^x + G[D^x] + omega_x for every fragment."""
@@ -294,6 +376,9 @@ class Fragments:
             Jxy = coulomb(self.eri[(x, y)], Ds[y])
             E_pair[(x, y)] = (np.sum(Ds[x] * self.V[(x, y)]) + np.sum(Ds[y] * self.V[(y, x)]) +
                               np.sum(Ds[x] * Jxy) + self.E_nn[(x, y)])
+        if self.far_field:
+            _, E_far = self.far_terms(Ds)
+            E_pair.update(E_far)
         E_x = E_int.copy()
         for (x, y), e in E_pair.items():
             E_x[x] += 0.5 * e

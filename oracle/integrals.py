@@ -60,6 +60,7 @@ def lib():
         L.or_kinetic.argtypes = [P, dp]
         L.or_nuclear.argtypes = [P, ctypes.c_int, dp, dp, dp]
         L.or_schwarz.argtypes = [P, dp]
+        L.or_moments.argtypes = [P, dp, dp]
         L.or_eri_block.argtypes = [P, P, dp, dp, ctypes.c_double, dp]
         L.or_count_quartets.argtypes = [P, P, dp, dp, ctypes.c_double]
         L.or_count_quartets.restype = ctypes.c_longlong
@@ -127,6 +128,14 @@ class ShellSet:
         z = np.ascontiguousarray(np.asarray(charges_Z, np.float64))
         ref, _keep = self._struct()
         lib().or_nuclear(ref, int(z.shape[0]), _dptr(c), _dptr(z), _dptr(out))
+        return out
+
+    def moments(self, centre_bohr) -> np.ndarray:
+        """M[k] = <mu|(r - c)^k|nu>, k = 1, x, y, z, xx, xy, xz, yy, yz, zz (shape (10, n, n))."""
+        out = np.zeros((10, self.n_ao, self.n_ao))
+        c = np.ascontiguousarray(np.asarray(centre_bohr, np.float64).reshape(3))
+        ref, _keep = self._struct()
+        lib().or_moments(ref, _dptr(c), _dptr(out))
         return out
 
     def schwarz(self) -> np.ndarray:

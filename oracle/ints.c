@@ -171,6 +171,49 @@ static void one_electron_st(const or_shells* s, double* Sout, double* Tout)
         }
 }
 
+/* Cartesian moment integrals about the point c: out[k][mu][nu] = <mu| (r - c)^k |nu> for k = 1, x, y, z,
+ * xx, xy, xz, yy, yz, zz.  In 1D, (x - c) x_B^j = x_B^{j+1} + (B - c) x_B^j, so every moment is a
+ * combination of overlaps with the ket's power raised by up to 2. */
+void or_moments(const or_shells* s, const double* c, double* out)
+{
+    int n = s->n_ao;
+    memset(out, 0, sizeof(double) * 10 * n * n);
+    for (int sa = 0; sa < s->n_sh; ++sa)
+        for (int sb = 0; sb < s->n_sh; ++sb) {
+            int la = s->l[sa], lb = s->l[sb];
+            const double* A = s->xyz + 3 * sa;
+            const double* B = s->xyz + 3 * sb;
+            for (int ka = 0; ka < s->np[sa]; ++ka)
+                for (int kb = 0; kb < s->np[sb]; ++kb) {
+                    double a = s->exps[s->p0[sa] + ka], b = s->exps[s->p0[sb] + kb];
+                    double cc = s->coef[s->p0[sa] + ka] * s->coef[s->p0[sb] + kb];
+                    double S1[3][8][8];
+                    for (int d = 0; d < 3; ++d) overlap_1d(la, lb + 2, a, b, A[d], B[d], S1[d]);
+                    for (int ia = 0; ia < ncart(la); ++ia)
+                        for (int ib = 0; ib < ncart(lb); ++ib) {
+                            int ca[3], cb[3];
+                            cart_of(la, ia, ca);
+                            cart_of(lb, ib, cb);
+                            double m[3][3]; /* m[d][k]: 1D moment of order k in direction d */
+                            for (int d = 0; d < 3; ++d) {
+                                int i = ca[d], j = cb[d];
+                                double bc = B[d] - c[d];
+                                m[d][0] = S1[d][i][j];
+                                m[d][1] = S1[d][i][j + 1] + bc * S1[d][i][j];
+                                m[d][2] = S1[d][i][j + 2] + 2.0 * bc * S1[d][i][j + 1] + bc * bc * S1[d][i][j];
+                            }
+                            const int kk[10][3] = {{0, 0, 0}, {1, 0, 0}, {0, 1, 0}, {0, 0, 1}, {2, 0, 0},
+                                                   {1, 1, 0}, {1, 0, 1}, {0, 2, 0}, {0, 1, 1}, {0, 0, 2}};
+                            int mu = s->ao0[sa] + ia, nu = s->ao0[sb] + ib;
+                            double sc = cc * s->ao_scale[mu] * s->ao_scale[nu];
+                            for (int k = 0; k < 10; ++k)
+                                out[(size_t)k * n * n + mu * n + nu] +=
+                                    sc * m[0][kk[k][0]] * m[1][kk[k][1]] * m[2][kk[k][2]];
+                        }
+                }
+        }
+}
+
 void or_overlap(const or_shells* s, double* S) { one_electron_st(s, S, NULL); }
 void or_kinetic(const or_shells* s, double* T) { one_electron_st(s, NULL, T); }
 
