@@ -113,11 +113,16 @@ typedef struct {
                                 FEF_ENGINE_DF64 = float-float arithmetic on the FP32 pipes (48-bit
                                 significand, ~1e-14 relative; s/p Hermite classes, d-shell classes
                                 stay FP64) */
+    int32_t far_field;       /* 1: fragment pairs beyond cutoff_A (> 0) still interact, through the
+                                multipoles (charge, dipole, second moments) of each fragment's nuclei and
+                                electrons about its nuclear-charge centroid, y's potential Taylor-expanded
+                                to second order about x's centroid (omega_x and the pair energies gain these
+                                terms; the truncation error falls as R^-5); 0 (default): the plain cutoff */
 } fef_options;
 
 /* Fill *opt with the defaults: FP64, no cutoff, schwarz 1e-12, e_tol 1e-8, micro_e_tol 1e-11,
- * micro_comm_tol 1e-9, max_macro 100, max_micro 200, diis_size 8, superposition start, no graph,
- * mixed_switch 1e-6, use_graph 1, exact_engine FEF_ENGINE_FP64. */
+ * micro_comm_tol 1e-9, max_macro 100, max_micro 200, diis_size 8, superposition start,
+ * mixed_switch 1e-6, use_graph 1, exact_engine FEF_ENGINE_FP64, far_field 0. */
 void fef_default_options(fef_options* opt);
 
 /* Build a context: validate and copy the inputs, then on the device normalise the basis, build
@@ -138,7 +143,8 @@ fef_status fef_ao_layout(const fef_ctx* ctx, int32_t* n_ao_per_frag, int64_t* of
  *   F^x = h^x + G[D^x] + sum_{y in N(x)} (V^y + J[D^y])   for every fragment x.
  * D: packed densities to build from (becomes the context's current density), or NULL to use the
  * current densities.  F_out: packed output, or NULL.  on_device: 1 if D/F_out are device pointers.
- * The inter-fragment J is the fused McMurchie-Davidson J-engine: no ERI tensor is formed.
+ * The inter-fragment J is the fused McMurchie-Davidson J-engine: no ERI tensor is formed.  With
+ * opt.far_field, omega_x also holds the multipole field of the fragments beyond the cutoff.
  * FP64 mode: the full FP64 J-engine.  MIXED: J[D^y] = J[D_ref] + J_fp32[D^y - D_ref] relative to the
  * last FP64 build of this context; without one the build is FP64 and becomes the reference.
  * Errors: ARG, CUDA, NUMERIC. */
@@ -168,7 +174,8 @@ fef_status fef_noninteracting_scf(fef_ctx* ctx);
  *   E_int[x] = tr[D^x (2 h^x + G[D^x])]/2 + sum_{A<B in x} Z_A Z_B / R_AB
  *   E_xy     = tr[D^x V^y] + tr[D^y V^x] + tr[D^x J[D^y]] + sum_{A in x, B in y} Z_A Z_B / R_AB
  *   E_total  = sum_x E_int[x] + sum_{x<y in N} E_xy;   E_frag[x] = E_int[x] + (1/2) sum_y E_xy.
- * Any output pointer may be NULL; E_frag/E_int are [n_frag] host arrays. */
+ * With opt.far_field the pairs beyond the cutoff add their multipole interaction energies to E_total
+ * and half to each E_frag.  Any output pointer may be NULL; E_frag/E_int are [n_frag] host arrays. */
 fef_status fef_energies(fef_ctx* ctx, double* E_frag, double* E_total, double* E_int);
 
 /* Monomer second-order energy of the FEF cluster perturbation theory (Eq. EM2, with the first-order

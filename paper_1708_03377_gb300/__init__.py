@@ -59,7 +59,7 @@ class fef_options(ctypes.Structure):
                 ("e_tol", ctypes.c_double), ("micro_e_tol", ctypes.c_double), ("micro_comm_tol", ctypes.c_double),
                 ("max_macro", ctypes.c_int32), ("max_micro", ctypes.c_int32), ("diis_size", ctypes.c_int32),
                 ("start", ctypes.c_int32), ("use_graph", ctypes.c_int32), ("deterministic", ctypes.c_int32),
-                ("mixed_switch", ctypes.c_double), ("exact_engine", ctypes.c_int32)]
+                ("mixed_switch", ctypes.c_double), ("exact_engine", ctypes.c_int32), ("far_field", ctypes.c_int32)]
 
 
 class fef_tile_plan(ctypes.Structure):

@@ -80,6 +80,10 @@ struct Buffers {
     int* scf_big = nullptr;    // fragments above kScfSmemMaxN AOs: one thread-block cluster each
     int n_scf_small = 0, n_scf_big = 0;
     double* gap = nullptr;     // [n_frag] HOMO-LUMO gap of each fragment's last Roothaan step
+    // far field (opt.far_field): moment integrals, nuclear moments and centroids (geometry time);
+    // multipoles, far potentials and half pair energies per fragment (per build)
+    double *far_M = nullptr, *far_Mnuc = nullptr, *far_cen = nullptr;
+    double *far_mult = nullptr, *far_pot = nullptr, *far_E = nullptr;
     double *e_nn_intra = nullptr, *e_nn_pair = nullptr;
     int* nmo = nullptr;
     // per-build data
@@ -165,6 +169,7 @@ extern "C" void fef_default_options(fef_options* o)
     o->deterministic = 0;
     o->mixed_switch = 1e-6;
     o->exact_engine = FEF_ENGINE_FP64;
+    o->far_field = 0;
 }
 
 // ---------------------------------------------------------------------------------------------- helpers
@@ -260,9 +265,14 @@ static void build_fock_device(fef_ctx* c, int kind)
     ck(launch_fock_energy(d, b->h, b->Venv, b->Jenv, b->eric, b->D, b->F, b->omega, b->e_nn_intra, b->E_int,
                           b->trV, b->trJ, s),
        "fock");
+    if (b->far_M)
+        ck(launch_far_field(d, b->far_M, b->far_Mnuc, b->far_cen, b->D, b->far_mult, b->far_pot, b->far_E, b->F,
+                            b->omega, s),
+           "far field");
     ck(launch_nuclear_traces(d, b->trf_off, b->trf, b->tr_xy, b->tr_yx, s), "nuclear traces");
     ck(launch_energies(d, b->E_int, b->trV, b->trJ, b->tr_xy, b->tr_yx, b->e_nn_pair, b->E_frag, b->E_tot, s),
        "energies");
+    if (b->far_M) ck(launch_far_energy(d, b->far_E, b->E_frag, b->E_tot, s), "far-field energies");
     ck(launch_check_finite(b->F, c->mat_total, b->err_flag, s), "check");
 }
 
@@ -464,6 +474,7 @@ extern "C" fef_status fef_create(const fef_geometry* g, const fef_basis* bs, con
         require(o.diis_size >= 1 && o.diis_size <= 8, FEF_ERR_ARG, "options: diis_size must be 1..8");
         require(o.max_macro >= 1 && o.max_micro >= 1, FEF_ERR_ARG, "options: iteration limits must be >= 1");
         require(o.precision == FEF_FP64 || o.precision == FEF_MIXED, FEF_ERR_ARG, "options: bad precision");
+        require(o.far_field == 0 || o.far_field == 1, FEF_ERR_ARG, "options: far_field must be 0 or 1");
         require(o.exact_engine == FEF_ENGINE_FP64 || o.exact_engine == FEF_ENGINE_DF64, FEF_ERR_ARG,
                 "options: bad exact_engine");
         require(o.schwarz >= 0.0 && std::isfinite(o.schwarz), FEF_ERR_ARG, "options: bad schwarz threshold");
@@ -715,6 +726,33 @@ extern "C" fef_status fef_create(const fef_geometry* g, const fef_basis* bs, con
         b->S = b->alloc<double>(c->mat_total, "S");
         b->h = b->alloc<double>(c->mat_total, "h");
         ck(launch_one_electron(d, b->S, b->h, s), "one-electron");
+        if (o.far_field && o.cutoff_A > 0.0) {
+            // centroids of nuclear charge and nuclear moments (bohr), moment integrals about them
+            std::vector<double> cen(3 * (size_t)nf, 0.0), mnuc(10 * (size_t)nf, 0.0);
+            for (int x = 0; x < nf; ++x) {
+                double zs = 0.0;
+                for (int a = frag_atom0[x]; a < frag_atom0[x] + frag_nat[x]; ++a) {
+                    zs += g->Z[a];
+                    for (int k = 0; k < 3; ++k) cen[3 * x + k] += g->Z[a] * g->xyz[3 * a + k] / 0.529177210903;
+                }
+                for (int k = 0; k < 3; ++k) cen[3 * x + k] /= zs;
+                for (int a = frag_atom0[x]; a < frag_atom0[x] + frag_nat[x]; ++a) {
+                    double r[3];
+                    for (int k = 0; k < 3; ++k) r[k] = g->xyz[3 * a + k] / 0.529177210903 - cen[3 * x + k];
+                    const double z = g->Z[a];
+                    const double v[10] = {z, z * r[0], z * r[1], z * r[2], z * r[0] * r[0], z * r[0] * r[1],
+                                          z * r[0] * r[2], z * r[1] * r[1], z * r[1] * r[2], z * r[2] * r[2]};
+                    for (int k = 0; k < 10; ++k) mnuc[10 * x + k] += v[k];
+                }
+            }
+            b->far_cen = b->upload(cen, s, "far field");
+            b->far_Mnuc = b->upload(mnuc, s, "far field");
+            b->far_M = b->alloc<double>(10 * c->mat_total, "moment integrals");
+            b->far_mult = b->alloc<double>(10 * (size_t)nf, "far field");
+            b->far_pot = b->alloc<double>(10 * (size_t)nf, "far field");
+            b->far_E = b->alloc<double>(nf, "far field");
+            ck(launch_moment_integrals(d, b->far_cen, b->far_M, s), "moment integrals");
+        }
         b->rot = b->alloc<double>((size_t)9 * nf, "frames");
         ck(launch_frames(d, b->rot, s), "frames");
         {  // the learned warm start needs fragments of one kind (same atoms and s/p basis)

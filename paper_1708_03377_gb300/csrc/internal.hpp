@@ -153,6 +153,13 @@ cudaError_t launch_boys_table32(const double* table64, float* table32, cudaStrea
 // Dh32 = float(Dh - Dh_ref) for every class
 cudaError_t launch_delta_density(const Dev& d, double* const Dh_ref[kClasses], cudaStream_t s);
 cudaError_t launch_one_electron(const Dev& d, double* S, double* h, cudaStream_t s);
+// far field (pairs beyond the cutoff): moment integrals about each fragment's centroid (10 n^2 at
+// 10 frag_moff), per build the fragments' multipoles, the far potentials and the Fock/omega terms,
+// and the energies (E_frag += E_far, E_tot recomputed)
+cudaError_t launch_moment_integrals(const Dev& d, const double* cen, double* M, cudaStream_t s);
+cudaError_t launch_far_field(const Dev& d, const double* M, const double* Mnuc, const double* cen, const double* D,
+                             double* mult, double* pot, double* E_far, double* F, double* omega, cudaStream_t s);
+cudaError_t launch_far_energy(const Dev& d, const double* E_far, double* E_frag, double* E_tot, cudaStream_t s);
 cudaError_t launch_intra_eri(const Dev& d, const int4* tasks, int n_tasks, double* eri, cudaStream_t s);
 cudaError_t launch_schwarz(const Dev& d, const double* eri, double* sp_Q, float* pp_Q[kClasses], cudaStream_t s);
 cudaError_t launch_coulomb_exchange(const Dev& d, const double* eri, double* eric, cudaStream_t s);

@@ -306,6 +306,215 @@ cudaError_t launch_one_electron(const Dev& d, double* S, double* h, cudaStream_t
     return cudaGetLastError();
 }
 
+// ------------------------------------------------------------------------------------------ far field
+// Fragment pairs beyond the cutoff interact through the multipoles of each fragment's nuclei and
+// electrons about its nuclear-charge centroid c_x (charge, dipole, second moments), the potential of
+// y Taylor-expanded to second order about c_x (the far-field extension of Eq. wc's sum over y).
+// Moment integrals (geometry time): M[k][mu][nu] = <mu|(r - c_x)^k|nu>, k = 1, x, y, z, xx, xy, xz,
+// yy, yz, zz, at 10 frag_moff[x] + k n^2, from the Hermite expansion of each primitive product:
+// int (x - c)^m Lambda_t dx = sqrt(pi/p) H^m_t with H^0_0 = 1, H^1_0 = X_PC, H^1_1 = 1,
+// H^2_0 = X_PC^2 + 1/(2p), H^2_1 = 2 X_PC, H^2_2 = 2.
+__global__ void k_moment_integrals(Dev d, const double* __restrict__ cen, double* M)
+{
+    const int x = blockIdx.y;
+    const int n = d.frag_nao[x];
+    const double* c = cen + 3 * x;
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n * n; e += gridDim.x * blockDim.x) {
+        const int mu = e / n, nu = e % n;
+        AOPair q = ao_pair(d, x, mu, nu);
+        double acc[10] = {};
+        for (int i = 0; i < q.na; ++i)
+            for (int j = 0; j < q.nb; ++j) {
+                const double a = d.p_exp[q.pa0 + i], b = d.p_exp[q.pb0 + j], p = a + b;
+                const double cc = d.p_coef[q.pa0 + i] * d.p_coef[q.pb0 + j];
+                double P[3], R2 = 0.0, m[3][3];
+                double E[3][3][3][5];
+                for (int k = 0; k < 3; ++k) {
+                    P[k] = (a * q.A[k] + b * q.B[k]) / p;
+                    R2 += (q.A[k] - q.B[k]) * (q.A[k] - q.B[k]);
+                    md_E1(q.la, q.lb, p, P[k] - q.A[k], P[k] - q.B[k], E[k]);
+                    const double* Et = E[k][q.ca[k]][q.cb[k]];
+                    const int tmax = q.ca[k] + q.cb[k];
+                    const double X = P[k] - c[k];
+                    const double e0 = Et[0], e1 = tmax >= 1 ? Et[1] : 0.0, e2 = tmax >= 2 ? Et[2] : 0.0;
+                    m[k][0] = e0;
+                    m[k][1] = X * e0 + e1;
+                    m[k][2] = (X * X + 0.5 / p) * e0 + 2.0 * X * e1 + 2.0 * e2;
+                }
+                const double pre = cc * exp(-a * b / p * R2) * pow(kPi / p, 1.5);
+                const int kk[10][3] = {{0, 0, 0}, {1, 0, 0}, {0, 1, 0}, {0, 0, 1}, {2, 0, 0},
+                                       {1, 1, 0}, {1, 0, 1}, {0, 2, 0}, {0, 1, 1}, {0, 0, 2}};
+                for (int k = 0; k < 10; ++k) acc[k] += pre * m[0][kk[k][0]] * m[1][kk[k][1]] * m[2][kk[k][2]];
+            }
+        for (int k = 0; k < 10; ++k) M[10 * d.frag_moff[x] + (int64_t)k * n * n + e] = acc[k] * q.scale;
+    }
+}
+
+cudaError_t launch_moment_integrals(const Dev& d, const double* cen, double* M, cudaStream_t s)
+{
+    dim3 g((d.max_nao * d.max_nao + 127) / 128, d.n_frag);
+    k_moment_integrals<<<g, 128, 0, s>>>(d, cen, M);
+    note_launches(1);
+    return cudaGetLastError();
+}
+
+// Multipoles of every fragment for the densities D: mult[x][k] = Mnuc[x][k] - tr(D^x M_k), one block
+// per fragment (charge, dipole, second moments xx xy xz yy yz zz).
+__global__ void k_far_multipoles(Dev d, const double* __restrict__ M, const double* __restrict__ Mnuc,
+                                 const double* __restrict__ D, double* mult)
+{
+    const int x = blockIdx.x;
+    const int n = d.frag_nao[x];
+    const double* Dx = D + d.frag_moff[x];
+    const double* Mx = M + 10 * d.frag_moff[x];
+    __shared__ double red[10][8];
+    double acc[10] = {};
+    for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
+        const double de = Dx[e];
+        for (int k = 0; k < 10; ++k) acc[k] = fma(de, Mx[(int64_t)k * n * n + e], acc[k]);
+    }
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    for (int k = 0; k < 10; ++k) {
+        double v = acc[k];
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if (lane == 0) red[k][w] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < 10) {
+        double t = 0.0;
+        for (int j = 0; j < (int)(blockDim.x >> 5); ++j) t += red[threadIdx.x][j];
+        mult[10 * x + threadIdx.x] = Mnuc[10 * x + threadIdx.x] - t;
+    }
+}
+
+// Potential of the far fragments at c_x, summed: pot[x] = (phi, grad phi[3], hess phi[xx xy xz yy yz zz]),
+// with y's potential phi(R) = q T - mu.T1 + (1/2) M2 : T2 at R = c_x - c_y (T_n the derivatives of
+// 1/|R|, contracted in closed form), and E_far[x] = (1/2) sum_y (q_x phi + mu_x . g + (1/2) M2_x : H).
+// One thread per fragment; pairs within the cutoff (the neighbour list) are skipped.
+__global__ void k_far_potential(Dev d, const double* __restrict__ cen, const double* __restrict__ mult, double* pot,
+                                double* E_far)
+{
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    if (x >= d.n_frag) return;
+    double ph = 0.0, g[3] = {}, H[3][3] = {};
+    double e_sum = 0.0;
+    const double* cx = cen + 3 * x;
+    const double* mx = mult + 10 * x;
+    const double Mx[3][3] = {{mx[4], mx[5], mx[6]}, {mx[5], mx[7], mx[8]}, {mx[6], mx[8], mx[9]}};
+    for (int y = 0; y < d.n_frag; ++y) {
+        if (y == x) continue;
+        bool near = false;
+        for (int c = d.frag_nbr0[x]; c < d.frag_nbr0[x + 1]; ++c) near = near || d.nbr[c] == y;
+        if (near) continue;
+        const double* my = mult + 10 * y;
+        const double q = my[0];
+        const double mu[3] = {my[1], my[2], my[3]};
+        const double M2[3][3] = {{my[4], my[5], my[6]}, {my[5], my[7], my[8]}, {my[6], my[8], my[9]}};
+        double R[3];
+        for (int a = 0; a < 3; ++a) R[a] = cx[a] - cen[3 * y + a];
+        const double r2 = R[0] * R[0] + R[1] * R[1] + R[2] * R[2];
+        const double ir = rsqrt(r2), ir2 = ir * ir;
+        const double ir3 = ir * ir2, ir5 = ir3 * ir2, ir7 = ir5 * ir2, ir9 = ir7 * ir2;
+        double MR[3];
+        for (int a = 0; a < 3; ++a) MR[a] = M2[a][0] * R[0] + M2[a][1] * R[1] + M2[a][2] * R[2];
+        const double RMR = R[0] * MR[0] + R[1] * MR[1] + R[2] * MR[2];
+        const double trM = M2[0][0] + M2[1][1] + M2[2][2];
+        const double muR = mu[0] * R[0] + mu[1] * R[1] + mu[2] * R[2];
+        // phi = q/r + mu.R/r^3 + (1/2)(3 RMR/r^5 - trM/r^3)
+        const double p = q * ir + muR * ir3 + 0.5 * (3.0 * RMR * ir5 - trM * ir3);
+        double gy[3], Hy[3][3];
+        for (int c = 0; c < 3; ++c) {
+            // g_c = q T_c - sum_a mu_a T_ac + (1/2) sum_ab M_ab T_abc
+            const double Tc = -R[c] * ir3;
+            const double muT2 = 3.0 * muR * R[c] * ir5 - mu[c] * ir3;
+            const double MT3 = -15.0 * RMR * R[c] * ir7 + 3.0 * (2.0 * MR[c] + trM * R[c]) * ir5;
+            gy[c] = q * Tc - muT2 + 0.5 * MT3;
+            for (int e = 0; e < 3; ++e) {
+                const double dce = c == e ? 1.0 : 0.0;
+                const double T2 = (3.0 * R[c] * R[e] - r2 * dce) * ir5;
+                const double muT3 = -15.0 * muR * R[c] * R[e] * ir7 + 3.0 * (mu[c] * R[e] + mu[e] * R[c] + muR * dce) * ir5;
+                const double MT4 = 105.0 * RMR * R[c] * R[e] * ir9
+                                   - 15.0 * (RMR * dce + 2.0 * R[c] * MR[e] + 2.0 * R[e] * MR[c] + trM * R[c] * R[e]) * ir7
+                                   + 3.0 * (trM * dce + 2.0 * M2[c][e]) * ir5;
+                Hy[c][e] = q * T2 - muT3 + 0.5 * MT4;
+            }
+        }
+        double exy = mx[0] * p;
+        for (int c = 0; c < 3; ++c) {
+            exy += mx[1 + c] * gy[c];
+            for (int e = 0; e < 3; ++e) exy += 0.5 * Mx[c][e] * Hy[c][e];
+        }
+        e_sum += exy;
+        ph += p;
+        for (int c = 0; c < 3; ++c) {
+            g[c] += gy[c];
+            for (int e = 0; e < 3; ++e) H[c][e] += Hy[c][e];
+        }
+    }
+    double* o = pot + 10 * x;
+    o[0] = ph;
+    o[1] = g[0]; o[2] = g[1]; o[3] = g[2];
+    o[4] = H[0][0]; o[5] = H[0][1]; o[6] = H[0][2]; o[7] = H[1][1]; o[8] = H[1][2]; o[9] = H[2][2];
+    E_far[x] = 0.5 * e_sum;
+}
+
+// F^x and omega_x += -(phi S + grad phi . <r> + (1/2) hess phi : <r r>) (the density derivative of
+// the far-field energy; off-diagonal second moments count twice).
+__global__ void k_far_fock(Dev d, const double* __restrict__ M, const double* __restrict__ pot, double* F,
+                           double* omega)
+{
+    const int x = blockIdx.y;
+    const int n = d.frag_nao[x];
+    const double* Mx = M + 10 * d.frag_moff[x];
+    const double* o = pot + 10 * x;
+    const double w[10] = {o[0], o[1], o[2], o[3], 0.5 * o[4], o[5], o[6], 0.5 * o[7], o[8], 0.5 * o[9]};
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n * n; e += gridDim.x * blockDim.x) {
+        double v = 0.0;
+        for (int k = 0; k < 10; ++k) v = fma(w[k], Mx[(int64_t)k * n * n + e], v);
+        const int64_t i = d.frag_moff[x] + e;
+        if (F) F[i] -= v;
+        if (omega) omega[i] -= v;
+    }
+}
+
+// E_frag[x] += E_far[x]; E_tot = sum_x E_frag[x] (one block).
+__global__ void k_far_energy(Dev d, const double* __restrict__ E_far, double* E_frag, double* E_tot)
+{
+    __shared__ double red[256];
+    double a = 0.0;
+    for (int x = threadIdx.x; x < d.n_frag; x += blockDim.x) {
+        const double e = E_frag[x] + E_far[x];
+        E_frag[x] = e;
+        a += e;
+    }
+    red[threadIdx.x] = a;
+    __syncthreads();
+    for (int st = blockDim.x / 2; st > 0; st >>= 1) {
+        if (threadIdx.x < st) red[threadIdx.x] += red[threadIdx.x + st];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *E_tot = red[0];
+}
+
+cudaError_t launch_far_field(const Dev& d, const double* M, const double* Mnuc, const double* cen, const double* D,
+                             double* mult, double* pot, double* E_far, double* F, double* omega, cudaStream_t s)
+{
+    if (d.n_frag <= 1) return cudaSuccess;
+    k_far_multipoles<<<d.n_frag, 128, 0, s>>>(d, M, Mnuc, D, mult);
+    k_far_potential<<<(d.n_frag + 127) / 128, 128, 0, s>>>(d, cen, mult, pot, E_far);
+    dim3 g((d.max_nao * d.max_nao + 127) / 128, d.n_frag);
+    k_far_fock<<<g, 128, 0, s>>>(d, M, pot, F, omega);
+    note_launches(3);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_far_energy(const Dev& d, const double* E_far, double* E_frag, double* E_tot, cudaStream_t s)
+{
+    k_far_energy<<<1, 256, 0, s>>>(d, E_far, E_frag, E_tot);
+    note_launches(1);
+    return cudaGetLastError();
+}
+
 // ------------------------------------------------------------------------------------------ nuclear (Hermite)
 // Field of the nuclei of fragment y on primitive pair P in Hermite form (McMurchie-Davidson):
 //   V~_P[tuv] = sum_{C in y} -Z_C (2 pi/p) R_tuv(p, P - C),
