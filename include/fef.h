@@ -250,7 +250,9 @@ typedef struct {
                                in shared memory, float-float), whose warps take items from a queue sorted
                                by decreasing cost (all fragment pairs and classes in one launch); the
                                tiers run concurrently.  0: one launch per class pair over whole ket
-                               ranges (ket_chunk unused). */
+                               ranges (ket_chunk unused).  2: the same class-pair kernels launched on
+                               three streams (graph branches when captured), largest classes first,
+                               so that they run concurrently (ket_chunk unused). */
     int32_t ket_chunk[25];  /* ket primitive pairs per item for the class pair L_bra*5 + L_ket
                                (L = l_a + l_b of the shell pair); 0 = the partner's whole class range */
     double tuned_ms;        /* J-engine time of one build measured by fef_autotune (0: not tuned) */
@@ -258,7 +260,7 @@ typedef struct {
 
 /* Read or replace the plan of one engine (FEF_JENGINE_FP64: FP64 builds; FEF_JENGINE_FP32: the FP32-core
  * builds of FEF_MIXED; FEF_JENGINE_DF64: float-float builds).  Default plans use whole ket ranges,
- * persistent for FEF_JENGINE_FP64 and one launch per class pair for the other two.  Setting rebuilds
+ * persistent (1) for FEF_JENGINE_FP64 and concurrent class-pair launches (2) for the other two.  Setting rebuilds
  * the work queues (synchronous).  Errors: ARG, CUDA. */
 fef_status fef_get_tile_plan(const fef_ctx* ctx, int32_t engine, fef_tile_plan* out);
 fef_status fef_set_tile_plan(fef_ctx* ctx, int32_t engine, const fef_tile_plan* plan);
@@ -267,7 +269,7 @@ fef_status fef_set_tile_plan(fef_ctx* ctx, int32_t engine, const fef_tile_plan* 
  * installs the fastest.  It chooses the ket chunk of each class pair (from whole range, 1024, 256, 64
  * ket pairs; classes in decreasing order of cost) on every k-th fragment pair, k chosen so that one
  * timed pass takes about budget_ms/64, then, when a full build fits the budget, persistent queues
- * against one launch per class pair.  Each candidate is timed reps times (best kept) after a warm-up.
+ * against one launch per class pair, serial or concurrent.  Each candidate is timed reps times (best kept) after a warm-up.
  * Runs between builds (it overwrites the J-engine accumulators; the next build starts afresh).
  * out (nullable) receives the chosen plan.  Errors: ARG, CUDA. */
 fef_status fef_autotune(fef_ctx* ctx, int32_t engine, int32_t reps, double budget_ms, fef_tile_plan* out);

@@ -1368,7 +1368,8 @@ extern "C" fef_status fef_set_tile_plan(fef_ctx* c, int32_t engine, const fef_ti
 {
     if (!c) return FEF_ERR_ARG;
     FEF_API_BEGIN
-    require(plan != nullptr && engine >= 0 && engine <= 2, FEF_ERR_ARG, "fef_set_tile_plan: bad engine or plan");
+    require(plan != nullptr && engine >= 0 && engine <= 2 && plan->persistent >= 0 && plan->persistent <= 2,
+            FEF_ERR_ARG, "fef_set_tile_plan: bad engine or plan");
     for (int i = 0; i < 25; ++i)
         require(plan->ket_chunk[i] >= 0 && plan->ket_chunk[i] < (1 << 26), FEF_ERR_ARG,
                 "fef_set_tile_plan: ket_chunk out of range");

@@ -183,6 +183,12 @@ cudaError_t launch_jengine(const Dev& d, const int2* tiles[kClasses][kClasses], 
                            int mode, cudaStream_t s);
 cudaError_t launch_jengine_df(const Dev& d, const int2* tiles[kClasses][kClasses], const int* n_tiles, float tau,
                               cudaStream_t s);
+// one class pair's per-class kernel (mode as launch_jengine), for concurrent launches on forked streams
+cudaError_t launch_jengine_class(const Dev& d, int LP, int LQ, const int2* t, int n, float tau, int mode,
+                                 cudaStream_t s);
+cudaError_t launch_jengine_big_class(const Dev& d, int LP, int LQ, const int2* t, int n, float tau, int fp32,
+                                     cudaStream_t s);
+cudaError_t launch_jengine_df_class(const Dev& d, int LP, int LQ, const int2* t, int n, float tau, cudaStream_t s);
 cudaError_t launch_df_setup(const Dev& d, float4* const Phi[kClasses], float4* const Plo[kClasses], float2* boysdf,
                             cudaStream_t s);
 cudaError_t launch_df_density(const Dev& d, cudaStream_t s);

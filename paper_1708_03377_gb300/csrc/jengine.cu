@@ -459,6 +459,29 @@ static void launch_one(const Dev& d, const int2* t, int n, float tau, int fp32, 
     note_launches(1);
 }
 
+// One class pair's kernel on stream s (mode 0 FP64, 1 FP32, 2 float-float for L_P <= 2): the plans
+// that run the class kernels concurrently on forked streams launch them one by one.
+cudaError_t launch_jengine_class(const Dev& d, int LP, int LQ, const int2* t, int n, float tau, int mode, cudaStream_t s)
+{
+    if (n <= 0) return cudaSuccess;
+    if (LP + LQ >= 5) return launch_jengine_big_class(d, LP, LQ, t, n, tau, mode == 1 ? 1 : 0, s);
+    if (mode == 2 && LP <= 2) return launch_jengine_df_class(d, LP, LQ, t, n, tau, s);
+    const int fp32 = mode == 1 ? 1 : 0;
+    switch (LP * kClasses + LQ) {
+        case 0 * kClasses + 0: launch_one<0, 0>(d, t, n, tau, fp32, s); break;
+        case 1 * kClasses + 0: launch_one<1, 0>(d, t, n, tau, fp32, s); break;
+        case 1 * kClasses + 1: launch_one<1, 1>(d, t, n, tau, fp32, s); break;
+        case 2 * kClasses + 0: launch_one<2, 0>(d, t, n, tau, fp32, s); break;
+        case 2 * kClasses + 1: launch_one<2, 1>(d, t, n, tau, fp32, s); break;
+        case 2 * kClasses + 2: launch_one<2, 2>(d, t, n, tau, fp32, s); break;
+        case 3 * kClasses + 0: launch_one<3, 0>(d, t, n, tau, fp32, s); break;
+        case 3 * kClasses + 1: launch_one<3, 1>(d, t, n, tau, fp32, s); break;
+        case 4 * kClasses + 0: launch_one<4, 0>(d, t, n, tau, fp32, s); break;
+        default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
 cudaError_t launch_jengine(const Dev& d, const int2* tiles[kClasses][kClasses], const int* n_tiles, double tau,
                            int mode, cudaStream_t s)
 {

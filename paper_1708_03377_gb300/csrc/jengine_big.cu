@@ -283,6 +283,21 @@ cudaError_t launch_jengine_big_persistent(const Dev& d, int fp32, const JQueue& 
     return cudaGetLastError();
 }
 
+cudaError_t launch_jengine_big_class(const Dev& d, int LP, int LQ, const int2* t, int n, float tau, int fp32,
+                                     cudaStream_t s)
+{
+    switch (LP * kClasses + LQ) {
+        case 3 * kClasses + 2: launch_big<3, 2>(d, t, n, tau, fp32, s); break;
+        case 3 * kClasses + 3: launch_big<3, 3>(d, t, n, tau, fp32, s); break;
+        case 4 * kClasses + 1: launch_big<4, 1>(d, t, n, tau, fp32, s); break;
+        case 4 * kClasses + 2: launch_big<4, 2>(d, t, n, tau, fp32, s); break;
+        case 4 * kClasses + 3: launch_big<4, 3>(d, t, n, tau, fp32, s); break;
+        case 4 * kClasses + 4: launch_big<4, 4>(d, t, n, tau, fp32, s); break;
+        default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
 cudaError_t launch_jengine_big(const Dev& d, const int2* tiles[kClasses][kClasses], const int* n_tiles, float tau,
                                int fp32, cudaStream_t s)
 {

@@ -389,6 +389,20 @@ cudaError_t launch_jengine_df_persistent(const Dev& d, const JQueue& q, float ta
     return cudaGetLastError();
 }
 
+cudaError_t launch_jengine_df_class(const Dev& d, int LP, int LQ, const int2* t, int n, float tau, cudaStream_t s)
+{
+    switch (LP * kClasses + LQ) {
+        case 0 * kClasses + 0: launch_df_one<0, 0>(d, t, n, tau, s); break;
+        case 1 * kClasses + 0: launch_df_one<1, 0>(d, t, n, tau, s); break;
+        case 1 * kClasses + 1: launch_df_one<1, 1>(d, t, n, tau, s); break;
+        case 2 * kClasses + 0: launch_df_one<2, 0>(d, t, n, tau, s); break;
+        case 2 * kClasses + 1: launch_df_one<2, 1>(d, t, n, tau, s); break;
+        case 2 * kClasses + 2: launch_df_one<2, 2>(d, t, n, tau, s); break;
+        default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
 // Class pairs with L_P <= 2 in df64; the others (d shells) in native FP64.
 cudaError_t launch_jengine_df(const Dev& d, const int2* tiles[kClasses][kClasses], const int* n_tiles, float tau,
                               cudaStream_t s)

@@ -34,6 +34,7 @@ def main(argv=None):
     ap.add_argument("--snapshots", type=int, default=1,
                     help="mixed workload: independent snapshots (seeds seed..seed+n-1) batched into one context")
     ap.add_argument("--autotune", action="store_true", help="autotune the tile plans of the engines used first")
+    ap.add_argument("--far-field", action="store_true", help="multipole coupling of the pairs beyond the cutoff")
     ap.add_argument("--waters", type=int, default=64)
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--cutoff", type=float, default=8.0)
@@ -61,7 +62,7 @@ def main(argv=None):
     prec = fef.FEF_MIXED if a.precision == "mixed" else fef.FEF_FP64
     eng = fef.FEF_ENGINE_DF64 if a.engine == "df64" else fef.FEF_ENGINE_FP64
     opts = fef.fef_default_options(cutoff_A=a.cutoff, schwarz=a.schwarz, e_tol=a.e_tol, precision=prec,
-                                   exact_engine=eng)
+                                   exact_engine=eng, far_field=1 if a.far_field else 0)
     stream = torch.cuda.Stream()
     with torch.cuda.stream(stream):
         for _ in range(a.repeat):

@@ -47,10 +47,10 @@ def test_plans_match_oracle_and_each_other(formamide_water, engine):
     jeng = fef.FEF_JENGINE_DF64 if engine == "df64" else fef.FEF_JENGINE_FP64
     ctx = fef.fef_create_system(system, fef.fef_default_options(schwarz=1e-12, exact_engine=eng))
     default = fef.fef_get_tile_plan(ctx, jeng)
-    assert default["persistent"] == (1 if engine == "fp64" else 0) and (default["ket_chunk"] == 0).all()
+    assert default["persistent"] == (1 if engine == "fp64" else 2) and (default["ket_chunk"] == 0).all()
     results = {}
     for name, plan in (("default", None), ("ragged", _plan(1, 5)), ("chunk64", _plan(1, 64)),
-                       ("per_class", _plan(0, 0)), ("persistent", _plan(1, 0))):
+                       ("per_class", _plan(0, 0)), ("persistent", _plan(1, 0)), ("concurrent", _plan(2, 0))):
         if plan is not None:
             fef.fef_set_tile_plan(ctx, jeng, plan)
             got = fef.fef_get_tile_plan(ctx, jeng)
@@ -66,12 +66,14 @@ def test_plans_match_oracle_and_each_other(formamide_water, engine):
 
 
 def test_mixed_iterate_with_chunked_fp32_plan(formamide_water):
-    """The FP32-core increments of FEF_MIXED under persistent plans (ragged and whole-range) converge
-    to the same fixed point as the default per-class plan (all end on exact references)."""
+    """The FP32-core increments of FEF_MIXED under persistent plans (ragged and whole-range) and serial
+    class launches converge to the same fixed point as the default concurrent class launches (all
+    end on exact references)."""
     fef = _fef()
     system = formamide_water[0]
     E = {}
-    for name, plan in (("default", None), ("ragged", _plan(1, 3)), ("persistent", _plan(1, 0))):
+    for name, plan in (("default", None), ("ragged", _plan(1, 3)), ("persistent", _plan(1, 0)),
+                       ("per_class", _plan(0, 0))):
         ctx = fef.fef_create_system(system, fef.fef_default_options(schwarz=1e-12, e_tol=1e-9,
                                                                     precision=fef.FEF_MIXED))
         if plan is not None:
@@ -79,7 +81,7 @@ def test_mixed_iterate_with_chunked_fp32_plan(formamide_water):
         fef.fef_iterate(ctx)
         E[name] = fef.fef_energies(ctx)[1]
         ctx.close()
-    assert abs(E["ragged"] - E["default"]) < 1e-8 and abs(E["persistent"] - E["default"]) < 1e-8, E
+    assert all(abs(E[k] - E["default"]) < 1e-8 for k in E), E
 
 
 def test_autotune_water_box():
@@ -108,4 +110,6 @@ def test_bad_plan_rejected():
         fef.fef_set_tile_plan(ctx, 3, _plan(1, 0))
     with pytest.raises(fef.FefError):
         fef.fef_set_tile_plan(ctx, 0, _plan(1, -4))
+    with pytest.raises(fef.FefError):
+        fef.fef_set_tile_plan(ctx, 0, _plan(3, 0))
     ctx.close()
