@@ -85,3 +85,40 @@ def test_mixed_snapshot_sampled_field():
     assert big, "the sampled fragment should have large d-shell neighbours"
     err = float(np.abs(F[x] - (own + om)).max())
     assert err <= 1e-10, err
+
+
+def _sampled_fields(fef, system, cutoff_A, xs, **opt):
+    ctx = fef.fef_create_system(system, fef.fef_default_options(cutoff_A=cutoff_A, schwarz=1e-12, **opt))
+    fef.fef_noninteracting_scf(ctx)
+    D = fef.fef_get_densities(ctx)
+    F = ctx.unpack(fef.fef_build_fock(ctx, D))
+    Db = ctx.unpack(D)
+    ctx.close()
+    errs = []
+    for x in xs:
+        own, om = _oracle_fragment_terms(system, x, Db, cutoff_A, 1e-12)
+        errs.append(float(np.abs(F[x] - (own + om)).max()))
+    return errs
+
+
+def test_solvated_heterocycle_sampled_fock():
+    """The 130-AO solute (d shells) among 1000 waters, 8 A cutoff: the full Fock matrices of the water
+    closest to the solute and of a far one (the oracle sums over their neighbours, the solute included)."""
+    fef = _fef()
+    system = S.solvated_heterocycle()
+    sol = system.frag_atoms(0)
+    dist = [np.linalg.norm(system.xyz[sol][:, None] - system.xyz[system.frag_atoms(x)][None], axis=2).min()
+            for x in range(1, system.n_frag)]
+    near = 1 + int(np.argmin(dist))
+    far = 1 + int(np.argmax(dist))
+    errs = _sampled_fields(fef, system, 8.0, (near, far))
+    assert max(errs) <= 1e-10, errs
+
+
+def test_water_box2000_sampled_fock():
+    """A held-out 2000-water snapshot of the learned-start workload (39.1 A cube, 8 A cutoff): three
+    sampled fragments' full Fock matrices (FP64 build of the isolated densities)."""
+    fef = _fef()
+    system = S.water_box(2000, seed=2000, basis_sets=S.water_box(8, seed=0).basis_sets)
+    errs = _sampled_fields(fef, system, 8.0, (0, 999, 1999))
+    assert max(errs) <= 1e-10, errs
