@@ -76,11 +76,6 @@ __device__ __forceinline__ df64 fma(df64 a, df64 b, df64 c)
     return quick_two_sum(t.hi, __fadd_rn(t.lo, __fadd_rn(e, c.lo)));
 }
 
-__device__ __forceinline__ df64 shfl_xor(df64 v, int o)
-{
-    return df64(__shfl_xor_sync(0xffffffffu, v.hi, o), __shfl_xor_sync(0xffffffffu, v.lo, o));
-}
-
 // 1/sqrt(x), x > 0: float seed, one float Newton step, one df64 Newton step (relative error ~1e-14).
 __device__ __forceinline__ df64 rsqrt_df(df64 x)
 {
