@@ -773,7 +773,7 @@ __device__ void eri_bra_row(const Dev& d, const int s1, const int s2, const int 
                     double X = P[0] - Q[0], Y = P[1] - Q[1], Z = P[2] - Q[2];
                     double F[kMaxLTot + 1], base[kMaxLTot + 1], R[nh(kMaxLTot)];
                     boys_fp64_rt(d.boys, alpha * (X * X + Y * Y + Z * Z), L, F);
-                    double pre = 2.0 * pow(kPi, 2.5) / (p * q * sqrt(p + q)) * Kab * Kcd;
+                    double pre = kSqrt2Pi52 * kSqrt2Pi52 / (p * q * sqrt(p + q)) * Kab * Kcd;  // 2 pi^{5/2}
                     for (int m = 0; m <= L; ++m) {
                         base[m] = pre * F[m];
                         pre *= -2.0 * alpha;
