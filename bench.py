@@ -18,6 +18,8 @@ Legs reported beside it (same workload, same 1e-8 Eh convergence, energies compa
   mixed                MIXED with the float-float reference build;
   mixed_learned        MIXED (float-float reference) from the learned warm start; the network is
                        trained beforehand (not timed) on 40 seeded snapshots drawn like the workload.
+e_m2 / e_d2: one fef_energy_m2 / fef_energy_d2 call on the converged FP64 state (second-order
+       energies, Eqs. EM2 and ED2), wall clock.
 e2e    = the same step plus the device->host read of every converged density, wall clock.
 roofline: the J-engine (one persistent FP64 launch per Fock build) against the FP64 ALU peak.
 --impl reference: the CPU oracle on a bounded sample of the same workload.
