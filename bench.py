@@ -417,6 +417,8 @@ def main():
         "time_to_1e-8_ms": float(np.mean(iter_ms)), "setup_and_energies_ms": total_ms / args.steps - float(np.mean(iter_ms)),
         "n_macro": last["n_macro"], "fock_builds_per_step": builds,
         "shell_quartets_per_build": st["shell_quartets"], "prim_quartets_per_build": int(np.sum(st["class_quartets"])),
+        "prim_quartets_per_s": value * float(np.sum(st["class_quartets"])) / max(st["shell_quartets"], 1),
+        "jengine_shell_quartets_per_s": st["shell_quartets"] / (jms_per_build * 1e-3),
         "E_tot": last["E_tot"],
         "df64": {**summary(df_ms, df_step_ms, dres), "exact_engine": "df64 (float-float on the FP32 pipes)",
                  "jengine_ms_per_build": float(np.mean([h["jengine_ms"] for h in dres["hist"]])),
