@@ -131,7 +131,9 @@ void fef_default_options(fef_options* opt);
  * two-electron tensor, the fragment-pair neighbour list within the cutoff, the environment nuclear
  * attraction sum_{y in N(x)} V^y (h~, the equation after Eq. wc) and the J-engine work lists.
  * cuda_stream: a cudaStream_t (NULL = default stream).  On success *out owns device memory until
- * fef_destroy.  Errors: ARG (NULL pointers, sizes), BASIS, GEOM, CUDA. */
+ * fef_destroy.  Errors: ARG (NULL pointers, an empty geometry or basis, an option out of range: diis_size
+ * outside 1..8, NaN cutoff_A, non-positive or non-finite e_tol / micro tolerances, negative schwarz
+ * or mixed_switch), BASIS, GEOM, CUDA.  Argument and option checks come before any device call. */
 fef_status fef_create(const fef_geometry* geom, const fef_basis* basis, const fef_options* opt,
                       void* cuda_stream, fef_ctx** out);
 

@@ -478,6 +478,12 @@ extern "C" fef_status fef_create(const fef_geometry* g, const fef_basis* bs, con
         require(o.exact_engine == FEF_ENGINE_FP64 || o.exact_engine == FEF_ENGINE_DF64, FEF_ERR_ARG,
                 "options: bad exact_engine");
         require(o.schwarz >= 0.0 && std::isfinite(o.schwarz), FEF_ERR_ARG, "options: bad schwarz threshold");
+        require(!std::isnan(o.cutoff_A), FEF_ERR_ARG, "options: cutoff_A is NaN");
+        require(o.e_tol > 0.0 && std::isfinite(o.e_tol), FEF_ERR_ARG, "options: e_tol must be finite and > 0");
+        require(o.micro_e_tol > 0.0 && std::isfinite(o.micro_e_tol) && o.micro_comm_tol > 0.0 &&
+                    std::isfinite(o.micro_comm_tol),
+                FEF_ERR_ARG, "options: micro_e_tol and micro_comm_tol must be finite and > 0");
+        require(o.mixed_switch >= 0.0 && std::isfinite(o.mixed_switch), FEF_ERR_ARG, "options: bad mixed_switch");
         c->stream = static_cast<cudaStream_t>(cuda_stream);
         ck(cudaGetDevice(&c->device), "cudaGetDevice");
 

@@ -46,3 +46,45 @@ def test_create_rejects_null_arguments_without_gpu():
     st = L.fef_create(None, None, None, None, ctypes.byref(out))
     assert st == fef.FEF_ERR_ARG
     assert b"NULL" in L.fef_last_error(None)
+
+
+
+@pytest.mark.parametrize("bad", [dict(), dict(n_atoms=0, n_frag=0), dict(n_frag=0), dict(diis_size=9),
+                                 dict(cutoff_A=float("nan")), dict(e_tol=0.0), dict(e_tol=float("inf")),
+                                 dict(micro_e_tol=-1.0), dict(micro_comm_tol=float("nan")),
+                                 dict(schwarz=-1e-12), dict(mixed_switch=float("nan")), dict(far_field=2),
+                                 dict(precision=7)])
+def test_create_rejects_empty_input_and_bad_options_without_gpu(bad):
+    """An empty geometry and out-of-range options fail with FEF_ERR_ARG before any device call; the
+    same single water with no bad item passes the host checks."""
+    import ctypes
+    import numpy as np
+    import paper_1708_03377_gb300 as fef
+    from synth import systems as S
+    bad = dict(bad)
+    n_atoms = bad.pop("n_atoms", 3)
+    n_frag = bad.pop("n_frag", 1)
+    system = S.water_dimer(0)
+    Z = np.ascontiguousarray(system.Z[:3], np.int32)
+    xyz = np.ascontiguousarray(system.xyz[:3], np.float64).reshape(-1)
+    foa = np.zeros(3, np.int32)
+    boa = np.ascontiguousarray(system.basis_of_atom[:3], np.int32)
+    so, sl, sn, ex, co = (np.ascontiguousarray(a) for a in system.flat_basis())
+    so, sl, sn = (a.astype(np.int32) for a in (so, sl, sn))
+    ex, co = ex.astype(np.float64), co.astype(np.float64)
+    p = lambda a, t: a.ctypes.data_as(ctypes.POINTER(t))
+    g = fef.fef_geometry(n_atoms, p(Z, ctypes.c_int32), p(xyz, ctypes.c_double), p(foa, ctypes.c_int32),
+                         p(boa, ctypes.c_int32), n_frag, None)
+    b = fef.fef_basis(int(so.shape[0]) - 1, p(so, ctypes.c_int32), p(sl, ctypes.c_int32), p(sn, ctypes.c_int32),
+                      p(ex, ctypes.c_double), p(co, ctypes.c_double))
+    opt = fef.fef_default_options(**bad)
+    out = ctypes.c_void_p()
+    st = fef.lib().fef_create(ctypes.byref(g), ctypes.byref(b), ctypes.byref(opt), None, ctypes.byref(out))
+    if not bad and n_atoms == 3 and n_frag == 1:
+        # the control: valid arguments pass every host check and reach the device (none here)
+        assert st in (fef.FEF_OK, fef.FEF_ERR_CUDA), fef.lib().fef_last_error(None)
+        if st == fef.FEF_OK:
+            fef.lib().fef_destroy(out)
+        return
+    assert st == fef.FEF_ERR_ARG, fef.lib().fef_last_error(None)
+    assert not out.value
