@@ -3,7 +3,8 @@ bench times, with its options; a 100-fragment snapshot of uneven s/p/d fragments
 against the CPU oracle evaluated fragment by fragment for a few sampled fragments.  The oracle
 builds F^x = h^x + G[D^x] + sum_{y in N(x)} (V^y + J[D^y]) (Theory, "Fragment Mean Field", Eq. wc
 and Eq. dp2e) from its own Obara-Saika integrals, with the same cutoff and shell-level Schwarz
-screening, from the densities the GPU used.  Bar: 1e-10 Eh per Fock element (FP64 mode)."""
+screening, from the densities the GPU used.  Bar: 1e-10 Eh per Fock element (FP64 mode).  The
+bench workload is also solved to self-consistency on both sides and its converged energies compared."""
 import numpy as np
 import pytest
 
