@@ -12,8 +12,9 @@
  *     fragment y and 2 v (Eq. dp2e) is the Coulomb matrix of y's density,
  *     J[D^y]_{mu nu} = sum_{lambda sigma in y} (mu nu|lambda sigma) D^y_{lambda sigma};
  *     there is no inter-fragment exchange;
- *   - the field is "fully relaxed to infinite order": every fragment's RHF is solved in the field of
- *     the others and the field rebuilt until all fragments are self-consistent.
+ *   - the field is relaxed to all orders (the polarisation-screened mean field): every fragment's
+ *     RHF is solved in the field of the others and the field rebuilt until all fragments are
+ *     self-consistent.
  *
  * Conventions used by every call:
  *   - Units: geometry in Angstrom on input (1 bohr = 0.529177210903 A); bohr and hartree inside
@@ -152,7 +153,7 @@ fef_status fef_ao_layout(const fef_ctx* ctx, int32_t* n_ao_per_frag, int64_t* of
  * Errors: ARG, CUDA, NUMERIC. */
 fef_status fef_build_fock(fef_ctx* ctx, const double* D, double* F_out, int on_device);
 
-/* FEF self-consistency (Theory, "Fragment Mean Field": omega_x fully relaxed to infinite order).
+/* FEF self-consistency (Theory, "Fragment Mean Field": omega_x relaxed to self-consistency).
  * Start from the option's start densities (superposition of isolated-fragment RHF densities, the
  * learned warm start (fef_set_warm_start), or the current/given ones); each macro-iteration k builds omega^(k) from
  * D^(k-1) of all fragments and solves every fragment's RHF in its frozen field (DIIS, canonical

@@ -13,8 +13,9 @@ Follows the paper's Theory section, "Fragment Mean Field":
   fragment (equation after Eq. wc) and 2 v^{mu j}_{nu j} with v from Eq. dp2e equals the Coulomb
   matrix J[D^y] of each other fragment's density, J[D^y]_{mu nu} = sum_{lambda sigma in y}
   (mu nu|lambda sigma) D^y_{lambda sigma};
-* the field is "fully relaxed to infinite order": every fragment's RHF is solved in the field of
-  the others and the field is rebuilt until all fragments are self-consistent;
+* the field is relaxed to all orders (the polarisation-screened mean field): every fragment's RHF
+  is solved in the field of the others and the field is rebuilt until all fragments are
+  self-consistent;
 * energies from the reference expectation values <H_x> and <H_xy> of the Hamiltonian partition
   (Eqs. NHx, NHxy, clusterH), with pairs counted once.
 
