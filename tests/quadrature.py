@@ -161,35 +161,51 @@ def _gauss2d(i, A, j, B, k, C, l, D, p, P, q, Q, u2):
     return np.sum(W * f, axis=(1, 2)) * np.exp(-const) / (L11 * L22)
 
 
+def _eri_element(ao1, ao2, ao3, ao4):
+    """(mu nu|lambda sigma) of four unscaled contracted Cartesian AOs by quadrature."""
+    (A, ca, ea, wa), (B, cb, eb, wb), (C, cc, ec, wc), (D, cd, ed, wd) = ao1, ao2, ao3, ao4
+    v = 0.0
+    for a, xa in zip(ea, wa):
+        for b, xb in zip(eb, wb):
+            p = a + b
+            P = (a * A + b * B) / p
+            Kab = math.exp(-a * b / p * np.sum((A - B) ** 2))
+            for c, xc in zip(ec, wc):
+                for d, xd in zip(ed, wd):
+                    qq = c + d
+                    Q = (c * C + d * D) / qq
+                    Kcd = math.exp(-c * d / qq * np.sum((C - D) ** 2))
+                    rho = p * qq / (p + qq)
+                    t = GL_T
+                    u2 = rho * t * t / (1 - t * t)
+                    du = math.sqrt(rho) * (1 - t * t) ** -1.5
+                    f = np.ones_like(t)
+                    for dd in range(3):
+                        f = f * _gauss2d(ca[dd], A[dd], cb[dd], B[dd], cc[dd], C[dd], cd[dd], D[dd],
+                                         p, P[dd], qq, Q[dd], u2)
+                    v += xa * xb * xc * xd * Kab * Kcd * (2 / math.sqrt(math.pi)) * np.sum(GL_WT * du * f)
+    return v
+
+
 def eri(q1: QShells, q2: QShells):
     """(mu nu|lambda sigma), mu nu in q1, lambda sigma in q2, by quadrature."""
     n1, n2 = q1.n, q2.n
     out = np.zeros((n1, n1, n2, n2))
-    for m1, (A, ca, ea, wa) in enumerate(q1.aos):
-        for m2, (B, cb, eb, wb) in enumerate(q1.aos):
-            for m3, (C, cc, ec, wc) in enumerate(q2.aos):
-                for m4, (D, cd, ed, wd) in enumerate(q2.aos):
-                    v = 0.0
-                    for a, xa in zip(ea, wa):
-                        for b, xb in zip(eb, wb):
-                            p = a + b
-                            P = (a * A + b * B) / p
-                            Kab = math.exp(-a * b / p * np.sum((A - B) ** 2))
-                            for c, xc in zip(ec, wc):
-                                for d, xd in zip(ed, wd):
-                                    qq = c + d
-                                    Q = (c * C + d * D) / qq
-                                    Kcd = math.exp(-c * d / qq * np.sum((C - D) ** 2))
-                                    rho = p * qq / (p + qq)
-                                    t = GL_T
-                                    u2 = rho * t * t / (1 - t * t)
-                                    du = math.sqrt(rho) * (1 - t * t) ** -1.5
-                                    f = np.ones_like(t)
-                                    for dd in range(3):
-                                        f = f * _gauss2d(ca[dd], A[dd], cb[dd], B[dd], cc[dd], C[dd], cd[dd], D[dd],
-                                                         p, P[dd], qq, Q[dd], u2)
-                                    v += xa * xb * xc * xd * Kab * Kcd * (2 / math.sqrt(math.pi)) * np.sum(GL_WT * du * f)
+    for m1, o1 in enumerate(q1.aos):
+        for m2, o2 in enumerate(q1.aos):
+            for m3, o3 in enumerate(q2.aos):
+                for m4, o4 in enumerate(q2.aos):
+                    v = _eri_element(o1, o2, o3, o4)
                     out[m1, m2, m3, m4] = v * q1.scale[m1] * q1.scale[m2] * q2.scale[m3] * q2.scale[m4]
+    return out
+
+
+def eri_diagonal(q: QShells):
+    """(mu nu|mu nu) for every AO pair of q, shape (n, n), by quadrature."""
+    out = np.zeros((q.n, q.n))
+    for m1, o1 in enumerate(q.aos):
+        for m2, o2 in enumerate(q.aos):
+            out[m1, m2] = _eri_element(o1, o2, o1, o2) * (q.scale[m1] * q.scale[m2]) ** 2
     return out
 
 

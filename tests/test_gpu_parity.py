@@ -310,3 +310,20 @@ def test_fragment_status_after_iterate(box8):
         assert st["homo_lumo_gap"][x] > 0
         assert abs(st["homo_lumo_gap"][x] - gap) < 1e-5
     ctx.close()
+
+
+def test_neighbour_list_hand_placed_cutoff():
+    """The GPU pair list keeps a fragment pair exactly when its minimum atom-atom distance is below
+    the cutoff: hand-placed two-atom fragments with closest distances 8 - 1e-9, 8, 8 + 1e-9 A
+    (the same geometry pins the oracle's pair list), cutoffs 5e-10 A either side of 8 A."""
+    fef = _fef()
+    from tests.test_oracle_pins import _hand_placed_clusters
+    from oracle.fef import Fragments
+    import types
+    system = _hand_placed_clusters()
+    host = types.SimpleNamespace(system=system, nf=system.n_frag,
+                                 atoms=[system.frag_atoms(x) for x in range(system.n_frag)])
+    for cut in (8.0 - 5e-10, 8.0 + 5e-10, 8.0 + 2e-9, 1.0):
+        ctx = fef.fef_create_system(system, fef.fef_default_options(cutoff_A=cut, schwarz=0.0))
+        assert fef.fef_stats(ctx)["n_pairs"] == len(Fragments.neighbour_pairs(host, cut)), cut
+        ctx.close()

@@ -643,3 +643,143 @@ def test_far_field_fock_is_energy_derivative():
         ep = sum(ref.far_terms(Dp)[1].values())
         em = sum(ref.far_terms(Dm)[1].values())
         assert abs((ep - em) / (2 * h) - np.sum(Dl * om[x])) < 1e-8
+
+
+# ----------------------------------------------------------------------------------------- screening and pairs
+# The sum over y != x of Eq. wc / Eq. dp2e is cut at a fragment-pair cutoff and the shell quartets
+# are screened by the Schwarz bound (both readings of the configurations): these pins fix the
+# oracle's screening factors, quartet counts and pair list by brute force.
+
+def _shell_ranges(ls):
+    out, k = [], 0
+    for l in ls:
+        n = (l + 1) * (l + 2) // 2
+        out.append(range(k, k + n))
+        k += n
+    return out
+
+
+def _schwarz_from_diagonal(diag, ls):
+    """Q_ab = sqrt(max_{mu in a, nu in b} |(mu nu|mu nu)|) from the AO-pair diagonal (n, n)."""
+    r = _shell_ranges(ls)
+    return np.array([[math.sqrt(np.abs(diag[np.ix_(ra, rb)]).max()) for rb in r] for ra in r])
+
+
+def test_schwarz_factors_against_quadrature():
+    """or_schwarz on contracted s, p and d shells: Q_ab from the diagonal ERIs (mu nu|mu nu) computed
+    by brute-force quadrature of the Gaussian transform of 1/r12, independent of the Obara-Saika code."""
+    o, q = _oracle_set(TINY), Q.QShells(TINY)
+    Qo = o.schwarz()
+    Qq = _schwarz_from_diagonal(Q.eri_diagonal(q), [s[1] for s in TINY])
+    assert Qo.shape == (3, 3)
+    assert np.abs(Qo - Qo.T).max() == 0.0
+    assert np.abs(Qo - Qq).max() < 1e-11 * Qq.max()
+
+
+def _spd_dimer(seed=3, r=3.1):
+    """Two water-like fragments whose oxygen carries s, p and d shells (a d-shell fragment)."""
+    rb, rg = S._streams(seed, 2)
+    bs = [S.random_basis_set(rb, S.SHELLS_HEAVY_SPD), S.random_basis_set(rb, S.SHELLS_H)]
+    z, w = S.water_geometry()
+    u = S.random_unit(rg)
+    frags = [(z, w @ S.random_rotation(rg).T + k * r * u) for k in range(2)]
+    return S._assemble(frags, bs, [np.array([0, 1, 1])] * 2, "spd dimer")
+
+
+@pytest.fixture(scope="module")
+def spd_pair():
+    system = _spd_dimer()
+    sh = [I.fragment_shells(system, x) for x in range(2)]
+    full = {k: I.eri_block(sh[k[0]], sh[k[1]]) for k in [(0, 0), (1, 1), (0, 1)]}
+    return sh, full
+
+
+def test_schwarz_factors_d_fragment(spd_pair):
+    """or_schwarz of a fragment with d shells equals sqrt of the largest diagonal element of each
+    shell pair's block, taken by brute force from the full (unscreened) ERI tensor."""
+    sh, full = spd_pair
+    for k in range(2):
+        n = sh[k].n_ao
+        diag = np.einsum("ijij->ij", full[(k, k)].reshape(n, n, n, n))
+        Qb = _schwarz_from_diagonal(diag, list(sh[k].l))
+        assert np.abs(sh[k].schwarz() - Qb).max() < 1e-14 * Qb.max()
+
+
+def test_quartet_count_brute_force(spd_pair):
+    """or_count_quartets equals a brute-force count over all a <= b in x, c <= d in y of
+    Q_ab Q_cd >= tau, a quartet whose product equals tau is kept, and every dropped quartet has
+    max |(ab|cd)| <= Q_ab Q_cd < tau (Schwarz inequality), zeroed by the screened ERI block."""
+    sh, full = spd_pair
+    Qx, Qy = sh[0].schwarz(), sh[1].schwarz()
+    rx, ry = _shell_ranges(list(sh[0].l)), _shell_ranges(list(sh[1].l))
+    quartets = [(a, b, c, d) for a in range(sh[0].n_sh) for b in range(a, sh[0].n_sh)
+                for c in range(sh[1].n_sh) for d in range(c, sh[1].n_sh)]
+    prods = np.array([Qx[a, b] * Qy[c, d] for a, b, c, d in quartets])
+    assert len(quartets) == (10 * 11 // 2) * (10 * 11 // 2)
+    tie = float(np.sort(prods)[len(prods) // 3])
+    for tau in [0.0, 1e-12, 1e-6, float(np.median(prods)), tie, np.nextafter(tie, np.inf), 2 * prods.max()]:
+        brute = int(sum(1 for p in prods if p >= tau))
+        assert I.count_quartets(sh[0], sh[1], Qx, Qy, tau) == brute, tau
+    assert I.count_quartets(sh[0], sh[1], Qx, Qy, tie) == I.count_quartets(sh[0], sh[1], Qx, Qy,
+                                                                          np.nextafter(tie, np.inf)) + \
+        int(np.sum(prods == tie))
+    tau = float(np.median(prods))
+    e_full = full[(0, 1)]
+    e_scr = I.eri_block(sh[0], sh[1], Qx, Qy, tau)
+    n_dropped = 0
+    for a in range(sh[0].n_sh):
+        for b in range(sh[0].n_sh):
+            for c in range(sh[1].n_sh):
+                for d in range(sh[1].n_sh):
+                    blk = np.ix_(rx[a], rx[b], ry[c], ry[d])
+                    if Qx[a, b] * Qy[c, d] < tau:
+                        n_dropped += 1
+                        assert np.abs(e_full[blk]).max() <= Qx[a, b] * Qy[c, d] * (1 + 1e-12) + 1e-300
+                        assert not np.any(e_scr[blk])
+                    else:
+                        assert np.array_equal(e_scr[blk], e_full[blk])
+    assert n_dropped > 0
+
+
+def _hand_placed_clusters():
+    """Two-atom fragments along the axes, so that inter-fragment distances are exact doubles:
+    the closest atoms of fragments 0 and 1 are 8 - 1e-9 A apart (second atom of 0, first of 1),
+    of fragments 0 and 2 exactly 8 A, of fragments 1 and 3 8 + 1e-9 A, of fragments 2 and 3
+    8 - 1e-9 A; every other pair is farther than 8 A apart."""
+    e = 1e-9
+    xyz = np.array([
+        [0.0, 0.0, 0.0], [-0.74, 0.0, 0.0],                  # fragment 0
+        [8.0 - e, 0.0, 0.0], [8.0 - e + 0.74, 0.0, 0.0],      # fragment 1
+        [-0.74, 0.0, -8.0], [-0.74, -0.74, -8.0],              # fragment 2
+        [8.0 - e + 0.74, 0.0, 8.0 + e], [-0.74, -0.74, -16.0 + e],  # fragment 3
+    ])
+    bs = S.random_basis_set(np.random.default_rng(0), S.SHELLS_H)
+    return S.System(Z=np.ones(8, np.int32), xyz=xyz, frag_of_atom=np.repeat(np.arange(4), 2).astype(np.int32),
+                    charge=np.zeros(4, np.int32), basis_of_atom=np.zeros(8, np.int32), basis_sets=[bs],
+                    name="hand-placed pairs")
+
+
+HAND_PLACED_PAIRS_8A = [(0, 1), (2, 3)]
+
+
+def test_neighbour_pairs_hand_placed():
+    """Fragments.neighbour_pairs keeps (x < y) exactly when the minimum inter-fragment atom-atom
+    distance is below the cutoff: against the hand-placed set and an explicit loop over all atoms."""
+    import types
+    system = _hand_placed_clusters()
+    atoms = [system.frag_atoms(x) for x in range(system.n_frag)]
+    host = types.SimpleNamespace(system=system, nf=system.n_frag, atoms=atoms)
+    got = Fragments.neighbour_pairs(host, 8.0)
+    assert got == HAND_PLACED_PAIRS_8A
+    brute = []
+    for x in range(system.n_frag):
+        for y in range(x + 1, system.n_frag):
+            dmin = min(math.dist(system.xyz[i], system.xyz[j]) for i in atoms[x] for j in atoms[y])
+            if dmin < 8.0:
+                brute.append((x, y))
+    assert got == brute
+    assert Fragments.neighbour_pairs(host, 8.0 + 2e-9) == [(0, 1), (0, 2), (1, 3), (2, 3)]
+    assert Fragments.neighbour_pairs(host, 8.0 - 5e-10) == [(0, 1), (2, 3)]
+    assert Fragments.neighbour_pairs(host, 8.0 + 5e-10) == [(0, 1), (0, 2), (2, 3)]
+    assert Fragments.neighbour_pairs(host, None) == [(x, y) for x in range(4) for y in range(x + 1, 4)]
+    assert Fragments.neighbour_pairs(host, 1.0) == []
