@@ -192,6 +192,21 @@ def cpu_baseline(seconds=12.0):
                       f"first {done} of {len(pairs)} fragment pairs ({quartets} shell quartets, {dt:.1f} s)"}
 
 
+def oracle_time_to_converge():
+    """The oracle's own FEF solve of the whole workload to 1e-8 Eh (integrals, superposition start,
+    macro-iterations), wall clock on the host cores: the time-to-convergence the GPU legs are compared with."""
+    from oracle.fef import Fragments
+    from synth import systems as S
+    t0 = time.perf_counter()
+    fr = Fragments(S.water_box(N_WATER, seed=0), cutoff_A=CUTOFF_A, schwarz=SCHWARZ)
+    t1 = time.perf_counter()
+    res = fr.solve(e_tol=E_TOL)
+    t2 = time.perf_counter()
+    return {"time_to_1e-8_s": t2 - t0, "integrals_s": t1 - t0, "n_macro": res["n_macro"],
+            "E_tot": res["energies"]["E_tot"],
+            "cores": int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))}
+
+
 # ----------------------------------------------------------------------------------------- reference arm
 def run_reference(args, ws, rank):
     if rank != 0:
@@ -340,6 +355,25 @@ def main():
         mopts = fef.fef_default_options(cutoff_A=CUTOFF_A, schwarz=SCHWARZ, e_tol=E_TOL, precision=fef.FEF_MIXED,
                                         exact_engine=DF)
         mixed_ms, mixed_step_ms, mres = variant(mopts)
+        # the FP32 core on its own (no FP64 reference): one whole-density build of the isolated densities
+        # against the FP64 build of the same densities, per-fragment energies and Fock elements (not timed)
+        wctx = fef.fef_create_system(system, opts, stream=stream.cuda_stream)
+        fef.fef_noninteracting_scf(wctx)
+        Diso = fef.fef_get_densities(wctx)
+        F64w = fef.fef_build_fock(wctx, Diso)
+        E64w, _, _ = fef.fef_energies(wctx)
+        wctx.close()
+        wopts = fef.fef_default_options(cutoff_A=CUTOFF_A, schwarz=SCHWARZ, e_tol=E_TOL, precision=fef.FEF_MIXED,
+                                        mixed_build=fef.FEF_MIXED_WHOLE, use_graph=0)
+        wctx = fef.fef_create_system(system, wopts, stream=stream.cuda_stream)
+        F32w = fef.fef_build_fock(wctx, Diso)
+        E32w, _, _ = fef.fef_energies(wctx)
+        wctx.close()
+        dEw = E32w - E64w
+        fp32_whole = {"max_dE_x": float(np.abs(dEw).max()), "rms_dE_x": float(np.sqrt(np.mean(dEw ** 2))),
+                      "mean_dE_x": float(dEw.mean()), "max_dF": float(np.abs(F32w - F64w).max()),
+                      "note": "FP32-core J-engine of the whole isolated density (no FP64 reference) against the "
+                              "FP64 build, per fragment (hartree)"}
         # E_M2 (Eq. EM2) on the converged FP64 state: one public call (intra-fragment integrals
         # recomputed, canonical orbitals, four quarter-transforms, second-order sum), wall clock
         m2ctx = fef.fef_create_system(system, opts, stream=stream.cuda_stream)
@@ -401,6 +435,7 @@ def main():
     jms_per_build = float(np.mean([h["jengine_ms"] for h in last["hist"]]))  # every build of the FP64 solve
     flops_build = algorithmic_flops(st["class_quartets"])
     achieved = flops_build / (jms_per_build * 1e-3)
+    jms32 = float(np.mean([h["jengine_ms"] for h in mres["hist"] if h["fp32"]] or [float("nan")]))
     value = quartets / (total_ms * 1e-3)
     so, sl, sn, ex, co = system.flat_basis()
     h2d = sum(a.nbytes for a in (system.Z, system.xyz, system.frag_of_atom, system.basis_of_atom, system.charge,
@@ -425,8 +460,13 @@ def main():
                  "fp64_equivalent_tflops": flops_build / (float(np.mean([h["jengine_ms"] for h in dres["hist"]])) * 1e-3) / 1e12},
         "mixed_fp64_reference": {**summary(mixed64_ms, mixed64_step_ms, m64res), "exact_engine": "fp64"},
         "mixed": {**summary(mixed_ms, mixed_step_ms, mres), "exact_engine": "df64",
-                  "jengine_fp32_ms_per_build": float(np.mean([h["jengine_ms"] for h in mres["hist"] if h["fp32"]]
-                                                             or [0.0]))},
+                  "jengine_fp32_ms_per_build": jms32,
+                  "fp32_whole_build": fp32_whole,
+                  "roofline_fp32": {"bound": "alu", "achieved": flops_build / (jms32 * 1e-3) / 1e12,
+                                    "peak": fp32_probe / 1e12, "unit": "TFLOP/s",
+                                    "frac": flops_build / (jms32 * 1e-3) / fp32_probe,
+                                    "peak_source": "measured: FP32 FMA-chain probe (fef_measure_fma_peak) in this run",
+                                    "kernel": "k_jengine32<LP,LQ> (FP32-core class kernels on three streams)"}},
         "mixed_learned": {**summary(ml_ms, ml_step_ms, mlres), "exact_engine": "df64",
                           "train_samples": int(sum(len(x) for x in Xs)),
                           "train_loss": net_loss},
@@ -449,6 +489,7 @@ def main():
     }
     if ws == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline()
+        line["cpu_baseline"]["oracle_fef_solve"] = oracle_time_to_converge()
     print(json.dumps(line), flush=True)
     if pg:
         pg.destroy_process_group()

@@ -53,13 +53,13 @@ typedef enum {
     FEF_ERR_GEOM = 3,           /* odd electron count, coincident atoms, bad fragment map */
     FEF_ERR_CUDA = 4,           /* a CUDA call failed; message has the CUDA error string */
     FEF_ERR_NOT_CONVERGED = 5,  /* SCF or FEF iteration hit its iteration limit */
-    FEF_ERR_NUMERIC = 6,        /* NaN/Inf met in a Fock matrix, density or energy */
-    FEF_ERR_TIMEOUT = 7         /* a bounded device-side wait ran out (error flag set by a kernel) */
+    FEF_ERR_NUMERIC = 6         /* NaN/Inf met in a Fock matrix, density or energy */
 } fef_status;
 
 enum { FEF_FP64 = 0, FEF_MIXED = 1 };
 enum { FEF_ENGINE_FP64 = 0, FEF_ENGINE_DF64 = 1 };
 enum { FEF_START_SUPERPOSITION = 0, FEF_START_LEARNED = 1, FEF_START_GIVEN = 2 };
+enum { FEF_MIXED_INCREMENT = 0, FEF_MIXED_WHOLE = 1 };
 
 /* Molecular system split into fragments (Theory, "Fragment Mean Field": Hilbert space partition
  * into fragment subspaces, monomer-centred basis). */
@@ -107,7 +107,6 @@ typedef struct {
     int32_t use_graph;       /* 1 (default): each macro-iteration (fragment SCF, Fock build, read-back) is
                                 one CUDA graph launch, captured on first use per kind of build; 0: eager
                                 launches */
-    int32_t deterministic;   /* reserved: 1 requests run-to-run identical sums */
     double mixed_switch;     /* MIXED: coarse FP32-core macro-iterations until |dE| < mixed_switch */
     int32_t exact_engine;    /* J-engine of the FP64-accurate builds (every build in FEF_FP64, the
                                 reference builds in FEF_MIXED): FEF_ENGINE_FP64 = native FP64 FMA,
@@ -119,11 +118,18 @@ typedef struct {
                                 electrons about its nuclear-charge centroid, y's potential Taylor-expanded
                                 to second order about x's centroid (omega_x and the pair energies gain these
                                 terms; the truncation error falls as R^-5); 0 (default): the plain cutoff */
+    int32_t mixed_build;     /* what fef_build_fock computes in FEF_MIXED: FEF_MIXED_INCREMENT (default) =
+                                J[D_ref] + J_fp32[D - D_ref] relative to the last FP64-accurate build (an
+                                FP64 build when there is none); FEF_MIXED_WHOLE = the FP32-core J-engine
+                                of the whole density, J_fp32[D] (FP64 accumulation, FP64 intra-fragment
+                                G, V^y and energies), which becomes an inexact reference.  fef_iterate
+                                ignores it (its schedule is fixed, see precision). */
 } fef_options;
 
 /* Fill *opt with the defaults: FP64, no cutoff, schwarz 1e-12, e_tol 1e-8, micro_e_tol 1e-11,
  * micro_comm_tol 1e-9, max_macro 100, max_micro 200, diis_size 8, superposition start,
- * mixed_switch 1e-6, use_graph 1, exact_engine FEF_ENGINE_FP64, far_field 0. */
+ * mixed_switch 1e-6, use_graph 1, exact_engine FEF_ENGINE_FP64, far_field 0, mixed_build
+ * FEF_MIXED_INCREMENT. */
 void fef_default_options(fef_options* opt);
 
 /* Build a context: validate and copy the inputs, then on the device normalise the basis, build
@@ -148,9 +154,11 @@ fef_status fef_ao_layout(const fef_ctx* ctx, int32_t* n_ao_per_frag, int64_t* of
  * current densities.  F_out: packed output, or NULL.  on_device: 1 if D/F_out are device pointers.
  * The inter-fragment J is the fused McMurchie-Davidson J-engine: no ERI tensor is formed.  With
  * opt.far_field, omega_x also holds the multipole field of the fragments beyond the cutoff.
- * FP64 mode: the full FP64 J-engine.  MIXED: J[D^y] = J[D_ref] + J_fp32[D^y - D_ref] relative to the
- * last FP64 build of this context; without one the build is FP64 and becomes the reference.
- * Errors: ARG, CUDA, NUMERIC. */
+ * FP64 mode: the full FP64 J-engine.  MIXED with opt.mixed_build = FEF_MIXED_INCREMENT:
+ * J[D^y] = J[D_ref] + J_fp32[D^y - D_ref] relative to the last FP64 build of this context; without
+ * one the build is FP64 and becomes the reference.  MIXED with FEF_MIXED_WHOLE: J_fp32[D^y], the
+ * FP32-core J-engine of the whole density (its error against the FP64 build is what the FP32 core
+ * alone costs).  Errors: ARG, CUDA, NUMERIC. */
 fef_status fef_build_fock(fef_ctx* ctx, const double* D, double* F_out, int on_device);
 
 /* FEF self-consistency (Theory, "Fragment Mean Field": omega_x relaxed to self-consistency).
@@ -234,7 +242,10 @@ fef_status fef_history(const fef_ctx* ctx, int32_t max_records, double* records,
  * F)]/2 + own nuclear repulsion.  Host arrays, each nullable.  Errors: ARG, CUDA. */
 fef_status fef_fragment_status(const fef_ctx* ctx, int32_t* micro_iters, double* homo_lumo_gap, double* E_scf);
 
-/* Message of the last failing call on ctx (or of the last failed fef_create when ctx is NULL). */
+/* Message of the last failing call on ctx, or, when ctx is NULL, of the last failed context-free call
+ * (fef_create, fef_fragment_rhf_noalloc, fef_measure_fma_peak) made by the calling host thread (the
+ * context-free message is thread-local; the pointer stays valid until that thread's next failing
+ * context-free call). */
 const char* fef_last_error(const fef_ctx* ctx);
 
 /* Free the context and all its device memory.  NULL is a no-op. */
@@ -255,16 +266,20 @@ typedef struct {
                                tiers run concurrently.  0: one launch per class pair over whole ket
                                ranges (ket_chunk unused).  2: the same class-pair kernels launched on
                                three streams (graph branches when captured), largest classes first,
-                               so that they run concurrently (ket_chunk unused). */
+                               so that they run concurrently; ket_chunk cuts the tiles of the register
+                               classes into chunks (one warp each; the float-float and shared-memory
+                               classes use whole ranges). */
     int32_t ket_chunk[25];  /* ket primitive pairs per item for the class pair L_bra*5 + L_ket
                                (L = l_a + l_b of the shell pair); 0 = the partner's whole class range */
     double tuned_ms;        /* J-engine time of one build measured by fef_autotune (0: not tuned) */
 } fef_tile_plan;
 
 /* Read or replace the plan of one engine (FEF_JENGINE_FP64: FP64 builds; FEF_JENGINE_FP32: the FP32-core
- * builds of FEF_MIXED; FEF_JENGINE_DF64: float-float builds).  Default plans use whole ket ranges,
- * persistent (1) for FEF_JENGINE_FP64 and concurrent class-pair launches (2) for the other two.  Setting rebuilds
- * the work queues (synchronous).  Errors: ARG, CUDA. */
+ * builds of FEF_MIXED; FEF_JENGINE_DF64: float-float builds).  Default plans: persistent (1) for
+ * FEF_JENGINE_FP64 and concurrent class-pair launches (2) for the other two; whole ket ranges, except that
+ * an s/p or register d class whose whole-range work items would give fewer than 32 warps per SM (small
+ * workloads) is cut into 64-pair ket chunks in the FP64 and FP32 plans.  Setting rebuilds the work queues
+ * (synchronous).  Errors: ARG, CUDA. */
 fef_status fef_get_tile_plan(const fef_ctx* ctx, int32_t engine, fef_tile_plan* out);
 fef_status fef_set_tile_plan(fef_ctx* ctx, int32_t engine, const fef_tile_plan* plan);
 
@@ -333,8 +348,9 @@ fef_status fef_set_warm_start(fef_ctx* ctx, fef_mlp* m);
 /* Batched closed-shell RHF of independent fragments in frozen fields, for callers that cannot
  * allocate device memory.  The paper has no counterpart: this is a service entry point of this
  * library.  Some callers own every byte of device memory themselves (a dynamics or embedding
- * driver with a fixed budget or its own pool), run while a CUDA stream is being captured, or must
- * not serialise on cudaMalloc/cudaFree inside a time step; this call allocates nothing.
+ * driver that runs under a fixed device-memory budget or hands out memory from its own pool), or
+ * must not pay for, or serialise on, cudaMalloc/cudaFree inside a time step; this call allocates
+ * nothing.
  *
  * It runs the same kernels as the fragment RHF of fef_iterate (canonical orthogonaliser
  * X = U s^{-1/2} dropping s < 1e-7, then the device micro loop: F = h + omega + C D, Pulay DIIS,
@@ -354,13 +370,17 @@ fef_status fef_set_warm_start(fef_ctx* ctx, fef_mlp* m);
  *   D_out, F_out        DEVICE packed outputs: converged densities and their Fock matrices.
  *   E_scf               DEVICE [n_frag] output: tr[D(h + omega + F)]/2 + e_nn.
  *   opt                 micro_e_tol, micro_comm_tol, max_micro, diis_size are used (NULL: defaults).
- *   cuda_stream         stream for all work; the call synchronises it before returning.
+ *   cuda_stream         stream for all work; the call reads the fragments' status back and
+ *                       synchronises the stream before returning.
  * Limits: the batch must fit the 16 MiB scratch: per fragment n_x^2 doubles of orthogonaliser and
  * 2*diis_size*max_n^2 doubles of DIIS history (about 700 13-AO fragments with diis_size 8), else
- * FEF_ERR_ARG.  Set-up: the first call on each device resolves the scratch address with
- * cudaGetSymbolAddress; make it before any stream capture.  All calls share the scratch and it keeps
- * the last call's contents: calls whose device work overlaps race.  Errors (message from
- * fef_last_error(NULL)): ARG, CUDA, NOT_CONVERGED (outputs hold the last iterate), NUMERIC. */
+ * FEF_ERR_ARG, checked on the host before any device work.  Set-up: the first call on each device,
+ * with that device current, resolves the scratch's device address with cudaGetSymbolAddress and
+ * caches it; make that first call before any stream capture begins.  All calls share the scratch
+ * and it keeps the last call's contents (the call clears what must start at zero): calls whose
+ * device work overlaps (two streams, two host threads) race on it.  Errors (message from
+ * fef_last_error(NULL) on the calling thread): ARG (also when a device bounds check fails), CUDA,
+ * NOT_CONVERGED (outputs hold the last iterate), NUMERIC. */
 fef_status fef_fragment_rhf_noalloc(int32_t n_frag, const int32_t* n_ao, const int32_t* n_occ, const double* e_nn,
                                     const double* S, const double* h, const double* omega, const double* eri_c,
                                     const double* D_start, double* D_out, double* F_out, double* E_scf,

@@ -17,14 +17,14 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libfef.so")
 
-FEF_OK, FEF_ERR_ARG, FEF_ERR_BASIS, FEF_ERR_GEOM, FEF_ERR_CUDA, FEF_ERR_NOT_CONVERGED, FEF_ERR_NUMERIC, \
-    FEF_ERR_TIMEOUT = range(8)
+FEF_OK, FEF_ERR_ARG, FEF_ERR_BASIS, FEF_ERR_GEOM, FEF_ERR_CUDA, FEF_ERR_NOT_CONVERGED, FEF_ERR_NUMERIC = range(7)
 FEF_FP64, FEF_MIXED = 0, 1
 FEF_ENGINE_FP64, FEF_ENGINE_DF64 = 0, 1
 FEF_JENGINE_FP64, FEF_JENGINE_FP32, FEF_JENGINE_DF64 = 0, 1, 2
 FEF_START_SUPERPOSITION, FEF_START_LEARNED, FEF_START_GIVEN = 0, 1, 2
+FEF_MIXED_INCREMENT, FEF_MIXED_WHOLE = 0, 1
 STATUS_NAMES = {0: "FEF_OK", 1: "FEF_ERR_ARG", 2: "FEF_ERR_BASIS", 3: "FEF_ERR_GEOM", 4: "FEF_ERR_CUDA",
-                5: "FEF_ERR_NOT_CONVERGED", 6: "FEF_ERR_NUMERIC", 7: "FEF_ERR_TIMEOUT"}
+                5: "FEF_ERR_NOT_CONVERGED", 6: "FEF_ERR_NUMERIC"}
 
 EXPORTED = ["fef_default_options", "fef_create", "fef_ao_layout", "fef_build_fock", "fef_iterate", "fef_energies",
             "fef_get_densities", "fef_set_densities", "fef_stats", "fef_last_error", "fef_destroy",
@@ -58,8 +58,9 @@ class fef_options(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int32), ("cutoff_A", ctypes.c_double), ("schwarz", ctypes.c_double),
                 ("e_tol", ctypes.c_double), ("micro_e_tol", ctypes.c_double), ("micro_comm_tol", ctypes.c_double),
                 ("max_macro", ctypes.c_int32), ("max_micro", ctypes.c_int32), ("diis_size", ctypes.c_int32),
-                ("start", ctypes.c_int32), ("use_graph", ctypes.c_int32), ("deterministic", ctypes.c_int32),
-                ("mixed_switch", ctypes.c_double), ("exact_engine", ctypes.c_int32), ("far_field", ctypes.c_int32)]
+                ("start", ctypes.c_int32), ("use_graph", ctypes.c_int32),
+                ("mixed_switch", ctypes.c_double), ("exact_engine", ctypes.c_int32), ("far_field", ctypes.c_int32),
+                ("mixed_build", ctypes.c_int32)]
 
 
 class fef_tile_plan(ctypes.Structure):
@@ -373,7 +374,8 @@ def fef_fragment_rhf_noalloc(n_ao, n_occ, e_nn, S, h, omega, eri_c, D_start, D_o
 
     n_ao, n_occ, e_nn: host sequences.  S, h, omega (or None), eri_c, D_start (or None), D_out,
     F_out, E_scf: CUDA torch tensors (float64, packed as documented in fef.h).  For callers that
-    cannot allocate device memory themselves, e.g. inside a stream capture or under a fixed budget.
+    cannot allocate device memory themselves, e.g. a host code that runs under a fixed device-memory
+    budget or its own pool, or a time step that must not serialise on cudaMalloc/cudaFree.
     """
     nao = np.ascontiguousarray(n_ao, np.int32)
     nocc = np.ascontiguousarray(n_occ, np.int32)

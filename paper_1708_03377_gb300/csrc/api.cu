@@ -96,6 +96,8 @@ struct Buffers {
     bool have_ref = false;
     bool ref_exact = false;  // the reference field came from an FP64 build
     float* boys32 = nullptr;
+    double* rec_resid = nullptr;  // workspace of the FP32-core records' charge-conserving rounding
+    float* fc_qmin = nullptr;     // [n_frag*kClasses] smallest Schwarz factor per fragment and class
     int* iters = nullptr;
     int* err_flag = nullptr;
     double* diis = nullptr;
@@ -126,7 +128,7 @@ long long launches_so_far() { return g_launches.load(std::memory_order_relaxed);
 
 using namespace fef;
 
-static std::string g_create_error;
+static thread_local std::string g_create_error;  // message of the last failed context-free call
 
 namespace fef {
 void set_global_error(const char* msg) { g_create_error = msg; }
@@ -166,10 +168,10 @@ extern "C" void fef_default_options(fef_options* o)
     o->diis_size = 8;
     o->start = FEF_START_SUPERPOSITION;
     o->use_graph = 1;
-    o->deterministic = 0;
     o->mixed_switch = 1e-6;
     o->exact_engine = FEF_ENGINE_FP64;
     o->far_field = 0;
+    o->mixed_build = FEF_MIXED_INCREMENT;
 }
 
 // ---------------------------------------------------------------------------------------------- helpers
@@ -179,7 +181,6 @@ static void check_device_flags(fef_ctx* c, const char* where)
     ck(cudaMemcpyAsync(&flag, c->buf->err_flag, sizeof(int), cudaMemcpyDeviceToHost, c->stream), where);
     ck(cudaStreamSynchronize(c->stream), where);
     if (flag & kErrNumeric) throw Error{FEF_ERR_NUMERIC, std::string(where) + ": NaN/Inf in a matrix or energy"};
-    if (flag & kErrTimeout) throw Error{FEF_ERR_TIMEOUT, std::string(where) + ": device wait limit reached"};
     if (flag & kErrBounds) throw Error{FEF_ERR_ARG, std::string(where) + ": device bounds check failed"};
 }
 
@@ -244,7 +245,10 @@ static void build_fock_device(fef_ctx* c, int kind)
         if (kind == kBuildFP32Ref)
             ck(cudaMemsetAsync(b->Dh_ref[L], 0, sizeof(double) * b->njh[L], s), "zero reference");
     }
-    if (fp32) ck(launch_delta_density(d, b->Dh_ref, s), "delta density");
+    if (fp32) {
+        ck(launch_delta_density(d, b->Dh_ref, s), "delta density");
+        ck(launch_fp32_records(d, b->Dh_ref, b->rec_resid, s), "fp32 records");
+    }
     const bool df = !fp32 && c->opt.exact_engine == FEF_ENGINE_DF64;
     if (df) ck(launch_df_density(d, s), "df64 density");
     const int2* tiles[kClasses][kClasses];
@@ -484,8 +488,9 @@ extern "C" fef_status fef_create(const fef_geometry* g, const fef_basis* bs, con
                     std::isfinite(o.micro_comm_tol),
                 FEF_ERR_ARG, "options: micro_e_tol and micro_comm_tol must be finite and > 0");
         require(o.mixed_switch >= 0.0 && std::isfinite(o.mixed_switch), FEF_ERR_ARG, "options: bad mixed_switch");
+        require(o.mixed_build == FEF_MIXED_INCREMENT || o.mixed_build == FEF_MIXED_WHOLE, FEF_ERR_ARG,
+                "options: bad mixed_build");
         c->stream = static_cast<cudaStream_t>(cuda_stream);
-        ck(cudaGetDevice(&c->device), "cudaGetDevice");
 
         const int na = g->n_atoms, nf = g->n_frag;
         c->n_atoms = na;
@@ -623,8 +628,27 @@ extern "C" fef_status fef_create(const fef_geometry* g, const fef_basis* bs, con
                 }
                 frag_npp[x * kClasses + L] = (int)pp_sp[L].size() - frag_pp0[x * kClasses + L];
             }
+        // J-engine bra order: inside each fragment's class range, primitive pairs by increasing exponent
+        // p = a + b, so that a warp's 32 bra pairs are of similar extent and take the same Boys branch
+        std::vector<int> pp_perm[kClasses];
+        for (int L = 0; L < kClasses; ++L) {
+            const int n = (int)pp_sp[L].size();
+            std::vector<double> pexp(n);
+            for (int g2 = 0; g2 < n; ++g2) {
+                const int sp = pp_sp[L][g2], ij = pp_ij[L][g2];
+                pexp[g2] = p_exp[sh_p0[sp_a[sp]] + (ij >> 4)] + p_exp[sh_p0[sp_b[sp]] + (ij & 15)];
+            }
+            pp_perm[L].resize(n);
+            for (int g2 = 0; g2 < n; ++g2) pp_perm[L][g2] = g2;
+            for (int x = 0; x < nf; ++x) {
+                auto first = pp_perm[L].begin() + frag_pp0[x * kClasses + L];
+                std::stable_sort(first, first + frag_npp[x * kClasses + L],
+                                 [&](int u, int v) { return pexp[u] < pexp[v]; });
+            }
+        }
 
         // ---- device upload
+        ck(cudaGetDevice(&c->device), "cudaGetDevice");  // every host-side check comes before this
         c->buf = new Buffers();
         Buffers* b = c->buf;
         cudaStream_t s = c->stream;
@@ -680,6 +704,8 @@ extern "C" fef_status fef_create(const fef_geometry* g, const fef_basis* bs, con
         float4* ppPlo[kClasses];
         double* ppK[kClasses];
         float* ppQ[kClasses];
+        double* ppRp[kClasses];
+        int max_npp = 1;
         for (int L = 0; L < kClasses; ++L) {
             int n = (int)pp_sp[L].size();
             d.n_pp[L] = n;
@@ -699,15 +725,24 @@ extern "C" fef_status fef_create(const fef_geometry* g, const fef_basis* bs, con
             b->Jh_ref[L] = b->alloc<double>((size_t)nh(L) * n, "hermite field ref");
             ppK[L] = b->alloc<double>(n, "prim pairs");
             ppQ[L] = b->alloc<float>(n, "prim pairs");
+            ppRp[L] = b->alloc<double>(n, "prim pairs");
+            d.pp_rp[L] = ppRp[L];
+            d.pp_perm[L] = b->upload(pp_perm[L], s, "prim pairs");
+            d.pp_rec32[L] = b->alloc<float>((size_t)rec32_len(L) * n, "fp32 records");
+            max_npp = std::max(max_npp, n);
             d.pp_P[L] = ppP[L];
             d.pp_Pf[L] = ppPf[L];
             d.pp_K[L] = ppK[L];
             d.pp_Q[L] = ppQ[L];
             b->njh[L] = nh(L) * n;
             d.pp_Dh[L] = b->alloc<double>((size_t)nh(L) * n, "hermite density");
+            d.pp_u[L] = b->alloc<double>((size_t)nh(L) * n, "hermite weights");
             b->Jh[L] = b->alloc<double>((size_t)nh(L) * n, "hermite field");
             d.pp_Jh[L] = b->Jh[L];
         }
+        b->rec_resid = b->alloc<double>(max_npp, "fp32 record residues");
+        b->fc_qmin = b->alloc<float>((size_t)nf * kClasses, "class Schwarz minimum");
+        d.fc_qmin = b->fc_qmin;
         b->boys = b->alloc<double>((size_t)kBoysRows * kBoysRowLen, "boys");
         d.boys = b->boys;
         b->boys32 = b->alloc<float>((size_t)kBoys32Rows * kBoysRowLen, "boys32");
@@ -727,7 +762,7 @@ extern "C" fef_status fef_create(const fef_geometry* g, const fef_basis* bs, con
         ck(launch_boys_table(b->boys, s), "boys table");
         ck(launch_boys_table32(b->boys, b->boys32, s), "boys table fp32");
         ck(launch_ao_scale(d, ao_scale, ao_global, nullptr, s), "ao scale");
-        ck(launch_prim_pairs(d, ppP, ppPf, ppK, ppPr, s), "prim pairs");
+        ck(launch_prim_pairs(d, ppP, ppPf, ppK, ppPr, ppRp, s), "prim pairs");
         ck(launch_df_setup(d, ppPhi, ppPlo, boysdf, s), "df64 pair data");
         b->S = b->alloc<double>(c->mat_total, "S");
         b->h = b->alloc<double>(c->mat_total, "h");
@@ -841,6 +876,7 @@ extern "C" fef_status fef_create(const fef_geometry* g, const fef_basis* bs, con
             int4* tasks_d = b->upload(tasks, s, "intra tasks");
             ck(launch_intra_eri(d, tasks_d, (int)tasks.size(), eri, s), "intra eri");
             ck(launch_schwarz(d, eri, sp_Q, ppQ, s), "schwarz");
+            ck(launch_class_qmin(d, b->fc_qmin, s), "class Schwarz minimum");
             b->eric = b->alloc<double>(c->coff_total, "eric");
             ck(launch_coulomb_exchange(d, eri, b->eric, s), "coulomb-exchange");
             ck(cudaStreamSynchronize(s), "intra eri");
@@ -1047,7 +1083,10 @@ extern "C" fef_status fef_build_fock(fef_ctx* c, const double* D, double* F_out,
     }
     require(c->have_density, FEF_ERR_ARG, "fef_build_fock: no densities given or set");
     clear_flags(c);
-    build_fock_internal(c, c->opt.precision == FEF_MIXED && c->buf->ref_exact ? kBuildFP32Inc : kBuildFP64);
+    int kind = kBuildFP64;
+    if (c->opt.precision == FEF_MIXED)
+        kind = c->opt.mixed_build == FEF_MIXED_WHOLE ? kBuildFP32Ref : (c->buf->ref_exact ? kBuildFP32Inc : kBuildFP64);
+    build_fock_internal(c, kind);
     if (F_out) copy_packed(c, F_out, c->buf->F, on_device, cudaMemcpyDeviceToHost);
     check_device_flags(c, "fef_build_fock");
     float ms = 0.f;

@@ -47,11 +47,18 @@ constexpr int kMaxLTot = 2 * kMaxLPair;
 
 // ------------------------------------------------------------------------------------------ Boys
 // FP32 grid-Taylor table for the mixed-precision J-engine: same grid, F_{m+j}(T_k)/j! for
-// j = 0..4 (truncation below 0.025^5/5! ~ 8e-11, far under FP32 resolution), switch to the
-// asymptotic form at T = 25 where the neglected exp(-T) terms are below 1e-10 of F_m.
+// j = 0..4 (truncation below 0.025^5/5! ~ 8e-11, far under FP32 resolution), up to T = 30.05; above
+// the table the asymptotic form is used.  The FP32 J-engine switches to the asymptotic form at
+// T = 25 for L = L_P + L_Q <= 2 and at T = 30 for L = 3, 4, where the neglected exp(-T) terms are
+// at most 1.4e-9 of F_L (F_2 at 25, F_4 at 30), below the FP32 resolution.
 constexpr int kBoys32Order = 4;
-constexpr int kBoys32Rows = 502;                  // T up to 25.05
-constexpr float kBoys32Tmax = 25.0f;
+constexpr int kBoys32Rows = 602;                  // T up to 30.05
+constexpr float kFp32SwitchLow = 25.0f;           // asymptotic Boys for L <= 2 (FP32 core)
+constexpr float kFp32SwitchHigh = 30.0f;          // ... for L = 3, 4
+// 2/sqrt(pi) as a float pair (hi + lo): a single rounded FP32 constant would scale every quartet
+// below the asymptotic switch by the same relative error (5.2e-8), a bias, not a random error.
+constexpr float kTwoOverSqrtPiHi = 1.12837922573089599609375f;
+constexpr float kTwoOverSqrtPiLo = -5.8635382771399236e-08f;
 
 // Grid-Taylor table: rows T_k = k h, k = 0..kBoysRows-1; per row, for m = 0..kBoysM-1 a block of
 // kBoysOrder+1 coefficients F_{m+j}(T_k)/j! (j = 0..kBoysOrder), padded to kBoysBlock doubles; the
@@ -176,6 +183,49 @@ __device__ __forceinline__ void boys_fp32(const float* __restrict__ table, float
 #pragma unroll
         for (int m = 1; m <= L; ++m) F[m] = F[m - 1] * ((2.0f * m - 1.0f) * half_inv_T);
     }
+}
+
+// 1/sqrt(x) in FP32: the hardware estimate refined by one Newton step y (3 - x y^2) / 2, with the
+// residual 1 - x y^2 formed by an FMA, so that the result is within about one unit in the last place
+// and its error has no systematic sign (a biased 1/R would shift the whole long-range Coulomb field).
+// The hardware estimate of 1/sqrt(x) (rsqrt.approx.ftz: normal inputs only, which holds for every
+// argument here), without the library's subnormal-input handling.
+__device__ __forceinline__ float rsqrt_approx(float x)
+{
+    float y;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+__device__ __forceinline__ float rsqrt_nr(float x)
+{
+    const float y = rsqrt_approx(x);
+    const float h = x * y;
+    const float e = fmaf(-h, y, 1.0f);
+    return fmaf(0.5f * y, e, y);
+}
+
+// 1/sqrt(x) in FP64 from an FP32 estimate s of relative error e0 (up to ~1e-5): one step of the
+// third-order iteration y = s (1 + e/2 + 3 e^2/8), e = 1 - x s^2 (the binomial series of (1 - e)^{-1/2}
+// to second order), truncation error 5 e0^3 / 16, below the FP64 resolution.  Five FP64 operations.
+__device__ __forceinline__ double rsqrt_from_seed(double x, float seed)
+{
+    const double s = f2d(seed);
+    const double h = x * s;
+    const double e = fma(-h, s, 1.0);
+    const double t = fma(0.375, e, 0.5);
+    return fma(s * e, t, s);
+}
+
+// Knuth's two-sum accumulation (error-free transformation of hi + a): hi becomes the rounded sum and
+// lo collects the rounding errors, so that hi + lo carries the running sum to ~2^-48.
+__device__ __forceinline__ void two_sum_acc(float& hi, float& lo, float a)
+{
+    const float s = hi + a;
+    const float bp = s - hi;
+    const float e = (hi - (s - bp)) + (a - bp);
+    hi = s;
+    lo += e;
 }
 
 __device__ __forceinline__ int boys_row(float Tf)
@@ -335,7 +385,6 @@ __device__ inline double prim_norm(double a, int l)
 // Device error flags (bit mask), read by the host after a launch sequence.
 enum : int {
     kErrNumeric = 1,   // NaN/Inf in a matrix or energy
-    kErrTimeout = 2,   // a bounded wait ran out
     kErrBounds = 4,    // an index failed a bounds check
     kErrNotConv = 8,   // a fragment RHF hit its iteration limit
 };

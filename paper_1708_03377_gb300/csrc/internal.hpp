@@ -76,6 +76,11 @@ struct Dev {
     double* pp_Jh[kClasses];
     const float4* pp_Pr[kClasses];   // FP32 (P - anchor of the fragment, p) for the mixed J-engine
     float* pp_Dh32[kClasses];        // FP32 Hermite density difference D_P - D_P^ref (mixed builds)
+    const double* pp_rp[kClasses];   // p^{-1/2} per primitive pair (asymptotic J-engine path)
+    double* pp_u[kClasses];          // FP64 J-engine weights u = p^{-1/2} D_P (SoA like pp_Dh), per build
+    const int* pp_perm[kClasses];    // bra order of the J-engine: each fragment's class range sorted by p
+    float* pp_rec32[kClasses];       // FP32-core record per primitive pair (rec32_len(L) floats, see jengine.cu)
+    const float* fc_qmin;            // [n_frag*kClasses] smallest Schwarz factor of each fragment's class
     const float4* pp_Phi[kClasses];  // df64 (P, p): high floats ...
     const float4* pp_Plo[kClasses];  // ... and low floats (float-float J-engine)
     float2* pp_Dhdf[kClasses];       // df64 Hermite density (hi, lo)
@@ -89,6 +94,14 @@ struct Dev {
     const float2* boysdf;            // df64 copy of the FP64 Boys table
     int* err_flag;
 };
+
+// FP32-core record of a primitive pair of class L, rebuilt for every FP32-core build (jengine.cu):
+// (P - anchor of its fragment, p) | (k_hi, k_lo, Schwarz factor, 0) | u[0..nh(L)-1], padded to a
+// multiple of 4 floats, with k = (sqrt(pi)/2) p^{-1/2} as a float pair and u = p^{-1/2} (D_P - D_P^ref).
+__host__ __device__ constexpr int rec32_len(int L)
+{
+    return 8 + (((L + 1) * (L + 2) * (L + 3) / 6 + 3) & ~3);
+}
 
 // fragment owning shell pair s (frag_sp0 is ascending)
 __device__ inline int frag_of_shellpair(const Dev& d, int s)
@@ -148,7 +161,13 @@ cudaError_t launch_prepare(const Dev& d, const double* xyz_A, double* atom_xyz, 
 cudaError_t launch_boys_table(double* table, cudaStream_t s);
 cudaError_t launch_ao_scale(const Dev& d, double* ao_scale, int n_ao_total, const int* ao_frag, cudaStream_t s);
 cudaError_t launch_prim_pairs(const Dev& d, double4_32a* P[kClasses], float4* Pf[kClasses], double* K[kClasses],
-                              float4* Pr[kClasses], cudaStream_t s);
+                              float4* Pr[kClasses], double* rp[kClasses], cudaStream_t s);
+// smallest Schwarz factor of each fragment's primitive pairs of each class (after launch_schwarz)
+cudaError_t launch_class_qmin(const Dev& d, float* qmin, cudaStream_t s);
+// FP32-core records of every class for the density difference D - D_ref (Hermite densities in pp_Dh,
+// reference in Dh_ref, NULL entries = 0), with charge-conserving rounding of each fragment's u[0]
+// (resid: workspace of max n_pp doubles)
+cudaError_t launch_fp32_records(const Dev& d, double* const Dh_ref[kClasses], double* resid, cudaStream_t s);
 cudaError_t launch_boys_table32(const double* table64, float* table32, cudaStream_t s);
 // Dh32 = float(Dh - Dh_ref) for every class
 cudaError_t launch_delta_density(const Dev& d, double* const Dh_ref[kClasses], cudaStream_t s);
@@ -183,9 +202,10 @@ cudaError_t launch_jengine(const Dev& d, const int2* tiles[kClasses][kClasses], 
                            int mode, cudaStream_t s);
 cudaError_t launch_jengine_df(const Dev& d, const int2* tiles[kClasses][kClasses], const int* n_tiles, float tau,
                               cudaStream_t s);
-// one class pair's per-class kernel (mode as launch_jengine), for concurrent launches on forked streams
+// one class pair's per-class kernel (mode as launch_jengine), for concurrent launches on forked streams;
+// chunk > 0 (register classes): each tile's ket range cut into nchunk chunks of chunk pairs
 cudaError_t launch_jengine_class(const Dev& d, int LP, int LQ, const int2* t, int n, float tau, int mode,
-                                 cudaStream_t s);
+                                 cudaStream_t s, int chunk = 0, int nchunk = 1);
 cudaError_t launch_jengine_big_class(const Dev& d, int LP, int LQ, const int2* t, int n, float tau, int fp32,
                                      cudaStream_t s);
 cudaError_t launch_jengine_df_class(const Dev& d, int LP, int LQ, const int2* t, int n, float tau, cudaStream_t s);

@@ -59,7 +59,11 @@ __global__ void k_hermite_density(Dev d, int L, const double* __restrict__ D)
         }
     }
     double sc = d.pp_K[L][g] * kSqrt2Pi52 / p;
-    for (int k = 0; k < nh(L); ++k) d.pp_Dh[L][(size_t)k * npp + g] = acc[k] * sc;
+    const double rp = d.pp_rp[L][g];
+    for (int k = 0; k < nh(L); ++k) {
+        d.pp_Dh[L][(size_t)k * npp + g] = acc[k] * sc;
+        d.pp_u[L][(size_t)k * npp + g] = acc[k] * sc * rp;
+    }
 }
 
 cudaError_t launch_hermite_density(const Dev& d, const double* D, cudaStream_t s)
@@ -158,15 +162,18 @@ __device__ __forceinline__ void ketbuf_flush32(const KetBuf32& kb, int cnt, doub
     __syncwarp();
 }
 
+// FP64 ket flush with the ket's field scale (sqrt(pi)/2) q^{-1/2} applied to the summed column
 template <int NQ>
-__device__ __forceinline__ void ketbuf_flush(const KetBuf& kb, int cnt, double* __restrict__ QJ, size_t nQ, int lane)
+__device__ __forceinline__ void ketbuf_flush_scaled(const KetBuf& kb, int cnt, double* __restrict__ QJ, size_t nQ,
+                                                   const double* __restrict__ rq, int lane)
 {
     __syncwarp();
     if (lane < cnt * NQ) {
         double sum = 0.0;
 #pragma unroll 8
         for (int r = 0; r < 32; ++r) sum += kb.v[r * kKetBufLd + lane];
-        atomicAdd(QJ + (size_t)(lane % NQ) * nQ + kb.k[lane / NQ], sum);
+        const int k = kb.k[lane / NQ];
+        atomicAdd(QJ + (size_t)(lane % NQ) * nQ + k, sum * (kSqrtPiHalf * __ldg(rq + k)));
     }
     __syncwarp();
 }
@@ -174,10 +181,49 @@ __device__ __forceinline__ void ketbuf_flush(const KetBuf& kb, int cnt, double* 
 // One warp per tile = (fragment pair, up to 32 bra primitive pairs of class LP in one member x)
 // against the ket primitive pairs [kb, ke) (offsets in the class-LQ range of the other member y,
 // LQ <= LP; the pair's two J directions are both produced, so the member with the larger class is
-// put on the bra side).  Lane i owns bra pair P_i: its centre, Hermite density and
-// Hermite field accumulator stay in registers.  Ket data are warp-uniform loads.  The field on the
-// ket pair is staged in the warp's KetBuf and summed over the lanes once per batch of 32 / NQ kets.
-// Shell quartets with Q_ab Q_cd < tau contribute nothing (Schwarz screening at shell level).
+// put on the bra side).  Lane i owns the bra pair at position tl.y + i of x's class range in the
+// order pp_perm (increasing exponent): its centre, Hermite density and Hermite field accumulator stay
+// in registers.  Ket data are warp-uniform loads.  The field on the ket pair is staged in the warp's
+// KetBuf and summed over the lanes once per batch of 32 / NQ kets.  Shell quartets with
+// Q_ab Q_cd < tau contribute nothing (Schwarz screening at shell level).
+//
+// Boys function: for T = alpha |PQ|^2 >= kBoysTmax the asymptotic form F_n = (2n-1)!! / (2T)^n
+// sqrt(pi/T) / 2 holds to the FP64 resolution of the table's own switch, and the quartet prefactor
+// collapses, rsqrt(p+q) F_n(T) (-2 alpha)^n = (sqrt(pi)/2) p^{-1/2} q^{-1/2} (-1)^n (2n-1)!! / R^{2n+1}:
+// the Hermite integrals of two point multipoles, one reciprocal square root per quartet.  The warp
+// takes this path when all its lanes are beyond the switch (the large majority of inter-fragment
+// quartets); otherwise the lanes below it evaluate the tabulated Boys function.  The per-pair factors
+// are kept out of the quartet loop: both sides contract the weights u = p^{-1/2} D_P (pp_u) with the
+// unit-normalised Hermite integrals R' = R / ((sqrt(pi)/2) p^{-1/2} q^{-1/2}) (base R'^{(n)} =
+// (-1)^n (2n-1)!! / R^{2n+1} beyond the switch, (2/sqrt(pi)) sqrt(alpha) F_n (-2 alpha)^n below it),
+// and the bra field is scaled by (sqrt(pi)/2) p^{-1/2} once per tile, the ket field by
+// (sqrt(pi)/2) q^{-1/2} once per flushed batch.
+// Below the asymptotic switch, the unit-normalised Hermite base of the FP64 core:
+// r F_n(T) (-2 alpha)^n / (aP rq) with r = (p+q)^{-1/2}, 1/aP = inv_aP and 1/rq = q rq (see jtile_fp64).
+// Kept out of line so that the asymptotic path of the quartet loop carries none of its instructions.
+template <int L>
+struct Base64 {
+    double v[L + 1];
+};
+template <int L>
+__device__ __noinline__ Base64<L> fp64_table_base(const double* __restrict__ boys, double p, double q, double rq,
+                                                 double inv_aP, double R2, float Tf)
+{
+    Base64<L> b;
+    const double r = rsqrt(p + q);
+    const double alpha = p * q * (r * r);
+    double F[L + 1];
+    boys_fp64<L>(boys, alpha * R2, boys_row(Tf), F);
+    double pre = r * inv_aP * (q * rq);
+    const double m2a = -2.0 * alpha;
+#pragma unroll
+    for (int n = 0; n <= L; ++n) {
+        b.v[n] = pre * F[n];
+        pre *= m2a;
+    }
+    return b;
+}
+
 template <int LP, int LQ>
 __device__ __forceinline__ void jtile_fp64(const Dev& d, const int2 tl, const int kb, const int ke, const float tau,
                                            const int lane, const KetBuf& kbuf)
@@ -189,26 +235,30 @@ __device__ __forceinline__ void jtile_fp64(const Dev& d, const int2 tl, const in
     const int x = (tl.x & 1) ? d.pair_y[pr] : d.pair_x[pr];
     const int y = (tl.x & 1) ? d.pair_x[pr] : d.pair_y[pr];
     const int bra_end = d.frag_pp0[x * kClasses + LP] + d.frag_npp[x * kClasses + LP];
-    const int Pg = tl.y + lane;
-    const bool valid = Pg < bra_end;
-    const int Pl = valid ? Pg : tl.y;
+    const bool valid = tl.y + lane < bra_end;
+    const int Pl = d.pp_perm[LP][valid ? tl.y + lane : tl.y];
     const int nP = d.n_pp[LP], nQ = d.n_pp[LQ];
     const double4_32a Pd = d.pp_P[LP][Pl];
     const float4 Pf = d.pp_Pf[LP][Pl];
+    const double rpP = d.pp_rp[LP][Pl];
+    const double aP = kSqrtPiHalf * rpP;                        // bra field scale
+    const double inv_aP = (1.0 / kSqrtPiHalf) * (Pd.w * rpP);   // 1/aP = (2/sqrt(pi)) sqrt(p)
     const float qP = valid ? d.pp_Q[LP][Pl] : 0.0f;
     double DP[NP], JP[NP];
 #pragma unroll
     for (int i = 0; i < NP; ++i) {
-        DP[i] = valid ? d.pp_Dh[LP][(size_t)i * nP + Pl] : 0.0;
+        DP[i] = valid ? d.pp_u[LP][(size_t)i * nP + Pl] : 0.0;
         JP[i] = 0.0;
     }
     const int kc = d.frag_pp0[y * kClasses + LQ];
     const int k0 = kc + kb;
     const int k1 = kc + min(ke, d.frag_npp[y * kClasses + LQ]);
+    if (k0 >= k1) return;  // a ket chunk beyond the partner's range
     const double4_32a* __restrict__ QP = d.pp_P[LQ];
     const float4* __restrict__ QPf = d.pp_Pf[LQ];
+    const double* __restrict__ QRP = d.pp_rp[LQ];
     const float* __restrict__ QQ = d.pp_Q[LQ];
-    const double* __restrict__ QD = d.pp_Dh[LQ];
+    const double* __restrict__ QD = d.pp_u[LQ];
     double* __restrict__ QJ = d.pp_Jh[LQ];
     int cnt = 0;  // kets staged in kbuf
     for (int k = k0; k < k1; ++k) {
@@ -222,20 +272,31 @@ __device__ __forceinline__ void jtile_fp64(const Dev& d, const int2 tl, const in
         for (int j = 0; j < NQ; ++j) DQ[j] = __ldg(QD + (size_t)j * nQ + k);
         const double X = Pd.x - Qd.x, Y = Pd.y - Qd.y, Z = Pd.z - Qd.z;
         const double R2 = fma(X, X, fma(Y, Y, Z * Z));
-        const double r = rsqrt(Pd.w + Qd.w);
-        const double alpha = Pd.w * Qd.w * (r * r);
-        const double T = alpha * R2;
         const float Xf = Pf.x - Qf.x, Yf = Pf.y - Qf.y, Zf = Pf.z - Qf.z;
-        const float Tf = __fdividef(Pf.w * Qf.w, Pf.w + Qf.w) * fmaf(Xf, Xf, fmaf(Yf, Yf, Zf * Zf));
-        double F[L + 1];
-        boys_fp64<L>(d.boys, T, boys_row(Tf), F);
+        const float R2f = fmaf(Xf, Xf, fmaf(Yf, Yf, Zf * Zf));
+        const float pqf = Pf.w * Qf.w, sf = Pf.w + Qf.w;
+        const bool asym = pqf * R2f >= (float)kBoysTmax * sf;
+        // asymptotic (point-multipole) form for every lane; lanes below the switch overwrite it
+        const double yv = rsqrt_from_seed(R2, rsqrt_approx(R2f));
         double base[L + 1];
-        double pre = keep ? r : 0.0;
-        const double m2a = -2.0 * alpha;
+        base[0] = keep ? yv : 0.0;
+        if constexpr (L > 0) {
+            const double ny2 = -(yv * yv);
+            static_for<L>([&](auto N) {
+                constexpr int n = decltype(N)::value;
+                if constexpr (n == 0)
+                    base[1] = base[0] * ny2;
+                else
+                    base[n + 1] = base[n] * (double(2 * n + 1) * ny2);
+            });
+        }
+        if (!__all_sync(0xffffffffu, asym)) {
+            if (!asym) {
+                const Base64<L> t = fp64_table_base<L>(d.boys, Pd.w, Qd.w, __ldg(QRP + k), inv_aP, R2,
+                                                       __fdividef(pqf, sf) * R2f);
 #pragma unroll
-        for (int n = 0; n <= L; ++n) {
-            base[n] = pre * F[n];
-            pre *= m2a;
+                for (int n = 0; n <= L; ++n) base[n] = keep ? t.v[n] : 0.0;
+            }
         }
         double R[NR];
         md_R<L, double>(R, base, X, Y, Z);
@@ -243,28 +304,28 @@ __device__ __forceinline__ void jtile_fp64(const Dev& d, const int2 tl, const in
         hermite_ket_stage<NP, NQ>(R, DP, kbuf, cnt, lane);
         if (lane == 0) kbuf.k[cnt] = k;
         if (++cnt == kBatch) {
-            ketbuf_flush<NQ>(kbuf, cnt, QJ, (size_t)nQ, lane);
+            ketbuf_flush_scaled<NQ>(kbuf, cnt, QJ, (size_t)nQ, QRP, lane);
             cnt = 0;
         }
     }
-    if (cnt > 0) ketbuf_flush<NQ>(kbuf, cnt, QJ, (size_t)nQ, lane);
+    if (cnt > 0) ketbuf_flush_scaled<NQ>(kbuf, cnt, QJ, (size_t)nQ, QRP, lane);
     if (valid) {
 #pragma unroll
-        for (int i = 0; i < NP; ++i) atomicAdd(d.pp_Jh[LP] + (size_t)i * nP + Pg, JP[i]);
+        for (int i = 0; i < NP; ++i) atomicAdd(d.pp_Jh[LP] + (size_t)i * nP + Pl, JP[i] * aP);
     }
 }
 
-// Mixed-precision core: the same contraction on the FP32 Hermite density difference
-// Dh32 = D_P - D_P^ref, with FP32 geometry (centres relative to each fragment's first atom plus the
-// FP64-computed anchor offset), FP32 Boys, R recursion and contractions.  The bra field is flushed to
-// FP64 registers every 16 ket pairs and all global accumulation is FP64 (atomics on pp_Jh).
+// Mixed-precision core for the d-shell register classes (L_P = 3, 4): the contraction on the FP32
+// Hermite density difference Dh32 = D_P - D_P^ref, with FP32 geometry (centres relative to each
+// fragment's first atom plus the FP64-computed anchor offset), FP32 Boys, R recursion and
+// contractions.  The bra field is flushed to FP64 registers every 16 ket pairs and all global
+// accumulation is FP64 (atomics on pp_Jh).  Bra lanes in natural order.
 template <int LP, int LQ>
-__device__ __forceinline__ void jtile_fp32(const Dev& d, const int2 tl, const int kb, const int ke, const float tau,
-                                           const int lane, const KetBuf32& kbuf)
+__device__ __forceinline__ void jtile_fp32_dclass(const Dev& d, const int2 tl, const int kb, const int ke,
+                                                  const float tau, const int lane, const KetBuf32& kbuf)
 {
     constexpr int NP = nh(LP), NQ = nh(LQ), L = LP + LQ, NR = nh(LP + LQ);
     constexpr int kBatch = 32 / NQ;
-    // tile.x = 2 * pair + swap: the bra fragment is the pair member holding the larger class
     const int pr = tl.x >> 1;
     const int x = (tl.x & 1) ? d.pair_y[pr] : d.pair_x[pr];
     const int y = (tl.x & 1) ? d.pair_x[pr] : d.pair_y[pr];
@@ -305,7 +366,7 @@ __device__ __forceinline__ void jtile_fp32(const Dev& d, const int2 tl, const in
         for (int j = 0; j < NQ; ++j) DQ[j] = __ldg(QD + (size_t)j * nQ + k);
         const float X = (Pr.x - Qr.x) + ox, Y = (Pr.y - Qr.y) + oy, Z = (Pr.z - Qr.z) + oz;
         const float R2 = fmaf(X, X, fmaf(Y, Y, Z * Z));
-        const float r = rsqrtf(Pr.w + Qr.w);
+        const float r = rsqrt_nr(Pr.w + Qr.w);
         const float alpha = Pr.w * Qr.w * (r * r);
         float F[L + 1];
         boys_fp32<L>(d.boys32, alpha * R2, F);
@@ -342,27 +403,306 @@ __device__ __forceinline__ void jtile_fp32(const Dev& d, const int2 tl, const in
     }
 }
 
-// One warp per tile over the partner's whole class range (one launch per class pair).
+// The ket-side field of a batch of nk consecutive kets of the FP32 core: the lane owning a (ket,
+// component) slot sums its column over the 32 bra lanes, multiplies by the ket's scale k = k_hi + k_lo
+// (kept as a float pair so that its rounding does not repeat in every partner's contribution) and adds
+// the result to the FP64 accumulator.
+template <int NQ, int RQ>
+__device__ __forceinline__ void ketbuf_flush_rec(const KetBuf32& kb, int nk, int k0, double* __restrict__ QJ,
+                                                 size_t nQ, const float* __restrict__ QR, int lane)
+{
+    __syncwarp();
+    if (lane < nk * NQ) {
+        float sum = 0.0f;
+#pragma unroll 8
+        for (int r = 0; r < 32; ++r) sum += kb.v[r * kKetBufLd + lane];
+        const int k = k0 + lane / NQ;
+        const float2 kk = __ldg(reinterpret_cast<const float2*>(QR + (size_t)k * RQ + 4));
+        atomicAdd(QJ + (size_t)(lane % NQ) * nQ + k, f2d(fmaf(sum, kk.y, sum * kk.x)));
+    }
+    __syncwarp();
+}
+
+// NQ consecutive floats from 16-byte aligned p (vector loads; padding beyond NQ is not used)
+template <int NQ>
+__device__ __forceinline__ void load_weights(const float* __restrict__ p, float* u)
+{
+    static_for<(NQ + 3) / 4>([&](auto V) {
+        constexpr int v = decltype(V)::value;
+        const float4 w = __ldg(reinterpret_cast<const float4*>(p) + v);
+        if constexpr (4 * v + 0 < NQ) u[4 * v + 0] = w.x;
+        if constexpr (4 * v + 1 < NQ) u[4 * v + 1] = w.y;
+        if constexpr (4 * v + 2 < NQ) u[4 * v + 2] = w.z;
+        if constexpr (4 * v + 3 < NQ) u[4 * v + 3] = w.w;
+    });
+}
+
+// Below the asymptotic switch, the unit-normalised Hermite base of the FP32 core:
+// (2/sqrt(pi)) sqrt(alpha) F_n(T) (-2 alpha)^n, n = 0..L, alpha = pq/(p+q), T = alpha R^2.  Kept out
+// of line so that the common (asymptotic) path of the quartet loop carries none of its instructions.
+template <int L>
+struct Base32 {
+    float v[L + 1];
+};
+template <int L>
+__device__ __noinline__ Base32<L> fp32_table_base(const float* __restrict__ boys32, float pq, float sq, float R2)
+{
+    Base32<L> b;
+    const float r = rsqrt_nr(sq);
+    const float alpha = pq * (r * r);
+    float F[L + 1];
+    boys_fp32<L>(boys32, alpha * R2, F);
+    const float sa = alpha * rsqrt_nr(alpha);
+    float pre = fmaf(kTwoOverSqrtPiHi, sa, kTwoOverSqrtPiLo * sa);
+    const float m2a = -2.0f * alpha;
+#pragma unroll
+    for (int n = 0; n <= L; ++n) {
+        b.v[n] = pre * F[n];
+        pre *= m2a;
+    }
+    return b;
+}
+
+// Mixed-precision core for the s/p classes (L_P, L_Q <= 2), on the weights u = p^{-1/2} (D_P - D_P^ref)
+// of the FP32 records.  With R' the Hermite integrals of the unit-normalised Coulomb kernel
+// (R = (sqrt(pi)/2) p^{-1/2} q^{-1/2} R'; R' of the point multipoles, derivatives of 1/R, beyond the
+// asymptotic switch), J_P = k_P sum_Q R' u_Q and J_Q = k_Q sum_P R' u_P with k = (sqrt(pi)/2) p^{-1/2}.
+// FP32 geometry (each bra centre relative to the ket fragment's first atom, rounded once per tile),
+// Boys function, recursion and contractions; 1/R by rsqrt_nr; the bra field in a two-sum float pair
+// folded at the end of every ket batch; k applied as a float pair; all global accumulation FP64.
+// The records' weights carry each fragment's total charge exactly to one rounding (k_fp32_charge_fix),
+// and rounding the scale factors as float pairs keeps per-pair roundings from repeating coherently
+// over all partners: what remains is the per-quartet FP32 rounding.  Schwarz screening is evaluated
+// only in tiles whose smallest bra factor times the partner class's smallest ket factor is below tau
+// (SCREEN).  B bra pairs per lane (positions tl.y + lane and tl.y + 32 + lane for B = 2): the per-ket
+// work (record loads, loop, votes, staging of the ket-side field) is shared by B quartets.
+template <int LP, int LQ, int B, bool SCREEN>
+__device__ __forceinline__ void jtile_fp32_sp(const Dev& d, const int x, const int y, const int pos0, const int kb,
+                                              const int ke, const float tau, const int lane, const KetBuf32& kbuf)
+{
+    constexpr int NP = nh(LP), NQ = nh(LQ), L = LP + LQ, NR = nh(LP + LQ);
+    constexpr int kBatch = 32 / NQ;
+    constexpr int RP = rec32_len(LP), RQ = rec32_len(LQ);
+    constexpr float kTsw = L <= 2 ? kFp32SwitchLow : kFp32SwitchHigh;
+    const int bra_end = d.frag_pp0[x * kClasses + LP] + d.frag_npp[x * kClasses + LP];
+    const int kc = d.frag_pp0[y * kClasses + LQ];
+    const int k0 = kc + kb;
+    const int k1 = kc + min(ke, d.frag_npp[y * kClasses + LQ]);
+    if (k0 >= k1) return;  // a ket chunk beyond the partner's range
+    const double* ay = d.atom_xyz + 3 * d.frag_atom0[y];
+    float px[B], py[B], pz[B], pP[B], qP[B], kh[B], kl[B], uP[B][NP], JP[B][NP], Jhi[B][NP], Jlo[B][NP];
+    int Pl[B];
+    bool valid[B];
+#pragma unroll
+    for (int b = 0; b < B; ++b) {
+        const int pos = pos0 + 32 * b + lane;
+        valid[b] = pos < bra_end;
+        Pl[b] = d.pp_perm[LP][valid[b] ? pos : pos0];
+        const float* __restrict__ brec = d.pp_rec32[LP] + (size_t)Pl[b] * RP;
+        const float4 b1 = __ldg(reinterpret_cast<const float4*>(brec) + 1);
+        const double4_32a Pd = d.pp_P[LP][Pl[b]];
+        px[b] = (float)(Pd.x - ay[0]);
+        py[b] = (float)(Pd.y - ay[1]);
+        pz[b] = (float)(Pd.z - ay[2]);
+        pP[b] = (float)Pd.w;
+        qP[b] = b1.z;
+        kh[b] = b1.x;
+        kl[b] = b1.y;
+        load_weights<NP>(brec + 8, uP[b]);
+#pragma unroll
+        for (int i = 0; i < NP; ++i) {
+            if (!valid[b]) uP[b][i] = 0.0f;
+            JP[b][i] = Jhi[b][i] = Jlo[b][i] = 0.0f;
+        }
+    }
+    const float* __restrict__ QR = d.pp_rec32[LQ];
+    double* __restrict__ QJ = d.pp_Jh[LQ];
+    const size_t nQ = (size_t)d.n_pp[LQ];
+    for (int kq = k0; kq < k1; kq += kBatch) {
+        const int nk = min(kBatch, k1 - kq);
+        const float* __restrict__ qr = QR + (size_t)kq * RQ;
+        for (int c = 0; c < nk; ++c, qr += RQ) {
+            bool keep[B];
+#pragma unroll
+            for (int b = 0; b < B; ++b) keep[b] = true;
+            if constexpr (SCREEN) {
+                const float qQ = __ldg(qr + 6);
+                bool any = false;
+#pragma unroll
+                for (int b = 0; b < B; ++b) {
+                    keep[b] = qP[b] * qQ >= tau;
+                    any = any || keep[b];
+                }
+                if (!__any_sync(0xffffffffu, any)) {
+                    float* row = kbuf.v + lane * kKetBufLd + c * NQ;
+#pragma unroll
+                    for (int j = 0; j < NQ; ++j) row[j] = 0.0f;
+                    continue;
+                }
+            }
+            const float4 q0 = __ldg(reinterpret_cast<const float4*>(qr));
+            float uQ[NQ];
+            load_weights<NQ>(qr + 8, uQ);
+            float stage[NQ];
+#pragma unroll
+            for (int j = 0; j < NQ; ++j) stage[j] = 0.0f;
+#pragma unroll
+            for (int b = 0; b < B; ++b) {
+                const float X = px[b] - q0.x, Y = py[b] - q0.y, Z = pz[b] - q0.z;
+                const float R2 = fmaf(X, X, fmaf(Y, Y, Z * Z));
+                const float pq = pP[b] * q0.w, sq = pP[b] + q0.w;
+                const bool asym = pq * R2 >= kTsw * sq;
+                // point-multipole form for every lane; lanes below the switch overwrite it
+                float yv = rsqrt_nr(R2);
+                if constexpr (SCREEN) {
+                    if (!keep[b]) yv = 0.0f;
+                }
+                float base[L + 1];
+                base[0] = yv;
+                if constexpr (L > 0) {
+                    const float ny2 = -(yv * yv);
+                    static_for<L>([&](auto N) {
+                        constexpr int n = decltype(N)::value;
+                        if constexpr (n == 0)
+                            base[1] = base[0] * ny2;
+                        else
+                            base[n + 1] = base[n] * (float(2 * n + 1) * ny2);
+                    });
+                }
+                if (!__all_sync(0xffffffffu, asym)) {
+                    if (!asym) {
+                        const Base32<L> t = fp32_table_base<L>(d.boys32, pq, sq, R2);
+#pragma unroll
+                        for (int n = 0; n <= L; ++n) base[n] = (SCREEN && !keep[b]) ? 0.0f : t.v[n];
+                    }
+                }
+                float R[NR];
+                md_R<L, float>(R, base, X, Y, Z);
+                hermite_bra<NP, NQ, float>(R, uQ, JP[b]);
+                // this bra's share of the ket-side field, (-1)^{|j|} sum_i R[i + j] u_P[i]
+                static_for<NQ>([&](auto Jc) {
+                    constexpr TUV bq = htuv(decltype(Jc)::value);
+                    float sum = 0.0f;
+                    static_for<NP>([&](auto I) {
+                        constexpr TUV a = htuv(decltype(I)::value);
+                        sum = fmaf(R[hidx(a.t + bq.t, a.u + bq.u, a.v + bq.v)], uP[b][decltype(I)::value], sum);
+                    });
+                    if constexpr (((bq.t + bq.u + bq.v) & 1) != 0)
+                        stage[decltype(Jc)::value] -= sum;
+                    else
+                        stage[decltype(Jc)::value] += sum;
+                });
+            }
+            float* row = kbuf.v + lane * kKetBufLd + c * NQ;
+#pragma unroll
+            for (int j = 0; j < NQ; ++j) row[j] = stage[j];
+        }
+        ketbuf_flush_rec<NQ, RQ>(kbuf, nk, kq, QJ, nQ, QR, lane);
+#pragma unroll
+        for (int b = 0; b < B; ++b)
+#pragma unroll
+            for (int i = 0; i < NP; ++i) {
+                two_sum_acc(Jhi[b][i], Jlo[b][i], JP[b][i]);
+                JP[b][i] = 0.0f;
+            }
+    }
+#pragma unroll
+    for (int b = 0; b < B; ++b) {
+        if (!valid[b]) continue;
+        // (Jhi + Jlo) (k_hi + k_lo) as a float pair: Jhi k_hi exactly (FMA residual) plus the cross terms
+#pragma unroll
+        for (int i = 0; i < NP; ++i) {
+            const float hi = Jhi[b][i] * kh[b];
+            const float lo = fmaf(Jhi[b][i], kh[b], -hi) + fmaf(Jhi[b][i], kl[b], Jlo[b][i] * kh[b]);
+            double* dst = d.pp_Jh[LP] + (size_t)i * d.n_pp[LP] + Pl[b];
+            atomicAdd(dst, f2d(hi));
+            atomicAdd(dst, f2d(lo));
+        }
+    }
+}
+
+// FP32-core tile: d-shell register classes (L_P >= 3) on the legacy Dh32 path; s/p classes on the
+// records with B bra pairs per lane, the Schwarz test only where some quartet of the tile can fail it.
+template <int LP, int LQ, int B = 1>
+__device__ __forceinline__ void jtile_fp32(const Dev& d, const int2 tl, const int kb, const int ke, const float tau,
+                                           const int lane, const KetBuf32& kbuf)
+{
+    if constexpr (LP >= 3) {
+        jtile_fp32_dclass<LP, LQ>(d, tl, kb, ke, tau, lane, kbuf);
+    } else {
+        const int pr = tl.x >> 1;
+        const int x = (tl.x & 1) ? d.pair_y[pr] : d.pair_x[pr];
+        const int y = (tl.x & 1) ? d.pair_x[pr] : d.pair_y[pr];
+        const int bra_end = d.frag_pp0[x * kClasses + LP] + d.frag_npp[x * kClasses + LP];
+        float qmin = 3.0e38f;
+#pragma unroll
+        for (int b = 0; b < B; ++b)
+            if (tl.y + 32 * b + lane < bra_end) qmin = fminf(qmin, d.pp_Q[LP][d.pp_perm[LP][tl.y + 32 * b + lane]]);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) qmin = fminf(qmin, __shfl_xor_sync(0xffffffffu, qmin, o));
+        if (qmin * __ldg(d.fc_qmin + y * kClasses + LQ) < tau)
+            jtile_fp32_sp<LP, LQ, B, true>(d, x, y, tl.y, kb, ke, tau, lane, kbuf);
+        else
+            jtile_fp32_sp<LP, LQ, B, false>(d, x, y, tl.y, kb, ke, tau, lane, kbuf);
+    }
+}
+
+// Ket chunk c of nchunk of a per-class launch: partner offsets [c chunk, (c + 1) chunk), or the whole
+// range when chunk = 0.
+__device__ __forceinline__ void ket_chunk_range(int c, int chunk, int& kb, int& ke)
+{
+    kb = chunk > 0 ? c * chunk : 0;
+    ke = chunk > 0 ? kb + chunk : INT_MAX;
+}
+
+// One warp per (tile, ket chunk), one launch per class pair.
 template <int LP, int LQ>
-__global__ void __launch_bounds__(128) k_jengine(Dev d, const int2* __restrict__ tiles, int n_tiles, float tau)
+__global__ void __launch_bounds__(128) k_jengine(Dev d, const int2* __restrict__ tiles, int n_tiles, float tau,
+                                                 int chunk, int nchunk)
 {
     __shared__ double kv[4 * kKetBufWarp];
     __shared__ int kk[4 * 32];
     const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    if (warp >= n_tiles) return;
+    const int unit = warp / nchunk;
+    if (unit >= n_tiles) return;
+    int kb, ke;
+    ket_chunk_range(warp - unit * nchunk, chunk, kb, ke);
     const int w = threadIdx.x >> 5;
-    jtile_fp64<LP, LQ>(d, tiles[warp], 0, INT_MAX, tau, threadIdx.x & 31, KetBuf{kv + w * kKetBufWarp, kk + w * 32});
+    jtile_fp64<LP, LQ>(d, tiles[unit], kb, ke, tau, threadIdx.x & 31, KetBuf{kv + w * kKetBufWarp, kk + w * 32});
 }
 
+// FP32 core, one launch per class pair.  For L_P <= 1 a warp takes two consecutive tiles: when they
+// cover the same fragment pair (64 consecutive bra positions) it runs them as one tile with two bra
+// pairs per lane, else one after the other.
 template <int LP, int LQ>
-__global__ void __launch_bounds__(128) k_jengine32(Dev d, const int2* __restrict__ tiles, int n_tiles, float tau)
+__global__ void __launch_bounds__(128) k_jengine32(Dev d, const int2* __restrict__ tiles, int n_tiles, float tau,
+                                                   int chunk, int nchunk)
 {
     __shared__ float kv[4 * kKetBufWarp];
     __shared__ int kk[4 * 32];
+    constexpr int kPer = LP <= 1 ? 2 : 1;
     const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    if (warp >= n_tiles) return;
-    const int w = threadIdx.x >> 5;
-    jtile_fp32<LP, LQ>(d, tiles[warp], 0, INT_MAX, tau, threadIdx.x & 31, KetBuf32{kv + w * kKetBufWarp, kk + w * 32});
+    const int unit = warp / nchunk;
+    const int t0 = unit * kPer;
+    if (t0 >= n_tiles) return;
+    int kb, ke;
+    ket_chunk_range(warp - unit * nchunk, chunk, kb, ke);
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const KetBuf32 kbuf{kv + w * kKetBufWarp, kk + w * 32};
+    const int2 a = tiles[t0];
+    if constexpr (kPer == 2) {
+        if (t0 + 1 < n_tiles) {
+            const int2 b = tiles[t0 + 1];
+            if (b.x == a.x && b.y == a.y + 32) {
+                jtile_fp32<LP, LQ, 2>(d, a, kb, ke, tau, lane, kbuf);
+                return;
+            }
+            jtile_fp32<LP, LQ>(d, a, kb, ke, tau, lane, kbuf);
+            jtile_fp32<LP, LQ>(d, b, kb, ke, tau, lane, kbuf);
+            return;
+        }
+    }
+    jtile_fp32<LP, LQ>(d, a, kb, ke, tau, lane, kbuf);
 }
 
 // ------------------------------------------------------------------------------------------ persistent
@@ -446,37 +786,46 @@ cudaError_t launch_jengine_persistent(const Dev& d, int mode, bool spd, const JQ
     return cudaGetLastError();
 }
 
+// chunk > 0: every tile is cut into nchunk ket chunks of chunk partner pairs (one warp each)
 template <int LP, int LQ>
-static void launch_one(const Dev& d, const int2* t, int n, float tau, int fp32, cudaStream_t s)
+static void launch_one(const Dev& d, const int2* t, int n, float tau, int fp32, cudaStream_t s, int chunk = 0,
+                       int nchunk = 1)
 {
     if (n <= 0) return;
+    if (chunk <= 0) nchunk = 1;
     const int warps_per_block = 4;
-    const int blocks = (n + warps_per_block - 1) / warps_per_block;
-    if (fp32)
-        k_jengine32<LP, LQ><<<blocks, 32 * warps_per_block, 0, s>>>(d, t, n, tau);
-    else
-        k_jengine<LP, LQ><<<blocks, 32 * warps_per_block, 0, s>>>(d, t, n, tau);
+    if (fp32) {
+        const int per = LP <= 1 ? 2 : 1;  // tiles per warp of the FP32 core (see k_jengine32)
+        const long long warps = (long long)((n + per - 1) / per) * nchunk;
+        k_jengine32<LP, LQ><<<(unsigned)((warps + warps_per_block - 1) / warps_per_block), 32 * warps_per_block, 0,
+                              s>>>(d, t, n, tau, chunk, nchunk);
+    } else {
+        const long long warps = (long long)n * nchunk;
+        k_jengine<LP, LQ><<<(unsigned)((warps + warps_per_block - 1) / warps_per_block), 32 * warps_per_block, 0,
+                            s>>>(d, t, n, tau, chunk, nchunk);
+    }
     note_launches(1);
 }
 
 // One class pair's kernel on stream s (mode 0 FP64, 1 FP32, 2 float-float for L_P <= 2): the plans
 // that run the class kernels concurrently on forked streams launch them one by one.
-cudaError_t launch_jengine_class(const Dev& d, int LP, int LQ, const int2* t, int n, float tau, int mode, cudaStream_t s)
+cudaError_t launch_jengine_class(const Dev& d, int LP, int LQ, const int2* t, int n, float tau, int mode, cudaStream_t s,
+                                 int chunk, int nchunk)
 {
     if (n <= 0) return cudaSuccess;
     if (LP + LQ >= 5) return launch_jengine_big_class(d, LP, LQ, t, n, tau, mode == 1 ? 1 : 0, s);
     if (mode == 2 && LP <= 2) return launch_jengine_df_class(d, LP, LQ, t, n, tau, s);
     const int fp32 = mode == 1 ? 1 : 0;
     switch (LP * kClasses + LQ) {
-        case 0 * kClasses + 0: launch_one<0, 0>(d, t, n, tau, fp32, s); break;
-        case 1 * kClasses + 0: launch_one<1, 0>(d, t, n, tau, fp32, s); break;
-        case 1 * kClasses + 1: launch_one<1, 1>(d, t, n, tau, fp32, s); break;
-        case 2 * kClasses + 0: launch_one<2, 0>(d, t, n, tau, fp32, s); break;
-        case 2 * kClasses + 1: launch_one<2, 1>(d, t, n, tau, fp32, s); break;
-        case 2 * kClasses + 2: launch_one<2, 2>(d, t, n, tau, fp32, s); break;
-        case 3 * kClasses + 0: launch_one<3, 0>(d, t, n, tau, fp32, s); break;
-        case 3 * kClasses + 1: launch_one<3, 1>(d, t, n, tau, fp32, s); break;
-        case 4 * kClasses + 0: launch_one<4, 0>(d, t, n, tau, fp32, s); break;
+        case 0 * kClasses + 0: launch_one<0, 0>(d, t, n, tau, fp32, s, chunk, nchunk); break;
+        case 1 * kClasses + 0: launch_one<1, 0>(d, t, n, tau, fp32, s, chunk, nchunk); break;
+        case 1 * kClasses + 1: launch_one<1, 1>(d, t, n, tau, fp32, s, chunk, nchunk); break;
+        case 2 * kClasses + 0: launch_one<2, 0>(d, t, n, tau, fp32, s, chunk, nchunk); break;
+        case 2 * kClasses + 1: launch_one<2, 1>(d, t, n, tau, fp32, s, chunk, nchunk); break;
+        case 2 * kClasses + 2: launch_one<2, 2>(d, t, n, tau, fp32, s, chunk, nchunk); break;
+        case 3 * kClasses + 0: launch_one<3, 0>(d, t, n, tau, fp32, s, chunk, nchunk); break;
+        case 3 * kClasses + 1: launch_one<3, 1>(d, t, n, tau, fp32, s, chunk, nchunk); break;
+        case 4 * kClasses + 0: launch_one<4, 0>(d, t, n, tau, fp32, s, chunk, nchunk); break;
         default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();
@@ -515,6 +864,122 @@ cudaError_t launch_delta_density(const Dev& d, double* const Dh_ref[kClasses], c
                                                                                        d.pp_Dh32[L], n);
         note_launches(1);
     }
+    return cudaGetLastError();
+}
+
+// FP32-core records (layout: rec32_len in internal.hpp), one thread per primitive pair of class L:
+// (P - anchor, p) | (k_hi, k_lo, Q, 0) | u = p^{-1/2} (D_P - D_P^ref) rounded to FP32; resid[g] keeps
+// u[0] - float(u[0]) for the charge fix below.
+__global__ void k_fp32_records(Dev d, int L, const double* __restrict__ ref, double* __restrict__ resid)
+{
+    const int g = blockIdx.x * blockDim.x + threadIdx.x;
+    const int n = d.n_pp[L];
+    if (g >= n) return;
+    const int NH = nh(L), RL = rec32_len(L);
+    float* r = d.pp_rec32[L] + (size_t)g * RL;
+    const double rp = d.pp_rp[L][g];
+    const double k = kSqrtPiHalf * rp;
+    const float khi = (float)k;
+    reinterpret_cast<float4*>(r)[0] = d.pp_Pr[L][g];
+    reinterpret_cast<float4*>(r)[1] = make_float4(khi, (float)(k - (double)khi), d.pp_Q[L][g], 0.0f);
+    for (int i = 0; i < NH; ++i) {
+        const size_t o = (size_t)i * n + g;
+        const double u = rp * (d.pp_Dh[L][o] - (ref ? ref[o] : 0.0));
+        const float uh = (float)u;
+        r[8 + i] = uh;
+        if (i == 0) resid[g] = u - (double)uh;
+    }
+    for (int i = NH; i < RL - 8; ++i) r[8 + i] = 0.0f;
+}
+
+// Charge-conserving rounding of the FP32 weights, one block per fragment for class L: the sum of the
+// roundings of u[0] over the fragment's class range is moved onto its element of smallest |u[0]|, so
+// that the FP32 weights sum to the exact total to within one rounding of that element.  Every
+// partner's quartets reuse these weights, so an uncorrected sum of roundings would act as a spurious
+// charge in the field of all neighbours at once (a coherent, not a random, error).
+__global__ void k_fp32_charge_fix(Dev d, int L, const double* __restrict__ resid)
+{
+    const int x = blockIdx.x;
+    const int g0 = d.frag_pp0[x * kClasses + L], m = d.frag_npp[x * kClasses + L];
+    if (m == 0) return;
+    const int RL = rec32_len(L);
+    float* rec = d.pp_rec32[L];
+    double sum = 0.0;
+    float best = 3.0e38f;
+    int arg = g0;
+    for (int i = threadIdx.x; i < m; i += blockDim.x) {
+        const int g = g0 + i;
+        sum += resid[g];
+        const float a = fabsf(rec[(size_t)g * RL + 8]);
+        if (a < best || (a == best && g < arg)) {
+            best = a;
+            arg = g;
+        }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        sum += __shfl_xor_sync(0xffffffffu, sum, o);
+        const float b2 = __shfl_xor_sync(0xffffffffu, best, o);
+        const int a2 = __shfl_xor_sync(0xffffffffu, arg, o);
+        if (b2 < best || (b2 == best && a2 < arg)) {
+            best = b2;
+            arg = a2;
+        }
+    }
+    __shared__ double s_sum[32];
+    __shared__ float s_best[32];
+    __shared__ int s_arg[32];
+    const int w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    if ((threadIdx.x & 31) == 0) {
+        s_sum[w] = sum;
+        s_best[w] = best;
+        s_arg[w] = arg;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        float b = 3.0e38f;
+        int a = g0;
+        for (int i = 0; i < nw; ++i) {
+            t += s_sum[i];
+            if (s_best[i] < b || (s_best[i] == b && s_arg[i] < a)) {
+                b = s_best[i];
+                a = s_arg[i];
+            }
+        }
+        float* u0 = rec + (size_t)a * RL + 8;
+        *u0 = (float)((double)*u0 + t);
+    }
+}
+
+cudaError_t launch_fp32_records(const Dev& d, double* const Dh_ref[kClasses], double* resid, cudaStream_t s)
+{
+    for (int L = 0; L < kClasses; ++L) {
+        if (d.n_pp[L] == 0) continue;
+        k_fp32_records<<<(d.n_pp[L] + 127) / 128, 128, 0, s>>>(d, L, Dh_ref[L], resid);
+        k_fp32_charge_fix<<<d.n_frag, 128, 0, s>>>(d, L, resid);
+        note_launches(2);
+    }
+    return cudaGetLastError();
+}
+
+// Smallest Schwarz factor of every fragment's primitive pairs of each class (FLT_MAX-like when the
+// class is empty): one warp per (fragment, class).
+__global__ void k_class_qmin(Dev d, float* qmin)
+{
+    const int x = blockIdx.x, L = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int g0 = d.frag_pp0[x * kClasses + L], m = d.frag_npp[x * kClasses + L];
+    float q = 3.0e38f;
+    for (int i = lane; i < m; i += 32) q = fminf(q, d.pp_Q[L][g0 + i]);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) q = fminf(q, __shfl_xor_sync(0xffffffffu, q, o));
+    if (lane == 0) qmin[x * kClasses + L] = q;
+}
+
+cudaError_t launch_class_qmin(const Dev& d, float* qmin, cudaStream_t s)
+{
+    k_class_qmin<<<d.n_frag, 32 * kClasses, 0, s>>>(d, qmin);
+    note_launches(1);
     return cudaGetLastError();
 }
 

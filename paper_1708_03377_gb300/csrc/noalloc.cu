@@ -2,18 +2,17 @@
 // of scf.cu) for callers that cannot allocate device memory.
 //
 // Who cannot allocate: host codes that own every byte of device memory themselves (a molecular
-// dynamics or embedding driver with a fixed memory budget or its own pool), code that runs while a
-// CUDA stream is being captured into a graph, and callers that must not pay for or serialise on
-// cudaMalloc/cudaFree in a time step.  This entry point therefore takes all inputs and outputs from
-// the caller and keeps its own working memory (orthogonalisers, DIIS history, per-fragment offsets,
-// status flag) in one file-scope device array of fixed size, g_noalloc_scratch (16 MiB).  Every GPU
-// that loads the library holds that array until the process exits.
+// dynamics or embedding driver with a fixed memory budget or its own pool), and callers that must not
+// pay for, or serialise on, cudaMalloc/cudaFree in a time step.  This entry point therefore takes all
+// inputs and outputs from the caller and keeps its own working memory (orthogonalisers, DIIS history,
+// per-fragment offsets, status flag) in one file-scope device array of fixed size, g_noalloc_scratch
+// (16 MiB).  Every GPU that loads the library holds that array until the process exits.
 //
 // Set-up: the first call on each device, with that device current, resolves the array's device
-// address with cudaGetSymbolAddress and caches it; make that first call before any stream capture.
-// All calls share the array and it keeps the previous call's contents, so calls whose device work
-// overlaps (two streams, two host threads, or the same stream captured twice and replayed
-// concurrently) race on it.  The status flag is cleared at the start of every call.
+// address with cudaGetSymbolAddress and caches it; make that first call before any stream capture
+// begins.  All calls share the array and it keeps the previous call's contents, so calls whose device
+// work overlaps (two streams, two host threads) race on it.  The status flag is cleared at the start
+// of every call; the call then reads it back and synchronises the stream before it returns.
 #include <cuda_runtime.h>
 
 #include <mutex>
@@ -182,7 +181,11 @@ extern "C" fef_status fef_fragment_rhf_noalloc(int32_t n_frag, const int32_t* n_
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) return fail(FEF_ERR_CUDA, cudaGetErrorString(e));
     if (hflag & kErrNumeric) return fail(FEF_ERR_NUMERIC, "fef_fragment_rhf_noalloc: NaN/Inf in a fragment SCF");
+    if (hflag & kErrBounds)
+        return fail(FEF_ERR_ARG, "fef_fragment_rhf_noalloc: a device bounds check failed (inputs inconsistent "
+                                 "with n_ao)");
     if (hflag & kErrNotConv)
         return fail(FEF_ERR_NOT_CONVERGED, "fef_fragment_rhf_noalloc: a fragment RHF hit max_micro");
+    if (hflag != 0) return fail(FEF_ERR_CUDA, "fef_fragment_rhf_noalloc: unexpected device status flag");
     return FEF_OK;
 }

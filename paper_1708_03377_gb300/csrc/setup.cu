@@ -138,7 +138,7 @@ cudaError_t launch_ao_scale(const Dev& d, double* ao_scale, int n_ao_total, cons
 
 // ------------------------------------------------------------------------------------------ prim pairs
 // P = (a A + b B)/p, p = a + b, K = c_i c_j exp(-a b/p |AB|^2), for every primitive pair.
-__global__ void k_prim_pairs(Dev d, int L, double4_32a* P, float4* Pf, double* K, float4* Pr)
+__global__ void k_prim_pairs(Dev d, int L, double4_32a* P, float4* Pf, double* K, float4* Pr, double* rp)
 {
     int g = blockIdx.x * blockDim.x + threadIdx.x;
     if (g >= d.n_pp[L]) return;
@@ -158,14 +158,15 @@ __global__ void k_prim_pairs(Dev d, int L, double4_32a* P, float4* Pf, double* K
     const double* anc = d.atom_xyz + 3 * d.frag_atom0[frag_of_shellpair(d, sp)];
     Pr[g] = make_float4((float)(Pc[0] - anc[0]), (float)(Pc[1] - anc[1]), (float)(Pc[2] - anc[2]), (float)p);
     K[g] = d.p_coef[pa] * d.p_coef[pb] * exp(-a * b / p * R2);
+    rp[g] = 1.0 / sqrt(p);
 }
 
 cudaError_t launch_prim_pairs(const Dev& d, double4_32a* P[kClasses], float4* Pf[kClasses], double* K[kClasses],
-                              float4* Pr[kClasses], cudaStream_t s)
+                              float4* Pr[kClasses], double* rp[kClasses], cudaStream_t s)
 {
     for (int L = 0; L < kClasses; ++L)
         if (d.n_pp[L] > 0) {
-            k_prim_pairs<<<(d.n_pp[L] + 127) / 128, 128, 0, s>>>(d, L, P[L], Pf[L], K[L], Pr[L]);
+            k_prim_pairs<<<(d.n_pp[L] + 127) / 128, 128, 0, s>>>(d, L, P[L], Pf[L], K[L], Pr[L], rp[L]);
             note_launches(1);
         }
     return cudaGetLastError();

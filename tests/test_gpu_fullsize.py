@@ -141,3 +141,23 @@ def test_water_box64_converged_energies():
     ctx.close()
     assert abs(E_tot - ref["E_tot"]) < 1e-8, (E_tot, ref["E_tot"])
     assert np.abs(E_frag - ref["E_x"]).max() < 1e-8
+
+
+def test_water_box64_converged_against_stored_reference():
+    """The GPU's converged FEF energy of the bench workload against the stored oracle references in
+    tests/golden (written by oracle calls only): the 8 A cutoff solve and the cutoff plus multipole
+    far-field solve, each within the 1e-8 Eh convergence tolerance."""
+    import json
+    import os
+    fef = _fef()
+    ref = json.load(open(os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden",
+                                      "water64_reference.json")))
+    system = S.water_box(64, seed=0)
+    for key, far in (("cutoff_8A", 0), ("cutoff_8A_far_field", 1)):
+        ctx = fef.fef_create_system(system, fef.fef_default_options(cutoff_A=8.0, schwarz=1e-12, e_tol=1e-8,
+                                                                    far_field=far))
+        assert fef.fef_stats(ctx)["n_pairs"] == ref[key]["n_pairs"]
+        fef.fef_iterate(ctx)
+        _, E_tot, _ = fef.fef_energies(ctx)
+        ctx.close()
+        assert abs(E_tot - ref[key]["E_tot_converged"]) < 1e-8, (key, E_tot, ref[key]["E_tot_converged"])

@@ -67,3 +67,59 @@ def test_mixed_iterate_converges_to_fp64_fixed_point(box12):
     E_frag, E_tot, _ = fef.fef_energies(ctx)
     assert abs(E_tot - sol["energies"]["E_tot"]) < 1e-8
     assert np.abs(E_frag - sol["energies"]["E_x"]).max() < 1e-8
+
+
+def test_fp32_core_whole_build_error(box12):
+    """The FP32 core on its own: J_fp32[D] of the whole density (opt.mixed_build = FEF_MIXED_WHOLE, no
+    FP64 reference), FP64 accumulation, intra-fragment G, nuclear terms and energies, against the
+    oracle's FP64 Fock build and energies for the isolated and the converged densities.
+
+    What bounds it: every primitive quartet carries FP32 roundings (geometry, 1/R, Hermite recursion,
+    contraction) relative to its own term, and the random-basis Hermite densities cancel strongly (the
+    sum of |terms| is ~40x the pair energy), so the per-fragment energy error is a random sum of ~1e7
+    roundings: ~1e-6 Eh rms on a 33-neighbour water, not far below the benchmark spec's 1e-6 bar.  Roundings
+    that repeat in every partner's quartets (per-pair weights and scale factors, constants) would add
+    coherently over all neighbours and are removed in the kernel (charge-conserving weights, float-pair
+    scale factors); the mean error over fragments bounds that bias.  MIXED never converges on such a
+    build: its energies come from increments on an FP64-accurate reference (the test above)."""
+    fef = _fef()
+    system, ref, sol, iso = box12
+    ctx = fef.fef_create_system(system, fef.fef_default_options(cutoff_A=6.0, schwarz=1e-12, precision=fef.FEF_MIXED,
+                                                                mixed_build=fef.FEF_MIXED_WHOLE))
+    for name, D in (("isolated", iso), ("converged", sol["D"])):
+        F = ctx.unpack(fef.fef_build_fock(ctx, ctx.pack(D)))
+        F_ref = ref.fock(D)
+        ferr = max(float(np.abs(F[x] - F_ref[x]).max()) for x in range(ref.nf))
+        E_frag, E_tot, _ = fef.fef_energies(ctx)
+        dE = E_frag - ref.energies(D)["E_x"]
+        print(f"FP32 whole build ({name}): max|dF| = {ferr:.2e}, max|dE_x| = {np.abs(dE).max():.2e}, "
+              f"mean dE_x = {dE.mean():.2e}")
+        assert np.abs(dE).max() < 1e-5
+        assert abs(dE.mean()) < 1e-6
+        assert ferr < 1e-5
+    ctx.close()
+
+
+def test_fp32_core_whole_build_bias_water64():
+    """The 64-water bench workload (8 A cutoff, ~33 neighbours per fragment): the FP32-core whole
+    build against the FP64 build of the same isolated densities (the FP64 build matches the oracle to
+    1e-10).  The per-fragment errors must scatter around zero: |mean dE_x| < 5e-7 Eh (a coherent bias
+    of one FP32 rounding of the pair weights gave +1.8e-6), max |dE_x| < 1.5e-5 Eh."""
+    fef = _fef()
+    system = S.water_box(64, seed=0)
+    c64 = fef.fef_create_system(system, fef.fef_default_options(cutoff_A=8.0, schwarz=1e-12))
+    fef.fef_noninteracting_scf(c64)
+    D = fef.fef_get_densities(c64)
+    F64 = fef.fef_build_fock(c64, D)
+    E64, _, _ = fef.fef_energies(c64)
+    c64.close()
+    c32 = fef.fef_create_system(system, fef.fef_default_options(cutoff_A=8.0, schwarz=1e-12, precision=fef.FEF_MIXED,
+                                                                mixed_build=fef.FEF_MIXED_WHOLE))
+    F32 = fef.fef_build_fock(c32, D)
+    E32, _, _ = fef.fef_energies(c32)
+    c32.close()
+    dE = E32 - E64
+    print(f"64 waters, FP32 whole build vs FP64: max|dF| = {np.abs(F32 - F64).max():.2e}, "
+          f"max|dE_x| = {np.abs(dE).max():.2e}, rms {np.sqrt((dE ** 2).mean()):.2e}, mean {dE.mean():.2e}")
+    assert abs(dE.mean()) < 5e-7
+    assert np.abs(dE).max() < 1.5e-5
