@@ -848,6 +848,8 @@ extern "C" fef_status fef_create(const fef_geometry* g, const fef_basis* bs, con
         c->h_sp_a = sp_a;
         c->h_sp_b = sp_b;
         c->h_sh_l = sh_l;
+        c->h_frag_pp0 = frag_pp0;
+        c->h_frag_npp = frag_npp;
         d.pair_x = b->upload(pair_x, s, "pairs");
         d.pair_y = b->upload(pair_y, s, "pairs");
         d.frag_nbr0 = b->upload(nbr0, s, "pairs");
@@ -1535,6 +1537,91 @@ extern "C" fef_status fef_energy_d2(fef_ctx* c, double* E_d2_frag, double* E_d2_
     double* jws = b->alloc<double>(std::max<int64_t>(2 * c->mat_total, 1), "E_D2 Jacobi workspace");
     std::vector<double> E_pair(c->n_pairs, 0.0);
     cudaError_t e = launch_canonical_orbitals(d, b->F, b->X, b->nmo, jws, C, eps, s);
+    // s/p fragments: transition Hermite densities and the many-density J-engine (ed2.cu)
+    bool sp_only = true;
+    for (int x = 0; x < nf; ++x)
+        for (int L = 3; L < kClasses; ++L) sp_only = sp_only && c->h_frag_npp[x * kClasses + L] == 0;
+    if (sp_only && e == cudaSuccess) {
+        std::vector<int> n_ov(nf), hoff(nf * kClasses), n_herm(nf);
+        std::vector<int64_t> uoff(nf + 1, 0);
+        int max_ov = 1;
+        for (int x = 0; x < nf; ++x) {
+            n_ov[x] = c->nocc[x] * (c->nmo[x] - c->nocc[x]);
+            max_ov = std::max(max_ov, n_ov[x]);
+            int hsum = 0;
+            for (int L = 0; L < kClasses; ++L) {
+                hoff[x * kClasses + L] = hsum;
+                hsum += c->h_frag_npp[x * kClasses + L] * nh(L);
+            }
+            n_herm[x] = hsum;
+            uoff[x + 1] = uoff[x] + (int64_t)hsum * n_ov[x];
+        }
+        int* n_ov_d = b->upload(n_ov, s, "E_D2 sizes");
+        int* hoff_d = b->upload(hoff, s, "E_D2 sizes");
+        int* nherm_d = b->upload(n_herm, s, "E_D2 sizes");
+        int64_t* uoff_d = b->upload(uoff, s, "E_D2 sizes");
+        double* U = b->alloc<double>(std::max<int64_t>(uoff[nf], 1), "E_D2 transition densities");
+        e = launch_ed2_transition(d, C, b->nmo, uoff_d, hoff_d, n_ov_d, max_ov, U, s);
+        const int64_t kMaxG = 1ll << 27;
+        std::vector<int> chunk;
+        std::vector<int64_t> goff(1, 0);
+        std::vector<int4> items[3];
+        auto run = [&]() {
+            if (chunk.empty() || e != cudaSuccess) return;
+            const int nq = (int)chunk.size();
+            int* pair_d = b->upload(chunk, s, "E_D2 pairs");
+            int64_t* goff_d = b->upload(goff, s, "E_D2 offsets");
+            double* G = b->alloc<double>(std::max<int64_t>(goff.back(), 1), "E_D2 fields");
+            int4* items_d[3] = {};
+            int n_items[3];
+            for (int L = 0; L < 3; ++L) {
+                n_items[L] = (int)items[L].size();
+                if (n_items[L]) items_d[L] = b->upload(items[L], s, "E_D2 items");
+            }
+            double* Ed = b->alloc<double>(nq, "E_D2");
+            std::vector<double> Eh(nq);
+            e = cudaMemsetAsync(G, 0, sizeof(double) * std::max<int64_t>(goff.back(), 1), s);
+            const int4* cit[3] = {items_d[0], items_d[1], items_d[2]};
+            if (e == cudaSuccess)
+                e = launch_ed2_pairs(d, U, uoff_d, hoff_d, n_ov_d, pair_d, goff_d, G, c->opt.schwarz, cit, n_items, s);
+            if (e == cudaSuccess)
+                e = launch_ed2_energy(d, nq, U, uoff_d, hoff_d, n_ov_d, pair_d, goff_d, G, C, eps, b->nmo, nherm_d, Ed, s);
+            if (e == cudaSuccess) e = cudaMemcpyAsync(Eh.data(), Ed, sizeof(double) * nq, cudaMemcpyDeviceToHost, s);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+            for (int q = 0; q < nq; ++q) E_pair[chunk[q]] = Eh[q];
+            for (void* p : {(void*)pair_d, (void*)goff_d, (void*)G, (void*)Ed, (void*)items_d[0], (void*)items_d[1],
+                            (void*)items_d[2]})
+                if (p) b->release(p);
+            chunk.clear();
+            goff.assign(1, 0);
+            for (auto& v : items) v.clear();
+        };
+        for (int p = 0; p < c->n_pairs && e == cudaSuccess; ++p) {
+            const int x = c->h_pair_x[p], y = c->h_pair_y[p];
+            const int64_t gx = (int64_t)n_herm[x] * n_ov[y], gy = (int64_t)n_herm[y] * n_ov[x];
+            if (!chunk.empty() && goff.back() + gx + gy > kMaxG) run();
+            const int q = (int)chunk.size();
+            chunk.push_back(p);
+            goff.push_back(goff.back() + gx);   // side 0: rows of x, columns jb of y
+            goff.push_back(goff.back() + gy);   // side 1: rows of y, columns ia of x
+            for (int side = 0; side < 2; ++side) {
+                const int bx = side ? y : x, ky = side ? x : y;
+                for (int LB = 0; LB < 3; ++LB) {
+                    bool any_ket = false;  // ket classes >= LB (side 0) or > LB (side 1)
+                    for (int LK = side ? LB + 1 : LB; LK < 3; ++LK) any_ket |= c->h_frag_npp[ky * kClasses + LK] > 0;
+                    const int nb = c->h_frag_npp[bx * kClasses + LB];
+                    if (!any_ket || nb == 0 || n_ov[ky] == 0) continue;
+                    const int jc = ed2_cols_per_item(LB);
+                    for (int o = 0; o < nb; o += 32)
+                        for (int j0 = 0; j0 < n_ov[ky]; j0 += jc)
+                            items[LB].push_back(make_int4(2 * q + side, c->h_frag_pp0[bx * kClasses + LB] + o, j0, 0));
+                }
+            }
+        }
+        run();
+        b->release(U);
+        for (void* p : {(void*)n_ov_d, (void*)hoff_d, (void*)nherm_d, (void*)uoff_d}) b->release(p);
+    }
     // pairs in chunks that bound the integral blocks, workspaces and task lists
     const int64_t kMaxChunkDoubles = 1ll << 27, kMaxChunkTasks = 1ll << 24;
     std::vector<int> chunk;
@@ -1563,7 +1650,7 @@ extern "C" fef_status fef_energy_d2(fef_ctx* c, double* E_d2_frag, double* E_d2_
         toff.assign(1, 0);
         tasks.clear();
     };
-    for (int p = 0; p < c->n_pairs && e == cudaSuccess; ++p) {
+    for (int p = 0; p < c->n_pairs && e == cudaSuccess && !sp_only; ++p) {
         const int x = c->h_pair_x[p], y = c->h_pair_y[p];
         const int nx = c->nao[x], ny = c->nao[y];
         const int64_t wsz = ((int64_t)nx * (nx + 1) / 2) * ((int64_t)ny * (ny + 1) / 2);

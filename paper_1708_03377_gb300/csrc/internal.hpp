@@ -130,6 +130,7 @@ struct fef_ctx {
     std::vector<int64_t> moff;
     std::vector<int> h_pair_x, h_pair_y;
     std::vector<int> h_frag_sp0, h_sp_a, h_sp_b, h_sh_l;  // shell pairs (intra-ERI tasks of E_M2)
+    std::vector<int> h_frag_pp0, h_frag_npp;              // [n_frag * 5] primitive-pair class ranges
     fef::Dev dev{};
     fef::Buffers* buf = nullptr;
     // counters
@@ -310,6 +311,21 @@ int64_t energy_d2_workspace(int nx, int ox, int mx, int ny, int oy, int my);  //
 cudaError_t launch_energy_d2(const Dev& d, int n_pairs, const int* pair_of, const int64_t* woff, const double* W,
                              const double* C, const double* eps, const int* nmo, const int64_t* toff, double* tws,
                              double* E, cudaStream_t s);
+// E_D2 on transition Hermite densities (ed2.cu; fragments with s and p shells): U = per fragment the
+// pre-scaled Hermite transition densities of all occupied-virtual pairs, rows (class offset hoff, local
+// primitive pair, Hermite component) x columns ov; per chunk of pairs the fields G of the partner's
+// transition densities on each bra primitive pair (items per bra class: 2 q + side, first bra pair,
+// first column), then E_D2 per pair.
+cudaError_t launch_ed2_transition(const Dev& d, const double* C, const int* nmo, const int64_t* uoff, const int* hoff,
+                                  const int* n_ov, int max_ov, double* U, cudaStream_t s);
+cudaError_t launch_ed2_pairs(const Dev& d, const double* U, const int64_t* uoff, const int* hoff, const int* n_ov,
+                             const int* pair_of, const int64_t* goff, double* G, double tau,
+                             const int4* const items[3], const int n_items[3], cudaStream_t s);
+cudaError_t launch_ed2_energy(const Dev& d, int n_pairs, const double* U, const int64_t* uoff, const int* hoff,
+                              const int* n_ov, const int* pair_of, const int64_t* goff, const double* G,
+                              const double* C, const double* eps, const int* nmo, const int* n_herm, double* E,
+                              cudaStream_t s);
+int ed2_cols_per_item(int LB);
 cudaError_t launch_energy_m2(const Dev& d, const double* F, const double* X, const int* nmo, const double* U,
                              const int64_t* ws_off, double* ws, double* E, cudaStream_t s);
 
