@@ -521,6 +521,13 @@ __device__ __forceinline__ void jtile_fp32_sp(const Dev& d, const int x, const i
     for (int kq = k0; kq < k1; kq += kBatch) {
         const int nk = min(kBatch, k1 - kq);
         const float* __restrict__ qr = QR + (size_t)kq * RQ;
+        // without screening the next ket's record is loaded while the current one is in use
+        float4 q0n;
+        float uQn[NQ];
+        if constexpr (!SCREEN) {
+            q0n = __ldg(reinterpret_cast<const float4*>(qr));
+            load_weights<NQ>(qr + 8, uQn);
+        }
         for (int c = 0; c < nk; ++c, qr += RQ) {
             bool keep[B];
 #pragma unroll
@@ -540,9 +547,20 @@ __device__ __forceinline__ void jtile_fp32_sp(const Dev& d, const int x, const i
                     continue;
                 }
             }
-            const float4 q0 = __ldg(reinterpret_cast<const float4*>(qr));
+            float4 q0;
             float uQ[NQ];
-            load_weights<NQ>(qr + 8, uQ);
+            if constexpr (SCREEN) {
+                q0 = __ldg(reinterpret_cast<const float4*>(qr));
+                load_weights<NQ>(qr + 8, uQ);
+            } else {
+                q0 = q0n;
+#pragma unroll
+                for (int j = 0; j < NQ; ++j) uQ[j] = uQn[j];
+                if (c + 1 < nk) {
+                    q0n = __ldg(reinterpret_cast<const float4*>(qr + RQ));
+                    load_weights<NQ>(qr + RQ + 8, uQn);
+                }
+            }
             float stage[NQ];
 #pragma unroll
             for (int j = 0; j < NQ; ++j) stage[j] = 0.0f;
