@@ -195,9 +195,9 @@ fef_status fef_energies(fef_ctx* ctx, double* E_frag, double* E_total, double* E
  * monomer effective Hamiltonian is the diagonal Fock operator and the doubles are driven by the
  * fragment's own two-electron interaction (the environment field is one-body), so
  *   E_M2^x = sum_{ij occ, ab virt} (ia|jb) [2 (ia|jb) - (ib|ja)] / (eps_i + eps_j - eps_a - eps_b).
- * E_m2[n_frag] (host, nullable) per fragment, *E_m2_total (nullable) their sum.  Fragments up to 64
- * AOs.  The fragments' integrals are recomputed into temporary device memory for the call.
- * Errors: ARG (no densities, a fragment above 64 AOs), CUDA. */
+ * E_m2[n_frag] (host, nullable) per fragment, *E_m2_total (nullable) their sum.  The fragments'
+ * integrals are recomputed into temporary device memory for the call (n^2 (n+1)^2 / 4 doubles per
+ * fragment of n AOs).  Errors: ARG (no densities), CUDA. */
 fef_status fef_energy_m2(fef_ctx* ctx, double* E_m2, double* E_m2_total);
 
 /* Dimer second-order energy of the FEF cluster perturbation theory (Eq. ED2, with the first-order
@@ -206,8 +206,10 @@ fef_status fef_energy_m2(fef_ctx* ctx, double* E_m2, double* E_m2_total);
  * each fragment and interact directly only (no inter-fragment exchange in the product ansatz):
  *   E_D2^{xy} = 4 sum_{i,a in x; j,b in y} (ia|jb)^2 / (eps_i + eps_j - eps_a - eps_b).
  * E_d2_frag[n_frag] (host, nullable) = half of each fragment's pair terms, *E_d2_total (nullable) =
- * sum over pairs.  Fragments up to 64 AOs; the pair integrals are computed into temporary device
- * memory, in chunks of pairs.  Errors: ARG (no densities, a fragment above 64 AOs), CUDA. */
+ * sum over pairs.  Fragments of s and p shells: the integrals come from the Hermite transition
+ * densities of the occupied-virtual pairs (no AO integral block); with d shells the pair integral
+ * blocks are computed into temporary device memory.  Both in chunks of pairs.
+ * Errors: ARG (no densities), CUDA. */
 fef_status fef_energy_d2(fef_ctx* ctx, double* E_d2_frag, double* E_d2_total);
 
 /* Checkpoint / resume: copy the current packed densities out, or replace them. */

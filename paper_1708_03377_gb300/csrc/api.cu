@@ -1477,8 +1477,6 @@ extern "C" fef_status fef_energy_m2(fef_ctx* c, double* E_m2, double* E_m2_total
     if (!c) return FEF_ERR_ARG;
     FEF_API_BEGIN
     require(c->have_density, FEF_ERR_ARG, "fef_energy_m2: no densities");
-    require(c->max_nao <= kM2MaxN, FEF_ERR_ARG,
-            "fef_energy_m2: fragments above " + std::to_string(kM2MaxN) + " AOs are not supported");
     Buffers* b = c->buf;
     const Dev& d = c->dev;
     cudaStream_t s = c->stream;
@@ -1523,8 +1521,6 @@ extern "C" fef_status fef_energy_d2(fef_ctx* c, double* E_d2_frag, double* E_d2_
     if (!c) return FEF_ERR_ARG;
     FEF_API_BEGIN
     require(c->have_density, FEF_ERR_ARG, "fef_energy_d2: no densities");
-    require(c->max_nao <= kM2MaxN, FEF_ERR_ARG,
-            "fef_energy_d2: fragments above " + std::to_string(kM2MaxN) + " AOs are not supported");
     Buffers* b = c->buf;
     const Dev& d = c->dev;
     cudaStream_t s = c->stream;
@@ -1566,6 +1562,7 @@ extern "C" fef_status fef_energy_d2(fef_ctx* c, double* E_d2_frag, double* E_d2_
         std::vector<int> chunk;
         std::vector<int64_t> goff(1, 0);
         std::vector<int4> items[3];
+        int max_entries = 1;  // largest n_ov(x) n_ov(y) of the chunk's pairs
         auto run = [&]() {
             if (chunk.empty() || e != cudaSuccess) return;
             const int nq = (int)chunk.size();
@@ -1578,23 +1575,31 @@ extern "C" fef_status fef_energy_d2(fef_ctx* c, double* E_d2_frag, double* E_d2_
                 n_items[L] = (int)items[L].size();
                 if (n_items[L]) items_d[L] = b->upload(items[L], s, "E_D2 items");
             }
-            double* Ed = b->alloc<double>(nq, "E_D2");
-            std::vector<double> Eh(nq);
+            const int ns = ed2_energy_slices(max_entries);
+            double* Ed = b->alloc<double>((int64_t)nq * ns, "E_D2");
+            std::vector<double> Eh((size_t)nq * ns);
             e = cudaMemsetAsync(G, 0, sizeof(double) * std::max<int64_t>(goff.back(), 1), s);
             const int4* cit[3] = {items_d[0], items_d[1], items_d[2]};
             if (e == cudaSuccess)
                 e = launch_ed2_pairs(d, U, uoff_d, hoff_d, n_ov_d, pair_d, goff_d, G, c->opt.schwarz, cit, n_items, s);
             if (e == cudaSuccess)
-                e = launch_ed2_energy(d, nq, U, uoff_d, hoff_d, n_ov_d, pair_d, goff_d, G, C, eps, b->nmo, nherm_d, Ed, s);
-            if (e == cudaSuccess) e = cudaMemcpyAsync(Eh.data(), Ed, sizeof(double) * nq, cudaMemcpyDeviceToHost, s);
+                e = launch_ed2_energy(d, nq, max_entries, U, uoff_d, hoff_d, n_ov_d, pair_d, goff_d, G, C, eps, b->nmo,
+                                      nherm_d, Ed, s);
+            if (e == cudaSuccess)
+                e = cudaMemcpyAsync(Eh.data(), Ed, sizeof(double) * Eh.size(), cudaMemcpyDeviceToHost, s);
             if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-            for (int q = 0; q < nq; ++q) E_pair[chunk[q]] = Eh[q];
+            for (int q = 0; q < nq; ++q) {
+                double sum = 0.0;
+                for (int k = 0; k < ns; ++k) sum += Eh[(size_t)q * ns + k];
+                E_pair[chunk[q]] = sum;
+            }
             for (void* p : {(void*)pair_d, (void*)goff_d, (void*)G, (void*)Ed, (void*)items_d[0], (void*)items_d[1],
                             (void*)items_d[2]})
                 if (p) b->release(p);
             chunk.clear();
             goff.assign(1, 0);
             for (auto& v : items) v.clear();
+            max_entries = 1;
         };
         for (int p = 0; p < c->n_pairs && e == cudaSuccess; ++p) {
             const int x = c->h_pair_x[p], y = c->h_pair_y[p];
@@ -1602,6 +1607,7 @@ extern "C" fef_status fef_energy_d2(fef_ctx* c, double* E_d2_frag, double* E_d2_
             if (!chunk.empty() && goff.back() + gx + gy > kMaxG) run();
             const int q = (int)chunk.size();
             chunk.push_back(p);
+            max_entries = std::max(max_entries, n_ov[x] * n_ov[y]);
             goff.push_back(goff.back() + gx);   // side 0: rows of x, columns jb of y
             goff.push_back(goff.back() + gy);   // side 1: rows of y, columns ia of x
             for (int side = 0; side < 2; ++side) {

@@ -13,6 +13,7 @@
 // G_P[tuv][jb] per pair.  The member with the smaller Hermite class of a class pair is the bra, so that
 // the lane's accumulators stay in registers; the quartet set is the J-engine's (cutoff pairs, shell-level
 // Schwarz screening).  No AO-basis integral block is formed.
+#include <algorithm>
 #include <climits>
 
 #include "common.cuh"
@@ -224,7 +225,11 @@ __global__ void __launch_bounds__(128) k_ed2_pair(Dev d, Ed2Args a, const int4* 
 }
 
 // E_D2 of each pair of the chunk: (ia|jb) = (sqrt(pi)/2) (sum_r U_x[r][ia] G_x[r][jb] + sum_r U_y[r][jb] G_y[r][ia]),
-// rows r over the fragments' Hermite components; one block per pair.
+// rows r over the fragments' Hermite components; block (q, slice) takes the entries
+// [slice * kEd2Entries, (slice + 1) * kEd2Entries) of pair q and writes its share to
+// E_out[q * gridDim.y + slice] (the host adds the slices in order, so the sum is reproducible).
+constexpr int kEd2Entries = 2048;
+
 __global__ void __launch_bounds__(256) k_ed2_energy(Dev d, Ed2Args a, const double* __restrict__ C,
                                                     const double* __restrict__ eps, const int* __restrict__ nmo,
                                                     const int* __restrict__ n_herm, double* __restrict__ E_out)
@@ -243,7 +248,8 @@ __global__ void __launch_bounds__(256) k_ed2_energy(Dev d, Ed2Args a, const doub
     const double* ex = eps + d.frag_ao0[x];
     const double* ey = eps + d.frag_ao0[y];
     double part = 0.0;
-    for (int e = threadIdx.x; e < nvx * nvy; e += blockDim.x) {
+    const int e0 = blockIdx.y * kEd2Entries, e1 = min(nvx * nvy, e0 + kEd2Entries);
+    for (int e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
         const int ia = e / nvy, jb = e % nvy;
         double v = 0.0;
         for (int r = 0; r < hx; ++r) v = fma(Ux[(int64_t)r * nvx + ia], Gx[(int64_t)r * nvy + jb], v);
@@ -260,7 +266,7 @@ __global__ void __launch_bounds__(256) k_ed2_energy(Dev d, Ed2Args a, const doub
     if (threadIdx.x == 0) {
         double s = 0.0;
         for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += red[w];
-        E_out[q] = 4.0 * s;
+        E_out[(int64_t)q * gridDim.y + blockIdx.y] = 4.0 * s;
     }
 }
 
@@ -291,18 +297,21 @@ cudaError_t launch_ed2_pairs(const Dev& d, const double* U, const int64_t* uoff,
     return cudaGetLastError();
 }
 
-cudaError_t launch_ed2_energy(const Dev& d, int n_pairs, const double* U, const int64_t* uoff, const int* hoff,
-                              const int* n_ov, const int* pair_of, const int64_t* goff, const double* G,
+cudaError_t launch_ed2_energy(const Dev& d, int n_pairs, int max_entries, const double* U, const int64_t* uoff,
+                              const int* hoff, const int* n_ov, const int* pair_of, const int64_t* goff, const double* G,
                               const double* C, const double* eps, const int* nmo, const int* n_herm, double* E,
                               cudaStream_t s)
 {
     if (n_pairs <= 0) return cudaSuccess;
     const Ed2Args a{U, uoff, hoff, n_ov, pair_of, goff, const_cast<double*>(G), 0.0f};
-    k_ed2_energy<<<n_pairs, 256, 0, s>>>(d, a, C, eps, nmo, n_herm, E);
+    const dim3 grid(n_pairs, ed2_energy_slices(max_entries));
+    k_ed2_energy<<<grid, 256, 0, s>>>(d, a, C, eps, nmo, n_herm, E);
     note_launches(1);
     return cudaGetLastError();
 }
 
 int ed2_cols_per_item(int LB) { return ed2_cols(LB); }
+
+int ed2_energy_slices(int max_entries) { return std::max(1, (max_entries + kEd2Entries - 1) / kEd2Entries); }
 
 }  // namespace fef

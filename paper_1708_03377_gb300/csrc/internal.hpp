@@ -297,9 +297,8 @@ struct ScfArgs {
 };
 cudaError_t launch_fragment_scf(const Dev& d, const ScfArgs& a, int max_n, cudaStream_t s);
 
-// E_M2 (Eq. EM2) per fragment, one block per fragment with at most kM2MaxN AOs: canonical orbitals of
+// E_M2 (Eq. EM2) per fragment, one block per fragment (any size up to kMaxFragAO): canonical orbitals of
 // F (packed), (ia|jb) by four quarter-transforms of the pair-packed U, closed-shell second-order sum.
-constexpr int kM2MaxN = 64;
 int64_t energy_m2_workspace(int n, int nocc, int nmo);  // doubles per fragment
 // E_D2 (Eq. ED2): canonical orbitals (C packed at frag_moff, eps at frag_ao0; Jacobi workspace
 // 2 frag_moff), inter-fragment pair blocks W (k_pair_eri), per-pair transform and second-order sum
@@ -315,17 +314,19 @@ cudaError_t launch_energy_d2(const Dev& d, int n_pairs, const int* pair_of, cons
 // pre-scaled Hermite transition densities of all occupied-virtual pairs, rows (class offset hoff, local
 // primitive pair, Hermite component) x columns ov; per chunk of pairs the fields G of the partner's
 // transition densities on each bra primitive pair (items per bra class: 2 q + side, first bra pair,
-// first column), then E_D2 per pair.
+// first column), then E_D2 per pair as ed2_energy_slices(max_entries) partial sums per pair
+// (E[q * slices + k], max_entries = the chunk's largest n_ov(x) n_ov(y)).
 cudaError_t launch_ed2_transition(const Dev& d, const double* C, const int* nmo, const int64_t* uoff, const int* hoff,
                                   const int* n_ov, int max_ov, double* U, cudaStream_t s);
 cudaError_t launch_ed2_pairs(const Dev& d, const double* U, const int64_t* uoff, const int* hoff, const int* n_ov,
                              const int* pair_of, const int64_t* goff, double* G, double tau,
                              const int4* const items[3], const int n_items[3], cudaStream_t s);
-cudaError_t launch_ed2_energy(const Dev& d, int n_pairs, const double* U, const int64_t* uoff, const int* hoff,
-                              const int* n_ov, const int* pair_of, const int64_t* goff, const double* G,
+cudaError_t launch_ed2_energy(const Dev& d, int n_pairs, int max_entries, const double* U, const int64_t* uoff,
+                              const int* hoff, const int* n_ov, const int* pair_of, const int64_t* goff, const double* G,
                               const double* C, const double* eps, const int* nmo, const int* n_herm, double* E,
                               cudaStream_t s);
 int ed2_cols_per_item(int LB);
+int ed2_energy_slices(int max_entries);
 cudaError_t launch_energy_m2(const Dev& d, const double* F, const double* X, const int* nmo, const double* U,
                              const int64_t* ws_off, double* ws, double* E, cudaStream_t s);
 

@@ -217,8 +217,8 @@ __global__ void __launch_bounds__(256) k_energy_m2(Dev d, const double* __restri
     const Team<1> t{0};
     __shared__ JacobiScratch js;
     __shared__ double red[40];
-    __shared__ int ord[kM2MaxN];
-    __shared__ double eps[kM2MaxN];
+    __shared__ int ord[kMaxFragAO];
+    __shared__ double eps[kMaxFragAO];
     const int64_t mo = d.frag_moff[x];
     const double* F = Fp + mo;
     const double* X = Xp + mo;
@@ -230,7 +230,7 @@ __global__ void __launch_bounds__(256) k_energy_m2(Dev d, const double* __restri
     double* T2 = T1 + (int64_t)nocc * n * np;
     double* T3 = T2 + (int64_t)nocc * nv * np;
     double* T4 = T3 + (int64_t)nocc * nv * nocc * n;
-    if (n > kM2MaxN || nocc <= 0 || nv <= 0) {
+    if (nocc <= 0 || nv <= 0) {
         if (threadIdx.x == 0) E_out[x] = 0.0;
         return;
     }
@@ -323,7 +323,7 @@ cudaError_t launch_energy_m2(const Dev& d, const double* F, const double* X, con
 namespace {
 
 // ------------------------------------------------------------------------------------------ E_D2
-// Canonical FEF orbitals of every fragment (n <= kM2MaxN): C (n x m, columns in ascending orbital
+// Canonical FEF orbitals of every fragment (n <= kMaxFragAO): C (n x m, columns in ascending orbital
 // energy) as the packed n x n block at frag_moff[x], eps[m] at frag_ao0[x]; one block per fragment,
 // Jacobi workspace 2 n^2 at 2 frag_moff[x].
 __global__ void __launch_bounds__(256) k_canonical_orbitals(Dev d, const double* __restrict__ Fp,
@@ -332,11 +332,10 @@ __global__ void __launch_bounds__(256) k_canonical_orbitals(Dev d, const double*
 {
     const int x = blockIdx.x;
     const int n = d.frag_nao[x], m = nmo_[x];
-    if (n > kM2MaxN) return;
     const Team<1> t{0};
     __shared__ JacobiScratch js;
     __shared__ double red[40];
-    __shared__ int ord[kM2MaxN];
+    __shared__ int ord[kMaxFragAO];
     const int64_t mo = d.frag_moff[x];
     const double* F = Fp + mo;
     const double* X = Xp + mo;

@@ -48,14 +48,34 @@ def test_e_m2_d_shell_waters():
     _check(_fef(), S.mixed_snapshot(n_frag=2, seed=1, weights=(1, 0, 0, 0)), schwarz=1e-12)
 
 
-def test_e_m2_rejects_large_fragments():
+def test_e_m2_e_d2_large_fragment():
+    """An 82-AO solute (s/p shells, 29 doubly occupied orbitals) with two waters: E_M2 of every
+    fragment and E_D2 of every pair against the oracle from the same converged densities, 1e-10 Eh.
+    The solute's E_M2 transform and its pairs' E_D2 contractions span several blocks of work per
+    fragment or pair (61,000 (ia|jb) entries per solute-water pair)."""
     fef = _fef()
-    system = S.solvated_heterocycle(n_water=2, side=9.0, seed=5, heavy_shells=S.SHELLS_O_SP)  # 82-AO solute
-    ctx = fef.fef_create_system(system, fef.fef_default_options())
-    fef.fef_noninteracting_scf(ctx)
-    with pytest.raises(fef.FefError):
-        fef.fef_energy_m2(ctx)
+    from oracle.fef import Fragments
+    system = S.solvated_heterocycle(n_water=2, side=9.0, seed=5, heavy_shells=S.SHELLS_O_SP)
+    ref = Fragments(system, schwarz=0.0)
+    assert max(ref.n_ao) == 82
+    ctx = fef.fef_create_system(system, fef.fef_default_options(e_tol=1e-10, schwarz=0.0))
+    fef.fef_iterate(ctx)
+    Em, _ = fef.fef_energy_m2(ctx)
+    Ef, tot = fef.fef_energy_d2(ctx)
+    D = ctx.unpack(fef.fef_get_densities(ctx))
+    assert fef.fef_stats(ctx)["n_pairs"] == len(ref.pairs) == 3
     ctx.close()
+    F = ref.fock(D)
+    Em_ref = np.array([ref.e_m2(x, F[x]) for x in range(ref.nf)])
+    assert np.abs(Em - Em_ref).max() < 1e-10, np.abs(Em - Em_ref).max()
+    E_ref, Ef_ref = 0.0, np.zeros(ref.nf)
+    for x, y in ref.pairs:
+        e = ref.e_d2(x, y, F[x], F[y])
+        E_ref += e
+        Ef_ref[x] += 0.5 * e
+        Ef_ref[y] += 0.5 * e
+    assert abs(tot - E_ref) < 1e-10, (tot, E_ref)
+    assert np.abs(Ef - Ef_ref).max() < 1e-10
 
 
 def _check_d2(fef, system, **opt):
