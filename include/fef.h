@@ -333,9 +333,11 @@ const char* fef_mlp_last_error(const fef_mlp* m);
 
 /* Features of the learned warm start for the densities D (packed, becomes the current density; NULL =
  * current): X [n_frag x n_feat] = per atom the potential and field (frame components) of all neighbour
- * fragments' nuclei and electrons (4 n_atoms values), then the environment operator omega_x of a
- * Fock build of D in the Loewdin basis (S^{-1/2} omega S^{-1/2}) and the molecule-fixed frame, upper
- * triangle (n_pack values): n_feat = 4 n_atoms + n_pack.  Y_local [n_frag x n_pack] = the
+ * fragments' nuclei and electrons (4 n_atoms values), then the multipole estimate of the environment
+ * operator: -(phi S + grad phi . <r> + (1/2) hess phi : <r r>) with phi the potential of the
+ * neighbours' charges, dipoles and second moments (about their nuclear-charge centroids) expanded to
+ * second order about x's centroid, in the Loewdin basis (S^{-1/2} omega S^{-1/2}) and the
+ * molecule-fixed frame, upper triangle (n_pack values): n_feat = 4 n_atoms + n_pack.  No Fock build.  Y_local [n_frag x n_pack] = the
  * density in the Loewdin basis (S^{1/2} D S^{1/2}, S^{1/2} symmetric) expressed in the molecule-fixed
  * frame, upper triangle row-major (n_pack = n(n+1)/2).  X, Y_local are
  * host arrays, or device arrays when on_device = 1; either may be NULL.  *n_feat, *n_pack (nullable)

@@ -84,6 +84,9 @@ struct Buffers {
     // multipoles, far potentials and half pair energies per fragment (per build)
     double *far_M = nullptr, *far_Mnuc = nullptr, *far_cen = nullptr;
     double *far_mult = nullptr, *far_pot = nullptr, *far_E = nullptr;
+    bool far_on = false;       // far-field terms in every build (opt.far_field with a cutoff)
+    double* omega_mp = nullptr;  // learned start: multipole estimate of omega
+    double* desc_part = nullptr; // learned start: descriptor terms per neighbour entry and atom
     double *e_nn_intra = nullptr, *e_nn_pair = nullptr;
     int* nmo = nullptr;
     // per-build data
@@ -223,6 +226,8 @@ static void mark(fef_ctx* c, int i)
     }
 }
 
+static void ensure_learn_buffers(fef_ctx* c);
+
 static int resolve_kind(const fef_ctx* c, int kind)
 {
     return (kind == kBuildFP32Inc && !c->buf->have_ref) ? kBuildFP64 : kind;
@@ -269,14 +274,14 @@ static void build_fock_device(fef_ctx* c, int kind)
     ck(launch_fock_energy(d, b->h, b->Venv, b->Jenv, b->eric, b->D, b->F, b->omega, b->e_nn_intra, b->E_int,
                           b->trV, b->trJ, s),
        "fock");
-    if (b->far_M)
+    if (b->far_on)
         ck(launch_far_field(d, b->far_M, b->far_Mnuc, b->far_cen, b->D, b->far_mult, b->far_pot, b->far_E, b->F,
                             b->omega, s),
            "far field");
     ck(launch_nuclear_traces(d, b->trf_off, b->trf, b->tr_xy, b->tr_yx, s), "nuclear traces");
     ck(launch_energies(d, b->E_int, b->trV, b->trJ, b->tr_xy, b->tr_yx, b->e_nn_pair, b->E_frag, b->E_tot, s),
        "energies");
-    if (b->far_M) ck(launch_far_energy(d, b->far_E, b->E_frag, b->E_tot, s), "far-field energies");
+    if (b->far_on) ck(launch_far_energy(d, b->far_E, b->E_frag, b->E_tot, s), "far-field energies");
     ck(launch_check_finite(b->F, c->mat_total, b->err_flag, s), "check");
 }
 
@@ -658,6 +663,7 @@ extern "C" fef_status fef_create(const fef_geometry* g, const fef_basis* bs, con
         d.n_shells = c->n_shells;
         d.n_sp = c->n_sp;
         d.max_nao = max_nao;
+        d.max_l = max_l;
         std::vector<double> xyzA(g->xyz, g->xyz + 3 * na), Zd(na);
         for (int a = 0; a < na; ++a) Zd[a] = g->Z[a];
         double* xyz_A = b->upload(xyzA, s, "xyz");
@@ -702,6 +708,7 @@ extern "C" fef_status fef_create(const fef_geometry* g, const fef_basis* bs, con
         float4* ppPr[kClasses];
         float4* ppPhi[kClasses];
         float4* ppPlo[kClasses];
+        float2* ppSq[kClasses];
         double* ppK[kClasses];
         float* ppQ[kClasses];
         double* ppRp[kClasses];
@@ -720,7 +727,9 @@ extern "C" fef_status fef_create(const fef_geometry* g, const fef_basis* bs, con
             ppPlo[L] = b->alloc<float4>(n, "prim pairs df64");
             d.pp_Phi[L] = ppPhi[L];
             d.pp_Plo[L] = ppPlo[L];
-            d.pp_Dhdf[L] = b->alloc<float2>((size_t)nh(L) * n, "hermite density df64");
+            d.pp_udf[L] = b->alloc<float2>((size_t)nh(L) * n, "hermite weights df64");
+            ppSq[L] = b->alloc<float2>(n, "prim pairs df64");
+            d.pp_sqdf[L] = ppSq[L];
             b->Dh_ref[L] = b->alloc<double>((size_t)nh(L) * n, "hermite density ref");
             b->Jh_ref[L] = b->alloc<double>((size_t)nh(L) * n, "hermite field ref");
             ppK[L] = b->alloc<double>(n, "prim pairs");
@@ -763,11 +772,21 @@ extern "C" fef_status fef_create(const fef_geometry* g, const fef_basis* bs, con
         ck(launch_boys_table32(b->boys, b->boys32, s), "boys table fp32");
         ck(launch_ao_scale(d, ao_scale, ao_global, nullptr, s), "ao scale");
         ck(launch_prim_pairs(d, ppP, ppPf, ppK, ppPr, ppRp, s), "prim pairs");
-        ck(launch_df_setup(d, ppPhi, ppPlo, boysdf, s), "df64 pair data");
+        ck(launch_df_setup(d, ppPhi, ppPlo, ppSq, boysdf, s), "df64 pair data");
         b->S = b->alloc<double>(c->mat_total, "S");
         b->h = b->alloc<double>(c->mat_total, "h");
         ck(launch_one_electron(d, b->S, b->h, s), "one-electron");
-        if (o.far_field && o.cutoff_A > 0.0) {
+        // the learned warm start needs fragments of one kind (same atoms and s/p basis)
+        bool learn_ok = true;
+        for (int x = 1; x < nf && learn_ok; ++x) learn_ok = frag_nat[x] == frag_nat[0] && frag_nao[x] == frag_nao[0];
+        learn_ok = learn_ok && max_l <= 1;
+        if (learn_ok) {
+            c->learn_desc = 4 * frag_nat[0];
+            c->learn_pack = frag_nao[0] * (frag_nao[0] + 1) / 2;
+            c->learn_feat = c->learn_desc + c->learn_pack;  // + the multipole estimate of omega
+        }
+        b->far_on = o.far_field && o.cutoff_A > 0.0;
+        if (b->far_on || learn_ok) {
             // centroids of nuclear charge and nuclear moments (bohr), moment integrals about them
             std::vector<double> cen(3 * (size_t)nf, 0.0), mnuc(10 * (size_t)nf, 0.0);
             for (int x = 0; x < nf; ++x) {
@@ -796,15 +815,6 @@ extern "C" fef_status fef_create(const fef_geometry* g, const fef_basis* bs, con
         }
         b->rot = b->alloc<double>((size_t)9 * nf, "frames");
         ck(launch_frames(d, b->rot, s), "frames");
-        {  // the learned warm start needs fragments of one kind (same atoms and s/p basis)
-            bool uniform = true;
-            for (int x = 1; x < nf && uniform; ++x) uniform = frag_nat[x] == frag_nat[0] && frag_nao[x] == frag_nao[0];
-            if (uniform && max_l <= 1) {
-                c->learn_desc = 4 * frag_nat[0];
-                c->learn_pack = frag_nao[0] * (frag_nao[0] + 1) / 2;
-                c->learn_feat = c->learn_desc + c->learn_pack;  // + the environment operator omega
-            }
-        }
         // neighbour list (within the cutoff) -> pairs x<y and CSR
         std::vector<unsigned char> flags((size_t)nf * nf, 0);
         {
@@ -854,6 +864,8 @@ extern "C" fef_status fef_create(const fef_geometry* g, const fef_basis* bs, con
         d.pair_y = b->upload(pair_y, s, "pairs");
         d.frag_nbr0 = b->upload(nbr0, s, "pairs");
         d.nbr = b->upload(nbr, s, "pairs");
+        c->n_nbr = (int)nbr.size();
+        if (c->learn_feat > 0) ensure_learn_buffers(c);  // no allocation inside fef_iterate's learned start
         d.nbr_pair = b->upload(nbr_pair, s, "pairs");
         b->e_nn_intra = b->alloc<double>(nf, "e_nn");
         b->e_nn_pair = b->alloc<double>(c->n_pairs, "e_nn");
@@ -1116,19 +1128,27 @@ static void ensure_learn_buffers(fef_ctx* c)
         b->Xd = b->alloc<float>((size_t)c->n_frag * c->learn_feat, "learned X");
         b->Yd = b->alloc<float>((size_t)c->n_frag * c->learn_pack, "learned Y");
         b->D_iso = b->alloc<double>(c->mat_total, "D_iso");
+        b->omega_mp = b->alloc<double>(c->mat_total, "multipole omega");
+        b->desc_part = b->alloc<double>((size_t)std::max(c->n_nbr, 1) * c->learn_desc, "descriptor terms");
     }
 }
 
-// Features of the current densities into b->Xd: potential and field at the atoms (columns
-// [0, learn_desc)) and the environment operator omega of a Fock build of the current densities in
-// the Loewdin basis and molecule-fixed frame (columns [learn_desc, learn_feat)).  The features are
-// FP32 network inputs, so omega comes from an FP32-core build.
+// Features of the current densities into b->Xd, with no Fock build: the potential and field of the
+// neighbours (nuclei and Hermite densities) at the atoms (columns [0, learn_desc)) and the multipole
+// estimate of the environment operator (each neighbour's charge, dipole and second moments about its
+// centroid, Taylor-expanded to second order about the fragment's centroid) in the Loewdin basis and
+// molecule-fixed frame (columns [learn_desc, learn_feat)).
 static void compute_features(fef_ctx* c)
 {
     Buffers* b = c->buf;
-    build_fock_internal(c, kBuildFP32Ref);  // omega of the current densities (and their Hermite densities)
-    ck(launch_descriptors(c->dev, b->rot, c->learn_feat, c->learn_desc / 4, b->Xd, c->stream), "descriptors");
-    ck(launch_local_density(c->dev, b->rot, b->Sih, b->omega, c->learn_feat, c->learn_desc, b->Xd, c->stream),
+    const Dev& d = c->dev;
+    ck(launch_hermite_density(d, b->D, c->stream), "hermite density");
+    ck(launch_descriptors(d, b->rot, c->learn_feat, c->learn_desc / 4, c->n_nbr, b->desc_part, b->Xd, c->stream),
+       "descriptors");
+    ck(launch_near_multipole_field(d, b->far_M, b->far_Mnuc, b->far_cen, b->D, b->far_mult, b->far_pot, b->omega_mp,
+                                   c->mat_total, c->stream),
+       "multipole environment operator");
+    ck(launch_local_density(d, b->rot, b->Sih, b->omega_mp, c->learn_feat, c->learn_desc, b->Xd, c->stream),
        "environment operator");
 }
 

@@ -28,6 +28,7 @@ constexpr int kClasses = 5;  // Hermite class L_P = l_a + l_b = 0..4
 struct Dev {
     int n_frag, n_atoms, n_shells, n_sp, n_pairs;
     int max_nao;
+    int max_l;  // largest shell angular momentum
     // atoms
     const double* atom_xyz;
     const double* atom_Z;
@@ -83,7 +84,8 @@ struct Dev {
     const float* fc_qmin;            // [n_frag*kClasses] smallest Schwarz factor of each fragment's class
     const float4* pp_Phi[kClasses];  // df64 (P, p): high floats ...
     const float4* pp_Plo[kClasses];  // ... and low floats (float-float J-engine)
-    float2* pp_Dhdf[kClasses];       // df64 Hermite density (hi, lo)
+    float2* pp_udf[kClasses];        // df64 weights u = p^{-1/2} D_P (hi, lo), per float-float build
+    const float2* pp_sqdf[kClasses]; // df64 sqrt(p)
     int n_pp[kClasses];
     // fragment pairs
     const int* pair_x;
@@ -124,6 +126,7 @@ struct fef_ctx {
     cudaStream_t stream = nullptr;
     int device = 0;
     int n_frag = 0, n_atoms = 0, n_shells = 0, n_prims = 0, n_sp = 0, n_pairs = 0;
+    int n_nbr = 0;  // entries of the neighbour CSR list (2 n_pairs)
     int64_t mat_total = 0, eri_total = 0, coff_total = 0;
     int max_nao = 0, max_nmo = 0;
     std::vector<int> nao, nmo, nocc;
@@ -180,6 +183,12 @@ cudaError_t launch_moment_integrals(const Dev& d, const double* cen, double* M, 
 cudaError_t launch_far_field(const Dev& d, const double* M, const double* Mnuc, const double* cen, const double* D,
                              double* mult, double* pot, double* E_far, double* F, double* omega, cudaStream_t s);
 cudaError_t launch_far_energy(const Dev& d, const double* E_far, double* E_frag, double* E_tot, cudaStream_t s);
+// The same multipole expansion over the neighbours within the cutoff: omega (n_omega doubles, zeroed
+// first) = -(phi S + grad phi . <r> + (1/2) hess phi : <r r>) of each fragment's neighbours' multipoles
+// for the densities D (the learned start's estimate of the environment operator, no Fock build).
+cudaError_t launch_near_multipole_field(const Dev& d, const double* M, const double* Mnuc, const double* cen,
+                                       const double* D, double* mult, double* pot, double* omega, int64_t n_omega,
+                                       cudaStream_t s);
 cudaError_t launch_intra_eri(const Dev& d, const int4* tasks, int n_tasks, double* eri, cudaStream_t s);
 cudaError_t launch_schwarz(const Dev& d, const double* eri, double* sp_Q, float* pp_Q[kClasses], cudaStream_t s);
 cudaError_t launch_coulomb_exchange(const Dev& d, const double* eri, double* eric, cudaStream_t s);
@@ -197,7 +206,7 @@ cudaError_t launch_orthogonaliser(const Dev& d, const double* S, double* X, int*
                                   double* ws = nullptr);
 cudaError_t launch_hermite_density(const Dev& d, const double* D, cudaStream_t s);
 // mode 0: FP64 J-engine on pp_Dh; mode 1: FP32-core J-engine on pp_Dh32; mode 2: float-float
-// J-engine on pp_Dhdf for the s/p classes, FP64 for the rest.  All add into the FP64 accumulators
+// J-engine on pp_udf for the s/p classes, FP64 for the rest.  All add into the FP64 accumulators
 // pp_Jh.
 cudaError_t launch_jengine(const Dev& d, const int2* tiles[kClasses][kClasses], const int* n_tiles, double tau,
                            int mode, cudaStream_t s);
@@ -210,8 +219,8 @@ cudaError_t launch_jengine_class(const Dev& d, int LP, int LQ, const int2* t, in
 cudaError_t launch_jengine_big_class(const Dev& d, int LP, int LQ, const int2* t, int n, float tau, int fp32,
                                      cudaStream_t s);
 cudaError_t launch_jengine_df_class(const Dev& d, int LP, int LQ, const int2* t, int n, float tau, cudaStream_t s);
-cudaError_t launch_df_setup(const Dev& d, float4* const Phi[kClasses], float4* const Plo[kClasses], float2* boysdf,
-                            cudaStream_t s);
+cudaError_t launch_df_setup(const Dev& d, float4* const Phi[kClasses], float4* const Plo[kClasses],
+                            float2* const sqdf[kClasses], float2* boysdf, cudaStream_t s);
 cudaError_t launch_df_density(const Dev& d, cudaStream_t s);
 cudaError_t launch_jengine_big(const Dev& d, const int2* tiles[kClasses][kClasses], const int* n_tiles, float tau,
                                int fp32, cudaStream_t s);
@@ -340,7 +349,9 @@ cudaError_t measure_fma_peak(double* fp64, double* fp32, double* mhz);
 
 // learned warm start (learned.cu, mlp.cu)
 cudaError_t launch_frames(const Dev& d, double* rot, cudaStream_t s);
-cudaError_t launch_descriptors(const Dev& d, const double* rot, int n_feat, int max_nat, float* X, cudaStream_t s);
+// descriptors: part holds n_nbr * max_nat * 4 doubles (per neighbour entry and atom)
+cudaError_t launch_descriptors(const Dev& d, const double* rot, int n_feat, int max_nat, int n_nbr, double* part,
+                               float* X, cudaStream_t s);
 cudaError_t launch_local_density(const Dev& d, const double* rot, const double* Sh, const double* D, int stride,
                                  int col0, float* out, cudaStream_t s);
 cudaError_t launch_apply_learned(const Dev& d, const double* rot, const double* Sih, const double* D_iso,

@@ -1003,56 +1003,115 @@ cudaError_t launch_class_qmin(const Dev& d, float* qmin, cudaStream_t s)
 
 // ------------------------------------------------------------------------------------------ back-transform
 // J^x_{mu nu} = (c/p) sum_{P in shell pair of (mu, nu)} sum_tuv E^{mu nu}_tuv(P) Jh_P[tuv], scaled to
-// normalised AOs.  One thread per (x, mu, nu).
-__global__ void k_back_transform(Dev d, double* J)
+// normalised AOs.  One warp per shell pair (a <= b) of every fragment: each lane takes primitive pairs
+// of the shell pair and forms their Hermite expansion coefficients once for all Cartesian component
+// pairs (compile-time l_a, l_b), the warp sums over the primitive pairs by a butterfly (a fixed order,
+// so the result is reproducible), and lane 0 writes J[mu][nu] and J[nu][mu].
+template <int LA, int LB>
+__device__ __forceinline__ void back_transform_pair(const Dev& d, int sp, int lane, double* __restrict__ J)
 {
-    int x = blockIdx.y;
-    int n = d.frag_nao[x];
-    int nsh = d.frag_nsh[x], sh0 = d.frag_sh0[x], ao0 = d.frag_ao0[x];
-    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n * n; e += gridDim.x * blockDim.x) {
-        int mu = e / n, nu = e % n;
-        int s1 = d.ao_sh[ao0 + mu], s2 = d.ao_sh[ao0 + nu];
-        int k1 = d.ao_k[ao0 + mu], k2 = d.ao_k[ao0 + nu];
-        if (s1 > s2) {
-            int t = s1; s1 = s2; s2 = t;
-            t = k1; k1 = k2; k2 = t;
+    constexpr int NA = ncart(LA), NB = ncart(LB), L = LA + LB, NH = nh(LA + LB);
+    const int s1 = d.sp_a[sp], s2 = d.sp_b[sp];
+    const int x = frag_of_shellpair(d, sp);
+    const double* A = d.atom_xyz + 3 * d.sh_atom[s1];
+    const double* B = d.atom_xyz + 3 * d.sh_atom[s2];
+    const int npp = d.n_pp[L];
+    const int np = d.sh_np[s1] * d.sh_np[s2];
+    const int g0 = d.sp_pp0[sp];
+    double acc[NA * NB];
+#pragma unroll
+    for (int e = 0; e < NA * NB; ++e) acc[e] = 0.0;
+    for (int k = lane; k < np; k += 32) {
+        const int g = g0 + k;
+        const double4_32a P = d.pp_P[L][g];
+        double E[3][3][3][5];
+        md_E1(LA, LB, P.w, P.x - A[0], P.x - B[0], E[0]);
+        md_E1(LA, LB, P.w, P.y - A[1], P.y - B[1], E[1]);
+        md_E1(LA, LB, P.w, P.z - A[2], P.z - B[2], E[2]);
+        double Jh[NH];
+#pragma unroll
+        for (int h = 0; h < NH; ++h) Jh[h] = d.pp_Jh[L][(size_t)h * npp + g];
+        const double sc = d.pp_K[L][g] * kSqrt2Pi52 / P.w;
+#pragma unroll
+        for (int ia = 0; ia < NA; ++ia) {
+            int ax, ay, az;
+            cart_of(LA, ia, ax, ay, az);
+#pragma unroll
+            for (int ib = 0; ib < NB; ++ib) {
+                int bx, by, bz;
+                cart_of(LB, ib, bx, by, bz);
+                double v = 0.0;
+#pragma unroll
+                for (int t = 0; t <= L; ++t)
+#pragma unroll
+                    for (int u = 0; u <= L - t; ++u)
+#pragma unroll
+                        for (int w = 0; w <= L - t - u; ++w)
+                            if (t <= ax + bx && u <= ay + by && w <= az + bz)
+                                v += E[0][ax][bx][t] * E[1][ay][by][u] * E[2][az][bz][w] * Jh[hidx(t, u, w)];
+                acc[ia * NB + ib] = fma(v, sc, acc[ia * NB + ib]);
+            }
         }
-        int a = s1 - sh0, b = s2 - sh0;
-        int sp = d.frag_sp0[x] + a * (2 * nsh - a + 1) / 2 + (b - a);
-        int L = d.sp_L[sp];
-        int la = d.sh_l[s1], lb = d.sh_l[s2];
-        int c1[3], c2[3];
-        cart_of(la, k1, c1[0], c1[1], c1[2]);
-        cart_of(lb, k2, c2[0], c2[1], c2[2]);
-        const double* A = d.atom_xyz + 3 * d.sh_atom[s1];
-        const double* B = d.atom_xyz + 3 * d.sh_atom[s2];
-        int npp = d.n_pp[L];
-        int np = d.sh_np[s1] * d.sh_np[s2];
-        double acc = 0.0;
-        for (int k = 0; k < np; ++k) {
-            int g = d.sp_pp0[sp] + k;
-            double4_32a P = d.pp_P[L][g];
-            double E[3][3][3][5];
-            md_E1(la, lb, P.w, P.x - A[0], P.x - B[0], E[0]);
-            md_E1(la, lb, P.w, P.y - A[1], P.y - B[1], E[1]);
-            md_E1(la, lb, P.w, P.z - A[2], P.z - B[2], E[2]);
-            double v = 0.0;
-            for (int t = 0; t <= c1[0] + c2[0]; ++t)
-                for (int u = 0; u <= c1[1] + c2[1]; ++u)
-                    for (int w = 0; w <= c1[2] + c2[2]; ++w)
-                        v += E[0][c1[0]][c2[0]][t] * E[1][c1[1]][c2[1]][u] * E[2][c1[2]][c2[2]][w] *
-                             d.pp_Jh[L][(size_t)hidx(t, u, w) * npp + g];
-            acc += v * d.pp_K[L][g] * kSqrt2Pi52 / P.w;
-        }
-        J[d.frag_moff[x] + e] = acc * d.ao_scale[ao0 + mu] * d.ao_scale[ao0 + nu];
+    }
+#pragma unroll
+    for (int e = 0; e < NA * NB; ++e)
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) acc[e] += __shfl_xor_sync(0xffffffffu, acc[e], o);
+    if (lane == 0) {
+        const int n = d.frag_nao[x], ao0 = d.frag_ao0[x];
+        const int mu0 = d.sh_ao[s1], nu0 = d.sh_ao[s2];
+        double* Jx = J + d.frag_moff[x];
+#pragma unroll
+        for (int ia = 0; ia < NA; ++ia)
+#pragma unroll
+            for (int ib = 0; ib < NB; ++ib) {
+                const int mu = mu0 + ia, nu = nu0 + ib;
+                const double v = acc[ia * NB + ib] * d.ao_scale[ao0 + mu] * d.ao_scale[ao0 + nu];
+                Jx[mu * n + nu] = v;
+                Jx[nu * n + mu] = v;
+            }
+    }
+}
+
+// Shell pairs of s and p shells, and (second kernel, so that the s/p one keeps its small register
+// footprint) the pairs with a d shell.
+__global__ void __launch_bounds__(128) k_back_transform_sp(Dev d, double* J)
+{
+    const int sp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+    if (sp >= d.n_sp) return;
+    switch (d.sh_l[d.sp_a[sp]] * 3 + d.sh_l[d.sp_b[sp]]) {
+        case 0: back_transform_pair<0, 0>(d, sp, lane, J); break;
+        case 1: back_transform_pair<0, 1>(d, sp, lane, J); break;
+        case 3: back_transform_pair<1, 0>(d, sp, lane, J); break;
+        case 4: back_transform_pair<1, 1>(d, sp, lane, J); break;
+        default: break;
+    }
+}
+
+__global__ void __launch_bounds__(128) k_back_transform_d(Dev d, double* J)
+{
+    const int sp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+    if (sp >= d.n_sp) return;
+    switch (d.sh_l[d.sp_a[sp]] * 3 + d.sh_l[d.sp_b[sp]]) {
+        case 2: back_transform_pair<0, 2>(d, sp, lane, J); break;
+        case 5: back_transform_pair<1, 2>(d, sp, lane, J); break;
+        case 6: back_transform_pair<2, 0>(d, sp, lane, J); break;
+        case 7: back_transform_pair<2, 1>(d, sp, lane, J); break;
+        case 8: back_transform_pair<2, 2>(d, sp, lane, J); break;
+        default: break;
     }
 }
 
 cudaError_t launch_back_transform(const Dev& d, double* J, cudaStream_t s)
 {
-    dim3 g((d.max_nao * d.max_nao + 127) / 128, d.n_frag);
-    k_back_transform<<<g, 128, 0, s>>>(d, J);
+    if (d.n_sp <= 0) return cudaSuccess;
+    const unsigned blocks = (unsigned)(((int64_t)d.n_sp * 32 + 127) / 128);
+    k_back_transform_sp<<<blocks, 128, 0, s>>>(d, J);
     note_launches(1);
+    if (d.max_l >= 2) {
+        k_back_transform_d<<<blocks, 128, 0, s>>>(d, J);
+        note_launches(1);
+    }
     return cudaGetLastError();
 }
 

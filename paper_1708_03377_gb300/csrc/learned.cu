@@ -86,22 +86,27 @@ __device__ __forceinline__ void pair_potential32(const Dev& d, int g, const doub
     });
 }
 
-// X[x][4a + (0..3)] = (phi, E_local) at atom a of fragment x.  One block per (fragment, atom); its
-// threads split every neighbour's nuclei and primitive pairs (terms in FP32, sums in FP64), then a
-// block reduction.
-constexpr int kDescThreads = 128;
+// Descriptors in two steps.  k_descriptor_terms: one block per (neighbour entry c of the CSR list,
+// atom a of its fragment x), its threads split neighbour y's nuclei and primitive pairs (terms in
+// FP32, sums in FP64) and write the block's sums (phi, E) to part[(c max_nat + a) 4 ..].
+// k_descriptor_sum: one thread per (x, a) adds its neighbours' parts in list order (reproducible) and
+// writes X[x][4a + (0..3)] = (phi, E in the frame).
+constexpr int kDescThreads = 64;
 
-__global__ void __launch_bounds__(kDescThreads) k_descriptors(Dev d, const double* rot, int n_feat, int max_nat,
-                                                              float* X)
+__global__ void __launch_bounds__(kDescThreads) k_descriptor_terms(Dev d, int max_nat, double* part)
 {
     __shared__ double red[kDescThreads / 32][4];
-    const int x = blockIdx.x / max_nat, a = blockIdx.x % max_nat;
-    if (a >= d.frag_nat[x]) return;  // whole block leaves together
+    const int c = blockIdx.x / max_nat, a = blockIdx.x % max_nat;
+    int lo = 0, hi = d.n_frag - 1;  // fragment x owning entry c (frag_nbr0 ascending)
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) / 2;
+        if (d.frag_nbr0[mid] <= c) lo = mid; else hi = mid - 1;
+    }
+    const int x = lo;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int c0 = d.frag_nbr0[x], c1 = d.frag_nbr0[x + 1];
-    const double* A = d.atom_xyz + 3 * (d.frag_atom0[x] + a);
     double v[4] = {0.0, 0.0, 0.0, 0.0};
-    for (int c = c0; c < c1; ++c) {
+    if (a < d.frag_nat[x]) {  // whole block
+        const double* A = d.atom_xyz + 3 * (d.frag_atom0[x] + a);
         const int y = d.nbr[c];
         const int naty = d.frag_nat[y];
         int n_items = naty;
@@ -122,12 +127,10 @@ __global__ void __launch_bounds__(kDescThreads) k_descriptors(Dev d, const doubl
                 while (u >= d.frag_npp[y * kClasses + L]) u -= d.frag_npp[y * kClasses + L++];
                 const int g = d.frag_pp0[y * kClasses + L] + u;
                 float o[4] = {0.f, 0.f, 0.f, 0.f};
-                switch (L) {
+                switch (L) {  // s/p fragments only (the learned start rejects d shells)
                     case 0: pair_potential32<0>(d, g, A, o); break;
                     case 1: pair_potential32<1>(d, g, A, o); break;
-                    case 2: pair_potential32<2>(d, g, A, o); break;
-                    case 3: pair_potential32<3>(d, g, A, o); break;
-                    default: pair_potential32<4>(d, g, A, o); break;
+                    default: pair_potential32<2>(d, g, A, o); break;
                 }
                 for (int k = 0; k < 4; ++k) v[k] += (double)o[k];
             }
@@ -139,16 +142,27 @@ __global__ void __launch_bounds__(kDescThreads) k_descriptors(Dev d, const doubl
         if (lane == 0) red[warp][k] = w;
     }
     __syncthreads();
-    if (tid == 0) {
-        double s4[4] = {0.0, 0.0, 0.0, 0.0};
-        for (int w = 0; w < kDescThreads / 32; ++w)
-            for (int k = 0; k < 4; ++k) s4[k] += red[w][k];
-        const double* R = rot + 9 * x;
-        float* out = X + (size_t)x * n_feat + 4 * a;
-        out[0] = (float)s4[0];
-        for (int k = 0; k < 3; ++k)
-            out[1 + k] = (float)(R[0 * 3 + k] * s4[1] + R[1 * 3 + k] * s4[2] + R[2 * 3 + k] * s4[3]);
+    if (tid < 4) {
+        double s4 = 0.0;
+        for (int w = 0; w < kDescThreads / 32; ++w) s4 += red[w][tid];
+        part[((size_t)c * max_nat + a) * 4 + tid] = s4;
     }
+}
+
+__global__ void k_descriptor_sum(Dev d, const double* rot, int n_feat, int max_nat, const double* __restrict__ part,
+                                 float* X)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= d.n_frag * max_nat) return;
+    const int x = i / max_nat, a = i % max_nat;
+    if (a >= d.frag_nat[x]) return;
+    double s4[4] = {0.0, 0.0, 0.0, 0.0};
+    for (int c = d.frag_nbr0[x]; c < d.frag_nbr0[x + 1]; ++c)
+        for (int k = 0; k < 4; ++k) s4[k] += part[((size_t)c * max_nat + a) * 4 + k];
+    const double* R = rot + 9 * x;
+    float* out = X + (size_t)x * n_feat + 4 * a;
+    out[0] = (float)s4[0];
+    for (int k = 0; k < 3; ++k) out[1 + k] = (float)(R[0 * 3 + k] * s4[1] + R[1 * 3 + k] * s4[2] + R[2 * 3 + k] * s4[3]);
 }
 
 // B (n x n) of fragment x into shared memory: 1 on s functions, Rot on each p shell.
@@ -275,9 +289,15 @@ cudaError_t launch_frames(const Dev& d, double* rot, cudaStream_t s)
     return cudaGetLastError();
 }
 
-cudaError_t launch_descriptors(const Dev& d, const double* rot, int n_feat, int max_nat, float* X, cudaStream_t s)
+cudaError_t launch_descriptors(const Dev& d, const double* rot, int n_feat, int max_nat, int n_nbr, double* part,
+                               float* X, cudaStream_t s)
 {
-    k_descriptors<<<d.n_frag * max_nat, kDescThreads, 0, s>>>(d, rot, n_feat, max_nat, X);
+    if (d.n_frag <= 0) return cudaSuccess;
+    if (n_nbr > 0) {
+        k_descriptor_terms<<<(unsigned)((int64_t)n_nbr * max_nat), kDescThreads, 0, s>>>(d, max_nat, part);
+        note_launches(1);
+    }
+    k_descriptor_sum<<<(d.n_frag * max_nat + 127) / 128, 128, 0, s>>>(d, rot, n_feat, max_nat, part, X);
     note_launches(1);
     return cudaGetLastError();
 }

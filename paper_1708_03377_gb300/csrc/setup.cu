@@ -388,10 +388,46 @@ __global__ void k_far_multipoles(Dev d, const double* __restrict__ M, const doub
     }
 }
 
+// Potential of y's multipoles (my: charge, dipole, second moments) at R = c_x - c_y, Taylor terms to
+// second order: phi = q T - mu.T1 + (1/2) M2 : T2 with T_n the derivatives of 1/|R| in closed form,
+// its gradient gy and Hessian Hy.
+__device__ __forceinline__ void multipole_potential(const double R[3], const double* __restrict__ my, double& p,
+                                                    double gy[3], double Hy[3][3])
+{
+    const double q = my[0];
+    const double mu[3] = {my[1], my[2], my[3]};
+    const double M2[3][3] = {{my[4], my[5], my[6]}, {my[5], my[7], my[8]}, {my[6], my[8], my[9]}};
+    const double r2 = R[0] * R[0] + R[1] * R[1] + R[2] * R[2];
+    const double ir = rsqrt(r2), ir2 = ir * ir;
+    const double ir3 = ir * ir2, ir5 = ir3 * ir2, ir7 = ir5 * ir2, ir9 = ir7 * ir2;
+    double MR[3];
+    for (int a = 0; a < 3; ++a) MR[a] = M2[a][0] * R[0] + M2[a][1] * R[1] + M2[a][2] * R[2];
+    const double RMR = R[0] * MR[0] + R[1] * MR[1] + R[2] * MR[2];
+    const double trM = M2[0][0] + M2[1][1] + M2[2][2];
+    const double muR = mu[0] * R[0] + mu[1] * R[1] + mu[2] * R[2];
+    // phi = q/r + mu.R/r^3 + (1/2)(3 RMR/r^5 - trM/r^3)
+    p = q * ir + muR * ir3 + 0.5 * (3.0 * RMR * ir5 - trM * ir3);
+    for (int c = 0; c < 3; ++c) {
+        // g_c = q T_c - sum_a mu_a T_ac + (1/2) sum_ab M_ab T_abc
+        const double Tc = -R[c] * ir3;
+        const double muT2 = 3.0 * muR * R[c] * ir5 - mu[c] * ir3;
+        const double MT3 = -15.0 * RMR * R[c] * ir7 + 3.0 * (2.0 * MR[c] + trM * R[c]) * ir5;
+        gy[c] = q * Tc - muT2 + 0.5 * MT3;
+        for (int e = 0; e < 3; ++e) {
+            const double dce = c == e ? 1.0 : 0.0;
+            const double T2 = (3.0 * R[c] * R[e] - r2 * dce) * ir5;
+            const double muT3 = -15.0 * muR * R[c] * R[e] * ir7 + 3.0 * (mu[c] * R[e] + mu[e] * R[c] + muR * dce) * ir5;
+            const double MT4 = 105.0 * RMR * R[c] * R[e] * ir9
+                               - 15.0 * (RMR * dce + 2.0 * R[c] * MR[e] + 2.0 * R[e] * MR[c] + trM * R[c] * R[e]) * ir7
+                               + 3.0 * (trM * dce + 2.0 * M2[c][e]) * ir5;
+            Hy[c][e] = q * T2 - muT3 + 0.5 * MT4;
+        }
+    }
+}
+
 // Potential of the far fragments at c_x, summed: pot[x] = (phi, grad phi[3], hess phi[xx xy xz yy yz zz]),
-// with y's potential phi(R) = q T - mu.T1 + (1/2) M2 : T2 at R = c_x - c_y (T_n the derivatives of
-// 1/|R|, contracted in closed form), and E_far[x] = (1/2) sum_y (q_x phi + mu_x . g + (1/2) M2_x : H).
-// One thread per fragment; pairs within the cutoff (the neighbour list) are skipped.
+// and E_far[x] = (1/2) sum_y (q_x phi + mu_x . g + (1/2) M2_x : H).  One thread per fragment; pairs
+// within the cutoff (the neighbour list) are skipped.
 __global__ void k_far_potential(Dev d, const double* __restrict__ cen, const double* __restrict__ mult, double* pot,
                                 double* E_far)
 {
@@ -407,39 +443,10 @@ __global__ void k_far_potential(Dev d, const double* __restrict__ cen, const dou
         bool near = false;
         for (int c = d.frag_nbr0[x]; c < d.frag_nbr0[x + 1]; ++c) near = near || d.nbr[c] == y;
         if (near) continue;
-        const double* my = mult + 10 * y;
-        const double q = my[0];
-        const double mu[3] = {my[1], my[2], my[3]};
-        const double M2[3][3] = {{my[4], my[5], my[6]}, {my[5], my[7], my[8]}, {my[6], my[8], my[9]}};
         double R[3];
         for (int a = 0; a < 3; ++a) R[a] = cx[a] - cen[3 * y + a];
-        const double r2 = R[0] * R[0] + R[1] * R[1] + R[2] * R[2];
-        const double ir = rsqrt(r2), ir2 = ir * ir;
-        const double ir3 = ir * ir2, ir5 = ir3 * ir2, ir7 = ir5 * ir2, ir9 = ir7 * ir2;
-        double MR[3];
-        for (int a = 0; a < 3; ++a) MR[a] = M2[a][0] * R[0] + M2[a][1] * R[1] + M2[a][2] * R[2];
-        const double RMR = R[0] * MR[0] + R[1] * MR[1] + R[2] * MR[2];
-        const double trM = M2[0][0] + M2[1][1] + M2[2][2];
-        const double muR = mu[0] * R[0] + mu[1] * R[1] + mu[2] * R[2];
-        // phi = q/r + mu.R/r^3 + (1/2)(3 RMR/r^5 - trM/r^3)
-        const double p = q * ir + muR * ir3 + 0.5 * (3.0 * RMR * ir5 - trM * ir3);
-        double gy[3], Hy[3][3];
-        for (int c = 0; c < 3; ++c) {
-            // g_c = q T_c - sum_a mu_a T_ac + (1/2) sum_ab M_ab T_abc
-            const double Tc = -R[c] * ir3;
-            const double muT2 = 3.0 * muR * R[c] * ir5 - mu[c] * ir3;
-            const double MT3 = -15.0 * RMR * R[c] * ir7 + 3.0 * (2.0 * MR[c] + trM * R[c]) * ir5;
-            gy[c] = q * Tc - muT2 + 0.5 * MT3;
-            for (int e = 0; e < 3; ++e) {
-                const double dce = c == e ? 1.0 : 0.0;
-                const double T2 = (3.0 * R[c] * R[e] - r2 * dce) * ir5;
-                const double muT3 = -15.0 * muR * R[c] * R[e] * ir7 + 3.0 * (mu[c] * R[e] + mu[e] * R[c] + muR * dce) * ir5;
-                const double MT4 = 105.0 * RMR * R[c] * R[e] * ir9
-                                   - 15.0 * (RMR * dce + 2.0 * R[c] * MR[e] + 2.0 * R[e] * MR[c] + trM * R[c] * R[e]) * ir7
-                                   + 3.0 * (trM * dce + 2.0 * M2[c][e]) * ir5;
-                Hy[c][e] = q * T2 - muT3 + 0.5 * MT4;
-            }
-        }
+        double p, gy[3], Hy[3][3];
+        multipole_potential(R, mult + 10 * y, p, gy, Hy);
         double exy = mx[0] * p;
         for (int c = 0; c < 3; ++c) {
             exy += mx[1 + c] * gy[c];
@@ -457,6 +464,33 @@ __global__ void k_far_potential(Dev d, const double* __restrict__ cen, const dou
     o[1] = g[0]; o[2] = g[1]; o[3] = g[2];
     o[4] = H[0][0]; o[5] = H[0][1]; o[6] = H[0][2]; o[7] = H[1][1]; o[8] = H[1][2]; o[9] = H[2][2];
     E_far[x] = 0.5 * e_sum;
+}
+
+// The same expansion over the neighbours within the cutoff instead (the learned start's multipole
+// estimate of the environment operator; no energy).  One warp per fragment, lanes over neighbours.
+__global__ void k_near_multipole_potential(Dev d, const double* __restrict__ cen, const double* __restrict__ mult,
+                                           double* pot)
+{
+    const int x = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+    if (x >= d.n_frag) return;
+    double acc[10] = {};
+    const double* cx = cen + 3 * x;
+    for (int c = d.frag_nbr0[x] + lane; c < d.frag_nbr0[x + 1]; c += 32) {
+        const int y = d.nbr[c];
+        double R[3];
+        for (int a = 0; a < 3; ++a) R[a] = cx[a] - cen[3 * y + a];
+        double p, gy[3], Hy[3][3];
+        multipole_potential(R, mult + 10 * y, p, gy, Hy);
+        acc[0] += p;
+        acc[1] += gy[0]; acc[2] += gy[1]; acc[3] += gy[2];
+        acc[4] += Hy[0][0]; acc[5] += Hy[0][1]; acc[6] += Hy[0][2]; acc[7] += Hy[1][1]; acc[8] += Hy[1][2];
+        acc[9] += Hy[2][2];
+    }
+    for (int k = 0; k < 10; ++k) {
+        double v = acc[k];
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if (lane == 0) pot[10 * x + k] = v;
+    }
 }
 
 // F^x and omega_x += -(phi S + grad phi . <r> + (1/2) hess phi : <r r>) (the density derivative of
@@ -505,6 +539,20 @@ cudaError_t launch_far_field(const Dev& d, const double* M, const double* Mnuc, 
     k_far_potential<<<(d.n_frag + 127) / 128, 128, 0, s>>>(d, cen, mult, pot, E_far);
     dim3 g((d.max_nao * d.max_nao + 127) / 128, d.n_frag);
     k_far_fock<<<g, 128, 0, s>>>(d, M, pot, F, omega);
+    note_launches(3);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_near_multipole_field(const Dev& d, const double* M, const double* Mnuc, const double* cen,
+                                       const double* D, double* mult, double* pot, double* omega, int64_t n_omega,
+                                       cudaStream_t s)
+{
+    cudaError_t e = cudaMemsetAsync(omega, 0, sizeof(double) * n_omega, s);
+    if (e != cudaSuccess || d.n_frag <= 0) return e;
+    k_far_multipoles<<<d.n_frag, 128, 0, s>>>(d, M, Mnuc, D, mult);
+    k_near_multipole_potential<<<(d.n_frag + 3) / 4, 128, 0, s>>>(d, cen, mult, pot);
+    dim3 g((d.max_nao * d.max_nao + 127) / 128, d.n_frag);
+    k_far_fock<<<g, 128, 0, s>>>(d, M, pot, nullptr, omega);
     note_launches(3);
     return cudaGetLastError();
 }
