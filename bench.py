@@ -18,6 +18,8 @@ Legs reported beside it (same workload, same 1e-8 Eh convergence, energies compa
   mixed                MIXED with the float-float reference build;
   mixed_learned        MIXED (float-float reference) from the learned warm start; the network is
                        trained beforehand (not timed) on 40 seeded snapshots drawn like the workload.
+learned_2000_waters: the learned start at full size, reduced: trained on 8 x 500-water boxes (not
+       timed), MIXED solves of 2 held-out 2000-water boxes from the superposition and the learned start.
 e_m2 / e_d2: one fef_energy_m2 / fef_energy_d2 call on the converged FP64 state (second-order
        energies, Eqs. EM2 and ED2), wall clock.
 e2e    = the same step plus the device->host read of every converged density, wall clock.
@@ -249,6 +251,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--ref-seconds", type=float, default=8.0)
+    ap.add_argument("--no-learned-2000", action="store_true",
+                    help="skip the reduced full-size learned-start leg (2000-water held-out boxes)")
     args = ap.parse_args()
     ws, rank, local = dist_env()
     if args.impl == "reference":
@@ -421,6 +425,14 @@ def main():
             e2e_ms.append(1e3 * (time.perf_counter() - t0))
         torch.cuda.synchronize()
 
+    # learned start at full size, reduced: trained on 8 x 500 waters (100 fragments each, not timed),
+    # then MIXED from the superposition and from the learned start on 2 held-out 2000-water boxes
+    # (time to 1e-8 Eh of fef_iterate by CUDA events, after one untimed solve per leg)
+    learned_2000 = None
+    if not args.no_learned_2000 and rank == 0:
+        learned_2000 = lrn.run_experiment(train_snapshots=8, train_waters=500, per_snapshot=100, test_snapshots=2,
+                                          test_waters=2000, fp64_test_snapshots=0, cutoff=CUTOFF_A, e_tol=E_TOL,
+                                          epochs=200, warmup=1)
     total_ms = float(sum(step_ms))
     if pg:
         total_ms, quartets, launches = reduce_over_replicas(pg, total_ms, quartets, launches, "cuda")
@@ -470,6 +482,7 @@ def main():
         "mixed_learned": {**summary(ml_ms, ml_step_ms, mlres), "exact_engine": "df64",
                           "train_samples": int(sum(len(x) for x in Xs)),
                           "train_loss": net_loss},
+        "learned_2000_waters": learned_2000,
         "e_m2": {"ms_per_call": float(min(m2_ms[1:])), "E_m2_total": m2_tot, "transform_flop": m2_flop,
                  "note": "monomer second-order energy (Eq. EM2) of all fragments on the FEF canonical orbitals"},
         "e_d2": {"ms_per_call": float(min(d2_ms[1:])), "E_d2_total": d2_tot,

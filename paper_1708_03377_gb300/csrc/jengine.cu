@@ -20,49 +20,93 @@
 namespace fef {
 
 // ------------------------------------------------------------------------------------------ densities
-__global__ void k_hermite_density(Dev d, int L, const double* __restrict__ D)
+// Hermite density of one primitive pair g of class L (shell pair of angular momenta LA, LB known at
+// compile time, so that the expansion coefficients stay in registers):
+//   Dh_P[tuv] = (2 pi^{5/2} K / p) sum_{mu in a, nu in b} w D_{mu nu} E^{mu nu}_tuv(P),
+// w = 2 for a != b (both triangles), and the J-engine weights u = p^{-1/2} Dh_P.
+template <int LA, int LB>
+__device__ __forceinline__ void hermite_density_pair(const Dev& d, int L, int g, const double* __restrict__ D)
 {
-    int g = blockIdx.x * blockDim.x + threadIdx.x;
-    int npp = d.n_pp[L];
-    if (g >= npp) return;
-    int sp = d.pp_sp[L][g], ij = d.pp_ij[L][g];
-    int sa = d.sp_a[sp], sb = d.sp_b[sp];
-    int x = frag_of_shellpair(d, sp);
-    int la = d.sh_l[sa], lb = d.sh_l[sb];
+    constexpr int NH = nh(LA + LB);
+    const int npp = d.n_pp[L];
+    const int sp = d.pp_sp[L][g];
+    const int sa = d.sp_a[sp], sb = d.sp_b[sp];
+    const int x = frag_of_shellpair(d, sp);
     const double* A = d.atom_xyz + 3 * d.sh_atom[sa];
     const double* B = d.atom_xyz + 3 * d.sh_atom[sb];
-    double4_32a P = d.pp_P[L][g];
-    double p = P.w;
+    const double4_32a P = d.pp_P[L][g];
+    const double p = P.w;
     double E[3][3][3][5];
-    md_E1(la, lb, p, P.x - A[0], P.x - B[0], E[0]);
-    md_E1(la, lb, p, P.y - A[1], P.y - B[1], E[1]);
-    md_E1(la, lb, p, P.z - A[2], P.z - B[2], E[2]);
+    md_E1(LA, LB, p, P.x - A[0], P.x - B[0], E[0]);
+    md_E1(LA, LB, p, P.y - A[1], P.y - B[1], E[1]);
+    md_E1(LA, LB, p, P.z - A[2], P.z - B[2], E[2]);
     const int n = d.frag_nao[x];
     const double* Dx = D + d.frag_moff[x];
     const int ao0 = d.frag_ao0[x];
-    double w = (sa == sb) ? 1.0 : 2.0;
-    double acc[nh(kMaxLPair)];
-    for (int k = 0; k < nh(L); ++k) acc[k] = 0.0;
-    for (int ia = 0; ia < ncart(la); ++ia) {
+    const double w = (sa == sb) ? 1.0 : 2.0;
+    const int mu0 = d.sh_ao[sa], nu0 = d.sh_ao[sb];
+    double acc[NH];
+#pragma unroll
+    for (int k = 0; k < NH; ++k) acc[k] = 0.0;
+#pragma unroll
+    for (int ia = 0; ia < ncart(LA); ++ia) {
         int ax, ay, az;
-        cart_of(la, ia, ax, ay, az);
-        int mu = d.sh_ao[sa] + ia;
-        for (int ib = 0; ib < ncart(lb); ++ib) {
+        cart_of(LA, ia, ax, ay, az);
+        const int mu = mu0 + ia;
+#pragma unroll
+        for (int ib = 0; ib < ncart(LB); ++ib) {
             int bx, by, bz;
-            cart_of(lb, ib, bx, by, bz);
-            int nu = d.sh_ao[sb] + ib;
-            double dmn = w * Dx[mu * n + nu] * d.ao_scale[ao0 + mu] * d.ao_scale[ao0 + nu];
-            for (int t = 0; t <= ax + bx; ++t)
-                for (int u = 0; u <= ay + by; ++u)
-                    for (int v = 0; v <= az + bz; ++v)
-                        acc[hidx(t, u, v)] += dmn * E[0][ax][bx][t] * E[1][ay][by][u] * E[2][az][bz][v];
+            cart_of(LB, ib, bx, by, bz);
+            const int nu = nu0 + ib;
+            const double dmn = w * Dx[mu * n + nu] * d.ao_scale[ao0 + mu] * d.ao_scale[ao0 + nu];
+#pragma unroll
+            for (int t = 0; t <= LA + LB; ++t)
+#pragma unroll
+                for (int u = 0; u <= LA + LB - t; ++u)
+#pragma unroll
+                    for (int v = 0; v <= LA + LB - t - u; ++v)
+                        if (t <= ax + bx && u <= ay + by && v <= az + bz)
+                            acc[hidx(t, u, v)] += dmn * E[0][ax][bx][t] * E[1][ay][by][u] * E[2][az][bz][v];
         }
     }
-    double sc = d.pp_K[L][g] * kSqrt2Pi52 / p;
+    const double sc = d.pp_K[L][g] * kSqrt2Pi52 / p;
     const double rp = d.pp_rp[L][g];
-    for (int k = 0; k < nh(L); ++k) {
+#pragma unroll
+    for (int k = 0; k < NH; ++k) {
         d.pp_Dh[L][(size_t)k * npp + g] = acc[k] * sc;
         d.pp_u[L][(size_t)k * npp + g] = acc[k] * sc * rp;
+    }
+}
+
+// Systems of s and p shells only (the smaller register footprint), and the general kernel.
+__global__ void k_hermite_density_sp(Dev d, int L, const double* __restrict__ D)
+{
+    const int g = blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= d.n_pp[L]) return;
+    const int sp = d.pp_sp[L][g];
+    switch (d.sh_l[d.sp_a[sp]] * 3 + d.sh_l[d.sp_b[sp]]) {
+        case 0: hermite_density_pair<0, 0>(d, L, g, D); break;
+        case 1: hermite_density_pair<0, 1>(d, L, g, D); break;
+        case 3: hermite_density_pair<1, 0>(d, L, g, D); break;
+        default: hermite_density_pair<1, 1>(d, L, g, D); break;
+    }
+}
+
+__global__ void k_hermite_density(Dev d, int L, const double* __restrict__ D)
+{
+    const int g = blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= d.n_pp[L]) return;
+    const int sp = d.pp_sp[L][g];
+    switch (d.sh_l[d.sp_a[sp]] * 3 + d.sh_l[d.sp_b[sp]]) {
+        case 0: hermite_density_pair<0, 0>(d, L, g, D); break;
+        case 1: hermite_density_pair<0, 1>(d, L, g, D); break;
+        case 2: hermite_density_pair<0, 2>(d, L, g, D); break;
+        case 3: hermite_density_pair<1, 0>(d, L, g, D); break;
+        case 4: hermite_density_pair<1, 1>(d, L, g, D); break;
+        case 5: hermite_density_pair<1, 2>(d, L, g, D); break;
+        case 6: hermite_density_pair<2, 0>(d, L, g, D); break;
+        case 7: hermite_density_pair<2, 1>(d, L, g, D); break;
+        default: hermite_density_pair<2, 2>(d, L, g, D); break;
     }
 }
 
@@ -70,7 +114,10 @@ cudaError_t launch_hermite_density(const Dev& d, const double* D, cudaStream_t s
 {
     for (int L = 0; L < kClasses; ++L)
         if (d.n_pp[L] > 0) {
-            k_hermite_density<<<(d.n_pp[L] + 127) / 128, 128, 0, s>>>(d, L, D);
+            if (d.max_l <= 1)
+                k_hermite_density_sp<<<(d.n_pp[L] + 127) / 128, 128, 0, s>>>(d, L, D);
+            else
+                k_hermite_density<<<(d.n_pp[L] + 127) / 128, 128, 0, s>>>(d, L, D);
             note_launches(1);
         }
     return cudaGetLastError();

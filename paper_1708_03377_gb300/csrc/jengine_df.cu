@@ -159,6 +159,27 @@ __device__ __forceinline__ void df_ketbuf_flush(const DfKetBuf& kb, int cnt, dou
     __syncwarp();
 }
 
+// Sum of df64 products kept unnormalised (s + c): each product x y adds its rounded leading part to s
+// by Knuth's two-sum and its error terms (the FMA residual of x.hi y.hi and the cross products) to c,
+// with no renormalisation per term (the compensated dot product of Ogita, Rump and Oishi, 2005);
+// 12 FP32 operations per term instead of 15 for a normalised df64 fma.
+struct dfacc {
+    float s, c;
+};
+
+__device__ __forceinline__ void acc_prod(dfacc& a, df64 x, df64 y)
+{
+    const float p = __fmul_rn(x.hi, y.hi);
+    float e = __fmaf_rn(x.hi, y.hi, -p);
+    e = __fmaf_rn(x.hi, y.lo, e);
+    e = __fmaf_rn(x.lo, y.hi, e);
+    const float s = __fadd_rn(a.s, p);
+    const float bp = __fsub_rn(s, a.s);
+    const float t = __fadd_rn(__fsub_rn(a.s, __fsub_rn(s, bp)), __fsub_rn(p, bp));
+    a.s = s;
+    a.c = __fadd_rn(a.c, __fadd_rn(t, e));
+}
+
 // 1/sqrt(x) of a df64 x > 0 from a float seed s ~ x.hi^{-1/2} (relative error <= 2^-22): one float
 // Newton step, then one df64 correction y = r + r e / 2 with e = 1 - x r^2 formed exactly enough
 // (r^2 as an exact float product pair, 1 - (x r^2).hi exact by Sterbenz); relative error ~1e-14.
@@ -239,12 +260,13 @@ __device__ __forceinline__ void jtile_df(const Dev& d, const int2 tl, const int 
     const df64 sqp(sqp2.x, sqp2.y);
     const float4 Pf = d.pp_Pf[LP][Pl];
     const float qP = valid ? d.pp_Q[LP][Pl] : 0.0f;
-    df64 DP[NP], JP[NP];
+    df64 DP[NP];
+    dfacc JP[NP];
     double JP64[NP];
 #pragma unroll
     for (int i = 0; i < NP; ++i) {
         DP[i] = valid ? ld_df(d.pp_udf[LP] + (size_t)i * nP + Pl) : df64(0.0f, 0.0f);
-        JP[i] = df64(0.0f, 0.0f);
+        JP[i] = dfacc{0.0f, 0.0f};
         JP64[i] = 0.0;
     }
     const float4* __restrict__ QH = d.pp_Phi[LQ];
@@ -292,31 +314,29 @@ __device__ __forceinline__ void jtile_df(const Dev& d, const int2 tl, const int 
         }
         df64 R[NR];
         md_R<L, df64>(R, base, X, Y, Z);
-        // field on the bra pair (registers)
+        // field on the bra pair (registers, unnormalised sums)
         static_for<NP>([&](auto I) {
             constexpr TUV a = htuv(decltype(I)::value);
-            df64 acc = JP[decltype(I)::value];
             static_for<NQ>([&](auto Jc) {
                 constexpr TUV b = htuv(decltype(Jc)::value);
                 constexpr int rr = hidx(a.t + b.t, a.u + b.u, a.v + b.v);
                 if constexpr (((b.t + b.u + b.v) & 1) != 0)
-                    acc = fma(-R[rr], DQ[decltype(Jc)::value], acc);
+                    acc_prod(JP[decltype(I)::value], -R[rr], DQ[decltype(Jc)::value]);
                 else
-                    acc = fma(R[rr], DQ[decltype(Jc)::value], acc);
+                    acc_prod(JP[decltype(I)::value], R[rr], DQ[decltype(Jc)::value]);
             });
-            JP[decltype(I)::value] = acc;
         });
-        // field on the ket pair: this lane's float-float partial sums, staged for the batch
+        // field on the ket pair: this lane's float-float partial sums (unnormalised), staged for the batch
         float2* row = kbuf.v + lane * kDfBufLd + cnt * NQ;
         static_for<NQ>([&](auto Jc) {
             constexpr TUV b = htuv(decltype(Jc)::value);
-            df64 s(0.0f, 0.0f);
+            dfacc s{0.0f, 0.0f};
             static_for<NP>([&](auto I) {
                 constexpr TUV a = htuv(decltype(I)::value);
-                s = fma(R[hidx(a.t + b.t, a.u + b.u, a.v + b.v)], DP[decltype(I)::value], s);
+                acc_prod(s, R[hidx(a.t + b.t, a.u + b.u, a.v + b.v)], DP[decltype(I)::value]);
             });
-            if ((b.t + b.u + b.v) & 1) s = -s;
-            row[decltype(Jc)::value] = make_float2(s.hi, s.lo);
+            if ((b.t + b.u + b.v) & 1) row[decltype(Jc)::value] = make_float2(-s.s, -s.c);
+            else row[decltype(Jc)::value] = make_float2(s.s, s.c);
         });
         if (lane == 0) kbuf.k[cnt] = k;
         if (++cnt == kBatch) {
@@ -327,8 +347,8 @@ __device__ __forceinline__ void jtile_df(const Dev& d, const int2 tl, const int 
             since_flush = 0;
 #pragma unroll
             for (int i = 0; i < NP; ++i) {
-                JP64[i] += f2d(JP[i].hi) + f2d(JP[i].lo);
-                JP[i] = df64(0.0f, 0.0f);
+                JP64[i] += f2d(JP[i].s) + f2d(JP[i].c);
+                JP[i] = dfacc{0.0f, 0.0f};
             }
         }
     }
@@ -337,7 +357,7 @@ __device__ __forceinline__ void jtile_df(const Dev& d, const int2 tl, const int 
         const double aP = kSqrtPiHalf * d.pp_rp[LP][Pl];
 #pragma unroll
         for (int i = 0; i < NP; ++i)
-            atomicAdd(d.pp_Jh[LP] + (size_t)i * nP + Pl, (JP64[i] + (f2d(JP[i].hi) + f2d(JP[i].lo))) * aP);
+            atomicAdd(d.pp_Jh[LP] + (size_t)i * nP + Pl, (JP64[i] + (f2d(JP[i].s) + f2d(JP[i].c))) * aP);
     }
 }
 

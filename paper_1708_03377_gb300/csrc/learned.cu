@@ -55,17 +55,17 @@ __global__ void k_frames(Dev d, double* rot)
     }
 }
 
-// Potential and field at A from the Hermite density of one primitive pair of class L, in FP32
-// (the descriptors are FP32 network inputs): Boys, R recursion and contraction in FP32 on the
-// FP64-formed difference Q - A.
+// Potential and field at the point r (relative to the anchor of the pair's fragment) from the
+// Hermite density Dt of one primitive pair of class L with centre Pr (same anchor) and exponent p,
+// all in FP32 (the descriptors are FP32 network inputs): Boys, R recursion and contraction.
 template <int L>
-__device__ __forceinline__ void pair_potential32(const Dev& d, int g, const double* A, float* out)
+__device__ __forceinline__ void pair_potential32(const float* __restrict__ boys32, float4 Pr, const float* Dt,
+                                                 const float* r, float* out)
 {
-    const double4_32a Q = d.pp_P[L][g];
-    const float q = (float)Q.w;
-    const float X = (float)(Q.x - A[0]), Y = (float)(Q.y - A[1]), Z = (float)(Q.z - A[2]);
+    const float q = Pr.w;
+    const float X = Pr.x - r[0], Y = Pr.y - r[1], Z = Pr.z - r[2];
     float F[L + 2], base[L + 2], R[nh(L + 1)];
-    boys_fp32<L + 1>(d.boys32, q * (X * X + Y * Y + Z * Z), F);
+    boys_fp32<L + 1>(boys32, q * (X * X + Y * Y + Z * Z), F);
     float f = 2.0f * (float)kPi / q;
 #pragma unroll
     for (int n = 0; n <= L + 1; ++n) {
@@ -73,79 +73,110 @@ __device__ __forceinline__ void pair_potential32(const Dev& d, int g, const doub
         f *= -2.0f * q;
     }
     md_R<L + 1, float>(R, base, X, Y, Z);
-    const int npp = d.n_pp[L];
-    const double sc = Q.w / kSqrt2Pi52;  // Dh holds D K c/q
     static_for<nh(L)>([&](auto kk) {
         constexpr int k = decltype(kk)::value;
         constexpr TUV c = htuv(k);
-        const float Dt = (float)(d.pp_Dh[L][(size_t)k * npp + g] * sc);
-        out[0] = fmaf(-Dt, R[k], out[0]);
-        out[1] = fmaf(-Dt, R[hidx(c.t + 1, c.u, c.v)], out[1]);
-        out[2] = fmaf(-Dt, R[hidx(c.t, c.u + 1, c.v)], out[2]);
-        out[3] = fmaf(-Dt, R[hidx(c.t, c.u, c.v + 1)], out[3]);
+        out[0] = fmaf(-Dt[k], R[k], out[0]);
+        out[1] = fmaf(-Dt[k], R[hidx(c.t + 1, c.u, c.v)], out[1]);
+        out[2] = fmaf(-Dt[k], R[hidx(c.t, c.u + 1, c.v)], out[2]);
+        out[3] = fmaf(-Dt[k], R[hidx(c.t, c.u, c.v + 1)], out[3]);
     });
 }
 
-// Descriptors in two steps.  k_descriptor_terms: one block per (neighbour entry c of the CSR list,
-// atom a of its fragment x), its threads split neighbour y's nuclei and primitive pairs (terms in
-// FP32, sums in FP64) and write the block's sums (phi, E) to part[(c max_nat + a) 4 ..].
+// FP32 Hermite densities of the current densities for the descriptors, Dt = Dh p / (2 pi^{5/2})
+// (Dh holds D K c 2 pi^{5/2} / p), into the FP32 scratch pp_Dh32 (rebuilt by every FP32-core build).
+__global__ void k_descriptor_density(Dev d, int L)
+{
+    const int npp = d.n_pp[L];
+    const int g = blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= npp) return;
+    const double sc = d.pp_P[L][g].w * (1.0 / kSqrt2Pi52);
+    for (int k = 0; k < nh(L); ++k) d.pp_Dh32[L][(size_t)k * npp + g] = (float)(d.pp_Dh[L][(size_t)k * npp + g] * sc);
+}
+
+// Descriptors in two steps.  k_descriptor_terms: one block per neighbour entry c = (x, y) of the CSR
+// list; its threads split y's nuclei and primitive pairs, each item contributes to every atom of x
+// (atoms and pair centres relative to y's anchor atom, FP32 terms and per-thread sums), and the block
+// writes its sums (phi, E) per atom to part[(c max_nat + a) 4 ..] (FP64 block reduction).
 // k_descriptor_sum: one thread per (x, a) adds its neighbours' parts in list order (reproducible) and
 // writes X[x][4a + (0..3)] = (phi, E in the frame).
-constexpr int kDescThreads = 64;
+constexpr int kDescThreads = 128;
+constexpr int kDescAtoms = 4;  // atoms of x per pass over y's items
 
 __global__ void __launch_bounds__(kDescThreads) k_descriptor_terms(Dev d, int max_nat, double* part)
 {
-    __shared__ double red[kDescThreads / 32][4];
-    const int c = blockIdx.x / max_nat, a = blockIdx.x % max_nat;
+    __shared__ double red[kDescThreads / 32][kDescAtoms * 4];
+    __shared__ float rel[kDescAtoms][3];
+    const int c = blockIdx.x;
     int lo = 0, hi = d.n_frag - 1;  // fragment x owning entry c (frag_nbr0 ascending)
     while (lo < hi) {
         const int mid = (lo + hi + 1) / 2;
         if (d.frag_nbr0[mid] <= c) lo = mid; else hi = mid - 1;
     }
-    const int x = lo;
+    const int x = lo, y = d.nbr[c];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    double v[4] = {0.0, 0.0, 0.0, 0.0};
-    if (a < d.frag_nat[x]) {  // whole block
-        const double* A = d.atom_xyz + 3 * (d.frag_atom0[x] + a);
-        const int y = d.nbr[c];
-        const int naty = d.frag_nat[y];
-        int n_items = naty;
-        for (int L = 0; L < kClasses; ++L) n_items += d.frag_npp[y * kClasses + L];
-        for (int t = tid; t < n_items; t += kDescThreads) {
-            if (t < naty) {
-                const double* B = d.atom_xyz + 3 * (d.frag_atom0[y] + t);
-                const double Zb = d.atom_Z[d.frag_atom0[y] + t];
-                const double dx = A[0] - B[0], dy = A[1] - B[1], dz = A[2] - B[2];
-                const double r2 = dx * dx + dy * dy + dz * dz, r = sqrt(r2);
-                const double f = Zb / (r2 * r);
-                v[0] += Zb / r;
-                v[1] += f * dx;
-                v[2] += f * dy;
-                v[3] += f * dz;
-            } else {
-                int u = t - naty, L = 0;
-                while (u >= d.frag_npp[y * kClasses + L]) u -= d.frag_npp[y * kClasses + L++];
-                const int g = d.frag_pp0[y * kClasses + L] + u;
-                float o[4] = {0.f, 0.f, 0.f, 0.f};
-                switch (L) {  // s/p fragments only (the learned start rejects d shells)
-                    case 0: pair_potential32<0>(d, g, A, o); break;
-                    case 1: pair_potential32<1>(d, g, A, o); break;
-                    default: pair_potential32<2>(d, g, A, o); break;
-                }
-                for (int k = 0; k < 4; ++k) v[k] += (double)o[k];
+    const int nat = d.frag_nat[x], naty = d.frag_nat[y];
+    const double* anc = d.atom_xyz + 3 * d.frag_atom0[y];
+    for (int a0 = 0; a0 < max_nat; a0 += kDescAtoms) {
+        const int na = max(0, min(kDescAtoms, nat - a0));
+        if (tid < 3 * kDescAtoms) {
+            const int a = tid / 3, k = tid % 3;
+            rel[a][k] = a < na ? (float)(d.atom_xyz[3 * (d.frag_atom0[x] + a0 + a) + k] - anc[k]) : 0.0f;
+        }
+        __syncthreads();
+        float v[kDescAtoms][4] = {};
+        // nuclei of y
+        for (int t = tid; t < naty; t += kDescThreads) {
+            const float Zb = (float)d.atom_Z[d.frag_atom0[y] + t];
+            const float bx = (float)(d.atom_xyz[3 * (d.frag_atom0[y] + t)] - anc[0]);
+            const float by = (float)(d.atom_xyz[3 * (d.frag_atom0[y] + t) + 1] - anc[1]);
+            const float bz = (float)(d.atom_xyz[3 * (d.frag_atom0[y] + t) + 2] - anc[2]);
+#pragma unroll
+            for (int a = 0; a < kDescAtoms; ++a) {
+                if (a >= na) break;
+                const float dx = rel[a][0] - bx, dy = rel[a][1] - by, dz = rel[a][2] - bz;
+                const float ir = rsqrtf(dx * dx + dy * dy + dz * dz);
+                const float f = Zb * ir * ir * ir;
+                v[a][0] += Zb * ir;
+                v[a][1] += f * dx;
+                v[a][2] += f * dy;
+                v[a][3] += f * dz;
             }
         }
-    }
-    for (int k = 0; k < 4; ++k) {
-        double w = v[k];
-        for (int off = 16; off > 0; off >>= 1) w += __shfl_xor_sync(0xffffffffu, w, off);
-        if (lane == 0) red[warp][k] = w;
-    }
-    __syncthreads();
-    if (tid < 4) {
-        double s4 = 0.0;
-        for (int w = 0; w < kDescThreads / 32; ++w) s4 += red[w][tid];
-        part[((size_t)c * max_nat + a) * 4 + tid] = s4;
+        // primitive pairs of y, class by class (s/p fragments: L <= 2)
+#pragma unroll
+        for (int L = 0; L <= 2; ++L) {
+            const int g0 = d.frag_pp0[y * kClasses + L], ng = d.frag_npp[y * kClasses + L];
+            const int npp = d.n_pp[L];
+            for (int u = tid; u < ng; u += kDescThreads) {
+                const int g = g0 + u;
+                const float4 Pr = d.pp_Pr[L][g];
+                float Dt[nh(2)];
+                for (int k = 0; k < nh(L); ++k) Dt[k] = d.pp_Dh32[L][(size_t)k * npp + g];
+#pragma unroll
+                for (int a = 0; a < kDescAtoms; ++a) {
+                    if (a >= na) break;
+                    if (L == 0) pair_potential32<0>(d.boys32, Pr, Dt, rel[a], v[a]);
+                    else if (L == 1) pair_potential32<1>(d.boys32, Pr, Dt, rel[a], v[a]);
+                    else pair_potential32<2>(d.boys32, Pr, Dt, rel[a], v[a]);
+                }
+            }
+        }
+#pragma unroll
+        for (int a = 0; a < kDescAtoms; ++a)
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                double w = (double)v[a][k];
+                for (int off = 16; off > 0; off >>= 1) w += __shfl_xor_sync(0xffffffffu, w, off);
+                if (lane == 0) red[warp][4 * a + k] = w;
+            }
+        __syncthreads();
+        if (tid < 4 * na) {
+            double s4 = 0.0;
+            for (int w = 0; w < kDescThreads / 32; ++w) s4 += red[w][tid];
+            part[((size_t)c * max_nat + a0 + tid / 4) * 4 + tid % 4] = s4;
+        }
+        __syncthreads();
     }
 }
 
@@ -294,7 +325,12 @@ cudaError_t launch_descriptors(const Dev& d, const double* rot, int n_feat, int 
 {
     if (d.n_frag <= 0) return cudaSuccess;
     if (n_nbr > 0) {
-        k_descriptor_terms<<<(unsigned)((int64_t)n_nbr * max_nat), kDescThreads, 0, s>>>(d, max_nat, part);
+        for (int L = 0; L <= 2; ++L)
+            if (d.n_pp[L] > 0) {
+                k_descriptor_density<<<(d.n_pp[L] + 127) / 128, 128, 0, s>>>(d, L);
+                note_launches(1);
+            }
+        k_descriptor_terms<<<(unsigned)n_nbr, kDescThreads, 0, s>>>(d, max_nat, part);
         note_launches(1);
     }
     k_descriptor_sum<<<(d.n_frag * max_nat + 127) / 128, 128, 0, s>>>(d, rot, n_feat, max_nat, part, X);

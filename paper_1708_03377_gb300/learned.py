@@ -79,23 +79,12 @@ def _timed_solve(system, opts, net=None):
     return int(n_macro), float(e0.elapsed_time(e1)), float(E)
 
 
-def main(argv=None):
+def run_experiment(train_snapshots=200, train_waters=500, per_snapshot=100, test_snapshots=20, test_waters=2000,
+                   fp64_test_snapshots=5, cutoff=8.0, e_tol=1e-8, epochs=200, warmup=1):
     """Learned warm start at the workload's full size: train on converged densities of seeded water
     boxes (seeds 1000...), evaluate macro-iterations and time to e_tol on held-out boxes (seeds
-    2000...) against the superposition start; prints one JSON line."""
-    ap = argparse.ArgumentParser(description=main.__doc__.splitlines()[0])
-    ap.add_argument("--train-snapshots", type=int, default=200)
-    ap.add_argument("--train-waters", type=int, default=500)
-    ap.add_argument("--per-snapshot", type=int, default=100)
-    ap.add_argument("--test-snapshots", type=int, default=20)
-    ap.add_argument("--test-waters", type=int, default=2000)
-    ap.add_argument("--fp64-test-snapshots", type=int, default=5,
-                    help="held-out snapshots also solved with the native FP64 engine")
-    ap.add_argument("--cutoff", type=float, default=8.0)
-    ap.add_argument("--e-tol", type=float, default=1e-8)
-    ap.add_argument("--epochs", type=int, default=200)
-    ap.add_argument("--out", default=None)
-    a = ap.parse_args(argv)
+    2000...) against the superposition start (after `warmup` untimed solves of the first held-out box
+    per leg); returns the summary dict."""
     root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
     if root not in sys.path:
         sys.path.insert(0, root)
@@ -105,10 +94,10 @@ def main(argv=None):
     rng = np.random.default_rng(0)
     t0 = time.time()
     Xs, Ts, skipped = [], [], 0
-    for sd in range(1000, 1000 + a.train_snapshots):
-        system = S.water_box(a.train_waters, seed=sd, basis_sets=basis)
+    for sd in range(1000, 1000 + train_snapshots):
+        system = S.water_box(train_waters, seed=sd, basis_sets=basis)
         try:
-            X, T = snapshot_samples(system, cutoff_A=a.cutoff, e_tol=a.e_tol, max_fragments=a.per_snapshot, rng=rng,
+            X, T = snapshot_samples(system, cutoff_A=cutoff, e_tol=e_tol, max_fragments=per_snapshot, rng=rng,
                                     precision=FEF_MIXED, exact_engine=FEF_ENGINE_DF64)
         except FefError:
             skipped += 1
@@ -118,18 +107,20 @@ def main(argv=None):
     X, T = np.concatenate(Xs), np.concatenate(Ts)
     t_data = time.time() - t0
     t0 = time.time()
-    net, loss = train_warm_start(X, T, hidden=256, epochs=a.epochs, batch=256)
+    net, loss = train_warm_start(X, T, hidden=256, epochs=epochs, batch=256)
     t_train = time.time() - t0
     legs = {"mixed_superposition": (FEF_MIXED, FEF_ENGINE_DF64, False), "mixed_learned": (FEF_MIXED, FEF_ENGINE_DF64, True),
             "fp64_superposition": (FEF_FP64, FEF_ENGINE_FP64, False), "fp64_learned": (FEF_FP64, FEF_ENGINE_FP64, True)}
     res = {k: [] for k in legs}
-    for i, sd in enumerate(range(2000, 2000 + a.test_snapshots)):
-        system = S.water_box(a.test_waters, seed=sd, basis_sets=basis)
+    for i, sd in enumerate(range(2000, 2000 + test_snapshots)):
+        system = S.water_box(test_waters, seed=sd, basis_sets=basis)
         for name, (prec, eng, learned) in legs.items():
-            if prec == FEF_FP64 and i >= a.fp64_test_snapshots:
+            if prec == FEF_FP64 and i >= fp64_test_snapshots:
                 continue
-            opts = fef_default_options(cutoff_A=a.cutoff, schwarz=1e-12, e_tol=a.e_tol, precision=prec, exact_engine=eng,
+            opts = fef_default_options(cutoff_A=cutoff, schwarz=1e-12, e_tol=e_tol, precision=prec, exact_engine=eng,
                                        start=FEF_START_LEARNED if learned else 0)
+            for _ in range(warmup if i == 0 else 0):
+                _timed_solve(system, opts, net if learned else None)
             res[name].append(_timed_solve(system, opts, net if learned else None))
     summary = {}
     for name, rows in res.items():
@@ -140,9 +131,9 @@ def main(argv=None):
     dE = [abs(l[2] - p[2]) for l, p in zip(res["mixed_learned"], res["mixed_superposition"])]
     dE64 = [abs(l[2] - p[2]) for l, p in zip(res["fp64_learned"], res["fp64_superposition"])]
     dEm = [abs(l[2] - p[2]) for l, p in zip(res["mixed_learned"], res["fp64_superposition"])]
-    out = dict(workload=f"learned warm start: train {a.train_snapshots} x {a.train_waters} waters "
-                        f"({a.per_snapshot} fragments each), test {a.test_snapshots} x {a.test_waters} waters, "
-                        f"{a.cutoff} A cutoff, e_tol {a.e_tol}",
+    out = dict(workload=f"learned warm start: train {train_snapshots} x {train_waters} waters "
+                        f"({per_snapshot} fragments each), test {test_snapshots} x {test_waters} waters, "
+                        f"{cutoff} A cutoff, e_tol {e_tol}",
                train_samples=int(X.shape[0]), train_skipped=skipped, train_loss=float(loss), data_s=round(t_data, 1),
                train_s=round(t_train, 1), legs=summary,
                max_dE_learned_vs_superposition_mixed=float(max(dE)) if dE else None,
@@ -155,6 +146,27 @@ def main(argv=None):
             t_ref = np.mean(summary[ref]["ms"][:n])
             t_leg = np.mean(summary[leg]["ms"][:n])
             out[f"speedup_{leg}_vs_{ref}"] = float(t_ref / t_leg)
+    return out
+
+
+def main(argv=None):
+    """Learned warm start at the workload's full size (run_experiment); prints one JSON line."""
+    ap = argparse.ArgumentParser(description=main.__doc__.splitlines()[0])
+    ap.add_argument("--train-snapshots", type=int, default=200)
+    ap.add_argument("--train-waters", type=int, default=500)
+    ap.add_argument("--per-snapshot", type=int, default=100)
+    ap.add_argument("--test-snapshots", type=int, default=20)
+    ap.add_argument("--test-waters", type=int, default=2000)
+    ap.add_argument("--fp64-test-snapshots", type=int, default=5,
+                    help="held-out snapshots also solved with the native FP64 engine")
+    ap.add_argument("--cutoff", type=float, default=8.0)
+    ap.add_argument("--e-tol", type=float, default=1e-8)
+    ap.add_argument("--epochs", type=int, default=200)
+    ap.add_argument("--out", default=None)
+    ap.add_argument("--warmup", type=int, default=1)
+    a = ap.parse_args(argv)
+    out = run_experiment(a.train_snapshots, a.train_waters, a.per_snapshot, a.test_snapshots, a.test_waters,
+                         a.fp64_test_snapshots, a.cutoff, a.e_tol, a.epochs, a.warmup)
     line = json.dumps(out)
     print(line, flush=True)
     if a.out:
