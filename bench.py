@@ -425,12 +425,12 @@ def main():
             e2e_ms.append(1e3 * (time.perf_counter() - t0))
         torch.cuda.synchronize()
 
-    # learned start at full size, reduced: trained on 8 x 500 waters (100 fragments each, not timed),
+    # learned start at full size, reduced: trained on 8 x 500 waters (every fragment, not timed),
     # then MIXED from the superposition and from the learned start on 2 held-out 2000-water boxes
     # (time to 1e-8 Eh of fef_iterate by CUDA events, after one untimed solve per leg)
     learned_2000 = None
     if not args.no_learned_2000 and rank == 0:
-        learned_2000 = lrn.run_experiment(train_snapshots=8, train_waters=500, per_snapshot=100, test_snapshots=2,
+        learned_2000 = lrn.run_experiment(train_snapshots=8, train_waters=500, per_snapshot=500, test_snapshots=2,
                                           test_waters=2000, fp64_test_snapshots=0, cutoff=CUTOFF_A, e_tol=E_TOL,
                                           epochs=200, warmup=1)
     total_ms = float(sum(step_ms))

@@ -228,6 +228,29 @@ static void mark(fef_ctx* c, int i)
 
 static void ensure_learn_buffers(fef_ctx* c);
 
+// Intra-fragment ERI tasks (fragment, shell pair s1, shell pair s2 >= s1, bra component) sorted by
+// angular-momentum class cls = ((la 3 + lb) 3 + lc) 3 + ld; cls_off[c] = first task of class c.
+static void intra_eri_tasks(int nf, const std::vector<int>& frag_sp0, const std::vector<int>& sp_a,
+                            const std::vector<int>& sp_b, const std::vector<int>& sh_l, std::vector<int4>& tasks,
+                            std::vector<int>& cls_off)
+{
+    std::vector<std::vector<int4>> by_cls(81);
+    for (int x = 0; x < nf; ++x)
+        for (int s1 = frag_sp0[x]; s1 < frag_sp0[x + 1]; ++s1)
+            for (int s2 = s1; s2 < frag_sp0[x + 1]; ++s2) {
+                const int la = sh_l[sp_a[s1]], lb = sh_l[sp_b[s1]], lc = sh_l[sp_a[s2]], ld = sh_l[sp_b[s2]];
+                const int cls = ((la * 3 + lb) * 3 + lc) * 3 + ld;
+                for (int k = 0; k < ncart(la) * ncart(lb); ++k) by_cls[cls].push_back(make_int4(x, s1, s2, k));
+            }
+    tasks.clear();
+    cls_off.assign(82, 0);
+    for (int c = 0; c < 81; ++c) {
+        cls_off[c] = (int)tasks.size();
+        tasks.insert(tasks.end(), by_cls[c].begin(), by_cls[c].end());
+    }
+    cls_off[81] = (int)tasks.size();
+}
+
 static int resolve_kind(const fef_ctx* c, int kind)
 {
     return (kind == kBuildFP32Inc && !c->buf->have_ref) ? kBuildFP64 : kind;
@@ -874,21 +897,11 @@ extern "C" fef_status fef_create(const fef_geometry* g, const fef_basis* bs, con
         {
             double* eri = b->alloc<double>(c->coff_total, "intra eri");  // pair-packed U[pq][rs]
             // tasks: (fragment, shell pair s1 <= s2, bra component), sorted by class
-            std::vector<std::pair<int, int4>> tk;
-            for (int x = 0; x < nf; ++x)
-                for (int s1 = frag_sp0[x]; s1 < frag_sp0[x + 1]; ++s1)
-                    for (int s2 = s1; s2 < frag_sp0[x + 1]; ++s2) {
-                        int la = sh_l[sp_a[s1]], lb = sh_l[sp_b[s1]], lc = sh_l[sp_a[s2]], ld = sh_l[sp_b[s2]];
-                        int cls = ((la * 3 + lb) * 3 + lc) * 3 + ld;
-                        for (int k = 0; k < ncart(la) * ncart(lb); ++k) tk.push_back({cls, make_int4(x, s1, s2, k)});
-                    }
-            std::stable_sort(tk.begin(), tk.end(), [](const std::pair<int, int4>& u, const std::pair<int, int4>& v) {
-                return u.first < v.first;
-            });
-            std::vector<int4> tasks(tk.size());
-            for (size_t i = 0; i < tk.size(); ++i) tasks[i] = tk[i].second;
+            std::vector<int4> tasks;
+            std::vector<int> cls_off;
+            intra_eri_tasks(nf, frag_sp0, sp_a, sp_b, sh_l, tasks, cls_off);
             int4* tasks_d = b->upload(tasks, s, "intra tasks");
-            ck(launch_intra_eri(d, tasks_d, (int)tasks.size(), eri, s), "intra eri");
+            ck(launch_intra_eri(d, tasks_d, cls_off, eri, s), "intra eri");
             ck(launch_schwarz(d, eri, sp_Q, ppQ, s), "schwarz");
             ck(launch_class_qmin(d, b->fc_qmin, s), "class Schwarz minimum");
             b->eric = b->alloc<double>(c->coff_total, "eric");
@@ -1504,12 +1517,8 @@ extern "C" fef_status fef_energy_m2(fef_ctx* c, double* E_m2, double* E_m2_total
     if (!c->energies_valid) build_fock_internal(c, kBuildFP64);  // F of the current densities
     // intra-fragment (mu nu|lambda sigma), pair-packed, recomputed into a temporary
     std::vector<int4> tasks;
-    for (int x = 0; x < nf; ++x)
-        for (int s1 = c->h_frag_sp0[x]; s1 < c->h_frag_sp0[x + 1]; ++s1)
-            for (int s2 = s1; s2 < c->h_frag_sp0[x + 1]; ++s2) {
-                const int la = c->h_sh_l[c->h_sp_a[s1]], lb = c->h_sh_l[c->h_sp_b[s1]];
-                for (int k = 0; k < ncart(la) * ncart(lb); ++k) tasks.push_back(make_int4(x, s1, s2, k));
-            }
+    std::vector<int> cls_off;
+    intra_eri_tasks(nf, c->h_frag_sp0, c->h_sp_a, c->h_sp_b, c->h_sh_l, tasks, cls_off);
     std::vector<int64_t> off(nf + 1, 0);
     for (int x = 0; x < nf; ++x) off[x + 1] = off[x] + energy_m2_workspace(c->nao[x], c->nocc[x], c->nmo[x]);
     double* U = b->alloc<double>(std::max<int64_t>(c->coff_total, 1), "E_M2 integrals");
@@ -1518,7 +1527,7 @@ extern "C" fef_status fef_energy_m2(fef_ctx* c, double* E_m2, double* E_m2_total
     double* ws = b->alloc<double>(std::max<int64_t>(off[nf], 1), "E_M2 workspace");
     double* E_d = b->alloc<double>(nf, "E_M2");
     std::vector<double> E(nf, 0.0);
-    cudaError_t e = launch_intra_eri(d, tasks_d, (int)tasks.size(), U, s);
+    cudaError_t e = launch_intra_eri(d, tasks_d, cls_off, U, s);
     if (e == cudaSuccess) e = launch_energy_m2(d, b->F, b->X, b->nmo, U, off_d, ws, E_d, s);
     if (e == cudaSuccess) e = cudaMemcpyAsync(E.data(), E_d, sizeof(double) * nf, cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);

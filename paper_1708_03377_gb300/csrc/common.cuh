@@ -349,7 +349,7 @@ __device__ inline void md_R_rt(int L, double* R, const double* base, double X, d
 //   E^{i+1,j}_t = E^{ij}_{t-1}/(2p) + X_PA E^{ij}_t + (t+1) E^{ij}_{t+1}
 //   E^{i,j+1}_t = E^{ij}_{t-1}/(2p) + X_PB E^{ij}_t + (t+1) E^{ij}_{t+1}
 // E is indexed [i][j][t] with fixed strides (3, 3, 5).
-__device__ inline void md_E1(int la, int lb, double p, double XPA, double XPB, double (*E)[3][5])
+__device__ __forceinline__ void md_E1(int la, int lb, double p, double XPA, double XPB, double (*E)[3][5])
 {
     const double h = 0.5 / p;
     for (int i = 0; i <= la; ++i)

@@ -189,7 +189,10 @@ cudaError_t launch_far_energy(const Dev& d, const double* E_far, double* E_frag,
 cudaError_t launch_near_multipole_field(const Dev& d, const double* M, const double* Mnuc, const double* cen,
                                        const double* D, double* mult, double* pot, double* omega, int64_t n_omega,
                                        cudaStream_t s);
-cudaError_t launch_intra_eri(const Dev& d, const int4* tasks, int n_tasks, double* eri, cudaStream_t s);
+// intra-fragment ERI rows for tasks (fragment, shell pair s1, shell pair s2 >= s1, bra component) sorted
+// by class cls = ((la 3 + lb) 3 + lc) 3 + ld, class c at [cls_off[c], cls_off[c + 1]) (intra_eri_tasks)
+cudaError_t launch_intra_eri(const Dev& d, const int4* tasks, const std::vector<int>& cls_off, double* eri,
+                             cudaStream_t s);
 cudaError_t launch_schwarz(const Dev& d, const double* eri, double* sp_Q, float* pp_Q[kClasses], cudaStream_t s);
 cudaError_t launch_coulomb_exchange(const Dev& d, const double* eri, double* eric, cudaStream_t s);
 cudaError_t launch_neighbours(const Dev& d, double cutoff_bohr, unsigned char* flags, cudaStream_t s);

@@ -854,17 +854,124 @@ __device__ void eri_bra_row(const Dev& d, const int s1, const int s2, const int 
         }
 }
 
-__global__ void k_intra_eri(Dev d, const int4* __restrict__ tasks, int n_tasks, double* eri)
+// The same row for shells of angular momenta known at compile time (s and p: 16 classes), from the
+// primitive-pair data of the J-engine (P, p, K = c_i c_j exp(-ab/p |AB|^2)): the bra component's
+// Hermite coefficients and the ket's, the Boys function, R recursion and both contractions in
+// registers, no transcendental per primitive quartet but one reciprocal square root.
+// Picks E[ai][bi][t] of the (LA+1) x (LB+1) table for runtime ai, bi with compile-time indices.
+template <int LA, int LB>
+__device__ __forceinline__ double e_pick(const double (*E)[3][5], int ai, int bi, int t)
 {
-    int w = blockIdx.x * blockDim.x + threadIdx.x;
-    if (w >= n_tasks) return;
-    const int4 tk = tasks[w];
+    double v = 0.0;
+#pragma unroll
+    for (int i = 0; i <= LA; ++i)
+#pragma unroll
+        for (int j = 0; j <= LB; ++j)
+            if (i == ai && j == bi) v = E[i][j][t];
+    return v;
+}
+
+template <int LA, int LB, int LC, int LD>
+__device__ __forceinline__ void eri_bra_row_t(const Dev& d, const int s1, const int s2, const int kb, double* out)
+{
+    constexpr int NBc = ncart(LB), NC = ncart(LC), ND = ncart(LD);
+    constexpr int LAB = LA + LB, LCD = LC + LD, L = LAB + LCD;
+    const int sa = d.sp_a[s1], sb = d.sp_b[s1], sc = d.sp_a[s2], sd = d.sp_b[s2];
+    int ax, ay, az, bx, by, bz;
+    cart_of(LA, kb / NBc, ax, ay, az);
+    cart_of(LB, kb % NBc, bx, by, bz);
+    const double *A = d.atom_xyz + 3 * d.sh_atom[sa], *B = d.atom_xyz + 3 * d.sh_atom[sb];
+    const double *C = d.atom_xyz + 3 * d.sh_atom[sc], *Dc = d.atom_xyz + 3 * d.sh_atom[sd];
+#pragma unroll
+    for (int k = 0; k < NC * ND; ++k) out[k] = 0.0;
+    const int gP0 = d.sp_pp0[s1], nP = d.sh_np[sa] * d.sh_np[sb];
+    const int gQ0 = d.sp_pp0[s2], nQ = d.sh_np[sc] * d.sh_np[sd];
+    for (int j = 0; j < nQ; ++j) {
+        const double4_32a Q = d.pp_P[LCD][gQ0 + j];
+        const double q = Q.w;
+        const double cq = d.pp_K[LCD][gQ0 + j] * kSqrt2Pi52 / q;
+        double Ek[3][3][3][5];
+        md_E1(LC, LD, q, Q.x - C[0], Q.x - Dc[0], Ek[0]);
+        md_E1(LC, LD, q, Q.y - C[1], Q.y - Dc[1], Ek[1]);
+        md_E1(LC, LD, q, Q.z - C[2], Q.z - Dc[2], Ek[2]);
+        for (int i = 0; i < nP; ++i) {
+            const double4_32a P = d.pp_P[LAB][gP0 + i];
+            const double p = P.w;
+            const double cp = d.pp_K[LAB][gP0 + i] * kSqrt2Pi52 / p;
+            double Eb[3][LAB + 1];
+            {
+                double E[3][3][5];
+                md_E1(LA, LB, p, P.x - A[0], P.x - B[0], E);
+#pragma unroll
+                for (int t = 0; t <= LAB; ++t) Eb[0][t] = e_pick<LA, LB>(E, ax, bx, t);
+                md_E1(LA, LB, p, P.y - A[1], P.y - B[1], E);
+#pragma unroll
+                for (int t = 0; t <= LAB; ++t) Eb[1][t] = e_pick<LA, LB>(E, ay, by, t);
+                md_E1(LA, LB, p, P.z - A[2], P.z - B[2], E);
+#pragma unroll
+                for (int t = 0; t <= LAB; ++t) Eb[2][t] = e_pick<LA, LB>(E, az, bz, t);
+            }
+            const double X = P.x - Q.x, Y = P.y - Q.y, Z = P.z - Q.z;
+            const double rs = rsqrt(p + q);
+            const double alpha = p * q * (rs * rs);
+            const double T = alpha * (X * X + Y * Y + Z * Z);
+            double F[L + 1], base[L + 1], R[nh(L)];
+            boys_fp64<L>(d.boys, T, boys_row((float)T), F);
+            double pre = cp * cq * rs;
+#pragma unroll
+            for (int m = 0; m <= L; ++m) {
+                base[m] = pre * F[m];
+                pre *= -2.0 * alpha;
+            }
+            md_R<L, double>(R, base, X, Y, Z);
+            double Yb[nh(LCD)];
+            static_for<nh(LCD)>([&](auto H) {
+                constexpr TUV c2 = htuv(decltype(H)::value);
+                double y = 0.0;
+#pragma unroll
+                for (int t = 0; t <= LAB; ++t)
+#pragma unroll
+                    for (int u = 0; u <= LAB - t; ++u)
+#pragma unroll
+                        for (int v = 0; v <= LAB - t - u; ++v)
+                            if (t <= ax + bx && u <= ay + by && v <= az + bz)
+                                y += Eb[0][t] * Eb[1][u] * Eb[2][v] * R[hidx(t + c2.t, u + c2.u, v + c2.v)];
+                Yb[decltype(H)::value] = ((c2.t + c2.u + c2.v) & 1) ? -y : y;
+            });
+#pragma unroll
+            for (int ic = 0; ic < NC; ++ic) {
+                int cx, cy, cz;
+                cart_of(LC, ic, cx, cy, cz);
+#pragma unroll
+                for (int id = 0; id < ND; ++id) {
+                    int dx, dy, dz;
+                    cart_of(LD, id, dx, dy, dz);
+                    double v = 0.0;
+#pragma unroll
+                    for (int t = 0; t <= LCD; ++t)
+#pragma unroll
+                        for (int u = 0; u <= LCD - t; ++u)
+#pragma unroll
+                            for (int w = 0; w <= LCD - t - u; ++w)
+                                if (t <= cx + dx && u <= cy + dy && w <= cz + dz)
+                                    v += e_pick<LC, LD>(Ek[0], cx, dx, t) * e_pick<LC, LD>(Ek[1], cy, dy, u) *
+                                         e_pick<LC, LD>(Ek[2], cz, dz, w) * Yb[hidx(t, u, w)];
+                    out[ic * ND + id] += v;
+                }
+            }
+        }
+    }
+}
+
+// Writes the row of task w (fragment x, shell pairs s1 <= s2, bra component kb) into U[pq][rs] and
+// U[rs][pq], scaled to normalised AOs (NC, ND > 0: the ket shells' component counts at compile time).
+template <int NC = 0, int ND = 0>
+__device__ __forceinline__ void intra_eri_store(const Dev& d, const int4 tk, const double* out, double* eri)
+{
     const int x = tk.x, s1 = tk.y, s2 = tk.z, kb = tk.w;
     const int sa = d.sp_a[s1], sb = d.sp_b[s1], sc = d.sp_a[s2], sd = d.sp_b[s2];
     const int lb = d.sh_l[sb];
-    const int nc = ncart(d.sh_l[sc]), nd = ncart(d.sh_l[sd]);
-    double out[36];
-    eri_bra_row(d, s1, s2, kb, out);
+    const int nc = NC > 0 ? NC : ncart(d.sh_l[sc]), nd = ND > 0 ? ND : ncart(d.sh_l[sd]);
     const int n = d.frag_nao[x];
     const int ao0 = d.frag_ao0[x];
     const int64_t np = (int64_t)n * (n + 1) / 2;
@@ -872,7 +979,9 @@ __global__ void k_intra_eri(Dev d, const int4* __restrict__ tasks, int n_tasks, 
     const int mu = d.sh_ao[sa] + kb / ncart(lb), nu = d.sh_ao[sb] + kb % ncart(lb);
     const double smn = d.ao_scale[ao0 + mu] * d.ao_scale[ao0 + nu];
     const int64_t pq = pair_pack(mu, nu, n);
-    for (int k = 0; k < nc * nd; ++k) {
+#pragma unroll
+    for (int k = 0; k < (NC > 0 ? NC * ND : 36); ++k) {
+        if (NC == 0 && k >= nc * nd) break;
         int la_ = d.sh_ao[sc] + k / nd, si = d.sh_ao[sd] + k % nd;
         double v = out[k] * smn * d.ao_scale[ao0 + la_] * d.ao_scale[ao0 + si];
         const int64_t rs = pair_pack(la_, si, n);
@@ -881,10 +990,55 @@ __global__ void k_intra_eri(Dev d, const int4* __restrict__ tasks, int n_tasks, 
     }
 }
 
-cudaError_t launch_intra_eri(const Dev& d, const int4* tasks, int n_tasks, double* eri, cudaStream_t s)
+template <int LA, int LB, int LC, int LD>
+__global__ void __launch_bounds__(128) k_intra_eri_t(Dev d, const int4* __restrict__ tasks, int n_tasks, double* eri)
 {
-    if (n_tasks > 0) {
-        k_intra_eri<<<(n_tasks + 127) / 128, 128, 0, s>>>(d, tasks, n_tasks, eri);
+    const int w = blockIdx.x * blockDim.x + threadIdx.x;
+    if (w >= n_tasks) return;
+    const int4 tk = tasks[w];
+    double out[ncart(LC) * ncart(LD)];
+    eri_bra_row_t<LA, LB, LC, LD>(d, tk.y, tk.z, tk.w, out);
+    intra_eri_store<ncart(LC), ncart(LD)>(d, tk, out, eri);
+}
+
+__global__ void k_intra_eri(Dev d, const int4* __restrict__ tasks, int n_tasks, double* eri)
+{
+    const int w = blockIdx.x * blockDim.x + threadIdx.x;
+    if (w >= n_tasks) return;
+    const int4 tk = tasks[w];
+    double out[36];
+    eri_bra_row(d, tk.y, tk.z, tk.w, out);
+    intra_eri_store<>(d, tk, out, eri);
+}
+
+template <int LA, int LB, int LC, int LD>
+void launch_intra_class(const Dev& d, const int4* tasks, int n, double* eri, cudaStream_t s)
+{
+    k_intra_eri_t<LA, LB, LC, LD><<<(n + 127) / 128, 128, 0, s>>>(d, tasks, n, eri);
+}
+
+cudaError_t launch_intra_eri(const Dev& d, const int4* tasks, const std::vector<int>& cls_off, double* eri,
+                             cudaStream_t s)
+{
+    for (int cls = 0; cls + 1 < (int)cls_off.size(); ++cls) {
+        const int n = cls_off[cls + 1] - cls_off[cls];
+        if (n <= 0) continue;
+        const int4* t = tasks + cls_off[cls];
+        const int la = cls / 27, lb = (cls / 9) % 3, lc = (cls / 3) % 3, ld = cls % 3;
+        if (la > 1 || lb > 1 || lc > 1 || ld > 1) {
+            k_intra_eri<<<(n + 127) / 128, 128, 0, s>>>(d, t, n, eri);
+        } else {
+            switch (la * 8 + lb * 4 + lc * 2 + ld) {
+#define FEF_IE(A, B, C, D) \
+    case A * 8 + B * 4 + C * 2 + D: launch_intra_class<A, B, C, D>(d, t, n, eri, s); break;
+                FEF_IE(0, 0, 0, 0) FEF_IE(0, 0, 0, 1) FEF_IE(0, 0, 1, 0) FEF_IE(0, 0, 1, 1)
+                FEF_IE(0, 1, 0, 0) FEF_IE(0, 1, 0, 1) FEF_IE(0, 1, 1, 0) FEF_IE(0, 1, 1, 1)
+                FEF_IE(1, 0, 0, 0) FEF_IE(1, 0, 0, 1) FEF_IE(1, 0, 1, 0) FEF_IE(1, 0, 1, 1)
+                FEF_IE(1, 1, 0, 0) FEF_IE(1, 1, 0, 1) FEF_IE(1, 1, 1, 0) FEF_IE(1, 1, 1, 1)
+#undef FEF_IE
+                default: break;
+            }
+        }
         note_launches(1);
     }
     return cudaGetLastError();
