@@ -871,8 +871,11 @@ __device__ __forceinline__ double e_pick(const double (*E)[3][5], int ai, int bi
     return v;
 }
 
+// Lane `sub` of the nsub lanes that share one task takes the primitive quartets sub, sub + nsub, ...
+// (its partial row in out; the caller sums the lanes).
 template <int LA, int LB, int LC, int LD>
-__device__ __forceinline__ void eri_bra_row_t(const Dev& d, const int s1, const int s2, const int kb, double* out)
+__device__ __forceinline__ void eri_bra_row_t(const Dev& d, const int s1, const int s2, const int kb, double* out,
+                                              const int sub, const int nsub)
 {
     constexpr int NBc = ncart(LB), NC = ncart(LC), ND = ncart(LD);
     constexpr int LAB = LA + LB, LCD = LC + LD, L = LAB + LCD;
@@ -886,7 +889,8 @@ __device__ __forceinline__ void eri_bra_row_t(const Dev& d, const int s1, const 
     for (int k = 0; k < NC * ND; ++k) out[k] = 0.0;
     const int gP0 = d.sp_pp0[s1], nP = d.sh_np[sa] * d.sh_np[sb];
     const int gQ0 = d.sp_pp0[s2], nQ = d.sh_np[sc] * d.sh_np[sd];
-    for (int j = 0; j < nQ; ++j) {
+    for (int pq = sub; pq < nP * nQ; pq += nsub) {
+        const int i = pq % nP, j = pq / nP;
         const double4_32a Q = d.pp_P[LCD][gQ0 + j];
         const double q = Q.w;
         const double cq = d.pp_K[LCD][gQ0 + j] * kSqrt2Pi52 / q;
@@ -894,7 +898,7 @@ __device__ __forceinline__ void eri_bra_row_t(const Dev& d, const int s1, const 
         md_E1(LC, LD, q, Q.x - C[0], Q.x - Dc[0], Ek[0]);
         md_E1(LC, LD, q, Q.y - C[1], Q.y - Dc[1], Ek[1]);
         md_E1(LC, LD, q, Q.z - C[2], Q.z - Dc[2], Ek[2]);
-        for (int i = 0; i < nP; ++i) {
+        {
             const double4_32a P = d.pp_P[LAB][gP0 + i];
             const double p = P.w;
             const double cp = d.pp_K[LAB][gP0 + i] * kSqrt2Pi52 / p;
@@ -990,15 +994,26 @@ __device__ __forceinline__ void intra_eri_store(const Dev& d, const int4 tk, con
     }
 }
 
+// kIntraLanes lanes per task (the primitive quartets split between them, partial rows summed by a
+// butterfly over the lane group in a fixed order).
+constexpr int kIntraLanes = 8;
+
 template <int LA, int LB, int LC, int LD>
 __global__ void __launch_bounds__(128) k_intra_eri_t(Dev d, const int4* __restrict__ tasks, int n_tasks, double* eri)
 {
-    const int w = blockIdx.x * blockDim.x + threadIdx.x;
-    if (w >= n_tasks) return;
-    const int4 tk = tasks[w];
-    double out[ncart(LC) * ncart(LD)];
-    eri_bra_row_t<LA, LB, LC, LD>(d, tk.y, tk.z, tk.w, out);
-    intra_eri_store<ncart(LC), ncart(LD)>(d, tk, out, eri);
+    constexpr int NK = ncart(LC) * ncart(LD);
+    const int w = (blockIdx.x * blockDim.x + threadIdx.x) / kIntraLanes, sub = threadIdx.x % kIntraLanes;
+    const bool on = w < n_tasks;  // whole lane groups (128 is a multiple of kIntraLanes)
+    const int4 tk = tasks[on ? w : 0];
+    double out[NK];
+    if (on) eri_bra_row_t<LA, LB, LC, LD>(d, tk.y, tk.z, tk.w, out, sub, kIntraLanes);
+#pragma unroll
+    for (int k = 0; k < NK; ++k) {
+        if (!on) out[k] = 0.0;
+#pragma unroll
+        for (int o = kIntraLanes / 2; o > 0; o >>= 1) out[k] += __shfl_xor_sync(0xffffffffu, out[k], o, kIntraLanes);
+    }
+    if (on && sub == 0) intra_eri_store<ncart(LC), ncart(LD)>(d, tk, out, eri);
 }
 
 __global__ void k_intra_eri(Dev d, const int4* __restrict__ tasks, int n_tasks, double* eri)
@@ -1014,7 +1029,7 @@ __global__ void k_intra_eri(Dev d, const int4* __restrict__ tasks, int n_tasks, 
 template <int LA, int LB, int LC, int LD>
 void launch_intra_class(const Dev& d, const int4* tasks, int n, double* eri, cudaStream_t s)
 {
-    k_intra_eri_t<LA, LB, LC, LD><<<(n + 127) / 128, 128, 0, s>>>(d, tasks, n, eri);
+    k_intra_eri_t<LA, LB, LC, LD><<<(unsigned)(((int64_t)n * kIntraLanes + 127) / 128), 128, 0, s>>>(d, tasks, n, eri);
 }
 
 cudaError_t launch_intra_eri(const Dev& d, const int4* tasks, const std::vector<int>& cls_off, double* eri,
