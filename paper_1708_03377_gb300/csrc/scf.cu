@@ -639,24 +639,23 @@ __device__ __forceinline__ void fragment_scf(const Dev& d, const ScfArgs& a, con
         }
         have_vp = true;
         t.sync();
-        if (tid == 0) {  // every block of the team orders the same eigenvalues the same way
-            for (int k = 0; k < m; ++k) order[k] = k;
-            for (int k = 0; k < nocc; ++k) {  // selection of the nocc lowest, ties by index
-                int best = k;
-                for (int j = k + 1; j < m; ++j) {
-                    double ej = A[order[j] * n + order[j]], eb = A[order[best] * n + order[best]];
-                    if (ej < eb || (ej == eb && order[j] < order[best])) best = j;
-                }
-                int tmp = order[k]; order[k] = order[best]; order[best] = tmp;
+        // ascending orbital energies, ties by index: thread k ranks eigenvalue k (every block of the
+        // team orders the same eigenvalues the same way); the nocc lowest are occupied
+        for (int k = tid; k < m; k += blockDim.x) {
+            const double ek = A[k * n + k];
+            int r = 0;
+            for (int j = 0; j < m; ++j) {
+                const double ej = A[j * n + j];
+                r += (ej < ek || (ej == ek && j < k)) ? 1 : 0;
             }
-            double homo = -1e300, lumo = 1e300;
-            for (int k = 0; k < m; ++k) {
-                const double ek = A[order[k] * n + order[k]];
-                if (k < nocc) homo = fmax(homo, ek); else lumo = fmin(lumo, ek);
-            }
-            gap = (nocc > 0 && nocc < m) ? lumo - homo - shift : 0.0;
+            order[r] = k;
         }
         __syncthreads();
+        if (tid == 0) {
+            const double homo = nocc > 0 ? A[order[nocc - 1] * n + order[nocc - 1]] : 0.0;
+            const double lumo = nocc < m ? A[order[nocc] * n + order[nocc]] : 0.0;
+            gap = (nocc > 0 && nocc < m) ? lumo - homo - shift : 0.0;
+        }
         for (int e = g0; e < n * nocc; e += gs) {  // W = C_occ = X V_occ  (n x nocc)
             int i = e / nocc, k = e % nocc;
             int col = order[k];
@@ -766,13 +765,41 @@ __device__ __forceinline__ void fragment_scf(const Dev& d, const ScfArgs& a, con
             he[(int64_t)slot * n2 + e] = (i < m && j < m) ? A[i * n + j] : 0.0;
         }
         t.sync();
-        for (int j = 0; j < hist; ++j) {
-            double pj = 0.0;
-            for (int e = g0; e < n2; e += gs) pj += he[(int64_t)slot * n2 + e] * he[(int64_t)j * n2 + e];
-            pj = team_sum(t, pj, red);
-            if (tid == 0) {
-                B[slot][j] = pj;
-                B[j][slot] = pj;
+        // the new row of B: all hist dot products in one pass and one reduction per block (CS = 1);
+        // across a cluster, one team reduction per product
+        if constexpr (CS == 1) {
+            double pj[8] = {};
+            for (int e = g0; e < n2; e += gs) {
+                const double se = he[(int64_t)slot * n2 + e];
+#pragma unroll
+                for (int j = 0; j < 8; ++j)
+                    if (j < hist) pj[j] = fma(se, he[(int64_t)j * n2 + e], pj[j]);
+            }
+            __shared__ double redh[8][8];
+            const int w8 = tid >> 5;
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                double v = pj[j];
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+                if (lane == 0 && w8 < 8) redh[w8][j] = v;
+            }
+            __syncthreads();
+            if (tid < hist) {
+                double v = 0.0;
+                for (int w = 0; w < (int)(blockDim.x >> 5); ++w) v += redh[w][tid];
+                B[slot][tid] = v;
+                B[tid][slot] = v;
+            }
+        } else {
+            for (int j = 0; j < hist; ++j) {
+                double pj = 0.0;
+                for (int e = g0; e < n2; e += gs) pj += he[(int64_t)slot * n2 + e] * he[(int64_t)j * n2 + e];
+                pj = team_sum(t, pj, red);
+                if (tid == 0) {
+                    B[slot][j] = pj;
+                    B[j][slot] = pj;
+                }
             }
         }
         __syncthreads();
@@ -795,9 +822,10 @@ __device__ __forceinline__ void fragment_scf(const Dev& d, const ScfArgs& a, con
                         if (fabs(M[r][col]) > fabs(M[piv][col])) piv = r;
                     if (fabs(M[piv][col]) < 1e-300) { ok = false; break; }
                     for (int j = 0; j <= sz; ++j) { double tmp = M[col][j]; M[col][j] = M[piv][j]; M[piv][j] = tmp; }
+                    const double inv = 1.0 / M[col][col];  // one division per pivot
                     for (int r = 0; r < sz; ++r) {
                         if (r == col) continue;
-                        double f = M[r][col] / M[col][col];
+                        const double f = M[r][col] * inv;
                         for (int j = col; j <= sz; ++j) M[r][j] -= f * M[col][j];
                     }
                 }
