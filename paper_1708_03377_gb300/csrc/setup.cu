@@ -3,6 +3,8 @@
 // Coulomb-minus-half-exchange form, Schwarz factors, the fragment neighbour test, the environment
 // nuclear attraction h~ (paper, "Fragment Mean Field", the equation after Eq. wc) and nuclear
 // repulsion.  All integrals use McMurchie-Davidson Hermite expansions (common.cuh).
+#include <algorithm>
+
 #include "common.cuh"
 #include "internal.hpp"
 
@@ -1032,20 +1034,48 @@ void launch_intra_class(const Dev& d, const int4* tasks, int n, double* eri, cud
     k_intra_eri_t<LA, LB, LC, LD><<<(unsigned)(((int64_t)n * kIntraLanes + 127) / 128), 128, 0, s>>>(d, tasks, n, eri);
 }
 
+// The class launches are small (a few hundred blocks each on the water workloads): they run on the
+// context stream and two side streams, forked and joined by events, the largest classes first, each
+// on the stream with the least work so far.
 cudaError_t launch_intra_eri(const Dev& d, const int4* tasks, const std::vector<int>& cls_off, double* eri,
                              cudaStream_t s)
 {
+    constexpr int kStreams = 3;
+    std::vector<std::pair<double, int>> order;
     for (int cls = 0; cls + 1 < (int)cls_off.size(); ++cls) {
         const int n = cls_off[cls + 1] - cls_off[cls];
         if (n <= 0) continue;
+        const int la = cls / 27, lb = (cls / 9) % 3, lc = (cls / 3) % 3, ld = cls % 3;
+        const double w = (double)n * ncart(lc) * ncart(ld) * (1 + la + lb + lc + ld);  // rough cost
+        order.push_back({-w, cls});
+    }
+    std::sort(order.begin(), order.end());
+    cudaStream_t st[kStreams] = {s, nullptr, nullptr};
+    cudaEvent_t fork = nullptr, join[kStreams] = {};
+    cudaError_t e = cudaEventCreateWithFlags(&fork, cudaEventDisableTiming);
+    for (int i = 1; i < kStreams && e == cudaSuccess; ++i) {
+        e = cudaStreamCreateWithFlags(&st[i], cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&join[i], cudaEventDisableTiming);
+    }
+    if (e == cudaSuccess) e = cudaEventRecord(fork, s);
+    for (int i = 1; i < kStreams && e == cudaSuccess; ++i) e = cudaStreamWaitEvent(st[i], fork, 0);
+    double load[kStreams] = {};
+    for (size_t o = 0; o < order.size() && e == cudaSuccess; ++o) {
+        const int cls = order[o].second;
+        const int n = cls_off[cls + 1] - cls_off[cls];
+        int si = 0;
+        for (int i = 1; i < kStreams; ++i)
+            if (load[i] < load[si]) si = i;
+        load[si] -= order[o].first;
+        const cudaStream_t sc = st[si];
         const int4* t = tasks + cls_off[cls];
         const int la = cls / 27, lb = (cls / 9) % 3, lc = (cls / 3) % 3, ld = cls % 3;
         if (la > 1 || lb > 1 || lc > 1 || ld > 1) {
-            k_intra_eri<<<(n + 127) / 128, 128, 0, s>>>(d, t, n, eri);
+            k_intra_eri<<<(n + 127) / 128, 128, 0, sc>>>(d, t, n, eri);
         } else {
             switch (la * 8 + lb * 4 + lc * 2 + ld) {
 #define FEF_IE(A, B, C, D) \
-    case A * 8 + B * 4 + C * 2 + D: launch_intra_class<A, B, C, D>(d, t, n, eri, s); break;
+    case A * 8 + B * 4 + C * 2 + D: launch_intra_class<A, B, C, D>(d, t, n, eri, sc); break;
                 FEF_IE(0, 0, 0, 0) FEF_IE(0, 0, 0, 1) FEF_IE(0, 0, 1, 0) FEF_IE(0, 0, 1, 1)
                 FEF_IE(0, 1, 0, 0) FEF_IE(0, 1, 0, 1) FEF_IE(0, 1, 1, 0) FEF_IE(0, 1, 1, 1)
                 FEF_IE(1, 0, 0, 0) FEF_IE(1, 0, 0, 1) FEF_IE(1, 0, 1, 0) FEF_IE(1, 0, 1, 1)
@@ -1055,8 +1085,17 @@ cudaError_t launch_intra_eri(const Dev& d, const int4* tasks, const std::vector<
             }
         }
         note_launches(1);
+        e = cudaGetLastError();
     }
-    return cudaGetLastError();
+    // join the side streams into s (also after an error, so that no work is left unordered)
+    for (int i = 1; i < kStreams; ++i) {
+        if (!st[i]) continue;
+        if (join[i] && cudaEventRecord(join[i], st[i]) == cudaSuccess) cudaStreamWaitEvent(s, join[i], 0);
+        cudaStreamDestroy(st[i]);
+        if (join[i]) cudaEventDestroy(join[i]);
+    }
+    if (fork) cudaEventDestroy(fork);
+    return e != cudaSuccess ? e : cudaGetLastError();
 }
 
 // Inter-fragment blocks for a list of fragment pairs: task (list position q, s1 in x, s2 in y, kb),
