@@ -7,6 +7,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -25,13 +26,44 @@ static void ck(cudaError_t e, const char* what)
     if (e != cudaSuccess) throw Error{FEF_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e)};
 }
 
+// Device memory of a context comes from one stream-ordered memory pool per device, shared by all
+// contexts and kept (up to kPoolKeepBytes) across them, so that creating and destroying contexts of
+// the same size repeatedly costs no cudaMalloc/cudaFree (and no device synchronisation) after the first.
+constexpr uint64_t kPoolKeepBytes = 4ull << 30;
+
+static cudaMemPool_t device_pool(int device)
+{
+    static std::mutex mu;
+    static std::vector<cudaMemPool_t> pools;
+    std::lock_guard<std::mutex> lock(mu);
+    if ((int)pools.size() <= device) pools.resize(device + 1, nullptr);
+    if (!pools[device]) {
+        cudaMemPoolProps props = {};
+        props.allocType = cudaMemAllocationTypePinned;
+        props.location.type = cudaMemLocationTypeDevice;
+        props.location.id = device;
+        cudaMemPool_t p = nullptr;
+        ck(cudaMemPoolCreate(&p, &props), "memory pool");
+        uint64_t keep = kPoolKeepBytes;
+        ck(cudaMemPoolSetAttribute(p, cudaMemPoolAttrReleaseThreshold, &keep), "memory pool");
+        pools[device] = p;
+    }
+    return pools[device];
+}
+
 struct Buffers {
     std::vector<void*> allocs;
+    cudaMemPool_t pool = nullptr;  // allocations in stream order on `as` (the context stream at creation)
+    cudaStream_t as = nullptr;
     template <typename T>
     T* alloc(size_t n, const char* what)
     {
         void* p = nullptr;
-        ck(cudaMalloc(&p, std::max<size_t>(n, 1) * sizeof(T)), what);
+        const size_t bytes = std::max<size_t>(n, 1) * sizeof(T);
+        if (pool)
+            ck(cudaMallocFromPoolAsync(&p, bytes, pool, as), what);
+        else
+            ck(cudaMalloc(&p, bytes), what);
         allocs.push_back(p);
         return static_cast<T*>(p);
     }
@@ -46,7 +78,10 @@ struct Buffers {
     {
         auto it = std::find(allocs.begin(), allocs.end(), p);
         if (it != allocs.end()) {
-            cudaFree(p);
+            if (pool)
+                cudaFreeAsync(p, as);  // after the context's work on `as` that used it
+            else
+                cudaFree(p);
             allocs.erase(it);
         }
     }
@@ -58,7 +93,14 @@ struct Buffers {
         if (jplan) jplan_destroy(jplan);
         if (stage) cudaFreeHost(stage);
         if (scf_tol_host) cudaFreeHost(scf_tol_host);
-        for (void* p : allocs) cudaFree(p);
+        if (pool) {
+            // the context's work may run on streams the caller owns: wait for the device, then
+            // return the memory to the pool
+            cudaDeviceSynchronize();
+            for (void* p : allocs) cudaFreeAsync(p, nullptr);
+        } else {
+            for (void* p : allocs) cudaFree(p);
+        }
     }
     // one CUDA graph per kind of macro-iteration (fragment SCF + Fock build + read-back), built on
     // first use; launches of this library inside each graph
@@ -680,6 +722,8 @@ extern "C" fef_status fef_create(const fef_geometry* g, const fef_basis* bs, con
         c->buf = new Buffers();
         Buffers* b = c->buf;
         cudaStream_t s = c->stream;
+        b->pool = device_pool(c->device);
+        b->as = s;
         Dev& d = c->dev;
         d.n_frag = nf;
         d.n_atoms = na;
