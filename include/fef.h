@@ -137,8 +137,10 @@ void fef_default_options(fef_options* opt);
  * orthogonaliser X^x = U s^{-1/2} (s >= 1e-7), shell-pair Schwarz factors, the intra-fragment
  * two-electron tensor, the fragment-pair neighbour list within the cutoff, the environment nuclear
  * attraction sum_{y in N(x)} V^y (h~, the equation after Eq. wc) and the J-engine work lists.
- * cuda_stream: a cudaStream_t (NULL = default stream).  On success *out owns device memory until
- * fef_destroy.  Errors: ARG (NULL pointers, an empty geometry or basis, an option out of range: diis_size
+ * cuda_stream: a cudaStream_t (NULL = default stream); it must outlive the context.  On success *out
+ * owns device memory until fef_destroy, taken in stream order on cuda_stream from one memory pool per
+ * device that the library shares between its contexts and that keeps up to 4 GiB cached after they
+ * are destroyed (so that contexts of similar size are created again without cudaMalloc).  Errors: ARG (NULL pointers, an empty geometry or basis, an option out of range: diis_size
  * outside 1..8, NaN cutoff_A, non-positive or non-finite e_tol / micro tolerances, negative schwarz
  * or mixed_switch), BASIS, GEOM, CUDA.  Argument and option checks come before any device call. */
 fef_status fef_create(const fef_geometry* geom, const fef_basis* basis, const fef_options* opt,
@@ -250,7 +252,8 @@ fef_status fef_fragment_status(const fef_ctx* ctx, int32_t* micro_iters, double*
  * context-free call). */
 const char* fef_last_error(const fef_ctx* ctx);
 
-/* Free the context and all its device memory.  NULL is a no-op. */
+/* Free the context and all its device memory (waits for the device, then returns the memory to the
+ * library's pool).  NULL is a no-op. */
 void fef_destroy(fef_ctx* ctx);
 
 /* ---------------------------------------------------------------------------------------------
