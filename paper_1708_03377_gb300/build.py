@@ -11,7 +11,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(HERE, "libfef.so")
 SOURCES = ["setup.cu", "jengine.cu", "jengine_big.cu", "jplan.cu", "scf.cu", "api.cu", "peak.cu", "noalloc.cu", "mlp.cu", "learned.cu", "jengine_df.cu", "ed2.cu"]
-HEADERS = ["common.cuh", "internal.hpp"]
+HEADERS = ["common.cuh", "internal.hpp", "df64.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

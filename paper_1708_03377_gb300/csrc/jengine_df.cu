@@ -25,70 +25,14 @@
 #include <climits>
 
 #include "common.cuh"
+#include "df64.cuh"
 #include "internal.hpp"
 
 namespace fef {
 
 namespace {
 
-struct df64 {
-    float hi, lo;
-    df64() = default;
-    __device__ __forceinline__ df64(float h, float l) : hi(h), lo(l) {}
-    __device__ __forceinline__ explicit df64(int i) : hi((float)i), lo(0.0f) {}
-};
-
-__device__ __forceinline__ df64 quick_two_sum(float a, float b)  // |a| >= |b|
-{
-    const float s = __fadd_rn(a, b);
-    return df64(s, __fsub_rn(b, __fsub_rn(s, a)));
-}
-
-__device__ __forceinline__ df64 two_sum(float a, float b)
-{
-    const float s = __fadd_rn(a, b);
-    const float bb = __fsub_rn(s, a);
-    return df64(s, __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb)));
-}
-
-__device__ __forceinline__ df64 operator+(df64 a, df64 b)
-{
-    const df64 t = two_sum(a.hi, b.hi);
-    return quick_two_sum(t.hi, __fadd_rn(t.lo, __fadd_rn(a.lo, b.lo)));
-}
-
-__device__ __forceinline__ df64 operator-(df64 a) { return df64(-a.hi, -a.lo); }
-__device__ __forceinline__ df64 operator-(df64 a, df64 b) { return a + (-b); }
-
-__device__ __forceinline__ df64 operator*(df64 a, df64 b)
-{
-    const float p = __fmul_rn(a.hi, b.hi);
-    float e = __fmaf_rn(a.hi, b.hi, -p);
-    e = __fmaf_rn(a.hi, b.lo, e);
-    e = __fmaf_rn(a.lo, b.hi, e);
-    return quick_two_sum(p, e);
-}
-
-// a b + c
-__device__ __forceinline__ df64 fma(df64 a, df64 b, df64 c)
-{
-    const float p = __fmul_rn(a.hi, b.hi);
-    float e = __fmaf_rn(a.hi, b.hi, -p);
-    e = __fmaf_rn(a.hi, b.lo, e);
-    e = __fmaf_rn(a.lo, b.hi, e);
-    const df64 t = two_sum(p, c.hi);
-    return quick_two_sum(t.hi, __fadd_rn(t.lo, __fadd_rn(e, c.lo)));
-}
-
-// 1/sqrt(x), x > 0: float seed, one float Newton step, one df64 Newton step (relative error ~1e-14).
-__device__ __forceinline__ df64 rsqrt_df(df64 x)
-{
-    float r = rsqrtf(x.hi);
-    r = r * (1.5f - 0.5f * x.hi * r * r);
-    const df64 y(r, 0.0f);
-    const df64 e = df64(1.0f, 0.0f) - x * (y * y);  // ~1e-7
-    return quick_two_sum(r, 0.5f * r * e.hi);
-}
+using namespace ffa;
 
 __device__ __forceinline__ df64 ld_df(const float2* p)
 {
