@@ -1631,6 +1631,8 @@ extern "C" fef_status fef_energy_d2(fef_ctx* c, double* E_d2_frag, double* E_d2_
         int64_t* uoff_d = b->upload(uoff, s, "E_D2 sizes");
         double* U = b->alloc<double>(std::max<int64_t>(uoff[nf], 1), "E_D2 transition densities");
         e = launch_ed2_transition(d, C, b->nmo, uoff_d, hoff_d, n_ov_d, max_ov, U, s);
+        float2* Udf = b->alloc<float2>(std::max<int64_t>(uoff[nf], 1), "E_D2 transition densities (float-float)");
+        if (e == cudaSuccess) e = launch_ed2_split(U, Udf, uoff[nf], s);
         const int64_t kMaxG = 1ll << 27;
         std::vector<int> chunk;
         std::vector<int64_t> goff(1, 0);
@@ -1654,7 +1656,8 @@ extern "C" fef_status fef_energy_d2(fef_ctx* c, double* E_d2_frag, double* E_d2_
             e = cudaMemsetAsync(G, 0, sizeof(double) * std::max<int64_t>(goff.back(), 1), s);
             const int4* cit[3] = {items_d[0], items_d[1], items_d[2]};
             if (e == cudaSuccess)
-                e = launch_ed2_pairs(d, U, uoff_d, hoff_d, n_ov_d, pair_d, goff_d, G, c->opt.schwarz, cit, n_items, s);
+                e = launch_ed2_pairs(d, U, Udf, uoff_d, hoff_d, n_ov_d, pair_d, goff_d, G, c->opt.schwarz, cit, n_items,
+                                     s);
             if (e == cudaSuccess)
                 e = launch_ed2_energy(d, nq, max_entries, U, uoff_d, hoff_d, n_ov_d, pair_d, goff_d, G, C, eps, b->nmo,
                                       nherm_d, Ed, s);
@@ -1699,6 +1702,7 @@ extern "C" fef_status fef_energy_d2(fef_ctx* c, double* E_d2_frag, double* E_d2_
         }
         run();
         b->release(U);
+        b->release(Udf);
         for (void* p : {(void*)n_ov_d, (void*)hoff_d, (void*)nherm_d, (void*)uoff_d}) b->release(p);
     }
     // pairs in chunks that bound the integral blocks, workspaces and task lists

@@ -17,6 +17,7 @@
 #include <climits>
 
 #include "common.cuh"
+#include "df64.cuh"
 #include "internal.hpp"
 
 namespace fef {
@@ -24,7 +25,7 @@ namespace fef {
 namespace {
 
 // jb columns of G per lane and bra Hermite component for bra class L (register budget of the lane's field)
-__host__ __device__ constexpr int ed2_cols(int L) { return L == 0 ? 40 : (L == 1 ? 20 : 6); }
+__host__ __device__ constexpr int ed2_cols(int L) { return L == 0 ? 40 : (L == 1 ? 10 : 4); }
 
 // Transition Hermite densities of every fragment for class L: thread per (primitive pair g, ov pair k).
 // U[uoff[x] + (hoff[x*5+L] + (g - pp0) nh(L) + h) n_ov(x) + k].
@@ -105,6 +106,7 @@ __device__ __noinline__ Ed2Base<L> ed2_table_base(const double* __restrict__ boy
 
 struct Ed2Args {
     const double* U;       // transition Hermite densities (k_ed2_transition)
+    const float2* Udf;     // the same as float-float pairs (the pair kernel's ket weights)
     const int64_t* uoff;   // [n_frag]
     const int* hoff;       // [n_frag * 5]
     const int* n_ov;       // [n_frag]
@@ -115,17 +117,21 @@ struct Ed2Args {
 };
 
 // Kets of class LK of fragment ky against the lane's bra pair (class LB): G[h][jj] += ...
+// The contraction runs in float-float on the FP32 pipes: each R value (FP64) is split once per
+// quartet, the weights are stored split, and G accumulates compensated unnormalised sums
+// (ffa::acc_prod), ~2^-48 relative per term: the same accuracy class as FP64 for these sums of
+// ~1e5 terms, at about a fifth of the FP64-pipe time of a DFMA per term on this part.
 template <int LB, int LK>
 __device__ __forceinline__ void ed2_kets(const Dev& d, const Ed2Args& a, int ky, int jb0, int nj, bool valid,
                                          const double4_32a& Pd, const float4& Pf, double rpP, float qP,
-                                         double (&G)[nh(LB)][ed2_cols(LB)])
+                                         ffa::dfacc (&G)[nh(LB)][ed2_cols(LB)])
 {
     constexpr int NP = nh(LB), NQ = nh(LK), L = LB + LK, NR = nh(L), JC = ed2_cols(LB);
     const int k0 = d.frag_pp0[ky * kClasses + LK], k1 = k0 + d.frag_npp[ky * kClasses + LK];
     if (k0 >= k1) return;
     const int nov = a.n_ov[ky];
-    const double* __restrict__ Uk =
-        a.U + a.uoff[ky] + (int64_t)a.hoff[ky * kClasses + LK] * nov + jb0;
+    const float2* __restrict__ Uk =
+        a.Udf + a.uoff[ky] + (int64_t)a.hoff[ky * kClasses + LK] * nov + jb0;
     for (int k = k0; k < k1; ++k) {
         const float qQ = __ldg(d.pp_Q[LK] + k);
         const bool keep = valid && qP * qQ >= a.tau;
@@ -161,18 +167,21 @@ __device__ __forceinline__ void ed2_kets(const Dev& d, const Ed2Args& a, int ky,
         }
         double R[NR];
         md_R<L, double>(R, base, X, Y, Z);
-        const double* __restrict__ uq = Uk + (int64_t)(k - k0) * NQ * nov;
+        ffa::df64 Rf[NR];
+#pragma unroll
+        for (int r = 0; r < NR; ++r) Rf[r] = ffa::from_double(R[r]);
+        const float2* __restrict__ uq = Uk + (int64_t)(k - k0) * NQ * nov;
         static_for<NQ>([&](auto Jc) {
             constexpr TUV b = htuv(decltype(Jc)::value);
             constexpr bool odd = ((b.t + b.u + b.v) & 1) != 0;
-            const double* __restrict__ row = uq + (int64_t)decltype(Jc)::value * nov;
+            const float2* __restrict__ row = uq + (int64_t)decltype(Jc)::value * nov;
 #pragma unroll
             for (int jj = 0; jj < JC; ++jj) {
-                const double w = jj < nj ? __ldg(row + jj) : 0.0;
+                const float2 w2 = jj < nj ? __ldg(row + jj) : make_float2(0.0f, 0.0f);
+                const ffa::df64 w(odd ? -w2.x : w2.x, odd ? -w2.y : w2.y);
                 static_for<NP>([&](auto I) {
                     constexpr TUV c = htuv(decltype(I)::value);
-                    const double r = R[hidx(c.t + b.t, c.u + b.u, c.v + b.v)];
-                    G[decltype(I)::value][jj] = fma(odd ? -r : r, w, G[decltype(I)::value][jj]);
+                    ffa::acc_prod(G[decltype(I)::value][jj], Rf[hidx(c.t + b.t, c.u + b.u, c.v + b.v)], w);
                 });
             }
         });
@@ -204,11 +213,11 @@ __global__ void __launch_bounds__(128) k_ed2_pair(Dev d, Ed2Args a, const int4* 
     const float4 Pf = d.pp_Pf[LB][Pl];
     const double rpP = d.pp_rp[LB][Pl];
     const float qP = d.pp_Q[LB][Pl];
-    double G[NP][JC];
+    ffa::dfacc G[NP][JC];
 #pragma unroll
     for (int i = 0; i < NP; ++i)
 #pragma unroll
-        for (int j = 0; j < JC; ++j) G[i][j] = 0.0;
+        for (int j = 0; j < JC; ++j) G[i][j] = ffa::dfacc{0.0f, 0.0f};
     // ket classes: >= LB when x is the bra, > LB when y is (each class pair once)
     if (side == 0 && LB <= 0) ed2_kets<LB, 0>(d, a, ky, jb0, nj, valid, Pd, Pf, rpP, qP, G);
     if ((side == 0 && LB <= 1) || (side == 1 && LB < 1)) ed2_kets<LB, 1>(d, a, ky, jb0, nj, valid, Pd, Pf, rpP, qP, G);
@@ -221,7 +230,16 @@ __global__ void __launch_bounds__(128) k_ed2_pair(Dev d, Ed2Args a, const int4* 
     for (int i = 0; i < NP; ++i)
 #pragma unroll
         for (int j = 0; j < JC; ++j)
-            if (j < nj) a.G[row0 + (int64_t)i * nov_k + j] = G[i][j];
+            if (j < nj) a.G[row0 + (int64_t)i * nov_k + j] = (double)G[i][j].s + (double)G[i][j].c;
+}
+
+// Float-float copy of the transition densities (the pair kernel's ket weights).
+__global__ void k_ed2_split(const double* __restrict__ U, float2* __restrict__ Udf, int64_t n)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const ffa::df64 v = ffa::from_double(U[i]);
+        Udf[i] = make_float2(v.hi, v.lo);
+    }
 }
 
 // E_D2 of each pair of the chunk: (ia|jb) = (sqrt(pi)/2) (sum_r U_x[r][ia] G_x[r][jb] + sum_r U_y[r][jb] G_y[r][ia]),
@@ -284,11 +302,19 @@ cudaError_t launch_ed2_transition(const Dev& d, const double* C, const int* nmo,
     return cudaGetLastError();
 }
 
-cudaError_t launch_ed2_pairs(const Dev& d, const double* U, const int64_t* uoff, const int* hoff, const int* n_ov,
-                             const int* pair_of, const int64_t* goff, double* G, double tau,
+cudaError_t launch_ed2_split(const double* U, float2* Udf, int64_t n, cudaStream_t s)
+{
+    if (n <= 0) return cudaSuccess;
+    k_ed2_split<<<(unsigned)std::min<int64_t>((n + 255) / 256, 4096), 256, 0, s>>>(U, Udf, n);
+    note_launches(1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_ed2_pairs(const Dev& d, const double* U, const float2* Udf, const int64_t* uoff, const int* hoff,
+                             const int* n_ov, const int* pair_of, const int64_t* goff, double* G, double tau,
                              const int4* const items[3], const int n_items[3], cudaStream_t s)
 {
-    const Ed2Args a{U, uoff, hoff, n_ov, pair_of, goff, G, (float)tau};
+    const Ed2Args a{U, Udf, uoff, hoff, n_ov, pair_of, goff, G, (float)tau};
     const int wpb = 4;
     if (n_items[0] > 0) k_ed2_pair<0><<<(n_items[0] + wpb - 1) / wpb, 32 * wpb, 0, s>>>(d, a, items[0], n_items[0]);
     if (n_items[1] > 0) k_ed2_pair<1><<<(n_items[1] + wpb - 1) / wpb, 32 * wpb, 0, s>>>(d, a, items[1], n_items[1]);
@@ -303,7 +329,7 @@ cudaError_t launch_ed2_energy(const Dev& d, int n_pairs, int max_entries, const 
                               cudaStream_t s)
 {
     if (n_pairs <= 0) return cudaSuccess;
-    const Ed2Args a{U, uoff, hoff, n_ov, pair_of, goff, const_cast<double*>(G), 0.0f};
+    const Ed2Args a{U, nullptr, uoff, hoff, n_ov, pair_of, goff, const_cast<double*>(G), 0.0f};
     const dim3 grid(n_pairs, ed2_energy_slices(max_entries));
     k_ed2_energy<<<grid, 256, 0, s>>>(d, a, C, eps, nmo, n_herm, E);
     note_launches(1);

@@ -330,8 +330,9 @@ cudaError_t launch_energy_d2(const Dev& d, int n_pairs, const int* pair_of, cons
 // (E[q * slices + k], max_entries = the chunk's largest n_ov(x) n_ov(y)).
 cudaError_t launch_ed2_transition(const Dev& d, const double* C, const int* nmo, const int64_t* uoff, const int* hoff,
                                   const int* n_ov, int max_ov, double* U, cudaStream_t s);
-cudaError_t launch_ed2_pairs(const Dev& d, const double* U, const int64_t* uoff, const int* hoff, const int* n_ov,
-                             const int* pair_of, const int64_t* goff, double* G, double tau,
+cudaError_t launch_ed2_split(const double* U, float2* Udf, int64_t n, cudaStream_t s);  // float-float copy of U
+cudaError_t launch_ed2_pairs(const Dev& d, const double* U, const float2* Udf, const int64_t* uoff, const int* hoff,
+                             const int* n_ov, const int* pair_of, const int64_t* goff, double* G, double tau,
                              const int4* const items[3], const int n_items[3], cudaStream_t s);
 cudaError_t launch_ed2_energy(const Dev& d, int n_pairs, int max_entries, const double* U, const int64_t* uoff,
                               const int* hoff, const int* n_ov, const int* pair_of, const int64_t* goff, const double* G,

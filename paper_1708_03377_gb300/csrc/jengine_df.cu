@@ -103,27 +103,6 @@ __device__ __forceinline__ void df_ketbuf_flush(const DfKetBuf& kb, int cnt, dou
     __syncwarp();
 }
 
-// Sum of df64 products kept unnormalised (s + c): each product x y adds its rounded leading part to s
-// by Knuth's two-sum and its error terms (the FMA residual of x.hi y.hi and the cross products) to c,
-// with no renormalisation per term (the compensated dot product of Ogita, Rump and Oishi, 2005);
-// 12 FP32 operations per term instead of 15 for a normalised df64 fma.
-struct dfacc {
-    float s, c;
-};
-
-__device__ __forceinline__ void acc_prod(dfacc& a, df64 x, df64 y)
-{
-    const float p = __fmul_rn(x.hi, y.hi);
-    float e = __fmaf_rn(x.hi, y.hi, -p);
-    e = __fmaf_rn(x.hi, y.lo, e);
-    e = __fmaf_rn(x.lo, y.hi, e);
-    const float s = __fadd_rn(a.s, p);
-    const float bp = __fsub_rn(s, a.s);
-    const float t = __fadd_rn(__fsub_rn(a.s, __fsub_rn(s, bp)), __fsub_rn(p, bp));
-    a.s = s;
-    a.c = __fadd_rn(a.c, __fadd_rn(t, e));
-}
-
 // 1/sqrt(x) of a df64 x > 0 from a float seed s ~ x.hi^{-1/2} (relative error <= 2^-22): one float
 // Newton step, then one df64 correction y = r + r e / 2 with e = 1 - x r^2 formed exactly enough
 // (r^2 as an exact float product pair, 1 - (x r^2).hi exact by Sterbenz); relative error ~1e-14.
