@@ -270,8 +270,9 @@ static void mark(fef_ctx* c, int i)
 
 static void ensure_learn_buffers(fef_ctx* c);
 
-// Intra-fragment ERI tasks (fragment, shell pair s1, shell pair s2 >= s1, bra component) sorted by
-// angular-momentum class cls = ((la 3 + lb) 3 + lc) 3 + ld; cls_off[c] = first task of class c.
+// Intra-fragment ERI tasks (fragment, shell pair s1, shell pair s2 >= s1, first bra component; the task
+// covers intra_nkb(la, lb, lc, ld) components) sorted by angular-momentum class
+// cls = ((la 3 + lb) 3 + lc) 3 + ld; cls_off[c] = first task of class c.
 static void intra_eri_tasks(int nf, const std::vector<int>& frag_sp0, const std::vector<int>& sp_a,
                             const std::vector<int>& sp_b, const std::vector<int>& sh_l, std::vector<int4>& tasks,
                             std::vector<int>& cls_off)
@@ -282,7 +283,8 @@ static void intra_eri_tasks(int nf, const std::vector<int>& frag_sp0, const std:
             for (int s2 = s1; s2 < frag_sp0[x + 1]; ++s2) {
                 const int la = sh_l[sp_a[s1]], lb = sh_l[sp_b[s1]], lc = sh_l[sp_a[s2]], ld = sh_l[sp_b[s2]];
                 const int cls = ((la * 3 + lb) * 3 + lc) * 3 + ld;
-                for (int k = 0; k < ncart(la) * ncart(lb); ++k) by_cls[cls].push_back(make_int4(x, s1, s2, k));
+                const int step = intra_nkb(la, lb, lc, ld);
+                for (int k = 0; k < ncart(la) * ncart(lb); k += step) by_cls[cls].push_back(make_int4(x, s1, s2, k));
             }
     tasks.clear();
     cls_off.assign(82, 0);

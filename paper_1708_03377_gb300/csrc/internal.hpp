@@ -189,6 +189,18 @@ cudaError_t launch_far_energy(const Dev& d, const double* E_far, double* E_frag,
 cudaError_t launch_near_multipole_field(const Dev& d, const double* M, const double* Mnuc, const double* cen,
                                        const double* D, double* mult, double* pot, double* omega, int64_t n_omega,
                                        cudaStream_t s);
+// Bra components per task of the specialised s/p intra-fragment ERI kernels: consecutive components
+// kb0 .. kb0 + NKB - 1 share each primitive quartet's Boys values and R recursion, as many as fit in
+// registers beside the bra's Hermite tables (all components when at most 27 outputs and no p-p bra
+// pair; for a p-p bra pair one Cartesian row against an s or p ket component set of at most 3, else
+// one component).  Tasks of classes with a d shell take one component each.
+__host__ __device__ constexpr int intra_nkb(int la, int lb, int lc, int ld)
+{
+    return (la > 1 || lb > 1 || lc > 1 || ld > 1) ? 1
+           : (la == 1 && lb == 1) ? ((1 + 2 * lc) * (1 + 2 * ld) <= 3 ? (lc + ld == 0 ? 9 : 3) : 1)
+           : ((1 + 2 * la) * (1 + 2 * lb) * (1 + 2 * lc) * (1 + 2 * ld) <= 27 ? (1 + 2 * la) * (1 + 2 * lb) : 1);
+}
+
 // intra-fragment ERI rows for tasks (fragment, shell pair s1, shell pair s2 >= s1, bra component) sorted
 // by class cls = ((la 3 + lb) 3 + lc) 3 + ld, class c at [cls_off[c], cls_off[c + 1]) (intra_eri_tasks)
 cudaError_t launch_intra_eri(const Dev& d, const int4* tasks, const std::vector<int>& cls_off, double* eri,

@@ -874,21 +874,24 @@ __device__ __forceinline__ double e_pick(const double (*E)[3][5], int ai, int bi
 }
 
 // Lane `sub` of the nsub lanes that share one task takes the primitive quartets sub, sub + nsub, ...
-// (its partial row in out; the caller sums the lanes).
-template <int LA, int LB, int LC, int LD>
-__device__ __forceinline__ void eri_bra_row_t(const Dev& d, const int s1, const int s2, const int kb, double* out,
+// (its partial rows in out[NKB][NC ND]; the caller sums the lanes).
+template <int LA, int LB, int LC, int LD, int NKB>
+__device__ __forceinline__ void eri_bra_row_t(const Dev& d, const int s1, const int s2, const int kb0, double* out,
                                               const int sub, const int nsub)
 {
-    constexpr int NBc = ncart(LB), NC = ncart(LC), ND = ncart(LD);
+    constexpr int NBc = ncart(LB), NC = ncart(LC), ND = ncart(LD), NK = NC * ND;
     constexpr int LAB = LA + LB, LCD = LC + LD, L = LAB + LCD;
     const int sa = d.sp_a[s1], sb = d.sp_b[s1], sc = d.sp_a[s2], sd = d.sp_b[s2];
-    int ax, ay, az, bx, by, bz;
-    cart_of(LA, kb / NBc, ax, ay, az);
-    cart_of(LB, kb % NBc, bx, by, bz);
+    int ax[NKB], ay[NKB], az[NKB], bx[NKB], by[NKB], bz[NKB];
+#pragma unroll
+    for (int j = 0; j < NKB; ++j) {
+        cart_of(LA, (kb0 + j) / NBc, ax[j], ay[j], az[j]);
+        cart_of(LB, (kb0 + j) % NBc, bx[j], by[j], bz[j]);
+    }
     const double *A = d.atom_xyz + 3 * d.sh_atom[sa], *B = d.atom_xyz + 3 * d.sh_atom[sb];
     const double *C = d.atom_xyz + 3 * d.sh_atom[sc], *Dc = d.atom_xyz + 3 * d.sh_atom[sd];
 #pragma unroll
-    for (int k = 0; k < NC * ND; ++k) out[k] = 0.0;
+    for (int k = 0; k < NKB * NK; ++k) out[k] = 0.0;
     const int gP0 = d.sp_pp0[s1], nP = d.sh_np[sa] * d.sh_np[sb];
     const int gQ0 = d.sp_pp0[s2], nQ = d.sh_np[sc] * d.sh_np[sd];
     for (int pq = sub; pq < nP * nQ; pq += nsub) {
@@ -904,19 +907,10 @@ __device__ __forceinline__ void eri_bra_row_t(const Dev& d, const int s1, const 
             const double4_32a P = d.pp_P[LAB][gP0 + i];
             const double p = P.w;
             const double cp = d.pp_K[LAB][gP0 + i] * kSqrt2Pi52 / p;
-            double Eb[3][LAB + 1];
-            {
-                double E[3][3][5];
-                md_E1(LA, LB, p, P.x - A[0], P.x - B[0], E);
-#pragma unroll
-                for (int t = 0; t <= LAB; ++t) Eb[0][t] = e_pick<LA, LB>(E, ax, bx, t);
-                md_E1(LA, LB, p, P.y - A[1], P.y - B[1], E);
-#pragma unroll
-                for (int t = 0; t <= LAB; ++t) Eb[1][t] = e_pick<LA, LB>(E, ay, by, t);
-                md_E1(LA, LB, p, P.z - A[2], P.z - B[2], E);
-#pragma unroll
-                for (int t = 0; t <= LAB; ++t) Eb[2][t] = e_pick<LA, LB>(E, az, bz, t);
-            }
+            double Ea[3][3][3][5];
+            md_E1(LA, LB, p, P.x - A[0], P.x - B[0], Ea[0]);
+            md_E1(LA, LB, p, P.y - A[1], P.y - B[1], Ea[1]);
+            md_E1(LA, LB, p, P.z - A[2], P.z - B[2], Ea[2]);
             const double X = P.x - Q.x, Y = P.y - Q.y, Z = P.z - Q.z;
             const double rs = rsqrt(p + q);
             const double alpha = p * q * (rs * rs);
@@ -930,6 +924,15 @@ __device__ __forceinline__ void eri_bra_row_t(const Dev& d, const int s1, const 
                 pre *= -2.0 * alpha;
             }
             md_R<L, double>(R, base, X, Y, Z);
+#pragma unroll
+            for (int jb = 0; jb < NKB; ++jb) {
+            double Eb[3][LAB + 1];
+#pragma unroll
+            for (int t = 0; t <= LAB; ++t) {
+                Eb[0][t] = e_pick<LA, LB>(Ea[0], ax[jb], bx[jb], t);
+                Eb[1][t] = e_pick<LA, LB>(Ea[1], ay[jb], by[jb], t);
+                Eb[2][t] = e_pick<LA, LB>(Ea[2], az[jb], bz[jb], t);
+            }
             double Yb[nh(LCD)];
             static_for<nh(LCD)>([&](auto H) {
                 constexpr TUV c2 = htuv(decltype(H)::value);
@@ -940,7 +943,7 @@ __device__ __forceinline__ void eri_bra_row_t(const Dev& d, const int s1, const 
                     for (int u = 0; u <= LAB - t; ++u)
 #pragma unroll
                         for (int v = 0; v <= LAB - t - u; ++v)
-                            if (t <= ax + bx && u <= ay + by && v <= az + bz)
+                            if (t <= ax[jb] + bx[jb] && u <= ay[jb] + by[jb] && v <= az[jb] + bz[jb])
                                 y += Eb[0][t] * Eb[1][u] * Eb[2][v] * R[hidx(t + c2.t, u + c2.u, v + c2.v)];
                 Yb[decltype(H)::value] = ((c2.t + c2.u + c2.v) & 1) ? -y : y;
             });
@@ -962,8 +965,9 @@ __device__ __forceinline__ void eri_bra_row_t(const Dev& d, const int s1, const 
                                 if (t <= cx + dx && u <= cy + dy && w <= cz + dz)
                                     v += e_pick<LC, LD>(Ek[0], cx, dx, t) * e_pick<LC, LD>(Ek[1], cy, dy, u) *
                                          e_pick<LC, LD>(Ek[2], cz, dz, w) * Yb[hidx(t, u, w)];
-                    out[ic * ND + id] += v;
+                    out[jb * NK + ic * ND + id] += v;
                 }
+            }
             }
         }
     }
@@ -1003,19 +1007,22 @@ constexpr int kIntraLanes = 8;
 template <int LA, int LB, int LC, int LD>
 __global__ void __launch_bounds__(128) k_intra_eri_t(Dev d, const int4* __restrict__ tasks, int n_tasks, double* eri)
 {
-    constexpr int NK = ncart(LC) * ncart(LD);
+    constexpr int NK = ncart(LC) * ncart(LD), NKB = intra_nkb(LA, LB, LC, LD);
     const int w = (blockIdx.x * blockDim.x + threadIdx.x) / kIntraLanes, sub = threadIdx.x % kIntraLanes;
     const bool on = w < n_tasks;  // whole lane groups (128 is a multiple of kIntraLanes)
     const int4 tk = tasks[on ? w : 0];
-    double out[NK];
-    if (on) eri_bra_row_t<LA, LB, LC, LD>(d, tk.y, tk.z, tk.w, out, sub, kIntraLanes);
+    double out[NKB * NK];
+    if (on) eri_bra_row_t<LA, LB, LC, LD, NKB>(d, tk.y, tk.z, tk.w, out, sub, kIntraLanes);
 #pragma unroll
-    for (int k = 0; k < NK; ++k) {
+    for (int k = 0; k < NKB * NK; ++k) {
         if (!on) out[k] = 0.0;
 #pragma unroll
         for (int o = kIntraLanes / 2; o > 0; o >>= 1) out[k] += __shfl_xor_sync(0xffffffffu, out[k], o, kIntraLanes);
     }
-    if (on && sub == 0) intra_eri_store<ncart(LC), ncart(LD)>(d, tk, out, eri);
+    if (on && sub == 0)
+#pragma unroll
+        for (int j = 0; j < NKB; ++j)
+            intra_eri_store<ncart(LC), ncart(LD)>(d, make_int4(tk.x, tk.y, tk.z, tk.w + j), out + j * NK, eri);
 }
 
 __global__ void k_intra_eri(Dev d, const int4* __restrict__ tasks, int n_tasks, double* eri)
