@@ -572,14 +572,14 @@ cudaError_t launch_far_energy(const Dev& d, const double* E_far, double* E_frag,
 // so that V^y_{mu nu} = sum_{P in (mu,nu)} K_P sum_tuv E^{mu nu}_tuv V~_P[tuv] and
 // tr(D^x V^y) = sum_P sum_tuv Dtrue_P[tuv] V~_P[tuv] with Dtrue_P = Dh_P p/c (c = sqrt(2 pi^{5/2})).
 template <int L>
-__device__ inline void nuclear_field(const Dev& d, const double4_32a P, int atom0, int nat, double* acc)
+__device__ __forceinline__ void nuclear_field(const Dev& d, const double4_32a P, int atom0, int nat, double (&acc)[nh(L)])
 {
     double F[L + 1], base[L + 1], R[nh(L)];
     for (int c = atom0; c < atom0 + nat; ++c) {
         const double* C = d.atom_xyz + 3 * c;
         double X = P.x - C[0], Y = P.y - C[1], Z = P.z - C[2];
         double T = P.w * (X * X + Y * Y + Z * Z);
-        boys_fp64_rt(d.boys, T, L, F);
+        boys_fp64<L>(d.boys, T, boys_row((float)T), F);
         double f = -d.atom_Z[c] * 2.0 * kPi / P.w;
 #pragma unroll
         for (int n = 0; n <= L; ++n) {
@@ -592,16 +592,6 @@ __device__ inline void nuclear_field(const Dev& d, const double4_32a P, int atom
     }
 }
 
-__device__ inline void nuclear_field_rt(const Dev& d, int L, const double4_32a P, int atom0, int nat, double* acc)
-{
-    switch (L) {
-        case 0: nuclear_field<0>(d, P, atom0, nat, acc); break;
-        case 1: nuclear_field<1>(d, P, atom0, nat, acc); break;
-        case 2: nuclear_field<2>(d, P, atom0, nat, acc); break;
-        case 3: nuclear_field<3>(d, P, atom0, nat, acc); break;
-        default: nuclear_field<4>(d, P, atom0, nat, acc); break;
-    }
-}
 
 // primitive pair number t of fragment x (classes in order) -> (class, global index in the class)
 __device__ inline bool frag_prim_pair(const Dev& d, int x, int t, int& L, int& g)
@@ -619,6 +609,38 @@ __device__ inline bool frag_prim_pair(const Dev& d, int x, int t, int& L, int& g
 
 // Environment field of all neighbours' nuclei on every primitive pair of x, in Hermite form,
 // stored pre-scaled by p/c so that the J back-transform turns it into V_env.
+template <int L>
+__device__ __forceinline__ void nuclear_env_pp(const Dev& d, int x, int g, double* vh)
+{
+    const double4_32a P = d.pp_P[L][g];
+    double acc[nh(L)];
+#pragma unroll
+    for (int k = 0; k < nh(L); ++k) acc[k] = 0.0;
+    for (int c = d.frag_nbr0[x]; c < d.frag_nbr0[x + 1]; ++c) {
+        const int y = d.nbr[c];
+        nuclear_field<L>(d, P, d.frag_atom0[y], d.frag_nat[y], acc);
+    }
+    const double sc = P.w / kSqrt2Pi52;
+#pragma unroll
+    for (int k = 0; k < nh(L); ++k) vh[(size_t)k * d.n_pp[L] + g] = acc[k] * sc;
+}
+
+// The field of y's nuclei on primitive pair g of x, into its slot of the (pair, direction) block.
+template <int L>
+__device__ __forceinline__ void nuclear_trace_pp(const Dev& d, int x, int y, int g, int64_t base, double* fields)
+{
+    const double4_32a P = d.pp_P[L][g];
+    double v[nh(L)];
+#pragma unroll
+    for (int k = 0; k < nh(L); ++k) v[k] = 0.0;
+    nuclear_field<L>(d, P, d.frag_atom0[y], d.frag_nat[y], v);
+    for (int L2 = 0; L2 < L; ++L2) base += (int64_t)nh(L2) * d.frag_npp[x * kClasses + L2];
+    const int n = d.frag_npp[x * kClasses + L], i = g - d.frag_pp0[x * kClasses + L];
+    const double sc = P.w / kSqrt2Pi52;
+#pragma unroll
+    for (int k = 0; k < nh(L); ++k) fields[base + (int64_t)k * n + i] = v[k] * sc;
+}
+
 __global__ void k_nuclear_env_h(Dev d, double* vh0, double* vh1, double* vh2, double* vh3, double* vh4)
 {
     double* vh[kClasses] = {vh0, vh1, vh2, vh3, vh4};
@@ -628,15 +650,13 @@ __global__ void k_nuclear_env_h(Dev d, double* vh0, double* vh1, double* vh2, do
     for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < npp; t += gridDim.x * blockDim.x) {
         int L, g;
         if (!frag_prim_pair(d, x, t, L, g)) continue;
-        double4_32a P = d.pp_P[L][g];
-        double acc[nh(kMaxLPair)];
-        for (int k = 0; k < nh(L); ++k) acc[k] = 0.0;
-        for (int c = d.frag_nbr0[x]; c < d.frag_nbr0[x + 1]; ++c) {
-            int y = d.nbr[c];
-            nuclear_field_rt(d, L, P, d.frag_atom0[y], d.frag_nat[y], acc);
+        switch (L) {
+            case 0: nuclear_env_pp<0>(d, x, g, vh[0]); break;
+            case 1: nuclear_env_pp<1>(d, x, g, vh[1]); break;
+            case 2: nuclear_env_pp<2>(d, x, g, vh[2]); break;
+            case 3: nuclear_env_pp<3>(d, x, g, vh[3]); break;
+            default: nuclear_env_pp<4>(d, x, g, vh[4]); break;
         }
-        double sc = P.w / kSqrt2Pi52;
-        for (int k = 0; k < nh(L); ++k) vh[L][(size_t)k * d.n_pp[L] + g] = acc[k] * sc;
     }
 }
 
@@ -667,15 +687,14 @@ __global__ void k_nuclear_trace_fields(Dev d, const int64_t* __restrict__ off, d
     for (int t = threadIdx.x; t < npp; t += blockDim.x) {
         int L, g;
         if (!frag_prim_pair(d, x, t, L, g)) continue;
-        const double4_32a P = d.pp_P[L][g];
-        double v[nh(kMaxLPair)];
-        for (int k = 0; k < nh(L); ++k) v[k] = 0.0;
-        nuclear_field_rt(d, L, P, d.frag_atom0[y], d.frag_nat[y], v);
-        int64_t base = off[2 * pr + dir];
-        for (int L2 = 0; L2 < L; ++L2) base += (int64_t)nh(L2) * d.frag_npp[x * kClasses + L2];
-        const int n = d.frag_npp[x * kClasses + L], i = g - d.frag_pp0[x * kClasses + L];
-        const double sc = P.w / kSqrt2Pi52;
-        for (int k = 0; k < nh(L); ++k) fields[base + (int64_t)k * n + i] = v[k] * sc;
+        const int64_t base = off[2 * pr + dir];
+        switch (L) {
+            case 0: nuclear_trace_pp<0>(d, x, y, g, base, fields); break;
+            case 1: nuclear_trace_pp<1>(d, x, y, g, base, fields); break;
+            case 2: nuclear_trace_pp<2>(d, x, y, g, base, fields); break;
+            case 3: nuclear_trace_pp<3>(d, x, y, g, base, fields); break;
+            default: nuclear_trace_pp<4>(d, x, y, g, base, fields); break;
+        }
     }
 }
 
