@@ -1,6 +1,7 @@
 """Failure detection and checkpoint/resume through the C ABI (no GPU fault, trap or hang).
 
-Faults are injected on the host: a NaN in the density handed to fef_build_fock (the device
+Context memory comes from the library pool and is reused across contexts (last test).  Faults are
+injected on the host: a NaN in the density handed to fef_build_fock (the device
 finiteness check of the Fock matrices turns it into FEF_ERR_NUMERIC, and the context stays usable),
 a fragment basis too linearly dependent for its electrons (FEF_ERR_BASIS after the canonical
 orthogonaliser), and an iteration limit that stops the FEF loop early (FEF_ERR_NOT_CONVERGED with
@@ -96,3 +97,28 @@ def test_checkpoint_resume_reaches_the_same_fixed_point():
     _, Et_again, _ = fef.fef_energies(resumed)
     assert n_again <= 2 and abs(Et_again - Et_full) < 1e-10
     resumed.close()
+
+
+def test_context_memory_is_reused():
+    """Contexts take their device memory from the library's stream-ordered pool: creating and
+    destroying the same 64-water context again does not take more device memory after the first
+    cycle (the pool's blocks are reused), and every cycle gives the same Fock matrices (to 1e-12: the
+    J-engine's FP64 atomics add in no fixed order)."""
+    fef = _fef()
+    import torch
+    system = S.water_box(64, 0)
+    opts = fef.fef_default_options(cutoff_A=8.0, schwarz=1e-12)
+    used, F0 = [], None
+    for cycle in range(6):
+        ctx = fef.fef_create_system(system, opts)
+        fef.fef_noninteracting_scf(ctx)
+        F = fef.fef_build_fock(ctx, fef.fef_get_densities(ctx))
+        ctx.close()
+        torch.cuda.synchronize()
+        free, total = torch.cuda.mem_get_info()
+        used.append(total - free)
+        if F0 is None:
+            F0 = F
+        assert np.abs(F - F0).max() < 1e-12
+    # after the first cycle the footprint is flat (64 MiB of slack for other allocations)
+    assert max(used[1:]) - min(used[1:]) < 64 * 2 ** 20, used
