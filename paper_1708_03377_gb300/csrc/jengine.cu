@@ -922,6 +922,8 @@ __global__ void k_delta_density(const double* __restrict__ Dh, const double* __r
 
 cudaError_t launch_delta_density(const Dev& d, double* const Dh_ref[kClasses], cudaStream_t s)
 {
+    // read only by the FP32 kernels of the d-shell classes (the s/p classes use the FP32 records)
+    if (d.max_l <= 1) return cudaSuccess;
     for (int L = 0; L < kClasses; ++L) {
         size_t n = (size_t)nh(L) * d.n_pp[L];
         if (n == 0) continue;
