@@ -22,6 +22,10 @@ learned_2000_waters: the learned start at full size, reduced: trained on 8 x 500
        timed), MIXED solves of 2 held-out 2000-water boxes from the superposition and the learned start.
 e_m2 / e_d2: one fef_energy_m2 / fef_energy_d2 call on the converged FP64 state (second-order
        energies, Eqs. EM2 and ED2), wall clock.
+heterocycle_1000_waters: the precision workload, a 130-AO C4N3OH5-like solute with s/p/d shells in
+       1000 waters (31 A cube, 8 A cutoff): the FP32 core's own error (one whole-density build of the
+       isolated densities against the FP64 build, per fragment and per Fock element), and the time
+       to 1e-8 Eh of FP64 and of MIXED (float-float reference) solves with autotuned tile plans.
 e2e    = the same step plus the device->host read of every converged density, wall clock.
 roofline: the J-engine (one persistent FP64 launch per Fock build) against the FP64 ALU peak.
 --impl reference: the CPU oracle on a bounded sample of the same workload.
@@ -243,6 +247,76 @@ def reduce_over_replicas(dist, total_ms, quartets, launches, device):
     return float(tmax[0]), float(t[1]), int(t[2])
 
 
+def heterocycle_leg(fef, S, stream):
+    """The precision workload: FP32-core whole build vs FP64 build of the isolated densities (per
+    fragment energy and Fock element errors), and FP64 vs MIXED time to 1e-8 Eh (CUDA events around
+    fef_iterate, after the isolated RHF and autotuning of the engines used)."""
+    import torch
+    system = S.solvated_heterocycle(n_water=1000, seed=0)
+    cut = 8.0
+
+    def timed(fn):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        out = fn()
+        e1.record(stream)
+        e1.synchronize()
+        return out, e0.elapsed_time(e1)
+
+    with torch.cuda.stream(stream):
+        o64 = fef.fef_default_options(cutoff_A=cut, schwarz=SCHWARZ, e_tol=E_TOL, use_graph=0)
+        t0 = time.perf_counter()
+        ctx = fef.fef_create_system(system, o64, stream=stream.cuda_stream)
+        stream.synchronize()
+        create_s = time.perf_counter() - t0
+        fef.fef_noninteracting_scf(ctx)
+        Diso = fef.fef_get_densities(ctx)
+        fef.fef_build_fock(ctx, Diso)
+        F64, b64_ms = timed(lambda: fef.fef_build_fock(ctx, Diso))
+        E64, _, _ = fef.fef_energies(ctx)
+        n0 = int(ctx.n_ao[0])  # the solute is fragment 0
+        ctx.close()
+        ow = fef.fef_default_options(cutoff_A=cut, schwarz=SCHWARZ, e_tol=E_TOL, precision=fef.FEF_MIXED,
+                                     mixed_build=fef.FEF_MIXED_WHOLE, use_graph=0)
+        ctx = fef.fef_create_system(system, ow, stream=stream.cuda_stream)
+        fef.fef_build_fock(ctx, Diso)
+        F32, b32_ms = timed(lambda: fef.fef_build_fock(ctx, Diso))
+        E32, _, _ = fef.fef_energies(ctx)
+        ctx.close()
+        dE = E32 - E64
+        dF = np.abs(F32 - F64)
+        solves = {}
+        for name, opts, engines in (
+                ("fp64", fef.fef_default_options(cutoff_A=cut, schwarz=SCHWARZ, e_tol=E_TOL), [fef.FEF_JENGINE_FP64]),
+                ("mixed", fef.fef_default_options(cutoff_A=cut, schwarz=SCHWARZ, e_tol=E_TOL, precision=fef.FEF_MIXED,
+                                                  exact_engine=fef.FEF_ENGINE_DF64),
+                 [fef.FEF_JENGINE_DF64, fef.FEF_JENGINE_FP32])):
+            ctx = fef.fef_create_system(system, opts, stream=stream.cuda_stream)
+            fef.fef_noninteracting_scf(ctx)
+            for e in engines:
+                fef.fef_autotune(ctx, e, reps=2, budget_ms=4000.0)
+            (n_macro, _), it_ms = timed(lambda: fef.fef_iterate(ctx))
+            _, E_tot, _ = fef.fef_energies(ctx)
+            E_x = fef.fef_energies(ctx)[0]
+            solves[name] = {"time_to_1e-8_ms": it_ms, "n_macro": int(n_macro), "E_tot": float(E_tot), "E_x": E_x}
+            ctx.close()
+    dEs = solves["mixed"]["E_x"] - solves["fp64"]["E_x"]
+    for v in solves.values():
+        del v["E_x"]
+    return {"workload": system.name + ", 8 A cutoff, Schwarz 1e-12", "n_frag": int(system.n_frag),
+            "solute_nao": int(n0), "create_s": create_s,
+            "fp32_whole_build": {"max_dE_x": float(np.abs(dE).max()), "rms_dE_x": float(np.sqrt(np.mean(dE ** 2))),
+                                 "solute_dE": float(dE[0]), "max_dF": float(dF.max()),
+                                 "solute_max_dF": float(dF[:n0 * n0].max()),
+                                 "fp32_build_ms": b32_ms, "fp64_build_ms": b64_ms,
+                                 "note": "FP32-core J-engine of the whole isolated density (no FP64 reference) "
+                                         "against the FP64 build (hartree)"},
+            "fp64": solves["fp64"], "mixed": solves["mixed"],
+            "mixed_speedup_vs_fp64": solves["fp64"]["time_to_1e-8_ms"] / solves["mixed"]["time_to_1e-8_ms"],
+            "mixed_converged": {"max_dE_x_vs_fp64": float(np.abs(dEs).max()),
+                                "dE_tot_vs_fp64": solves["mixed"]["E_tot"] - solves["fp64"]["E_tot"]}}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -253,6 +327,8 @@ def main():
     ap.add_argument("--ref-seconds", type=float, default=8.0)
     ap.add_argument("--no-learned-2000", action="store_true",
                     help="skip the reduced full-size learned-start leg (2000-water held-out boxes)")
+    ap.add_argument("--no-heterocycle", action="store_true",
+                    help="skip the precision leg (130-AO solute in 1000 waters)")
     args = ap.parse_args()
     ws, rank, local = dist_env()
     if args.impl == "reference":
@@ -433,6 +509,9 @@ def main():
         learned_2000 = lrn.run_experiment(train_snapshots=8, train_waters=500, per_snapshot=500, test_snapshots=2,
                                           test_waters=2000, fp64_test_snapshots=0, cutoff=CUTOFF_A, e_tol=E_TOL,
                                           epochs=200, warmup=1)
+    hetero = None
+    if not args.no_heterocycle and rank == 0:
+        hetero = heterocycle_leg(fef, S, stream)
     total_ms = float(sum(step_ms))
     if pg:
         total_ms, quartets, launches = reduce_over_replicas(pg, total_ms, quartets, launches, "cuda")
@@ -483,6 +562,7 @@ def main():
                           "train_samples": int(sum(len(x) for x in Xs)),
                           "train_loss": net_loss},
         "learned_2000_waters": learned_2000,
+        "heterocycle_1000_waters": hetero,
         "e_m2": {"ms_per_call": float(min(m2_ms[1:])), "E_m2_total": m2_tot, "transform_flop": m2_flop,
                  "note": "monomer second-order energy (Eq. EM2) of all fragments on the FEF canonical orbitals"},
         "e_d2": {"ms_per_call": float(min(d2_ms[1:])), "E_d2_total": d2_tot,

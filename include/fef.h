@@ -293,8 +293,12 @@ fef_status fef_set_tile_plan(fef_ctx* ctx, int32_t engine, const fef_tile_plan* 
  * ket pairs; classes in decreasing order of cost) on every k-th fragment pair, k chosen so that one
  * timed pass takes about budget_ms/64, then, when a full build fits the budget, persistent queues
  * against one launch per class pair, serial or concurrent.  Each candidate is timed reps times (best kept) after a warm-up.
- * Runs between builds (it overwrites the J-engine accumulators; the next build starts afresh).
- * out (nullable) receives the chosen plan.  Errors: ARG, CUDA. */
+ * The timed passes run on the context's current densities, prepared as a build of that engine prepares
+ * them (Hermite densities; for FEF_JENGINE_FP32 the FP32 records relative to the stored reference
+ * density, or to zero before the first reference build).  Runs between builds (it overwrites the
+ * J-engine accumulators and the per-build Hermite data; the next build recomputes both from its own
+ * density; the reference of FEF_MIXED is left unchanged).  out (nullable) receives the chosen plan.
+ * Errors: ARG, CUDA. */
 fef_status fef_autotune(fef_ctx* ctx, int32_t engine, int32_t reps, double budget_ms, fef_tile_plan* out);
 
 /* Measure this GPU's FP64 and FP32 FMA throughput with a register-resident FMA chain kernel.

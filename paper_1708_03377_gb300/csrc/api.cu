@@ -817,6 +817,15 @@ extern "C" fef_status fef_create(const fef_geometry* g, const fef_basis* bs, con
             d.pp_u[L] = b->alloc<double>((size_t)nh(L) * n, "hermite weights");
             b->Jh[L] = b->alloc<double>((size_t)nh(L) * n, "hermite field");
             d.pp_Jh[L] = b->Jh[L];
+            // pool memory comes back with old contents: the per-build inputs start as zeros (no
+            // reference density; FP32 records of zero weight) until a build or fef_autotune fills them
+            const size_t nhn = (size_t)nh(L) * n;
+            ck(cudaMemsetAsync(b->Dh_ref[L], 0, sizeof(double) * nhn, s), "zero");
+            ck(cudaMemsetAsync(d.pp_Dh[L], 0, sizeof(double) * nhn, s), "zero");
+            ck(cudaMemsetAsync(d.pp_u[L], 0, sizeof(double) * nhn, s), "zero");
+            ck(cudaMemsetAsync(d.pp_Dh32[L], 0, sizeof(float) * nhn, s), "zero");
+            ck(cudaMemsetAsync(d.pp_udf[L], 0, sizeof(float2) * nhn, s), "zero");
+            ck(cudaMemsetAsync(d.pp_rec32[L], 0, sizeof(float) * rec32_len(L) * (size_t)n, s), "zero");
         }
         b->rec_resid = b->alloc<double>(max_npp, "fp32 record residues");
         b->fc_qmin = b->alloc<float>((size_t)nf * kClasses, "class Schwarz minimum");
@@ -1518,6 +1527,17 @@ extern "C" fef_status fef_autotune(fef_ctx* c, int32_t engine, int32_t reps, dou
             "fef_autotune: bad engine, reps or budget");
     Buffers* b = c->buf;
     ck(cudaStreamSynchronize(c->stream), "autotune");
+    // the engine's inputs from the current densities (the same preparation as a build of that
+    // engine, relative to the stored reference for FP32), so that the timed passes see the
+    // context's own pair data and weights; the reference itself is left unchanged
+    const Dev& d = c->dev;
+    ck(launch_hermite_density(d, b->D, c->stream), "autotune: hermite density");
+    if (engine == 1) {
+        ck(launch_delta_density(d, b->Dh_ref, c->stream), "autotune: delta density");
+        ck(launch_fp32_records(d, b->Dh_ref, b->rec_resid, c->stream), "autotune: fp32 records");
+    } else if (engine == 2) {
+        ck(launch_df_density(d, c->stream), "autotune: df64 density");
+    }
     const int2* tiles[kClasses][kClasses];
     for (int i = 0; i < kClasses; ++i)
         for (int j = 0; j < kClasses; ++j) tiles[i][j] = b->tiles[i][j];

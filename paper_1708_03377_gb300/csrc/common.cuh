@@ -162,11 +162,32 @@ __device__ __forceinline__ void boys_fp64(const double* __restrict__ table, doub
     }
 }
 
+// The hardware estimate of 1/sqrt(x) (rsqrt.approx.ftz: normal inputs only, which holds for every
+// argument here), without the library's subnormal-input handling.
+__device__ __forceinline__ float rsqrt_approx(float x)
+{
+    float y;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+// 1/sqrt(x) in FP32: the hardware estimate refined by one Newton step y (3 - x y^2) / 2, with the
+// residual 1 - x y^2 formed by an FMA, so that the result is within about one unit in the last place
+// and its error has no systematic sign (a biased 1/R would shift the whole long-range Coulomb field).
+__device__ __forceinline__ float rsqrt_nr(float x)
+{
+    const float y = rsqrt_approx(x);
+    const float h = x * y;
+    const float e = fmaf(-h, y, 1.0f);
+    return fmaf(0.5f * y, e, y);
+}
+
 // F_0..F_L at T in FP32 (mixed-precision core).
 template <int L>
 __device__ __forceinline__ void boys_fp32(const float* __restrict__ table, float T, float* F)
 {
-    const int k = (int)(fminf(T, (float)(kBoys32Rows - 1) * (float)kBoysH) * (float)kBoysInvH + 0.5f);
+    // the row index is clamped to the table on both sides, whatever T is (T < 0 or NaN: row 0)
+    const int k = (int)(fmaxf(fminf(T, (float)(kBoys32Rows - 1) * (float)kBoysH), 0.0f) * (float)kBoysInvH + 0.5f);
     if (k < kBoys32Rows - 1) {
         const float* row = table + (size_t)k * kBoysRowLen;
         const float d = __ldg(row + kBoys32Order + 3) - T;
@@ -177,32 +198,13 @@ __device__ __forceinline__ void boys_fp32(const float* __restrict__ table, float
             F[m] = fmaf(d, fmaf(d, fmaf(d, fmaf(d, c4, c.w), c.z), c.y), c.x);
         }
     } else {
-        const float rt = rsqrtf(T);
+        // refined reciprocal square root: the far-field quartets of every partner share its error
+        const float rt = rsqrt_nr(T);
         const float half_inv_T = 0.5f * rt * rt;
         F[0] = (float)kSqrtPiHalf * rt;
 #pragma unroll
         for (int m = 1; m <= L; ++m) F[m] = F[m - 1] * ((2.0f * m - 1.0f) * half_inv_T);
     }
-}
-
-// 1/sqrt(x) in FP32: the hardware estimate refined by one Newton step y (3 - x y^2) / 2, with the
-// residual 1 - x y^2 formed by an FMA, so that the result is within about one unit in the last place
-// and its error has no systematic sign (a biased 1/R would shift the whole long-range Coulomb field).
-// The hardware estimate of 1/sqrt(x) (rsqrt.approx.ftz: normal inputs only, which holds for every
-// argument here), without the library's subnormal-input handling.
-__device__ __forceinline__ float rsqrt_approx(float x)
-{
-    float y;
-    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
-    return y;
-}
-
-__device__ __forceinline__ float rsqrt_nr(float x)
-{
-    const float y = rsqrt_approx(x);
-    const float h = x * y;
-    const float e = fmaf(-h, y, 1.0f);
-    return fmaf(0.5f * y, e, y);
 }
 
 // 1/sqrt(x) in FP64 from an FP32 estimate s of relative error e0 (up to ~1e-5): one step of the
@@ -230,14 +232,16 @@ __device__ __forceinline__ void two_sum_acc(float& hi, float& lo, float a)
 
 __device__ __forceinline__ int boys_row(float Tf)
 {
-    float k = fminf(Tf, (float)(kBoysRows - 1) * (float)kBoysH) * (float)kBoysInvH + 0.5f;
-    return (int)k;  // T >= Tmax + h/2 maps to the last row, which selects the asymptotic branch
+    // clamped to the table on both sides: T >= Tmax + h/2 maps to the last row, which selects the
+    // asymptotic branch; T < 0 or NaN (never produced by valid pair data) to row 0
+    float k = fmaxf(fminf(Tf, (float)(kBoysRows - 1) * (float)kBoysH), 0.0f) * (float)kBoysInvH + 0.5f;
+    return (int)k;
 }
 
 // Runtime-L variant for the non-hot kernels (one-electron, Schwarz, intra-fragment).
 __device__ inline void boys_fp64_rt(const double* __restrict__ table, double T, int L, double* F)
 {
-    int k = (int)(fmin(T, (kBoysRows - 1) * kBoysH) * kBoysInvH + 0.5);
+    int k = (int)(fmax(fmin(T, (kBoysRows - 1) * kBoysH), 0.0) * kBoysInvH + 0.5);
     if (k < kBoysRows - 1) {
         const double* row = table + (size_t)k * kBoysRowLen;
         const double d = row[kBoysOrder + 1] - T;

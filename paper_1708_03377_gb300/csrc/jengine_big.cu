@@ -142,7 +142,7 @@ __device__ __forceinline__ void jtile_big(const Dev& d, const int2 tl, const int
             X = (Pr.x - Qr.x) + ox;
             Y = (Pr.y - Qr.y) + oy;
             Z = (Pr.z - Qr.z) + oz;
-            const float r = rsqrtf(Pr.w + Qr.w);
+            const float r = rsqrt_nr(Pr.w + Qr.w);
             const float alpha = Pr.w * Qr.w * (r * r);
             float F[L + 1];
             boys_fp32<L>(d.boys32, alpha * fmaf(X, X, fmaf(Y, Y, Z * Z)), F);

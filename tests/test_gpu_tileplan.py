@@ -105,6 +105,31 @@ def test_autotune_water_box():
     ctx.close()
 
 
+def test_autotune_mixed_engines_before_first_build(formamide_water):
+    """Autotuning the float-float and FP32-core engines of a MIXED context with d shells before its
+    first build, in memory that an earlier context returned to the pool: the tuner prepares each
+    engine's inputs from the current densities itself, and the tuned solve reaches the same fixed
+    point as an untuned one (both end on exact references)."""
+    fef = _fef()
+    system = formamide_water[0]
+    opts = fef.fef_default_options(schwarz=1e-12, e_tol=1e-9, precision=fef.FEF_MIXED,
+                                   exact_engine=fef.FEF_ENGINE_DF64)
+    ctx = fef.fef_create_system(system, opts)
+    fef.fef_iterate(ctx)
+    E_ref = fef.fef_energies(ctx)[1]
+    ctx.close()  # its memory goes back to the pool with its contents
+    for after_scf in (False, True):
+        ctx = fef.fef_create_system(system, opts)
+        if after_scf:
+            fef.fef_noninteracting_scf(ctx)
+        for eng in (fef.FEF_JENGINE_DF64, fef.FEF_JENGINE_FP32):
+            plan = fef.fef_autotune(ctx, eng, reps=1, budget_ms=200.0)
+            assert plan["tuned_ms"] > 0.0
+        fef.fef_iterate(ctx)
+        assert abs(fef.fef_energies(ctx)[1] - E_ref) < 1e-8
+        ctx.close()
+
+
 def test_bad_plan_rejected():
     fef = _fef()
     ctx = fef.fef_create_system(S.water_dimer(0), fef.fef_default_options())
