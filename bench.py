@@ -147,19 +147,21 @@ def dist_env():
 
 def profile_traffic():
     """DRAM bytes per J-engine build from the committed ncu summary, if it was taken on the
-    current J-engine source (matching hash); else None."""
+    current J-engine sources (jengine.cu and common.cuh, matching hashes); else None."""
     path = os.path.join(ROOT, "profiles", "jengine_water64_fp64.txt")
-    src = os.path.join(ROOT, "paper_1708_03377_gb300", "csrc", "jengine.cu")
+    csrc = os.path.join(ROOT, "paper_1708_03377_gb300", "csrc")
     if not os.path.exists(path):
         return None
-    h = hashlib.sha1(open(src, "rb").read()).hexdigest()[:12]
-    traffic, hh = None, None
+    want = {k: hashlib.sha1(open(os.path.join(csrc, f), "rb").read()).hexdigest()[:12]
+            for k, f in (("jengine_source_sha1", "jengine.cu"), ("common_source_sha1", "common.cuh"))}
+    got, traffic = {}, None
     for line in open(path):
-        if line.startswith("jengine_source_sha1:"):
-            hh = line.split(":", 1)[1].strip()
-        if line.startswith("dram_bytes_per_build:"):
+        key = line.split(":", 1)[0]
+        if key in want:
+            got[key] = line.split(":", 1)[1].strip()
+        if key == "dram_bytes_per_build":
             traffic = float(line.split(":", 1)[1].strip())
-    return traffic if hh == h else None
+    return traffic if got == want else None
 
 
 def cpu_baseline(seconds=12.0):
