@@ -317,10 +317,7 @@ static void build_fock_device(fef_ctx* c, int kind)
         if (kind == kBuildFP32Ref)
             ck(cudaMemsetAsync(b->Dh_ref[L], 0, sizeof(double) * b->njh[L], s), "zero reference");
     }
-    if (fp32) {
-        ck(launch_delta_density(d, b->Dh_ref, s), "delta density");
-        ck(launch_fp32_records(d, b->Dh_ref, b->rec_resid, s), "fp32 records");
-    }
+    if (fp32) ck(launch_fp32_records(d, b->Dh_ref, b->rec_resid, s), "fp32 records");
     const bool df = !fp32 && c->opt.exact_engine == FEF_ENGINE_DF64;
     if (df) ck(launch_df_density(d, s), "df64 density");
     const int2* tiles[kClasses][kClasses];
@@ -791,7 +788,7 @@ extern "C" fef_status fef_create(const fef_geometry* g, const fef_basis* bs, con
             ppPf[L] = b->alloc<float4>(n, "prim pairs");
             ppPr[L] = b->alloc<float4>(n, "prim pairs");
             d.pp_Pr[L] = ppPr[L];
-            d.pp_Dh32[L] = b->alloc<float>((size_t)nh(L) * n, "hermite density fp32");
+            d.pp_Dh32[L] = b->alloc<float>((size_t)nh(L) * n, "fp32 pair scratch");
             ppPhi[L] = b->alloc<float4>(n, "prim pairs df64");
             ppPlo[L] = b->alloc<float4>(n, "prim pairs df64");
             d.pp_Phi[L] = ppPhi[L];
@@ -1533,7 +1530,6 @@ extern "C" fef_status fef_autotune(fef_ctx* c, int32_t engine, int32_t reps, dou
     const Dev& d = c->dev;
     ck(launch_hermite_density(d, b->D, c->stream), "autotune: hermite density");
     if (engine == 1) {
-        ck(launch_delta_density(d, b->Dh_ref, c->stream), "autotune: delta density");
         ck(launch_fp32_records(d, b->Dh_ref, b->rec_resid, c->stream), "autotune: fp32 records");
     } else if (engine == 2) {
         ck(launch_df_density(d, c->stream), "autotune: df64 density");

@@ -207,6 +207,32 @@ __device__ __forceinline__ void boys_fp32(const float* __restrict__ table, float
     }
 }
 
+// Below the asymptotic switch, the unit-normalised Hermite base of the FP32 core:
+// (2/sqrt(pi)) sqrt(alpha) F_n(T) (-2 alpha)^n, n = 0..L, alpha = pq/(p+q), T = alpha R^2.  Kept out
+// of line so that the common (asymptotic) path of the quartet loop carries none of its instructions.
+template <int L>
+struct Base32 {
+    float v[L + 1];
+};
+template <int L>
+__device__ __noinline__ Base32<L> fp32_table_base(const float* __restrict__ boys32, float pq, float sq, float R2)
+{
+    Base32<L> b;
+    const float r = rsqrt_nr(sq);
+    const float alpha = pq * (r * r);
+    float F[L + 1];
+    boys_fp32<L>(boys32, alpha * R2, F);
+    const float sa = alpha * rsqrt_nr(alpha);
+    float pre = fmaf(kTwoOverSqrtPiHi, sa, kTwoOverSqrtPiLo * sa);
+    const float m2a = -2.0f * alpha;
+#pragma unroll
+    for (int n = 0; n <= L; ++n) {
+        b.v[n] = pre * F[n];
+        pre *= m2a;
+    }
+    return b;
+}
+
 // 1/sqrt(x) in FP64 from an FP32 estimate s of relative error e0 (up to ~1e-5): one step of the
 // third-order iteration y = s (1 + e/2 + 3 e^2/8), e = 1 - x s^2 (the binomial series of (1 - e)^{-1/2}
 // to second order), truncation error 5 e0^3 / 16, below the FP64 resolution.  Five FP64 operations.

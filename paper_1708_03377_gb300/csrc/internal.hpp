@@ -76,7 +76,7 @@ struct Dev {
     double* pp_Dh[kClasses];
     double* pp_Jh[kClasses];
     const float4* pp_Pr[kClasses];   // FP32 (P - anchor of the fragment, p) for the mixed J-engine
-    float* pp_Dh32[kClasses];        // FP32 Hermite density difference D_P - D_P^ref (mixed builds)
+    float* pp_Dh32[kClasses];        // FP32 scratch of nh(L) floats per pair (learned-start descriptors)
     const double* pp_rp[kClasses];   // p^{-1/2} per primitive pair (asymptotic J-engine path)
     double* pp_u[kClasses];          // FP64 J-engine weights u = p^{-1/2} D_P (SoA like pp_Dh), per build
     const int* pp_perm[kClasses];    // bra order of the J-engine: each fragment's class range sorted by p
@@ -174,7 +174,6 @@ cudaError_t launch_class_qmin(const Dev& d, float* qmin, cudaStream_t s);
 cudaError_t launch_fp32_records(const Dev& d, double* const Dh_ref[kClasses], double* resid, cudaStream_t s);
 cudaError_t launch_boys_table32(const double* table64, float* table32, cudaStream_t s);
 // Dh32 = float(Dh - Dh_ref) for every class
-cudaError_t launch_delta_density(const Dev& d, double* const Dh_ref[kClasses], cudaStream_t s);
 cudaError_t launch_one_electron(const Dev& d, double* S, double* h, cudaStream_t s);
 // far field (pairs beyond the cutoff): moment integrals about each fragment's centroid (10 n^2 at
 // 10 frag_moff), per build the fragments' multipoles, the far potentials and the Fock/omega terms,
@@ -220,7 +219,7 @@ cudaError_t launch_orthogonaliser(const Dev& d, const double* S, double* X, int*
                                   cudaStream_t s, double* Sh = nullptr, double* Sih = nullptr,
                                   double* ws = nullptr);
 cudaError_t launch_hermite_density(const Dev& d, const double* D, cudaStream_t s);
-// mode 0: FP64 J-engine on pp_Dh; mode 1: FP32-core J-engine on pp_Dh32; mode 2: float-float
+// mode 0: FP64 J-engine on pp_Dh; mode 1: FP32-core J-engine on the FP32 records; mode 2: float-float
 // J-engine on pp_udf for the s/p classes, FP64 for the rest.  All add into the FP64 accumulators
 // pp_Jh.
 cudaError_t launch_jengine(const Dev& d, const int2* tiles[kClasses][kClasses], const int* n_tiles, double tau,

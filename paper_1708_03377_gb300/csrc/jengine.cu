@@ -362,94 +362,6 @@ __device__ __forceinline__ void jtile_fp64(const Dev& d, const int2 tl, const in
     }
 }
 
-// Mixed-precision core for the d-shell register classes (L_P = 3, 4): the contraction on the FP32
-// Hermite density difference Dh32 = D_P - D_P^ref, with FP32 geometry (centres relative to each
-// fragment's first atom plus the FP64-computed anchor offset), FP32 Boys, R recursion and
-// contractions.  The bra field is flushed to FP64 registers every 16 ket pairs and all global
-// accumulation is FP64 (atomics on pp_Jh).  Bra lanes in natural order.
-template <int LP, int LQ>
-__device__ __forceinline__ void jtile_fp32_dclass(const Dev& d, const int2 tl, const int kb, const int ke,
-                                                  const float tau, const int lane, const KetBuf32& kbuf)
-{
-    constexpr int NP = nh(LP), NQ = nh(LQ), L = LP + LQ, NR = nh(LP + LQ);
-    constexpr int kBatch = 32 / NQ;
-    const int pr = tl.x >> 1;
-    const int x = (tl.x & 1) ? d.pair_y[pr] : d.pair_x[pr];
-    const int y = (tl.x & 1) ? d.pair_x[pr] : d.pair_y[pr];
-    const double* ax = d.atom_xyz + 3 * d.frag_atom0[x];
-    const double* ay = d.atom_xyz + 3 * d.frag_atom0[y];
-    const float ox = (float)(ax[0] - ay[0]), oy = (float)(ax[1] - ay[1]), oz = (float)(ax[2] - ay[2]);
-    const int bra_end = d.frag_pp0[x * kClasses + LP] + d.frag_npp[x * kClasses + LP];
-    const int Pg = tl.y + lane;
-    const bool valid = Pg < bra_end;
-    const int Pl = valid ? Pg : tl.y;
-    const int nP = d.n_pp[LP], nQ = d.n_pp[LQ];
-    const float4 Pr = d.pp_Pr[LP][Pl];
-    const float qP = valid ? d.pp_Q[LP][Pl] : 0.0f;
-    float DP[NP], JP[NP];
-    double JP64[NP];
-#pragma unroll
-    for (int i = 0; i < NP; ++i) {
-        DP[i] = valid ? d.pp_Dh32[LP][(size_t)i * nP + Pl] : 0.0f;
-        JP[i] = 0.0f;
-        JP64[i] = 0.0;
-    }
-    const int kc = d.frag_pp0[y * kClasses + LQ];
-    const int k0 = kc + kb;
-    const int k1 = kc + min(ke, d.frag_npp[y * kClasses + LQ]);
-    const float4* __restrict__ QPr = d.pp_Pr[LQ];
-    const float* __restrict__ QQ = d.pp_Q[LQ];
-    const float* __restrict__ QD = d.pp_Dh32[LQ];
-    double* __restrict__ QJ = d.pp_Jh[LQ];
-    int since_flush = 0;
-    int cnt = 0;  // kets staged in kbuf
-    for (int k = k0; k < k1; ++k) {
-        const float qQ = __ldg(QQ + k);
-        const bool keep = qP * qQ >= tau;
-        if (!__any_sync(0xffffffffu, keep)) continue;
-        const float4 Qr = __ldg(QPr + k);
-        float DQ[NQ];
-#pragma unroll
-        for (int j = 0; j < NQ; ++j) DQ[j] = __ldg(QD + (size_t)j * nQ + k);
-        const float X = (Pr.x - Qr.x) + ox, Y = (Pr.y - Qr.y) + oy, Z = (Pr.z - Qr.z) + oz;
-        const float R2 = fmaf(X, X, fmaf(Y, Y, Z * Z));
-        const float r = rsqrt_nr(Pr.w + Qr.w);
-        const float alpha = Pr.w * Qr.w * (r * r);
-        float F[L + 1];
-        boys_fp32<L>(d.boys32, alpha * R2, F);
-        float base[L + 1];
-        float pre = keep ? r : 0.0f;
-        const float m2a = -2.0f * alpha;
-#pragma unroll
-        for (int n = 0; n <= L; ++n) {
-            base[n] = pre * F[n];
-            pre *= m2a;
-        }
-        float R[NR];
-        md_R<L, float>(R, base, X, Y, Z);
-        hermite_bra<NP, NQ, float>(R, DQ, JP);
-        hermite_ket_stage32<NP, NQ>(R, DP, kbuf, cnt, lane);
-        if (lane == 0) kbuf.k[cnt] = k;
-        if (++cnt == kBatch) {
-            ketbuf_flush32<NQ>(kbuf, cnt, QJ, (size_t)nQ, lane);
-            cnt = 0;
-        }
-        if (++since_flush == 16) {
-            since_flush = 0;
-#pragma unroll
-            for (int i = 0; i < NP; ++i) {
-                JP64[i] += f2d(JP[i]);
-                JP[i] = 0.0f;
-            }
-        }
-    }
-    if (cnt > 0) ketbuf_flush32<NQ>(kbuf, cnt, QJ, (size_t)nQ, lane);
-    if (valid) {
-#pragma unroll
-        for (int i = 0; i < NP; ++i) atomicAdd(d.pp_Jh[LP] + (size_t)i * nP + Pg, JP64[i] + f2d(JP[i]));
-    }
-}
-
 // The ket-side field of a batch of nk consecutive kets of the FP32 core: the lane owning a (ket,
 // component) slot sums its column over the 32 bra lanes, multiplies by the ket's scale k = k_hi + k_lo
 // (kept as a float pair so that its rounding does not repeat in every partner's contribution) and adds
@@ -484,33 +396,7 @@ __device__ __forceinline__ void load_weights(const float* __restrict__ p, float*
     });
 }
 
-// Below the asymptotic switch, the unit-normalised Hermite base of the FP32 core:
-// (2/sqrt(pi)) sqrt(alpha) F_n(T) (-2 alpha)^n, n = 0..L, alpha = pq/(p+q), T = alpha R^2.  Kept out
-// of line so that the common (asymptotic) path of the quartet loop carries none of its instructions.
-template <int L>
-struct Base32 {
-    float v[L + 1];
-};
-template <int L>
-__device__ __noinline__ Base32<L> fp32_table_base(const float* __restrict__ boys32, float pq, float sq, float R2)
-{
-    Base32<L> b;
-    const float r = rsqrt_nr(sq);
-    const float alpha = pq * (r * r);
-    float F[L + 1];
-    boys_fp32<L>(boys32, alpha * R2, F);
-    const float sa = alpha * rsqrt_nr(alpha);
-    float pre = fmaf(kTwoOverSqrtPiHi, sa, kTwoOverSqrtPiLo * sa);
-    const float m2a = -2.0f * alpha;
-#pragma unroll
-    for (int n = 0; n <= L; ++n) {
-        b.v[n] = pre * F[n];
-        pre *= m2a;
-    }
-    return b;
-}
-
-// Mixed-precision core for the s/p classes (L_P, L_Q <= 2), on the weights u = p^{-1/2} (D_P - D_P^ref)
+// Mixed-precision core for the register classes (L_P + L_Q <= 4), on the weights u = p^{-1/2} (D_P - D_P^ref)
 // of the FP32 records.  With R' the Hermite integrals of the unit-normalised Coulomb kernel
 // (R = (sqrt(pi)/2) p^{-1/2} q^{-1/2} R'; R' of the point multipoles, derivatives of 1/R, beyond the
 // asymptotic switch), J_P = k_P sum_Q R' u_Q and J_Q = k_Q sum_P R' u_P with k = (sqrt(pi)/2) p^{-1/2}.
@@ -686,30 +572,26 @@ __device__ __forceinline__ void jtile_fp32_sp(const Dev& d, const int x, const i
     }
 }
 
-// FP32-core tile: d-shell register classes (L_P >= 3) on the legacy Dh32 path; s/p classes on the
-// records with B bra pairs per lane, the Schwarz test only where some quartet of the tile can fail it.
+// FP32-core tile of a register class (L_P + L_Q <= 4, d-shell classes included) on the records with B
+// bra pairs per lane, the Schwarz test only where some quartet of the tile can fail it.
 template <int LP, int LQ, int B = 1>
 __device__ __forceinline__ void jtile_fp32(const Dev& d, const int2 tl, const int kb, const int ke, const float tau,
                                            const int lane, const KetBuf32& kbuf)
 {
-    if constexpr (LP >= 3) {
-        jtile_fp32_dclass<LP, LQ>(d, tl, kb, ke, tau, lane, kbuf);
-    } else {
-        const int pr = tl.x >> 1;
-        const int x = (tl.x & 1) ? d.pair_y[pr] : d.pair_x[pr];
-        const int y = (tl.x & 1) ? d.pair_x[pr] : d.pair_y[pr];
-        const int bra_end = d.frag_pp0[x * kClasses + LP] + d.frag_npp[x * kClasses + LP];
-        float qmin = 3.0e38f;
+    const int pr = tl.x >> 1;
+    const int x = (tl.x & 1) ? d.pair_y[pr] : d.pair_x[pr];
+    const int y = (tl.x & 1) ? d.pair_x[pr] : d.pair_y[pr];
+    const int bra_end = d.frag_pp0[x * kClasses + LP] + d.frag_npp[x * kClasses + LP];
+    float qmin = 3.0e38f;
 #pragma unroll
-        for (int b = 0; b < B; ++b)
-            if (tl.y + 32 * b + lane < bra_end) qmin = fminf(qmin, d.pp_Q[LP][d.pp_perm[LP][tl.y + 32 * b + lane]]);
+    for (int b = 0; b < B; ++b)
+        if (tl.y + 32 * b + lane < bra_end) qmin = fminf(qmin, d.pp_Q[LP][d.pp_perm[LP][tl.y + 32 * b + lane]]);
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) qmin = fminf(qmin, __shfl_xor_sync(0xffffffffu, qmin, o));
-        if (qmin * __ldg(d.fc_qmin + y * kClasses + LQ) < tau)
-            jtile_fp32_sp<LP, LQ, B, true>(d, x, y, tl.y, kb, ke, tau, lane, kbuf);
-        else
-            jtile_fp32_sp<LP, LQ, B, false>(d, x, y, tl.y, kb, ke, tau, lane, kbuf);
-    }
+    for (int o = 16; o > 0; o >>= 1) qmin = fminf(qmin, __shfl_xor_sync(0xffffffffu, qmin, o));
+    if (qmin * __ldg(d.fc_qmin + y * kClasses + LQ) < tau)
+        jtile_fp32_sp<LP, LQ, B, true>(d, x, y, tl.y, kb, ke, tau, lane, kbuf);
+    else
+        jtile_fp32_sp<LP, LQ, B, false>(d, x, y, tl.y, kb, ke, tau, lane, kbuf);
 }
 
 // Ket chunk c of nchunk of a per-class launch: partner offsets [c chunk, (c + 1) chunk), or the whole
@@ -911,27 +793,6 @@ cudaError_t launch_jengine(const Dev& d, const int2* tiles[kClasses][kClasses], 
     FEF_J(3, 0); FEF_J(3, 1); FEF_J(4, 0);
 #undef FEF_J
     return launch_jengine_big(d, tiles, n_tiles, ft, fp32, s);  // classes with L_P + L_Q >= 5
-}
-
-// Dh32 = float(Dh - Dh_ref): the Hermite density of D - D_ref (linear in D).
-__global__ void k_delta_density(const double* __restrict__ Dh, const double* __restrict__ ref, float* out, size_t n)
-{
-    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
-        out[i] = (float)(Dh[i] - ref[i]);
-}
-
-cudaError_t launch_delta_density(const Dev& d, double* const Dh_ref[kClasses], cudaStream_t s)
-{
-    // read only by the FP32 kernels of the d-shell classes (the s/p classes use the FP32 records)
-    if (d.max_l <= 1) return cudaSuccess;
-    for (int L = 0; L < kClasses; ++L) {
-        size_t n = (size_t)nh(L) * d.n_pp[L];
-        if (n == 0) continue;
-        k_delta_density<<<(unsigned)std::min<size_t>((n + 255) / 256, 2048), 256, 0, s>>>(d.pp_Dh[L], Dh_ref[L],
-                                                                                       d.pp_Dh32[L], n);
-        note_launches(1);
-    }
-    return cudaGetLastError();
 }
 
 // FP32-core records (layout: rec32_len in internal.hpp), one thread per primitive pair of class L:

@@ -23,9 +23,11 @@ __host__ __device__ constexpr int big_slice()  // Reals per warp: R slices of 32
     return 32 * nh(LP + LQ) + ((nh(LQ) + 1) & ~1);
 }
 
+// The ket-side field of the FP32 core is scaled by the ket's k = k_hi + k_lo (kQ, a float pair) as it
+// leaves FP32; the FP64 core passes (1, 0).
 template <int NP, int NQ, typename Real, typename RArr>
 __device__ __forceinline__ void contract_big(RArr R, const Real* DP, const Real* DQ, Real* JP,
-                                             double* __restrict__ QJ, size_t nQ, int k, int lane)
+                                             double* __restrict__ QJ, size_t nQ, int k, int lane, float2 kQ)
 {
     static_for<NP>([&](auto I) {
         constexpr TUV a = htuv(decltype(I)::value);
@@ -66,13 +68,22 @@ __device__ __forceinline__ void contract_big(RArr R, const Real* DP, const Real*
         if (lane == 0)
             static_for<CH>([&](auto Jj) {
                 constexpr int j = j0 + decltype(Jj)::value;
-                if constexpr (j < NQ) atomicAdd(QJ + (size_t)j * nQ + k, f2d(sq[decltype(Jj)::value]));
+                if constexpr (j < NQ) {
+                    if constexpr (std::is_same<Real, float>::value)
+                        atomicAdd(QJ + (size_t)j * nQ + k,
+                                  f2d(fmaf(sq[decltype(Jj)::value], kQ.y, sq[decltype(Jj)::value] * kQ.x)));
+                    else
+                        atomicAdd(QJ + (size_t)j * nQ + k, f2d(sq[decltype(Jj)::value]));
+                }
             });
     });
 }
 
-// Real = double: full FP64 build on pp_Dh.  Real = float: the mixed-precision core on pp_Dh32 with
-// FP32 geometry relative to each fragment's first atom, flushed to FP64 every 16 ket pairs.
+// Real = double: full FP64 build on pp_Dh.  Real = float: the FP32 core on the FP32 records (the same
+// as the register classes of jengine.cu: weights u = p^{-1/2} (D_P - D_P^ref) with charge-conserving
+// rounding, the unit-normalised Hermite integrals R' with the point-multipole form beyond the Boys
+// switch, each bra centre relative to the ket fragment's first atom, the scale factors
+// k = (sqrt(pi)/2) p^{-1/2} applied as float pairs), the bra field flushed to FP64 every 16 ket pairs.
 // One warp-tile (32 bra primitive pairs from tl.y) against the ket pairs [kb, ke) (offsets in the
 // partner's class range); sm = this warp's shared-memory slice of big_slice<LP, LQ>() Reals.
 template <int LP, int LQ, typename Real>
@@ -81,6 +92,7 @@ __device__ __forceinline__ void jtile_big(const Dev& d, const int2 tl, const int
 {
     constexpr bool F32 = std::is_same<Real, float>::value;
     constexpr int NP = nh(LP), NQ = nh(LQ), L = LP + LQ;
+    constexpr int RP = rec32_len(LP), RQ = rec32_len(LQ);
     LaneSlice<Real> R{sm + lane};
     Real* DQ = sm + 32 * nh(L);
     const int pr = tl.x >> 1;
@@ -94,34 +106,35 @@ __device__ __forceinline__ void jtile_big(const Dev& d, const int2 tl, const int
     const float qP = valid ? d.pp_Q[LP][Pl] : 0.0f;
     Real DP[NP], JP[NP];
     double JP64[NP];
+    const double4_32a Pd = d.pp_P[LP][Pl];
+    float4 Pf{};
+    float px = 0.f, py = 0.f, pz = 0.f, pP = 0.f;
+    double kP = 0.0;  // bra field scale k_hi + k_lo (FP32 core)
+    if constexpr (F32) {
+        const float* __restrict__ brec = d.pp_rec32[LP] + (size_t)Pl * RP;
+        const double* ay = d.atom_xyz + 3 * d.frag_atom0[y];
+        px = (float)(Pd.x - ay[0]);
+        py = (float)(Pd.y - ay[1]);
+        pz = (float)(Pd.z - ay[2]);
+        pP = (float)Pd.w;
+        kP = f2d(brec[4]) + f2d(brec[5]);
+#pragma unroll
+        for (int i = 0; i < NP; ++i) DP[i] = valid ? brec[8 + i] : 0.0f;
+    } else {
+        Pf = d.pp_Pf[LP][Pl];
+#pragma unroll
+        for (int i = 0; i < NP; ++i) DP[i] = valid ? d.pp_Dh[LP][(size_t)i * nP + Pl] : 0.0;
+    }
 #pragma unroll
     for (int i = 0; i < NP; ++i) {
-        if constexpr (F32)
-            DP[i] = valid ? d.pp_Dh32[LP][(size_t)i * nP + Pl] : 0.0f;
-        else
-            DP[i] = valid ? d.pp_Dh[LP][(size_t)i * nP + Pl] : 0.0;
         JP[i] = Real(0);
         JP64[i] = 0.0;
-    }
-    // geometry of the bra pair
-    double4_32a Pd{};
-    float4 Pf{}, Pr{};
-    float ox = 0.f, oy = 0.f, oz = 0.f;
-    if constexpr (F32) {
-        const double* ax = d.atom_xyz + 3 * d.frag_atom0[x];
-        const double* ay = d.atom_xyz + 3 * d.frag_atom0[y];
-        ox = (float)(ax[0] - ay[0]);
-        oy = (float)(ax[1] - ay[1]);
-        oz = (float)(ax[2] - ay[2]);
-        Pr = d.pp_Pr[LP][Pl];
-    } else {
-        Pd = d.pp_P[LP][Pl];
-        Pf = d.pp_Pf[LP][Pl];
     }
     const int kc = d.frag_pp0[y * kClasses + LQ];
     const int k0 = kc + kb;
     const int k1 = kc + min(ke, d.frag_npp[y * kClasses + LQ]);
     double* __restrict__ QJ = d.pp_Jh[LQ];
+    const float* __restrict__ QR = d.pp_rec32[LQ];
     int since_flush = 0;
     for (int k = k0; k < k1; ++k) {
         const float qQ = __ldg(d.pp_Q[LQ] + k);
@@ -130,27 +143,35 @@ __device__ __forceinline__ void jtile_big(const Dev& d, const int2 tl, const int
         __syncwarp();
         for (int j = lane; j < NQ; j += 32) {
             if constexpr (F32)
-                DQ[j] = __ldg(d.pp_Dh32[LQ] + (size_t)j * nQ + k);
+                DQ[j] = __ldg(QR + (size_t)k * RQ + 8 + j);
             else
                 DQ[j] = __ldg(d.pp_Dh[LQ] + (size_t)j * nQ + k);
         }
         __syncwarp();
         Real base[L + 1];
         Real X, Y, Z;
+        float2 kQ = make_float2(1.0f, 0.0f);
         if constexpr (F32) {
-            const float4 Qr = __ldg(d.pp_Pr[LQ] + k);
-            X = (Pr.x - Qr.x) + ox;
-            Y = (Pr.y - Qr.y) + oy;
-            Z = (Pr.z - Qr.z) + oz;
-            const float r = rsqrt_nr(Pr.w + Qr.w);
-            const float alpha = Pr.w * Qr.w * (r * r);
-            float F[L + 1];
-            boys_fp32<L>(d.boys32, alpha * fmaf(X, X, fmaf(Y, Y, Z * Z)), F);
-            float pre = keep ? r : 0.0f;
+            const float4 q0 = __ldg(reinterpret_cast<const float4*>(QR + (size_t)k * RQ));
+            kQ = __ldg(reinterpret_cast<const float2*>(QR + (size_t)k * RQ + 4));
+            X = px - q0.x;
+            Y = py - q0.y;
+            Z = pz - q0.z;
+            const float R2 = fmaf(X, X, fmaf(Y, Y, Z * Z));
+            const float pq = pP * q0.w, sq = pP + q0.w;
+            // point multipoles beyond the switch (R'^{(n)} = (-1)^n (2n-1)!! / R^{2n+1}); table below it
+            const float yv = keep ? rsqrt_nr(R2) : 0.0f;
+            const float ny2 = -(yv * yv);
+            base[0] = yv;
 #pragma unroll
-            for (int n = 0; n <= L; ++n) {
-                base[n] = pre * F[n];
-                pre *= -2.0f * alpha;
+            for (int n = 0; n < L; ++n) base[n + 1] = base[n] * (float(2 * n + 1) * ny2);
+            const bool asym = pq * R2 >= kFp32SwitchHigh * sq;
+            if (!__all_sync(0xffffffffu, asym)) {
+                if (!asym) {
+                    const Base32<L> t = fp32_table_base<L>(d.boys32, pq, sq, R2);
+#pragma unroll
+                    for (int n = 0; n <= L; ++n) base[n] = keep ? t.v[n] : 0.0f;
+                }
             }
         } else {
             const double4_32a Qd = d.pp_P[LQ][k];
@@ -172,7 +193,7 @@ __device__ __forceinline__ void jtile_big(const Dev& d, const int2 tl, const int
             }
         }
         md_R<L, Real>(R, base, X, Y, Z);
-        contract_big<NP, NQ, Real>(R, DP, DQ, JP, QJ, (size_t)nQ, k, lane);
+        contract_big<NP, NQ, Real>(R, DP, DQ, JP, QJ, (size_t)nQ, k, lane, kQ);
         if constexpr (F32) {
             if (++since_flush == 16) {
                 since_flush = 0;
@@ -186,7 +207,10 @@ __device__ __forceinline__ void jtile_big(const Dev& d, const int2 tl, const int
     }
     if (valid) {
 #pragma unroll
-        for (int i = 0; i < NP; ++i) atomicAdd(d.pp_Jh[LP] + (size_t)i * nP + Pg, JP64[i] + f2d(JP[i]));
+        for (int i = 0; i < NP; ++i) {
+            const double j = JP64[i] + f2d(JP[i]);
+            atomicAdd(d.pp_Jh[LP] + (size_t)i * nP + Pg, F32 ? j * kP : j);
+        }
     }
 }
 

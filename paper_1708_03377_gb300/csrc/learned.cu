@@ -84,8 +84,7 @@ __device__ __forceinline__ void pair_potential32(const float* __restrict__ boys3
 }
 
 // FP32 Hermite densities of the current densities for the descriptors, Dt = Dh p / (2 pi^{5/2})
-// (Dh holds D K c 2 pi^{5/2} / p), into the FP32 scratch pp_Dh32 (otherwise read only by the FP32
-// kernels of d-shell classes, which rebuild it in every FP32-core build).
+// (Dh holds D K c 2 pi^{5/2} / p), into the FP32 scratch pp_Dh32.
 __global__ void k_descriptor_density(Dev d, int L)
 {
     const int npp = d.n_pp[L];
