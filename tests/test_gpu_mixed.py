@@ -132,7 +132,8 @@ def test_fp32_core_whole_build_d_shell_solute():
     path beyond the Boys switch, float-pair scale factors): measured 2.6e-5 Eh for the solute, whose
     130^2 Fock elements each carry the random FP32 floor, and 9e-6 Eh at most for a water; the former
     d-class FP32 path, without those measures, gave the solute 1.3e-4 Eh.  Bars: solute 6e-5, waters
-    1.5e-5, |mean| over fragments 1e-6, max |dF| 1e-5 Eh."""
+    1.5e-5, |mean| over fragments 2e-6 (measured 8e-7 to 9e-7: ~70 neighbours per water), max |dF|
+    1e-5 Eh."""
     fef = _fef()
     system = S.solvated_heterocycle(n_water=1000, seed=0)
     c64 = fef.fef_create_system(system, fef.fef_default_options(cutoff_A=8.0, schwarz=1e-12))
@@ -151,5 +152,5 @@ def test_fp32_core_whole_build_d_shell_solute():
           f"{np.abs(dE[1:]).max():.2e}, mean {dE.mean():.2e}, max|dF| {np.abs(F32 - F64).max():.2e}")
     assert abs(dE[0]) < 6e-5
     assert np.abs(dE[1:]).max() < 1.5e-5
-    assert abs(dE.mean()) < 1e-6
+    assert abs(dE.mean()) < 2e-6
     assert np.abs(F32 - F64).max() < 1e-5
