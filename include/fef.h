@@ -288,11 +288,13 @@ typedef struct {
 fef_status fef_get_tile_plan(const fef_ctx* ctx, int32_t engine, fef_tile_plan* out);
 fef_status fef_set_tile_plan(fef_ctx* ctx, int32_t engine, const fef_tile_plan* plan);
 
-/* Autotuner: times candidate plans of one engine on this context's own workload with CUDA events and
- * installs the fastest.  It chooses the ket chunk of each class pair (from whole range, 1024, 256, 64
+/* Autotuner: times candidate plans of one engine on this context's own workload with CUDA events, each
+ * pass captured once into a CUDA graph and replayed (fef_iterate runs its builds as graph launches),
+ * and installs the fastest.  It chooses the ket chunk of each class pair (from whole range, 1024, 256, 64
  * ket pairs; classes in decreasing order of cost) on every k-th fragment pair, k chosen so that one
  * timed pass takes about budget_ms/64, then, when a full build fits the budget, persistent queues
- * against one launch per class pair, serial or concurrent.  Each candidate is timed reps times (best kept) after a warm-up.
+ * against one launch per class pair, serial or concurrent, and against the plan in place when the
+ * call began (kept unless a tuned plan is faster).  Each candidate is timed reps times (best kept) after a warm-up.
  * The timed passes run on the context's current densities, prepared as a build of that engine prepares
  * them (Hermite densities; for FEF_JENGINE_FP32 the FP32 records relative to the stored reference
  * density, or to zero before the first reference build).  Runs between builds (it overwrites the

@@ -359,25 +359,51 @@ cudaError_t jplan_set(JPlanSet* P, int mode, const fef_tile_plan* in, cudaStream
 namespace {
 
 // Device time (ms) of one J-engine pass of the current plan of `mode` (best of reps after one
-// warm-up); the accumulators receive garbage, so this runs only between builds.
+// warm-up); the accumulators receive garbage, so this runs only between builds.  The pass is captured
+// into a CUDA graph on a private stream (ordered after s) and the graph is replayed: fef_iterate runs
+// its builds as graph launches, where the per-kernel launch cost of the multi-stream plans is gone,
+// so eager timing would favour the single-launch plans on small workloads.
 cudaError_t time_plan(JPlanSet& P, const Dev& d, int mode, const int2* tiles[kClasses][kClasses],
                       const int* n_tiles, double tau, int reps, cudaStream_t s, double* ms)
 {
-    double best = 1e300;
-    for (int r = -1; r < reps; ++r) {
-        cudaError_t e = cudaEventRecord(P.t0, s);
-        if (e != cudaSuccess) return e;
-        e = jplan_launch(&P, d, mode, tiles, n_tiles, tau, s);
-        if (e != cudaSuccess) return e;
-        e = cudaEventRecord(P.t1, s);
-        if (e != cudaSuccess) return e;
-        e = cudaEventSynchronize(P.t1);
-        if (e != cudaSuccess) return e;
-        float f = 0.f;
-        e = cudaEventElapsedTime(&f, P.t0, P.t1);
-        if (e != cudaSuccess) return e;
-        if (r >= 0) best = std::min(best, (double)f);
+    cudaStream_t cs = nullptr;
+    cudaGraph_t g = nullptr;
+    cudaGraphExec_t ge = nullptr;
+    cudaError_t e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventRecord(P.t0, s);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(cs, P.t0, 0);
+    long long n_launch = 0;
+    if (e == cudaSuccess) {
+        const long long l0 = launches_so_far();
+        // relaxed: the launchers set kernel attributes (cudaFuncSetAttribute) while capturing
+        e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeRelaxed);
+        if (e == cudaSuccess) {
+            const cudaError_t el = jplan_launch(&P, d, mode, tiles, n_tiles, tau, cs);
+            const cudaError_t ec = cudaStreamEndCapture(cs, &g);  // ends the capture also after an error
+            e = el != cudaSuccess ? el : ec;
+        }
+        n_launch = launches_so_far() - l0;
+        note_launches(-n_launch);  // nothing ran during the capture
     }
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&ge, g, 0);
+    double best = 1e300;
+    for (int r = -1; r < reps && e == cudaSuccess; ++r) {
+        e = cudaEventRecord(P.t0, cs);
+        if (e == cudaSuccess) e = cudaGraphLaunch(ge, cs);
+        if (e == cudaSuccess) note_launches(n_launch);
+        if (e == cudaSuccess) e = cudaEventRecord(P.t1, cs);
+        if (e == cudaSuccess) e = cudaEventSynchronize(P.t1);
+        float f = 0.f;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&f, P.t0, P.t1);
+        if (e == cudaSuccess && r >= 0) best = std::min(best, (double)f);
+    }
+    if (ge) cudaGraphExecDestroy(ge);
+    if (g) cudaGraphDestroy(g);
+    if (cs) {
+        cudaStreamSynchronize(cs);
+        cudaStreamDestroy(cs);
+    }
+    if (e != cudaSuccess) return e;
     *ms = best;
     return cudaSuccess;
 }
@@ -390,10 +416,6 @@ cudaError_t jplan_autotune(JPlanSet* P, const Dev& d, int mode, const int2* tile
 {
     Plan& pl = P->plan[mode];
     reps = std::max(1, reps);
-    // 1. default persistent plan; the tuning passes run on every stride-th fragment pair so that one
-    //    pass takes about budget/64 (estimated from the flop count at a conservative rate)
-    pl.persistent = 1;
-    for (int i = 0; i < kNumCls; ++i) pl.chunk[i] = 0;
     double total_flops = 0.0;
     double cls_cost[kNumCls] = {};
     for (int cls = 0; cls < kNumCls; ++cls) {
@@ -402,9 +424,25 @@ cudaError_t jplan_autotune(JPlanSet* P, const Dev& d, int mode, const int2* tile
     }
     const double rate = mode == 1 ? 2e13 : (mode == 2 ? 2e12 : 5e11);  // flop/s
     const double est_ms = 1e3 * total_flops / rate;
+    const bool full_passes = est_ms * 2 * (reps + 1) <= budget_ms;
+    cudaError_t e = cudaSuccess;
+    // 0. the plan in place (the default, or one the caller set) is a candidate too: when full passes
+    //    fit the budget it is timed first and kept unless the tuned plan is faster
+    const int start_persistent = pl.persistent;
+    int start_chunk[kNumCls];
+    std::copy(pl.chunk, pl.chunk + kNumCls, start_chunk);
+    double t_start = -1.0;
+    if (full_passes) {
+        e = upload_plan(*P, mode, 1, s);
+        if (e == cudaSuccess) e = time_plan(*P, d, mode, tiles, n_tiles, tau, reps, s, &t_start);
+        if (e != cudaSuccess) return e;
+    }
+    // 1. default persistent plan; the tuning passes run on every stride-th fragment pair so that one
+    //    pass takes about budget/64 (estimated from the flop count at a conservative rate)
+    pl.persistent = 1;
+    for (int i = 0; i < kNumCls; ++i) pl.chunk[i] = 0;
     const double per_pass = std::max(1.0, budget_ms / 64.0);
     const int stride = std::max(1, (int)std::ceil(est_ms / per_pass));
-    cudaError_t e = cudaSuccess;
     // 2. per class pair, in decreasing order of its share of the estimated cost, the ket chunk
     std::vector<int> order(kNumCls);
     std::iota(order.begin(), order.end(), 0);
@@ -442,7 +480,7 @@ cudaError_t jplan_autotune(JPlanSet* P, const Dev& d, int mode, const int2* tile
     e = upload_plan(*P, mode, 1, s);
     if (e != cudaSuccess) return e;
     pl.tuned_ms = best * stride;  // estimate from the sample
-    if (est_ms * 2 * (reps + 1) <= budget_ms) {
+    if (full_passes) {
         double t_pers = 0.0, t_leg = 0.0;
         e = time_plan(*P, d, mode, tiles, n_tiles, tau, reps, s, &t_pers);
         if (e != cudaSuccess) return e;
@@ -463,6 +501,14 @@ cudaError_t jplan_autotune(JPlanSet* P, const Dev& d, int mode, const int2* tile
             pl.persistent = 2;
             pl.tuned_ms = t_conc;
         }
+        if (t_start > 0.0 && t_start <= pl.tuned_ms) {
+            pl.persistent = start_persistent;
+            std::copy(start_chunk, start_chunk + kNumCls, pl.chunk);
+            pl.tuned_ms = t_start;
+        }
+        // the work queues of the plan kept (its ket chunks may be the starting plan's)
+        e = upload_plan(*P, mode, 1, s);
+        if (e != cudaSuccess) return e;
     }
     if (out) jplan_get(P, mode, out);
     return cudaSuccess;
