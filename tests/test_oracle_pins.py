@@ -705,6 +705,36 @@ def test_schwarz_factors_d_fragment(spd_pair):
         assert np.abs(sh[k].schwarz() - Qb).max() < 1e-14 * Qb.max()
 
 
+def test_packed_coulomb_exchange_tensor(spd_pair):
+    """The pair-packed Coulomb-minus-half-exchange tensor that the GPU keeps per fragment,
+    CT[rs][pq] = C[pq][rs] + [la != si] C[pq][(si la)] with C[mn][ls] = (mn|ls) - (ml|ns)/2 over
+    pairs mu <= nu and la <= si (row-major upper triangle), gives G[D] = J[D] - K[D]/2 as one product
+    G_pq = sum_rs CT[rs][pq] D_rs for a symmetric D (against the oracle's plain J and K), and it
+    factorises as CT[rs][pq] = Cs[pq][rs] w_rs with Cs symmetric (w = 1 for la != si, 1/2 for
+    la = si): the identity that lets one triangle of Cs hold the whole tensor."""
+    from oracle.fef import coulomb, exchange
+    sh, full = spd_pair
+    n = sh[0].n_ao
+    eri = full[(0, 0)].reshape(n, n, n, n)
+    iu = np.triu_indices(n)
+    C = eri - 0.5 * eri.transpose(0, 2, 1, 3)
+    rows = C[iu[0], iu[1]]                 # C[pq][l, s]
+    Cpk = rows[:, iu[0], iu[1]]            # C[pq][rs]
+    Cswap = rows[:, iu[1], iu[0]]          # C[pq][(si la)]
+    off = (iu[0] != iu[1]).astype(np.float64)
+    CT = (Cpk + off[None, :] * Cswap).T    # CT[rs][pq]
+    rng = np.random.default_rng(11)
+    A = rng.standard_normal((n, n))
+    D = A + A.T
+    G_ref = coulomb(eri, D) - 0.5 * exchange(eri, D)
+    G_pk = CT.T @ D[iu]
+    assert np.abs(G_pk - G_ref[iu]).max() <= 1e-12 * np.abs(G_ref).max()
+    Cs = Cpk + Cswap
+    w = np.where(off > 0, 1.0, 0.5)
+    assert np.abs(CT - (Cs * w[None, :]).T).max() <= 1e-14 * np.abs(CT).max()
+    assert np.abs(Cs - Cs.T).max() <= 1e-13 * np.abs(Cs).max()
+
+
 def test_quartet_count_brute_force(spd_pair):
     """or_count_quartets equals a brute-force count over all a <= b in x, c <= d in y of
     Q_ab Q_cd >= tau, a quartet whose product equals tau is kept, and every dropped quartet has
