@@ -433,15 +433,17 @@ def mixed_snapshot(n_frag: int = 500, seed: int = 0, weights=(0.85, 0.08, 0.05, 
 
 
 def batch(systems, gap: float = 20.0) -> System:
-    """Independent snapshots in one system: snapshot k is translated along x by k times (the widest
-    snapshot's extent + gap), so that no fragment pair across snapshots falls within a cutoff below
-    gap (A); basis sets are concatenated and re-indexed."""
-    width = max(float(np.ptp(sy.xyz[:, 0])) for sy in systems) + gap
+    """Independent snapshots in one system: each snapshot is translated along x so that its smallest
+    x lies gap (A) beyond the largest x of the one before, so that no atom pair (and no fragment pair)
+    across snapshots is closer than gap; basis sets are concatenated and re-indexed."""
     Z, xyz, foa, boa, charge, bases = [], [], [], [], [], []
     f0 = 0
+    x_end = None
     for k, sy in enumerate(systems):
+        shift = 0.0 if x_end is None else x_end + gap - float(sy.xyz[:, 0].min())
+        x_end = float(sy.xyz[:, 0].max()) + shift
         Z.append(sy.Z)
-        xyz.append(sy.xyz + np.array([k * width, 0.0, 0.0]))
+        xyz.append(sy.xyz + np.array([shift, 0.0, 0.0]))
         foa.append(sy.frag_of_atom + f0)
         boa.append(sy.basis_of_atom + len(bases))
         charge.append(sy.charge)

@@ -42,3 +42,4 @@ def test_traffic_read_only_for_matching_sources(tmp_path, monkeypatch):
     with open(csrc / "common.cuh", "a") as fh:
         fh.write("\n// changed\n")
     assert bench.profile_traffic() is None
+
